@@ -1,0 +1,10 @@
+"""Seeded synthetic graph streams shared by the tests, the benchmark and the oracle checks.
+
+This package only draws inputs (graphs in CSR form and edge-update batches).
+It holds none of the community-detection arithmetic.
+"""
+from .streams import (  # noqa: F401
+    Graph, csr_from_arcs, unit_f64, splitmix64, uniform_u64, planted_partition, rmat_directed,
+    random_small_graph, EdgeStream, planted_stream, rmat_stream, random_batch,
+    powerlaw_planted, powerlaw_stream, config_graph, INSERT, DELETE, REWEIGHT,
+)

@@ -1,0 +1,509 @@
+"""Seeded graph and edge-batch generators.
+
+Every random draw comes from a counter-based SplitMix64 stream (Steele, Lea and
+Flood, "Fast splittable pseudorandom number generators", OOPSLA 2014): the
+i-th value of stream (seed, purpose) is mix64(key + (i + 1) * GOLDEN) with
+key = mix64(seed * GOLDEN + purpose).  The same (seed, purpose, index) gives
+the same value on any machine, so a workload is fully named by its recipe.
+
+Graph shapes stand in for the paper's datasets (its Table III streams, which
+are not available here):
+  * planted_partition: the SBM-style planted-partition graph of the paper's
+    synthetic-recovery study (Sec. IV-E), undirected, int32 weights.
+  * rmat_directed: a directed weighted R-MAT graph with the usual skew
+    (0.57, 0.19, 0.19, 0.05), standing in for the directed social streams.
+  * powerlaw_planted: an LFR-like undirected graph with power-law degrees and
+    community sizes and a mixing fraction.
+Batches are lists of (src, dst, op, w) int32 quadruples with op in
+{INSERT, DELETE, REWEIGHT}; an EdgeStream keeps the current edge set so that
+deletes and reweights always name existing edges and inserts name new ones.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+from typing import Callable, Optional
+
+import numpy as np
+
+INSERT, DELETE, REWEIGHT = 0, 1, 2
+
+_GOLDEN = np.uint64(0x9E3779B97F4A7C15)
+_C1 = np.uint64(0xBF58476D1CE4E5B9)
+_C2 = np.uint64(0x94D049BB133111EB)
+_S30, _S27, _S31, _S32, _S11 = (np.uint64(s) for s in (30, 27, 31, 32, 11))
+
+
+def _mix64(z: np.ndarray) -> np.ndarray:
+    z = (z ^ (z >> _S30)) * _C1
+    z = (z ^ (z >> _S27)) * _C2
+    return z ^ (z >> _S31)
+
+
+def splitmix64(seed: int, purpose: int, idx) -> np.ndarray:
+    """Value number `idx` (array or scalar) of the stream (seed, purpose), uint64."""
+    with np.errstate(over="ignore"):
+        key = _mix64(np.array([seed], dtype=np.uint64) * _GOLDEN + np.uint64(purpose))
+        i = np.asarray(idx, dtype=np.uint64)
+        return _mix64(key + (i + np.uint64(1)) * _GOLDEN)
+
+
+def uniform_u64(seed: int, purpose: int, idx, k) -> np.ndarray:
+    """Integers in [0, k) (k < 2**32, scalar or array) from the stream, int64."""
+    x = splitmix64(seed, purpose, idx) >> _S32
+    with np.errstate(over="ignore"):
+        return ((x * np.asarray(k, dtype=np.uint64)) >> _S32).astype(np.int64)
+
+
+def unit_f64(seed: int, purpose: int, idx) -> np.ndarray:
+    """Doubles in [0, 1) from the top 53 bits of the stream."""
+    return (splitmix64(seed, purpose, idx) >> _S11).astype(np.float64) * (1.0 / 9007199254740992.0)
+
+
+@dataclass
+class Graph:
+    """A weighted graph in CSR form (row_ptr int64[n+1], col int32, w int32).
+
+    Undirected graphs store both arcs of every edge (a symmetric matrix) and
+    a self-loop once."""
+    n: int
+    directed: bool
+    row_ptr: np.ndarray
+    col: np.ndarray
+    w: np.ndarray
+    planted: Optional[np.ndarray] = None
+    name: str = ""
+
+    @property
+    def nnz(self) -> int:
+        return int(self.col.shape[0])
+
+    def arcs(self):
+        src = np.repeat(np.arange(self.n, dtype=np.int64), np.diff(self.row_ptr))
+        return src, self.col.astype(np.int64), self.w.astype(np.int64)
+
+
+def csr_from_arcs(n: int, src, dst, w, directed: bool) -> Graph:
+    """CSR of the arc list; duplicate arcs are merged by summing their weights.
+
+    For an undirected graph each (src, dst) edge is mirrored first."""
+    src = np.asarray(src, dtype=np.int64)
+    dst = np.asarray(dst, dtype=np.int64)
+    w = np.asarray(w, dtype=np.int64)
+    if not directed:
+        off = src != dst
+        src, dst, w = (np.concatenate([src, dst[off]]), np.concatenate([dst, src[off]]),
+                       np.concatenate([w, w[off]]))
+    key = src * n + dst
+    order = np.argsort(key, kind="stable")
+    key = key[order]
+    w = w[order]
+    uniq, start = np.unique(key, return_index=True)
+    wsum = np.add.reduceat(w, start) if len(key) else w
+    s = uniq // n
+    d = uniq % n
+    row_ptr = np.zeros(n + 1, dtype=np.int64)
+    np.add.at(row_ptr, s + 1, 1)
+    row_ptr = np.cumsum(row_ptr)
+    return Graph(n, directed, row_ptr, d.astype(np.int32), wsum.astype(np.int32))
+
+
+def planted_partition(n: int = 10000, block: int = 100, intra: int = 5, inter: int = 1,
+                      wmax: int = 4, seed: int = 1) -> Graph:
+    """Undirected planted partition: n vertices in n/block equal blocks.
+
+    Every vertex draws `intra` partners inside its block and `inter` partners
+    in other blocks, so the mean degree is 2*(intra+inter) with a 5:1
+    intra/inter ratio at the defaults (about 10 intra and 2 inter neighbours,
+    60k edges at n=10,000).  Weights are uniform in 1..wmax; repeated pairs
+    sum their weights; there are no self-loops."""
+    nb = n // block
+    v = np.arange(n, dtype=np.int64)
+    srcs, dsts, ws = [], [], []
+    for j in range(intra):
+        idx = v * (intra + inter) + j
+        r = uniform_u64(seed, 11, idx, block - 1)
+        loc = v % block
+        r = r + (r >= loc)
+        srcs.append(v)
+        dsts.append((v // block) * block + r)
+        ws.append(uniform_u64(seed, 12, idx, wmax) + 1)
+    for j in range(inter):
+        idx = v * (intra + inter) + intra + j
+        ob = uniform_u64(seed, 13, idx, nb - 1)
+        ob = ob + (ob >= v // block)
+        srcs.append(v)
+        dsts.append(ob * block + uniform_u64(seed, 14, idx, block))
+        ws.append(uniform_u64(seed, 12, idx, wmax) + 1)
+    src = np.concatenate(srcs)
+    dst = np.concatenate(dsts)
+    w = np.concatenate(ws)
+    lo, hi = np.minimum(src, dst), np.maximum(src, dst)
+    g = csr_from_arcs(n, lo, hi, w, directed=False)
+    g.planted = (v // block).astype(np.int32)
+    g.name = f"planted n={n} blocks={nb}"
+    return g
+
+
+def _rmat_draw(seed: int, purpose: int, base: int, count: int, scale: int, probs):
+    a, b, c, _ = probs
+    idx0 = np.arange(base, base + count, dtype=np.int64)
+    src = np.zeros(count, dtype=np.int64)
+    dst = np.zeros(count, dtype=np.int64)
+    for lvl in range(scale):
+        u = unit_f64(seed, purpose, idx0 * scale + lvl)
+        sb = (u >= a + b).astype(np.int64)
+        db = (((u >= a) & (u < a + b)) | (u >= a + b + c)).astype(np.int64)
+        src = (src << 1) | sb
+        dst = (dst << 1) | db
+    return src, dst
+
+
+def rmat_directed(scale: int = 20, arcs: int = 1 << 24, probs=(0.57, 0.19, 0.19, 0.05),
+                  wmax: int = 16, seed: int = 2) -> Graph:
+    """Directed weighted R-MAT: arcs are drawn until `arcs` distinct non-loop
+    arcs have appeared; each keeps the first draw's weight, uniform in 1..wmax."""
+    n = 1 << scale
+    got_keys = np.zeros(0, dtype=np.int64)
+    got_first = np.zeros(0, dtype=np.int64)
+    base = 0
+    chunk = max(1024, int(arcs * 1.3))
+    while True:
+        s, d = _rmat_draw(seed, 21, base, chunk, scale, probs)
+        keep = s != d
+        idx = np.arange(base, base + chunk, dtype=np.int64)[keep]
+        key = (s * n + d)[keep]
+        allk = np.concatenate([got_keys, key])
+        allf = np.concatenate([got_first, idx])
+        order = np.argsort(allk, kind="stable")
+        allk, allf = allk[order], allf[order]
+        u, first = np.unique(allk, return_index=True)
+        got_keys, got_first = u, allf[first]
+        base += chunk
+        if len(got_keys) >= arcs:
+            break
+        chunk = max(1024, int((arcs - len(got_keys)) * 2))
+    sel = np.argsort(got_first, kind="stable")[:arcs]
+    key = got_keys[sel]
+    w = uniform_u64(seed, 22, got_first[sel], wmax) + 1
+    g = csr_from_arcs(n, key // n, key % n, w, directed=True)
+    g.name = f"rmat directed scale={scale} arcs={arcs}"
+    return g
+
+
+def random_small_graph(n: int, p: float, directed: bool, wmax: int = 5, seed: int = 0,
+                       self_loops: bool = False) -> Graph:
+    """Erdos-Renyi style graph for tiny brute-force checks."""
+    i, j = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    i, j = i.ravel(), j.ravel()
+    if directed:
+        keep = (i != j) | self_loops
+    else:
+        keep = (i < j) | ((i == j) & self_loops)
+    i, j = i[keep], j[keep]
+    idx = np.arange(len(i))
+    sel = unit_f64(seed, 31, idx) < p
+    w = uniform_u64(seed, 32, idx, wmax) + 1
+    return csr_from_arcs(n, i[sel], j[sel], w[sel], directed)
+
+
+@dataclass
+class EdgeStream:
+    """Current edge set of a graph under a stream of batches.
+
+    Keys are src*n+dst for directed graphs and min*n+max for undirected ones;
+    weights are kept beside them in key order."""
+    n: int
+    directed: bool
+    keys: np.ndarray
+    wts: np.ndarray
+    seed: int
+    batches_made: int = 0
+    draw_counter: int = field(default=0)
+
+    @classmethod
+    def from_graph(cls, g: Graph, seed: int) -> "EdgeStream":
+        s, d, w = g.arcs()
+        if not g.directed:
+            keep = s <= d
+            s, d, w = s[keep], d[keep], w[keep]
+        key = s * g.n + d
+        order = np.argsort(key)
+        return cls(g.n, g.directed, key[order], w[order], seed)
+
+    def has(self, key: np.ndarray) -> np.ndarray:
+        pos = np.searchsorted(self.keys, key)
+        pos = np.minimum(pos, len(self.keys) - 1)
+        return (len(self.keys) > 0) & (self.keys[pos] == key)
+
+    def canon(self, s: np.ndarray, d: np.ndarray) -> np.ndarray:
+        if self.directed:
+            return s * self.n + d
+        return np.minimum(s, d) * self.n + np.maximum(s, d)
+
+    def make_batch(self, n_ins: int, n_del: int, n_rew: int,
+                   sampler: Callable[[int, int], tuple], wmax: int) -> np.ndarray:
+        """Draw one batch and apply it to the edge set.
+
+        sampler(base, count) -> (src, dst) proposes insert endpoints from a
+        counter window; proposals that are loops, existing edges or repeats
+        inside the batch are skipped."""
+        t = self.batches_made
+        seed = self.seed
+        # inserts of new edges
+        ins_s, ins_d, ins_k = [], [], []
+        need = n_ins
+        seen = set()
+        tries = 0
+        while need > 0 and tries < 64:  # a nearly complete graph may have no new edge left
+            tries += 1
+            cnt = max(64, 2 * need)
+            s, d = sampler(self.draw_counter, cnt)
+            self.draw_counter += cnt
+            s = np.asarray(s, dtype=np.int64)
+            d = np.asarray(d, dtype=np.int64)
+            k = self.canon(s, d)
+            ok = (s != d) & ~self.has(k)
+            for si, di, ki in zip(s[ok], d[ok], k[ok]):
+                if need == 0:
+                    break
+                if ki in seen:
+                    continue
+                seen.add(int(ki))
+                ins_s.append(si)
+                ins_d.append(di)
+                ins_k.append(ki)
+                need -= 1
+        ins_w = uniform_u64(seed, 41, np.arange(len(ins_k)) + t * 1_000_003, wmax) + 1
+        # deletes and reweights of distinct existing edges
+        m = len(self.keys)
+        n_old = min(n_del + n_rew, m)
+        pri = splitmix64(seed, 42 + t * 7, np.arange(m))
+        pick = np.argpartition(pri, n_old - 1)[:n_old] if n_old and n_old < m else np.arange(n_old)
+        pick = pick[np.argsort(pri[pick], kind="stable")]
+        dels = pick[:min(n_del, n_old)]
+        rews = pick[min(n_del, n_old):]
+        rew_w = uniform_u64(seed, 43, np.arange(len(rews)) + t * 1_000_003, wmax) + 1
+        flip = uniform_u64(seed, 44, np.arange(len(pick)) + t * 1_000_003, 2)
+
+        def endpoints(idx, fl):
+            key = self.keys[idx]
+            s, d = key // self.n, key % self.n
+            if not self.directed:
+                s, d = np.where(fl == 1, d, s), np.where(fl == 1, s, d)
+            return s, d
+        ds, dd = endpoints(dels, flip[:len(dels)])
+        rs, rd = endpoints(rews, flip[len(dels):])
+        src = np.concatenate([np.array(ins_s, dtype=np.int64), ds, rs])
+        dst = np.concatenate([np.array(ins_d, dtype=np.int64), dd, rd])
+        op = np.concatenate([np.full(len(ins_s), INSERT), np.full(len(ds), DELETE),
+                             np.full(len(rs), REWEIGHT)]).astype(np.int64)
+        w = np.concatenate([ins_w, np.zeros(len(ds), dtype=np.int64), rew_w])
+        order = np.argsort(splitmix64(seed, 45 + t * 7, np.arange(len(src))), kind="stable")
+        batch = np.stack([src[order], dst[order], op[order], w[order]], axis=1).astype(np.int32)
+        # apply to the edge set
+        keep = np.ones(m, dtype=bool)
+        keep[dels] = False
+        wts = self.wts.copy()
+        wts[rews] = rew_w
+        keys = np.concatenate([self.keys[keep], np.array(ins_k, dtype=np.int64)])
+        wts = np.concatenate([wts[keep], ins_w])
+        order = np.argsort(keys, kind="stable")
+        self.keys, self.wts = keys[order], wts[order]
+        self.batches_made += 1
+        return batch
+
+
+def planted_stream(g: Graph, batches: int = 10, size: int = 100, seed: int = 1,
+                   block: int = 100, intra_frac: float = 0.8, wmax: int = 4):
+    """Batches for the planted-partition graph: 70% inserts of new edges
+    (intra_frac of them inside a block), 20% deletes, 10% reweights."""
+    st = EdgeStream.from_graph(g, seed * 1000 + 7)
+    n = g.n
+    nb = n // block
+    n_ins = int(round(size * 0.7))
+    n_del = int(round(size * 0.2))
+    n_rew = size - n_ins - n_del
+
+    def sampler(base, cnt):
+        idx = np.arange(base, base + cnt, dtype=np.int64)
+        v = uniform_u64(seed, 51, idx, n)
+        intra = unit_f64(seed, 52, idx) < intra_frac
+        r = uniform_u64(seed, 53, idx, block - 1)
+        r = r + (r >= v % block)
+        same = (v // block) * block + r
+        ob = uniform_u64(seed, 54, idx, nb - 1)
+        ob = ob + (ob >= v // block)
+        other = ob * block + uniform_u64(seed, 55, idx, block)
+        return v, np.where(intra, same, other)
+    return [st.make_batch(n_ins, n_del, n_rew, sampler, wmax) for _ in range(batches)]
+
+
+def rmat_stream(g: Graph, batches: int = 100, size: int = 10000, seed: int = 2,
+                probs=(0.57, 0.19, 0.19, 0.05), wmax: int = 16, ins_frac: float = 0.8):
+    """Batches for the directed R-MAT graph: ins_frac inserts of new arcs drawn
+    with the same R-MAT skew, the rest deletes of existing arcs."""
+    st = EdgeStream.from_graph(g, seed * 1000 + 9)
+    scale = int(g.n).bit_length() - 1
+    n_ins = int(round(size * ins_frac))
+    n_del = size - n_ins
+
+    def sampler(base, cnt):
+        return _rmat_draw(seed, 61, base, cnt, scale, probs)
+    return [st.make_batch(n_ins, n_del, 0, sampler, wmax) for _ in range(batches)]
+
+
+def random_batch(st: EdgeStream, n_ins: int, n_del: int, n_rew: int, wmax: int, seed: int):
+    """A batch of uniformly random new edges, deletes and reweights (tiny tests)."""
+    n = st.n
+
+    def sampler(base, cnt):
+        idx = np.arange(base, base + cnt, dtype=np.int64)
+        return uniform_u64(seed, 71, idx, n), uniform_u64(seed, 72, idx, n)
+    return st.make_batch(n_ins, n_del, n_rew, sampler, wmax)
+
+
+def config_graph(n: int, degrees: np.ndarray, comm: np.ndarray, mu: float, seed: int) -> Graph:
+    """Configuration-model wiring with a mixing fraction: each vertex splits its
+    stubs into (1-mu) internal and mu external ones; internal stubs are paired
+    at random inside the community, external stubs across the whole graph.
+    Loops are dropped and repeated pairs merged (unit weights are summed)."""
+    deg = degrees.astype(np.int64)
+    ext = np.floor(deg * mu + unit_f64(seed, 81, np.arange(n))).astype(np.int64)
+    ext = np.minimum(ext, deg)
+    internal = deg - ext
+    srcs, dsts = [], []
+    # internal stubs, paired inside each community
+    stubs = np.repeat(np.arange(n, dtype=np.int64), internal)
+    c = comm[stubs].astype(np.int64)
+    pri = splitmix64(seed, 82, np.arange(len(stubs)))
+    order = np.lexsort((pri, c))
+    stubs, c = stubs[order], c[order]
+    starts = np.flatnonzero(np.r_[True, c[1:] != c[:-1]])
+    seg = np.diff(np.r_[starts, len(c)])
+    pos = np.arange(len(c)) - np.repeat(starts, seg)
+    even = (pos % 2 == 0) & (pos + 1 < np.repeat(seg, seg))
+    srcs.append(stubs[even])
+    dsts.append(stubs[np.flatnonzero(even) + 1])
+    # external stubs, paired across the graph
+    stubs = np.repeat(np.arange(n, dtype=np.int64), ext)
+    pri = splitmix64(seed, 83, np.arange(len(stubs)))
+    stubs = stubs[np.argsort(pri, kind="stable")]
+    h = len(stubs) // 2
+    srcs.append(stubs[0:2 * h:2])
+    dsts.append(stubs[1:2 * h:2])
+    s = np.concatenate(srcs)
+    d = np.concatenate(dsts)
+    keep = s != d
+    s, d = s[keep], d[keep]
+    lo, hi = np.minimum(s, d), np.maximum(s, d)
+    g = csr_from_arcs(n, lo, hi, np.ones(len(lo), dtype=np.int64), directed=False)
+    g.planted = comm.astype(np.int32)
+    return g
+
+
+def powerlaw_planted(n: int = 1 << 24, mean_deg: float = 32.0, deg_exp: float = 2.5,
+                     kmax: int = 40000, cmin: int = 50, cmax: int = 50000, comm_exp: float = 1.5,
+                     mu: float = 0.2, seed: int = 3) -> Graph:
+    """LFR-like undirected graph: Pareto degrees (pdf exponent deg_exp, scaled to
+    the requested mean, capped at kmax), power-law community sizes in
+    [cmin, cmax] (exponent comm_exp), mixing fraction mu, unit weights."""
+    u = unit_f64(seed, 91, np.arange(n))
+    a = deg_exp - 1.0
+    xmin = mean_deg * (a - 1.0) / a
+    deg = np.minimum(np.floor(xmin * (1.0 - u) ** (-1.0 / a)), kmax).astype(np.int64)
+    deg = np.maximum(deg, 1)
+    # community sizes: inverse-CDF power law on [cmin, cmax]
+    sizes = []
+    tot = 0
+    i = 0
+    while tot < n:
+        uu = unit_f64(seed, 92, np.arange(i, i + 4096))
+        b = 1.0 - comm_exp
+        s = np.floor((cmin ** b + uu * (cmax ** b - cmin ** b)) ** (1.0 / b)).astype(np.int64)
+        for x in s:
+            if tot >= n:
+                break
+            x = int(min(x, n - tot))
+            sizes.append(x)
+            tot += x
+        i += 4096
+    comm = np.repeat(np.arange(len(sizes), dtype=np.int64), sizes)
+    perm = np.argsort(splitmix64(seed, 93, np.arange(n)), kind="stable")
+    comm = comm[np.argsort(perm, kind="stable")]
+    g = config_graph(n, deg, comm, mu, seed)
+    g.name = f"powerlaw n={n} mean_deg={mean_deg}"
+    return g
+
+
+def powerlaw_stream(g: Graph, size: int, batches: int, seed: int = 3, ins_frac: float = 0.8,
+                    region_factor: int = 4):
+    """Batches whose endpoints lie in a seed region: a BFS ball around a seeded
+    random vertex grown to at least region_factor*size vertices."""
+    n = g.n
+    start = int(uniform_u64(seed, 101, np.array([size]), n)[0])
+    want = max(2, region_factor * size)
+    seen = np.zeros(n, dtype=bool)
+    seen[start] = True
+    front = np.array([start], dtype=np.int64)
+    region = [front]
+    count = 1
+    while count < want and len(front):
+        nb = np.concatenate([g.col[g.row_ptr[v]:g.row_ptr[v + 1]] for v in front]).astype(np.int64) \
+            if len(front) < 4096 else _neighbors(g, front)
+        nb = np.unique(nb)
+        nb = nb[~seen[nb]]
+        seen[nb] = True
+        region.append(nb)
+        count += len(nb)
+        front = nb
+    region = np.concatenate(region)
+    st = EdgeStream.from_graph(g, seed * 1000 + 11 + size)
+    n_ins = int(round(size * ins_frac))
+    n_del = size - n_ins
+
+    def sampler(base, cnt):
+        idx = np.arange(base, base + cnt, dtype=np.int64)
+        return (region[uniform_u64(seed, 102, idx, len(region))],
+                region[uniform_u64(seed, 103, idx, len(region))])
+    out = []
+    for _ in range(batches):
+        out.append(_region_batch(st, n_ins, n_del, sampler, region, seed))
+    return out
+
+
+def _neighbors(g: Graph, vs: np.ndarray) -> np.ndarray:
+    starts = g.row_ptr[vs]
+    lens = g.row_ptr[vs + 1] - starts
+    idx = np.repeat(starts - np.r_[0, np.cumsum(lens)[:-1]], lens) + np.arange(lens.sum())
+    return g.col[idx].astype(np.int64)
+
+
+def _region_batch(st: EdgeStream, n_ins, n_del, sampler, region, seed):
+    """Inserts drawn inside the region; deletes of existing edges with an
+    endpoint in the region."""
+    n = st.n
+    inreg = np.zeros(n, dtype=bool)
+    inreg[region] = True
+    s_all, d_all = st.keys // n, st.keys % n
+    cand = np.flatnonzero(inreg[s_all] | inreg[d_all])
+    t = st.batches_made
+    pri = splitmix64(seed, 104 + t, np.arange(len(cand)))
+    k = min(n_del, len(cand))
+    pick = cand[np.argsort(pri, kind="stable")[:k]]
+    # reuse the generic machinery by temporarily restricting the delete pool
+    keys, wts = st.keys, st.wts
+    sub = EdgeStream(n, st.directed, keys[pick], wts[pick], st.seed, st.batches_made, st.draw_counter)
+    sub.has = st.has  # inserts must be new with respect to the whole graph
+    b = sub.make_batch(n_ins, k, 0, sampler, 1)
+    st.draw_counter = sub.draw_counter
+    # apply to the full edge set
+    keep = np.ones(len(keys), dtype=bool)
+    keep[pick] = False
+    ins = b[b[:, 2] == INSERT]
+    ik = st.canon(ins[:, 0].astype(np.int64), ins[:, 1].astype(np.int64))
+    allk = np.concatenate([keys[keep], ik])
+    allw = np.concatenate([wts[keep], np.ones(len(ik), dtype=np.int64)])
+    order = np.argsort(allk, kind="stable")
+    st.keys, st.wts = allk[order], allw[order]
+    st.batches_made += 1
+    return b
