@@ -1,0 +1,189 @@
+/*
+ * ldl.h -- C ABI of the GB300 LD-Leiden batch-update library.
+ *
+ * The library keeps a weighted graph, its community partition and its Leiden
+ * hierarchy resident on one GPU and updates them batch by batch, following the
+ * paper's Algorithm 1 (LD-Leiden batch update): apply the edge batch, repair
+ * the statistics along the parent chain, then run frontier-restricted move,
+ * refine and aggregate-repair stages level by level.  The partition quality is
+ * the directed weighted modularity of Eq. 1; moves are ranked by the exact
+ * one-step gain of Eq. 2; accepted moves pass the decoupling filter of
+ * Sec. III-E; aggregate levels are repaired by the subtract-add rule of Eq. 3.
+ *
+ * All arithmetic that decides anything is integer (int64 weights and totals,
+ * int128 gains), so results are bit-reproducible and independent of launch
+ * configuration.
+ *
+ * Conventions
+ *   - Vertex ids are int32 in [0, n); n is fixed at creation.
+ *   - Undirected graphs are symmetric weight matrices: an edge {i, j} is the
+ *     two arcs (i, j) and (j, i); a self-loop is one arc.  m = sum_ij w_ij.
+ *   - Level-0 weights are int32 >= 1; aggregate weights and all totals int64.
+ *   - Every entry point returns an ldl_status; LDL_OK is 0.  On any error the
+ *     state is left exactly as it was before the call (a batch is atomic) and
+ *     ldl_last_error() describes the failure.
+ *   - Pointers marked "host" are read or written with ordinary host access;
+ *     "device" pointers are GPU global memory of the context's device.
+ *   - The context owns all device state.  Pointers it returns stay valid until
+ *     the next ldl_apply_batch() or ldl_destroy() on that context.
+ *   - A context is not thread safe; distinct contexts are independent.
+ */
+#ifndef LDL_H
+#define LDL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ldl_ctx ldl_ctx;
+
+typedef enum {
+  LDL_OK = 0,
+  LDL_E_INVALID = 1,    /* malformed argument, op code or CSR */
+  LDL_E_RANGE = 2,      /* vertex id outside [0, n) */
+  LDL_E_NO_EDGE = 3,    /* delete or reweight of an absent edge */
+  LDL_E_NEG_WEIGHT = 4, /* reweight to a negative weight */
+  LDL_E_NOMEM = 5,      /* device allocation failed */
+  LDL_E_CUDA = 6,       /* CUDA runtime error */
+  LDL_E_TIMEOUT = 7,    /* a bounded device wait gave up */
+  LDL_E_OVERFLOW = 8    /* weight above INT32_MAX or m >= 2^50 */
+} ldl_status;
+
+/* Edge-update op codes (Sec. II: every op is a signed weight increment). */
+enum { LDL_INSERT = 0, LDL_DELETE = 1, LDL_REWEIGHT = 2 };
+
+/*
+ * Parameters.  N, L, M, alpha = 1/alpha_inv and beta = 1/beta_inv are the
+ * budgets and thresholds of Algorithm 1; the paper's defaults (Sec. IV-D) are
+ * N=2, L=4, M=5, alpha=0.001, beta=0.01.  gamma = gamma_num/gamma_den is the
+ * Eq. 1 resolution (1 in all of the paper's experiments); both parts must be
+ * in [1, 1024].  M_static is the round budget of the static Leiden run that
+ * builds the initial hierarchy in ldl_create (default 20).  cuda_stream is a
+ * cudaStream_t (NULL: the legacy default stream).
+ */
+typedef struct {
+  int32_t directed;
+  int32_t gamma_num, gamma_den;
+  int32_t N, L, M, M_static;
+  int32_t alpha_inv, beta_inv;
+  void* cuda_stream;
+} ldl_params;
+
+/* Fills p with the defaults above (undirected, gamma = 1). */
+void ldl_default_params(ldl_params* p);
+
+/*
+ * One edge update (Sec. II batch Delta_t): INSERT adds w >= 1 to the weight of
+ * (src, dst) (creating the edge if absent), DELETE removes the edge (w is
+ * ignored), REWEIGHT sets the weight to w >= 0 (0 removes the edge).  Several
+ * updates of one edge in a batch apply in array order.  For undirected graphs
+ * (src, dst) and (dst, src) name the same edge and both arcs change.
+ */
+typedef struct {
+  int32_t src, dst, op, w;
+} ldl_update;
+
+/*
+ * Result of the last batch.  labels is the level-0 partition P_t (device,
+ * int32[n], owned by the context).  changed lists the vertices whose label
+ * differs from before the batch (device, int32[n_changed]).  levels is the
+ * hierarchy height T+1.  The counters describe the work done.
+ */
+typedef struct {
+  const int32_t* labels;
+  int64_t n;
+  const int32_t* changed;
+  int64_t n_changed;
+  int32_t levels;
+  int64_t frontier_nodes[8]; /* |A^r| summed over passes, per level */
+  int64_t edges_scanned;     /* adjacency entries read by BestMove / BestRef */
+  int64_t moves, refine_moves, rejected, rollbacks, rounds, agg_records;
+} ldl_result;
+
+/*
+ * ldl_create -- upload a CSR snapshot and build the initial hierarchy with the
+ * deterministic static Leiden run (every node active, move / refine /
+ * aggregate from singletons, up to level L).
+ *   n        vertices (1 .. 2^31-1)
+ *   nnz      stored entries; row_ptr int64[n+1] with row_ptr[0]=0,
+ *            row_ptr[n]=nnz; col int32[nnz] in [0,n); w int32[nnz] >= 1
+ *            (host).  Repeated (row, col) entries are summed.  Undirected
+ *            CSR must be symmetric.
+ *   out      receives the context on LDL_OK.
+ * Errors: INVALID (bad sizes, params, asymmetric undirected input, w < 1),
+ * RANGE (col outside [0,n)), OVERFLOW (summed weight > INT32_MAX or
+ * m >= 2^50), NOMEM, CUDA.
+ */
+ldl_status ldl_create(const ldl_params* params, int64_t n, int64_t nnz, const int64_t* row_ptr,
+                      const int32_t* col, const int32_t* w, ldl_ctx** out);
+
+/*
+ * ldl_apply_batch -- Algorithm 1 for one batch of `count` updates.
+ *   updates  host array (updates_on_device = 0) or device array (= 1) of
+ *            ldl_update; read only, may be freed after the call.
+ *   out      optional (may be NULL); filled on LDL_OK.
+ * Errors: RANGE, INVALID, NEG_WEIGHT, NO_EDGE, OVERFLOW (the lowest-index
+ * failing update decides; single-update checks come before sequence checks),
+ * NOMEM, CUDA.  On error the state is unchanged.
+ */
+ldl_status ldl_apply_batch(ldl_ctx* ctx, const ldl_update* updates, int64_t count,
+                           int32_t updates_on_device, ldl_result* out);
+
+/* Eq. 1 modularity of the current partition, from the maintained integer
+ * numerator (no graph scan): q = Qnum / (gamma_den * m^2). */
+ldl_status ldl_modularity(const ldl_ctx* ctx, double* q);
+
+/* The exact numerator gamma_den*m^2*Q as two's-complement (hi, lo) halves, and m. */
+ldl_status ldl_modularity_num(const ldl_ctx* ctx, int64_t* q_hi, uint64_t* q_lo, int64_t* m);
+
+/* Frees every device allocation of the context.  NULL is ignored. */
+void ldl_destroy(ldl_ctx* ctx);
+
+/* Text of the last error on ctx (or of the last failed ldl_create when ctx is
+ * NULL); never NULL. */
+const char* ldl_last_error(const ldl_ctx* ctx);
+
+/* ----------------------------------------------------------------------------
+ * Introspection (copies device state to host; for tests and tooling).
+ * -------------------------------------------------------------------------- */
+
+/* Hierarchy height T+1. */
+int32_t ldl_levels(const ldl_ctx* ctx);
+
+/*
+ * Per-node arrays of level r (0 <= r <= T), each of length n (host, caller
+ * allocated; any may be NULL): lab = P^r, par = pi_r (-1 at the top level or
+ * for absent nodes), kout / kin = strengths, cnt = number of level r-1
+ * children (1 at level 0), alive = 1 when the node exists at level r.
+ */
+ldl_status ldl_get_level(const ldl_ctx* ctx, int32_t r, int32_t* lab, int32_t* par,
+                         int64_t* kout, int64_t* kin, int32_t* cnt, uint8_t* alive);
+
+/* Number of stored out-arcs at level r. */
+ldl_status ldl_level_nnz(const ldl_ctx* ctx, int32_t r, int64_t* nnz);
+
+/* Out-adjacency of level r as CSR sorted by (row, col) (host, caller
+ * allocated: row_ptr int64[n+1], col int32[nnz], w int64[nnz]). */
+ldl_status ldl_get_adjacency(const ldl_ctx* ctx, int32_t r, int64_t* row_ptr, int32_t* col,
+                             int64_t* w);
+
+/* Community totals K^out, K^in and internal weight e, int64[n] each (host). */
+ldl_status ldl_get_communities(const ldl_ctx* ctx, int64_t* kout, int64_t* kin, int64_t* e);
+
+/* Device time in milliseconds spent in each stage kernel group during the
+ * last batch: [ingest, repair, expand, bestmove, decouple, commit, refine,
+ * aggregate, pushdown]; `times` has room for 16.  Enabled by ldl_set_timing. */
+ldl_status ldl_stage_times(const ldl_ctx* ctx, double* times);
+ldl_status ldl_set_timing(ldl_ctx* ctx, int32_t on);
+
+/* Test hook: make the k-th device allocation from now on fail (k >= 1);
+ * k = 0 disables.  Lets a test check that NOMEM leaves the state intact. */
+void ldl_debug_fail_alloc_after(int64_t k);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LDL_H */

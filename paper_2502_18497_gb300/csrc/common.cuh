@@ -1,0 +1,214 @@
+// Shared device helpers and internal declarations of the LD-Leiden library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/ldl.h"
+
+typedef __int128 i128;
+typedef int64_t i64;
+typedef uint64_t u64;
+
+#define LDL_NONE (-1)
+#define WARP 32
+
+// ---------------------------------------------------------------- errors
+struct LdlError {
+  ldl_status st;
+  std::string msg;
+};
+
+void ldl_throw(ldl_status st, const std::string& msg);
+void ldl_cuda_check(cudaError_t e, const char* what, const char* file, int line);
+#define CK(x) ldl_cuda_check((x), #x, __FILE__, __LINE__)
+#define CKL(name) ldl_cuda_check(cudaGetLastError(), name, __FILE__, __LINE__)
+
+// ---------------------------------------------------------------- device memory
+// All device allocations of a context go through dalloc/dfree so that a test
+// can make the k-th one fail.
+void* dalloc(size_t bytes);
+void dfree(void* p);
+
+template <class T>
+struct DBuf {
+  T* p = nullptr;
+  int64_t cap = 0;
+  void reserve(int64_t n, cudaStream_t s, bool keep = false) {
+    if (n <= cap) return;
+    int64_t nc = cap ? cap : 1024;
+    while (nc < n) nc = nc * 3 / 2 + 1024;
+    T* q = (T*)dalloc((size_t)nc * sizeof(T));
+    if (keep && p && cap) CK(cudaMemcpyAsync(q, p, (size_t)cap * sizeof(T), cudaMemcpyDeviceToDevice, s));
+    if (p) {
+      CK(cudaStreamSynchronize(s));
+      dfree(p);
+    }
+    p = q;
+    cap = nc;
+  }
+  void exact(int64_t n) {  // allocate exactly n (no growth policy)
+    if (n <= cap) return;
+    T* q = (T*)dalloc((size_t)(n > 0 ? n : 1) * sizeof(T));
+    if (p) dfree(p);
+    p = q;
+    cap = n;
+  }
+  void release() {
+    if (p) dfree(p);
+    p = nullptr;
+    cap = 0;
+  }
+};
+
+// ---------------------------------------------------------------- int128 helpers
+struct I128 {  // two's complement halves; host and device
+  int64_t hi;
+  uint64_t lo;
+};
+
+__host__ __device__ inline i128 i128_of(int64_t hi, uint64_t lo) {
+  return (i128)(((unsigned __int128)(uint64_t)hi << 64) | (unsigned __int128)lo);
+}
+
+// Atomic add of a signed 128-bit value into (hi, lo) halves.
+__device__ inline void atomic_add_i128(I128* dst, i128 v) {
+  if (v == 0) return;
+  uint64_t vl = (uint64_t)v;
+  int64_t vh = (int64_t)(v >> 64);
+  unsigned long long old = atomicAdd((unsigned long long*)&dst->lo, (unsigned long long)vl);
+  uint64_t carry = ((uint64_t)old + vl) < (uint64_t)old ? 1 : 0;
+  int64_t add_hi = vh + (int64_t)carry;
+  if (add_hi != 0) atomicAdd((unsigned long long*)&dst->hi, (unsigned long long)add_hi);
+}
+
+__device__ inline void atomic_add_i64(int64_t* p, int64_t v) {
+  atomicAdd((unsigned long long*)p, (unsigned long long)v);
+}
+
+__device__ inline i128 shfl_down_i128(i128 v, int d) {
+  uint64_t lo = (uint64_t)v;
+  int64_t hi = (int64_t)(v >> 64);
+  lo = __shfl_down_sync(0xffffffffu, lo, d);
+  hi = __shfl_down_sync(0xffffffffu, hi, d);
+  return i128_of(hi, lo);
+}
+
+__device__ inline i128 shfl_i128(i128 v, int src) {
+  uint64_t lo = (uint64_t)v;
+  int64_t hi = (int64_t)(v >> 64);
+  lo = __shfl_sync(0xffffffffu, lo, src);
+  hi = __shfl_sync(0xffffffffu, hi, src);
+  return i128_of(hi, lo);
+}
+
+__device__ inline i128 warp_sum_i128(i128 v) {
+  for (int d = 16; d > 0; d >>= 1) v += shfl_down_i128(v, d);
+  return v;  // valid in lane 0
+}
+
+__device__ inline int64_t warp_sum_i64(int64_t v) {
+  for (int d = 16; d > 0; d >>= 1) v += __shfl_down_sync(0xffffffffu, v, d);
+  return v;
+}
+
+__device__ inline int warp_sum_i32(int v) {
+  for (int d = 16; d > 0; d >>= 1) v += __shfl_down_sync(0xffffffffu, v, d);
+  return v;
+}
+
+// Argmax pair (g, c): larger g wins, equal g goes to the smaller c; "have"
+// marks a valid entry.  Reduced over the whole warp (result in every lane).
+struct Best {
+  i128 g;
+  int32_t c;
+  int32_t have;
+};
+
+__device__ inline bool best_better(const Best& a, const Best& b) {  // a beats b
+  if (!a.have) return false;
+  if (!b.have) return true;
+  if (a.g != b.g) return a.g > b.g;
+  return a.c < b.c;
+}
+
+__device__ inline Best warp_best(Best x) {
+  for (int d = 16; d > 0; d >>= 1) {
+    Best o;
+    o.g = shfl_down_i128(x.g, d);
+    o.c = __shfl_down_sync(0xffffffffu, x.c, d);
+    o.have = __shfl_down_sync(0xffffffffu, x.have, d);
+    if (best_better(o, x)) x = o;
+  }
+  x.g = shfl_i128(x.g, 0);
+  x.c = __shfl_sync(0xffffffffu, x.c, 0);
+  x.have = __shfl_sync(0xffffffffu, x.have, 0);
+  return x;
+}
+
+__device__ inline uint32_t hash32(uint32_t x) {
+  x ^= x >> 16;
+  x *= 0x7feb352dU;
+  x ^= x >> 15;
+  x *= 0x846ca68bU;
+  x ^= x >> 16;
+  return x;
+}
+
+// Append to a list with a dedup stamp: returns true if x was newly added.
+__device__ inline bool stamp_add(int32_t* stamp, int32_t ep, int32_t x, int32_t* list, int32_t* count) {
+  if (stamp[x] == ep) return false;
+  if (atomicExch(&stamp[x], ep) == ep) return false;
+  int32_t pos = atomicAdd(count, 1);
+  list[pos] = x;
+  return true;
+}
+
+inline int div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+inline int grid_for(int64_t n, int block, int cap = 152 * 32) {
+  int64_t g = (n + block - 1) / block;
+  if (g < 1) g = 1;
+  if (g > cap) g = cap;
+  return (int)g;
+}
+
+// ---------------------------------------------------------------- slack CSR
+// Rows in [0, n): row v occupies pool[off[v], off[v]+len[v]) with capacity
+// cap[v].  A row that outgrows its capacity is moved to the end of the pool.
+template <class WT>
+struct SlackCSR {
+  int64_t n = 0;
+  DBuf<int64_t> off;
+  DBuf<int32_t> len, cap;
+  DBuf<int32_t> col;
+  DBuf<WT> w;
+  int64_t pool_top = 0;  // host mirror of the first free pool slot
+  void release() {
+    off.release(); len.release(); cap.release(); col.release(); w.release();
+    pool_top = 0;
+  }
+};
+
+// ---------------------------------------------------------------- scalar block
+// One small device struct read back in a single copy.
+struct DevScalars {
+  I128 dq;          // numerator change of the current mini-batch
+  I128 dp;          // change of sum_C K_out K_in
+  I128 p_old, p_new;
+  int64_t de;       // change of sum_C e_C
+  int64_t dm;       // change of m (batch)
+  int64_t need;     // pool slots needed by relocation
+  int64_t scanned;  // adjacency entries scanned
+  int64_t err_key;  // packed (index << 8 | status) of the first failing update
+  int64_t pool_top;
+  int32_t cnt[16];  // list counters
+  int32_t undecided;
+  int32_t pad;
+};
+
+enum {  // indices into DevScalars::cnt
+  C_LIST0 = 0, C_LIST1, C_LIST2, C_LIST3, C_LIST4, C_LIST5, C_LIST6, C_LIST7,
+  C_CAND, C_REC, C_SEG, C_ACC, C_TC, C_X, C_Y, C_Z
+};

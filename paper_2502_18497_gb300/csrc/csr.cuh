@@ -1,0 +1,30 @@
+// Declarations of the slack-CSR operations (csr.cu).
+#pragma once
+#include "common.cuh"
+#include "prims.cuh"
+
+struct CsrScratch {
+  DBuf<int64_t> seg, oldw, rs, tmp64;
+  DBuf<int32_t> pos, newcap;
+  void release() {
+    seg.release(); oldw.release(); rs.release(); tmp64.release(); pos.release(); newcap.release();
+  }
+};
+
+// Build g over rows [0,n) from sorted unique records (key = row<<bshift|col,
+// vals = weights), with slack_pct percent spare capacity per row.
+template <class WT>
+void csr_build(SlackCSR<WT>& g, int64_t n, const u64* keys, const int64_t* vals, int64_t nrec, int bshift,
+               int slack_pct, CsrScratch& S, Prims& P, cudaStream_t s);
+
+// For each sorted unique record key: pos[i] = entry index in its row (or -1)
+// and oldw[i] = current weight (or 0).  d_nseg is a device counter.
+template <class WT>
+void csr_lookup(const SlackCSR<WT>& g, const u64* keys, int64_t nrec, int bshift, int32_t* pos, int64_t* oldw,
+                CsrScratch& S, Prims& P, cudaStream_t s, int32_t* d_nseg);
+
+// Add delta to each record's entry: absent entries are inserted, entries that
+// reach zero are removed.  Synchronises once (pool growth decision).
+template <class WT>
+void csr_apply(SlackCSR<WT>& g, const u64* keys, const int64_t* delta, int64_t nrec, int bshift, CsrScratch& S,
+               Prims& P, cudaStream_t s, DevScalars* d_sc);

@@ -1,0 +1,127 @@
+// The library context: device-resident hierarchy, community statistics and
+// the scratch of one LD-Leiden instance.
+#pragma once
+#include <vector>
+
+#include "common.cuh"
+#include "csr.cuh"
+#include "prims.cuh"
+
+// Adjacency view of one level: level 0 stores int32 weights, aggregate levels
+// int64.  For undirected graphs the in-view aliases the out-view.
+template <class WT>
+struct Adj {
+  const int64_t* off;
+  const int32_t* len;
+  const int32_t* col;
+  const WT* w;
+};
+
+struct LevelState {
+  SlackCSR<int32_t> out0, in0;   // level 0
+  SlackCSR<int64_t> out, in;     // levels >= 1
+  SlackCSR<int32_t> children;    // keyed by level r+1 node: its level-r members (r < T)
+  DBuf<int32_t> lab, par, cnt;   // P^r, pi_r (NONE = -1), number of level r-1 children
+  DBuf<int64_t> kout, kin;       // strengths (kin aliases kout when undirected)
+  DBuf<uint8_t> alive;
+  DBuf<int32_t> stA, lA;         // frontier A^r (dedup stamp + list)
+  bool allocated = false;
+  void release() {
+    out0.release(); in0.release(); out.release(); in.release(); children.release();
+    lab.release(); par.release(); cnt.release(); kout.release(); kin.release(); alive.release();
+    stA.release(); lA.release();
+    allocated = false;
+  }
+};
+
+// Device counters (indices into ldl_ctx::dcnt).
+enum {
+  K_U = 0, K_S, K_USTAR, K_MV, K_M0, K_D, K_C, K_R, K_R2, K_X, K_T, K_E, K_E2, K_CH, K_CAND, K_B,
+  K_UNDEC, K_SMALL, K_MID, K_LARGE, K_REC, K_CREC, K_NREC, K_ERR, K_TMP, K_TMP2, K_CHG,
+  K_A0 = 32,  // K_A0 + r: |A^r|
+  K_COUNT = 48
+};
+
+struct ldl_ctx {
+  ldl_params prm{};
+  int64_t n = 0;
+  int directed = 0;
+  int bits = 1;          // bits to hold a node id
+  int T = 0;             // top level
+  cudaStream_t s = 0;
+  std::vector<LevelState> lv;
+
+  DBuf<int64_t> Kout, Kin, e;  // community totals (Kin aliases Kout when undirected)
+  int64_t m = 0;               // total weight
+  int64_t E = 0;               // sum_C e_C
+  i128 Psum = 0;               // sum_C K_out K_in
+
+  DevScalars* d_sc = nullptr;
+  int32_t* dcnt = nullptr;
+  int32_t epoch = 0;
+
+  // dedup stamps (one int32 per node id) and lists
+  DBuf<int32_t> stS, stU, stMv, stB, stM0, stD, stC, stR, stX, stT, stE, stCh;
+  DBuf<int32_t> lU, lS, lUstar, lMv, lM0, lD, lC, lR, lR2, lX, lT, lE, lE2, lCh, lChg, lTmp;
+  // candidates and accepted moves
+  DBuf<int32_t> cv, csrc, cdst, cst, bv, bsrc, bdst, best, role;
+  DBuf<int64_t> cghi;
+  DBuf<uint64_t> cglo;
+  // commit / refine scratch
+  DBuf<int32_t> oldlab, par_old, lab_before;
+  DBuf<int64_t> snapKo, snapKi, snapE;
+  // sweep binning
+  DBuf<int32_t> binS, binM, binL;
+  DBuf<int64_t> binLoff, binLsz;
+  DBuf<int32_t> gkeys;
+  DBuf<int64_t> gvals;
+  // records
+  DBuf<u64> rk, rv, tk, tv, rk2, rv2;
+  DBuf<int64_t> rsum, rsum2;
+  DBuf<int32_t> ndx, ndx2;
+  DBuf<int64_t> ndko, ndki, ndko2, ndki2;
+  DBuf<u64> crk, crv, fk;
+  DBuf<ldl_update> upd;
+  Prims P;
+  CsrScratch CS;
+
+  // counters of the last batch
+  ldl_result res{};
+  int64_t frontier[8] = {0};
+  int timing = 0;
+  double stage_ms[16] = {0};
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  std::string err;
+
+  int32_t next_epoch() { return ++epoch; }
+};
+
+// ---------------------------------------------------------------- helpers
+inline Adj<int32_t> adj_out0(ldl_ctx& c) {
+  auto& g = c.lv[0].out0;
+  return Adj<int32_t>{g.off.p, g.len.p, g.col.p, g.w.p};
+}
+inline Adj<int32_t> adj_in0(ldl_ctx& c) {
+  auto& g = c.directed ? c.lv[0].in0 : c.lv[0].out0;
+  return Adj<int32_t>{g.off.p, g.len.p, g.col.p, g.w.p};
+}
+inline Adj<int64_t> adj_out(ldl_ctx& c, int r) {
+  auto& g = c.lv[r].out;
+  return Adj<int64_t>{g.off.p, g.len.p, g.col.p, g.w.p};
+}
+inline Adj<int64_t> adj_in(ldl_ctx& c, int r) {
+  auto& g = c.directed ? c.lv[r].in : c.lv[r].out;
+  return Adj<int64_t>{g.off.p, g.len.p, g.col.p, g.w.p};
+}
+inline int64_t* kin_of(ldl_ctx& c, int r) { return c.directed ? c.lv[r].kin.p : c.lv[r].kout.p; }
+inline int64_t* Kin_of(ldl_ctx& c) { return c.directed ? c.Kin.p : c.Kout.p; }
+
+// host reads of device counters (synchronise)
+int32_t rd_cnt(ldl_ctx& c, int idx);
+void zero_cnt(ldl_ctx& c, int idx);
+void set_cnt(ldl_ctx& c, int idx, int32_t v);
+
+// stage timing
+void stage_begin(ldl_ctx& c);
+void stage_end(ldl_ctx& c, int stage);
+enum { ST_INGEST = 0, ST_REPAIR, ST_EXPAND, ST_BEST, ST_DECOUPLE, ST_COMMIT, ST_REFINE, ST_AGG, ST_PUSH };

@@ -1,0 +1,1080 @@
+// Hierarchy maintenance of Algorithm 1: batch ingest and validation (line 1),
+// statistic repair along the parent chain (line 2, InitFrontier line 3),
+// label push-down after supernode moves, TouchedRefined / dissolve (line 16),
+// and the Eq. 3 subtract-add aggregate repair with NextFrontier (lines 23-24).
+#include "kern.cuh"
+
+namespace {
+
+constexpr int TPB = 256;
+
+#define GRID_STRIDE(i, n) \
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)
+
+// ---------------------------------------------------------------- ingest
+__device__ inline void set_err(unsigned long long* err, int64_t idx, int code) {
+  atomicMin(err, ((unsigned long long)idx << 8) | (unsigned long long)code);
+}
+
+__global__ void k_validate(const ldl_update* u, int64_t cnt, int64_t n, unsigned long long* err) {
+  GRID_STRIDE(i, cnt) {
+    const ldl_update x = u[i];
+    int code = 0;
+    if (x.src < 0 || x.src >= n || x.dst < 0 || x.dst >= n) code = LDL_E_RANGE;
+    else if (x.op != LDL_INSERT && x.op != LDL_DELETE && x.op != LDL_REWEIGHT) code = LDL_E_INVALID;
+    else if (x.op == LDL_INSERT && x.w < 1) code = LDL_E_INVALID;
+    else if (x.op == LDL_REWEIGHT && x.w < 0) code = LDL_E_NEG_WEIGHT;
+    if (code) set_err(err, i, code);
+  }
+}
+
+__global__ void k_upd_keys(const ldl_update* u, int64_t cnt, int bits, int directed, u64* keys, u64* vals) {
+  GRID_STRIDE(i, cnt) {
+    int64_t a = u[i].src, b = u[i].dst;
+    if (!directed && a > b) {
+      int64_t t = a; a = b; b = t;
+    }
+    keys[i] = ((u64)a << bits) | (u64)b;
+    vals[i] = (u64)i;
+  }
+}
+
+__global__ void k_unique_starts(const u64* keys, int64_t n, const int32_t* flag, const int64_t* pos, u64* ukeys,
+                                int64_t* ustart) {
+  GRID_STRIDE(i, n) {
+    if (flag[i]) {
+      ukeys[pos[i]] = keys[i];
+      ustart[pos[i]] = i;
+    }
+  }
+}
+
+// Per edge key: apply its updates in array order to the current weight.
+__global__ void k_seq(const ldl_update* u, int64_t cnt, const u64* vals, const int64_t* ustart, int64_t nu,
+                      const u64* ukeys, const int64_t* oldw, int bits, int directed, int64_t* delta,
+                      unsigned long long* err, int64_t* dm) {
+  GRID_STRIDE(k, nu) {
+    const int64_t s = ustart[k], e = (k + 1 < nu) ? ustart[k + 1] : cnt;
+    const int64_t w0 = oldw[k];
+    int64_t cur = w0;
+    for (int64_t t = s; t < e; ++t) {
+      const int64_t idx = (int64_t)vals[t];
+      const ldl_update x = u[idx];
+      int bad = 0;
+      if (x.op == LDL_INSERT) {
+        cur += x.w;
+        if (cur > INT32_MAX) bad = LDL_E_OVERFLOW;
+      } else if (x.op == LDL_DELETE) {
+        if (cur == 0) bad = LDL_E_NO_EDGE;
+        cur = 0;
+      } else {
+        if (cur == 0) bad = LDL_E_NO_EDGE;
+        cur = x.w;
+      }
+      if (bad) {
+        set_err(err, idx, bad);
+        cur = w0;
+        break;
+      }
+    }
+    const int64_t d = cur - w0;
+    delta[k] = d;
+    if (d) {
+      const u64 key = ukeys[k];
+      const int64_t a = (int64_t)(key >> bits), b = (int64_t)(key & ((((u64)1) << bits) - 1));
+      atomic_add_i64(dm, (directed || a == b) ? d : 2 * d);
+    }
+  }
+}
+
+__global__ void k_emit_arcs(const u64* ukeys, const int64_t* delta, int64_t nu, int bits, int directed, u64* ok,
+                            u64* ov, int32_t* cnt) {
+  GRID_STRIDE(k, nu) {
+    const int64_t d = delta[k];
+    if (!d) continue;
+    const u64 key = ukeys[k];
+    const u64 a = key >> bits, b = key & ((((u64)1) << bits) - 1);
+    int32_t p = atomicAdd(cnt, 1);
+    ok[p] = key;
+    ov[p] = (u64)d;
+    if (!directed && a != b) {
+      p = atomicAdd(cnt, 1);
+      ok[p] = (b << bits) | a;
+      ov[p] = (u64)d;
+    }
+  }
+}
+
+__global__ void k_transpose(const u64* k, const u64* v, int64_t n, int bits, u64* ok, u64* ov) {
+  const u64 mask = (((u64)1) << bits) - 1;
+  GRID_STRIDE(i, n) {
+    ok[i] = ((k[i] & mask) << bits) | (k[i] >> bits);
+    ov[i] = v[i];
+  }
+}
+
+// ---------------------------------------------------------------- repair
+__global__ void k_dirty(const u64* keys, int64_t na, int bits, const int32_t* lab, int32_t* stT, int32_t epT,
+                        int32_t* lT, int32_t* nT) {
+  const u64 mask = (((u64)1) << bits) - 1;
+  GRID_STRIDE(i, na) {
+    stamp_add(stT, epT, lab[keys[i] >> bits], lT, nT);
+    stamp_add(stT, epT, lab[keys[i] & mask], lT, nT);
+  }
+}
+
+// sum over listed communities of K_out * K_in into an int128 accumulator
+__global__ void k_psum(const int32_t* list, const int32_t* nlist, const int64_t* Kout, const int64_t* Kin,
+                       I128* acc) {
+  const int32_t n = *nlist;
+  i128 s = 0;
+  for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const int32_t c = list[k];
+    s += (i128)Kout[c] * Kin[c];
+  }
+  s = warp_sum_i128(s);
+  if ((threadIdx.x & 31) == 0) atomic_add_i128(acc, s);
+}
+
+__global__ void k_stat_arcs(const u64* keys, const int64_t* delta, int64_t na, int bits, int directed,
+                            const int32_t* lab, int64_t* kout, int64_t* kin, int64_t* Kout, int64_t* Kin, int64_t* e,
+                            int64_t* de, int32_t* stA, int32_t epA, int32_t* lA, int32_t* nA) {
+  const u64 mask = (((u64)1) << bits) - 1;
+  int64_t sde = 0;
+  GRID_STRIDE(t, na) {
+    const int32_t i = (int32_t)(keys[t] >> bits), j = (int32_t)(keys[t] & mask);
+    const int64_t d = delta[t];
+    atomic_add_i64(&kout[i], d);
+    if (directed) atomic_add_i64(&kin[j], d);
+    const int32_t ci = lab[i], cj = lab[j];
+    atomic_add_i64(&Kout[ci], d);
+    if (directed) atomic_add_i64(&Kin[cj], d);
+    if (ci == cj) {
+      atomic_add_i64(&e[ci], d);
+      sde += d;
+    }
+    stamp_add(stA, epA, i, lA, nA);
+    stamp_add(stA, epA, j, lA, nA);
+  }
+  if (sde) atomic_add_i64(de, sde);
+}
+
+// Map level-q records through pi_q to level q+1 (records whose endpoint has
+// no parent are dropped).  Optionally adds strengths and marks A^{q+1}.
+__global__ void k_map_records(const u64* keys, const int64_t* vals, int64_t n, int bits, const int32_t* par,
+                              int64_t* kout, int64_t* kin, int directed, u64* ok, u64* ov, int32_t* cnt) {
+  const u64 mask = (((u64)1) << bits) - 1;
+  GRID_STRIDE(t, n) {
+    const int32_t x = par[keys[t] >> bits], y = par[keys[t] & mask];
+    if (x < 0 || y < 0) continue;
+    const int64_t d = vals[t];
+    if (kout) {
+      atomic_add_i64(&kout[x], d);
+      if (directed) atomic_add_i64(&kin[y], d);
+    }
+    const int32_t p = atomicAdd(cnt, 1);
+    ok[p] = ((u64)x << bits) | (u64)y;
+    ov[p] = (u64)d;
+  }
+}
+
+// InitFrontier above level 0: A^{q+1} = pi_q(A^q).
+__global__ void k_map_list(const int32_t* l, const int32_t* n, const int32_t* par, int32_t* stA, int32_t epA,
+                           int32_t* lA, int32_t* nA) {
+  const int32_t m = *n;
+  for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x) {
+    const int32_t p = par[l[k]];
+    if (p >= 0) stamp_add(stA, epA, p, lA, nA);
+  }
+}
+
+// ---------------------------------------------------------------- push-down
+// Children of each listed level-(q+1) node take its label at level q.
+__global__ void k_push(const int32_t* list, const int32_t* nlist, const int32_t* lab_up, Adj<int32_t> ch,
+                       int32_t* lab, int32_t* olist, int32_t* nout, int32_t* stCh, int32_t epCh, int32_t* lCh,
+                       int32_t* nCh, int32_t* lab_before) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int32_t nl = *nlist;
+  for (int64_t t = warp; t < nl; t += nw) {
+    const int32_t x = list[t];
+    const int32_t L = lab_up[x];
+    const int64_t o = ch.off[x];
+    const int32_t l = ch.len[x];
+    for (int32_t k = lane; k < l; k += 32) {
+      const int32_t u = ch.col[o + k];
+      if (stCh) {
+        if (stamp_add(stCh, epCh, u, lCh, nCh)) lab_before[u] = lab[u];
+      }
+      lab[u] = L;
+      if (olist) olist[atomicAdd(nout, 1)] = u;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- dissolve
+__global__ void k_touched(const int32_t* lU, const int32_t* nU, const int32_t* par, int32_t* stD, int32_t epD,
+                          int32_t* lD, int32_t* nD, int32_t* stX, int32_t epX, int32_t* lX, int32_t* nX) {
+  const int32_t n = *nU;
+  for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const int32_t u = lU[k];
+    const int32_t p = par[u];
+    if (p < 0) stamp_add(stD, epD, u, lD, nD);
+    else stamp_add(stX, epX, p, lX, nX);
+  }
+}
+
+__global__ void k_collect(const int32_t* lX, const int32_t* nX, Adj<int32_t> ch, int32_t* stD, int32_t epD,
+                          int32_t* lD, int32_t* nD) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int32_t nl = *nX;
+  for (int64_t t = warp; t < nl; t += nw) {
+    const int32_t x = lX[t];
+    const int64_t o = ch.off[x];
+    const int32_t l = ch.len[x];
+    for (int32_t k = lane; k < l; k += 32) stamp_add(stD, epD, ch.col[o + k], lD, nD);
+  }
+}
+
+__global__ void k_stamp_list(const int32_t* l, const int32_t* n, int32_t* st, int32_t ep) {
+  const int32_t m = *n;
+  for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x) st[l[k]] = ep;
+}
+
+__global__ void k_dissolve(const int32_t* lD, const int32_t* nD, int32_t* par, int32_t* par_old,
+                           const int64_t* kout, const int64_t* kin, int64_t* kout1, int64_t* kin1, int32_t* cnt1,
+                           int directed) {
+  const int32_t n = *nD;
+  for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const int32_t u = lD[k];
+    const int32_t p = par[u];
+    par_old[u] = p;
+    if (p >= 0) {
+      atomic_add_i64(&kout1[p], -kout[u]);
+      if (directed) atomic_add_i64(&kin1[p], -kin[u]);
+      atomicAdd(&cnt1[p], -1);
+    }
+    par[u] = u;
+    atomic_add_i64(&kout1[u], kout[u]);
+    if (directed) atomic_add_i64(&kin1[u], kin[u]);
+    atomicAdd(&cnt1[u], 1);
+  }
+}
+
+__global__ void k_reset_par(const int32_t* lD, int32_t nD, int32_t* par, int64_t* kout1, int64_t* kin1,
+                            int32_t* cnt1, int directed) {
+  for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < nD; k += gridDim.x * blockDim.x) {
+    const int32_t u = lD[k];
+    par[u] = -1;
+    kout1[u] = 0;
+    if (directed) kin1[u] = 0;
+    cnt1[u] = 0;
+  }
+}
+
+// ---------------------------------------------------------------- aggregate
+__global__ void k_changed(const int32_t* lD, const int32_t* nD, const int32_t* par, const int32_t* par_old,
+                          int32_t* stC, int32_t epC, int32_t* lC, int32_t* nC) {
+  const int32_t n = *nD;
+  for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const int32_t u = lD[k];
+    if (par[u] != par_old[u]) stamp_add(stC, epC, u, lC, nC);
+  }
+}
+
+template <class WT>
+__global__ void k_deg_sum(Adj<WT> out, Adj<WT> in, const int32_t* l, const int32_t* n, int64_t* acc) {
+  const int32_t m = *n;
+  int64_t s = 0;
+  for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x)
+    s += (int64_t)out.len[l[k]] + in.len[l[k]];
+  s = warp_sum_i64(s);
+  if ((threadIdx.x & 31) == 0 && s) atomic_add_i64(acc, s);
+}
+
+// Subtract-add records of Eq. 3 for every arc incident to a changed node,
+// each arc counted once (from its changed tail's out-row, or from its changed
+// head's in-row when the tail is unchanged).
+template <class WT>
+__global__ void k_emit(Adj<WT> out, Adj<WT> in, const int32_t* lC, const int32_t* nC, const int32_t* par,
+                       const int32_t* par_old, const int32_t* stC, int32_t epC, int bits, u64* rk, u64* rv,
+                       int32_t* cnt) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int32_t nl = *nC;
+  for (int64_t t = warp; t < nl; t += nw) {
+    const int32_t u = lC[t];
+    const int32_t po = par_old[u], pn = par[u];
+    {
+      const int64_t o = out.off[u];
+      const int32_t l = out.len[u];
+      for (int32_t k = lane; k < l; k += 32) {
+        const int32_t v = out.col[o + k];
+        const int64_t w = (int64_t)out.w[o + k];
+        const bool vc = stC[v] == epC;
+        const int32_t pvo = vc ? par_old[v] : par[v];
+        const int32_t pvn = par[v];
+        if (po >= 0 && pvo >= 0) {
+          const int32_t p = atomicAdd(cnt, 1);
+          rk[p] = ((u64)po << bits) | (u64)pvo;
+          rv[p] = (u64)(-w);
+        }
+        const int32_t p = atomicAdd(cnt, 1);
+        rk[p] = ((u64)pn << bits) | (u64)pvn;
+        rv[p] = (u64)w;
+      }
+    }
+    {
+      const int64_t o = in.off[u];
+      const int32_t l = in.len[u];
+      for (int32_t k = lane; k < l; k += 32) {
+        const int32_t v = in.col[o + k];
+        if (stC[v] == epC) continue;
+        const int64_t w = (int64_t)in.w[o + k];
+        const int32_t pv = par[v];
+        if (po >= 0) {
+          const int32_t p = atomicAdd(cnt, 1);
+          rk[p] = ((u64)pv << bits) | (u64)po;
+          rv[p] = (u64)(-w);
+        }
+        const int32_t p = atomicAdd(cnt, 1);
+        rk[p] = ((u64)pv << bits) | (u64)pn;
+        rv[p] = (u64)w;
+      }
+    }
+  }
+}
+
+// Node records (strength moves between parents) and children-list records.
+__global__ void k_emit_nodes(const int32_t* lC, const int32_t* nC, const int32_t* par, const int32_t* par_old,
+                             const int64_t* kout, const int64_t* kin, int bits, int32_t* ndx, int64_t* ndko,
+                             int64_t* ndki, int32_t* nnd, u64* ck, u64* cv, int32_t* ncr) {
+  const int32_t n = *nC;
+  for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const int32_t u = lC[k];
+    const int32_t po = par_old[u], pn = par[u];
+    if (ndx) {
+      if (po >= 0) {
+        const int32_t p = atomicAdd(nnd, 1);
+        ndx[p] = po;
+        ndko[p] = -kout[u];
+        ndki[p] = -kin[u];
+      }
+      const int32_t p = atomicAdd(nnd, 1);
+      ndx[p] = pn;
+      ndko[p] = kout[u];
+      ndki[p] = kin[u];
+    }
+    if (po >= 0) {
+      const int32_t p = atomicAdd(ncr, 1);
+      ck[p] = ((u64)po << bits) | (u64)u;
+      cv[p] = (u64)(int64_t)-1;
+    }
+    const int32_t p = atomicAdd(ncr, 1);
+    ck[p] = ((u64)pn << bits) | (u64)u;
+    cv[p] = (u64)(int64_t)1;
+  }
+}
+
+__global__ void k_map_nodes(const int32_t* ndx, const int64_t* ndko, const int64_t* ndki, int32_t n,
+                            const int32_t* par, int64_t* kout, int64_t* kin, int directed, int32_t* ox,
+                            int64_t* oko, int64_t* oki, int32_t* cnt) {
+  for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const int32_t x = par[ndx[k]];
+    if (x < 0) continue;
+    atomic_add_i64(&kout[x], ndko[k]);
+    if (directed) atomic_add_i64(&kin[x], ndki[k]);
+    const int32_t p = atomicAdd(cnt, 1);
+    ox[p] = x;
+    oko[p] = ndko[k];
+    oki[p] = ndki[k];
+  }
+}
+
+__global__ void k_exist_cands(const int32_t* lC, const int32_t* nC, const int32_t* par, const int32_t* par_old,
+                              int32_t* stE, int32_t epE, int32_t* lE, int32_t* nE) {
+  const int32_t n = *nC;
+  for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const int32_t u = lC[k];
+    if (par_old[u] >= 0) stamp_add(stE, epE, par_old[u], lE, nE);
+    stamp_add(stE, epE, par[u], lE, nE);
+  }
+}
+
+// Existence at level q: a node with members appears; an emptied node leaves
+// its parent (its weights are already zero), which may empty the parent.
+__global__ void k_exist(const int32_t* lE, const int32_t* nE, const int32_t* cnt, uint8_t* alive, int32_t* par,
+                        int32_t* cnt_up, int bits, u64* ck, u64* cv, int32_t* ncr, int32_t* stE, int32_t epE2,
+                        int32_t* lE2, int32_t* nE2, int32_t* err) {
+  const int32_t n = *nE;
+  for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const int32_t x = lE[k];
+    const int32_t c = cnt[x];
+    if (!alive[x] && c > 0) {
+      alive[x] = 1;
+      if (par && par[x] >= 0) atomicExch(err, 2);
+    } else if (alive[x] && c == 0) {
+      alive[x] = 0;
+      if (par) {
+        const int32_t p = par[x];
+        if (p >= 0) {
+          atomicAdd(&cnt_up[p], -1);
+          const int32_t q = atomicAdd(ncr, 1);
+          ck[q] = ((u64)p << bits) | (u64)x;
+          cv[q] = (u64)(int64_t)-1;
+          par[x] = -1;
+          stamp_add(stE, epE2, p, lE2, nE2);
+        }
+      }
+    }
+  }
+}
+
+__global__ void k_relabel(const int32_t* l, const int32_t* n, const int32_t* par, const int32_t* lab,
+                          int32_t* lab_up) {
+  const int32_t m = *n;
+  for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x) {
+    const int32_t u = l[k];
+    lab_up[par[u]] = lab[u];
+  }
+}
+
+__global__ void k_nf_records(const u64* keys, int64_t n, int bits, const uint8_t* alive, int32_t* stA, int32_t epA,
+                             int32_t* lA, int32_t* nA) {
+  const u64 mask = (((u64)1) << bits) - 1;
+  GRID_STRIDE(t, n) {
+    const int32_t x = (int32_t)(keys[t] >> bits), y = (int32_t)(keys[t] & mask);
+    if (alive[x]) stamp_add(stA, epA, x, lA, nA);
+    if (alive[y]) stamp_add(stA, epA, y, lA, nA);
+  }
+}
+
+__global__ void k_nf_nodes(const int32_t* l, const int32_t* n, const int32_t* par, const int32_t* par_old,
+                           const uint8_t* alive, int32_t* stA, int32_t epA, int32_t* lA, int32_t* nA) {
+  const int32_t m = *n;
+  for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x) {
+    const int32_t u = l[k];
+    const int32_t p = par[u];
+    if (p >= 0 && alive[p]) stamp_add(stA, epA, p, lA, nA);
+    if (par_old) {
+      const int32_t q = par_old[u];
+      if (q >= 0 && alive[q]) stamp_add(stA, epA, q, lA, nA);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- static set-up
+__global__ void k_csr_records(const int64_t* rp, const int32_t* col, const int32_t* w, int64_t n, int bits,
+                              u64* rk, u64* rv, unsigned long long* err) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t v = warp; v < n; v += nw) {
+    const int64_t s = rp[v], e = rp[v + 1];
+    if (e < s) {
+      if (lane == 0) set_err(err, 0, LDL_E_INVALID);
+      continue;
+    }
+    for (int64_t k = s + lane; k < e; k += 32) {
+      const int32_t c = col[k];
+      if (c < 0 || c >= n) {
+        set_err(err, 0, LDL_E_RANGE);
+        rk[k] = 0;
+        rv[k] = 0;
+        continue;
+      }
+      if (w[k] < 1) set_err(err, 0, LDL_E_INVALID);
+      rk[k] = ((u64)v << bits) | (u64)c;
+      rv[k] = (u64)(int64_t)w[k];
+    }
+  }
+}
+
+__global__ void k_check_max(const int64_t* s, int64_t n, unsigned long long* err) {
+  GRID_STRIDE(i, n) {
+    if (s[i] > INT32_MAX) set_err(err, 0, LDL_E_OVERFLOW);
+  }
+}
+
+__global__ void k_compare(const u64* a, const int64_t* av, const u64* b, const u64* bv, int64_t n,
+                          unsigned long long* err) {
+  GRID_STRIDE(i, n) {
+    if (a[i] != b[i] || (u64)av[i] != bv[i]) set_err(err, 0, LDL_E_INVALID);
+  }
+}
+
+template <class WT>
+__global__ void k_row_sums(Adj<WT> a, int64_t n, int64_t* out, int64_t* self, int64_t* total) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  int64_t tot = 0;
+  for (int64_t v = warp; v < n; v += nw) {
+    const int64_t o = a.off[v];
+    const int32_t l = a.len[v];
+    int64_t s = 0, sl = 0;
+    for (int32_t k = lane; k < l; k += 32) {
+      const int64_t w = (int64_t)a.w[o + k];
+      s += w;
+      if (a.col[o + k] == v) sl += w;
+    }
+    s = warp_sum_i64(s);
+    sl = warp_sum_i64(sl);
+    if (lane == 0) {
+      out[v] = s;
+      if (self) self[v] = sl;
+      tot += s;
+    }
+  }
+  if (lane == 0 && total && tot) atomic_add_i64(total, tot);
+}
+
+__global__ void k_iota(int32_t* a, int64_t n) {
+  GRID_STRIDE(i, n) a[i] = (int32_t)i;
+}
+
+__global__ void k_fill_i32(int32_t* a, int64_t n, int32_t v) {
+  GRID_STRIDE(i, n) a[i] = v;
+}
+
+__global__ void k_alive_list(const uint8_t* alive, int64_t n, int32_t* l, int32_t* cnt) {
+  GRID_STRIDE(i, n) {
+    if (!alive || alive[i]) l[atomicAdd(cnt, 1)] = (int32_t)i;
+  }
+}
+
+__global__ void k_all_alive(const int32_t* cnt, int64_t n, uint8_t* alive) {
+  GRID_STRIDE(i, n) alive[i] = cnt[i] > 0 ? 1 : 0;
+}
+
+__global__ void k_esum(const int64_t* e, const int64_t* Kout, const int64_t* Kin, int64_t n, int64_t* E, I128* P) {
+  int64_t se = 0;
+  i128 sp = 0;
+  GRID_STRIDE(i, n) {
+    se += e[i];
+    sp += (i128)Kout[i] * Kin[i];
+  }
+  se = warp_sum_i64(se);
+  sp = warp_sum_i128(sp);
+  if ((threadIdx.x & 31) == 0) {
+    if (se) atomic_add_i64(E, se);
+    atomic_add_i128(P, sp);
+  }
+}
+
+__global__ void k_changed_final(const int32_t* lCh, const int32_t* nCh, const int32_t* lab,
+                                const int32_t* lab_before, int32_t* out, int32_t* nout) {
+  const int32_t n = *nCh;
+  for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const int32_t u = lCh[k];
+    if (lab[u] != lab_before[u]) out[atomicAdd(nout, 1)] = u;
+  }
+}
+
+}  // namespace
+
+// ================================================================== host side
+static void throw_err(ldl_ctx& c, unsigned long long* d_err, const char* what) {
+  unsigned long long e = 0;
+  CK(cudaMemcpyAsync(&e, d_err, sizeof(e), cudaMemcpyDeviceToHost, c.s));
+  CK(cudaStreamSynchronize(c.s));
+  if (e != ~0ull) {
+    const int code = (int)(e & 255);
+    const long long idx = (long long)(e >> 8);
+    char buf[160];
+    snprintf(buf, sizeof buf, "%s: status %d at update %lld", what, code, idx);
+    ldl_throw((ldl_status)code, buf);
+  }
+}
+
+static void reset_err(ldl_ctx& c) {
+  CK(cudaMemsetAsync(&c.d_sc->err_key, 0xff, sizeof(int64_t), c.s));
+}
+
+static unsigned long long* err_ptr(ldl_ctx& c) { return (unsigned long long*)&c.d_sc->err_key; }
+
+int64_t ingest(ldl_ctx& c, const ldl_update* upd, int64_t count, int on_device, int64_t* dm) {
+  *dm = 0;
+  if (count <= 0) return 0;
+  const ldl_update* du = upd;
+  if (!on_device) {
+    c.upd.reserve(count, c.s);
+    CK(cudaMemcpyAsync(c.upd.p, upd, sizeof(ldl_update) * (size_t)count, cudaMemcpyHostToDevice, c.s));
+    du = c.upd.p;
+  }
+  reset_err(c);
+  const int g = grid_for(count, TPB);
+  k_validate<<<g, TPB, 0, c.s>>>(du, count, c.n, err_ptr(c));
+  CKL("k_validate");
+  throw_err(c, err_ptr(c), "invalid update");
+  c.rk.reserve(2 * count + 2, c.s);
+  c.rv.reserve(2 * count + 2, c.s);
+  k_upd_keys<<<g, TPB, 0, c.s>>>(du, count, c.bits, c.directed, c.rk.p, c.rv.p);
+  CKL("k_upd_keys");
+  sort_pairs(c.rk, c.rv, c.tk, c.tv, count, 2 * c.bits, c.P, c.s);
+  // unique keys and their first positions
+  c.P.flag.reserve(count + 1, c.s);
+  c.P.pos.reserve(count + 1, c.s);
+  c.rk2.reserve(count + 1, c.s);
+  c.rsum.reserve(count + 1, c.s);
+  c.rsum2.reserve(count + 1, c.s);
+  heads_launch(c.rk.p, count, c.P.flag.p, c.s);
+  const int64_t nu = scan_exclusive_i32(c.P.flag.p, c.P.pos.p, count, c.P, c.s, true);
+  k_unique_starts<<<g, TPB, 0, c.s>>>(c.rk.p, count, c.P.flag.p, c.P.pos.p, c.rk2.p, c.rsum.p);
+  CKL("k_unique_starts");
+  c.CS.pos.reserve(nu + 1, c.s);
+  c.CS.oldw.reserve(nu + 1, c.s);
+  csr_lookup<int32_t>(c.lv[0].out0, c.rk2.p, nu, c.bits, c.CS.pos.p, c.CS.oldw.p, c.CS, c.P, c.s,
+                      &c.d_sc->cnt[C_SEG]);
+  CK(cudaMemsetAsync(&c.d_sc->dm, 0, sizeof(int64_t), c.s));
+  k_seq<<<grid_for(nu, TPB), TPB, 0, c.s>>>(du, count, c.rv.p, c.rsum.p, nu, c.rk2.p, c.CS.oldw.p, c.bits,
+                                            c.directed, c.rsum2.p, err_ptr(c), &c.d_sc->dm);
+  CKL("k_seq");
+  throw_err(c, err_ptr(c), "invalid update sequence");
+  CK(cudaMemcpyAsync(dm, &c.d_sc->dm, sizeof(int64_t), cudaMemcpyDeviceToHost, c.s));
+  CK(cudaStreamSynchronize(c.s));
+  if (c.m + *dm >= ((int64_t)1 << 50) || c.m + *dm < 0) ldl_throw(LDL_E_OVERFLOW, "total weight m would reach 2^50");
+  zero_cnt(c, K_REC);
+  k_emit_arcs<<<grid_for(nu, TPB), TPB, 0, c.s>>>(c.rk2.p, c.rsum2.p, nu, c.bits, c.directed, c.rk.p, c.rv.p,
+                                                  c.dcnt + K_REC);
+  CKL("k_emit_arcs");
+  const int64_t na = rd_cnt(c, K_REC);
+  sort_pairs(c.rk, c.rv, c.tk, c.tv, na, 2 * c.bits, c.P, c.s);
+  return na;
+}
+
+// apply sorted unique records to a level's out (and transposed in) adjacency
+static void apply_level(ldl_ctx& c, int r, DBuf<u64>& keys, DBuf<u64>& vals, int64_t nr) {
+  if (nr <= 0) return;
+  if (r == 0)
+    csr_apply<int32_t>(c.lv[0].out0, keys.p, (const int64_t*)vals.p, nr, c.bits, c.CS, c.P, c.s, c.d_sc);
+  else
+    csr_apply<int64_t>(c.lv[r].out, keys.p, (const int64_t*)vals.p, nr, c.bits, c.CS, c.P, c.s, c.d_sc);
+  if (c.directed) {
+    c.rk2.reserve(nr, c.s);
+    c.rv2.reserve(nr, c.s);
+    k_transpose<<<grid_for(nr, TPB), TPB, 0, c.s>>>(keys.p, vals.p, nr, c.bits, c.rk2.p, c.rv2.p);
+    CKL("k_transpose");
+    sort_pairs(c.rk2, c.rv2, c.tk, c.tv, nr, 2 * c.bits, c.P, c.s);
+    if (r == 0)
+      csr_apply<int32_t>(c.lv[0].in0, c.rk2.p, (const int64_t*)c.rv2.p, nr, c.bits, c.CS, c.P, c.s, c.d_sc);
+    else
+      csr_apply<int64_t>(c.lv[r].in, c.rk2.p, (const int64_t*)c.rv2.p, nr, c.bits, c.CS, c.P, c.s, c.d_sc);
+  }
+}
+
+// Map records (keys, vals) of level q to level q+1, reduce, and apply there.
+// Result (reduced) ends in (keys, vals); returns the count.
+static int64_t propagate_once(ldl_ctx& c, int q, DBuf<u64>& keys, DBuf<u64>& vals, int64_t n, bool add_k) {
+  if (n <= 0) return 0;
+  LevelState& up = c.lv[q + 1];
+  c.rk2.reserve(n, c.s);
+  c.rv2.reserve(n, c.s);
+  zero_cnt(c, K_REC);
+  k_map_records<<<grid_for(n, TPB), TPB, 0, c.s>>>(keys.p, (const int64_t*)vals.p, n, c.bits, c.lv[q].par.p,
+                                                   add_k ? up.kout.p : nullptr, add_k ? kin_of(c, q + 1) : nullptr,
+                                                   c.directed, c.rk2.p, c.rv2.p, c.dcnt + K_REC);
+  CKL("k_map_records");
+  const int64_t nm = rd_cnt(c, K_REC);
+  sort_pairs(c.rk2, c.rv2, c.tk, c.tv, nm, 2 * c.bits, c.P, c.s);
+  c.rsum.reserve(nm + 1, c.s);
+  const int64_t nr = reduce_by_key(c.rk2.p, c.rv2.p, nm, keys.p, c.rsum.p, c.P, c.s);
+  if (nr) CK(cudaMemcpyAsync(vals.p, c.rsum.p, sizeof(int64_t) * (size_t)nr, cudaMemcpyDeviceToDevice, c.s));
+  apply_level(c, q + 1, keys, vals, nr);
+  return nr;
+}
+
+void repair_batch(ldl_ctx& c, int64_t na, const int32_t* epA, int32_t epT, int64_t dm) {
+  if (na <= 0) return;
+  // Algorithm 1 line 1: the batch changes level 0
+  apply_level(c, 0, c.rk, c.rv, na);
+  // line 2: m, degrees, community totals (exactly, with sum_C K_out K_in)
+  LevelState& L0 = c.lv[0];
+  zero_cnt(c, K_T);
+  k_dirty<<<grid_for(na, TPB), TPB, 0, c.s>>>(c.rk.p, na, c.bits, L0.lab.p, c.stT.p, epT, c.lT.p, c.dcnt + K_T);
+  CKL("k_dirty");
+  CK(cudaMemsetAsync(&c.d_sc->p_old, 0, sizeof(I128) * 2, c.s));
+  CK(cudaMemsetAsync(&c.d_sc->de, 0, sizeof(int64_t), c.s));
+  k_psum<<<grid_for(2 * na, TPB), TPB, 0, c.s>>>(c.lT.p, c.dcnt + K_T, c.Kout.p, Kin_of(c), &c.d_sc->p_old);
+  CKL("k_psum");
+  k_stat_arcs<<<grid_for(na, TPB), TPB, 0, c.s>>>(c.rk.p, (const int64_t*)c.rv.p, na, c.bits, c.directed, L0.lab.p,
+                                                  L0.kout.p, kin_of(c, 0), c.Kout.p, Kin_of(c), c.e.p, &c.d_sc->de,
+                                                  L0.stA.p, epA[0], L0.lA.p, c.dcnt + K_A0);
+  CKL("k_stat_arcs");
+  k_psum<<<grid_for(2 * na, TPB), TPB, 0, c.s>>>(c.lT.p, c.dcnt + K_T, c.Kout.p, Kin_of(c), &c.d_sc->p_new);
+  CKL("k_psum");
+  DevScalars h;
+  CK(cudaMemcpyAsync(&h, c.d_sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, c.s));
+  CK(cudaStreamSynchronize(c.s));
+  c.m += dm;
+  c.E += h.de;
+  c.Psum += i128_of(h.p_new.hi, h.p_new.lo) - i128_of(h.p_old.hi, h.p_old.lo);
+  // the aggregate chain: W_r(anc(i), anc(j)) += delta, strengths, A^r
+  int64_t cur = na;
+  for (int q = 0; q < c.T; ++q) {
+    const int32_t nq = rd_cnt(c, K_A0 + q);
+    if (nq > 0) {
+      k_map_list<<<grid_for(nq, TPB), TPB, 0, c.s>>>(c.lv[q].lA.p, c.dcnt + K_A0 + q, c.lv[q].par.p,
+                                                     c.lv[q + 1].stA.p, epA[q + 1], c.lv[q + 1].lA.p,
+                                                     c.dcnt + K_A0 + q + 1);
+      CKL("k_map_list");
+    }
+    if (cur > 0) cur = propagate_once(c, q, c.rk, c.rv, cur, true);
+  }
+}
+
+void pushdown(ldl_ctx& c, int r, int32_t epCh) {
+  // lMv holds the level-r nodes moved in this level's move loop
+  int32_t* src = c.lMv.p;
+  int idx = K_MV;
+  int32_t n = rd_cnt(c, K_MV);
+  int32_t* bufs[2] = {c.lTmp.p, c.lE2.p};
+  int idxs[2] = {K_TMP, K_TMP2};
+  int flip = 0;
+  for (int q = r - 1; q >= 0 && n > 0; --q) {
+    LevelState& L = c.lv[q];
+    Adj<int32_t> ch{L.children.off.p, L.children.len.p, L.children.col.p, L.children.w.p};
+    int32_t* dst = q > 0 ? bufs[flip] : nullptr;
+    zero_cnt(c, idxs[flip]);
+    k_push<<<grid_for((int64_t)n * 32, TPB), TPB, 0, c.s>>>(
+        src, c.dcnt + idx, c.lv[q + 1].lab.p, ch, L.lab.p, dst, c.dcnt + idxs[flip], q == 0 ? c.stCh.p : nullptr,
+        epCh, c.lCh.p, c.dcnt + K_CH, c.lab_before.p);
+    CKL("k_push");
+    if (q > 0) {
+      src = bufs[flip];
+      idx = idxs[flip];
+      n = rd_cnt(c, idx);
+      flip ^= 1;
+    }
+  }
+}
+
+int32_t dissolve(ldl_ctx& c, int r, int32_t epD, int32_t epX, bool all_nodes) {
+  LevelState& L = c.lv[r];
+  LevelState& N = c.lv[r + 1];
+  zero_cnt(c, K_D);
+  if (all_nodes) {
+    k_alive_list<<<grid_for(c.n, TPB), TPB, 0, c.s>>>(r ? L.alive.p : nullptr, c.n, c.lD.p, c.dcnt + K_D);
+    CKL("k_alive_list");
+    k_stamp_list<<<grid_for(c.n, TPB), TPB, 0, c.s>>>(c.lD.p, c.dcnt + K_D, c.stD.p, epD);
+    CKL("k_stamp_list");
+  } else {
+    const int32_t nu = rd_cnt(c, K_USTAR);
+    zero_cnt(c, K_X);
+    k_touched<<<grid_for(nu, TPB), TPB, 0, c.s>>>(c.lUstar.p, c.dcnt + K_USTAR, L.par.p, c.stD.p, epD, c.lD.p,
+                                                  c.dcnt + K_D, c.stX.p, epX, c.lX.p, c.dcnt + K_X);
+    CKL("k_touched");
+    const int32_t nx = rd_cnt(c, K_X);
+    if (nx > 0) {
+      Adj<int32_t> ch{L.children.off.p, L.children.len.p, L.children.col.p, L.children.w.p};
+      k_collect<<<grid_for((int64_t)nx * 32, TPB), TPB, 0, c.s>>>(c.lX.p, c.dcnt + K_X, ch, c.stD.p, epD, c.lD.p,
+                                                                  c.dcnt + K_D);
+      CKL("k_collect");
+    }
+  }
+  const int32_t nd = rd_cnt(c, K_D);
+  if (nd > 0) {
+    k_dissolve<<<grid_for(nd, TPB), TPB, 0, c.s>>>(c.lD.p, c.dcnt + K_D, L.par.p, c.par_old.p, L.kout.p,
+                                                   kin_of(c, r), N.kout.p, kin_of(c, r + 1), N.cnt.p, c.directed);
+    CKL("k_dissolve");
+  }
+  return nd;
+}
+
+void reset_par(ldl_ctx& c, int r, int32_t nD) {
+  if (nD <= 0) return;
+  k_reset_par<<<grid_for(nD, TPB), TPB, 0, c.s>>>(c.lD.p, nD, c.lv[r].par.p, c.lv[r + 1].kout.p,
+                                                  kin_of(c, r + 1), c.lv[r + 1].cnt.p, c.directed);
+  CKL("k_reset_par");
+}
+
+template <class WT>
+static void emit_records(ldl_ctx& c, int r, Adj<WT> out, Adj<WT> in, int32_t nC, int32_t epC) {
+  CK(cudaMemsetAsync(&c.d_sc->need, 0, sizeof(int64_t), c.s));
+  k_deg_sum<WT><<<grid_for(nC, TPB), TPB, 0, c.s>>>(out, in, c.lC.p, c.dcnt + K_C, &c.d_sc->need);
+  CKL("k_deg_sum");
+  int64_t deg = 0;
+  CK(cudaMemcpyAsync(&deg, &c.d_sc->need, sizeof(int64_t), cudaMemcpyDeviceToHost, c.s));
+  CK(cudaStreamSynchronize(c.s));
+  const int64_t cap = 2 * deg + 16;
+  c.rk2.reserve(cap, c.s);
+  c.rv2.reserve(cap, c.s);
+  zero_cnt(c, K_REC);
+  k_emit<WT><<<grid_for((int64_t)nC * 32, TPB), TPB, 0, c.s>>>(out, in, c.lC.p, c.dcnt + K_C, c.lv[r].par.p,
+                                                                c.par_old.p, c.stC.p, epC, c.bits, c.rk2.p, c.rv2.p,
+                                                                c.dcnt + K_REC);
+  CKL("k_emit");
+}
+
+void aggregate(ldl_ctx& c, int r, int32_t epD, int32_t epC, int32_t epA_next, bool build) {
+  (void)epD;
+  LevelState& L = c.lv[r];
+  LevelState& N = c.lv[r + 1];
+  // changed nodes
+  zero_cnt(c, K_C);
+  const int32_t nD = rd_cnt(c, K_D);
+  k_changed<<<grid_for(nD, TPB), TPB, 0, c.s>>>(c.lD.p, c.dcnt + K_D, L.par.p, c.par_old.p, c.stC.p, epC, c.lC.p,
+                                                c.dcnt + K_C);
+  CKL("k_changed");
+  const int32_t nC = rd_cnt(c, K_C);
+  int64_t nr = 0;
+  if (nC > 0) {
+    if (r == 0) emit_records<int32_t>(c, r, adj_out0(c), adj_in0(c), nC, epC);
+    else emit_records<int64_t>(c, r, adj_out(c, r), adj_in(c, r), nC, epC);
+    const int64_t nrec = rd_cnt(c, K_REC);
+    sort_pairs(c.rk2, c.rv2, c.tk, c.tv, nrec, 2 * c.bits, c.P, c.s);
+    c.rk.reserve(nrec + 1, c.s);
+    c.rv.reserve(nrec + 1, c.s);
+    c.rsum.reserve(nrec + 1, c.s);
+    nr = reduce_by_key(c.rk2.p, c.rv2.p, nrec, c.rk.p, c.rsum.p, c.P, c.s);
+    CK(cudaMemcpyAsync(c.rv.p, c.rsum.p, sizeof(int64_t) * (size_t)nr, cudaMemcpyDeviceToDevice, c.s));
+    c.res.agg_records += nr;
+    // node and children records
+    c.ndx.reserve(2 * (int64_t)nC + 2, c.s);
+    c.ndko.reserve(2 * (int64_t)nC + 2, c.s);
+    c.ndki.reserve(2 * (int64_t)nC + 2, c.s);
+    c.crk.reserve(2 * (int64_t)nC + 2, c.s);
+    c.crv.reserve(2 * (int64_t)nC + 2, c.s);
+    zero_cnt(c, K_NREC);
+    zero_cnt(c, K_CREC);
+    k_emit_nodes<<<grid_for(nC, TPB), TPB, 0, c.s>>>(c.lC.p, c.dcnt + K_C, L.par.p, c.par_old.p, L.kout.p,
+                                                     kin_of(c, r), c.bits, c.ndx.p, c.ndko.p, c.ndki.p,
+                                                     c.dcnt + K_NREC, c.crk.p, c.crv.p, c.dcnt + K_CREC);
+    CKL("k_emit_nodes");
+    const int64_t ncr = rd_cnt(c, K_CREC);
+    sort_pairs(c.crk, c.crv, c.tk, c.tv, ncr, 2 * c.bits, c.P, c.s);
+    // keep the level r+1 record keys for NextFrontier
+    c.fk.reserve(nr + 1, c.s);
+    if (nr) CK(cudaMemcpyAsync(c.fk.p, c.rk.p, sizeof(u64) * (size_t)nr, cudaMemcpyDeviceToDevice, c.s));
+    if (build) {
+      // level r+1 starts empty: build its adjacency and the children lists
+      csr_build<int64_t>(N.out, c.n, c.rk.p, c.rsum.p, nr, c.bits, 25, c.CS, c.P, c.s);
+      if (c.directed) {
+        c.rk2.reserve(nr + 1, c.s);
+        c.rv2.reserve(nr + 1, c.s);
+        k_transpose<<<grid_for(nr, TPB), TPB, 0, c.s>>>(c.rk.p, c.rv.p, nr, c.bits, c.rk2.p, c.rv2.p);
+        CKL("k_transpose");
+        sort_pairs(c.rk2, c.rv2, c.tk, c.tv, nr, 2 * c.bits, c.P, c.s);
+        csr_build<int64_t>(N.in, c.n, c.rk2.p, (const int64_t*)c.rv2.p, nr, c.bits, 25, c.CS, c.P, c.s);
+      }
+      csr_build<int32_t>(L.children, c.n, c.crk.p, (const int64_t*)c.crv.p, ncr, c.bits, 25, c.CS, c.P, c.s);
+    } else {
+      apply_level(c, r + 1, c.rk, c.rv, nr);
+      csr_apply<int32_t>(L.children, c.crk.p, (const int64_t*)c.crv.p, ncr, c.bits, c.CS, c.P, c.s, c.d_sc);
+    }
+    // propagate level r+1 changes up the current parent chain
+    int64_t cur = nr;
+    int32_t nnd = rd_cnt(c, K_NREC);
+    for (int q = r + 1; q < c.T; ++q) {
+      if (cur > 0) cur = propagate_once(c, q, c.rk, c.rv, cur, false);
+      if (nnd > 0) {
+        c.ndx2.reserve(nnd + 1, c.s);
+        c.ndko2.reserve(nnd + 1, c.s);
+        c.ndki2.reserve(nnd + 1, c.s);
+        zero_cnt(c, K_TMP);
+        k_map_nodes<<<grid_for(nnd, TPB), TPB, 0, c.s>>>(c.ndx.p, c.ndko.p, c.ndki.p, nnd, c.lv[q].par.p,
+                                                         c.lv[q + 1].kout.p, kin_of(c, q + 1), c.directed,
+                                                         c.ndx2.p, c.ndko2.p, c.ndki2.p, c.dcnt + K_TMP);
+        CKL("k_map_nodes");
+        nnd = rd_cnt(c, K_TMP);
+        swap_buf(c.ndx, c.ndx2);
+        swap_buf(c.ndko, c.ndko2);
+        swap_buf(c.ndki, c.ndki2);
+      }
+    }
+    // existence: appear at r+1, emptied nodes cascade upwards
+    int32_t epE = c.next_epoch();
+    zero_cnt(c, K_E);
+    k_exist_cands<<<grid_for(nC, TPB), TPB, 0, c.s>>>(c.lC.p, c.dcnt + K_C, L.par.p, c.par_old.p, c.stE.p, epE,
+                                                      c.lE.p, c.dcnt + K_E);
+    CKL("k_exist_cands");
+    int32_t* le = c.lE.p;
+    int ie = K_E;
+    int32_t* le2 = c.lE2.p;
+    int ie2 = K_E2;
+    for (int q = r + 1; q <= c.T; ++q) {
+      const int32_t ne = rd_cnt(c, ie);
+      if (ne == 0) break;
+      const bool has_up = q < c.T;
+      const int32_t epE2 = c.next_epoch();
+      zero_cnt(c, ie2);
+      zero_cnt(c, K_CREC);
+      c.crk.reserve(ne + 1, c.s);
+      c.crv.reserve(ne + 1, c.s);
+      k_exist<<<grid_for(ne, TPB), TPB, 0, c.s>>>(le, c.dcnt + ie, c.lv[q].cnt.p, c.lv[q].alive.p,
+                                                  has_up ? c.lv[q].par.p : nullptr,
+                                                  has_up ? c.lv[q + 1].cnt.p : nullptr, c.bits, c.crk.p, c.crv.p,
+                                                  c.dcnt + K_CREC, c.stE.p, epE2, le2, c.dcnt + ie2,
+                                                  c.dcnt + K_ERR);
+      CKL("k_exist");
+      const int64_t nd = rd_cnt(c, K_CREC);
+      if (nd > 0) {
+        sort_pairs(c.crk, c.crv, c.tk, c.tv, nd, 2 * c.bits, c.P, c.s);
+        csr_apply<int32_t>(c.lv[q].children, c.crk.p, (const int64_t*)c.crv.p, nd, c.bits, c.CS, c.P, c.s, c.d_sc);
+      }
+      int32_t* t = le;
+      le = le2;
+      le2 = t;
+      int ti = ie;
+      ie = ie2;
+      ie2 = ti;
+    }
+    if (rd_cnt(c, K_ERR)) ldl_throw(LDL_E_INVALID, "internal: new supernode already has a parent");
+  } else if (build) {
+    // nothing changed parent (cannot happen in the static run, which stops earlier)
+  }
+  // relabel the level-(r+1) images of frontier and dissolved nodes
+  const int32_t nUs = rd_cnt(c, K_USTAR);
+  if (nUs > 0) {
+    k_relabel<<<grid_for(nUs, TPB), TPB, 0, c.s>>>(c.lUstar.p, c.dcnt + K_USTAR, L.par.p, L.lab.p, N.lab.p);
+    CKL("k_relabel");
+  }
+  if (nD > 0) {
+    k_relabel<<<grid_for(nD, TPB), TPB, 0, c.s>>>(c.lD.p, c.dcnt + K_D, L.par.p, L.lab.p, N.lab.p);
+    CKL("k_relabel");
+  }
+  // NextFrontier for level r+1
+  if (epA_next) {
+    if (nr > 0) {
+      k_nf_records<<<grid_for(nr, TPB), TPB, 0, c.s>>>(c.fk.p, nr, c.bits, N.alive.p, N.stA.p,
+                                                       epA_next, N.lA.p, c.dcnt + K_A0 + r + 1);
+      CKL("k_nf_records");
+    }
+    if (nD > 0) {
+      k_nf_nodes<<<grid_for(nD, TPB), TPB, 0, c.s>>>(c.lD.p, c.dcnt + K_D, L.par.p, c.par_old.p, N.alive.p, N.stA.p,
+                                                     epA_next, N.lA.p, c.dcnt + K_A0 + r + 1);
+      CKL("k_nf_nodes");
+    }
+    if (nUs > 0) {
+      k_nf_nodes<<<grid_for(nUs, TPB), TPB, 0, c.s>>>(c.lUstar.p, c.dcnt + K_USTAR, L.par.p, nullptr, N.alive.p,
+                                                      N.stA.p, epA_next, N.lA.p, c.dcnt + K_A0 + r + 1);
+      CKL("k_nf_nodes");
+    }
+  }
+}
+
+void level_alloc(ldl_ctx& c, int r) {
+  LevelState& L = c.lv[r];
+  if (L.allocated) return;
+  const int64_t n = c.n;
+  L.lab.exact(n);
+  L.par.exact(n);
+  L.cnt.exact(n);
+  L.kout.exact(n);
+  if (c.directed) L.kin.exact(n);
+  L.alive.exact(n);
+  L.stA.exact(n);
+  L.lA.exact(n);
+  CK(cudaMemsetAsync(L.lab.p, 0, sizeof(int32_t) * (size_t)n, c.s));
+  CK(cudaMemsetAsync(L.par.p, 0xff, sizeof(int32_t) * (size_t)n, c.s));
+  CK(cudaMemsetAsync(L.cnt.p, 0, sizeof(int32_t) * (size_t)n, c.s));
+  CK(cudaMemsetAsync(L.kout.p, 0, sizeof(int64_t) * (size_t)n, c.s));
+  if (c.directed) CK(cudaMemsetAsync(L.kin.p, 0, sizeof(int64_t) * (size_t)n, c.s));
+  CK(cudaMemsetAsync(L.alive.p, 0, (size_t)n, c.s));
+  CK(cudaMemsetAsync(L.stA.p, 0, sizeof(int32_t) * (size_t)n, c.s));
+  L.allocated = true;
+}
+
+void level_free(ldl_ctx& c, int r) { c.lv[r].release(); }
+
+int32_t alive_list(ldl_ctx& c, int r, int32_t* list, int idx) {
+  zero_cnt(c, idx);
+  k_alive_list<<<grid_for(c.n, TPB), TPB, 0, c.s>>>(r ? c.lv[r].alive.p : nullptr, c.n, list, c.dcnt + idx);
+  CKL("k_alive_list");
+  return rd_cnt(c, idx);
+}
+
+int32_t changed_labels(ldl_ctx& c, int32_t epCh) {
+  (void)epCh;
+  const int32_t n = rd_cnt(c, K_CH);
+  zero_cnt(c, K_CHG);
+  if (n > 0) {
+    k_changed_final<<<grid_for(n, TPB), TPB, 0, c.s>>>(c.lCh.p, c.dcnt + K_CH, c.lv[0].lab.p, c.lab_before.p,
+                                                       c.lChg.p, c.dcnt + K_CHG);
+    CKL("k_changed_final");
+  }
+  return rd_cnt(c, K_CHG);
+}
+
+void upload_graph(ldl_ctx& c, int64_t nnz, const int64_t* row_ptr, const int32_t* col, const int32_t* w) {
+  const int64_t n = c.n;
+  DBuf<int64_t> drp;
+  DBuf<int32_t> dcol, dw;
+  drp.exact(n + 1);
+  dcol.exact(nnz + 1);
+  dw.exact(nnz + 1);
+  CK(cudaMemcpyAsync(drp.p, row_ptr, sizeof(int64_t) * (size_t)(n + 1), cudaMemcpyHostToDevice, c.s));
+  if (nnz) {
+    CK(cudaMemcpyAsync(dcol.p, col, sizeof(int32_t) * (size_t)nnz, cudaMemcpyHostToDevice, c.s));
+    CK(cudaMemcpyAsync(dw.p, w, sizeof(int32_t) * (size_t)nnz, cudaMemcpyHostToDevice, c.s));
+  }
+  c.rk.reserve(nnz + 1, c.s);
+  c.rv.reserve(nnz + 1, c.s);
+  reset_err(c);
+  k_csr_records<<<grid_for(n * 32, TPB), TPB, 0, c.s>>>(drp.p, dcol.p, dw.p, n, c.bits, c.rk.p, c.rv.p, err_ptr(c));
+  CKL("k_csr_records");
+  CK(cudaStreamSynchronize(c.s));
+  drp.release();
+  dcol.release();
+  dw.release();
+  throw_err(c, err_ptr(c), "invalid CSR");
+  sort_pairs(c.rk, c.rv, c.tk, c.tv, nnz, 2 * c.bits, c.P, c.s);
+  c.rk2.reserve(nnz + 1, c.s);
+  c.rsum.reserve(nnz + 1, c.s);
+  const int64_t na = reduce_by_key(c.rk.p, c.rv.p, nnz, c.rk2.p, c.rsum.p, c.P, c.s);
+  reset_err(c);
+  k_check_max<<<grid_for(na, TPB), TPB, 0, c.s>>>(c.rsum.p, na, err_ptr(c));
+  CKL("k_check_max");
+  throw_err(c, err_ptr(c), "summed weight above INT32_MAX");
+  // (rk2, rsum) = unique arcs
+  CK(cudaMemcpyAsync(c.rk.p, c.rk2.p, sizeof(u64) * (size_t)na, cudaMemcpyDeviceToDevice, c.s));
+  CK(cudaMemcpyAsync(c.rv.p, c.rsum.p, sizeof(int64_t) * (size_t)na, cudaMemcpyDeviceToDevice, c.s));
+  if (na) {
+    c.rk2.reserve(na + 1, c.s);
+    c.rv2.reserve(na + 1, c.s);
+    k_transpose<<<grid_for(na, TPB), TPB, 0, c.s>>>(c.rk.p, c.rv.p, na, c.bits, c.rk2.p, c.rv2.p);
+    CKL("k_transpose");
+    sort_pairs(c.rk2, c.rv2, c.tk, c.tv, na, 2 * c.bits, c.P, c.s);
+    if (!c.directed) {
+      reset_err(c);
+      k_compare<<<grid_for(na, TPB), TPB, 0, c.s>>>(c.rk.p, (const int64_t*)c.rv.p, c.rk2.p, c.rv2.p, na,
+                                                    err_ptr(c));
+      CKL("k_compare");
+      throw_err(c, err_ptr(c), "undirected CSR is not symmetric");
+    }
+  }
+  LevelState& L0 = c.lv[0];
+  csr_build<int32_t>(L0.out0, n, c.rk.p, (const int64_t*)c.rv.p, na, c.bits, 25, c.CS, c.P, c.s);
+  if (c.directed) csr_build<int32_t>(L0.in0, n, c.rk2.p, (const int64_t*)c.rv2.p, na, c.bits, 25, c.CS, c.P, c.s);
+  // strengths, m, labels, community totals
+  CK(cudaMemsetAsync(&c.d_sc->dm, 0, sizeof(int64_t), c.s));
+  const int gw = grid_for(n * 32, TPB);
+  k_row_sums<int32_t><<<gw, TPB, 0, c.s>>>(adj_out0(c), n, L0.kout.p, c.e.p, &c.d_sc->dm);
+  CKL("k_row_sums");
+  if (c.directed) {
+    k_row_sums<int32_t><<<gw, TPB, 0, c.s>>>(adj_in0(c), n, L0.kin.p, nullptr, nullptr);
+    CKL("k_row_sums(in)");
+  }
+  k_iota<<<grid_for(n, TPB), TPB, 0, c.s>>>(L0.lab.p, n);
+  CKL("k_iota");
+  k_fill_i32<<<grid_for(n, TPB), TPB, 0, c.s>>>(L0.cnt.p, n, 1);
+  CKL("k_fill_i32");
+  CK(cudaMemsetAsync(L0.alive.p, 1, (size_t)n, c.s));
+  CK(cudaMemcpyAsync(c.Kout.p, L0.kout.p, sizeof(int64_t) * (size_t)n, cudaMemcpyDeviceToDevice, c.s));
+  if (c.directed) CK(cudaMemcpyAsync(c.Kin.p, L0.kin.p, sizeof(int64_t) * (size_t)n, cudaMemcpyDeviceToDevice, c.s));
+  CK(cudaMemsetAsync(&c.d_sc->de, 0, sizeof(int64_t), c.s));
+  CK(cudaMemsetAsync(&c.d_sc->p_new, 0, sizeof(I128), c.s));
+  k_esum<<<grid_for(n, TPB), TPB, 0, c.s>>>(c.e.p, c.Kout.p, Kin_of(c), n, &c.d_sc->de, &c.d_sc->p_new);
+  CKL("k_esum");
+  DevScalars h;
+  CK(cudaMemcpyAsync(&h, c.d_sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, c.s));
+  CK(cudaStreamSynchronize(c.s));
+  c.m = h.dm;
+  if (c.m >= ((int64_t)1 << 50)) ldl_throw(LDL_E_OVERFLOW, "total weight m reaches 2^50");
+  c.E = h.de;
+  c.Psum = i128_of(h.p_new.hi, h.p_new.lo);
+}

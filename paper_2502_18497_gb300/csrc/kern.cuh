@@ -1,0 +1,42 @@
+// Host-side launchers of the algorithm kernels (sweep.cu, hier.cu).
+#pragma once
+#include "ctx.cuh"
+
+struct CommitOut {
+  i128 dq;     // exact change of the Eq. 1 numerator
+  i128 dp;     // change of sum_C K_out K_in
+  int64_t de;  // change of sum_C e_C
+  int32_t ntc; // touched communities
+};
+
+// ---- sweep.cu
+void expand_set(ldl_ctx& c, int r, const int32_t* list, int idx_n, int32_t* stamp, int32_t ep, int32_t* olist,
+                int idx_out, int64_t n_hint);
+void filter_alive(ldl_ctx& c, int r, const int32_t* list, int idx_n, int32_t* olist, int idx_out, int64_t n_hint);
+void union_into(ldl_ctx& c, const int32_t* list, int idx_n, int32_t* stamp, int32_t ep, int32_t* olist, int idx_out,
+                int64_t n_hint);
+int32_t sweep(ldl_ctx& c, int r, int mode, const int32_t* list, int idx_n, int64_t n_hint);
+int32_t decouple(ldl_ctx& c, int32_t nc);
+CommitOut commit_move(ldl_ctx& c, int r, int32_t nb, int32_t epB, int32_t epT, int32_t epCh);
+void rollback_move(ldl_ctx& c, int r, int32_t nb, int32_t ntc);
+void mark_moved(ldl_ctx& c, int r, int32_t nb, int32_t epMv, int32_t epM0);
+void commit_ref(ldl_ctx& c, int r, int32_t nb);
+void spexpand(ldl_ctx& c, int r, int32_t nb, int32_t epD, int32_t epR, int32_t* lR, int idx_R);
+
+// ---- hier.cu
+// Batch validation and net deltas; leaves the sorted arcs in (c.rk, c.rv)
+// and returns their count.  Throws (state untouched) on a bad batch.
+int64_t ingest(ldl_ctx& c, const ldl_update* upd, int64_t count, int on_device, int64_t* dm);
+// Apply the level-0 arcs to the adjacency and repair every statistic along
+// the parent chain; marks InitFrontier in the A lists (epA per level).
+void repair_batch(ldl_ctx& c, int64_t na, const int32_t* epA, int32_t epT, int64_t dm);
+void pushdown(ldl_ctx& c, int r, int32_t epCh);
+int32_t dissolve(ldl_ctx& c, int r, int32_t epD, int32_t epX, bool all_nodes);
+void aggregate(ldl_ctx& c, int r, int32_t epD, int32_t epC, int32_t epA_next, bool build);
+// static set-up of level 0 from a host CSR
+void upload_graph(ldl_ctx& c, int64_t nnz, const int64_t* row_ptr, const int32_t* col, const int32_t* w);
+void level_alloc(ldl_ctx& c, int r);
+void level_free(ldl_ctx& c, int r);
+int32_t alive_list(ldl_ctx& c, int r, int32_t* list, int idx);
+void reset_par(ldl_ctx& c, int r, int32_t nD);
+int32_t changed_labels(ldl_ctx& c, int32_t epCh);

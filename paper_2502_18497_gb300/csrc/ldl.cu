@@ -1,0 +1,579 @@
+// C ABI and host control of the LD-Leiden batch update (Algorithm 1).
+//
+// The host only sequences kernels and reads back the few integers that
+// decide control flow (list sizes, dQ(B), the pass gain); every step of the
+// method runs in the kernels of sweep.cu, hier.cu, csr.cu and prims.cu.
+#include <algorithm>
+#include <atomic>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "kern.cuh"
+
+// ---------------------------------------------------------------- errors / memory
+void ldl_throw(ldl_status st, const std::string& msg) { throw LdlError{st, msg}; }
+
+void ldl_cuda_check(cudaError_t e, const char* what, const char* file, int line) {
+  if (e == cudaSuccess) return;
+  char buf[512];
+  snprintf(buf, sizeof buf, "%s: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
+  if (e == cudaErrorMemoryAllocation) ldl_throw(LDL_E_NOMEM, buf);
+  ldl_throw(LDL_E_CUDA, buf);
+}
+
+static std::atomic<int64_t> g_fail_after{0};
+
+void* dalloc(size_t bytes) {
+  int64_t k = g_fail_after.load();
+  if (k > 0) {
+    if (g_fail_after.fetch_sub(1) == 1) ldl_throw(LDL_E_NOMEM, "injected allocation failure");
+  }
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, bytes ? bytes : 1);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    char buf[128];
+    snprintf(buf, sizeof buf, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+    ldl_throw(e == cudaErrorMemoryAllocation ? LDL_E_NOMEM : LDL_E_CUDA, buf);
+  }
+  return p;
+}
+
+void dfree(void* p) {
+  if (p) cudaFree(p);
+}
+
+int32_t rd_cnt(ldl_ctx& c, int idx) {
+  int32_t v = 0;
+  CK(cudaMemcpyAsync(&v, c.dcnt + idx, sizeof(int32_t), cudaMemcpyDeviceToHost, c.s));
+  CK(cudaStreamSynchronize(c.s));
+  return v;
+}
+
+void zero_cnt(ldl_ctx& c, int idx) { CK(cudaMemsetAsync(c.dcnt + idx, 0, sizeof(int32_t), c.s)); }
+
+void set_cnt(ldl_ctx& c, int idx, int32_t v) {
+  CK(cudaMemcpyAsync(c.dcnt + idx, &v, sizeof(int32_t), cudaMemcpyHostToDevice, c.s));
+  CK(cudaStreamSynchronize(c.s));
+}
+
+void stage_begin(ldl_ctx& c) {
+  if (c.timing) CK(cudaEventRecord(c.ev0, c.s));
+}
+
+void stage_end(ldl_ctx& c, int stage) {
+  if (!c.timing) return;
+  CK(cudaEventRecord(c.ev1, c.s));
+  CK(cudaEventSynchronize(c.ev1));
+  float ms = 0;
+  CK(cudaEventElapsedTime(&ms, c.ev0, c.ev1));
+  c.stage_ms[stage] += ms;
+}
+
+static std::string g_create_err = "no error";
+
+// ---------------------------------------------------------------- numerator
+static i128 qnum(const ldl_ctx& c) {
+  return (i128)c.prm.gamma_den * c.m * c.E - (i128)c.prm.gamma_num * c.Psum;
+}
+
+// ---------------------------------------------------------------- allocation
+static void alloc_globals(ldl_ctx& c) {
+  const int64_t n = c.n;
+  c.Kout.exact(n);
+  if (c.directed) c.Kin.exact(n);
+  c.e.exact(n);
+  DBuf<int32_t>* st[] = {&c.stS, &c.stU, &c.stMv, &c.stB, &c.stM0, &c.stD, &c.stC, &c.stR, &c.stX, &c.stT, &c.stE,
+                         &c.stCh};
+  for (auto* b : st) {
+    b->exact(n);
+    CK(cudaMemsetAsync(b->p, 0, sizeof(int32_t) * (size_t)n, c.s));
+  }
+  DBuf<int32_t>* ls[] = {&c.lU, &c.lS, &c.lUstar, &c.lMv, &c.lM0, &c.lD, &c.lC, &c.lR, &c.lR2, &c.lX, &c.lT,
+                         &c.lE, &c.lE2, &c.lCh, &c.lChg, &c.lTmp, &c.cv, &c.csrc, &c.cdst, &c.cst, &c.bv,
+                         &c.bsrc, &c.bdst, &c.oldlab, &c.par_old, &c.lab_before, &c.binS, &c.binM, &c.binL};
+  for (auto* b : ls) b->exact(n);
+  c.best.exact(n);
+  CK(cudaMemsetAsync(c.best.p, 0xff, sizeof(int32_t) * (size_t)n, c.s));
+  c.role.exact(n);
+  CK(cudaMemsetAsync(c.role.p, 0, sizeof(int32_t) * (size_t)n, c.s));
+  c.cghi.exact(n);
+  c.cglo.exact(n);
+  c.snapKo.exact(2 * n);
+  c.snapKi.exact(2 * n);
+  c.snapE.exact(2 * n);
+  c.binLoff.exact(n);
+  c.binLsz.exact(n);
+  c.d_sc = (DevScalars*)dalloc(sizeof(DevScalars));
+  CK(cudaMemsetAsync(c.d_sc, 0, sizeof(DevScalars), c.s));
+  c.dcnt = (int32_t*)dalloc(sizeof(int32_t) * K_COUNT);
+  CK(cudaMemsetAsync(c.dcnt, 0, sizeof(int32_t) * K_COUNT, c.s));
+}
+
+static void free_all(ldl_ctx& c) {
+  if (c.s) cudaStreamSynchronize(c.s);
+  for (auto& L : c.lv) L.release();
+  DBuf<int64_t>* b64[] = {&c.Kout, &c.Kin, &c.e, &c.cghi, &c.snapKo, &c.snapKi, &c.snapE, &c.binLoff, &c.binLsz,
+                          &c.gvals, &c.rsum, &c.rsum2, &c.ndko, &c.ndki, &c.ndko2, &c.ndki2};
+  for (auto* b : b64) b->release();
+  DBuf<int32_t>* b32[] = {&c.stS, &c.stU, &c.stMv, &c.stB, &c.stM0, &c.stD, &c.stC, &c.stR, &c.stX, &c.stT,
+                          &c.stE, &c.stCh, &c.lU, &c.lS, &c.lUstar, &c.lMv, &c.lM0, &c.lD, &c.lC, &c.lR,
+                          &c.lR2, &c.lX, &c.lT, &c.lE, &c.lE2, &c.lCh, &c.lChg, &c.lTmp, &c.cv, &c.csrc,
+                          &c.cdst, &c.cst, &c.bv, &c.bsrc, &c.bdst, &c.best, &c.role, &c.oldlab, &c.par_old,
+                          &c.lab_before, &c.binS, &c.binM, &c.binL, &c.gkeys, &c.ndx, &c.ndx2};
+  for (auto* b : b32) b->release();
+  DBuf<u64>* bu[] = {&c.rk, &c.rv, &c.tk, &c.tv, &c.rk2, &c.rv2, &c.crk, &c.crv, &c.fk};
+  for (auto* b : bu) b->release();
+  c.cglo.release();
+  c.upd.release();
+  c.P.release();
+  c.CS.release();
+  if (c.d_sc) dfree(c.d_sc);
+  if (c.dcnt) dfree(c.dcnt);
+  c.d_sc = nullptr;
+  c.dcnt = nullptr;
+  if (c.ev0) cudaEventDestroy(c.ev0);
+  if (c.ev1) cudaEventDestroy(c.ev1);
+  c.ev0 = c.ev1 = nullptr;
+}
+
+// ---------------------------------------------------------------- move loop
+// Algorithm 1 lines 6-15 at level r.  Precondition: lU holds U = A^r, and
+// lUstar / stU (epoch epU) hold U*.  Moved nodes go to lMv (epMv) and, at
+// level 0, to lM0 (epM0).
+static void move_loop(ldl_ctx& c, int r, int rounds, int32_t epU, int32_t epMv, int32_t epM0, int32_t epCh) {
+  const i128 Q0 = qnum(c);
+  const int64_t ainv = c.prm.alpha_inv, binv = c.prm.beta_inv;
+  for (int j = 0; j < rounds; ++j) {
+    const int32_t nU = rd_cnt(c, K_U);
+    if (nU == 0) break;
+    c.res.rounds++;
+    stage_begin(c);
+    const int32_t epS = c.next_epoch();
+    zero_cnt(c, K_S);
+    expand_set(c, r, c.lU.p, K_U, c.stS.p, epS, c.lS.p, K_S, nU);
+    const int32_t nS = rd_cnt(c, K_S);
+    stage_end(c, ST_EXPAND);
+    stage_begin(c);
+    const int32_t nc = sweep(c, r, 0, c.lS.p, K_S, nS);
+    stage_end(c, ST_BEST);
+    if (nc == 0) break;
+    stage_begin(c);
+    const int32_t nb = decouple(c, nc);
+    stage_end(c, ST_DECOUPLE);
+    c.res.rejected += nc - nb;
+    if (nb == 0) break;
+    stage_begin(c);
+    const int32_t epB = c.next_epoch(), epT = c.next_epoch();
+    CommitOut co = commit_move(c, r, nb, epB, epT, epCh);
+    if (co.dq < 0) {
+      rollback_move(c, r, nb, co.ntc);
+      c.res.rollbacks++;
+      stage_end(c, ST_COMMIT);
+      break;
+    }
+    c.E += co.de;
+    c.Psum += co.dp;
+    c.res.moves += nb;
+    mark_moved(c, r, nb, epMv, epM0);
+    stage_end(c, ST_COMMIT);
+    stage_begin(c);
+    const int32_t epS2 = c.next_epoch();
+    zero_cnt(c, K_U);
+    expand_set(c, r, c.bv.p, K_B, c.stS.p, epS2, c.lU.p, K_U, nb);
+    const int32_t nU2 = rd_cnt(c, K_U);
+    union_into(c, c.lU.p, K_U, c.stU.p, epU, c.lUstar.p, K_USTAR, nU2);
+    stage_end(c, ST_EXPAND);
+    if (co.dq * (i128)ainv < Q0) break;
+    if ((int64_t)nb * binv < (int64_t)nS) break;
+  }
+}
+
+// Algorithm 1 lines 16-22 at level r over the dissolved set lD (epoch epD).
+static int64_t refine_loop(ldl_ctx& c, int r, int rounds, int32_t epD) {
+  const int32_t nD = rd_cnt(c, K_D);
+  if (nD == 0) return 0;
+  CK(cudaMemcpyAsync(c.lR.p, c.lD.p, sizeof(int32_t) * (size_t)nD, cudaMemcpyDeviceToDevice, c.s));
+  set_cnt(c, K_R, nD);
+  int32_t* R = c.lR.p;
+  int32_t* R2 = c.lR2.p;
+  int iR = K_R, iR2 = K_R2;
+  int64_t merges = 0;
+  const int64_t binv = c.prm.beta_inv;
+  for (int j = 0; j < rounds; ++j) {
+    const int32_t nR = rd_cnt(c, iR);
+    if (nR == 0) break;
+    c.res.rounds++;
+    const int32_t nc = sweep(c, r, 1, R, iR, nR);
+    if (nc == 0) break;
+    const int32_t nb = decouple(c, nc);
+    c.res.rejected += nc - nb;
+    if (nb == 0) break;
+    commit_ref(c, r, nb);
+    merges += nb;
+    c.res.refine_moves += nb;
+    if ((int64_t)nb * binv < (int64_t)nR) break;
+    const int32_t epR = c.next_epoch();
+    zero_cnt(c, iR2);
+    spexpand(c, r, nb, epD, epR, R2, iR2);
+    std::swap(R, R2);
+    std::swap(iR, iR2);
+  }
+  return merges;
+}
+
+// ---------------------------------------------------------------- static build
+static void static_build(ldl_ctx& c) {
+  const int L = c.prm.L;
+  c.T = 0;
+  for (int r = 0; r <= L; ++r) {
+    const int32_t nU = alive_list(c, r, c.lU.p, K_U);
+    const int32_t epU = c.next_epoch();
+    zero_cnt(c, K_USTAR);
+    union_into(c, c.lU.p, K_U, c.stU.p, epU, c.lUstar.p, K_USTAR, nU);
+    const int32_t epMv = c.next_epoch(), epM0 = c.next_epoch(), epCh = c.next_epoch();
+    zero_cnt(c, K_MV);
+    zero_cnt(c, K_M0);
+    zero_cnt(c, K_CH);
+    move_loop(c, r, c.prm.M_static, epU, epMv, epM0, epCh);
+    if (r > 0) pushdown(c, r, epCh);
+    if (r == L) break;
+    level_alloc(c, r + 1);
+    c.T = r + 1;
+    const int32_t epD = c.next_epoch();
+    const int32_t nD = dissolve(c, r, epD, 0, true);
+    const int64_t merges = refine_loop(c, r, c.prm.M_static, epD);
+    if (merges == 0) {
+      reset_par(c, r, nD);
+      level_free(c, r + 1);
+      c.T = r;
+      break;
+    }
+    const int32_t epC = c.next_epoch();
+    aggregate(c, r, epD, epC, 0, true);
+  }
+  CK(cudaStreamSynchronize(c.s));
+}
+
+// ---------------------------------------------------------------- batch update
+static void apply_batch(ldl_ctx& c, const ldl_update* upd, int64_t count, int on_device) {
+  memset(&c.res, 0, sizeof(c.res));
+  for (double& x : c.stage_ms) x = 0;
+  const int T = c.T;
+  int64_t dm = 0;
+  stage_begin(c);
+  const int64_t na = ingest(c, upd, count, on_device, &dm);
+  stage_end(c, ST_INGEST);
+  const int32_t epCh = c.next_epoch();
+  zero_cnt(c, K_CH);
+  if (na == 0) {
+    c.res.n_changed = 0;
+    return;
+  }
+  std::vector<int32_t> epA(T + 2, 0);
+  for (int r = 0; r <= T; ++r) {
+    epA[r] = c.next_epoch();
+    zero_cnt(c, K_A0 + r);
+  }
+  stage_begin(c);
+  const int32_t epT = c.next_epoch();
+  repair_batch(c, na, epA.data(), epT, dm);
+  stage_end(c, ST_REPAIR);
+  const int64_t ainv = c.prm.alpha_inv;
+  for (int pass = 0; pass < c.prm.N; ++pass) {
+    const i128 Qpass = qnum(c);
+    const int32_t epM0 = c.next_epoch();
+    zero_cnt(c, K_M0);
+    for (int r = 0; r <= T; ++r) {
+      const int32_t nA = rd_cnt(c, K_A0 + r);
+      if (nA == 0) continue;
+      zero_cnt(c, K_U);
+      filter_alive(c, r, c.lv[r].lA.p, K_A0 + r, c.lU.p, K_U, nA);
+      const int32_t nU = rd_cnt(c, K_U);
+      if (nU == 0) continue;
+      if (r < 8) c.res.frontier_nodes[r] += nU;
+      const int32_t epU = c.next_epoch();
+      zero_cnt(c, K_USTAR);
+      union_into(c, c.lU.p, K_U, c.stU.p, epU, c.lUstar.p, K_USTAR, nU);
+      const int32_t epMv = c.next_epoch();
+      zero_cnt(c, K_MV);
+      move_loop(c, r, c.prm.M, epU, epMv, epM0, epCh);
+      if (r > 0) {
+        stage_begin(c);
+        pushdown(c, r, epCh);
+        stage_end(c, ST_PUSH);
+      }
+      if (r < T) {
+        stage_begin(c);
+        const int32_t epD = c.next_epoch(), epX = c.next_epoch();
+        dissolve(c, r, epD, epX, false);
+        refine_loop(c, r, c.prm.M, epD);
+        stage_end(c, ST_REFINE);
+        stage_begin(c);
+        const int32_t epC = c.next_epoch();
+        aggregate(c, r, epD, epC, epA[r + 1], false);
+        stage_end(c, ST_AGG);
+      }
+    }
+    // frontiers of the next pass: A^0 = Expand_0(level-0 moves), others empty
+    const int32_t nM0 = rd_cnt(c, K_M0);
+    for (int r = 0; r <= T; ++r) {
+      epA[r] = c.next_epoch();
+      zero_cnt(c, K_A0 + r);
+    }
+    if (nM0 > 0) expand_set(c, 0, c.lM0.p, K_M0, c.lv[0].stA.p, epA[0], c.lv[0].lA.p, K_A0, nM0);
+    if (rd_cnt(c, K_A0) == 0) break;
+    if ((qnum(c) - Qpass) * (i128)ainv < Qpass) break;
+  }
+  c.res.n_changed = changed_labels(c, epCh);
+}
+
+template <class WT>
+static void copy_adj(ldl_ctx& c, const SlackCSR<WT>& g, std::vector<int64_t>& off, std::vector<int32_t>& len,
+                     std::vector<int32_t>& col, std::vector<WT>& w) {
+  const size_t n = (size_t)c.n;
+  off.resize(n);
+  len.resize(n);
+  col.resize((size_t)g.pool_top);
+  w.resize((size_t)g.pool_top);
+  CK(cudaMemcpyAsync(off.data(), g.off.p, 8 * n, cudaMemcpyDeviceToHost, c.s));
+  CK(cudaMemcpyAsync(len.data(), g.len.p, 4 * n, cudaMemcpyDeviceToHost, c.s));
+  if (g.pool_top) {
+    CK(cudaMemcpyAsync(col.data(), g.col.p, 4 * (size_t)g.pool_top, cudaMemcpyDeviceToHost, c.s));
+    CK(cudaMemcpyAsync(w.data(), g.w.p, sizeof(WT) * (size_t)g.pool_top, cudaMemcpyDeviceToHost, c.s));
+  }
+  CK(cudaStreamSynchronize(c.s));
+}
+
+// ================================================================== C ABI
+extern "C" {
+
+void ldl_default_params(ldl_params* p) {
+  if (!p) return;
+  memset(p, 0, sizeof(*p));
+  p->directed = 0;
+  p->gamma_num = 1;
+  p->gamma_den = 1;
+  p->N = 2;
+  p->L = 4;
+  p->M = 5;
+  p->M_static = 20;
+  p->alpha_inv = 1000;
+  p->beta_inv = 100;
+  p->cuda_stream = nullptr;
+}
+
+ldl_status ldl_create(const ldl_params* params, int64_t n, int64_t nnz, const int64_t* row_ptr,
+                      const int32_t* col, const int32_t* w, ldl_ctx** out) {
+  if (!out || !params || !row_ptr || (nnz > 0 && (!col || !w))) {
+    g_create_err = "null argument";
+    return LDL_E_INVALID;
+  }
+  *out = nullptr;
+  const ldl_params& p = *params;
+  if (n <= 0 || n > INT32_MAX - 1 || nnz < 0 || p.L < 0 || p.L > 7 || p.N < 0 || p.M < 0 || p.M_static < 0 ||
+      p.alpha_inv <= 0 || p.beta_inv <= 0 || p.gamma_num < 1 || p.gamma_den < 1 || p.gamma_num > 1024 ||
+      p.gamma_den > 1024) {
+    g_create_err = "invalid size or parameter";
+    return LDL_E_INVALID;
+  }
+  if (row_ptr[0] != 0 || row_ptr[n] != nnz) {
+    g_create_err = "row_ptr must start at 0 and end at nnz";
+    return LDL_E_INVALID;
+  }
+  ldl_ctx* c = new (std::nothrow) ldl_ctx();
+  if (!c) return LDL_E_NOMEM;
+  try {
+    c->prm = p;
+    c->n = n;
+    c->directed = p.directed ? 1 : 0;
+    c->bits = std::max(1, bits_for(n));
+    c->s = (cudaStream_t)p.cuda_stream;
+    CK(cudaEventCreate(&c->ev0));
+    CK(cudaEventCreate(&c->ev1));
+    c->lv.resize(p.L + 1);
+    alloc_globals(*c);
+    level_alloc(*c, 0);
+    upload_graph(*c, nnz, row_ptr, col, w);
+    static_build(*c);
+  } catch (const LdlError& e) {
+    g_create_err = e.msg;
+    free_all(*c);
+    delete c;
+    cudaGetLastError();
+    return e.st;
+  }
+  *out = c;
+  return LDL_OK;
+}
+
+ldl_status ldl_apply_batch(ldl_ctx* c, const ldl_update* updates, int64_t count, int32_t on_device,
+                           ldl_result* out) {
+  if (!c) return LDL_E_INVALID;
+  if (count < 0 || (count > 0 && !updates)) {
+    c->err = "bad batch arguments";
+    return LDL_E_INVALID;
+  }
+  try {
+    apply_batch(*c, updates, count, on_device);
+    CK(cudaStreamSynchronize(c->s));
+  } catch (const LdlError& e) {
+    c->err = e.msg;
+    cudaGetLastError();
+    return e.st;
+  }
+  if (out) {
+    *out = c->res;
+    out->labels = c->lv[0].lab.p;
+    out->n = c->n;
+    out->changed = c->lChg.p;
+    out->levels = c->T + 1;
+  }
+  return LDL_OK;
+}
+
+ldl_status ldl_modularity(const ldl_ctx* c, double* q) {
+  if (!c || !q) return LDL_E_INVALID;
+  if (c->m == 0) {
+    *q = 0.0;
+    return LDL_OK;
+  }
+  const double m = (double)c->m;
+  *q = (double)qnum(*c) / ((double)c->prm.gamma_den * m * m);
+  return LDL_OK;
+}
+
+ldl_status ldl_modularity_num(const ldl_ctx* c, int64_t* q_hi, uint64_t* q_lo, int64_t* m) {
+  if (!c) return LDL_E_INVALID;
+  const i128 q = qnum(*c);
+  if (q_hi) *q_hi = (int64_t)(q >> 64);
+  if (q_lo) *q_lo = (uint64_t)q;
+  if (m) *m = c->m;
+  return LDL_OK;
+}
+
+void ldl_destroy(ldl_ctx* c) {
+  if (!c) return;
+  try {
+    free_all(*c);
+  } catch (...) {
+  }
+  delete c;
+}
+
+const char* ldl_last_error(const ldl_ctx* c) { return c ? c->err.c_str() : g_create_err.c_str(); }
+
+int32_t ldl_levels(const ldl_ctx* c) { return c ? c->T + 1 : 0; }
+
+ldl_status ldl_get_level(const ldl_ctx* cc, int32_t r, int32_t* lab, int32_t* par, int64_t* kout, int64_t* kin,
+                         int32_t* cnt, uint8_t* alive) {
+  if (!cc || r < 0 || r > cc->T) return LDL_E_INVALID;
+  ldl_ctx& c = const_cast<ldl_ctx&>(*cc);
+  try {
+    const LevelState& L = c.lv[r];
+    const size_t n = (size_t)c.n;
+    if (lab) CK(cudaMemcpyAsync(lab, L.lab.p, 4 * n, cudaMemcpyDeviceToHost, c.s));
+    if (par) CK(cudaMemcpyAsync(par, L.par.p, 4 * n, cudaMemcpyDeviceToHost, c.s));
+    if (kout) CK(cudaMemcpyAsync(kout, L.kout.p, 8 * n, cudaMemcpyDeviceToHost, c.s));
+    if (kin) CK(cudaMemcpyAsync(kin, kin_of(c, r), 8 * n, cudaMemcpyDeviceToHost, c.s));
+    if (cnt) CK(cudaMemcpyAsync(cnt, L.cnt.p, 4 * n, cudaMemcpyDeviceToHost, c.s));
+    if (alive) CK(cudaMemcpyAsync(alive, L.alive.p, n, cudaMemcpyDeviceToHost, c.s));
+    CK(cudaStreamSynchronize(c.s));
+    if (r == c.T && par)
+      for (size_t v = 0; v < n; ++v) par[v] = -1;
+  } catch (const LdlError& e) {
+    c.err = e.msg;
+    return e.st;
+  }
+  return LDL_OK;
+}
+
+ldl_status ldl_level_nnz(const ldl_ctx* cc, int32_t r, int64_t* nnz) {
+  if (!cc || !nnz || r < 0 || r > cc->T) return LDL_E_INVALID;
+  ldl_ctx& c = const_cast<ldl_ctx&>(*cc);
+  try {
+    std::vector<int32_t> len((size_t)c.n);
+    const DBuf<int32_t>& lp = r == 0 ? c.lv[0].out0.len : c.lv[r].out.len;
+    CK(cudaMemcpyAsync(len.data(), lp.p, 4 * (size_t)c.n, cudaMemcpyDeviceToHost, c.s));
+    CK(cudaStreamSynchronize(c.s));
+    int64_t s = 0;
+    for (int32_t x : len) s += x;
+    *nnz = s;
+  } catch (const LdlError& e) {
+    c.err = e.msg;
+    return e.st;
+  }
+  return LDL_OK;
+}
+
+ldl_status ldl_get_adjacency(const ldl_ctx* cc, int32_t r, int64_t* row_ptr, int32_t* col, int64_t* w) {
+  if (!cc || !row_ptr || r < 0 || r > cc->T) return LDL_E_INVALID;
+  ldl_ctx& c = const_cast<ldl_ctx&>(*cc);
+  try {
+    std::vector<int64_t> off;
+    std::vector<int32_t> len, cl;
+    std::vector<std::pair<int32_t, int64_t>> row;
+    int64_t k = 0;
+    auto emit = [&](auto& wv) {
+      for (int64_t v = 0; v < c.n; ++v) {
+        row_ptr[v] = k;
+        row.clear();
+        for (int32_t j = 0; j < len[v]; ++j) row.emplace_back(cl[off[v] + j], (int64_t)wv[off[v] + j]);
+        std::sort(row.begin(), row.end());
+        for (auto& p : row) {
+          if (col) col[k] = p.first;
+          if (w) w[k] = p.second;
+          ++k;
+        }
+      }
+      row_ptr[c.n] = k;
+    };
+    if (r == 0) {
+      std::vector<int32_t> wv;
+      copy_adj<int32_t>(c, c.lv[0].out0, off, len, cl, wv);
+      emit(wv);
+    } else {
+      std::vector<int64_t> wv;
+      copy_adj<int64_t>(c, c.lv[r].out, off, len, cl, wv);
+      emit(wv);
+    }
+  } catch (const LdlError& e) {
+    c.err = e.msg;
+    return e.st;
+  }
+  return LDL_OK;
+}
+
+ldl_status ldl_get_communities(const ldl_ctx* cc, int64_t* kout, int64_t* kin, int64_t* e) {
+  if (!cc) return LDL_E_INVALID;
+  ldl_ctx& c = const_cast<ldl_ctx&>(*cc);
+  try {
+    const size_t n = (size_t)c.n;
+    if (kout) CK(cudaMemcpyAsync(kout, c.Kout.p, 8 * n, cudaMemcpyDeviceToHost, c.s));
+    if (kin) CK(cudaMemcpyAsync(kin, Kin_of(c), 8 * n, cudaMemcpyDeviceToHost, c.s));
+    if (e) CK(cudaMemcpyAsync(e, c.e.p, 8 * n, cudaMemcpyDeviceToHost, c.s));
+    CK(cudaStreamSynchronize(c.s));
+  } catch (const LdlError& er) {
+    c.err = er.msg;
+    return er.st;
+  }
+  return LDL_OK;
+}
+
+ldl_status ldl_stage_times(const ldl_ctx* c, double* times) {
+  if (!c || !times) return LDL_E_INVALID;
+  for (int i = 0; i < 16; ++i) times[i] = c->stage_ms[i];
+  return LDL_OK;
+}
+
+ldl_status ldl_set_timing(ldl_ctx* c, int32_t on) {
+  if (!c) return LDL_E_INVALID;
+  c->timing = on ? 1 : 0;
+  return LDL_OK;
+}
+
+void ldl_debug_fail_alloc_after(int64_t k) { g_fail_after.store(k > 0 ? k : 0); }
+
+}  // extern "C"

@@ -1,0 +1,56 @@
+// Declarations of the device primitives (prims.cu).
+#pragma once
+#include "common.cuh"
+
+struct Prims {  // scratch owned by a context
+  DBuf<int64_t> bsum, hist, hoff, pos, usum;
+  DBuf<int32_t> flag;
+  DBuf<u64> ukeys;
+  void release() {
+    bsum.release(); hist.release(); hoff.release(); pos.release(); usum.release();
+    flag.release(); ukeys.release();
+  }
+};
+
+// out[i] = sum of in[0..i); returns the total when want_total (synchronises).
+int64_t scan_exclusive(const int64_t* in, int64_t* out, int64_t n, Prims& P, cudaStream_t s, bool want_total);
+int64_t scan_exclusive_i32(const int32_t* in, int64_t* out, int64_t n, Prims& P, cudaStream_t s, bool want_total);
+
+// Stable LSD radix sort of n (key, value) pairs on the low `bits` key bits,
+// 8 bits per pass.  The sorted data ends in (keys, vals); the pointers are
+// swapped with (tk, tv) as the passes ping-pong.
+void radix_sort_pairs(u64*& keys, u64*& vals, u64*& tk, u64*& tv, int64_t n, int bits, Prims& P, cudaStream_t s);
+
+// Sorted keys -> unique keys with the int64 sum of their values, zero sums
+// dropped, order kept.  Returns the number of output pairs (synchronises).
+int64_t reduce_by_key(const u64* keys, const u64* vals, int64_t n, u64* okeys, int64_t* ovals, Prims& P,
+                      cudaStream_t s);
+
+// flag[i] = 1 where keys[i] differs from keys[i-1] (or i == 0)
+void heads_launch(const u64* keys, int64_t n, int32_t* flag, cudaStream_t s);
+
+template <class T>
+inline void swap_buf(DBuf<T>& a, DBuf<T>& b) {
+  DBuf<T> t = a;
+  a = b;
+  b = t;
+}
+
+// Sort the first n pairs of (k, v) in place (by DBuf identity) using (tk, tv).
+inline void sort_pairs(DBuf<u64>& k, DBuf<u64>& v, DBuf<u64>& tk, DBuf<u64>& tv, int64_t n, int bits, Prims& P,
+                       cudaStream_t s) {
+  tk.reserve(n, s);
+  tv.reserve(n, s);
+  u64 *kp = k.p, *vp = v.p, *tkp = tk.p, *tvp = tv.p;
+  radix_sort_pairs(kp, vp, tkp, tvp, n, bits, P, s);
+  if (kp != k.p) {
+    swap_buf(k, tk);
+    swap_buf(v, tv);
+  }
+}
+
+inline int bits_for(int64_t n) {  // bits to hold values in [0, n)
+  int b = 0;
+  while (((int64_t)1 << b) < n) ++b;
+  return b;
+}

@@ -1,0 +1,720 @@
+// Frontier sweeps of Algorithm 1: candidate-set expansion (lines 8, 12, 21),
+// BestMove / BestRef with the exact Eq. 2 gain (lines 9, 18), the decoupling
+// filter of Sec. III-E as deterministic parallel rounds, and the commit of an
+// accepted mini-batch with the additive repair of the community totals and
+// the exact modularity change dQ(B) (lines 10-11).
+#include "kern.cuh"
+
+namespace {
+
+constexpr int TPB = 256;
+constexpr int HW = 256;      // per-warp hash slots (small bin)
+constexpr int SMALL_DEG = 96;
+constexpr int HB = 8192;     // per-block hash slots (mid bin)
+constexpr int MID_DEG = 3072;
+
+// ---------------------------------------------------------------- expand
+// out = U plus every out- and in-neighbour of U (dedup by stamp).
+template <class WT>
+__global__ void k_expand(Adj<WT> out, Adj<WT> in, int directed, const int32_t* list, const int32_t* nlist,
+                         int32_t* stamp, int32_t ep, int32_t* olist, int32_t* nout) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int32_t nl = *nlist;
+  for (int64_t t = warp; t < nl; t += nw) {
+    const int32_t v = list[t];
+    if (lane == 0) stamp_add(stamp, ep, v, olist, nout);
+    {
+      const int64_t o = out.off[v];
+      const int32_t l = out.len[v];
+      for (int32_t k = lane; k < l; k += 32) stamp_add(stamp, ep, out.col[o + k], olist, nout);
+    }
+    if (directed) {
+      const int64_t o = in.off[v];
+      const int32_t l = in.len[v];
+      for (int32_t k = lane; k < l; k += 32) stamp_add(stamp, ep, in.col[o + k], olist, nout);
+    }
+  }
+}
+
+__global__ void k_filter_alive(const int32_t* list, const int32_t* nlist, const uint8_t* alive, int32_t* olist,
+                               int32_t* nout) {
+  const int32_t nl = *nlist;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nl; t += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t v = list[t];
+    if (!alive || alive[v]) olist[atomicAdd(nout, 1)] = v;
+  }
+}
+
+__global__ void k_union(const int32_t* list, const int32_t* nlist, int32_t* stamp, int32_t ep, int32_t* olist,
+                        int32_t* nout) {
+  const int32_t nl = *nlist;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nl; t += (int64_t)gridDim.x * blockDim.x)
+    stamp_add(stamp, ep, list[t], olist, nout);
+}
+
+// ---------------------------------------------------------------- sweep
+// MODE 0: BestMove over community labels.  MODE 1: BestRef over refined ids
+// (level-r parents) restricted to neighbours of the same community.
+template <class WT>
+struct SweepArgs {
+  Adj<WT> out, in;
+  int directed;
+  const int32_t* lab;
+  const int32_t* par;
+  const int64_t* kout;
+  const int64_t* kin;
+  const int64_t* Tout;  // MODE 0: community K_out; MODE 1: level r+1 k_out
+  const int64_t* Tin;
+  int64_t m, gn, gd;
+  int32_t* cv;
+  int32_t* csrc;
+  int32_t* cdst;
+  int64_t* cghi;
+  uint64_t* cglo;
+  int32_t* ncand;
+  int64_t* scanned;
+};
+
+__device__ inline void hash_add(int32_t* K, int64_t* V, uint32_t mask, int32_t key, int64_t w) {
+  uint32_t h = hash32((uint32_t)key) & mask;
+  while (true) {
+    const int32_t prev = atomicCAS(&K[h], -1, key);
+    if (prev == -1 || prev == key) {
+      atomicAdd((unsigned long long*)&V[h], (unsigned long long)w);
+      return;
+    }
+    h = (h + 1) & mask;
+  }
+}
+
+__device__ inline int64_t hash_get(const int32_t* K, const int64_t* V, uint32_t mask, int32_t key) {
+  uint32_t h = hash32((uint32_t)key) & mask;
+  while (true) {
+    const int32_t k = K[h];
+    if (k == key) return V[h];
+    if (k == -1) return 0;
+    h = (h + 1) & mask;
+  }
+}
+
+template <class WT, int MODE>
+__device__ inline void accumulate(const SweepArgs<WT>& A, const Adj<WT>& adj, int32_t v, int32_t cv_, int32_t* K,
+                                  int64_t* V, uint32_t mask, int tid, int nthreads) {
+  const int64_t o = adj.off[v];
+  const int32_t l = adj.len[v];
+  for (int32_t k = tid; k < l; k += nthreads) {
+    const int32_t u = adj.col[o + k];
+    if (u == v) continue;
+    if (MODE == 1 && A.lab[u] != cv_) continue;
+    const int32_t key = MODE == 0 ? A.lab[u] : A.par[u];
+    hash_add(K, V, mask, key, (int64_t)adj.w[o + k]);
+  }
+}
+
+// Exact gain of v into key (see Eq. 2 with a' = a \ {v}).
+template <int MODE>
+__device__ inline i128 gain_of(int32_t key, int64_t acc, int64_t wa, int32_t a, int64_t ko, int64_t ki,
+                               const int64_t* Tout, const int64_t* Tin, int64_t m, int64_t gn, int64_t gd,
+                               int64_t mult) {
+  if (MODE == 0) {
+    const i128 dw = (i128)mult * (acc - wa);
+    const i128 dd = (i128)ko * (Tin[key] - Tin[a] + ki) + (i128)ki * (Tout[key] - Tout[a] + ko);
+    return (i128)gd * m * dw - (i128)gn * dd;
+  } else {
+    const i128 dw = (i128)mult * acc;
+    const i128 dd = (i128)ko * Tin[key] + (i128)ki * Tout[key];
+    return (i128)gd * m * dw - (i128)gn * dd;
+  }
+}
+
+template <class WT>
+__device__ inline void emit_cand(const SweepArgs<WT>& A, int32_t v, int32_t src, const Best& b) {
+  const int32_t p = atomicAdd(A.ncand, 1);
+  A.cv[p] = v;
+  A.csrc[p] = src;
+  A.cdst[p] = b.c;
+  A.cghi[p] = (int64_t)(b.g >> 64);
+  A.cglo[p] = (uint64_t)b.g;
+}
+
+// one warp per node, warp-private shared hash
+template <class WT, int MODE>
+__global__ void __launch_bounds__(TPB) k_sweep_warp(SweepArgs<WT> A, const int32_t* list, const int32_t* nlist) {
+  __shared__ int32_t hk[TPB / 32][HW];
+  __shared__ int64_t hv[TPB / 32][HW];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  int32_t* K = hk[wid];
+  int64_t* V = hv[wid];
+  const int32_t nl = *nlist;
+  const int64_t mult = A.directed ? 1 : 2;
+  int64_t scanned = 0;
+  for (int64_t t = warp; t < nl; t += nw) {
+    const int32_t v = list[t];
+    for (int k = lane; k < HW; k += 32) {
+      K[k] = -1;
+      V[k] = 0;
+    }
+    __syncwarp();
+    const int32_t a = A.lab[v];
+    accumulate<WT, MODE>(A, A.out, v, a, K, V, HW - 1, lane, 32);
+    if (A.directed) accumulate<WT, MODE>(A, A.in, v, a, K, V, HW - 1, lane, 32);
+    if (lane == 0) scanned += A.out.len[v] + (A.directed ? A.in.len[v] : 0);
+    __syncwarp();
+    const int64_t wa = MODE == 0 ? hash_get(K, V, HW - 1, a) : 0;
+    const int64_t ko = A.kout[v], ki = A.kin[v];
+    Best b{0, 0, 0};
+    for (int k = lane; k < HW; k += 32) {
+      const int32_t key = K[k];
+      if (key < 0) continue;
+      if (MODE == 0 ? key == a : key == v) continue;
+      const i128 g = gain_of<MODE>(key, V[k], wa, a, ko, ki, A.Tout, A.Tin, A.m, A.gn, A.gd, mult);
+      if (g > 0) {
+        Best c{g, key, 1};
+        if (best_better(c, b)) b = c;
+      }
+    }
+    b = warp_best(b);
+    if (lane == 0 && b.have) emit_cand(A, v, MODE == 0 ? a : v, b);
+    __syncwarp();
+  }
+  if (lane == 0 && scanned) atomic_add_i64(A.scanned, scanned);
+}
+
+// one block per node; the hash lives in dynamic shared memory (mid degrees)
+// or in a global-memory slice (hubs, table != nullptr)
+template <class WT, int MODE>
+__global__ void __launch_bounds__(TPB) k_sweep_block(SweepArgs<WT> A, const int32_t* list, const int32_t* nlist,
+                                                     const int64_t* toff, const int64_t* tsz, int32_t* gK,
+                                                     int64_t* gV) {
+  extern __shared__ unsigned char smem[];
+  __shared__ Best wb[TPB / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int32_t nl = *nlist;
+  const int64_t mult = A.directed ? 1 : 2;
+  for (int64_t t = blockIdx.x; t < nl; t += gridDim.x) {
+    const int32_t v = list[t];
+    int32_t* K;
+    int64_t* V;
+    uint32_t H;
+    if (gK) {
+      K = gK + toff[t];
+      V = gV + toff[t];
+      H = (uint32_t)tsz[t];
+    } else {
+      V = (int64_t*)smem;
+      K = (int32_t*)(smem + sizeof(int64_t) * HB);
+      H = HB;
+    }
+    for (uint32_t k = threadIdx.x; k < H; k += TPB) {
+      K[k] = -1;
+      V[k] = 0;
+    }
+    __syncthreads();
+    const int32_t a = A.lab[v];
+    accumulate<WT, MODE>(A, A.out, v, a, K, V, H - 1, threadIdx.x, TPB);
+    if (A.directed) accumulate<WT, MODE>(A, A.in, v, a, K, V, H - 1, threadIdx.x, TPB);
+    __syncthreads();
+    const int64_t wa = MODE == 0 ? hash_get(K, V, H - 1, a) : 0;
+    const int64_t ko = A.kout[v], ki = A.kin[v];
+    Best b{0, 0, 0};
+    for (uint32_t k = threadIdx.x; k < H; k += TPB) {
+      const int32_t key = K[k];
+      if (key < 0) continue;
+      if (MODE == 0 ? key == a : key == v) continue;
+      const i128 g = gain_of<MODE>(key, V[k], wa, a, ko, ki, A.Tout, A.Tin, A.m, A.gn, A.gd, mult);
+      if (g > 0) {
+        Best c{g, key, 1};
+        if (best_better(c, b)) b = c;
+      }
+    }
+    b = warp_best(b);
+    if (lane == 0) wb[wid] = b;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      Best r = wb[0];
+      for (int w = 1; w < TPB / 32; ++w)
+        if (best_better(wb[w], r)) r = wb[w];
+      if (r.have) emit_cand(A, v, MODE == 0 ? a : v, r);
+      atomic_add_i64(A.scanned, (int64_t)A.out.len[v] + (A.directed ? A.in.len[v] : 0));
+    }
+    __syncthreads();
+  }
+}
+
+template <class WT>
+__global__ void k_bin(Adj<WT> out, Adj<WT> in, int directed, const int32_t* list, const int32_t* nlist,
+                      int32_t* bs, int32_t* ns, int32_t* bm, int32_t* nm, int32_t* bl, int32_t* nlarge,
+                      int64_t* loff, int64_t* lsz, int64_t* tabtop) {
+  const int32_t nl = *nlist;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nl; t += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t v = list[t];
+    const int64_t d = (int64_t)out.len[v] + (directed ? in.len[v] : 0);
+    if (d <= SMALL_DEG) {
+      bs[atomicAdd(ns, 1)] = v;
+    } else if (d <= MID_DEG) {
+      bm[atomicAdd(nm, 1)] = v;
+    } else {
+      int64_t sz = 1;
+      while (sz < 2 * d) sz <<= 1;
+      const int32_t p = atomicAdd(nlarge, 1);
+      bl[p] = v;
+      lsz[p] = sz;
+      loff[p] = (int64_t)atomicAdd((unsigned long long*)tabtop, (unsigned long long)sz);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- decouple
+// Candidate i precedes j when its gain is larger, or equal with a smaller node.
+__device__ inline bool precedes(const int64_t* ghi, const uint64_t* glo, const int32_t* cv, int32_t i, int32_t j) {
+  const i128 gi = i128_of(ghi[i], glo[i]), gj = i128_of(ghi[j], glo[j]);
+  if (gi != gj) return gi > gj;
+  return cv[i] < cv[j];
+}
+
+__device__ inline void claim(int32_t* best, int32_t c, int32_t i, const int64_t* ghi, const uint64_t* glo,
+                             const int32_t* cv) {
+  int32_t cur = best[c];
+  while (cur == -1 || precedes(ghi, glo, cv, i, cur)) {
+    const int32_t old = atomicCAS(&best[c], cur, i);
+    if (old == cur) return;
+    cur = old;
+  }
+}
+
+__global__ void k_dec_claim(int32_t nc, const int32_t* cst, const int32_t* src, const int32_t* dst,
+                            const int64_t* ghi, const uint64_t* glo, const int32_t* cv, const int32_t* role,
+                            int32_t* best) {
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) {
+    if (cst[i] != 0) continue;
+    if (role[src[i]] == 0) claim(best, src[i], i, ghi, glo, cv);
+    if (role[dst[i]] == 0) claim(best, dst[i], i, ghi, glo, cv);
+  }
+}
+
+// A candidate is decided once every earlier candidate touching its source and
+// its target is decided: either the community already has a role (set by its
+// first accepted candidate, which precedes every undecided one) or this
+// candidate is the earliest undecided one touching it.
+__global__ void k_dec_decide(int32_t nc, int32_t* cst, const int32_t* src, const int32_t* dst, const int32_t* role,
+                             const int32_t* best, int32_t* undecided) {
+  int32_t left = 0;
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) {
+    if (cst[i] != 0) continue;
+    const int32_t ra = role[src[i]], rb = role[dst[i]];
+    const bool da = ra != 0 || best[src[i]] == i;
+    const bool db = rb != 0 || best[dst[i]] == i;
+    if (da && db) {
+      cst[i] = (ra != 2 && rb != 1) ? 3 : 2;  // 3: accepted, roles pending
+    } else {
+      ++left;
+    }
+  }
+  if (left) atomicAdd(undecided, left);
+}
+
+__global__ void k_dec_roles(int32_t nc, int32_t* cst, const int32_t* src, const int32_t* dst, int32_t* role,
+                            int32_t* best) {
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) {
+    best[src[i]] = -1;
+    best[dst[i]] = -1;
+    if (cst[i] == 3) {
+      role[src[i]] = 1;  // emitter
+      role[dst[i]] = 2;  // acceptor
+      cst[i] = 1;
+    }
+  }
+}
+
+__global__ void k_dec_finish(int32_t nc, const int32_t* cst, const int32_t* cv, const int32_t* src,
+                             const int32_t* dst, int32_t* role, int32_t* bv, int32_t* bsrc, int32_t* bdst,
+                             int32_t* nb) {
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) {
+    role[src[i]] = 0;
+    role[dst[i]] = 0;
+    if (cst[i] == 1) {
+      const int32_t p = atomicAdd(nb, 1);
+      bv[p] = cv[i];
+      bsrc[p] = src[i];
+      bdst[p] = dst[i];
+    }
+  }
+}
+
+// ---------------------------------------------------------------- commit (move)
+__global__ void k_commit_mark(int32_t nb, const int32_t* bv, const int32_t* bsrc, const int32_t* bdst,
+                              int32_t* lab, int32_t* oldlab, int32_t* stB, int32_t epB, int32_t* stT, int32_t epT,
+                              int32_t* lT, int32_t* nT, int32_t* stCh, int32_t epCh, int32_t* lCh, int32_t* nCh,
+                              int32_t* lab_before, int level0) {
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nb; i += gridDim.x * blockDim.x) {
+    const int32_t v = bv[i];
+    oldlab[v] = bsrc[i];
+    stB[v] = epB;
+    if (level0 && stamp_add(stCh, epCh, v, lCh, nCh)) lab_before[v] = bsrc[i];
+    lab[v] = bdst[i];
+    stamp_add(stT, epT, bsrc[i], lT, nT);
+    stamp_add(stT, epT, bdst[i], lT, nT);
+  }
+}
+
+__global__ void k_snap(const int32_t* lT, const int32_t* nT, const int64_t* Kout, const int64_t* Kin,
+                       const int64_t* e, int64_t* sko, int64_t* ski, int64_t* se) {
+  const int32_t n = *nT;
+  for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const int32_t c = lT[k];
+    sko[k] = Kout[c];
+    ski[k] = Kin[c];
+    se[k] = e[c];
+  }
+}
+
+__global__ void k_commit_K(int32_t nb, const int32_t* bv, const int32_t* bsrc, const int32_t* bdst,
+                           const int64_t* kout, const int64_t* kin, int64_t* Kout, int64_t* Kin, int directed) {
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nb; i += gridDim.x * blockDim.x) {
+    const int32_t v = bv[i];
+    atomic_add_i64(&Kout[bsrc[i]], -kout[v]);
+    atomic_add_i64(&Kout[bdst[i]], kout[v]);
+    if (directed) {
+      atomic_add_i64(&Kin[bsrc[i]], -kin[v]);
+      atomic_add_i64(&Kin[bdst[i]], kin[v]);
+    }
+  }
+}
+
+// Internal-weight repair: every arc with a moved endpoint is counted once
+// (from the moved tail's out-row, or from the moved head's in-row when the
+// tail did not move).
+template <class WT>
+__global__ void k_commit_e(Adj<WT> out, Adj<WT> in, int32_t nb, const int32_t* bv, const int32_t* bsrc,
+                           const int32_t* bdst, const int32_t* lab, const int32_t* oldlab, const int32_t* stB,
+                           int32_t epB, int64_t* e) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t t = warp; t < nb; t += nw) {
+    const int32_t v = bv[t], a = bsrc[t], b = bdst[t];
+    int64_t da = 0, db = 0;
+    {
+      const int64_t o = out.off[v];
+      const int32_t l = out.len[v];
+      for (int32_t k = lane; k < l; k += 32) {
+        const int32_t u = out.col[o + k];
+        const int64_t w = (int64_t)out.w[o + k];
+        const bool mu = stB[u] == epB;
+        const int32_t cold = mu ? oldlab[u] : lab[u];
+        const int32_t cnew = lab[u];
+        if (cold == a) da -= w;
+        if (cnew == b) db += w;
+      }
+    }
+    {
+      const int64_t o = in.off[v];
+      const int32_t l = in.len[v];
+      for (int32_t k = lane; k < l; k += 32) {
+        const int32_t u = in.col[o + k];
+        if (stB[u] == epB) continue;
+        const int64_t w = (int64_t)in.w[o + k];
+        const int32_t cu = lab[u];
+        if (cu == a) da -= w;
+        if (cu == b) db += w;
+      }
+    }
+    da = warp_sum_i64(da);
+    db = warp_sum_i64(db);
+    if (lane == 0) {
+      if (da) atomic_add_i64(&e[a], da);
+      if (db) atomic_add_i64(&e[b], db);
+    }
+  }
+}
+
+// dQ(B) = sum over touched communities of gd*m*de_C - gn*d(K_out K_in).
+__global__ void k_commit_dq(const int32_t* lT, const int32_t* nT, const int64_t* Kout, const int64_t* Kin,
+                            const int64_t* e, const int64_t* sko, const int64_t* ski, const int64_t* se, int64_t m,
+                            int64_t gn, int64_t gd, DevScalars* sc) {
+  const int32_t n = *nT;
+  i128 dq = 0, dp = 0;
+  int64_t de = 0;
+  for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const int32_t c = lT[k];
+    const int64_t dec = e[c] - se[k];
+    const i128 dpc = (i128)Kout[c] * Kin[c] - (i128)sko[k] * ski[k];
+    de += dec;
+    dp += dpc;
+    dq += (i128)gd * m * dec - (i128)gn * dpc;
+  }
+  dq = warp_sum_i128(dq);
+  dp = warp_sum_i128(dp);
+  de = warp_sum_i64(de);
+  if ((threadIdx.x & 31) == 0) {
+    atomic_add_i128(&sc->dq, dq);
+    atomic_add_i128(&sc->dp, dp);
+    if (de) atomic_add_i64(&sc->de, de);
+  }
+}
+
+__global__ void k_rollback(int32_t nb, const int32_t* bv, const int32_t* bsrc, int32_t* lab, const int32_t* lT,
+                           const int32_t* nT, int64_t* Kout, int64_t* Kin, int64_t* e, const int64_t* sko,
+                           const int64_t* ski, const int64_t* se, int directed) {
+  const int32_t n = *nT;
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nb; i += gridDim.x * blockDim.x) lab[bv[i]] = bsrc[i];
+  for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const int32_t c = lT[k];
+    Kout[c] = sko[k];
+    if (directed) Kin[c] = ski[k];
+    e[c] = se[k];
+  }
+}
+
+__global__ void k_mark_moved(int32_t nb, const int32_t* bv, int32_t* stMv, int32_t epMv, int32_t* lMv, int32_t* nMv,
+                             int32_t* stM0, int32_t epM0, int32_t* lM0, int32_t* nM0) {
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nb; i += gridDim.x * blockDim.x) {
+    stamp_add(stMv, epMv, bv[i], lMv, nMv);
+    if (stM0) stamp_add(stM0, epM0, bv[i], lM0, nM0);
+  }
+}
+
+// ---------------------------------------------------------------- refine commit
+__global__ void k_commit_ref(int32_t nb, const int32_t* bv, const int32_t* bdst, int32_t* par, const int64_t* kout,
+                             const int64_t* kin, int64_t* kout1, int64_t* kin1, int32_t* cnt1, int directed) {
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nb; i += gridDim.x * blockDim.x) {
+    const int32_t v = bv[i], X = bdst[i];
+    par[v] = X;
+    atomic_add_i64(&kout1[X], kout[v]);
+    atomic_add_i64(&kout1[v], -kout[v]);
+    if (directed) {
+      atomic_add_i64(&kin1[X], kin[v]);
+      atomic_add_i64(&kin1[v], -kin[v]);
+    }
+    atomicAdd(&cnt1[X], 1);
+    atomicAdd(&cnt1[v], -1);
+  }
+}
+
+// SPExpand: dissolved, still-singleton neighbours of moved nodes inside the
+// moved node's community.
+template <class WT>
+__global__ void k_spexpand(Adj<WT> out, Adj<WT> in, int directed, int32_t nb, const int32_t* bv,
+                           const int32_t* lab, const int32_t* par, const int32_t* cnt1, const int32_t* stD,
+                           int32_t epD, int32_t* stR, int32_t epR, int32_t* lR, int32_t* nR) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t t = warp; t < nb; t += nw) {
+    const int32_t v = bv[t];
+    const int32_t cv_ = lab[v];
+    for (int pass = 0; pass < (directed ? 2 : 1); ++pass) {
+      const Adj<WT>& A = pass ? in : out;
+      const int64_t o = A.off[v];
+      const int32_t l = A.len[v];
+      for (int32_t k = lane; k < l; k += 32) {
+        const int32_t u = A.col[o + k];
+        if (stD[u] == epD && lab[u] == cv_ && par[u] == u && cnt1[u] == 1) stamp_add(stR, epR, u, lR, nR);
+      }
+    }
+  }
+}
+
+}  // namespace
+
+// ================================================================== host side
+void expand_set(ldl_ctx& c, int r, const int32_t* list, int idx_n, int32_t* stamp, int32_t ep, int32_t* olist,
+                int idx_out, int64_t n_hint) {
+  const int g = grid_for(n_hint * 32, TPB);
+  if (r == 0)
+    k_expand<int32_t><<<g, TPB, 0, c.s>>>(adj_out0(c), adj_in0(c), c.directed, list, c.dcnt + idx_n, stamp, ep,
+                                          olist, c.dcnt + idx_out);
+  else
+    k_expand<int64_t><<<g, TPB, 0, c.s>>>(adj_out(c, r), adj_in(c, r), c.directed, list, c.dcnt + idx_n, stamp,
+                                          ep, olist, c.dcnt + idx_out);
+  CKL("k_expand");
+}
+
+void filter_alive(ldl_ctx& c, int r, const int32_t* list, int idx_n, int32_t* olist, int idx_out, int64_t n_hint) {
+  k_filter_alive<<<grid_for(n_hint, TPB), TPB, 0, c.s>>>(list, c.dcnt + idx_n, r ? c.lv[r].alive.p : nullptr, olist,
+                                                         c.dcnt + idx_out);
+  CKL("k_filter_alive");
+}
+
+void union_into(ldl_ctx& c, const int32_t* list, int idx_n, int32_t* stamp, int32_t ep, int32_t* olist, int idx_out,
+                int64_t n_hint) {
+  k_union<<<grid_for(n_hint, TPB), TPB, 0, c.s>>>(list, c.dcnt + idx_n, stamp, ep, olist, c.dcnt + idx_out);
+  CKL("k_union");
+}
+
+template <class WT, int MODE>
+static int32_t sweep_t(ldl_ctx& c, int r, Adj<WT> out, Adj<WT> in, const int32_t* list, int idx_n, int64_t n_hint) {
+  LevelState& L = c.lv[r];
+  SweepArgs<WT> A;
+  A.out = out;
+  A.in = in;
+  A.directed = c.directed;
+  A.lab = L.lab.p;
+  A.par = L.par.p;
+  A.kout = L.kout.p;
+  A.kin = kin_of(c, r);
+  if (MODE == 0) {
+    A.Tout = c.Kout.p;
+    A.Tin = Kin_of(c);
+  } else {
+    A.Tout = c.lv[r + 1].kout.p;
+    A.Tin = kin_of(c, r + 1);
+  }
+  A.m = c.m;
+  A.gn = c.prm.gamma_num;
+  A.gd = c.prm.gamma_den;
+  A.cv = c.cv.p;
+  A.csrc = c.csrc.p;
+  A.cdst = c.cdst.p;
+  A.cghi = c.cghi.p;
+  A.cglo = c.cglo.p;
+  A.ncand = c.dcnt + K_CAND;
+  A.scanned = &c.d_sc->scanned;
+  zero_cnt(c, K_CAND);
+  zero_cnt(c, K_SMALL);
+  zero_cnt(c, K_MID);
+  zero_cnt(c, K_LARGE);
+  CK(cudaMemsetAsync(&c.d_sc->need, 0, sizeof(int64_t), c.s));
+  k_bin<WT><<<grid_for(n_hint, TPB), TPB, 0, c.s>>>(out, in, c.directed, list, c.dcnt + idx_n, c.binS.p,
+                                                     c.dcnt + K_SMALL, c.binM.p, c.dcnt + K_MID, c.binL.p,
+                                                     c.dcnt + K_LARGE, c.binLoff.p, c.binLsz.p, &c.d_sc->need);
+  CKL("k_bin");
+  int32_t counts[3];
+  int64_t tab = 0;
+  CK(cudaMemcpyAsync(counts, c.dcnt + K_SMALL, sizeof(int32_t) * 3, cudaMemcpyDeviceToHost, c.s));
+  CK(cudaMemcpyAsync(&tab, &c.d_sc->need, sizeof(int64_t), cudaMemcpyDeviceToHost, c.s));
+  CK(cudaStreamSynchronize(c.s));
+  if (counts[0] > 0) {
+    k_sweep_warp<WT, MODE><<<grid_for((int64_t)counts[0] * 32, TPB), TPB, 0, c.s>>>(A, c.binS.p, c.dcnt + K_SMALL);
+    CKL("k_sweep_warp");
+  }
+  if (counts[1] > 0) {
+    const size_t sm = (sizeof(int64_t) + sizeof(int32_t)) * HB;
+    CK(cudaFuncSetAttribute(k_sweep_block<WT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_sweep_block<WT, MODE><<<grid_for(counts[1], 1, 152 * 8), TPB, sm, c.s>>>(A, c.binM.p, c.dcnt + K_MID, nullptr,
+                                                                             nullptr, nullptr, nullptr);
+    CKL("k_sweep_block(mid)");
+  }
+  if (counts[2] > 0) {
+    c.gkeys.reserve(tab, c.s);
+    c.gvals.reserve(tab, c.s);
+    k_sweep_block<WT, MODE><<<grid_for(counts[2], 1, 152 * 4), TPB, 0, c.s>>>(
+        A, c.binL.p, c.dcnt + K_LARGE, c.binLoff.p, c.binLsz.p, c.gkeys.p, c.gvals.p);
+    CKL("k_sweep_block(hub)");
+  }
+  return rd_cnt(c, K_CAND);
+}
+
+int32_t sweep(ldl_ctx& c, int r, int mode, const int32_t* list, int idx_n, int64_t n_hint) {
+  if (r == 0)
+    return mode == 0 ? sweep_t<int32_t, 0>(c, r, adj_out0(c), adj_in0(c), list, idx_n, n_hint)
+                     : sweep_t<int32_t, 1>(c, r, adj_out0(c), adj_in0(c), list, idx_n, n_hint);
+  return mode == 0 ? sweep_t<int64_t, 0>(c, r, adj_out(c, r), adj_in(c, r), list, idx_n, n_hint)
+                   : sweep_t<int64_t, 1>(c, r, adj_out(c, r), adj_in(c, r), list, idx_n, n_hint);
+}
+
+int32_t decouple(ldl_ctx& c, int32_t nc) {
+  if (nc <= 0) return 0;
+  CK(cudaMemsetAsync(c.cst.p, 0, sizeof(int32_t) * (size_t)nc, c.s));
+  const int g = grid_for(nc, TPB);
+  int rounds = 0;
+  while (true) {
+    // a few rounds per host check: rounds past completion change nothing
+    for (int k = 0; k < 4; ++k) {
+      k_dec_claim<<<g, TPB, 0, c.s>>>(nc, c.cst.p, c.csrc.p, c.cdst.p, c.cghi.p, c.cglo.p, c.cv.p, c.role.p,
+                                      c.best.p);
+      CKL("k_dec_claim");
+      zero_cnt(c, K_UNDEC);
+      k_dec_decide<<<g, TPB, 0, c.s>>>(nc, c.cst.p, c.csrc.p, c.cdst.p, c.role.p, c.best.p, c.dcnt + K_UNDEC);
+      CKL("k_dec_decide");
+      k_dec_roles<<<g, TPB, 0, c.s>>>(nc, c.cst.p, c.csrc.p, c.cdst.p, c.role.p, c.best.p);
+      CKL("k_dec_roles");
+      ++rounds;
+    }
+    if (rd_cnt(c, K_UNDEC) == 0) break;
+    if (rounds > 4 * (int64_t)nc + 64) ldl_throw(LDL_E_INVALID, "internal: decoupling did not converge");
+  }
+  zero_cnt(c, K_B);
+  k_dec_finish<<<g, TPB, 0, c.s>>>(nc, c.cst.p, c.cv.p, c.csrc.p, c.cdst.p, c.role.p, c.bv.p, c.bsrc.p, c.bdst.p,
+                                   c.dcnt + K_B);
+  CKL("k_dec_finish");
+  return rd_cnt(c, K_B);
+}
+
+CommitOut commit_move(ldl_ctx& c, int r, int32_t nb, int32_t epB, int32_t epT, int32_t epCh) {
+  LevelState& L = c.lv[r];
+  const int g = grid_for(nb, TPB);
+  zero_cnt(c, K_T);
+  k_commit_mark<<<g, TPB, 0, c.s>>>(nb, c.bv.p, c.bsrc.p, c.bdst.p, L.lab.p, c.oldlab.p, c.stB.p, epB, c.stT.p, epT,
+                                    c.lT.p, c.dcnt + K_T, c.stCh.p, epCh, c.lCh.p, c.dcnt + K_CH, c.lab_before.p,
+                                    r == 0);
+  CKL("k_commit_mark");
+  k_snap<<<grid_for(2 * (int64_t)nb, TPB), TPB, 0, c.s>>>(c.lT.p, c.dcnt + K_T, c.Kout.p, Kin_of(c), c.e.p,
+                                                          c.snapKo.p, c.snapKi.p, c.snapE.p);
+  CKL("k_snap");
+  k_commit_K<<<g, TPB, 0, c.s>>>(nb, c.bv.p, c.bsrc.p, c.bdst.p, L.kout.p, kin_of(c, r), c.Kout.p, Kin_of(c),
+                                 c.directed);
+  CKL("k_commit_K");
+  const int gw = grid_for((int64_t)nb * 32, TPB);
+  if (r == 0)
+    k_commit_e<int32_t><<<gw, TPB, 0, c.s>>>(adj_out0(c), adj_in0(c), nb, c.bv.p, c.bsrc.p, c.bdst.p, L.lab.p,
+                                             c.oldlab.p, c.stB.p, epB, c.e.p);
+  else
+    k_commit_e<int64_t><<<gw, TPB, 0, c.s>>>(adj_out(c, r), adj_in(c, r), nb, c.bv.p, c.bsrc.p, c.bdst.p, L.lab.p,
+                                             c.oldlab.p, c.stB.p, epB, c.e.p);
+  CKL("k_commit_e");
+  CK(cudaMemsetAsync(&c.d_sc->dq, 0, sizeof(I128), c.s));
+  CK(cudaMemsetAsync(&c.d_sc->dp, 0, sizeof(I128), c.s));
+  CK(cudaMemsetAsync(&c.d_sc->de, 0, sizeof(int64_t), c.s));
+  k_commit_dq<<<grid_for(2 * (int64_t)nb, TPB), TPB, 0, c.s>>>(c.lT.p, c.dcnt + K_T, c.Kout.p, Kin_of(c), c.e.p,
+                                                               c.snapKo.p, c.snapKi.p, c.snapE.p, c.m,
+                                                               c.prm.gamma_num, c.prm.gamma_den, c.d_sc);
+  CKL("k_commit_dq");
+  DevScalars h;
+  CK(cudaMemcpyAsync(&h, c.d_sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, c.s));
+  CK(cudaStreamSynchronize(c.s));
+  CommitOut o;
+  o.dq = i128_of(h.dq.hi, h.dq.lo);
+  o.dp = i128_of(h.dp.hi, h.dp.lo);
+  o.de = h.de;
+  o.ntc = rd_cnt(c, K_T);
+  return o;
+}
+
+void rollback_move(ldl_ctx& c, int r, int32_t nb, int32_t ntc) {
+  LevelState& L = c.lv[r];
+  const int64_t m = nb > ntc ? nb : ntc;
+  k_rollback<<<grid_for(m, TPB), TPB, 0, c.s>>>(nb, c.bv.p, c.bsrc.p, L.lab.p, c.lT.p, c.dcnt + K_T, c.Kout.p,
+                                                Kin_of(c), c.e.p, c.snapKo.p, c.snapKi.p, c.snapE.p, c.directed);
+  CKL("k_rollback");
+}
+
+void mark_moved(ldl_ctx& c, int r, int32_t nb, int32_t epMv, int32_t epM0) {
+  k_mark_moved<<<grid_for(nb, TPB), TPB, 0, c.s>>>(nb, c.bv.p, c.stMv.p, epMv, c.lMv.p, c.dcnt + K_MV,
+                                                   r == 0 ? c.stM0.p : nullptr, epM0, c.lM0.p, c.dcnt + K_M0);
+  CKL("k_mark_moved");
+}
+
+void commit_ref(ldl_ctx& c, int r, int32_t nb) {
+  LevelState& L = c.lv[r];
+  LevelState& N = c.lv[r + 1];
+  k_commit_ref<<<grid_for(nb, TPB), TPB, 0, c.s>>>(nb, c.bv.p, c.bdst.p, L.par.p, L.kout.p, kin_of(c, r), N.kout.p,
+                                                   kin_of(c, r + 1), N.cnt.p, c.directed);
+  CKL("k_commit_ref");
+}
+
+void spexpand(ldl_ctx& c, int r, int32_t nb, int32_t epD, int32_t epR, int32_t* lR, int idx_R) {
+  LevelState& L = c.lv[r];
+  const int g = grid_for((int64_t)nb * 32, TPB);
+  if (r == 0)
+    k_spexpand<int32_t><<<g, TPB, 0, c.s>>>(adj_out0(c), adj_in0(c), c.directed, nb, c.bv.p, L.lab.p, L.par.p,
+                                            c.lv[r + 1].cnt.p, c.stD.p, epD, c.stR.p, epR, lR, c.dcnt + idx_R);
+  else
+    k_spexpand<int64_t><<<g, TPB, 0, c.s>>>(adj_out(c, r), adj_in(c, r), c.directed, nb, c.bv.p, L.lab.p, L.par.p,
+                                            c.lv[r + 1].cnt.p, c.stD.p, epD, c.stR.p, epR, lR, c.dcnt + idx_R);
+  CKL("k_spexpand");
+}

@@ -1,0 +1,228 @@
+"""Python binding of the C ABI in include/ldl.h (argument marshalling only).
+
+Every step of the update runs in the CUDA library libldl.so; this module only
+converts numpy arrays / torch tensors to pointers and status codes to
+exceptions.  There is no CPU fallback: if the library cannot be loaded the
+import of LDL raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+from typing import Optional
+
+import numpy as np
+
+from .build import LIB, build
+
+LDL_OK, LDL_E_INVALID, LDL_E_RANGE, LDL_E_NO_EDGE, LDL_E_NEG_WEIGHT, LDL_E_NOMEM, LDL_E_CUDA, \
+    LDL_E_TIMEOUT, LDL_E_OVERFLOW = range(9)
+INSERT, DELETE, REWEIGHT = 0, 1, 2
+STATUS_NAMES = {0: "OK", 1: "INVALID", 2: "RANGE", 3: "NO_EDGE", 4: "NEG_WEIGHT", 5: "NOMEM",
+                6: "CUDA", 7: "TIMEOUT", 8: "OVERFLOW"}
+STAGES = ["ingest", "repair", "expand", "bestmove", "decouple", "commit", "refine", "aggregate",
+          "pushdown"]
+
+
+class ldl_params(C.Structure):
+    _fields_ = [("directed", C.c_int32), ("gamma_num", C.c_int32), ("gamma_den", C.c_int32),
+                ("N", C.c_int32), ("L", C.c_int32), ("M", C.c_int32), ("M_static", C.c_int32),
+                ("alpha_inv", C.c_int32), ("beta_inv", C.c_int32), ("cuda_stream", C.c_void_p)]
+
+
+class ldl_result(C.Structure):
+    _fields_ = [("labels", C.c_void_p), ("n", C.c_int64), ("changed", C.c_void_p),
+                ("n_changed", C.c_int64), ("levels", C.c_int32),
+                ("frontier_nodes", C.c_int64 * 8), ("edges_scanned", C.c_int64),
+                ("moves", C.c_int64), ("refine_moves", C.c_int64), ("rejected", C.c_int64),
+                ("rollbacks", C.c_int64), ("rounds", C.c_int64), ("agg_records", C.c_int64)]
+
+
+class LdlError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def load(path: Optional[str] = None):
+    """Load libldl.so (building it first when the sources are newer)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if path is None:
+        path = build()
+    if not os.path.exists(path):
+        raise OSError(f"CUDA library not found: {path}")
+    lib = C.CDLL(path)
+    P, I32, I64 = C.c_void_p, C.c_int32, C.c_int64
+    sig = {
+        "ldl_default_params": (None, [P]),
+        "ldl_create": (I32, [P, I64, I64, P, P, P, P]),
+        "ldl_apply_batch": (I32, [P, P, I64, I32, P]),
+        "ldl_modularity": (I32, [P, P]),
+        "ldl_modularity_num": (I32, [P, P, P, P]),
+        "ldl_destroy": (None, [P]),
+        "ldl_last_error": (C.c_char_p, [P]),
+        "ldl_levels": (I32, [P]),
+        "ldl_get_level": (I32, [P, I32, P, P, P, P, P, P]),
+        "ldl_level_nnz": (I32, [P, I32, P]),
+        "ldl_get_adjacency": (I32, [P, I32, P, P, P]),
+        "ldl_get_communities": (I32, [P, P, P, P]),
+        "ldl_stage_times": (I32, [P, P]),
+        "ldl_set_timing": (I32, [P, I32]),
+        "ldl_debug_fail_alloc_after": (None, [I64]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    """Names the header declares (for the export check)."""
+    return ["ldl_default_params", "ldl_create", "ldl_apply_batch", "ldl_modularity",
+            "ldl_modularity_num", "ldl_destroy", "ldl_last_error", "ldl_levels", "ldl_get_level",
+            "ldl_level_nnz", "ldl_get_adjacency", "ldl_get_communities", "ldl_stage_times",
+            "ldl_set_timing", "ldl_debug_fail_alloc_after"]
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return C.c_void_p(a.data_ptr())
+    return a.ctypes.data_as(C.c_void_p)
+
+
+@dataclass
+class Level:
+    lab: np.ndarray
+    par: np.ndarray
+    kout: np.ndarray
+    kin: np.ndarray
+    cnt: np.ndarray
+    alive: np.ndarray
+
+
+class LDL:
+    """One device-resident LD-Leiden instance (ldl_create ... ldl_destroy)."""
+
+    def __init__(self, n, row_ptr, col, w, directed=False, gamma_num=1, gamma_den=1, N=2, L=4, M=5,
+                 M_static=20, alpha_inv=1000, beta_inv=100, stream=None):
+        lib = load()
+        p = ldl_params()
+        lib.ldl_default_params(C.byref(p))
+        p.directed, p.gamma_num, p.gamma_den = int(directed), gamma_num, gamma_den
+        p.N, p.L, p.M, p.M_static = N, L, M, M_static
+        p.alpha_inv, p.beta_inv = alpha_inv, beta_inv
+        p.cuda_stream = stream
+        self.n = int(n)
+        self.directed = bool(directed)
+        rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+        cl = np.ascontiguousarray(col, dtype=np.int32)
+        wt = np.ascontiguousarray(w, dtype=np.int32)
+        h = C.c_void_p()
+        st = lib.ldl_create(C.byref(p), self.n, len(cl), _ptr(rp), _ptr(cl), _ptr(wt), C.byref(h))
+        if st != LDL_OK:
+            raise LdlError(st, lib.ldl_last_error(None).decode())
+        self._h = h
+        self.last = ldl_result()
+
+    @classmethod
+    def from_graph(cls, g, **kw):
+        return cls(g.n, g.row_ptr, g.col, g.w, directed=g.directed, **kw)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().ldl_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st):
+        if st != LDL_OK:
+            raise LdlError(st, load().ldl_last_error(self._h).decode())
+
+    def apply(self, batch, on_device: bool = False) -> ldl_result:
+        """Apply one batch: an int32 array of shape (count, 4) = (src, dst, op, w),
+        host (numpy) or device (torch CUDA tensor with on_device=True)."""
+        if on_device:
+            cnt = int(batch.shape[0])
+            ptr = _ptr(batch)
+        else:
+            batch = np.ascontiguousarray(batch, dtype=np.int32).reshape(-1, 4)
+            cnt = batch.shape[0]
+            ptr = _ptr(batch)
+        self._check(load().ldl_apply_batch(self._h, ptr, cnt, int(on_device), C.byref(self.last)))
+        return self.last
+
+    def try_apply(self, batch) -> int:
+        batch = np.ascontiguousarray(batch, dtype=np.int32).reshape(-1, 4)
+        return int(load().ldl_apply_batch(self._h, _ptr(batch), batch.shape[0], 0, C.byref(self.last)))
+
+    def modularity(self) -> float:
+        q = C.c_double()
+        self._check(load().ldl_modularity(self._h, C.byref(q)))
+        return q.value
+
+    def numerator(self):
+        hi, lo, m = C.c_int64(), C.c_uint64(), C.c_int64()
+        self._check(load().ldl_modularity_num(self._h, C.byref(hi), C.byref(lo), C.byref(m)))
+        return int(m.value), (int(hi.value) << 64) + int(lo.value)
+
+    @property
+    def levels(self) -> int:
+        return int(load().ldl_levels(self._h))
+
+    @property
+    def top(self) -> int:
+        return self.levels - 1
+
+    def level(self, r: int) -> Level:
+        n = self.n
+        a = [np.zeros(n, np.int32), np.zeros(n, np.int32), np.zeros(n, np.int64),
+             np.zeros(n, np.int64), np.zeros(n, np.int32), np.zeros(n, np.uint8)]
+        self._check(load().ldl_get_level(self._h, r, *[_ptr(x) for x in a]))
+        return Level(*a)
+
+    def labels(self) -> np.ndarray:
+        return self.level(0).lab
+
+    def level_adj(self, r: int):
+        nnz = C.c_int64()
+        self._check(load().ldl_level_nnz(self._h, r, C.byref(nnz)))
+        rp = np.zeros(self.n + 1, np.int64)
+        col = np.zeros(nnz.value, np.int32)
+        w = np.zeros(nnz.value, np.int64)
+        self._check(load().ldl_get_adjacency(self._h, r, _ptr(rp), _ptr(col), _ptr(w)))
+        return rp, col, w
+
+    def comm(self):
+        a = [np.zeros(self.n, np.int64) for _ in range(3)]
+        self._check(load().ldl_get_communities(self._h, *[_ptr(x) for x in a]))
+        return tuple(a)
+
+    def set_timing(self, on: bool = True):
+        self._check(load().ldl_set_timing(self._h, int(on)))
+
+    def stage_times(self) -> dict:
+        t = np.zeros(16, np.float64)
+        self._check(load().ldl_stage_times(self._h, _ptr(t)))
+        return dict(zip(STAGES, t.tolist()))
+
+    def result_dict(self) -> dict:
+        r = self.last
+        return dict(n_changed=r.n_changed, levels=r.levels, frontier_nodes=list(r.frontier_nodes),
+                    edges_scanned=r.edges_scanned, moves=r.moves, refine_moves=r.refine_moves,
+                    rejected=r.rejected, rollbacks=r.rollbacks, rounds=r.rounds,
+                    agg_records=r.agg_records)

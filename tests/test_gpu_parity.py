@@ -1,0 +1,116 @@
+"""GPU parity: the CUDA library against the oracle, bit for bit (GB300 only).
+
+Every test builds the same seeded graph and batches for both sides, runs the
+oracle on the CPU and the library through its C ABI, and compares the whole
+state (hierarchy, labels, strengths, adjacency of every level, community
+totals, m and the Eq. 1 numerator) after creation and after every batch.
+Integer state must match exactly; the reported modularity within 1e-12
+relative.
+"""
+import numpy as np
+import pytest
+
+from oracle import Oracle
+from synth import (EdgeStream, planted_partition, planted_stream, random_batch, random_small_graph,
+                   rmat_directed, rmat_stream)
+from tests.parity import compare_states
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ldl():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    from paper_2502_18497_gb300 import ldl as mod
+    mod.load()
+    return mod
+
+
+def _pair(ldl, g, **params):
+    o = Oracle(g, **params)
+    d = ldl.LDL.from_graph(g, **params)
+    return o, d
+
+
+def _assert_same(o, d, where, **kw):
+    msgs = compare_states(o, d, where, **kw)
+    assert not msgs, "\n".join(msgs[:12])
+
+
+@pytest.mark.parametrize("directed", [False, True])
+@pytest.mark.parametrize("L,Mst", [(0, 1), (0, 3), (0, 20), (1, 1), (1, 20), (4, 20)])
+def test_static_build_small(ldl, directed, L, Mst):
+    for seed in range(6):
+        g = random_small_graph(12 + 5 * seed, 0.25, directed, wmax=5, seed=seed, self_loops=seed % 2 == 0)
+        if not g.nnz:
+            continue
+        o, d = _pair(ldl, g, L=L, M_static=Mst)
+        _assert_same(o, d, f"seed {seed} create")
+
+
+@pytest.mark.parametrize("directed", [False, True])
+def test_random_streams(ldl, directed):
+    for seed in range(8):
+        g = random_small_graph(20 + 7 * seed, 0.2, directed, wmax=4, seed=50 + seed)
+        if not g.nnz:
+            continue
+        params = dict(L=1 + seed % 4, M_static=2 + seed % 5, M=1 + seed % 5, N=1 + seed % 3)
+        o, d = _pair(ldl, g, **params)
+        _assert_same(o, d, f"seed {seed} create")
+        st = EdgeStream.from_graph(g, seed)
+        for t in range(8):
+            m = len(st.keys)
+            b = random_batch(st, 4, min(3, m), min(2, max(0, m - 3)), 4, seed * 97 + t)
+            assert o.apply(b) == 0
+            d.apply(b)
+            _assert_same(o, d, f"seed {seed} batch {t}")
+
+
+def test_planted_partition_full(ldl):
+    """The 10,000-vertex planted-partition stream: static Leiden, then 10
+    batches of 100 updates (70 inserts, 20 deletes, 10 reweights)."""
+    g = planted_partition()
+    o, d = _pair(ldl, g)
+    _assert_same(o, d, "create")
+    for t, b in enumerate(planted_stream(g)):
+        assert o.apply(b) == 0
+        d.apply(b)
+        _assert_same(o, d, f"batch {t}")
+        assert np.array_equal(o.labels(), np.asarray(d.labels()))
+
+
+def test_rmat_directed_reduced(ldl):
+    """Directed R-MAT with the paper-stream skew at 2^14 vertices / 2^18 arcs,
+    20 batches of 1,000 arc updates (80% inserts, 20% deletes)."""
+    g = rmat_directed(scale=14, arcs=1 << 18, seed=12)
+    o, d = _pair(ldl, g)
+    _assert_same(o, d, "create", adjacency=False)
+    for t, b in enumerate(rmat_stream(g, batches=20, size=1000, seed=12)):
+        assert o.apply(b) == 0
+        d.apply(b)
+        _assert_same(o, d, f"batch {t}", adjacency=(t % 5 == 4))
+
+
+@pytest.mark.parametrize("bad,status", [
+    ([[0, 10_000, 0, 1]], 2), ([[0, 1, 7, 1]], 1), ([[0, 1, 0, 0]], 1), ([[0, 1, 2, -3]], 4),
+    ([[2, 999, 1, 0]], 3), ([[5, 6, 0, 2**31 - 1], [5, 6, 0, 2**31 - 1]], 8),
+])
+def test_invalid_batches(ldl, bad, status):
+    g = planted_partition(n=1000, block=50, seed=7)
+    o, d = _pair(ldl, g)
+    batch = np.array([[1, 2, 0, 1]] + bad, np.int32)
+    assert o.apply(batch) == status
+    assert d.try_apply(batch) == status
+    _assert_same(o, d, "after rejected batch")
+
+
+def test_empty_and_null_batches(ldl):
+    g = planted_partition(n=1000, block=50, seed=6)
+    o, d = _pair(ldl, g)
+    s, t, w = int(g.arcs()[0][0]), int(g.arcs()[1][0]), int(g.w[0])
+    for b in (np.zeros((0, 4), np.int32), np.array([[s, t, 2, w + 1], [s, t, 2, w]], np.int32)):
+        assert o.apply(b) == 0
+        d.apply(b)
+        _assert_same(o, d, "after null batch")
