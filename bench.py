@@ -1,0 +1,289 @@
+#!/usr/bin/env python3
+"""Throughput of LD-Leiden batch updates on GB300.
+
+Workload: a directed weighted R-MAT graph (a,b,c,d) = (0.57,0.19,0.19,0.05),
+2^20 vertices, 2^24 arcs, weights uniform 1..16, built into its initial
+hierarchy by the library's static Leiden run, then a stream of batches of
+10^4 arc updates (80% inserts of new R-MAT-skewed arcs, 20% deletes of
+existing arcs).  A step is one ldl_apply_batch: ingest, statistic repair,
+N=2 passes of frontier move / refine / aggregate repair over every level.
+
+Reported (one JSON line on rank 0):
+  value      updates/s with the batches already resident in HBM
+  e2e        the same through the public API from pinned host buffers, with
+             the batch upload and the read-back of the changed labels inside
+             the timed region
+  roofline   the dominant sweep kernel's algorithmic bytes / its event-timed
+             duration, against the measured HBM copy bandwidth
+  cpu_baseline  the sequential oracle on the host on a bounded sample
+The graph state (adjacency of every level plus per-level arrays) is larger
+than the 129 MB L2, so no explicit flush is done between steps.
+
+Multi-GPU (torchrun): every rank runs an independent replica (the path has no
+exchange step); value is the total updates of all ranks / the slowest rank.
+`--impl reference` times the oracle instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+SCALE, ARCS, WMAX, SEED, BATCH = 20, 1 << 24, 16, 2, 10_000
+WORKLOAD = ("directed R-MAT (0.57,0.19,0.19,0.05), 2^20 vertices, 2^24 arcs, weights 1..16; "
+            "batches of 10^4 arc updates (80% insert / 20% delete)")
+
+# DRAM traffic of the dominant sweep kernel from one ncu capture, valid only
+# for the sweep source it was taken with (sha256 of csrc/sweep.cu); bytes per
+# launch at this workload.  None until a capture exists.
+NCU_TRAFFIC = {"sha256": None, "bytes_per_launch": None, "kernel": None}
+
+
+def _workload(nbatches: int):
+    from synth import rmat_workload
+    return rmat_workload(nbatches, scale=SCALE, arcs=ARCS, batch=BATCH, seed=SEED, wmax=WMAX)
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            p = json.load(f)
+        return float(p.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.p = None
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                       "-i", str(index), "-lms", "200"], stdout=subprocess.PIPE,
+                                      stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+            out, _ = self.p.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_baseline(g, batches, budget_s: float = 30.0):
+    """The oracle as it stands, single-threaded on the host: its own static
+    Leiden (untimed), then whole batches of the same stream until the budget."""
+    from oracle import Oracle
+    t0 = time.perf_counter()
+    o = Oracle(g)
+    create_s = time.perf_counter() - t0
+    done, spent = 0, 0.0
+    for b in batches:
+        t = time.perf_counter()
+        assert o.apply(b) == 0
+        spent += time.perf_counter() - t
+        done += 1
+        if spent >= budget_s:
+            break
+    ups = done * len(batches[0]) / spent
+    return {"value": ups, "unit": "updates/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {done} batch(es) of 10^4 updates of the same stream after the oracle's own "
+                      f"static Leiden ({create_s:.0f} s, untimed); sequential C++, 1 of {os.cpu_count()} cores"}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    g, batches = _workload(args.warmup + args.steps + 1)
+    from oracle import Oracle
+    t0 = time.perf_counter()
+    o = Oracle(g)
+    create_s = time.perf_counter() - t0
+    for b in batches[:args.warmup]:
+        o.apply(b)
+    t = time.perf_counter()
+    for b in batches[args.warmup:args.warmup + args.steps]:
+        assert o.apply(b) == 0
+    el = time.perf_counter() - t
+    ups = args.steps * BATCH / el
+    line = {"metric": "updates/s", "value": ups, "unit": "updates/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": WORKLOAD, "parallelism": "single-threaded oracle"},
+            "cpu_baseline": {"value": ups, "unit": "updates/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} timed batches after {args.warmup} warm-up batches and "
+                                       f"the oracle's own static Leiden ({create_s:.0f} s, untimed)"},
+            "e2e": {"value": ups, "unit": "updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--stage-times", action="store_true", help="per-stage device times (adds syncs)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2502_18497_gb300 import LDL, ldl as binding
+
+    W, K = args.warmup, args.steps
+    g, batches = _workload(W + 2 * K)
+    t0 = time.perf_counter()
+    d = LDL.from_graph(g)
+    torch.cuda.synchronize()
+    create_s = time.perf_counter() - t0
+    dev = [torch.from_numpy(np.ascontiguousarray(b)).cuda() for b in batches[:W + K]]
+    for b in dev[:W]:
+        d.apply(b, on_device=True)
+    torch.cuda.synchronize()
+
+    # ---- device-resident timed region
+    d.set_kernel_stats(True)
+    if args.stage_times:
+        d.set_timing(True)
+    clocks = ClockSampler(local)
+    launches0 = binding.launch_count()
+    scanned = 0
+    lat = []
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for b in dev[W:W + K]:
+        t = time.perf_counter()
+        r = d.apply(b, on_device=True)
+        lat.append(time.perf_counter() - t)
+        scanned += r.edges_scanned
+    e1.record()
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    ms = e0.elapsed_time(e1)
+    launches = binding.launch_count() - launches0
+    clk = clocks.stop()
+    ks = d.kernel_stats()
+    stage = d.stage_times() if args.stage_times else None
+    d.set_kernel_stats(False)
+    d.set_timing(False)
+    if ws > 1:
+        tt = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        ms = float(tt.item())
+    ups = ws * K * BATCH / (ms / 1e3)
+
+    # ---- end to end through the public API from pinned host memory
+    host = [torch.from_numpy(np.ascontiguousarray(b)).pin_memory() for b in batches[W + K:W + 2 * K]]
+    h2d = d2h = 0
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for b in host:
+        d.apply(b)
+        ids, labs = d.changed()
+        h2d += b.numel() * 4
+        d2h += ids.nbytes + labs.nbytes
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t
+    if ws > 1:
+        tt = torch.tensor([e2e_s], device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    e2e = {"value": ws * K * BATCH / e2e_s, "unit": "updates/s", "h2d_bytes_per_step": h2d // K,
+           "d2h_bytes_per_step": d2h // K}
+
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return
+
+    # ---- roofline of the dominant sweep kernel
+    peak, peak_src = _peaks()
+    dom = max(ks, key=lambda k: ks[k]["ms"])
+    k = ks[dom]
+    achieved = k["bytes"] / (k["ms"] / 1e3) / 1e9 if k["ms"] > 0 else 0.0
+    sha = hashlib.sha256(open(os.path.join(ROOT, "paper_2502_18497_gb300", "csrc", "sweep.cu"), "rb").read()).hexdigest()
+    traffic = NCU_TRAFFIC["bytes_per_launch"] if NCU_TRAFFIC["sha256"] == sha and NCU_TRAFFIC["kernel"] == dom else None
+    roofline = {"bound": "hbm", "kernel": f"k_{dom}", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": peak_src, "traffic": traffic,
+                "launches": k["launches"], "ms_total": k["ms"], "algorithmic_bytes_per_launch":
+                    k["bytes"] / max(k["launches"], 1)}
+
+    line = {"metric": "updates/s", "value": ups, "unit": "updates/s", "n_gpus": ws, "steps": K, "warmup": W,
+            "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "int64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "l2": "state larger than L2 (no flush)",
+                       "parallelism": "replicas" if ws > 1 else "single GPU", "create_s": round(create_s, 2)},
+            "frontier_edges_per_s": scanned / (ms / 1e3) * ws,
+            "latency_ms": {"p50": 1e3 * float(np.percentile(lat, 50)), "p99": 1e3 * float(np.percentile(lat, 99))},
+            "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk}
+    if stage:
+        line["stage_ms_per_step"] = {k2: v / K for k2, v in stage.items()}
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(g, batches[:3], args.cpu_budget)
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -172,11 +172,31 @@ ldl_status ldl_get_adjacency(const ldl_ctx* ctx, int32_t r, int64_t* row_ptr, in
 /* Community totals K^out, K^in and internal weight e, int64[n] each (host). */
 ldl_status ldl_get_communities(const ldl_ctx* ctx, int64_t* kout, int64_t* kin, int64_t* e);
 
-/* Device time in milliseconds spent in each stage kernel group during the
- * last batch: [ingest, repair, expand, bestmove, decouple, commit, refine,
- * aggregate, pushdown]; `times` has room for 16.  Enabled by ldl_set_timing. */
+/* Device time in milliseconds spent in each stage since timing was last
+ * enabled: [ingest, repair, expand, bestmove, decouple, commit, refine,
+ * aggregate, pushdown]; `times` has room for 16.  ldl_set_timing(ctx, 1)
+ * enables the events (one synchronisation per stage) and resets the sums. */
 ldl_status ldl_stage_times(const ldl_ctx* ctx, double* times);
 ldl_status ldl_set_timing(ldl_ctx* ctx, int32_t on);
+
+/* Copies the last batch's changed vertices (ids) and their new labels to host
+ * arrays of length n_changed (labels may be NULL). */
+ldl_status ldl_copy_changed(const ldl_ctx* ctx, int32_t* ids, int32_t* labels);
+
+/* Number of CUDA kernels this library has launched in this process. */
+int64_t ldl_launch_count(void);
+
+/*
+ * Per-kernel statistics of the BestMove / BestRef sweep kernels, measured
+ * with CUDA events on the context's stream while enabled (enabling resets
+ * them).  out[8] = {warp-bin launches, ms, algorithmic bytes, entries,
+ * block-bin launches, ms, algorithmic bytes, entries}.  Algorithmic bytes
+ * count, per adjacency entry, the neighbour id, its weight and its label
+ * (refinement: also its parent); per swept node its offsets, lengths, label
+ * and strengths; per evaluated (node, target) pair the target's totals.
+ */
+ldl_status ldl_set_kernel_stats(ldl_ctx* ctx, int32_t on);
+ldl_status ldl_get_kernel_stats(const ldl_ctx* ctx, double* out);
 
 /* Test hook: make the k-th device allocation from now on fail (k >= 1);
  * k = 0 disables.  Lets a test check that NOMEM leaves the state intact. */

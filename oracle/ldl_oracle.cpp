@@ -179,16 +179,101 @@ struct Orc {
     s.erase(std::unique(s.begin(), s.end()), s.end());
   }
 
-  // N_r(U) together with U (out- and in-neighbours).
-  std::vector<int32_t> expand(int r, const std::vector<int32_t>& U) {
-    std::vector<int32_t> S(U);
-    for (int32_t v : U) {
-      for (auto& p : lv[r].out[v]) S.push_back(p.first);
-      if (directed)
-        for (auto& p : lv[r].in[v]) S.push_back(p.first);
+  // Records (key, value) grouped by key with their values summed; zero sums
+  // are dropped.  Plain sort-then-merge.
+  typedef std::pair<std::pair<int32_t, int32_t>, i64> ERec;
+  typedef std::pair<int32_t, std::pair<i64, i64>> NRec;
+  static void group(std::vector<ERec>& v) {
+    std::sort(v.begin(), v.end(), [](const ERec& a, const ERec& b) { return a.first < b.first; });
+    size_t k = 0;
+    for (size_t i = 0; i < v.size();) {
+      size_t j = i;
+      i64 s = 0;
+      while (j < v.size() && v[j].first == v[i].first) s += v[j++].second;
+      if (s != 0) v[k++] = ERec(v[i].first, s);
+      i = j;
     }
-    uniq(S);
+    v.resize(k);
+  }
+  static void group(std::vector<NRec>& v) {
+    std::sort(v.begin(), v.end(), [](const NRec& a, const NRec& b) { return a.first < b.first; });
+    size_t k = 0;
+    for (size_t i = 0; i < v.size();) {
+      size_t j = i;
+      i64 a = 0, b = 0;
+      while (j < v.size() && v[j].first == v[i].first) { a += v[j].second.first; b += v[j].second.second; ++j; }
+      if (a != 0 || b != 0) v[k++] = NRec(v[i].first, std::make_pair(a, b));
+      i = j;
+    }
+    v.resize(k);
+  }
+
+  // Adds grouped records (sorted by (row, col), nonzero) to the rows: each
+  // touched row is merged with its records in one pass; entries that reach
+  // zero disappear.
+  static void merge_rows_with(std::vector<Row>& rows, const std::vector<ERec>& recs) {
+    Row merged;
+    for (size_t i = 0; i < recs.size();) {
+      const int32_t x = recs[i].first.first;
+      size_t j = i;
+      while (j < recs.size() && recs[j].first.first == x) ++j;
+      Row& row = rows[x];
+      merged.clear();
+      size_t a = 0, b = i;
+      while (a < row.size() || b < j) {
+        if (b == j || (a < row.size() && row[a].first < recs[b].first.second)) {
+          merged.push_back(row[a++]);
+        } else if (a == row.size() || recs[b].first.second < row[a].first) {
+          if (recs[b].second < 0) die("negative weight on insert");
+          merged.push_back(std::make_pair(recs[b].first.second, recs[b].second));
+          ++b;
+        } else {
+          const i64 v = row[a].second + recs[b].second;
+          if (v < 0) die("negative weight");
+          if (v != 0) merged.push_back(std::make_pair(row[a].first, v));
+          ++a;
+          ++b;
+        }
+      }
+      row.swap(merged);
+      i = j;
+    }
+  }
+
+  // Applies grouped arc records to level r (out-rows, and in-rows when directed).
+  void apply_arcs(int r, const std::vector<ERec>& recs) {
+    merge_rows_with(lv[r].out, recs);
+    if (directed) {
+      std::vector<ERec> t;
+      t.reserve(recs.size());
+      for (auto& x : recs) t.push_back(ERec({x.first.second, x.first.first}, x.second));
+      std::sort(t.begin(), t.end(), [](const ERec& a, const ERec& b) { return a.first < b.first; });
+      merge_rows_with(lv[r].in, t);
+    }
+  }
+
+  // N_r(U) together with U (out- and in-neighbours), without repeats.
+  std::vector<int32_t> expand(int r, const std::vector<int32_t>& U) {
+    std::vector<int32_t> S;
+    auto add = [&](int32_t x) {
+      if (!flag2[x]) { flag2[x] = 1; S.push_back(x); }
+    };
+    for (int32_t v : U) {
+      add(v);
+      for (auto& p : lv[r].out[v]) add(p.first);
+      if (directed)
+        for (auto& p : lv[r].in[v]) add(p.first);
+    }
+    for (int32_t x : S) flag2[x] = 0;
     return S;
+  }
+
+  // Union of two node sets given as vectors without repeats.
+  void unite(std::vector<int32_t>& A, const std::vector<int32_t>& B) {
+    for (int32_t x : A) flag2[x] = 1;
+    for (int32_t x : B)
+      if (!flag2[x]) { flag2[x] = 1; A.push_back(x); }
+    for (int32_t x : A) flag2[x] = 0;
   }
 
   // ---------------------------------------------------------------- BestMove
@@ -326,11 +411,10 @@ struct Orc {
       uniq(V);
       moved.insert(moved.end(), V.begin(), V.end());
       U = expand(r, V);
-      Ustar.insert(Ustar.end(), U.begin(), U.end());
+      unite(Ustar, U);
       if (dq * (i128)ainv < Q0) break;
       if ((i64)V.size() * binv < (i64)S.size()) break;
     }
-    uniq(Ustar);
     return Ustar;
   }
 
@@ -492,68 +576,62 @@ struct Orc {
     std::vector<int32_t> Dc;
     for (int32_t u : D)
       if (Lr.par[u] != par_old[u]) { changed[u] = 1; Dc.push_back(u); }
-    std::map<std::pair<int32_t, int32_t>, i64> rec;
-    std::map<int32_t, std::pair<i64, i64>> nd;
+    std::vector<ERec> rec;
+    std::vector<NRec> nd;
     for (int32_t u : Dc) {
       const int32_t po = par_old[u], pn = Lr.par[u];
       for (auto& p : Lr.out[u]) {
         int32_t v = p.first;
         int32_t pvo = changed[v] ? par_old[v] : Lr.par[v];
         int32_t pvn = Lr.par[v];
-        if (po != NONE && pvo != NONE) rec[{po, pvo}] -= p.second;
-        rec[{pn, pvn}] += p.second;
+        if (po != NONE && pvo != NONE) rec.push_back(ERec({po, pvo}, -p.second));
+        rec.push_back(ERec({pn, pvn}, p.second));
       }
       for (auto& p : inrow(r, u)) {
         int32_t v = p.first;
         if (changed[v]) continue;  // counted from v's out-row (or the self-loop)
-        if (po != NONE) rec[{Lr.par[v], po}] -= p.second;
-        rec[{Lr.par[v], pn}] += p.second;
+        if (po != NONE) rec.push_back(ERec({Lr.par[v], po}, -p.second));
+        rec.push_back(ERec({Lr.par[v], pn}, p.second));
       }
-      if (po != NONE) { nd[po].first -= Lr.kout[u]; nd[po].second -= Lr.kin[u]; }
-      nd[pn].first += Lr.kout[u];
-      nd[pn].second += Lr.kin[u];
+      if (po != NONE) nd.push_back(NRec(po, std::make_pair(-Lr.kout[u], -Lr.kin[u])));
+      nd.push_back(NRec(pn, std::make_pair(Lr.kout[u], Lr.kin[u])));
     }
+    group(rec);
+    group(nd);
     std::vector<int32_t> ends;
-    std::vector<std::pair<std::pair<int32_t, int32_t>, i64>> cur;
-    for (auto& kv : rec)
-      if (kv.second != 0) {
-        cur.push_back(kv);
-        ends.push_back(kv.first.first);
-        ends.push_back(kv.first.second);
-      }
+    std::vector<ERec> cur(rec);
+    for (auto& kv : cur) {
+      ends.push_back(kv.first.first);
+      ends.push_back(kv.first.second);
+    }
     ctr.agg_records += (i64)cur.size();
-    std::vector<std::pair<int32_t, std::pair<i64, i64>>> curk;
-    for (auto& kv : nd)
-      if (kv.second.first != 0 || kv.second.second != 0) {
-        curk.push_back(kv);
-        ends.push_back(kv.first);
-      }
+    std::vector<NRec> curk(nd);
+    for (auto& kv : curk) ends.push_back(kv.first);
     // level r+1: weights change here; strengths already follow live
-    for (auto& x : cur) add_arc(r + 1, x.first.first, x.first.second, x.second);
+    apply_arcs(r + 1, cur);
     // levels r+2..T: propagate through the current parent maps
     for (int q = r + 1; q < T; ++q) {
-      std::map<std::pair<int32_t, int32_t>, i64> up;
-      std::map<int32_t, std::pair<i64, i64>> upk;
+      std::vector<ERec> up;
+      std::vector<NRec> upk;
       for (auto& x : cur) {
         int32_t a = lv[q].par[x.first.first], b = lv[q].par[x.first.second];
         if (a == NONE || b == NONE) continue;
-        up[{a, b}] += x.second;
+        up.push_back(ERec({a, b}, x.second));
       }
       for (auto& x : curk) {
         int32_t a = lv[q].par[x.first];
         if (a == NONE) continue;
-        upk[a].first += x.second.first;
-        upk[a].second += x.second.second;
+        upk.push_back(NRec(a, x.second));
       }
-      cur.clear();
-      curk.clear();
-      for (auto& kv : up)
-        if (kv.second != 0) { cur.push_back(kv); add_arc(q + 1, kv.first.first, kv.first.second, kv.second); }
+      group(up);
+      group(upk);
+      apply_arcs(q + 1, up);
       for (auto& kv : upk) {
         lv[q + 1].kout[kv.first] += kv.second.first;
         lv[q + 1].kin[kv.first] += kv.second.second;
-        if (kv.second.first != 0 || kv.second.second != 0) curk.push_back(kv);
       }
+      cur.swap(up);
+      curk.swap(upk);
     }
     // existence: new nodes appear, emptied nodes leave their parents
     for (int q = r + 1; q <= T; ++q) {
@@ -617,15 +695,35 @@ struct Orc {
     lv.assign(1, Level());
     alloc_level(lv[0]);
     Level& L0 = lv[0];
-    i64 msum = 0;
+    // rows collected, then sorted with repeated entries summed
     for (i64 v = 0; v < n; ++v)
       for (i64 k = rp[v]; k < rp[v + 1]; ++k) {
-        i64 cur = row_get(L0.out[v], col[k]);
-        if (cur + w[k] > INT32_MAX) return ST_OVERFLOW;
-        add_arc(0, (int32_t)v, col[k], w[k]);
-        msum += w[k];
-        if (msum >= ((i64)1 << 50)) return ST_OVERFLOW;
+        L0.out[v].push_back(std::make_pair(col[k], (i64)w[k]));
+        if (directed) L0.in[col[k]].push_back(std::make_pair((int32_t)v, (i64)w[k]));
       }
+    auto merge_rows = [](std::vector<Row>& rows) {
+      for (Row& row : rows) {
+        std::sort(row.begin(), row.end());
+        size_t k = 0;
+        for (size_t i = 0; i < row.size();) {
+          size_t j = i;
+          i64 s = 0;
+          while (j < row.size() && row[j].first == row[i].first) s += row[j++].second;
+          row[k++] = std::make_pair(row[i].first, s);
+          i = j;
+        }
+        row.resize(k);
+      }
+    };
+    merge_rows(L0.out);
+    if (directed) merge_rows(L0.in);
+    i64 msum = 0;
+    for (i64 v = 0; v < n; ++v)
+      for (auto& p : L0.out[v]) {
+        if (p.second > INT32_MAX) return ST_OVERFLOW;
+        msum += p.second;
+      }
+    if (msum >= ((i64)1 << 50)) return ST_OVERFLOW;
     if (!directed)
       for (i64 v = 0; v < n; ++v)
         for (auto& p : L0.out[v])
@@ -722,20 +820,22 @@ struct Orc {
     for (auto& d : deltas) mnew += (directed || d.first.first == d.first.second) ? d.second : 2 * d.second;
     if (mnew >= ((i64)1 << 50)) return ST_OVERFLOW;
     // Algorithm 1 line 1: apply the batch to level 0, S_t = changed endpoints
-    std::vector<std::pair<std::pair<int32_t, int32_t>, i64>> arcs;
+    std::vector<ERec> arcs;
     for (auto& d : deltas) {
       arcs.push_back(d);
       if (!directed && d.first.first != d.first.second)
         arcs.push_back(std::make_pair(std::make_pair(d.first.second, d.first.first), d.second));
     }
     std::vector<int32_t> St;
+    std::sort(arcs.begin(), arcs.end(), [](const ERec& a, const ERec& b) { return a.first < b.first; });
+    apply_arcs(0, arcs);
     for (auto& a : arcs) {
-      add_arc(0, a.first.first, a.first.second, a.second);
       St.push_back(a.first.first);
       St.push_back(a.first.second);
     }
     uniq(St);
     // line 2: repair m, degrees, community totals and the aggregate chain
+    std::vector<ERec> chain(arcs);
     for (auto& a : arcs) {
       const int32_t i = a.first.first, j = a.first.second;
       const i64 d = a.second;
@@ -746,15 +846,20 @@ struct Orc {
       Kout[ci] += d;
       Kin[cj] += d;
       if (ci == cj) e[ci] += d;
-      int32_t x = i, y = j;
-      for (int r = 1; r <= T; ++r) {
-        x = lv[r - 1].par[x];
-        y = lv[r - 1].par[y];
+    }
+    // W_r(anc(i), anc(j)) += delta and the strengths, level by level
+    for (int r = 1; r <= T; ++r) {
+      std::vector<ERec> up;
+      for (auto& a : chain) {
+        const int32_t x = lv[r - 1].par[a.first.first], y = lv[r - 1].par[a.first.second];
         if (x == NONE || y == NONE) die("batch endpoint without ancestor");
-        add_arc(r, x, y, d);
-        lv[r].kout[x] += d;
-        lv[r].kin[y] += d;
+        up.push_back(ERec({x, y}, a.second));
+        lv[r].kout[x] += a.second;
+        lv[r].kin[y] += a.second;
       }
+      group(up);
+      apply_arcs(r, up);
+      chain.swap(up);
     }
     Q = q_from_stats();
     Qrep = Q;

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <string>
 
 #include "../../include/ldl.h"
@@ -24,7 +25,8 @@ struct LdlError {
 void ldl_throw(ldl_status st, const std::string& msg);
 void ldl_cuda_check(cudaError_t e, const char* what, const char* file, int line);
 #define CK(x) ldl_cuda_check((x), #x, __FILE__, __LINE__)
-#define CKL(name) ldl_cuda_check(cudaGetLastError(), name, __FILE__, __LINE__)
+extern std::atomic<int64_t> g_launches;  // kernels launched by this library
+#define CKL(name) (g_launches.fetch_add(1, std::memory_order_relaxed), ldl_cuda_check(cudaGetLastError(), name, __FILE__, __LINE__))
 
 // ---------------------------------------------------------------- device memory
 // All device allocations of a context go through dalloc/dfree so that a test
@@ -203,6 +205,9 @@ struct DevScalars {
   int64_t scanned;  // adjacency entries scanned
   int64_t err_key;  // packed (index << 8 | status) of the first failing update
   int64_t pool_top;
+  int64_t sw_entries[2];  // sweep kernels (0: warp bin, 1: block bins): adjacency entries read
+  int64_t sw_pairs[2];    // distinct (node, target) pairs evaluated
+  int64_t sw_nodes[2];    // nodes swept
   int32_t cnt[16];  // list counters
   int32_t undecided;
   int32_t pad;

@@ -91,6 +91,10 @@ struct ldl_ctx {
   int timing = 0;
   double stage_ms[16] = {0};
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // per-kernel statistics of the sweep kernels (enabled by ldl_set_kernel_stats)
+  int kstats = 0;
+  cudaEvent_t kev[4] = {nullptr, nullptr, nullptr, nullptr};
+  double ks_launch[2] = {0, 0}, ks_ms[2] = {0, 0}, ks_bytes[2] = {0, 0}, ks_entries[2] = {0, 0};
   std::string err;
 
   int32_t next_epoch() { return ++epoch; }

@@ -575,9 +575,18 @@ __global__ void k_changed_final(const int32_t* lCh, const int32_t* nCh, const in
   }
 }
 
+__global__ void k_gather(const int32_t* ids, int32_t k, const int32_t* lab, int32_t* out) {
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < k; i += gridDim.x * blockDim.x) out[i] = lab[ids[i]];
+}
+
 }  // namespace
 
 // ================================================================== host side
+void gather_labels(ldl_ctx& c, const int32_t* ids, int32_t k, int32_t* out) {
+  if (k <= 0) return;
+  k_gather<<<grid_for(k, TPB), TPB, 0, c.s>>>(ids, k, c.lv[0].lab.p, out);
+  CKL("k_gather");
+}
 static void throw_err(ldl_ctx& c, unsigned long long* d_err, const char* what) {
   unsigned long long e = 0;
   CK(cudaMemcpyAsync(&e, d_err, sizeof(e), cudaMemcpyDeviceToHost, c.s));

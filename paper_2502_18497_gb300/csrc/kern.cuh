@@ -40,3 +40,4 @@ void level_free(ldl_ctx& c, int r);
 int32_t alive_list(ldl_ctx& c, int r, int32_t* list, int idx);
 void reset_par(ldl_ctx& c, int r, int32_t nD);
 int32_t changed_labels(ldl_ctx& c, int32_t epCh);
+void gather_labels(ldl_ctx& c, const int32_t* ids, int32_t k, int32_t* out);

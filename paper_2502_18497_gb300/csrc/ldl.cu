@@ -24,6 +24,7 @@ void ldl_cuda_check(cudaError_t e, const char* what, const char* file, int line)
 }
 
 static std::atomic<int64_t> g_fail_after{0};
+std::atomic<int64_t> g_launches{0};
 
 void* dalloc(size_t bytes) {
   int64_t k = g_fail_after.load();
@@ -137,6 +138,10 @@ static void free_all(ldl_ctx& c) {
   if (c.ev0) cudaEventDestroy(c.ev0);
   if (c.ev1) cudaEventDestroy(c.ev1);
   c.ev0 = c.ev1 = nullptr;
+  for (auto& ev : c.kev) {
+    if (ev) cudaEventDestroy(ev);
+    ev = nullptr;
+  }
 }
 
 // ---------------------------------------------------------------- move loop
@@ -260,7 +265,7 @@ static void static_build(ldl_ctx& c) {
 // ---------------------------------------------------------------- batch update
 static void apply_batch(ldl_ctx& c, const ldl_update* upd, int64_t count, int on_device) {
   memset(&c.res, 0, sizeof(c.res));
-  for (double& x : c.stage_ms) x = 0;
+  CK(cudaMemsetAsync(&c.d_sc->scanned, 0, sizeof(int64_t), c.s));
   const int T = c.T;
   int64_t dm = 0;
   stage_begin(c);
@@ -328,6 +333,8 @@ static void apply_batch(ldl_ctx& c, const ldl_update* upd, int64_t count, int on
     if ((qnum(c) - Qpass) * (i128)ainv < Qpass) break;
   }
   c.res.n_changed = changed_labels(c, epCh);
+  CK(cudaMemcpyAsync(&c.res.edges_scanned, &c.d_sc->scanned, sizeof(int64_t), cudaMemcpyDeviceToHost, c.s));
+  CK(cudaStreamSynchronize(c.s));
 }
 
 template <class WT>
@@ -393,6 +400,7 @@ ldl_status ldl_create(const ldl_params* params, int64_t n, int64_t nnz, const in
     c->s = (cudaStream_t)p.cuda_stream;
     CK(cudaEventCreate(&c->ev0));
     CK(cudaEventCreate(&c->ev1));
+    for (auto& ev : c->kev) CK(cudaEventCreate(&ev));
     c->lv.resize(p.L + 1);
     alloc_globals(*c);
     level_alloc(*c, 0);
@@ -571,9 +579,51 @@ ldl_status ldl_stage_times(const ldl_ctx* c, double* times) {
 ldl_status ldl_set_timing(ldl_ctx* c, int32_t on) {
   if (!c) return LDL_E_INVALID;
   c->timing = on ? 1 : 0;
+  for (double& x : c->stage_ms) x = 0;
   return LDL_OK;
 }
 
 void ldl_debug_fail_alloc_after(int64_t k) { g_fail_after.store(k > 0 ? k : 0); }
+
+int64_t ldl_launch_count(void) { return g_launches.load(); }
+
+ldl_status ldl_copy_changed(const ldl_ctx* cc, int32_t* ids, int32_t* labels) {
+  if (!cc) return LDL_E_INVALID;
+  ldl_ctx& c = const_cast<ldl_ctx&>(*cc);
+  const int64_t k = c.res.n_changed;
+  if (k == 0) return LDL_OK;
+  if (!ids) return LDL_E_INVALID;
+  try {
+    CK(cudaMemcpyAsync(ids, c.lChg.p, sizeof(int32_t) * (size_t)k, cudaMemcpyDeviceToHost, c.s));
+    CK(cudaStreamSynchronize(c.s));
+    if (labels) {
+      gather_labels(c, c.lChg.p, (int32_t)k, c.lTmp.p);
+      CK(cudaMemcpyAsync(labels, c.lTmp.p, sizeof(int32_t) * (size_t)k, cudaMemcpyDeviceToHost, c.s));
+      CK(cudaStreamSynchronize(c.s));
+    }
+  } catch (const LdlError& e) {
+    c.err = e.msg;
+    return e.st;
+  }
+  return LDL_OK;
+}
+
+ldl_status ldl_set_kernel_stats(ldl_ctx* c, int32_t on) {
+  if (!c) return LDL_E_INVALID;
+  c->kstats = on ? 1 : 0;
+  for (int k = 0; k < 2; ++k) c->ks_launch[k] = c->ks_ms[k] = c->ks_bytes[k] = c->ks_entries[k] = 0;
+  return LDL_OK;
+}
+
+ldl_status ldl_get_kernel_stats(const ldl_ctx* c, double* out) {
+  if (!c || !out) return LDL_E_INVALID;
+  for (int k = 0; k < 2; ++k) {
+    out[4 * k + 0] = c->ks_launch[k];
+    out[4 * k + 1] = c->ks_ms[k];
+    out[4 * k + 2] = c->ks_bytes[k];
+    out[4 * k + 3] = c->ks_entries[k];
+  }
+  return LDL_OK;
+}
 
 }  // extern "C"

@@ -75,6 +75,7 @@ struct SweepArgs {
   uint64_t* cglo;
   int32_t* ncand;
   int64_t* scanned;
+  DevScalars* stats;
 };
 
 __device__ inline void hash_add(int32_t* K, int64_t* V, uint32_t mask, int32_t key, int64_t w) {
@@ -151,7 +152,7 @@ __global__ void __launch_bounds__(TPB) k_sweep_warp(SweepArgs<WT> A, const int32
   int64_t* V = hv[wid];
   const int32_t nl = *nlist;
   const int64_t mult = A.directed ? 1 : 2;
-  int64_t scanned = 0;
+  int64_t scanned = 0, pairs = 0, nodes = 0;
   for (int64_t t = warp; t < nl; t += nw) {
     const int32_t v = list[t];
     for (int k = lane; k < HW; k += 32) {
@@ -167,10 +168,12 @@ __global__ void __launch_bounds__(TPB) k_sweep_warp(SweepArgs<WT> A, const int32
     const int64_t wa = MODE == 0 ? hash_get(K, V, HW - 1, a) : 0;
     const int64_t ko = A.kout[v], ki = A.kin[v];
     Best b{0, 0, 0};
+    if (lane == 0) ++nodes;
     for (int k = lane; k < HW; k += 32) {
       const int32_t key = K[k];
       if (key < 0) continue;
       if (MODE == 0 ? key == a : key == v) continue;
+      ++pairs;
       const i128 g = gain_of<MODE>(key, V[k], wa, a, ko, ki, A.Tout, A.Tin, A.m, A.gn, A.gd, mult);
       if (g > 0) {
         Best c{g, key, 1};
@@ -181,7 +184,15 @@ __global__ void __launch_bounds__(TPB) k_sweep_warp(SweepArgs<WT> A, const int32
     if (lane == 0 && b.have) emit_cand(A, v, MODE == 0 ? a : v, b);
     __syncwarp();
   }
-  if (lane == 0 && scanned) atomic_add_i64(A.scanned, scanned);
+  pairs = warp_sum_i64(pairs);
+  if (lane == 0) {
+    if (scanned) {
+      atomic_add_i64(A.scanned, scanned);
+      atomic_add_i64(&A.stats->sw_entries[0], scanned);
+    }
+    if (pairs) atomic_add_i64(&A.stats->sw_pairs[0], pairs);
+    if (nodes) atomic_add_i64(&A.stats->sw_nodes[0], nodes);
+  }
 }
 
 // one block per node; the hash lives in dynamic shared memory (mid degrees)
@@ -221,10 +232,12 @@ __global__ void __launch_bounds__(TPB) k_sweep_block(SweepArgs<WT> A, const int3
     const int64_t wa = MODE == 0 ? hash_get(K, V, H - 1, a) : 0;
     const int64_t ko = A.kout[v], ki = A.kin[v];
     Best b{0, 0, 0};
+    int64_t pairs = 0;
     for (uint32_t k = threadIdx.x; k < H; k += TPB) {
       const int32_t key = K[k];
       if (key < 0) continue;
       if (MODE == 0 ? key == a : key == v) continue;
+      ++pairs;
       const i128 g = gain_of<MODE>(key, V[k], wa, a, ko, ki, A.Tout, A.Tin, A.m, A.gn, A.gd, mult);
       if (g > 0) {
         Best c{g, key, 1};
@@ -232,14 +245,21 @@ __global__ void __launch_bounds__(TPB) k_sweep_block(SweepArgs<WT> A, const int3
       }
     }
     b = warp_best(b);
-    if (lane == 0) wb[wid] = b;
+    pairs = warp_sum_i64(pairs);
+    if (lane == 0) {
+      wb[wid] = b;
+      if (pairs) atomic_add_i64(&A.stats->sw_pairs[1], pairs);
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
       Best r = wb[0];
       for (int w = 1; w < TPB / 32; ++w)
         if (best_better(wb[w], r)) r = wb[w];
       if (r.have) emit_cand(A, v, MODE == 0 ? a : v, r);
-      atomic_add_i64(A.scanned, (int64_t)A.out.len[v] + (A.directed ? A.in.len[v] : 0));
+      const int64_t ent = (int64_t)A.out.len[v] + (A.directed ? A.in.len[v] : 0);
+      atomic_add_i64(A.scanned, ent);
+      atomic_add_i64(&A.stats->sw_entries[1], ent);
+      atomic_add_i64(&A.stats->sw_nodes[1], 1);
     }
     __syncthreads();
   }
@@ -574,6 +594,10 @@ static int32_t sweep_t(ldl_ctx& c, int r, Adj<WT> out, Adj<WT> in, const int32_t
   A.cglo = c.cglo.p;
   A.ncand = c.dcnt + K_CAND;
   A.scanned = &c.d_sc->scanned;
+  A.stats = c.d_sc;
+  if (c.kstats) {
+    CK(cudaMemsetAsync(c.d_sc->sw_entries, 0, sizeof(int64_t) * 6, c.s));
+  }
   zero_cnt(c, K_CAND);
   zero_cnt(c, K_SMALL);
   zero_cnt(c, K_MID);
@@ -588,10 +612,12 @@ static int32_t sweep_t(ldl_ctx& c, int r, Adj<WT> out, Adj<WT> in, const int32_t
   CK(cudaMemcpyAsync(counts, c.dcnt + K_SMALL, sizeof(int32_t) * 3, cudaMemcpyDeviceToHost, c.s));
   CK(cudaMemcpyAsync(&tab, &c.d_sc->need, sizeof(int64_t), cudaMemcpyDeviceToHost, c.s));
   CK(cudaStreamSynchronize(c.s));
+  if (c.kstats) CK(cudaEventRecord(c.kev[0], c.s));
   if (counts[0] > 0) {
     k_sweep_warp<WT, MODE><<<grid_for((int64_t)counts[0] * 32, TPB), TPB, 0, c.s>>>(A, c.binS.p, c.dcnt + K_SMALL);
     CKL("k_sweep_warp");
   }
+  if (c.kstats) CK(cudaEventRecord(c.kev[1], c.s));
   if (counts[1] > 0) {
     const size_t sm = (sizeof(int64_t) + sizeof(int32_t)) * HB;
     CK(cudaFuncSetAttribute(k_sweep_block<WT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
@@ -605,6 +631,32 @@ static int32_t sweep_t(ldl_ctx& c, int r, Adj<WT> out, Adj<WT> in, const int32_t
     k_sweep_block<WT, MODE><<<grid_for(counts[2], 1, 152 * 4), TPB, 0, c.s>>>(
         A, c.binL.p, c.dcnt + K_LARGE, c.binLoff.p, c.binLsz.p, c.gkeys.p, c.gvals.p);
     CKL("k_sweep_block(hub)");
+  }
+  if (c.kstats) {
+    CK(cudaEventRecord(c.kev[2], c.s));
+    CK(cudaEventSynchronize(c.kev[2]));
+    float ms0 = 0, ms1 = 0;
+    CK(cudaEventElapsedTime(&ms0, c.kev[0], c.kev[1]));
+    CK(cudaEventElapsedTime(&ms1, c.kev[1], c.kev[2]));
+    DevScalars h;
+    CK(cudaMemcpy(&h, c.d_sc, sizeof(DevScalars), cudaMemcpyDeviceToHost));
+    // algorithmic bytes: per entry the neighbour id, its weight and its
+    // label (refine: also its parent); per node offsets, lengths, label and
+    // strengths; per evaluated pair the target's two totals; per candidate
+    // the 28-byte tuple
+    const double per_entry = 4.0 + sizeof(WT) + 4.0 + (MODE == 1 ? 4.0 : 0.0);
+    const double per_node = (8.0 + 4.0) * (c.directed ? 2 : 1) + 4.0 + 16.0 + 4.0;
+    const double per_pair = c.directed ? 16.0 : 8.0;
+    const int kinds[2] = {counts[0] > 0, counts[1] + counts[2] > 0};
+    const double ms[2] = {ms0, ms1};
+    for (int k = 0; k < 2; ++k) {
+      if (!kinds[k]) continue;
+      c.ks_launch[k] += (k == 0) ? 1 : (counts[1] > 0) + (counts[2] > 0);
+      c.ks_ms[k] += ms[k];
+      c.ks_entries[k] += (double)h.sw_entries[k];
+      c.ks_bytes[k] += per_entry * (double)h.sw_entries[k] + per_node * (double)h.sw_nodes[k] +
+                       per_pair * (double)h.sw_pairs[k];
+    }
   }
   return rd_cnt(c, K_CAND);
 }

@@ -75,6 +75,10 @@ def load(path: Optional[str] = None):
         "ldl_stage_times": (I32, [P, P]),
         "ldl_set_timing": (I32, [P, I32]),
         "ldl_debug_fail_alloc_after": (None, [I64]),
+        "ldl_copy_changed": (I32, [P, P, P]),
+        "ldl_launch_count": (I64, []),
+        "ldl_set_kernel_stats": (I32, [P, I32]),
+        "ldl_get_kernel_stats": (I32, [P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -89,7 +93,12 @@ def exported_symbols():
     return ["ldl_default_params", "ldl_create", "ldl_apply_batch", "ldl_modularity",
             "ldl_modularity_num", "ldl_destroy", "ldl_last_error", "ldl_levels", "ldl_get_level",
             "ldl_level_nnz", "ldl_get_adjacency", "ldl_get_communities", "ldl_stage_times",
-            "ldl_set_timing", "ldl_debug_fail_alloc_after"]
+            "ldl_set_timing", "ldl_debug_fail_alloc_after", "ldl_copy_changed", "ldl_launch_count",
+            "ldl_set_kernel_stats", "ldl_get_kernel_stats"]
+
+
+def launch_count() -> int:
+    return int(load().ldl_launch_count())
 
 
 def _ptr(a):
@@ -156,9 +165,12 @@ class LDL:
     def apply(self, batch, on_device: bool = False) -> ldl_result:
         """Apply one batch: an int32 array of shape (count, 4) = (src, dst, op, w),
         host (numpy) or device (torch CUDA tensor with on_device=True)."""
-        if on_device:
+        if hasattr(batch, "data_ptr"):  # a torch tensor, host (pinned) or device
             cnt = int(batch.shape[0])
             ptr = _ptr(batch)
+            on_device = bool(batch.is_cuda)
+        elif on_device:
+            raise ValueError("on_device needs a CUDA tensor")
         else:
             batch = np.ascontiguousarray(batch, dtype=np.int32).reshape(-1, 4)
             cnt = batch.shape[0]
@@ -219,6 +231,25 @@ class LDL:
         t = np.zeros(16, np.float64)
         self._check(load().ldl_stage_times(self._h, _ptr(t)))
         return dict(zip(STAGES, t.tolist()))
+
+    def changed(self):
+        """(ids, labels) of the vertices whose label changed in the last batch."""
+        k = int(self.last.n_changed)
+        ids = np.zeros(k, np.int32)
+        lab = np.zeros(k, np.int32)
+        self._check(load().ldl_copy_changed(self._h, _ptr(ids), _ptr(lab)))
+        return ids, lab
+
+    def set_kernel_stats(self, on: bool = True):
+        self._check(load().ldl_set_kernel_stats(self._h, int(on)))
+
+    def kernel_stats(self) -> dict:
+        t = np.zeros(8, np.float64)
+        self._check(load().ldl_get_kernel_stats(self._h, _ptr(t)))
+        out = {}
+        for k, name in enumerate(("sweep_warp", "sweep_block")):
+            out[name] = dict(launches=t[4 * k], ms=t[4 * k + 1], bytes=t[4 * k + 2], entries=t[4 * k + 3])
+        return out
 
     def result_dict(self) -> dict:
         r = self.last

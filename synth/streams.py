@@ -145,16 +145,25 @@ def planted_partition(n: int = 10000, block: int = 100, intra: int = 5, inter: i
 
 
 def _rmat_draw(seed: int, purpose: int, base: int, count: int, scale: int, probs):
+    """R-MAT endpoints: each recursion level picks a quadrant with
+    probabilities (a, b, c, d) quantised to 1/65536; one 64-bit draw serves
+    four levels (16 bits each)."""
     a, b, c, _ = probs
+    ta, tb, tc = (np.int64(round(x * 65536)) for x in (a, a + b, a + b + c))
+    per = (scale + 3) // 4
     idx0 = np.arange(base, base + count, dtype=np.int64)
     src = np.zeros(count, dtype=np.int64)
     dst = np.zeros(count, dtype=np.int64)
-    for lvl in range(scale):
-        u = unit_f64(seed, purpose, idx0 * scale + lvl)
-        sb = (u >= a + b).astype(np.int64)
-        db = (((u >= a) & (u < a + b)) | (u >= a + b + c)).astype(np.int64)
-        src = (src << 1) | sb
-        dst = (dst << 1) | db
+    for k in range(per):
+        x = splitmix64(seed, purpose, idx0 * per + k)
+        for j in range(4):
+            if 4 * k + j >= scale:
+                break
+            u = ((x >> np.uint64(16 * j)) & np.uint64(0xFFFF)).astype(np.int64)
+            sb = (u >= tb).astype(np.int64)
+            db = (((u >= ta) & (u < tb)) | (u >= tc)).astype(np.int64)
+            src = (src << 1) | sb
+            dst = (dst << 1) | db
     return src, dst
 
 
@@ -188,6 +197,38 @@ def rmat_directed(scale: int = 20, arcs: int = 1 << 24, probs=(0.57, 0.19, 0.19,
     g = csr_from_arcs(n, key // n, key % n, w, directed=True)
     g.name = f"rmat directed scale={scale} arcs={arcs}"
     return g
+
+
+def cached(name: str, make):
+    """Memoise a generated workload on disk (LDL_SYNTH_CACHE, default a
+    per-user temp directory) so that tests and the benchmark draw it once per
+    machine.  The cache only stores what `make` returns (graph and batches)."""
+    import os
+    import pickle
+    import tempfile
+    root = os.environ.get("LDL_SYNTH_CACHE", os.path.join(tempfile.gettempdir(), "ldl_synth_cache"))
+    os.makedirs(root, exist_ok=True)
+    path = os.path.join(root, name + ".pkl")
+    if os.path.exists(path):
+        with open(path, "rb") as f:
+            return pickle.load(f)
+    obj = make()
+    tmp = path + f".{os.getpid()}"
+    with open(tmp, "wb") as f:
+        pickle.dump(obj, f, protocol=4)
+    os.replace(tmp, path)
+    return obj
+
+
+def rmat_workload(nbatches: int, scale: int = 20, arcs: int = 1 << 24, batch: int = 10_000, seed: int = 2,
+                  wmax: int = 16):
+    """The directed R-MAT stream workload (graph and its first `nbatches`
+    batches), cached on disk by recipe."""
+    g = cached(f"rmat_graph_s{scale}_a{arcs}_w{wmax}_seed{seed}",
+               lambda: rmat_directed(scale=scale, arcs=arcs, wmax=wmax, seed=seed))
+    bs = cached(f"rmat_stream_s{scale}_a{arcs}_w{wmax}_seed{seed}_b{batch}_n{nbatches}",
+                lambda: rmat_stream(g, batches=nbatches, size=batch, seed=seed, wmax=wmax))
+    return g, bs
 
 
 def random_small_graph(n: int, p: float, directed: bool, wmax: int = 5, seed: int = 0,
@@ -277,9 +318,16 @@ class EdgeStream:
         # deletes and reweights of distinct existing edges
         m = len(self.keys)
         n_old = min(n_del + n_rew, m)
-        pri = splitmix64(seed, 42 + t * 7, np.arange(m))
-        pick = np.argpartition(pri, n_old - 1)[:n_old] if n_old and n_old < m else np.arange(n_old)
-        pick = pick[np.argsort(pri[pick], kind="stable")]
+        pick = np.zeros(0, dtype=np.int64)
+        if n_old:
+            want = 2 * n_old + 64
+            if want < m // 4:
+                draw = uniform_u64(seed, 42 + t * 7, np.arange(want), m)
+                _, first = np.unique(draw, return_index=True)
+                pick = draw[np.sort(first)][:n_old]
+            if len(pick) < n_old:
+                pri = splitmix64(seed, 46 + t * 7, np.arange(m))
+                pick = np.argsort(pri, kind="stable")[:n_old]
         dels = pick[:min(n_del, n_old)]
         rews = pick[min(n_del, n_old):]
         rew_w = uniform_u64(seed, 43, np.arange(len(rews)) + t * 1_000_003, wmax) + 1
@@ -300,15 +348,17 @@ class EdgeStream:
         w = np.concatenate([ins_w, np.zeros(len(ds), dtype=np.int64), rew_w])
         order = np.argsort(splitmix64(seed, 45 + t * 7, np.arange(len(src))), kind="stable")
         batch = np.stack([src[order], dst[order], op[order], w[order]], axis=1).astype(np.int32)
-        # apply to the edge set
-        keep = np.ones(m, dtype=bool)
-        keep[dels] = False
+        # apply to the edge set (keys stay sorted)
         wts = self.wts.copy()
         wts[rews] = rew_w
-        keys = np.concatenate([self.keys[keep], np.array(ins_k, dtype=np.int64)])
-        wts = np.concatenate([wts[keep], ins_w])
-        order = np.argsort(keys, kind="stable")
-        self.keys, self.wts = keys[order], wts[order]
+        keep = np.ones(m, dtype=bool)
+        keep[dels] = False
+        keys, wts = self.keys[keep], wts[keep]
+        ik = np.array(ins_k, dtype=np.int64)
+        order = np.argsort(ik, kind="stable")
+        ik, iw = ik[order], ins_w[order]
+        at = np.searchsorted(keys, ik)
+        self.keys, self.wts = np.insert(keys, at, ik), np.insert(wts, at, iw)
         self.batches_made += 1
         return batch
 

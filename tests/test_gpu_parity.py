@@ -93,6 +93,20 @@ def test_rmat_directed_reduced(ldl):
         _assert_same(o, d, f"batch {t}", adjacency=(t % 5 == 4))
 
 
+def test_rmat_directed_full_size(ldl):
+    """The benchmark workload at full size (directed R-MAT, 2^20 vertices,
+    2^24 arcs): the static build and the first two batches of 10^4 updates,
+    compared bit for bit including every level's adjacency."""
+    from synth import rmat_workload
+    g, bs = rmat_workload(2)
+    o, d = _pair(ldl, g)
+    _assert_same(o, d, "create")
+    for t, b in enumerate(bs):
+        assert o.apply(b) == 0
+        d.apply(b)
+        _assert_same(o, d, f"batch {t}")
+
+
 @pytest.mark.parametrize("bad,status", [
     ([[0, 10_000, 0, 1]], 2), ([[0, 1, 7, 1]], 1), ([[0, 1, 0, 0]], 1), ([[0, 1, 2, -3]], 4),
     ([[2, 999, 1, 0]], 3), ([[5, 6, 0, 2**31 - 1], [5, 6, 0, 2**31 - 1]], 8),
