@@ -210,6 +210,7 @@ def main():
     clocks = ClockSampler(local)
     launches0 = binding.launch_count()
     scanned = 0
+    work = {}
     lat = []
     if ws > 1:
         torch.distributed.barrier()
@@ -222,6 +223,9 @@ def main():
         r = d.apply(b, on_device=True)
         lat.append(time.perf_counter() - t)
         scanned += r.edges_scanned
+        for k2, v2 in d.result_dict().items():
+            if isinstance(v2, int):
+                work[k2] = work.get(k2, 0) + v2
     e1.record()
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_pop()
@@ -288,6 +292,7 @@ def main():
             "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk}
     if stage:
         line["stage_ms_per_step"] = {k2: v / K for k2, v in stage.items()}
+        line["work_per_step"] = {k2: v / K for k2, v in work.items()}
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(g, batches[:3], args.cpu_budget)
     print(json.dumps(line), flush=True)

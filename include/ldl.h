@@ -100,6 +100,7 @@ typedef struct {
   int64_t frontier_nodes[8]; /* |A^r| summed over passes, per level */
   int64_t edges_scanned;     /* adjacency entries read by BestMove / BestRef */
   int64_t moves, refine_moves, rejected, rollbacks, rounds, agg_records;
+  int64_t decouple_rounds;   /* parallel resolution rounds of the decoupling filter */
 } ldl_result;
 
 /*

@@ -1,217 +1,231 @@
 // Device-resident CSR with per-row slack (Sec. III-A keeps adjacency at
-// every level; edge inserts go into the row's slack, deletes compact the row,
-// a row out of slack moves to the end of the pool).
+// every level; inserts go into the row's slack, deletes shrink the row, a row
+// out of slack moves to the end of the pool).
 //
-// Records are (key, delta) pairs with key = row << bshift | col, sorted by
-// key and unique.  One warp owns one row segment, so updates need no atomics
-// on the row itself; physical entry order inside a row never affects results
-// because every consumer reduces integers.
+// Every row is kept sorted by neighbour id.  Records are (key, delta) pairs
+// with key = row << bshift | col, sorted by key and unique.  Matching a record
+// is a binary search in its row (one thread per record); a row that gains or
+// loses entries is rebuilt by a flattened scatter in which every kept entry
+// and every inserted entry computes its own destination, so hub rows spread
+// over the whole GPU instead of one warp.
 #include "csr.cuh"
 #include "prims.cuh"
 
 namespace {
 
-__device__ inline int64_t seg_end(const u64* keys, int64_t s, int64_t nrec, int bshift) {
-  // first index > s whose row differs from row(s)
-  const u64 row = keys[s] >> bshift;
-  const u64 bound = (row + 1) << bshift;
-  int64_t lo = s + 1, hi = nrec;
+#define GRID_STRIDE(i, n) \
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)
+
+constexpr int TPB = 256;
+
+// binary search of col in a sorted row: returns the lower bound index
+__device__ inline int32_t row_lower_bound(const int32_t* col, int64_t off, int32_t len, int32_t c) {
+  int32_t lo = 0, hi = len;
   while (lo < hi) {
-    int64_t mid = (lo + hi) >> 1;
-    if (keys[mid] < bound) lo = mid + 1; else hi = mid;
+    const int32_t mid = (lo + hi) >> 1;
+    if (col[off + mid] < c) lo = mid + 1; else hi = mid;
   }
   return lo;
 }
 
-__global__ void k_seg_heads(const u64* keys, int64_t nrec, int bshift, int64_t* seg, int32_t* nseg) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nrec; i += (int64_t)gridDim.x * blockDim.x) {
-    if (i == 0 || (keys[i] >> bshift) != (keys[i - 1] >> bshift)) seg[atomicAdd(nseg, 1)] = i;
-  }
-}
-
 template <class WT>
-__global__ void k_match(const int64_t* off, const int32_t* len, const int32_t* col, const WT* w, const u64* keys,
-                        int64_t nrec, int bshift, const int64_t* seg, const int32_t* nseg, int32_t* pos,
-                        int64_t* oldw) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+__global__ void k_lookup(const int64_t* off, const int32_t* len, const int32_t* col, const WT* w, const u64* keys,
+                         int64_t nrec, int bshift, int32_t* pos, int32_t* lb, int64_t* oldw) {
   const u64 cmask = (((u64)1) << bshift) - 1;
-  const int64_t ns = *nseg;
-  for (int64_t si = warp; si < ns; si += nw) {
-    const int64_t s = seg[si];
-    const int64_t e = seg_end(keys, s, nrec, bshift);
-    const int64_t row = (int64_t)(keys[s] >> bshift);
-    const int64_t ro = off[row];
-    const int32_t rl = len[row];
-    for (int32_t k = lane; k < rl; k += 32) {
-      const int32_t c = col[ro + k];
-      if (c < 0) continue;
-      int64_t lo = s, hi = e;
-      while (lo < hi) {
-        int64_t mid = (lo + hi) >> 1;
-        if ((int64_t)(keys[mid] & cmask) < (int64_t)c) lo = mid + 1; else hi = mid;
-      }
-      if (lo < e && (int64_t)(keys[lo] & cmask) == (int64_t)c) {
-        pos[lo] = k;
-        if (oldw) oldw[lo] = (int64_t)w[ro + k];
-      }
+  GRID_STRIDE(i, nrec) {
+    const int64_t row = (int64_t)(keys[i] >> bshift);
+    const int32_t c = (int32_t)(keys[i] & cmask);
+    const int64_t o = off[row];
+    const int32_t l = len[row];
+    const int32_t p = row_lower_bound(col, o, l, c);
+    const bool found = p < l && col[o + p] == c;
+    pos[i] = found ? p : -1;
+    if (lb) lb[i] = p;
+    oldw[i] = found ? (int64_t)w[o + p] : 0;
+  }
+}
+
+// per record: insert / delete flags and segment heads (row changes)
+__global__ void k_rec_flags(const u64* keys, const int64_t* delta, int64_t nrec, int bshift, const int32_t* pos,
+                            const int64_t* oldw, int32_t* fins, int32_t* fdel, int32_t* fhead, int32_t* err) {
+  GRID_STRIDE(i, nrec) {
+    const bool found = pos[i] >= 0;
+    const int64_t nv = (found ? oldw[i] : 0) + delta[i];
+    if (nv < 0 || (!found && nv == 0)) atomicExch(err, 1);
+    fins[i] = (!found && nv > 0) ? 1 : 0;
+    fdel[i] = (found && nv == 0) ? 1 : 0;
+    fhead[i] = (i == 0 || (keys[i] >> bshift) != (keys[i - 1] >> bshift)) ? 1 : 0;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    fins[nrec] = 0;
+    fdel[nrec] = 0;
+    fhead[nrec] = 0;
+  }
+}
+
+__global__ void k_seg_info(const u64* keys, int64_t nrec, int bshift, const int32_t* fhead, const int64_t* segid,
+                           int64_t* seg_start, int64_t* seg_row) {
+  GRID_STRIDE(i, nrec) {
+    if (fhead[i]) {
+      seg_start[segid[i]] = i;
+      seg_row[segid[i]] = (int64_t)(keys[i] >> bshift);
     }
   }
 }
 
-// Per segment: count inserts and deletes, decide relocation.
-__global__ void k_plan(const int32_t* len, const int32_t* cap, const u64* keys, const int64_t* delta, int64_t nrec,
-                       int bshift, const int64_t* seg, const int32_t* nseg, const int32_t* pos, const int64_t* oldw,
-                       int32_t* newcap, int64_t* need, int32_t* err) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  const int64_t ns = *nseg;
-  for (int64_t si = warp; si < ns; si += nw) {
-    const int64_t s = seg[si];
-    const int64_t e = seg_end(keys, s, nrec, bshift);
-    const int64_t row = (int64_t)(keys[s] >> bshift);
-    int ins = 0, del = 0, bad = 0;
-    for (int64_t i = s + lane; i < e; i += 32) {
-      const bool found = pos[i] >= 0;
-      const int64_t nw_ = (found ? oldw[i] : 0) + delta[i];
-      if (nw_ < 0) bad = 1;
-      if (!found && nw_ > 0) ++ins;
-      if (!found && nw_ == 0) bad = 1;  // a zero delta on an absent entry never reaches here
-      if (found && nw_ == 0) ++del;
+// Per segment: new length, whether the row is rebuilt, relocation size.
+__global__ void k_plan(int64_t nseg, int64_t nrec, const int64_t* seg_start, const int64_t* seg_row,
+                       const int64_t* pins, const int64_t* pdel, const int32_t* len, const int32_t* cap,
+                       int32_t* newcap, int64_t* scratch_len, int64_t* work_len, int64_t* need) {
+  GRID_STRIDE(s, nseg) {
+    const int64_t a = seg_start[s];
+    const int64_t b = s + 1 < nseg ? seg_start[s + 1] : nrec;
+    const int64_t row = seg_row[s];
+    const int64_t ins = pins[b] - pins[a], del = pdel[b] - pdel[a];
+    const int64_t l = len[row];
+    const int64_t nl = l - del + ins;
+    const bool rewrite = ins > 0 || del > 0;
+    int32_t nc = 0;
+    if (nl > cap[row]) {
+      int64_t want = nl + (nl >> 1) + 4;
+      want = (want + 3) & ~(int64_t)3;
+      nc = (int32_t)want;
+      atomic_add_i64(need, want);
     }
-    ins = warp_sum_i32(ins);
-    del = warp_sum_i32(del);
-    bad = warp_sum_i32(bad);
-    if (lane == 0) {
-      if (bad) atomicExch(err, 1);
-      const int64_t nl = (int64_t)len[row] - del + ins;
-      int32_t nc = 0;
-      if (nl > cap[row]) {
-        int64_t want = nl + (nl >> 1) + 4;
-        want = (want + 3) & ~(int64_t)3;
-        nc = (int32_t)want;
-        atomic_add_i64(need, want);
-      }
-      newcap[si] = nc;
-    }
+    newcap[s] = nc;
+    scratch_len[s] = rewrite ? l : 0;
+    work_len[s] = rewrite ? l + ins : 0;
   }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    scratch_len[nseg] = 0;
+    work_len[nseg] = 0;
+  }
+}
+
+// weight updates in place; deleted entries get weight 0 (live weights are >= 1)
+template <class WT>
+__global__ void k_update(const int64_t* off, const u64* keys, const int64_t* delta, int64_t nrec, int bshift,
+                         const int32_t* pos, const int64_t* oldw, WT* w) {
+  GRID_STRIDE(i, nrec) {
+    if (pos[i] < 0) continue;
+    const int64_t row = (int64_t)(keys[i] >> bshift);
+    w[off[row] + pos[i]] = (WT)(oldw[i] + delta[i]);
+  }
+}
+
+__device__ inline int64_t find_seg(const int64_t* pre, int64_t nseg, int64_t t) {
+  // last s with pre[s] <= t (pre is an exclusive scan, pre[0] = 0)
+  int64_t lo = 0, hi = nseg;
+  while (hi - lo > 1) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (pre[mid] <= t) lo = mid; else hi = mid;
+  }
+  return lo;
 }
 
 template <class WT>
-__global__ void k_relocate(int64_t* off, int32_t* len, int32_t* cap, int32_t* col, WT* w, const u64* keys,
-                           int bshift, const int64_t* seg, const int32_t* nseg, const int32_t* newcap,
+__global__ void k_copy_scratch(const int64_t* off, const int64_t* seg_row, int64_t nseg, const int64_t* soff,
+                               int64_t total, const int32_t* col, const WT* w, int32_t* scol, WT* sw) {
+  GRID_STRIDE(t, total) {
+    const int64_t s = find_seg(soff, nseg, t);
+    const int64_t row = seg_row[s];
+    const int64_t k = t - soff[s];
+    scol[t] = col[off[row] + k];
+    sw[t] = w[off[row] + k];
+  }
+}
+
+__global__ void k_relocate(int64_t nseg, const int64_t* seg_row, const int32_t* newcap, int64_t* off, int32_t* cap,
                            int64_t* pool_top) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  const int64_t ns = *nseg;
-  for (int64_t si = warp; si < ns; si += nw) {
-    const int32_t nc = newcap[si];
+  GRID_STRIDE(s, nseg) {
+    const int32_t nc = newcap[s];
     if (nc == 0) continue;
-    const int64_t row = (int64_t)(keys[seg[si]] >> bshift);
-    int64_t no = 0;
-    if (lane == 0) no = (int64_t)atomicAdd((unsigned long long*)pool_top, (unsigned long long)nc);
-    no = __shfl_sync(0xffffffffu, no, 0);
-    const int64_t oo = off[row];
-    const int32_t rl = len[row];
-    for (int32_t k = lane; k < rl; k += 32) {
-      col[no + k] = col[oo + k];
-      w[no + k] = w[oo + k];
-    }
-    __syncwarp();
-    if (lane == 0) {
-      off[row] = no;
-      cap[row] = nc;
+    const int64_t row = seg_row[s];
+    off[row] = (int64_t)atomicAdd((unsigned long long*)pool_top, (unsigned long long)nc);
+    cap[row] = nc;
+  }
+}
+
+// Rebuild of rows with inserts or deletes: item t is either a kept old entry
+// (from scratch) or an inserted record; each computes its sorted position.
+template <class WT>
+__global__ void k_scatter_rows(int64_t nseg, int64_t nrec, const int64_t* seg_start, const int64_t* seg_row,
+                               const int64_t* woff, const int64_t* soff, int64_t total, const int32_t* scol,
+                               const WT* sw, const u64* keys, const int64_t* delta, const int32_t* lb,
+                               const int32_t* fins, const int64_t* pins, const int64_t* pdel, int bshift,
+                               const int64_t* off, int32_t* col, WT* w) {
+  const u64 cmask = (((u64)1) << bshift) - 1;
+  GRID_STRIDE(t, total) {
+    const int64_t s = find_seg(woff, nseg, t);
+    const int64_t a = seg_start[s];
+    const int64_t b = s + 1 < nseg ? seg_start[s + 1] : nrec;
+    const int64_t row = seg_row[s];
+    const int64_t lold = (woff[s + 1] - woff[s]) - (pins[b] - pins[a]);
+    const int64_t k = t - woff[s];
+    if (k < lold) {
+      const int64_t i = k;
+      const WT x = sw[soff[s] + i];
+      if (x == 0) continue;  // deleted
+      const int32_t c = scol[soff[s] + i];
+      // records of this segment with a smaller column
+      int64_t lo = a, hi = b;
+      while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if ((int32_t)(keys[mid] & cmask) < c) lo = mid + 1; else hi = mid;
+      }
+      const int64_t dst = i - (pdel[lo] - pdel[a]) + (pins[lo] - pins[a]);
+      col[off[row] + dst] = c;
+      w[off[row] + dst] = x;
+    } else {
+      const int64_t q = k - lold;  // q-th insert of the segment
+      int64_t lo = a, hi = b - 1;
+      while (lo < hi) {  // first J with pins[J] - pins[a] >= q and fins[J]
+        const int64_t mid = (lo + hi) >> 1;
+        if (pins[mid + 1] - pins[a] <= q) lo = mid + 1; else hi = mid;
+      }
+      const int64_t J = lo;
+      const int64_t dst = (int64_t)lb[J] - (pdel[J] - pdel[a]) + q;
+      col[off[row] + dst] = (int32_t)(keys[J] & cmask);
+      w[off[row] + dst] = (WT)delta[J];
+      (void)fins;
     }
   }
 }
 
+__global__ void k_set_len(int64_t nseg, int64_t nrec, const int64_t* seg_start, const int64_t* seg_row,
+                          const int64_t* pins, const int64_t* pdel, int32_t* len) {
+  GRID_STRIDE(s, nseg) {
+    const int64_t a = seg_start[s];
+    const int64_t b = s + 1 < nseg ? seg_start[s + 1] : nrec;
+    const int64_t row = seg_row[s];
+    len[row] = (int32_t)(len[row] - (pdel[b] - pdel[a]) + (pins[b] - pins[a]));
+  }
+}
+
+// compaction: rows copied contiguously into a fresh pool (offsets = scan of caps)
 template <class WT>
-__global__ void k_write(const int64_t* off, int32_t* len, int32_t* col, WT* w, const u64* keys, const int64_t* delta,
-                        int64_t nrec, int bshift, const int64_t* seg, const int32_t* nseg, const int32_t* pos,
-                        const int64_t* oldw) {
+__global__ void k_compact_rows(int64_t n, const int64_t* off, const int32_t* len, const int64_t* noff,
+                               const int32_t* col, const WT* w, int32_t* ncol, WT* nw) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  const u64 cmask = (((u64)1) << bshift) - 1;
-  const int64_t ns = *nseg;
-  for (int64_t si = warp; si < ns; si += nw) {
-    const int64_t s = seg[si];
-    const int64_t e = seg_end(keys, s, nrec, bshift);
-    const int64_t row = (int64_t)(keys[s] >> bshift);
-    const int64_t ro = off[row];
-    int del = 0;
-    for (int64_t i = s + lane; i < e; i += 32) {
-      if (pos[i] >= 0) {
-        const int64_t nv = oldw[i] + delta[i];
-        if (nv == 0) {
-          col[ro + pos[i]] = -1;
-          ++del;
-        } else {
-          w[ro + pos[i]] = (WT)nv;
-        }
-      }
+  const int64_t nwp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t v = warp; v < n; v += nwp) {
+    const int64_t o = off[v], d = noff[v];
+    const int32_t l = len[v];
+    for (int32_t k = lane; k < l; k += 32) {
+      ncol[d + k] = col[o + k];
+      nw[d + k] = w[o + k];
     }
-    del = warp_sum_i32(del);
-    del = __shfl_sync(0xffffffffu, del, 0);
-    __syncwarp();
-    int32_t rl = len[row];
-    if (del > 0) {  // stable in-place compaction of the row
-      int32_t out = 0;
-      for (int32_t base = 0; base < rl; base += 32) {
-        const int32_t k = base + lane;
-        int32_t c = -1;
-        WT x = 0;
-        if (k < rl) {
-          c = col[ro + k];
-          x = w[ro + k];
-        }
-        const bool keep = c >= 0;
-        const unsigned bal = __ballot_sync(0xffffffffu, keep);
-        __syncwarp();
-        if (keep) {
-          const int32_t o = out + __popc(bal & ((1u << lane) - 1u));
-          col[ro + o] = c;
-          w[ro + o] = x;
-        }
-        out += __popc(bal);
-        __syncwarp();
-      }
-      rl = out;
-    }
-    // append inserts in record order
-    int32_t top = rl;
-    for (int64_t b = s; b < e; b += 32) {
-      const int64_t i = b + lane;
-      bool ins = false;
-      int64_t nv = 0;
-      if (i < e && pos[i] < 0) {
-        nv = delta[i];
-        ins = nv > 0;
-      }
-      const unsigned bal = __ballot_sync(0xffffffffu, ins);
-      if (ins) {
-        const int32_t o = top + __popc(bal & ((1u << lane) - 1u));
-        col[ro + o] = (int32_t)(keys[i] & cmask);
-        w[ro + o] = (WT)nv;
-      }
-      top += __popc(bal);
-    }
-    __syncwarp();
-    if (lane == 0) len[row] = top;
   }
 }
 
 // ---------------------------------------------------------------- build
 __global__ void k_count_rows(const u64* keys, int64_t nrec, int bshift, int32_t* cnt) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nrec; i += (int64_t)gridDim.x * blockDim.x)
-    atomicAdd(&cnt[keys[i] >> bshift], 1);
+  GRID_STRIDE(i, nrec) atomicAdd(&cnt[keys[i] >> bshift], 1);
 }
 
 __global__ void k_caps(const int32_t* cnt, int64_t n, int32_t* cap, int slack_pct) {
-  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+  GRID_STRIDE(v, n) {
     const int64_t d = cnt[v];
     int64_t c = d + (d * slack_pct) / 100 + (d ? 2 : 0);
     c = (c + 1) & ~(int64_t)1;
@@ -223,7 +237,7 @@ template <class WT>
 __global__ void k_scatter_build(const u64* keys, const int64_t* vals, int64_t nrec, int bshift, const int64_t* rs,
                                 const int64_t* off, int32_t* col, WT* w) {
   const u64 cmask = (((u64)1) << bshift) - 1;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nrec; i += (int64_t)gridDim.x * blockDim.x) {
+  GRID_STRIDE(i, nrec) {
     const int64_t row = (int64_t)(keys[i] >> bshift);
     const int64_t p = off[row] + (i - rs[row]);
     col[p] = (int32_t)(keys[i] & cmask);
@@ -232,8 +246,7 @@ __global__ void k_scatter_build(const u64* keys, const int64_t* vals, int64_t nr
 }
 
 __global__ void k_i32_to_i64(const int32_t* a, int64_t* b, int64_t n) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    b[i] = a[i];
+  GRID_STRIDE(i, n) b[i] = a[i];
 }
 
 }  // namespace
@@ -248,17 +261,17 @@ void csr_build(SlackCSR<WT>& g, int64_t n, const u64* keys, const int64_t* vals,
   g.cap.exact(n + 1);
   CK(cudaMemsetAsync(g.len.p, 0, sizeof(int32_t) * (size_t)(n + 1), s));
   if (nrec > 0) {
-    k_count_rows<<<grid_for(nrec, 256), 256, 0, s>>>(keys, nrec, bshift, g.len.p);
+    k_count_rows<<<grid_for(nrec, TPB), TPB, 0, s>>>(keys, nrec, bshift, g.len.p);
     CKL("k_count_rows");
   }
-  k_caps<<<grid_for(n, 256), 256, 0, s>>>(g.len.p, n, g.cap.p, slack_pct);
+  k_caps<<<grid_for(n, TPB), TPB, 0, s>>>(g.len.p, n, g.cap.p, slack_pct);
   CKL("k_caps");
   S.rs.reserve(n + 1, s);
   S.tmp64.reserve(n + 1, s);
-  k_i32_to_i64<<<grid_for(n, 256), 256, 0, s>>>(g.len.p, S.tmp64.p, n);
+  k_i32_to_i64<<<grid_for(n, TPB), TPB, 0, s>>>(g.len.p, S.tmp64.p, n);
   CKL("k_i32_to_i64");
   scan_exclusive(S.tmp64.p, S.rs.p, n, P, s, false);
-  k_i32_to_i64<<<grid_for(n, 256), 256, 0, s>>>(g.cap.p, S.tmp64.p, n);
+  k_i32_to_i64<<<grid_for(n, TPB), TPB, 0, s>>>(g.cap.p, S.tmp64.p, n);
   CKL("k_i32_to_i64");
   const int64_t total = scan_exclusive(S.tmp64.p, g.off.p, n, P, s, true);
   const int64_t pool = total + total / 8 + 1024;
@@ -268,8 +281,7 @@ void csr_build(SlackCSR<WT>& g, int64_t n, const u64* keys, const int64_t* vals,
   g.w.exact(pool);
   g.pool_top = total;
   if (nrec > 0) {
-    k_scatter_build<WT><<<grid_for(nrec, 256), 256, 0, s>>>(keys, vals, nrec, bshift, S.rs.p, g.off.p, g.col.p,
-                                                            g.w.p);
+    k_scatter_build<WT><<<grid_for(nrec, TPB), TPB, 0, s>>>(keys, vals, nrec, bshift, S.rs.p, g.off.p, g.col.p, g.w.p);
     CKL("k_scatter_build");
   }
 }
@@ -278,16 +290,37 @@ template <class WT>
 void csr_lookup(const SlackCSR<WT>& g, const u64* keys, int64_t nrec, int bshift, int32_t* pos, int64_t* oldw,
                 CsrScratch& S, Prims& P, cudaStream_t s, int32_t* d_nseg) {
   (void)P;
+  (void)S;
+  (void)d_nseg;
   if (nrec <= 0) return;
-  S.seg.reserve(nrec + 1, s);
-  CK(cudaMemsetAsync(d_nseg, 0, sizeof(int32_t), s));
-  CK(cudaMemsetAsync(pos, 0xff, sizeof(int32_t) * (size_t)nrec, s));
-  CK(cudaMemsetAsync(oldw, 0, sizeof(int64_t) * (size_t)nrec, s));
-  k_seg_heads<<<grid_for(nrec, 256), 256, 0, s>>>(keys, nrec, bshift, S.seg.p, d_nseg);
-  CKL("k_seg_heads");
-  k_match<WT><<<grid_for(nrec * 32, 256), 256, 0, s>>>(g.off.p, g.len.p, g.col.p, g.w.p, keys, nrec, bshift,
-                                                      S.seg.p, d_nseg, pos, oldw);
-  CKL("k_match");
+  k_lookup<WT><<<grid_for(nrec, TPB), TPB, 0, s>>>(g.off.p, g.len.p, g.col.p, g.w.p, keys, nrec, bshift, pos, nullptr,
+                                                   oldw);
+  CKL("k_lookup");
+}
+
+// Copy every row into a fresh pool of `cap_total + extra` slots.
+template <class WT>
+static void compact_pool(SlackCSR<WT>& g, int64_t extra, CsrScratch& S, Prims& P, cudaStream_t s) {
+  const int64_t n = g.n;
+  S.tmp64.reserve(n + 1, s);
+  S.rs.reserve(n + 1, s);
+  k_i32_to_i64<<<grid_for(n, TPB), TPB, 0, s>>>(g.cap.p, S.tmp64.p, n);
+  CKL("k_i32_to_i64");
+  const int64_t total = scan_exclusive(S.tmp64.p, S.rs.p, n, P, s, true);  // new offsets
+  const int64_t pool = total + extra + (total + extra) / 4 + 4096;
+  int32_t* c2 = (int32_t*)dalloc(sizeof(int32_t) * (size_t)pool);
+  WT* w2 = (WT*)dalloc(sizeof(WT) * (size_t)pool);
+  k_compact_rows<WT><<<grid_for(n * 32, TPB), TPB, 0, s>>>(n, g.off.p, g.len.p, S.rs.p, g.col.p, g.w.p, c2, w2);
+  CKL("k_compact_rows");
+  CK(cudaMemcpyAsync(g.off.p, S.rs.p, sizeof(int64_t) * (size_t)n, cudaMemcpyDeviceToDevice, s));
+  CK(cudaStreamSynchronize(s));
+  dfree(g.col.p);
+  dfree(g.w.p);
+  g.col.p = c2;
+  g.col.cap = pool;
+  g.w.p = w2;
+  g.w.cap = pool;
+  g.pool_top = total;
 }
 
 template <class WT>
@@ -295,47 +328,74 @@ void csr_apply(SlackCSR<WT>& g, const u64* keys, const int64_t* delta, int64_t n
                Prims& P, cudaStream_t s, DevScalars* d_sc) {
   if (nrec <= 0) return;
   S.pos.reserve(nrec + 1, s);
+  S.lb.reserve(nrec + 1, s);
   S.oldw.reserve(nrec + 1, s);
-  S.newcap.reserve(nrec + 1, s);
-  int32_t* d_nseg = &d_sc->cnt[C_SEG];
-  csr_lookup<WT>(g, keys, nrec, bshift, S.pos.p, S.oldw.p, S, P, s, d_nseg);
-  CK(cudaMemsetAsync(&d_sc->need, 0, sizeof(int64_t), s));
+  S.fins.reserve(nrec + 1, s);
+  S.fdel.reserve(nrec + 1, s);
+  S.fhead.reserve(nrec + 1, s);
+  S.pins.reserve(nrec + 1, s);
+  S.pdel.reserve(nrec + 1, s);
+  S.segid.reserve(nrec + 1, s);
+  const int gr = grid_for(nrec, TPB);
+  k_lookup<WT><<<gr, TPB, 0, s>>>(g.off.p, g.len.p, g.col.p, g.w.p, keys, nrec, bshift, S.pos.p, S.lb.p, S.oldw.p);
+  CKL("k_lookup");
   CK(cudaMemsetAsync(&d_sc->cnt[C_Z], 0, sizeof(int32_t), s));
-  const int gw = grid_for(nrec * 32, 256);
-  k_plan<<<gw, 256, 0, s>>>(g.len.p, g.cap.p, keys, delta, nrec, bshift, S.seg.p, d_nseg, S.pos.p, S.oldw.p,
-                            S.newcap.p, &d_sc->need, &d_sc->cnt[C_Z]);
+  k_rec_flags<<<gr, TPB, 0, s>>>(keys, delta, nrec, bshift, S.pos.p, S.oldw.p, S.fins.p, S.fdel.p, S.fhead.p,
+                                 &d_sc->cnt[C_Z]);
+  CKL("k_rec_flags");
+  scan_exclusive_i32(S.fins.p, S.pins.p, nrec + 1, P, s, false);
+  scan_exclusive_i32(S.fdel.p, S.pdel.p, nrec + 1, P, s, false);
+  const int64_t nseg = scan_exclusive_i32(S.fhead.p, S.segid.p, nrec, P, s, true);
+  S.seg.reserve(nseg + 1, s);
+  S.segrow.reserve(nseg + 1, s);
+  S.newcap.reserve(nseg + 1, s);
+  S.slen.reserve(nseg + 2, s);
+  S.wlen.reserve(nseg + 2, s);
+  S.soff.reserve(nseg + 2, s);
+  S.woff.reserve(nseg + 2, s);
+  k_seg_info<<<gr, TPB, 0, s>>>(keys, nrec, bshift, S.fhead.p, S.segid.p, S.seg.p, S.segrow.p);
+  CKL("k_seg_info");
+  CK(cudaMemsetAsync(&d_sc->need, 0, sizeof(int64_t), s));
+  const int gs = grid_for(nseg, TPB);
+  k_plan<<<gs, TPB, 0, s>>>(nseg, nrec, S.seg.p, S.segrow.p, S.pins.p, S.pdel.p, g.len.p, g.cap.p, S.newcap.p,
+                            S.slen.p, S.wlen.p, &d_sc->need);
   CKL("k_plan");
-  int64_t need = 0;
+  scan_exclusive(S.slen.p, S.soff.p, nseg + 1, P, s, false);
+  scan_exclusive(S.wlen.p, S.woff.p, nseg + 1, P, s, false);
+  int64_t tot[3] = {0, 0, 0};
   int32_t bad = 0;
-  CK(cudaMemcpyAsync(&need, &d_sc->need, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(&tot[0], &d_sc->need, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(&tot[1], S.soff.p + nseg, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(&tot[2], S.woff.p + nseg, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(&bad, &d_sc->cnt[C_Z], sizeof(int32_t), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   if (bad) ldl_throw(LDL_E_INVALID, "internal: adjacency update would make a weight negative");
-  if (need > 0) {
-    if (g.pool_top + need > g.col.cap) {
-      int64_t nc = (g.pool_top + need) + (g.pool_top + need) / 4 + 4096;
-      // grow the pool keeping its contents
-      int32_t* c2 = (int32_t*)dalloc(sizeof(int32_t) * (size_t)nc);
-      WT* w2 = (WT*)dalloc(sizeof(WT) * (size_t)nc);
-      CK(cudaMemcpyAsync(c2, g.col.p, sizeof(int32_t) * (size_t)g.pool_top, cudaMemcpyDeviceToDevice, s));
-      CK(cudaMemcpyAsync(w2, g.w.p, sizeof(WT) * (size_t)g.pool_top, cudaMemcpyDeviceToDevice, s));
-      CK(cudaStreamSynchronize(s));
-      dfree(g.col.p);
-      dfree(g.w.p);
-      g.col.p = c2;
-      g.col.cap = nc;
-      g.w.p = w2;
-      g.w.cap = nc;
+  const int64_t need = tot[0], stotal = tot[1], wtotal = tot[2];
+  if (g.pool_top + need > g.col.cap) compact_pool<WT>(g, need, S, P, s);
+  k_update<WT><<<gr, TPB, 0, s>>>(g.off.p, keys, delta, nrec, bshift, S.pos.p, S.oldw.p, g.w.p);
+  CKL("k_update");
+  if (wtotal > 0) {
+    S.scol.reserve(stotal + 1, s);
+    DBuf<WT>& sw = S.template sw_of<WT>();
+    sw.reserve(stotal + 1, s);
+    if (stotal > 0) {
+      k_copy_scratch<WT><<<grid_for(stotal, TPB), TPB, 0, s>>>(g.off.p, S.segrow.p, nseg, S.soff.p, stotal, g.col.p,
+                                                               g.w.p, S.scol.p, sw.p);
+      CKL("k_copy_scratch");
     }
-    CK(cudaMemcpyAsync(&d_sc->pool_top, &g.pool_top, sizeof(int64_t), cudaMemcpyHostToDevice, s));
-    k_relocate<WT><<<gw, 256, 0, s>>>(g.off.p, g.len.p, g.cap.p, g.col.p, g.w.p, keys, bshift, S.seg.p, d_nseg,
-                                      S.newcap.p, &d_sc->pool_top);
-    CKL("k_relocate");
-    g.pool_top += need;
+    if (need > 0) {
+      CK(cudaMemcpyAsync(&d_sc->pool_top, &g.pool_top, sizeof(int64_t), cudaMemcpyHostToDevice, s));
+      k_relocate<<<gs, TPB, 0, s>>>(nseg, S.segrow.p, S.newcap.p, g.off.p, g.cap.p, &d_sc->pool_top);
+      CKL("k_relocate");
+      g.pool_top += need;
+    }
+    k_scatter_rows<WT><<<grid_for(wtotal, TPB), TPB, 0, s>>>(nseg, nrec, S.seg.p, S.segrow.p, S.woff.p, S.soff.p,
+                                                             wtotal, S.scol.p, sw.p, keys, delta, S.lb.p, S.fins.p,
+                                                             S.pins.p, S.pdel.p, bshift, g.off.p, g.col.p, g.w.p);
+    CKL("k_scatter_rows");
+    k_set_len<<<gs, TPB, 0, s>>>(nseg, nrec, S.seg.p, S.segrow.p, S.pins.p, S.pdel.p, g.len.p);
+    CKL("k_set_len");
   }
-  k_write<WT><<<gw, 256, 0, s>>>(g.off.p, g.len.p, g.col.p, g.w.p, keys, delta, nrec, bshift, S.seg.p, d_nseg,
-                                 S.pos.p, S.oldw.p);
-  CKL("k_write");
 }
 
 template void csr_build<int32_t>(SlackCSR<int32_t>&, int64_t, const u64*, const int64_t*, int64_t, int, int,

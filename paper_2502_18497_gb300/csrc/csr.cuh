@@ -4,12 +4,23 @@
 #include "prims.cuh"
 
 struct CsrScratch {
-  DBuf<int64_t> seg, oldw, rs, tmp64;
-  DBuf<int32_t> pos, newcap;
+  DBuf<int64_t> seg, segrow, oldw, rs, tmp64, pins, pdel, segid, slen, wlen, soff, woff;
+  DBuf<int32_t> pos, lb, newcap, fins, fdel, fhead, scol, sw32;
+  DBuf<int64_t> sw64;
+  template <class WT>
+  DBuf<WT>& sw_of();
   void release() {
-    seg.release(); oldw.release(); rs.release(); tmp64.release(); pos.release(); newcap.release();
+    DBuf<int64_t>* a[] = {&seg, &segrow, &oldw, &rs, &tmp64, &pins, &pdel, &segid, &slen, &wlen, &soff, &woff,
+                          &sw64};
+    for (auto* b : a) b->release();
+    DBuf<int32_t>* c[] = {&pos, &lb, &newcap, &fins, &fdel, &fhead, &scol, &sw32};
+    for (auto* b : c) b->release();
   }
 };
+template <>
+inline DBuf<int32_t>& CsrScratch::sw_of<int32_t>() { return sw32; }
+template <>
+inline DBuf<int64_t>& CsrScratch::sw_of<int64_t>() { return sw64; }
 
 // Build g over rows [0,n) from sorted unique records (key = row<<bshift|col,
 // vals = weights), with slack_pct percent spare capacity per row.

@@ -81,6 +81,7 @@ struct ldl_ctx {
   DBuf<int32_t> ndx, ndx2;
   DBuf<int64_t> ndko, ndki, ndko2, ndki2;
   DBuf<u64> crk, crv, fk;
+  DBuf<int64_t> chunk_cnt, chunk_pre;
   DBuf<ldl_update> upd;
   Prims P;
   CsrScratch CS;
@@ -90,7 +91,7 @@ struct ldl_ctx {
   int64_t frontier[8] = {0};
   int timing = 0;
   double stage_ms[16] = {0};
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr, ev3 = nullptr;
   // per-kernel statistics of the sweep kernels (enabled by ldl_set_kernel_stats)
   int kstats = 0;
   cudaEvent_t kev[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -128,4 +129,8 @@ void set_cnt(ldl_ctx& c, int idx, int32_t v);
 // stage timing
 void stage_begin(ldl_ctx& c);
 void stage_end(ldl_ctx& c, int stage);
-enum { ST_INGEST = 0, ST_REPAIR, ST_EXPAND, ST_BEST, ST_DECOUPLE, ST_COMMIT, ST_REFINE, ST_AGG, ST_PUSH };
+enum { ST_INGEST = 0, ST_REPAIR, ST_EXPAND, ST_BEST, ST_DECOUPLE, ST_COMMIT, ST_REFINE, ST_AGG, ST_PUSH,
+       SU_AGG_EMIT, SU_AGG_SORT, SU_AGG_APPLY, SU_AGG_UP, SU_AGG_EXIST, SU_REF_DISSOLVE, SU_REF_LOOP };
+// nested sub-stage timers (their own events)
+void sub_begin(ldl_ctx& c);
+void sub_end(ldl_ctx& c, int stage);

@@ -2,6 +2,7 @@
 // statistic repair along the parent chain (line 2, InitFrontier line 3),
 // label push-down after supernode moves, TouchedRefined / dissolve (line 16),
 // and the Eq. 3 subtract-add aggregate repair with NextFrontier (lines 23-24).
+#include "chunks.cuh"
 #include "kern.cuh"
 
 namespace {
@@ -190,25 +191,32 @@ __global__ void k_map_list(const int32_t* l, const int32_t* n, const int32_t* pa
 
 // ---------------------------------------------------------------- push-down
 // Children of each listed level-(q+1) node take its label at level q.
-__global__ void k_push(const int32_t* list, const int32_t* nlist, const int32_t* lab_up, Adj<int32_t> ch,
-                       int32_t* lab, int32_t* olist, int32_t* nout, int32_t* stCh, int32_t epCh, int32_t* lCh,
-                       int32_t* nCh, int32_t* lab_before) {
+__global__ void k_push(ChunkMap m, const int32_t* lab_up, Adj<int32_t> ch_adj, int32_t* lab, int32_t* olist,
+                       int32_t* nout, int32_t* stCh, int32_t epCh, int32_t* lCh, int32_t* nCh, int32_t* lab_before) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  const int32_t nl = *nlist;
-  for (int64_t t = warp; t < nl; t += nw) {
-    const int32_t x = list[t];
-    const int32_t L = lab_up[x];
-    const int64_t o = ch.off[x];
-    const int32_t l = ch.len[x];
-    for (int32_t k = lane; k < l; k += 32) {
-      const int32_t u = ch.col[o + k];
-      if (stCh) {
-        if (stamp_add(stCh, epCh, u, lCh, nCh)) lab_before[u] = lab[u];
+  const int64_t total = m.pre[m.n_hint];
+  for (int64_t c = warp; c < total; c += nw) {
+    const Chunk ch = chunk_of(m, c);
+    if (ch.row < 0) continue;
+    const int32_t L = lab_up[ch.v];
+    const int64_t o = ch_adj.off[ch.v];
+    for (int32_t base = ch.k0; base < ch.k1; base += 32) {
+      const int32_t k = base + lane;
+      const bool valid = k < ch.k1;
+      int32_t u = 0;
+      bool first = false;
+      if (valid) {
+        u = ch_adj.col[o + k];
+        if (stCh) {
+          first = stamp_claim(stCh, epCh, u);
+          if (first) lab_before[u] = lab[u];
+        }
+        lab[u] = L;
       }
-      lab[u] = L;
-      if (olist) olist[atomicAdd(nout, 1)] = u;
+      if (stCh) warp_append(first, u, lCh, nCh);
+      if (olist) warp_append(valid, u, olist, nout);
     }
   }
 }
@@ -225,17 +233,25 @@ __global__ void k_touched(const int32_t* lU, const int32_t* nU, const int32_t* p
   }
 }
 
-__global__ void k_collect(const int32_t* lX, const int32_t* nX, Adj<int32_t> ch, int32_t* stD, int32_t epD,
-                          int32_t* lD, int32_t* nD) {
+__global__ void k_collect(Adj<int32_t> ch_adj, ChunkMap m, int32_t* stD, int32_t epD, int32_t* lD, int32_t* nD) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  const int32_t nl = *nX;
-  for (int64_t t = warp; t < nl; t += nw) {
-    const int32_t x = lX[t];
-    const int64_t o = ch.off[x];
-    const int32_t l = ch.len[x];
-    for (int32_t k = lane; k < l; k += 32) stamp_add(stD, epD, ch.col[o + k], lD, nD);
+  const int64_t total = m.pre[m.n_hint];
+  for (int64_t c = warp; c < total; c += nw) {
+    const Chunk ch = chunk_of(m, c);
+    if (ch.row < 0) continue;
+    const int64_t o = ch_adj.off[ch.v];
+    for (int32_t base = ch.k0; base < ch.k1; base += 32) {
+      const int32_t k = base + lane;
+      bool want = false;
+      int32_t u = 0;
+      if (k < ch.k1) {
+        u = ch_adj.col[o + k];
+        want = stamp_claim(stD, epD, u);
+      }
+      warp_append(want, u, lD, nD);
+    }
   }
 }
 
@@ -299,52 +315,48 @@ __global__ void k_deg_sum(Adj<WT> out, Adj<WT> in, const int32_t* l, const int32
 // each arc counted once (from its changed tail's out-row, or from its changed
 // head's in-row when the tail is unchanged).
 template <class WT>
-__global__ void k_emit(Adj<WT> out, Adj<WT> in, const int32_t* lC, const int32_t* nC, const int32_t* par,
-                       const int32_t* par_old, const int32_t* stC, int32_t epC, int bits, u64* rk, u64* rv,
-                       int32_t* cnt) {
+__global__ void k_emit(Adj<WT> out, Adj<WT> in, ChunkMap m, const int32_t* par, const int32_t* par_old,
+                       const int32_t* stC, int32_t epC, int bits, u64* rk, u64* rv, int32_t* cnt) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  const int32_t nl = *nC;
-  for (int64_t t = warp; t < nl; t += nw) {
-    const int32_t u = lC[t];
+  const int64_t total = m.pre[m.n_hint];
+  for (int64_t c = warp; c < total; c += nw) {
+    const Chunk ch = chunk_of(m, c);
+    if (ch.row < 0) continue;
+    const int32_t u = ch.v;
     const int32_t po = par_old[u], pn = par[u];
-    {
-      const int64_t o = out.off[u];
-      const int32_t l = out.len[u];
-      for (int32_t k = lane; k < l; k += 32) {
-        const int32_t v = out.col[o + k];
-        const int64_t w = (int64_t)out.w[o + k];
+    const Adj<WT>& A = ch.row ? in : out;
+    const int64_t o = A.off[u];
+    for (int32_t base = ch.k0; base < ch.k1; base += 32) {
+      const int32_t k = base + lane;
+      bool w1 = false, w2 = false;
+      u64 k1 = 0, v1 = 0, k2 = 0, v2 = 0;
+      if (k < ch.k1) {
+        const int32_t v = A.col[o + k];
+        const int64_t w = (int64_t)A.w[o + k];
         const bool vc = stC[v] == epC;
-        const int32_t pvo = vc ? par_old[v] : par[v];
-        const int32_t pvn = par[v];
-        if (po >= 0 && pvo >= 0) {
-          const int32_t p = atomicAdd(cnt, 1);
-          rk[p] = ((u64)po << bits) | (u64)pvo;
-          rv[p] = (u64)(-w);
+        if (ch.row == 0) {  // arc (u, v) from u's out-row
+          const int32_t pvo = vc ? par_old[v] : par[v];
+          const int32_t pvn = par[v];
+          w1 = po >= 0 && pvo >= 0;
+          k1 = ((u64)po << bits) | (u64)pvo;
+          v1 = (u64)(-w);
+          w2 = true;
+          k2 = ((u64)pn << bits) | (u64)pvn;
+          v2 = (u64)w;
+        } else if (!vc) {  // arc (v, u) from u's in-row, v unchanged
+          const int32_t pv = par[v];
+          w1 = po >= 0;
+          k1 = ((u64)pv << bits) | (u64)po;
+          v1 = (u64)(-w);
+          w2 = true;
+          k2 = ((u64)pv << bits) | (u64)pn;
+          v2 = (u64)w;
         }
-        const int32_t p = atomicAdd(cnt, 1);
-        rk[p] = ((u64)pn << bits) | (u64)pvn;
-        rv[p] = (u64)w;
       }
-    }
-    {
-      const int64_t o = in.off[u];
-      const int32_t l = in.len[u];
-      for (int32_t k = lane; k < l; k += 32) {
-        const int32_t v = in.col[o + k];
-        if (stC[v] == epC) continue;
-        const int64_t w = (int64_t)in.w[o + k];
-        const int32_t pv = par[v];
-        if (po >= 0) {
-          const int32_t p = atomicAdd(cnt, 1);
-          rk[p] = ((u64)pv << bits) | (u64)po;
-          rv[p] = (u64)(-w);
-        }
-        const int32_t p = atomicAdd(cnt, 1);
-        rk[p] = ((u64)pv << bits) | (u64)pn;
-        rv[p] = (u64)w;
-      }
+      warp_append_rec(w1, k1, v1, rk, rv, cnt);
+      warp_append_rec(w2, k2, v2, rk, rv, cnt);
     }
   }
 }
@@ -749,9 +761,10 @@ void pushdown(ldl_ctx& c, int r, int32_t epCh) {
     Adj<int32_t> ch{L.children.off.p, L.children.len.p, L.children.col.p, L.children.w.p};
     int32_t* dst = q > 0 ? bufs[flip] : nullptr;
     zero_cnt(c, idxs[flip]);
-    k_push<<<grid_for((int64_t)n * 32, TPB), TPB, 0, c.s>>>(
-        src, c.dcnt + idx, c.lv[q + 1].lab.p, ch, L.lab.p, dst, c.dcnt + idxs[flip], q == 0 ? c.stCh.p : nullptr,
-        epCh, c.lCh.p, c.dcnt + K_CH, c.lab_before.p);
+    ChunkMap m = chunk_map(c, src, c.dcnt + idx, n, L.children.len.p, nullptr);
+    k_push<<<grid_for((int64_t)n * 64, TPB, 152 * 16), TPB, 0, c.s>>>(
+        m, c.lv[q + 1].lab.p, ch, L.lab.p, dst, c.dcnt + idxs[flip], q == 0 ? c.stCh.p : nullptr, epCh, c.lCh.p,
+        c.dcnt + K_CH, c.lab_before.p);
     CKL("k_push");
     if (q > 0) {
       src = bufs[flip];
@@ -780,8 +793,9 @@ int32_t dissolve(ldl_ctx& c, int r, int32_t epD, int32_t epX, bool all_nodes) {
     const int32_t nx = rd_cnt(c, K_X);
     if (nx > 0) {
       Adj<int32_t> ch{L.children.off.p, L.children.len.p, L.children.col.p, L.children.w.p};
-      k_collect<<<grid_for((int64_t)nx * 32, TPB), TPB, 0, c.s>>>(c.lX.p, c.dcnt + K_X, ch, c.stD.p, epD, c.lD.p,
-                                                                  c.dcnt + K_D);
+      ChunkMap m = chunk_map(c, c.lX.p, c.dcnt + K_X, nx, L.children.len.p, nullptr);
+      k_collect<<<grid_for((int64_t)nx * 64, TPB, 152 * 16), TPB, 0, c.s>>>(ch, m, c.stD.p, epD, c.lD.p,
+                                                                           c.dcnt + K_D);
       CKL("k_collect");
     }
   }
@@ -813,9 +827,10 @@ static void emit_records(ldl_ctx& c, int r, Adj<WT> out, Adj<WT> in, int32_t nC,
   c.rk2.reserve(cap, c.s);
   c.rv2.reserve(cap, c.s);
   zero_cnt(c, K_REC);
-  k_emit<WT><<<grid_for((int64_t)nC * 32, TPB), TPB, 0, c.s>>>(out, in, c.lC.p, c.dcnt + K_C, c.lv[r].par.p,
-                                                                c.par_old.p, c.stC.p, epC, c.bits, c.rk2.p, c.rv2.p,
-                                                                c.dcnt + K_REC);
+  ChunkMap m = chunk_map(c, c.lC.p, c.dcnt + K_C, nC, out.len, in.len);
+  k_emit<WT><<<grid_for((int64_t)nC * 64, TPB, 152 * 16), TPB, 0, c.s>>>(out, in, m, c.lv[r].par.p, c.par_old.p,
+                                                                          c.stC.p, epC, c.bits, c.rk2.p, c.rv2.p,
+                                                                          c.dcnt + K_REC);
   CKL("k_emit");
 }
 
@@ -824,6 +839,7 @@ void aggregate(ldl_ctx& c, int r, int32_t epD, int32_t epC, int32_t epA_next, bo
   LevelState& L = c.lv[r];
   LevelState& N = c.lv[r + 1];
   // changed nodes
+  sub_begin(c);
   zero_cnt(c, K_C);
   const int32_t nD = rd_cnt(c, K_D);
   k_changed<<<grid_for(nD, TPB), TPB, 0, c.s>>>(c.lD.p, c.dcnt + K_D, L.par.p, c.par_old.p, c.stC.p, epC, c.lC.p,
@@ -835,6 +851,8 @@ void aggregate(ldl_ctx& c, int r, int32_t epD, int32_t epC, int32_t epA_next, bo
     if (r == 0) emit_records<int32_t>(c, r, adj_out0(c), adj_in0(c), nC, epC);
     else emit_records<int64_t>(c, r, adj_out(c, r), adj_in(c, r), nC, epC);
     const int64_t nrec = rd_cnt(c, K_REC);
+    sub_end(c, SU_AGG_EMIT);
+    sub_begin(c);
     sort_pairs(c.rk2, c.rv2, c.tk, c.tv, nrec, 2 * c.bits, c.P, c.s);
     c.rk.reserve(nrec + 1, c.s);
     c.rv.reserve(nrec + 1, c.s);
@@ -842,6 +860,8 @@ void aggregate(ldl_ctx& c, int r, int32_t epD, int32_t epC, int32_t epA_next, bo
     nr = reduce_by_key(c.rk2.p, c.rv2.p, nrec, c.rk.p, c.rsum.p, c.P, c.s);
     CK(cudaMemcpyAsync(c.rv.p, c.rsum.p, sizeof(int64_t) * (size_t)nr, cudaMemcpyDeviceToDevice, c.s));
     c.res.agg_records += nr;
+    sub_end(c, SU_AGG_SORT);
+    sub_begin(c);
     // node and children records
     c.ndx.reserve(2 * (int64_t)nC + 2, c.s);
     c.ndko.reserve(2 * (int64_t)nC + 2, c.s);
@@ -875,6 +895,8 @@ void aggregate(ldl_ctx& c, int r, int32_t epD, int32_t epC, int32_t epA_next, bo
       apply_level(c, r + 1, c.rk, c.rv, nr);
       csr_apply<int32_t>(L.children, c.crk.p, (const int64_t*)c.crv.p, ncr, c.bits, c.CS, c.P, c.s, c.d_sc);
     }
+    sub_end(c, SU_AGG_APPLY);
+    sub_begin(c);
     // propagate level r+1 changes up the current parent chain
     int64_t cur = nr;
     int32_t nnd = rd_cnt(c, K_NREC);
@@ -895,6 +917,8 @@ void aggregate(ldl_ctx& c, int r, int32_t epD, int32_t epC, int32_t epA_next, bo
         swap_buf(c.ndki, c.ndki2);
       }
     }
+    sub_end(c, SU_AGG_UP);
+    sub_begin(c);
     // existence: appear at r+1, emptied nodes cascade upwards
     int32_t epE = c.next_epoch();
     zero_cnt(c, K_E);
@@ -933,8 +957,9 @@ void aggregate(ldl_ctx& c, int r, int32_t epD, int32_t epC, int32_t epA_next, bo
       ie2 = ti;
     }
     if (rd_cnt(c, K_ERR)) ldl_throw(LDL_E_INVALID, "internal: new supernode already has a parent");
-  } else if (build) {
-    // nothing changed parent (cannot happen in the static run, which stops earlier)
+  } else {
+    sub_end(c, SU_AGG_EMIT);
+    sub_begin(c);
   }
   // relabel the level-(r+1) images of frontier and dissolved nodes
   const int32_t nUs = rd_cnt(c, K_USTAR);
@@ -964,6 +989,7 @@ void aggregate(ldl_ctx& c, int r, int32_t epD, int32_t epC, int32_t epA_next, bo
       CKL("k_nf_nodes");
     }
   }
+  sub_end(c, SU_AGG_EXIST);
 }
 
 void level_alloc(ldl_ctx& c, int r) {

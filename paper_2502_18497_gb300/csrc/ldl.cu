@@ -73,6 +73,19 @@ void stage_end(ldl_ctx& c, int stage) {
   c.stage_ms[stage] += ms;
 }
 
+void sub_begin(ldl_ctx& c) {
+  if (c.timing) CK(cudaEventRecord(c.ev2, c.s));
+}
+
+void sub_end(ldl_ctx& c, int stage) {
+  if (!c.timing) return;
+  CK(cudaEventRecord(c.ev3, c.s));
+  CK(cudaEventSynchronize(c.ev3));
+  float ms = 0;
+  CK(cudaEventElapsedTime(&ms, c.ev2, c.ev3));
+  c.stage_ms[stage] += ms;
+}
+
 static std::string g_create_err = "no error";
 
 // ---------------------------------------------------------------- numerator
@@ -117,7 +130,8 @@ static void free_all(ldl_ctx& c) {
   if (c.s) cudaStreamSynchronize(c.s);
   for (auto& L : c.lv) L.release();
   DBuf<int64_t>* b64[] = {&c.Kout, &c.Kin, &c.e, &c.cghi, &c.snapKo, &c.snapKi, &c.snapE, &c.binLoff, &c.binLsz,
-                          &c.gvals, &c.rsum, &c.rsum2, &c.ndko, &c.ndki, &c.ndko2, &c.ndki2};
+                          &c.gvals, &c.rsum, &c.rsum2, &c.ndko, &c.ndki, &c.ndko2, &c.ndki2,
+                          &c.chunk_cnt, &c.chunk_pre};
   for (auto* b : b64) b->release();
   DBuf<int32_t>* b32[] = {&c.stS, &c.stU, &c.stMv, &c.stB, &c.stM0, &c.stD, &c.stC, &c.stR, &c.stX, &c.stT,
                           &c.stE, &c.stCh, &c.lU, &c.lS, &c.lUstar, &c.lMv, &c.lM0, &c.lD, &c.lC, &c.lR,
@@ -137,7 +151,9 @@ static void free_all(ldl_ctx& c) {
   c.dcnt = nullptr;
   if (c.ev0) cudaEventDestroy(c.ev0);
   if (c.ev1) cudaEventDestroy(c.ev1);
-  c.ev0 = c.ev1 = nullptr;
+  if (c.ev2) cudaEventDestroy(c.ev2);
+  if (c.ev3) cudaEventDestroy(c.ev3);
+  c.ev0 = c.ev1 = c.ev2 = c.ev3 = nullptr;
   for (auto& ev : c.kev) {
     if (ev) cudaEventDestroy(ev);
     ev = nullptr;
@@ -313,8 +329,12 @@ static void apply_batch(ldl_ctx& c, const ldl_update* upd, int64_t count, int on
       if (r < T) {
         stage_begin(c);
         const int32_t epD = c.next_epoch(), epX = c.next_epoch();
+        sub_begin(c);
         dissolve(c, r, epD, epX, false);
+        sub_end(c, SU_REF_DISSOLVE);
+        sub_begin(c);
         refine_loop(c, r, c.prm.M, epD);
+        sub_end(c, SU_REF_LOOP);
         stage_end(c, ST_REFINE);
         stage_begin(c);
         const int32_t epC = c.next_epoch();
@@ -400,6 +420,8 @@ ldl_status ldl_create(const ldl_params* params, int64_t n, int64_t nnz, const in
     c->s = (cudaStream_t)p.cuda_stream;
     CK(cudaEventCreate(&c->ev0));
     CK(cudaEventCreate(&c->ev1));
+    CK(cudaEventCreate(&c->ev2));
+    CK(cudaEventCreate(&c->ev3));
     for (auto& ev : c->kev) CK(cudaEventCreate(&ev));
     c->lv.resize(p.L + 1);
     alloc_globals(*c);

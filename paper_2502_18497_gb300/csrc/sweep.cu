@@ -3,6 +3,7 @@
 // filter of Sec. III-E as deterministic parallel rounds, and the commit of an
 // accepted mini-batch with the additive repair of the community totals and
 // the exact modularity change dQ(B) (lines 10-11).
+#include "chunks.cuh"
 #include "kern.cuh"
 
 namespace {
@@ -16,24 +17,27 @@ constexpr int MID_DEG = 3072;
 // ---------------------------------------------------------------- expand
 // out = U plus every out- and in-neighbour of U (dedup by stamp).
 template <class WT>
-__global__ void k_expand(Adj<WT> out, Adj<WT> in, int directed, const int32_t* list, const int32_t* nlist,
-                         int32_t* stamp, int32_t ep, int32_t* olist, int32_t* nout) {
+__global__ void k_expand(Adj<WT> out, Adj<WT> in, ChunkMap m, int32_t* stamp, int32_t ep, int32_t* olist,
+                         int32_t* nout) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  const int32_t nl = *nlist;
-  for (int64_t t = warp; t < nl; t += nw) {
-    const int32_t v = list[t];
-    if (lane == 0) stamp_add(stamp, ep, v, olist, nout);
-    {
-      const int64_t o = out.off[v];
-      const int32_t l = out.len[v];
-      for (int32_t k = lane; k < l; k += 32) stamp_add(stamp, ep, out.col[o + k], olist, nout);
-    }
-    if (directed) {
-      const int64_t o = in.off[v];
-      const int32_t l = in.len[v];
-      for (int32_t k = lane; k < l; k += 32) stamp_add(stamp, ep, in.col[o + k], olist, nout);
+  const int64_t total = m.pre[m.n_hint];
+  for (int64_t c = warp; c < total; c += nw) {
+    const Chunk ch = chunk_of(m, c);
+    if (ch.first && lane == 0) stamp_add(stamp, ep, ch.v, olist, nout);
+    if (ch.row < 0) continue;
+    const Adj<WT>& A = ch.row ? in : out;
+    const int64_t o = A.off[ch.v];
+    for (int32_t base = ch.k0; base < ch.k1; base += 32) {
+      const int32_t k = base + lane;
+      bool want = false;
+      int32_t u = 0;
+      if (k < ch.k1) {
+        u = A.col[o + k];
+        want = stamp_claim(stamp, ep, u);
+      }
+      warp_append(want, u, olist, nout);
     }
   }
 }
@@ -218,7 +222,9 @@ __global__ void __launch_bounds__(TPB) k_sweep_block(SweepArgs<WT> A, const int3
     } else {
       V = (int64_t*)smem;
       K = (int32_t*)(smem + sizeof(int64_t) * HB);
-      H = HB;
+      const int64_t d = (int64_t)A.out.len[v] + (A.directed ? A.in.len[v] : 0);
+      H = 256;
+      while (H < 2 * d && H < HB) H <<= 1;
     }
     for (uint32_t k = threadIdx.x; k < H; k += TPB) {
       K[k] = -1;
@@ -409,19 +415,20 @@ __global__ void k_commit_K(int32_t nb, const int32_t* bv, const int32_t* bsrc, c
 // (from the moved tail's out-row, or from the moved head's in-row when the
 // tail did not move).
 template <class WT>
-__global__ void k_commit_e(Adj<WT> out, Adj<WT> in, int32_t nb, const int32_t* bv, const int32_t* bsrc,
-                           const int32_t* bdst, const int32_t* lab, const int32_t* oldlab, const int32_t* stB,
-                           int32_t epB, int64_t* e) {
+__global__ void k_commit_e(Adj<WT> out, Adj<WT> in, ChunkMap m, const int32_t* bsrc, const int32_t* bdst,
+                           const int32_t* lab, const int32_t* oldlab, const int32_t* stB, int32_t epB, int64_t* e) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t t = warp; t < nb; t += nw) {
-    const int32_t v = bv[t], a = bsrc[t], b = bdst[t];
+  const int64_t total = m.pre[m.n_hint];
+  for (int64_t c = warp; c < total; c += nw) {
+    const Chunk ch = chunk_of(m, c);
+    if (ch.row < 0) continue;
+    const int32_t a = bsrc[ch.idx], b = bdst[ch.idx];
     int64_t da = 0, db = 0;
-    {
-      const int64_t o = out.off[v];
-      const int32_t l = out.len[v];
-      for (int32_t k = lane; k < l; k += 32) {
+    if (ch.row == 0) {
+      const int64_t o = out.off[ch.v];
+      for (int32_t k = ch.k0 + lane; k < ch.k1; k += 32) {
         const int32_t u = out.col[o + k];
         const int64_t w = (int64_t)out.w[o + k];
         const bool mu = stB[u] == epB;
@@ -430,11 +437,9 @@ __global__ void k_commit_e(Adj<WT> out, Adj<WT> in, int32_t nb, const int32_t* b
         if (cold == a) da -= w;
         if (cnew == b) db += w;
       }
-    }
-    {
-      const int64_t o = in.off[v];
-      const int32_t l = in.len[v];
-      for (int32_t k = lane; k < l; k += 32) {
+    } else {
+      const int64_t o = in.off[ch.v];
+      for (int32_t k = ch.k0 + lane; k < ch.k1; k += 32) {
         const int32_t u = in.col[o + k];
         if (stB[u] == epB) continue;
         const int64_t w = (int64_t)in.w[o + k];
@@ -518,23 +523,28 @@ __global__ void k_commit_ref(int32_t nb, const int32_t* bv, const int32_t* bdst,
 // SPExpand: dissolved, still-singleton neighbours of moved nodes inside the
 // moved node's community.
 template <class WT>
-__global__ void k_spexpand(Adj<WT> out, Adj<WT> in, int directed, int32_t nb, const int32_t* bv,
-                           const int32_t* lab, const int32_t* par, const int32_t* cnt1, const int32_t* stD,
-                           int32_t epD, int32_t* stR, int32_t epR, int32_t* lR, int32_t* nR) {
+__global__ void k_spexpand(Adj<WT> out, Adj<WT> in, ChunkMap m, const int32_t* lab, const int32_t* par,
+                           const int32_t* cnt1, const int32_t* stD, int32_t epD, int32_t* stR, int32_t epR,
+                           int32_t* lR, int32_t* nR) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t t = warp; t < nb; t += nw) {
-    const int32_t v = bv[t];
-    const int32_t cv_ = lab[v];
-    for (int pass = 0; pass < (directed ? 2 : 1); ++pass) {
-      const Adj<WT>& A = pass ? in : out;
-      const int64_t o = A.off[v];
-      const int32_t l = A.len[v];
-      for (int32_t k = lane; k < l; k += 32) {
-        const int32_t u = A.col[o + k];
-        if (stD[u] == epD && lab[u] == cv_ && par[u] == u && cnt1[u] == 1) stamp_add(stR, epR, u, lR, nR);
+  const int64_t total = m.pre[m.n_hint];
+  for (int64_t c = warp; c < total; c += nw) {
+    const Chunk ch = chunk_of(m, c);
+    if (ch.row < 0) continue;
+    const Adj<WT>& A = ch.row ? in : out;
+    const int64_t o = A.off[ch.v];
+    const int32_t cv_ = lab[ch.v];
+    for (int32_t base = ch.k0; base < ch.k1; base += 32) {
+      const int32_t k = base + lane;
+      bool want = false;
+      int32_t u = 0;
+      if (k < ch.k1) {
+        u = A.col[o + k];
+        want = stD[u] == epD && lab[u] == cv_ && par[u] == u && cnt1[u] == 1 && stamp_claim(stR, epR, u);
       }
+      warp_append(want, u, lR, nR);
     }
   }
 }
@@ -542,15 +552,21 @@ __global__ void k_spexpand(Adj<WT> out, Adj<WT> in, int directed, int32_t nb, co
 }  // namespace
 
 // ================================================================== host side
+static int chunk_grid(int64_t n_hint) { return grid_for(n_hint * 64, TPB, 152 * 16); }
+
 void expand_set(ldl_ctx& c, int r, const int32_t* list, int idx_n, int32_t* stamp, int32_t ep, int32_t* olist,
                 int idx_out, int64_t n_hint) {
-  const int g = grid_for(n_hint * 32, TPB);
-  if (r == 0)
-    k_expand<int32_t><<<g, TPB, 0, c.s>>>(adj_out0(c), adj_in0(c), c.directed, list, c.dcnt + idx_n, stamp, ep,
-                                          olist, c.dcnt + idx_out);
-  else
-    k_expand<int64_t><<<g, TPB, 0, c.s>>>(adj_out(c, r), adj_in(c, r), c.directed, list, c.dcnt + idx_n, stamp,
-                                          ep, olist, c.dcnt + idx_out);
+  if (n_hint <= 0) return;
+  const int g = chunk_grid(n_hint);
+  if (r == 0) {
+    Adj<int32_t> o = adj_out0(c), i = adj_in0(c);
+    ChunkMap m = chunk_map(c, list, c.dcnt + idx_n, n_hint, o.len, c.directed ? i.len : nullptr);
+    k_expand<int32_t><<<g, TPB, 0, c.s>>>(o, i, m, stamp, ep, olist, c.dcnt + idx_out);
+  } else {
+    Adj<int64_t> o = adj_out(c, r), i = adj_in(c, r);
+    ChunkMap m = chunk_map(c, list, c.dcnt + idx_n, n_hint, o.len, c.directed ? i.len : nullptr);
+    k_expand<int64_t><<<g, TPB, 0, c.s>>>(o, i, m, stamp, ep, olist, c.dcnt + idx_out);
+  }
   CKL("k_expand");
 }
 
@@ -688,6 +704,7 @@ int32_t decouple(ldl_ctx& c, int32_t nc) {
       ++rounds;
     }
     if (rd_cnt(c, K_UNDEC) == 0) break;
+    c.res.decouple_rounds += 4;
     if (rounds > 4 * (int64_t)nc + 64) ldl_throw(LDL_E_INVALID, "internal: decoupling did not converge");
   }
   zero_cnt(c, K_B);
@@ -711,13 +728,16 @@ CommitOut commit_move(ldl_ctx& c, int r, int32_t nb, int32_t epB, int32_t epT, i
   k_commit_K<<<g, TPB, 0, c.s>>>(nb, c.bv.p, c.bsrc.p, c.bdst.p, L.kout.p, kin_of(c, r), c.Kout.p, Kin_of(c),
                                  c.directed);
   CKL("k_commit_K");
-  const int gw = grid_for((int64_t)nb * 32, TPB);
-  if (r == 0)
-    k_commit_e<int32_t><<<gw, TPB, 0, c.s>>>(adj_out0(c), adj_in0(c), nb, c.bv.p, c.bsrc.p, c.bdst.p, L.lab.p,
-                                             c.oldlab.p, c.stB.p, epB, c.e.p);
-  else
-    k_commit_e<int64_t><<<gw, TPB, 0, c.s>>>(adj_out(c, r), adj_in(c, r), nb, c.bv.p, c.bsrc.p, c.bdst.p, L.lab.p,
-                                             c.oldlab.p, c.stB.p, epB, c.e.p);
+  const int gw = chunk_grid(nb);
+  if (r == 0) {
+    Adj<int32_t> o = adj_out0(c), i = adj_in0(c);
+    ChunkMap m = chunk_map(c, c.bv.p, c.dcnt + K_B, nb, o.len, i.len);
+    k_commit_e<int32_t><<<gw, TPB, 0, c.s>>>(o, i, m, c.bsrc.p, c.bdst.p, L.lab.p, c.oldlab.p, c.stB.p, epB, c.e.p);
+  } else {
+    Adj<int64_t> o = adj_out(c, r), i = adj_in(c, r);
+    ChunkMap m = chunk_map(c, c.bv.p, c.dcnt + K_B, nb, o.len, i.len);
+    k_commit_e<int64_t><<<gw, TPB, 0, c.s>>>(o, i, m, c.bsrc.p, c.bdst.p, L.lab.p, c.oldlab.p, c.stB.p, epB, c.e.p);
+  }
   CKL("k_commit_e");
   CK(cudaMemsetAsync(&c.d_sc->dq, 0, sizeof(I128), c.s));
   CK(cudaMemsetAsync(&c.d_sc->dp, 0, sizeof(I128), c.s));
@@ -761,12 +781,17 @@ void commit_ref(ldl_ctx& c, int r, int32_t nb) {
 
 void spexpand(ldl_ctx& c, int r, int32_t nb, int32_t epD, int32_t epR, int32_t* lR, int idx_R) {
   LevelState& L = c.lv[r];
-  const int g = grid_for((int64_t)nb * 32, TPB);
-  if (r == 0)
-    k_spexpand<int32_t><<<g, TPB, 0, c.s>>>(adj_out0(c), adj_in0(c), c.directed, nb, c.bv.p, L.lab.p, L.par.p,
-                                            c.lv[r + 1].cnt.p, c.stD.p, epD, c.stR.p, epR, lR, c.dcnt + idx_R);
-  else
-    k_spexpand<int64_t><<<g, TPB, 0, c.s>>>(adj_out(c, r), adj_in(c, r), c.directed, nb, c.bv.p, L.lab.p, L.par.p,
-                                            c.lv[r + 1].cnt.p, c.stD.p, epD, c.stR.p, epR, lR, c.dcnt + idx_R);
+  const int g = chunk_grid(nb);
+  if (r == 0) {
+    Adj<int32_t> o = adj_out0(c), i = adj_in0(c);
+    ChunkMap m = chunk_map(c, c.bv.p, c.dcnt + K_B, nb, o.len, c.directed ? i.len : nullptr);
+    k_spexpand<int32_t><<<g, TPB, 0, c.s>>>(o, i, m, L.lab.p, L.par.p, c.lv[r + 1].cnt.p, c.stD.p, epD, c.stR.p,
+                                            epR, lR, c.dcnt + idx_R);
+  } else {
+    Adj<int64_t> o = adj_out(c, r), i = adj_in(c, r);
+    ChunkMap m = chunk_map(c, c.bv.p, c.dcnt + K_B, nb, o.len, c.directed ? i.len : nullptr);
+    k_spexpand<int64_t><<<g, TPB, 0, c.s>>>(o, i, m, L.lab.p, L.par.p, c.lv[r + 1].cnt.p, c.stD.p, epD, c.stR.p,
+                                            epR, lR, c.dcnt + idx_R);
+  }
   CKL("k_spexpand");
 }

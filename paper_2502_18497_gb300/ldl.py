@@ -22,7 +22,7 @@ INSERT, DELETE, REWEIGHT = 0, 1, 2
 STATUS_NAMES = {0: "OK", 1: "INVALID", 2: "RANGE", 3: "NO_EDGE", 4: "NEG_WEIGHT", 5: "NOMEM",
                 6: "CUDA", 7: "TIMEOUT", 8: "OVERFLOW"}
 STAGES = ["ingest", "repair", "expand", "bestmove", "decouple", "commit", "refine", "aggregate",
-          "pushdown"]
+          "pushdown", "agg.emit", "agg.sort", "agg.apply", "agg.up", "agg.exist", "ref.dissolve", "ref.loop"]
 
 
 class ldl_params(C.Structure):
@@ -36,7 +36,8 @@ class ldl_result(C.Structure):
                 ("n_changed", C.c_int64), ("levels", C.c_int32),
                 ("frontier_nodes", C.c_int64 * 8), ("edges_scanned", C.c_int64),
                 ("moves", C.c_int64), ("refine_moves", C.c_int64), ("rejected", C.c_int64),
-                ("rollbacks", C.c_int64), ("rounds", C.c_int64), ("agg_records", C.c_int64)]
+                ("rollbacks", C.c_int64), ("rounds", C.c_int64), ("agg_records", C.c_int64),
+                ("decouple_rounds", C.c_int64)]
 
 
 class LdlError(RuntimeError):
@@ -256,4 +257,4 @@ class LDL:
         return dict(n_changed=r.n_changed, levels=r.levels, frontier_nodes=list(r.frontier_nodes),
                     edges_scanned=r.edges_scanned, moves=r.moves, refine_moves=r.refine_moves,
                     rejected=r.rejected, rollbacks=r.rollbacks, rounds=r.rounds,
-                    agg_records=r.agg_records)
+                    agg_records=r.agg_records, decouple_rounds=r.decouple_rounds)
