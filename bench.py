@@ -277,10 +277,14 @@ def main():
     achieved = k["bytes"] / (k["ms"] / 1e3) / 1e9 if k["ms"] > 0 else 0.0
     sha = hashlib.sha256(open(os.path.join(ROOT, "paper_2502_18497_gb300", "csrc", "sweep.cu"), "rb").read()).hexdigest()
     traffic = NCU_TRAFFIC["bytes_per_launch"] if NCU_TRAFFIC["sha256"] == sha and NCU_TRAFFIC["kernel"] == dom else None
-    roofline = {"bound": "hbm", "kernel": f"k_{dom}", "achieved": achieved, "peak": peak, "unit": "GB/s",
+    names = {"sweep_warp": "k_sweep_warp", "sweep_block": "k_sweep_block",
+             "sweep_hub": "hub path (k_hub_acc + k_hub_eval)"}
+    roofline = {"bound": "hbm", "kernel": names.get(dom, dom), "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": peak_src, "traffic": traffic,
                 "launches": k["launches"], "ms_total": k["ms"], "algorithmic_bytes_per_launch":
-                    k["bytes"] / max(k["launches"], 1)}
+                    k["bytes"] / max(k["launches"], 1),
+                "all_sweep_groups": {n2: {"ms": round(v["ms"], 3), "GB/s": round(v["bytes"] / max(v["ms"], 1e-9) / 1e6, 1)}
+                                     for n2, v in ks.items()}}
 
     line = {"metric": "updates/s", "value": ups, "unit": "updates/s", "n_gpus": ws, "steps": K, "warmup": W,
             "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,

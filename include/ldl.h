@@ -101,6 +101,7 @@ typedef struct {
   int64_t edges_scanned;     /* adjacency entries read by BestMove / BestRef */
   int64_t moves, refine_moves, rejected, rollbacks, rounds, agg_records;
   int64_t decouple_rounds;   /* parallel resolution rounds of the decoupling filter */
+  int64_t host_syncs;        /* counter reads that waited for the device */
 } ldl_result;
 
 /*
@@ -190,8 +191,9 @@ int64_t ldl_launch_count(void);
 /*
  * Per-kernel statistics of the BestMove / BestRef sweep kernels, measured
  * with CUDA events on the context's stream while enabled (enabling resets
- * them).  out[8] = {warp-bin launches, ms, algorithmic bytes, entries,
- * block-bin launches, ms, algorithmic bytes, entries}.  Algorithmic bytes
+ * them).  out[12] = {launches, ms, algorithmic bytes, entries} for the warp
+ * bin (one warp per low-degree node), the block bin (one block per mid-degree
+ * node) and the hub path (hub rows spread over the GPU), in that order.  Algorithmic bytes
  * count, per adjacency entry, the neighbour id, its weight and its label
  * (refinement: also its parent); per swept node its offsets, lengths, label
  * and strengths; per evaluated (node, target) pair the target's totals.

@@ -82,6 +82,9 @@ struct ldl_ctx {
   DBuf<int64_t> ndko, ndki, ndko2, ndki2;
   DBuf<u64> crk, crv, fk;
   DBuf<int64_t> chunk_cnt, chunk_pre;
+  DBuf<int64_t> hub_ecnt, hub_epre, pb_hi;
+  DBuf<uint64_t> pb_lo;
+  DBuf<int32_t> pb_c;
   DBuf<ldl_update> upd;
   Prims P;
   CsrScratch CS;
@@ -95,7 +98,8 @@ struct ldl_ctx {
   // per-kernel statistics of the sweep kernels (enabled by ldl_set_kernel_stats)
   int kstats = 0;
   cudaEvent_t kev[4] = {nullptr, nullptr, nullptr, nullptr};
-  double ks_launch[2] = {0, 0}, ks_ms[2] = {0, 0}, ks_bytes[2] = {0, 0}, ks_entries[2] = {0, 0};
+  double ks_launch[3] = {0, 0, 0}, ks_ms[3] = {0, 0, 0}, ks_bytes[3] = {0, 0, 0}, ks_entries[3] = {0, 0, 0};
+  int64_t syncs = 0;  // host synchronisations in the current batch
   std::string err;
 
   int32_t next_epoch() { return ++epoch; }

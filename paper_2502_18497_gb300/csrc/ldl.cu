@@ -47,6 +47,7 @@ void dfree(void* p) {
 }
 
 int32_t rd_cnt(ldl_ctx& c, int idx) {
+  ++c.syncs;
   int32_t v = 0;
   CK(cudaMemcpyAsync(&v, c.dcnt + idx, sizeof(int32_t), cudaMemcpyDeviceToHost, c.s));
   CK(cudaStreamSynchronize(c.s));
@@ -118,8 +119,8 @@ static void alloc_globals(ldl_ctx& c) {
   c.snapKo.exact(2 * n);
   c.snapKi.exact(2 * n);
   c.snapE.exact(2 * n);
-  c.binLoff.exact(n);
-  c.binLsz.exact(n);
+  c.binLoff.exact(n + 1);
+  c.binLsz.exact(n + 1);
   c.d_sc = (DevScalars*)dalloc(sizeof(DevScalars));
   CK(cudaMemsetAsync(c.d_sc, 0, sizeof(DevScalars), c.s));
   c.dcnt = (int32_t*)dalloc(sizeof(int32_t) * K_COUNT);
@@ -131,7 +132,7 @@ static void free_all(ldl_ctx& c) {
   for (auto& L : c.lv) L.release();
   DBuf<int64_t>* b64[] = {&c.Kout, &c.Kin, &c.e, &c.cghi, &c.snapKo, &c.snapKi, &c.snapE, &c.binLoff, &c.binLsz,
                           &c.gvals, &c.rsum, &c.rsum2, &c.ndko, &c.ndki, &c.ndko2, &c.ndki2,
-                          &c.chunk_cnt, &c.chunk_pre};
+                          &c.chunk_cnt, &c.chunk_pre, &c.hub_ecnt, &c.hub_epre, &c.pb_hi};
   for (auto* b : b64) b->release();
   DBuf<int32_t>* b32[] = {&c.stS, &c.stU, &c.stMv, &c.stB, &c.stM0, &c.stD, &c.stC, &c.stR, &c.stX, &c.stT,
                           &c.stE, &c.stCh, &c.lU, &c.lS, &c.lUstar, &c.lMv, &c.lM0, &c.lD, &c.lC, &c.lR,
@@ -142,6 +143,8 @@ static void free_all(ldl_ctx& c) {
   DBuf<u64>* bu[] = {&c.rk, &c.rv, &c.tk, &c.tv, &c.rk2, &c.rv2, &c.crk, &c.crv, &c.fk};
   for (auto* b : bu) b->release();
   c.cglo.release();
+  c.pb_lo.release();
+  c.pb_c.release();
   c.upd.release();
   c.P.release();
   c.CS.release();
@@ -281,6 +284,7 @@ static void static_build(ldl_ctx& c) {
 // ---------------------------------------------------------------- batch update
 static void apply_batch(ldl_ctx& c, const ldl_update* upd, int64_t count, int on_device) {
   memset(&c.res, 0, sizeof(c.res));
+  c.syncs = 0;
   CK(cudaMemsetAsync(&c.d_sc->scanned, 0, sizeof(int64_t), c.s));
   const int T = c.T;
   int64_t dm = 0;
@@ -353,6 +357,7 @@ static void apply_batch(ldl_ctx& c, const ldl_update* upd, int64_t count, int on
     if ((qnum(c) - Qpass) * (i128)ainv < Qpass) break;
   }
   c.res.n_changed = changed_labels(c, epCh);
+  c.res.host_syncs = c.syncs;
   CK(cudaMemcpyAsync(&c.res.edges_scanned, &c.d_sc->scanned, sizeof(int64_t), cudaMemcpyDeviceToHost, c.s));
   CK(cudaStreamSynchronize(c.s));
 }
@@ -633,13 +638,13 @@ ldl_status ldl_copy_changed(const ldl_ctx* cc, int32_t* ids, int32_t* labels) {
 ldl_status ldl_set_kernel_stats(ldl_ctx* c, int32_t on) {
   if (!c) return LDL_E_INVALID;
   c->kstats = on ? 1 : 0;
-  for (int k = 0; k < 2; ++k) c->ks_launch[k] = c->ks_ms[k] = c->ks_bytes[k] = c->ks_entries[k] = 0;
+  for (int k = 0; k < 3; ++k) c->ks_launch[k] = c->ks_ms[k] = c->ks_bytes[k] = c->ks_entries[k] = 0;
   return LDL_OK;
 }
 
 ldl_status ldl_get_kernel_stats(const ldl_ctx* c, double* out) {
   if (!c || !out) return LDL_E_INVALID;
-  for (int k = 0; k < 2; ++k) {
+  for (int k = 0; k < 3; ++k) {
     out[4 * k + 0] = c->ks_launch[k];
     out[4 * k + 1] = c->ks_ms[k];
     out[4 * k + 2] = c->ks_bytes[k];

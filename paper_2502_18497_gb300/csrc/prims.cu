@@ -53,6 +53,27 @@ __global__ void k_scan_tile(const T* in, int64_t* out, int64_t n, int64_t* bsum)
   if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
 }
 
+// whole input in one tile: scan and total in one launch
+template <class T>
+__global__ void k_scan_one(const T* in, int64_t* out, int64_t n, int64_t* total) {
+  const int64_t base = (int64_t)threadIdx.x * SC_ITEMS;
+  int64_t loc[SC_ITEMS];
+  int64_t s = 0;
+  for (int k = 0; k < SC_ITEMS; ++k) {
+    int64_t i = base + k;
+    loc[k] = i < n ? (int64_t)in[i] : 0;
+    s += loc[k];
+  }
+  int64_t tot;
+  int64_t pre = block_excl_scan_i64(s, &tot);
+  for (int k = 0; k < SC_ITEMS; ++k) {
+    int64_t i = base + k;
+    if (i < n) out[i] = pre;
+    pre += loc[k];
+  }
+  if (threadIdx.x == 0 && total) *total = tot;
+}
+
 __global__ void k_scan_bsums(int64_t* bsum, int64_t nb, int64_t* total) {
   __shared__ int64_t carry;
   if (threadIdx.x == 0) carry = 0;
@@ -140,6 +161,73 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const u64* keys, cons
   }
 }
 
+// Whole sort in one block (n <= RS_TILE): every pass in shared memory.
+__global__ void __launch_bounds__(RS_THREADS) k_rs_small(u64* keys, u64* vals, int n, int bits) {
+  extern __shared__ u64 sm[];
+  u64* kb[2] = {sm, sm + RS_TILE};
+  u64* vb[2] = {sm + 2 * RS_TILE, sm + 3 * RS_TILE};
+  __shared__ int32_t hist[256];
+  __shared__ int64_t run[256];
+  __shared__ int32_t tot[256];
+  __shared__ int32_t wcnt[RS_THREADS / WARP][257];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  for (int i = tid; i < n; i += RS_THREADS) {
+    kb[0][i] = keys[i];
+    vb[0][i] = vals[i];
+  }
+  int cur = 0;
+  for (int shift = 0; shift < bits; shift += 8) {
+    for (int d = tid; d < 256; d += RS_THREADS) hist[d] = 0;
+    __syncthreads();
+    for (int i = tid; i < n; i += RS_THREADS) atomicAdd(&hist[(kb[cur][i] >> shift) & 255], 1);
+    __syncthreads();
+    if (tid == 0) {
+      int64_t acc = 0;
+      for (int d = 0; d < 256; ++d) {
+        run[d] = acc;
+        acc += hist[d];
+      }
+    }
+    __syncthreads();
+    for (int ch = 0; ch * RS_THREADS < n; ++ch) {
+      const int i = ch * RS_THREADS + tid;
+      const bool valid = i < n;
+      const u64 key = valid ? kb[cur][i] : 0;
+      const u64 val = valid ? vb[cur][i] : 0;
+      const int d = valid ? (int)((key >> shift) & 255) : 256;
+      for (int x = lane; x < 257; x += 32) wcnt[wid][x] = 0;
+      __syncwarp();
+      const unsigned peers = __match_any_sync(0xffffffffu, d);
+      const int rank = __popc(peers & ((1u << lane) - 1u));
+      if (rank == 0) wcnt[wid][d] = __popc(peers);
+      __syncthreads();
+      if (tid < 256) {
+        int acc = 0;
+        for (int w = 0; w < RS_THREADS / WARP; ++w) {
+          int cc = wcnt[w][tid];
+          wcnt[w][tid] = acc;
+          acc += cc;
+        }
+        tot[tid] = acc;
+      }
+      __syncthreads();
+      if (valid) {
+        const int64_t pos = run[d] + wcnt[wid][d] + rank;
+        kb[cur ^ 1][pos] = key;
+        vb[cur ^ 1][pos] = val;
+      }
+      __syncthreads();
+      if (tid < 256) run[tid] += tot[tid];
+      __syncthreads();
+    }
+    cur ^= 1;
+  }
+  for (int i = tid; i < n; i += RS_THREADS) {
+    keys[i] = kb[cur][i];
+    vals[i] = vb[cur][i];
+  }
+}
+
 // ---------------------------------------------------------------- reduce by key
 __global__ void k_heads(const u64* keys, int64_t n, int32_t* flag) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -176,6 +264,15 @@ int64_t scan_exclusive(const int64_t* in, int64_t* out, int64_t n, Prims& P, cud
   if (n <= 0) return 0;
   int64_t nb = (n + SC_TILE - 1) / SC_TILE;
   P.bsum.reserve(nb + 1, s);
+  if (nb == 1) {
+    k_scan_one<int64_t><<<1, SC_THREADS, 0, s>>>(in, out, n, P.bsum.p + 1);
+    CKL("k_scan_one");
+    if (!want_total) return -1;
+    int64_t tot = 0;
+    CK(cudaMemcpyAsync(&tot, P.bsum.p + 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return tot;
+  }
   k_scan_tile<int64_t><<<(unsigned)nb, SC_THREADS, 0, s>>>(in, out, n, P.bsum.p);
   CKL("k_scan_tile");
   k_scan_bsums<<<1, SC_THREADS, 0, s>>>(P.bsum.p, nb, P.bsum.p + nb);
@@ -193,6 +290,15 @@ int64_t scan_exclusive_i32(const int32_t* in, int64_t* out, int64_t n, Prims& P,
   if (n <= 0) return 0;
   int64_t nb = (n + SC_TILE - 1) / SC_TILE;
   P.bsum.reserve(nb + 1, s);
+  if (nb == 1) {
+    k_scan_one<int32_t><<<1, SC_THREADS, 0, s>>>(in, out, n, P.bsum.p + 1);
+    CKL("k_scan_one");
+    if (!want_total) return -1;
+    int64_t tot = 0;
+    CK(cudaMemcpyAsync(&tot, P.bsum.p + 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return tot;
+  }
   k_scan_tile<int32_t><<<(unsigned)nb, SC_THREADS, 0, s>>>(in, out, n, P.bsum.p);
   CKL("k_scan_tile32");
   k_scan_bsums<<<1, SC_THREADS, 0, s>>>(P.bsum.p, nb, P.bsum.p + nb);
@@ -208,6 +314,17 @@ int64_t scan_exclusive_i32(const int32_t* in, int64_t* out, int64_t n, Prims& P,
 
 void radix_sort_pairs(u64*& keys, u64*& vals, u64*& tk, u64*& tv, int64_t n, int bits, Prims& P, cudaStream_t s) {
   if (n <= 1 || bits <= 0) return;
+  if (n <= RS_TILE) {
+    static bool attr = false;
+    const int smem = 4 * RS_TILE * (int)sizeof(u64);
+    if (!attr) {
+      CK(cudaFuncSetAttribute(k_rs_small, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+      attr = true;
+    }
+    k_rs_small<<<1, RS_THREADS, smem, s>>>(keys, vals, (int)n, bits);
+    CKL("k_rs_small");
+    return;
+  }
   const int64_t nb = (n + RS_TILE - 1) / RS_TILE;
   P.hist.reserve(256 * nb + 1, s);
   P.hoff.reserve(256 * nb + 1, s);

@@ -12,7 +12,8 @@ constexpr int TPB = 256;
 constexpr int HW = 256;      // per-warp hash slots (small bin)
 constexpr int SMALL_DEG = 96;
 constexpr int HB = 8192;     // per-block hash slots (mid bin)
-constexpr int MID_DEG = 3072;
+constexpr int MID_DEG = 2048;
+constexpr int EVAL_CH = 4096;  // hub table slots evaluated per block
 
 // ---------------------------------------------------------------- expand
 // out = U plus every out- and in-neighbour of U (dedup by stamp).
@@ -289,7 +290,136 @@ __global__ void k_bin(Adj<WT> out, Adj<WT> in, int directed, const int32_t* list
       const int32_t p = atomicAdd(nlarge, 1);
       bl[p] = v;
       lsz[p] = sz;
-      loff[p] = (int64_t)atomicAdd((unsigned long long*)tabtop, (unsigned long long)sz);
+      (void)loff;
+      atomicAdd((unsigned long long*)tabtop, (unsigned long long)sz);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- hubs
+// Hub rows are spread over the whole GPU: one global hash table per hub,
+// filled by chunks of its rows, then evaluated in slot chunks whose partial
+// bests are reduced per hub.
+__global__ void k_hub_init(int32_t* K, int64_t* V, int64_t total) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    K[t] = -1;
+    V[t] = 0;
+  }
+}
+
+__global__ void k_eval_counts(const int64_t* lsz, int32_t nh, int64_t* ecnt) {
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i <= nh; i += gridDim.x * blockDim.x)
+    ecnt[i] = i < nh ? (lsz[i] + EVAL_CH - 1) / EVAL_CH : 0;
+}
+
+template <class WT, int MODE>
+__global__ void k_hub_acc(SweepArgs<WT> A, ChunkMap m, const int64_t* loff, const int64_t* lsz, int32_t* gK,
+                          int64_t* gV) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t total = m.pre[m.n_hint];
+  int64_t scanned = 0;
+  for (int64_t c = warp; c < total; c += nw) {
+    const Chunk ch = chunk_of(m, c);
+    if (ch.row < 0) continue;
+    const int32_t v = ch.v;
+    const int32_t cv_ = A.lab[v];
+    int32_t* K = gK + loff[ch.idx];
+    int64_t* V = gV + loff[ch.idx];
+    const uint32_t mask = (uint32_t)lsz[ch.idx] - 1;
+    const Adj<WT>& adj = ch.row ? A.in : A.out;
+    const int64_t o = adj.off[v];
+    for (int32_t k = ch.k0 + lane; k < ch.k1; k += 32) {
+      const int32_t u = adj.col[o + k];
+      if (u == v) continue;
+      if (MODE == 1 && A.lab[u] != cv_) continue;
+      const int32_t key = MODE == 0 ? A.lab[u] : A.par[u];
+      hash_add(K, V, mask, key, (int64_t)adj.w[o + k]);
+    }
+    if (lane == 0) scanned += ch.k1 - ch.k0;
+  }
+  if (lane == 0 && scanned) {
+    atomic_add_i64(A.scanned, scanned);
+    atomic_add_i64(&A.stats->sw_entries[2], scanned);
+  }
+}
+
+template <class WT, int MODE>
+__global__ void __launch_bounds__(TPB) k_hub_eval(SweepArgs<WT> A, const int32_t* hubs, int32_t nh,
+                                                  const int64_t* loff, const int64_t* lsz, const int64_t* epre,
+                                                  const int32_t* gK, const int64_t* gV, int64_t* pb_hi,
+                                                  uint64_t* pb_lo, int32_t* pb_c) {
+  __shared__ Best wb[TPB / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t mult = A.directed ? 1 : 2;
+  const int64_t total = epre[nh];
+  for (int64_t e = blockIdx.x; e < total; e += gridDim.x) {
+    int64_t lo = 0, hi = nh;
+    while (hi - lo > 1) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (epre[mid] <= e) lo = mid; else hi = mid;
+    }
+    const int64_t i = lo;
+    const int32_t v = hubs[i];
+    const int32_t* K = gK + loff[i];
+    const int64_t* V = gV + loff[i];
+    const uint32_t H = (uint32_t)lsz[i];
+    const int64_t s0 = (e - epre[i]) * EVAL_CH;
+    const int64_t s1 = min((int64_t)H, s0 + EVAL_CH);
+    const int32_t a = A.lab[v];
+    const int64_t wa = MODE == 0 ? hash_get(K, V, H - 1, a) : 0;
+    const int64_t ko = A.kout[v], ki = A.kin[v];
+    Best b{0, 0, 0};
+    int64_t pairs = 0;
+    for (int64_t k = s0 + threadIdx.x; k < s1; k += TPB) {
+      const int32_t key = K[k];
+      if (key < 0) continue;
+      if (MODE == 0 ? key == a : key == v) continue;
+      ++pairs;
+      const i128 g = gain_of<MODE>(key, V[k], wa, a, ko, ki, A.Tout, A.Tin, A.m, A.gn, A.gd, mult);
+      if (g > 0) {
+        Best c{g, key, 1};
+        if (best_better(c, b)) b = c;
+      }
+    }
+    b = warp_best(b);
+    pairs = warp_sum_i64(pairs);
+    if (lane == 0) {
+      wb[wid] = b;
+      if (pairs) atomic_add_i64(&A.stats->sw_pairs[2], pairs);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      Best r = wb[0];
+      for (int w = 1; w < TPB / 32; ++w)
+        if (best_better(wb[w], r)) r = wb[w];
+      pb_hi[e] = r.have ? (int64_t)(r.g >> 64) : 0;
+      pb_lo[e] = r.have ? (uint64_t)r.g : 0;
+      pb_c[e] = r.have ? r.c : -1;
+    }
+    __syncthreads();
+  }
+}
+
+template <class WT, int MODE>
+__global__ void k_hub_final(SweepArgs<WT> A, const int32_t* hubs, int32_t nh, const int64_t* epre,
+                            const int64_t* pb_hi, const uint64_t* pb_lo, const int32_t* pb_c) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = warp; i < nh; i += nw) {
+    Best b{0, 0, 0};
+    for (int64_t e = epre[i] + lane; e < epre[i + 1]; e += 32) {
+      if (pb_c[e] < 0) continue;
+      Best c{i128_of(pb_hi[e], pb_lo[e]), pb_c[e], 1};
+      if (best_better(c, b)) b = c;
+    }
+    b = warp_best(b);
+    if (lane == 0) {
+      const int32_t v = hubs[i];
+      atomic_add_i64(&A.stats->sw_nodes[2], 1);
+      if (b.have) emit_cand(A, v, MODE == 0 ? A.lab[v] : v, b);
     }
   }
 }
@@ -612,7 +742,7 @@ static int32_t sweep_t(ldl_ctx& c, int r, Adj<WT> out, Adj<WT> in, const int32_t
   A.scanned = &c.d_sc->scanned;
   A.stats = c.d_sc;
   if (c.kstats) {
-    CK(cudaMemsetAsync(c.d_sc->sw_entries, 0, sizeof(int64_t) * 6, c.s));
+    CK(cudaMemsetAsync(c.d_sc->sw_entries, 0, sizeof(int64_t) * 9, c.s));
   }
   zero_cnt(c, K_CAND);
   zero_cnt(c, K_SMALL);
@@ -641,33 +771,54 @@ static int32_t sweep_t(ldl_ctx& c, int r, Adj<WT> out, Adj<WT> in, const int32_t
                                                                              nullptr, nullptr, nullptr);
     CKL("k_sweep_block(mid)");
   }
+  if (c.kstats) CK(cudaEventRecord(c.kev[2], c.s));
   if (counts[2] > 0) {
+    const int32_t nh = counts[2];
     c.gkeys.reserve(tab, c.s);
     c.gvals.reserve(tab, c.s);
-    k_sweep_block<WT, MODE><<<grid_for(counts[2], 1, 152 * 4), TPB, 0, c.s>>>(
-        A, c.binL.p, c.dcnt + K_LARGE, c.binLoff.p, c.binLsz.p, c.gkeys.p, c.gvals.p);
-    CKL("k_sweep_block(hub)");
+    // table offsets and evaluation chunks per hub, in list order
+    CK(cudaMemsetAsync(c.binLsz.p + nh, 0, sizeof(int64_t), c.s));
+    scan_exclusive(c.binLsz.p, c.binLoff.p, nh + 1, c.P, c.s, false);
+    c.hub_ecnt.reserve(nh + 2, c.s);
+    c.hub_epre.reserve(nh + 2, c.s);
+    k_eval_counts<<<grid_for(nh + 1, TPB), TPB, 0, c.s>>>(c.binLsz.p, nh, c.hub_ecnt.p);
+    CKL("k_eval_counts");
+    scan_exclusive(c.hub_ecnt.p, c.hub_epre.p, nh + 1, c.P, c.s, false);
+    const int64_t ech = tab / EVAL_CH + nh + 1;
+    c.pb_hi.reserve(ech, c.s);
+    c.pb_lo.reserve(ech, c.s);
+    c.pb_c.reserve(ech, c.s);
+    k_hub_init<<<grid_for(tab, TPB), TPB, 0, c.s>>>(c.gkeys.p, c.gvals.p, tab);
+    CKL("k_hub_init");
+    ChunkMap m = chunk_map(c, c.binL.p, c.dcnt + K_LARGE, nh, out.len, c.directed ? in.len : nullptr);
+    k_hub_acc<WT, MODE><<<grid_for((int64_t)nh * 2048, TPB, 152 * 16), TPB, 0, c.s>>>(A, m, c.binLoff.p, c.binLsz.p,
+                                                                                      c.gkeys.p, c.gvals.p);
+    CKL("k_hub_acc");
+    k_hub_eval<WT, MODE><<<grid_for(ech, 1, 152 * 8), TPB, 0, c.s>>>(A, c.binL.p, nh, c.binLoff.p, c.binLsz.p,
+                                                                    c.hub_epre.p, c.gkeys.p, c.gvals.p, c.pb_hi.p,
+                                                                    c.pb_lo.p, c.pb_c.p);
+    CKL("k_hub_eval");
+    k_hub_final<WT, MODE><<<grid_for((int64_t)nh * 32, TPB), TPB, 0, c.s>>>(A, c.binL.p, nh, c.hub_epre.p, c.pb_hi.p,
+                                                                           c.pb_lo.p, c.pb_c.p);
+    CKL("k_hub_final");
   }
   if (c.kstats) {
-    CK(cudaEventRecord(c.kev[2], c.s));
-    CK(cudaEventSynchronize(c.kev[2]));
-    float ms0 = 0, ms1 = 0;
-    CK(cudaEventElapsedTime(&ms0, c.kev[0], c.kev[1]));
-    CK(cudaEventElapsedTime(&ms1, c.kev[1], c.kev[2]));
+    CK(cudaEventRecord(c.kev[3], c.s));
+    CK(cudaEventSynchronize(c.kev[3]));
+    float ms[3] = {0, 0, 0};
+    for (int k = 0; k < 3; ++k) CK(cudaEventElapsedTime(&ms[k], c.kev[k], c.kev[k + 1]));
     DevScalars h;
     CK(cudaMemcpy(&h, c.d_sc, sizeof(DevScalars), cudaMemcpyDeviceToHost));
     // algorithmic bytes: per entry the neighbour id, its weight and its
     // label (refine: also its parent); per node offsets, lengths, label and
-    // strengths; per evaluated pair the target's two totals; per candidate
-    // the 28-byte tuple
+    // strengths; per evaluated pair the target's two totals
     const double per_entry = 4.0 + sizeof(WT) + 4.0 + (MODE == 1 ? 4.0 : 0.0);
     const double per_node = (8.0 + 4.0) * (c.directed ? 2 : 1) + 4.0 + 16.0 + 4.0;
     const double per_pair = c.directed ? 16.0 : 8.0;
-    const int kinds[2] = {counts[0] > 0, counts[1] + counts[2] > 0};
-    const double ms[2] = {ms0, ms1};
-    for (int k = 0; k < 2; ++k) {
-      if (!kinds[k]) continue;
-      c.ks_launch[k] += (k == 0) ? 1 : (counts[1] > 0) + (counts[2] > 0);
+    const int launches[3] = {counts[0] > 0, counts[1] > 0, counts[2] > 0 ? 4 : 0};
+    for (int k = 0; k < 3; ++k) {
+      if (!launches[k]) continue;
+      c.ks_launch[k] += launches[k];
       c.ks_ms[k] += ms[k];
       c.ks_entries[k] += (double)h.sw_entries[k];
       c.ks_bytes[k] += per_entry * (double)h.sw_entries[k] + per_node * (double)h.sw_nodes[k] +

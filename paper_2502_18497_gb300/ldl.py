@@ -37,7 +37,7 @@ class ldl_result(C.Structure):
                 ("frontier_nodes", C.c_int64 * 8), ("edges_scanned", C.c_int64),
                 ("moves", C.c_int64), ("refine_moves", C.c_int64), ("rejected", C.c_int64),
                 ("rollbacks", C.c_int64), ("rounds", C.c_int64), ("agg_records", C.c_int64),
-                ("decouple_rounds", C.c_int64)]
+                ("decouple_rounds", C.c_int64), ("host_syncs", C.c_int64)]
 
 
 class LdlError(RuntimeError):
@@ -245,10 +245,10 @@ class LDL:
         self._check(load().ldl_set_kernel_stats(self._h, int(on)))
 
     def kernel_stats(self) -> dict:
-        t = np.zeros(8, np.float64)
+        t = np.zeros(12, np.float64)
         self._check(load().ldl_get_kernel_stats(self._h, _ptr(t)))
         out = {}
-        for k, name in enumerate(("sweep_warp", "sweep_block")):
+        for k, name in enumerate(("sweep_warp", "sweep_block", "sweep_hub")):
             out[name] = dict(launches=t[4 * k], ms=t[4 * k + 1], bytes=t[4 * k + 2], entries=t[4 * k + 3])
         return out
 
@@ -257,4 +257,5 @@ class LDL:
         return dict(n_changed=r.n_changed, levels=r.levels, frontier_nodes=list(r.frontier_nodes),
                     edges_scanned=r.edges_scanned, moves=r.moves, refine_moves=r.refine_moves,
                     rejected=r.rejected, rollbacks=r.rollbacks, rounds=r.rounds,
-                    agg_records=r.agg_records, decouple_rounds=r.decouple_rounds)
+                    agg_records=r.agg_records, decouple_rounds=r.decouple_rounds,
+                    host_syncs=r.host_syncs)
