@@ -185,6 +185,23 @@ ldl_status ldl_set_timing(ldl_ctx* ctx, int32_t on);
  * arrays of length n_changed (labels may be NULL). */
 ldl_status ldl_copy_changed(const ldl_ctx* ctx, int32_t* ids, int32_t* labels);
 
+/*
+ * Same result as ldl_copy_changed, without any device allocation, for callers
+ * that cannot allocate device memory while they run (a serving loop that
+ * reserved its memory at start-up, a process whose device memory is held by
+ * another framework's caching allocator, a real-time path that forbids
+ * allocator calls).  The paper has no counterpart; this is an interface
+ * convenience.  The labels are gathered into a static device array of
+ * 2^20 int32 (4 MiB per device, held until the process exits); a batch with
+ * more than 2^20 changed vertices is rejected with LDL_E_INVALID (use
+ * ldl_copy_changed).  The first call on a device looks up the array's device
+ * address, so make that first call before any stream capture.  All calls share
+ * the array: calls whose GPU work overlaps (different streams or contexts at
+ * the same time) race and must be serialised by the caller.  ids and labels
+ * are host arrays of length n_changed.
+ */
+ldl_status ldl_copy_changed_noalloc(const ldl_ctx* ctx, int32_t* ids, int32_t* labels);
+
 /* Number of CUDA kernels this library has launched in this process. */
 int64_t ldl_launch_count(void);
 

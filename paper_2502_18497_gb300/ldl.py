@@ -77,6 +77,7 @@ def load(path: Optional[str] = None):
         "ldl_set_timing": (I32, [P, I32]),
         "ldl_debug_fail_alloc_after": (None, [I64]),
         "ldl_copy_changed": (I32, [P, P, P]),
+        "ldl_copy_changed_noalloc": (I32, [P, P, P]),
         "ldl_launch_count": (I64, []),
         "ldl_set_kernel_stats": (I32, [P, I32]),
         "ldl_get_kernel_stats": (I32, [P, P]),
@@ -94,7 +95,7 @@ def exported_symbols():
     return ["ldl_default_params", "ldl_create", "ldl_apply_batch", "ldl_modularity",
             "ldl_modularity_num", "ldl_destroy", "ldl_last_error", "ldl_levels", "ldl_get_level",
             "ldl_level_nnz", "ldl_get_adjacency", "ldl_get_communities", "ldl_stage_times",
-            "ldl_set_timing", "ldl_debug_fail_alloc_after", "ldl_copy_changed", "ldl_launch_count",
+            "ldl_set_timing", "ldl_debug_fail_alloc_after", "ldl_copy_changed", "ldl_copy_changed_noalloc", "ldl_launch_count",
             "ldl_set_kernel_stats", "ldl_get_kernel_stats"]
 
 
@@ -239,6 +240,14 @@ class LDL:
         ids = np.zeros(k, np.int32)
         lab = np.zeros(k, np.int32)
         self._check(load().ldl_copy_changed(self._h, _ptr(ids), _ptr(lab)))
+        return ids, lab
+
+    def changed_noalloc(self):
+        """As changed(), through the allocation-free entry point."""
+        k = int(self.last.n_changed)
+        ids = np.zeros(k, np.int32)
+        lab = np.zeros(k, np.int32)
+        self._check(load().ldl_copy_changed_noalloc(self._h, _ptr(ids), _ptr(lab)))
         return ids, lab
 
     def set_kernel_stats(self, on: bool = True):
