@@ -37,7 +37,7 @@ struct LevelState {
 // Device counters (indices into ldl_ctx::dcnt).
 enum {
   K_U = 0, K_S, K_USTAR, K_MV, K_M0, K_D, K_C, K_R, K_R2, K_X, K_T, K_E, K_E2, K_CH, K_CAND, K_B,
-  K_UNDEC, K_SMALL, K_MID, K_LARGE, K_REC, K_CREC, K_NREC, K_ERR, K_TMP, K_TMP2, K_CHG,
+  K_UNDEC, K_SMALL, K_MID, K_LARGE, K_REC, K_CREC, K_NREC, K_ERR, K_TMP, K_TMP2, K_CHG, K_MID2,
   K_A0 = 32,  // K_A0 + r: |A^r|
   K_COUNT = 48
 };
@@ -71,7 +71,7 @@ struct ldl_ctx {
   DBuf<int32_t> oldlab, par_old, lab_before;
   DBuf<int64_t> snapKo, snapKi, snapE;
   // sweep binning
-  DBuf<int32_t> binS, binM, binL;
+  DBuf<int32_t> binS, binM, binM2, binL;
   DBuf<int64_t> binLoff, binLsz;
   DBuf<int32_t> gkeys;
   DBuf<int64_t> gvals;

@@ -108,7 +108,7 @@ static void alloc_globals(ldl_ctx& c) {
   }
   DBuf<int32_t>* ls[] = {&c.lU, &c.lS, &c.lUstar, &c.lMv, &c.lM0, &c.lD, &c.lC, &c.lR, &c.lR2, &c.lX, &c.lT,
                          &c.lE, &c.lE2, &c.lCh, &c.lChg, &c.lTmp, &c.cv, &c.csrc, &c.cdst, &c.cst, &c.bv,
-                         &c.bsrc, &c.bdst, &c.oldlab, &c.par_old, &c.lab_before, &c.binS, &c.binM, &c.binL};
+                         &c.bsrc, &c.bdst, &c.oldlab, &c.par_old, &c.lab_before, &c.binS, &c.binM, &c.binM2, &c.binL};
   for (auto* b : ls) b->exact(n);
   c.best.exact(n);
   CK(cudaMemsetAsync(c.best.p, 0xff, sizeof(int32_t) * (size_t)n, c.s));
@@ -138,7 +138,7 @@ static void free_all(ldl_ctx& c) {
                           &c.stE, &c.stCh, &c.lU, &c.lS, &c.lUstar, &c.lMv, &c.lM0, &c.lD, &c.lC, &c.lR,
                           &c.lR2, &c.lX, &c.lT, &c.lE, &c.lE2, &c.lCh, &c.lChg, &c.lTmp, &c.cv, &c.csrc,
                           &c.cdst, &c.cst, &c.bv, &c.bsrc, &c.bdst, &c.best, &c.role, &c.oldlab, &c.par_old,
-                          &c.lab_before, &c.binS, &c.binM, &c.binL, &c.gkeys, &c.ndx, &c.ndx2};
+                          &c.lab_before, &c.binS, &c.binM, &c.binM2, &c.binL, &c.gkeys, &c.ndx, &c.ndx2};
   for (auto* b : b32) b->release();
   DBuf<u64>* bu[] = {&c.rk, &c.rv, &c.tk, &c.tv, &c.rk2, &c.rv2, &c.crk, &c.crv, &c.fk};
   for (auto* b : bu) b->release();

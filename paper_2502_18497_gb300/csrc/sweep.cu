@@ -11,7 +11,8 @@ namespace {
 constexpr int TPB = 256;
 constexpr int HW = 256;      // per-warp hash slots (small bin)
 constexpr int SMALL_DEG = 96;
-constexpr int HB = 8192;     // per-block hash slots (mid bin)
+constexpr int HB = 4096;     // per-block hash slots (upper mid bin)
+constexpr int MID1_DEG = 384;  // lower mid bin: 128 threads, 1024 slots
 constexpr int MID_DEG = 2048;
 constexpr int EVAL_CH = 4096;  // hub table slots evaluated per block
 
@@ -160,21 +161,24 @@ __global__ void __launch_bounds__(TPB) k_sweep_warp(SweepArgs<WT> A, const int32
   int64_t scanned = 0, pairs = 0, nodes = 0;
   for (int64_t t = warp; t < nl; t += nw) {
     const int32_t v = list[t];
-    for (int k = lane; k < HW; k += 32) {
+    const int32_t deg = A.out.len[v] + (A.directed ? A.in.len[v] : 0);
+    int H = 32;
+    while (H < 2 * deg && H < HW) H <<= 1;
+    for (int k = lane; k < H; k += 32) {
       K[k] = -1;
       V[k] = 0;
     }
     __syncwarp();
     const int32_t a = A.lab[v];
-    accumulate<WT, MODE>(A, A.out, v, a, K, V, HW - 1, lane, 32);
-    if (A.directed) accumulate<WT, MODE>(A, A.in, v, a, K, V, HW - 1, lane, 32);
-    if (lane == 0) scanned += A.out.len[v] + (A.directed ? A.in.len[v] : 0);
+    accumulate<WT, MODE>(A, A.out, v, a, K, V, H - 1, lane, 32);
+    if (A.directed) accumulate<WT, MODE>(A, A.in, v, a, K, V, H - 1, lane, 32);
+    if (lane == 0) scanned += deg;
     __syncwarp();
-    const int64_t wa = MODE == 0 ? hash_get(K, V, HW - 1, a) : 0;
+    const int64_t wa = MODE == 0 ? hash_get(K, V, H - 1, a) : 0;
     const int64_t ko = A.kout[v], ki = A.kin[v];
     Best b{0, 0, 0};
     if (lane == 0) ++nodes;
-    for (int k = lane; k < HW; k += 32) {
+    for (int k = lane; k < H; k += 32) {
       const int32_t key = K[k];
       if (key < 0) continue;
       if (MODE == 0 ? key == a : key == v) continue;
@@ -202,45 +206,34 @@ __global__ void __launch_bounds__(TPB) k_sweep_warp(SweepArgs<WT> A, const int32
 
 // one block per node; the hash lives in dynamic shared memory (mid degrees)
 // or in a global-memory slice (hubs, table != nullptr)
-template <class WT, int MODE>
-__global__ void __launch_bounds__(TPB) k_sweep_block(SweepArgs<WT> A, const int32_t* list, const int32_t* nlist,
-                                                     const int64_t* toff, const int64_t* tsz, int32_t* gK,
-                                                     int64_t* gV) {
+template <class WT, int MODE, int NT, int HMAX>
+__global__ void __launch_bounds__(NT) k_sweep_block(SweepArgs<WT> A, const int32_t* list, const int32_t* nlist) {
   extern __shared__ unsigned char smem[];
-  __shared__ Best wb[TPB / 32];
+  __shared__ Best wb[NT / 32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int32_t nl = *nlist;
   const int64_t mult = A.directed ? 1 : 2;
   for (int64_t t = blockIdx.x; t < nl; t += gridDim.x) {
     const int32_t v = list[t];
-    int32_t* K;
-    int64_t* V;
-    uint32_t H;
-    if (gK) {
-      K = gK + toff[t];
-      V = gV + toff[t];
-      H = (uint32_t)tsz[t];
-    } else {
-      V = (int64_t*)smem;
-      K = (int32_t*)(smem + sizeof(int64_t) * HB);
-      const int64_t d = (int64_t)A.out.len[v] + (A.directed ? A.in.len[v] : 0);
-      H = 256;
-      while (H < 2 * d && H < HB) H <<= 1;
-    }
-    for (uint32_t k = threadIdx.x; k < H; k += TPB) {
+    int64_t* V = (int64_t*)smem;
+    int32_t* K = (int32_t*)(smem + sizeof(int64_t) * HMAX);
+    const int64_t d = (int64_t)A.out.len[v] + (A.directed ? A.in.len[v] : 0);
+    uint32_t H = 256;
+    while (H < 2 * d && H < HMAX) H <<= 1;
+    for (uint32_t k = threadIdx.x; k < H; k += NT) {
       K[k] = -1;
       V[k] = 0;
     }
     __syncthreads();
     const int32_t a = A.lab[v];
-    accumulate<WT, MODE>(A, A.out, v, a, K, V, H - 1, threadIdx.x, TPB);
-    if (A.directed) accumulate<WT, MODE>(A, A.in, v, a, K, V, H - 1, threadIdx.x, TPB);
+    accumulate<WT, MODE>(A, A.out, v, a, K, V, H - 1, threadIdx.x, NT);
+    if (A.directed) accumulate<WT, MODE>(A, A.in, v, a, K, V, H - 1, threadIdx.x, NT);
     __syncthreads();
     const int64_t wa = MODE == 0 ? hash_get(K, V, H - 1, a) : 0;
     const int64_t ko = A.kout[v], ki = A.kin[v];
     Best b{0, 0, 0};
     int64_t pairs = 0;
-    for (uint32_t k = threadIdx.x; k < H; k += TPB) {
+    for (uint32_t k = threadIdx.x; k < H; k += NT) {
       const int32_t key = K[k];
       if (key < 0) continue;
       if (MODE == 0 ? key == a : key == v) continue;
@@ -260,7 +253,7 @@ __global__ void __launch_bounds__(TPB) k_sweep_block(SweepArgs<WT> A, const int3
     __syncthreads();
     if (threadIdx.x == 0) {
       Best r = wb[0];
-      for (int w = 1; w < TPB / 32; ++w)
+      for (int w = 1; w < NT / 32; ++w)
         if (best_better(wb[w], r)) r = wb[w];
       if (r.have) emit_cand(A, v, MODE == 0 ? a : v, r);
       const int64_t ent = (int64_t)A.out.len[v] + (A.directed ? A.in.len[v] : 0);
@@ -274,16 +267,18 @@ __global__ void __launch_bounds__(TPB) k_sweep_block(SweepArgs<WT> A, const int3
 
 template <class WT>
 __global__ void k_bin(Adj<WT> out, Adj<WT> in, int directed, const int32_t* list, const int32_t* nlist,
-                      int32_t* bs, int32_t* ns, int32_t* bm, int32_t* nm, int32_t* bl, int32_t* nlarge,
-                      int64_t* loff, int64_t* lsz, int64_t* tabtop) {
+                      int32_t* bs, int32_t* ns, int32_t* bm, int32_t* nm, int32_t* bm2, int32_t* nm2,
+                      int32_t* bl, int32_t* nlarge, int64_t* loff, int64_t* lsz, int64_t* tabtop) {
   const int32_t nl = *nlist;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nl; t += (int64_t)gridDim.x * blockDim.x) {
     const int32_t v = list[t];
     const int64_t d = (int64_t)out.len[v] + (directed ? in.len[v] : 0);
     if (d <= SMALL_DEG) {
       bs[atomicAdd(ns, 1)] = v;
-    } else if (d <= MID_DEG) {
+    } else if (d <= MID1_DEG) {
       bm[atomicAdd(nm, 1)] = v;
+    } else if (d <= MID_DEG) {
+      bm2[atomicAdd(nm2, 1)] = v;
     } else {
       int64_t sz = 1;
       while (sz < 2 * d) sz <<= 1;
@@ -749,13 +744,16 @@ static int32_t sweep_t(ldl_ctx& c, int r, Adj<WT> out, Adj<WT> in, const int32_t
   zero_cnt(c, K_MID);
   zero_cnt(c, K_LARGE);
   CK(cudaMemsetAsync(&c.d_sc->need, 0, sizeof(int64_t), c.s));
+  zero_cnt(c, K_MID2);
   k_bin<WT><<<grid_for(n_hint, TPB), TPB, 0, c.s>>>(out, in, c.directed, list, c.dcnt + idx_n, c.binS.p,
-                                                     c.dcnt + K_SMALL, c.binM.p, c.dcnt + K_MID, c.binL.p,
-                                                     c.dcnt + K_LARGE, c.binLoff.p, c.binLsz.p, &c.d_sc->need);
+                                                     c.dcnt + K_SMALL, c.binM.p, c.dcnt + K_MID, c.binM2.p,
+                                                     c.dcnt + K_MID2, c.binL.p, c.dcnt + K_LARGE, c.binLoff.p,
+                                                     c.binLsz.p, &c.d_sc->need);
   CKL("k_bin");
-  int32_t counts[3];
+  int32_t counts[3], cm2 = 0;
   int64_t tab = 0;
   CK(cudaMemcpyAsync(counts, c.dcnt + K_SMALL, sizeof(int32_t) * 3, cudaMemcpyDeviceToHost, c.s));
+  CK(cudaMemcpyAsync(&cm2, c.dcnt + K_MID2, sizeof(int32_t), cudaMemcpyDeviceToHost, c.s));
   CK(cudaMemcpyAsync(&tab, &c.d_sc->need, sizeof(int64_t), cudaMemcpyDeviceToHost, c.s));
   CK(cudaStreamSynchronize(c.s));
   if (c.kstats) CK(cudaEventRecord(c.kev[0], c.s));
@@ -765,11 +763,20 @@ static int32_t sweep_t(ldl_ctx& c, int r, Adj<WT> out, Adj<WT> in, const int32_t
   }
   if (c.kstats) CK(cudaEventRecord(c.kev[1], c.s));
   if (counts[1] > 0) {
+    const size_t sm = (sizeof(int64_t) + sizeof(int32_t)) * 1024;
+    k_sweep_block<WT, MODE, 128, 1024><<<grid_for(counts[1], 1, 152 * 16), 128, sm, c.s>>>(A, c.binM.p,
+                                                                                         c.dcnt + K_MID);
+    CKL("k_sweep_block(mid1)");
+  }
+  if (cm2 > 0) {
     const size_t sm = (sizeof(int64_t) + sizeof(int32_t)) * HB;
-    CK(cudaFuncSetAttribute(k_sweep_block<WT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    k_sweep_block<WT, MODE><<<grid_for(counts[1], 1, 152 * 8), TPB, sm, c.s>>>(A, c.binM.p, c.dcnt + K_MID, nullptr,
-                                                                             nullptr, nullptr, nullptr);
-    CKL("k_sweep_block(mid)");
+    static bool attr = false;
+    if (!attr) {
+      CK(cudaFuncSetAttribute(k_sweep_block<WT, MODE, 256, HB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+      attr = true;
+    }
+    k_sweep_block<WT, MODE, 256, HB><<<grid_for(cm2, 1, 152 * 4), 256, sm, c.s>>>(A, c.binM2.p, c.dcnt + K_MID2);
+    CKL("k_sweep_block(mid2)");
   }
   if (c.kstats) CK(cudaEventRecord(c.kev[2], c.s));
   if (counts[2] > 0) {
@@ -815,7 +822,7 @@ static int32_t sweep_t(ldl_ctx& c, int r, Adj<WT> out, Adj<WT> in, const int32_t
     const double per_entry = 4.0 + sizeof(WT) + 4.0 + (MODE == 1 ? 4.0 : 0.0);
     const double per_node = (8.0 + 4.0) * (c.directed ? 2 : 1) + 4.0 + 16.0 + 4.0;
     const double per_pair = c.directed ? 16.0 : 8.0;
-    const int launches[3] = {counts[0] > 0, counts[1] > 0, counts[2] > 0 ? 4 : 0};
+    const int launches[3] = {counts[0] > 0, (counts[1] > 0) + (cm2 > 0), counts[2] > 0 ? 4 : 0};
     for (int k = 0; k < 3; ++k) {
       if (!launches[k]) continue;
       c.ks_launch[k] += launches[k];
