@@ -170,6 +170,124 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_batched(args):
+    """Batched form: many independent graphs, one batch each per step.
+    Reports updates/s of the concurrent multi-stream executor next to the
+    plain form (the same contexts updated one after another)."""
+    import torch
+    from paper_2502_18497_gb300 import LDL, apply_batches
+    from synth import cached, multi_graph_workload
+    G, W, K = args.graphs, args.warmup, args.steps
+    work = cached(f"multi_g{G}_s{W + 2 * K}_seed4_v1", lambda: multi_graph_workload(graphs=G, steps=W + 2 * K))
+    streams = [torch.cuda.Stream() for _ in work]
+    t0 = time.perf_counter()
+    gpus = [LDL.from_graph(g, stream=st.cuda_stream) for (g, _), st in zip(work, streams)]
+    torch.cuda.synchronize()
+    create_s = time.perf_counter() - t0
+    per_step = sum(len(bs[0]) for _, bs in work)
+    for s_ in range(W):
+        apply_batches(gpus, [bs[s_] for _, bs in work], threads=args.threads)
+    torch.cuda.synchronize()
+    # plain form: one context after another
+    t = time.perf_counter()
+    for s_ in range(W, W + K):
+        for d, (_, bs) in zip(gpus, work):
+            d.apply(bs[s_])
+    torch.cuda.synchronize()
+    plain = K * per_step / (time.perf_counter() - t)
+    # batched form: all contexts concurrently
+    lat = []
+    t = time.perf_counter()
+    for s_ in range(W + K, W + 2 * K):
+        t1 = time.perf_counter()
+        apply_batches(gpus, [bs[s_] for _, bs in work], threads=args.threads)
+        lat.append(time.perf_counter() - t1)
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t
+    ups = K * per_step / el
+    line = {"metric": "updates/s", "value": ups, "unit": "updates/s", "n_gpus": 1, "steps": K, "warmup": W,
+            "ms_per_step": 1e3 * el / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "int64", "data": "synthetic", "form": "batched",
+            "config": {"workload": f"{G} independent graphs, n log-uniform 1e3..1e5, half directed R-MAT (8 arcs/vertex), "
+                                   f"half undirected planted partition; batches of 0.1% of each graph's edges",
+                       "edges_total": int(sum(g.nnz if g.directed else g.nnz // 2 for g, _ in work)),
+                       "updates_per_step": per_step, "threads": args.threads, "create_s": round(create_s, 1)},
+            "plain_value": plain, "speedup_vs_plain": ups / plain,
+            "latency_ms": {"p50": 1e3 * float(np.percentile(lat, 50)), "p99": 1e3 * float(np.percentile(lat, 99))}}
+    print(json.dumps(line), flush=True)
+
+
+def run_served(args):
+    """Served form: tenants receive batches of log-uniform size (10..10^4) as a
+    Poisson stream; the native server runs them with `threads` workers
+    (requests of one tenant in order, tenants overlapping).  Reports
+    throughput and p50/p99 latency (queue + service) at an arrival rate set to
+    `load` x the capacity measured with one worker, next to that one-worker
+    (plain) service."""
+    import torch
+    from paper_2502_18497_gb300 import Server
+    from synth import cached, rmat_directed, sized_stream, splitmix64, unit_f64
+    T, R = args.tenants, args.requests
+    order = (splitmix64(12, 0, np.arange(R)) % np.uint64(T)).astype(int)
+
+    def make():
+        out = []
+        for k in range(T):
+            g = rmat_directed(scale=17, arcs=1 << 21, seed=500 + k)
+            cnt = int((order == k).sum()) + 4 * T
+            sizes = np.exp(np.log(10) + unit_f64(7, k, np.arange(cnt)) * (np.log(1e4) - np.log(10))).astype(int)
+            out.append((g, sized_stream(g, sizes, seed=900 + k)))
+        return out
+    work = cached(f"served_t{T}_r{R}_v2", make)
+
+    def serve(workers, rate, nreq):
+        srv = Server(workers=workers)
+        streams = [torch.cuda.Stream() for _ in work]
+        gpus = [srv.admit(g, stream=st.cuda_stream) for (g, _), st in zip(work, streams)]
+        torch.cuda.synchronize()
+        gaps = -np.log(1.0 - unit_f64(11, workers, np.arange(nreq))) / rate if rate else np.zeros(nreq)
+        nxt = [0] * T
+        tickets, upd = [], 0
+        t0 = time.perf_counter()
+        due = t0
+        for i in range(nreq):
+            due += gaps[i]
+            while time.perf_counter() < due:
+                pass
+            k = order[i]
+            b = work[k][1][nxt[k]]
+            nxt[k] += 1
+            tickets.append((time.perf_counter(), srv.submit(gpus[k], b)))
+            upd += len(b)
+        lat = []
+        for ts, tk in tickets:
+            st, res, q, sv = srv.wait(tk)
+            assert st == 0
+            lat.append((q + sv) / 1e3)
+        el = time.perf_counter() - t0
+        srv.close()
+        return upd / el, lat, el
+    cap, _, _ = serve(1, 0.0, min(R, 4 * T))            # one worker, back to back: capacity
+    # (each serve() call starts from freshly admitted tenants, so the same
+    # request sequence is valid again)
+    mean_batch = np.mean([len(b) for _, bs in work for b in bs])
+    rate = args.load * cap / mean_batch                   # requests per second
+    ups1, lat1, _ = serve(1, rate, R)
+    upsN, latN, el = serve(args.threads, rate, R)
+    line = {"metric": "updates/s", "value": upsN, "unit": "updates/s", "n_gpus": 1, "steps": R, "warmup": 0,
+            "ms_per_step": 1e3 * el / R, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "int64", "data": "synthetic", "form": "served",
+            "config": {"workload": f"{T} tenants, each a directed R-MAT 2^17 vertices / 2^21 arcs; batches of "
+                                   f"log-uniform 10..10^4 updates arriving as a Poisson stream at "
+                                   f"{args.load:.2f} x one-worker capacity", "workers": args.threads,
+                       "requests": R},
+            "latency_ms": {"p50": float(np.percentile(latN, 50)), "p99": float(np.percentile(latN, 99))},
+            "plain": {"updates_per_s": ups1, "latency_ms": {"p50": float(np.percentile(lat1, 50)),
+                                                             "p99": float(np.percentile(lat1, 99))}},
+            "capacity_one_worker": cap}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -180,9 +298,19 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--ref-budget", type=float, default=120.0, help="seconds of oracle batches (reference arm)")
     ap.add_argument("--stage-times", action="store_true", help="per-stage device times (adds syncs)")
+    ap.add_argument("--workload", default="rmat", choices=["rmat", "batched", "served"])
+    ap.add_argument("--graphs", type=int, default=512, help="batched form: number of graphs")
+    ap.add_argument("--threads", type=int, default=16, help="batched/served: host worker threads")
+    ap.add_argument("--tenants", type=int, default=16, help="served form: graphs")
+    ap.add_argument("--requests", type=int, default=400, help="served form: requests")
+    ap.add_argument("--load", type=float, default=0.9, help="served form: arrival rate / one-worker capacity")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched":
+        return run_batched(args)
+    if args.workload == "served":
+        return run_served(args)
 
     import torch
     ws, rank, local = _dist()

@@ -148,6 +148,46 @@ void ldl_destroy(ldl_ctx* ctx);
 const char* ldl_last_error(const ldl_ctx* ctx);
 
 /* ----------------------------------------------------------------------------
+ * Execution forms (the arithmetic of every context is that of ldl_apply_batch)
+ * -------------------------------------------------------------------------- */
+
+/*
+ * Batched form: applies updates[i] (counts[i] entries) to ctxs[i] for i < g,
+ * concurrently from `threads` host threads (0: up to 16).  Contexts created
+ * with distinct cuda_stream values overlap on the device; contexts must be
+ * distinct.  statuses / results (optional, length g) receive each context's
+ * outcome; the return value is LDL_OK or the first failing status.
+ */
+ldl_status ldl_apply_batches(ldl_ctx* const* ctxs, const ldl_update* const* updates, const int64_t* counts,
+                             int32_t g, int32_t updates_on_device, int32_t threads, ldl_status* statuses,
+                             ldl_result* results);
+
+/* Estimated device bytes of a context with n vertices and nnz stored entries. */
+ldl_status ldl_estimate_bytes(const ldl_params* params, int64_t n, int64_t nnz, int64_t* bytes);
+
+/*
+ * Served form: a request server with `workers` host threads.  Requests
+ * (batches) on one context run in submission order; requests on different
+ * contexts overlap on the device (give each context its own stream).
+ * ldl_server_admit creates a context only when the device's free memory
+ * covers its estimated footprint (LDL_E_NOMEM otherwise, nothing allocated).
+ * ldl_server_submit copies the host updates and returns a ticket;
+ * ldl_server_wait blocks until the ticket's batch is done (timeout_ms < 0:
+ * no limit; LDL_E_TIMEOUT when it runs out) and reports its status, result,
+ * time queued and time in service (microseconds).  A ticket can be waited
+ * once.  ldl_server_destroy runs the queue dry and joins the workers.
+ */
+typedef struct ldl_server ldl_server;
+ldl_status ldl_server_create(int32_t workers, ldl_server** out);
+ldl_status ldl_server_admit(ldl_server* server, const ldl_params* params, int64_t n, int64_t nnz,
+                            const int64_t* row_ptr, const int32_t* col, const int32_t* w, ldl_ctx** out);
+ldl_status ldl_server_submit(ldl_server* server, ldl_ctx* ctx, const ldl_update* updates, int64_t count,
+                             int64_t* ticket);
+ldl_status ldl_server_wait(ldl_server* server, int64_t ticket, int32_t timeout_ms, ldl_status* status,
+                           ldl_result* result, double* queue_us, double* service_us);
+void ldl_server_destroy(ldl_server* server);
+
+/* ----------------------------------------------------------------------------
  * Introspection (copies device state to host; for tests and tooling).
  * -------------------------------------------------------------------------- */
 

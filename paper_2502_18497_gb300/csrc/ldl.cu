@@ -87,7 +87,7 @@ void sub_end(ldl_ctx& c, int stage) {
   c.stage_ms[stage] += ms;
 }
 
-static std::string g_create_err = "no error";
+static thread_local std::string g_create_err = "no error";
 
 // ---------------------------------------------------------------- numerator
 static i128 qnum(const ldl_ctx& c) {

@@ -315,12 +315,8 @@ int64_t scan_exclusive_i32(const int32_t* in, int64_t* out, int64_t n, Prims& P,
 void radix_sort_pairs(u64*& keys, u64*& vals, u64*& tk, u64*& tv, int64_t n, int bits, Prims& P, cudaStream_t s) {
   if (n <= 1 || bits <= 0) return;
   if (n <= RS_TILE) {
-    static bool attr = false;
     const int smem = 4 * RS_TILE * (int)sizeof(u64);
-    if (!attr) {
-      CK(cudaFuncSetAttribute(k_rs_small, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-      attr = true;
-    }
+    CK(cudaFuncSetAttribute(k_rs_small, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     k_rs_small<<<1, RS_THREADS, smem, s>>>(keys, vals, (int)n, bits);
     CKL("k_rs_small");
     return;

@@ -770,11 +770,7 @@ static int32_t sweep_t(ldl_ctx& c, int r, Adj<WT> out, Adj<WT> in, const int32_t
   }
   if (cm2 > 0) {
     const size_t sm = (sizeof(int64_t) + sizeof(int32_t)) * HB;
-    static bool attr = false;
-    if (!attr) {
-      CK(cudaFuncSetAttribute(k_sweep_block<WT, MODE, 256, HB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-      attr = true;
-    }
+    CK(cudaFuncSetAttribute(k_sweep_block<WT, MODE, 256, HB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     k_sweep_block<WT, MODE, 256, HB><<<grid_for(cm2, 1, 152 * 4), 256, sm, c.s>>>(A, c.binM2.p, c.dcnt + K_MID2);
     CKL("k_sweep_block(mid2)");
   }

@@ -81,6 +81,13 @@ def load(path: Optional[str] = None):
         "ldl_launch_count": (I64, []),
         "ldl_set_kernel_stats": (I32, [P, I32]),
         "ldl_get_kernel_stats": (I32, [P, P]),
+        "ldl_apply_batches": (I32, [P, P, P, I32, I32, I32, P, P]),
+        "ldl_estimate_bytes": (I32, [P, I64, I64, P]),
+        "ldl_server_create": (I32, [I32, P]),
+        "ldl_server_admit": (I32, [P, P, I64, I64, P, P, P, P]),
+        "ldl_server_submit": (I32, [P, P, P, I64, P]),
+        "ldl_server_wait": (I32, [P, I64, I32, P, P, P, P]),
+        "ldl_server_destroy": (None, [P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -96,7 +103,9 @@ def exported_symbols():
             "ldl_modularity_num", "ldl_destroy", "ldl_last_error", "ldl_levels", "ldl_get_level",
             "ldl_level_nnz", "ldl_get_adjacency", "ldl_get_communities", "ldl_stage_times",
             "ldl_set_timing", "ldl_debug_fail_alloc_after", "ldl_copy_changed", "ldl_copy_changed_noalloc", "ldl_launch_count",
-            "ldl_set_kernel_stats", "ldl_get_kernel_stats"]
+            "ldl_set_kernel_stats", "ldl_get_kernel_stats", "ldl_apply_batches", "ldl_estimate_bytes",
+            "ldl_server_create", "ldl_server_admit", "ldl_server_submit", "ldl_server_wait",
+            "ldl_server_destroy"]
 
 
 def launch_count() -> int:
@@ -121,25 +130,38 @@ class Level:
     alive: np.ndarray
 
 
+def make_params(directed=False, gamma_num=1, gamma_den=1, N=2, L=4, M=5, M_static=20, alpha_inv=1000,
+                beta_inv=100, stream=None) -> ldl_params:
+    p = ldl_params()
+    load().ldl_default_params(C.byref(p))
+    p.directed, p.gamma_num, p.gamma_den = int(directed), gamma_num, gamma_den
+    p.N, p.L, p.M, p.M_static = N, L, M, M_static
+    p.alpha_inv, p.beta_inv = alpha_inv, beta_inv
+    p.cuda_stream = stream
+    return p
+
+
 class LDL:
-    """One device-resident LD-Leiden instance (ldl_create ... ldl_destroy)."""
+    """One device-resident LD-Leiden instance (ldl_create ... ldl_destroy).
+
+    `stream` is a cudaStream_t handle (e.g. torch.cuda.Stream().cuda_stream);
+    None uses the legacy default stream."""
 
     def __init__(self, n, row_ptr, col, w, directed=False, gamma_num=1, gamma_den=1, N=2, L=4, M=5,
-                 M_static=20, alpha_inv=1000, beta_inv=100, stream=None):
+                 M_static=20, alpha_inv=1000, beta_inv=100, stream=None, server=None):
         lib = load()
-        p = ldl_params()
-        lib.ldl_default_params(C.byref(p))
-        p.directed, p.gamma_num, p.gamma_den = int(directed), gamma_num, gamma_den
-        p.N, p.L, p.M, p.M_static = N, L, M, M_static
-        p.alpha_inv, p.beta_inv = alpha_inv, beta_inv
-        p.cuda_stream = stream
+        p = make_params(directed, gamma_num, gamma_den, N, L, M, M_static, alpha_inv, beta_inv, stream)
         self.n = int(n)
         self.directed = bool(directed)
         rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
         cl = np.ascontiguousarray(col, dtype=np.int32)
         wt = np.ascontiguousarray(w, dtype=np.int32)
         h = C.c_void_p()
-        st = lib.ldl_create(C.byref(p), self.n, len(cl), _ptr(rp), _ptr(cl), _ptr(wt), C.byref(h))
+        if server is None:
+            st = lib.ldl_create(C.byref(p), self.n, len(cl), _ptr(rp), _ptr(cl), _ptr(wt), C.byref(h))
+        else:
+            st = lib.ldl_server_admit(server._h, C.byref(p), self.n, len(cl), _ptr(rp), _ptr(cl), _ptr(wt),
+                                      C.byref(h))
         if st != LDL_OK:
             raise LdlError(st, lib.ldl_last_error(None).decode())
         self._h = h
@@ -268,3 +290,63 @@ class LDL:
                     rejected=r.rejected, rollbacks=r.rollbacks, rounds=r.rounds,
                     agg_records=r.agg_records, decouple_rounds=r.decouple_rounds,
                     host_syncs=r.host_syncs)
+
+
+def apply_batches(instances, batches, threads: int = 0):
+    """Batched form: one batch per instance, applied concurrently.  Returns
+    the per-instance statuses (raises on the first failure)."""
+    g = len(instances)
+    arrs = [np.ascontiguousarray(b, dtype=np.int32).reshape(-1, 4) for b in batches]
+    ctxs = (C.c_void_p * g)(*[d._h.value for d in instances])
+    ptrs = (C.c_void_p * g)(*[a.ctypes.data for a in arrs])
+    counts = (C.c_int64 * g)(*[a.shape[0] for a in arrs])
+    st = (C.c_int32 * g)()
+    res = (ldl_result * g)()
+    rc = load().ldl_apply_batches(ctxs, ptrs, counts, g, 0, threads, st, res)
+    for d, r in zip(instances, res):
+        d.last = r
+    if rc != LDL_OK:
+        i = next(k for k in range(g) if st[k] != LDL_OK)
+        raise LdlError(rc, load().ldl_last_error(instances[i]._h).decode())
+    return list(st)
+
+
+class Server:
+    """Served form: a native request server (ldl_server_*)."""
+
+    def __init__(self, workers: int = 4):
+        h = C.c_void_p()
+        st = load().ldl_server_create(workers, C.byref(h))
+        if st != LDL_OK:
+            raise LdlError(st, "server create")
+        self._h = h
+
+    def admit(self, g, **kw) -> LDL:
+        return LDL(g.n, g.row_ptr, g.col, g.w, directed=g.directed, server=self, **kw)
+
+    def submit(self, inst: LDL, batch) -> int:
+        b = np.ascontiguousarray(batch, dtype=np.int32).reshape(-1, 4)
+        t = C.c_int64()
+        st = load().ldl_server_submit(self._h, inst._h, _ptr(b), b.shape[0], C.byref(t))
+        if st != LDL_OK:
+            raise LdlError(st, "submit")
+        return int(t.value)
+
+    def wait(self, ticket: int, timeout_ms: int = -1):
+        st, res = C.c_int32(), ldl_result()
+        q, sv = C.c_double(), C.c_double()
+        rc = load().ldl_server_wait(self._h, ticket, timeout_ms, C.byref(st), C.byref(res), C.byref(q), C.byref(sv))
+        if rc != LDL_OK:
+            raise LdlError(rc, "wait")
+        return int(st.value), res, q.value, sv.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().ldl_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

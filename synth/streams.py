@@ -231,6 +231,48 @@ def rmat_workload(nbatches: int, scale: int = 20, arcs: int = 1 << 24, batch: in
     return g, bs
 
 
+def multi_graph_workload(graphs: int = 512, nmin: int = 1000, nmax: int = 100_000, steps: int = 8,
+                         frac: float = 0.001, seed: int = 4):
+    """Many independent graphs for the batched form: vertex counts
+    log-uniform in [nmin, nmax]; even graphs directed R-MAT (16 arcs per
+    vertex), odd graphs undirected planted partitions
+    (100-vertex blocks, weights 1..8); R-MAT graphs have 8 arcs per vertex; every graph gets `steps` batches of
+    `frac` of its edges (at least 4 updates), with the planted-partition
+    op mix (70% insert, 20% delete, 10% reweight) for odd graphs and 80/20
+    insert/delete for the R-MAT ones."""
+    u = unit_f64(seed, 111, np.arange(graphs))
+    ns = np.exp(np.log(nmin) + u * (np.log(nmax) - np.log(nmin))).astype(np.int64)
+    out = []
+    for i, n in enumerate(ns.tolist()):
+        if i % 2 == 0:
+            scale = max(8, int(round(np.log2(n))))
+            g = rmat_directed(scale=scale, arcs=8 << scale, wmax=8, seed=seed * 1000 + i)
+            size = max(4, int(g.nnz * frac))
+            bs = rmat_stream(g, batches=steps, size=size, seed=seed * 1000 + i, wmax=8)
+        else:
+            nb = max(2, n // 100)
+            g = planted_partition(n=nb * 100, block=100, seed=seed * 1000 + i, wmax=8)
+            size = max(4, int(g.nnz // 2 * frac))
+            bs = planted_stream(g, batches=steps, size=size, seed=seed * 1000 + i, block=100, wmax=8)
+        out.append((g, bs))
+    return out
+
+
+def sized_stream(g: Graph, sizes, seed: int, ins_frac: float = 0.8, wmax: int = 16, probs=(0.57, 0.19, 0.19, 0.05)):
+    """Batches of the given sizes for an R-MAT graph, drawn as one consistent
+    stream (inserts of new R-MAT arcs, deletes of existing arcs)."""
+    st = EdgeStream.from_graph(g, seed * 1000 + 13)
+    scale = int(g.n).bit_length() - 1
+
+    def sampler(base, cnt):
+        return _rmat_draw(seed, 62, base, cnt, scale, probs)
+    out = []
+    for sz in sizes:
+        n_ins = int(round(sz * ins_frac))
+        out.append(st.make_batch(n_ins, int(sz) - n_ins, 0, sampler, wmax))
+    return out
+
+
 def random_small_graph(n: int, p: float, directed: bool, wmax: int = 5, seed: int = 0,
                        self_loops: bool = False) -> Graph:
     """Erdos-Renyi style graph for tiny brute-force checks."""
