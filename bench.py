@@ -114,6 +114,22 @@ def _dist():
     return ws, rank, local
 
 
+def reduce_over_ranks(per_rank_updates: int, elapsed: float, device=None):
+    """Whole-job throughput over replicas: every rank processed
+    `per_rank_updates` in `elapsed` seconds; the job takes as long as its
+    slowest rank.  Returns (total updates / max elapsed, max elapsed)."""
+    import torch
+    import torch.distributed as dist
+    ws = dist.get_world_size() if dist.is_initialized() else 1
+    if ws == 1:
+        return per_rank_updates / elapsed, elapsed
+    t = torch.tensor([elapsed], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    u = torch.tensor([per_rank_updates], dtype=torch.float64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(u.item()) / float(t.item()), float(t.item())
+
+
 def cpu_baseline(g, batches, budget_s: float = 30.0):
     """The oracle as it stands, single-threaded on the host: its own static
     Leiden (untimed), then whole batches of the same stream until the budget."""
@@ -288,6 +304,47 @@ def run_served(args):
     print(json.dumps(line), flush=True)
 
 
+def run_powerlaw(args):
+    """Batch-size sweep on the LFR-like power-law planted partition
+    (2^scale vertices, mean degree 32, exponent 2.5, community sizes 50..50,000,
+    mixing 0.2): for each batch size B in 10^2..10^6 a fresh instance (same
+    initial state) applies `steps` region-localised batches of B updates
+    (80% inserts / 20% deletes).  Reports time per batch and updates/s per B,
+    and the time ratio per 10x smaller batch."""
+    import torch
+    from paper_2502_18497_gb300 import LDL
+    from synth import cached, powerlaw_planted, powerlaw_stream
+    n = 1 << args.scale
+    g = cached(f"powerlaw_n{n}_seed3_v1", lambda: powerlaw_planted(n=n, seed=3))
+    sizes = [10 ** k for k in range(2, 7) if 10 ** k <= n // 8]
+    sweep = {}
+    for B in sizes:
+        bs = cached(f"powerlaw_n{n}_b{B}_k{args.steps}_seed3_v1",
+                    lambda: powerlaw_stream(g, size=B, batches=args.steps, seed=3))
+        d = LDL.from_graph(g)
+        dev = [torch.from_numpy(np.ascontiguousarray(b)).cuda() for b in bs]
+        torch.cuda.synchronize()
+        times, scanned = [], 0
+        for b in dev:
+            t = time.perf_counter()
+            r = d.apply(b, on_device=True)
+            times.append(time.perf_counter() - t)
+            scanned += r.edges_scanned
+        sweep[B] = {"ms_per_batch": 1e3 * float(np.mean(times)), "updates_per_s": B * len(times) / sum(times),
+                    "frontier_entries_per_batch": scanned / len(times)}
+        d.close()
+    ratios = [sweep[a]["ms_per_batch"] / sweep[b]["ms_per_batch"] for a, b in zip(sizes[1:], sizes[:-1])]
+    top = sizes[-1]
+    line = {"metric": "updates/s", "value": sweep[top]["updates_per_s"], "unit": "updates/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": 0, "ms_per_step": sweep[top]["ms_per_batch"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic", "form": "batch-size sweep",
+            "config": {"workload": f"power-law planted partition, 2^{args.scale} vertices, {g.nnz // 2} edges, "
+                                   f"mean degree 32, mixing 0.2; region-localised batches", "value_at_batch": top},
+            "sweep": {str(k): v for k, v in sweep.items()},
+            "time_ratio_per_10x_smaller_batch": ratios}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -298,7 +355,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--ref-budget", type=float, default=120.0, help="seconds of oracle batches (reference arm)")
     ap.add_argument("--stage-times", action="store_true", help="per-stage device times (adds syncs)")
-    ap.add_argument("--workload", default="rmat", choices=["rmat", "batched", "served"])
+    ap.add_argument("--workload", default="rmat", choices=["rmat", "batched", "served", "powerlaw"])
+    ap.add_argument("--scale", type=int, default=24, help="powerlaw: log2 of the vertex count")
     ap.add_argument("--graphs", type=int, default=512, help="batched form: number of graphs")
     ap.add_argument("--threads", type=int, default=16, help="batched/served: host worker threads")
     ap.add_argument("--tenants", type=int, default=16, help="served form: graphs")
@@ -311,6 +369,8 @@ def main():
         return run_batched(args)
     if args.workload == "served":
         return run_served(args)
+    if args.workload == "powerlaw":
+        return run_powerlaw(args)
 
     import torch
     ws, rank, local = _dist()
@@ -360,17 +420,14 @@ def main():
     if ws > 1:
         torch.distributed.barrier()
     ms = e0.elapsed_time(e1)
+    ups, el = reduce_over_ranks(K * BATCH, ms / 1e3, device="cuda")
+    ms = el * 1e3
     launches = binding.launch_count() - launches0
     clk = clocks.stop()
     ks = d.kernel_stats()
     stage = d.stage_times() if args.stage_times else None
     d.set_kernel_stats(False)
     d.set_timing(False)
-    if ws > 1:
-        tt = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        ms = float(tt.item())
-    ups = ws * K * BATCH / (ms / 1e3)
 
     # ---- end to end through the public API from pinned host memory
     host = [torch.from_numpy(np.ascontiguousarray(b)).pin_memory() for b in batches[W + K:W + 2 * K]]
@@ -386,11 +443,8 @@ def main():
         d2h += ids.nbytes + labs.nbytes
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t
-    if ws > 1:
-        tt = torch.tensor([e2e_s], device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(tt.item())
-    e2e = {"value": ws * K * BATCH / e2e_s, "unit": "updates/s", "h2d_bytes_per_step": h2d // K,
+    e2e_ups, e2e_s = reduce_over_ranks(K * BATCH, e2e_s, device="cuda")
+    e2e = {"value": e2e_ups, "unit": "updates/s", "h2d_bytes_per_step": h2d // K,
            "d2h_bytes_per_step": d2h // K}
 
     if rank != 0:

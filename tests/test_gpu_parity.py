@@ -128,3 +128,31 @@ def test_empty_and_null_batches(ldl):
         assert o.apply(b) == 0
         d.apply(b)
         _assert_same(o, d, "after null batch")
+
+
+@pytest.mark.parametrize("size", [100, 1000])
+def test_powerlaw_planted_reduced(ldl, size):
+    """The LFR-like power-law planted partition at 2^16 vertices (mean degree
+    ~28, mixing 0.2), two region-localised batches per batch size, each size
+    starting from the same initial state."""
+    from synth import powerlaw_planted, powerlaw_stream
+    g = powerlaw_planted(n=1 << 16, seed=3)
+    o, d = _pair(ldl, g)
+    for t, b in enumerate(powerlaw_stream(g, size=size, batches=2, seed=3)):
+        assert o.apply(b) == 0
+        d.apply(b)
+        _assert_same(o, d, f"size {size} batch {t}")
+
+
+def test_injected_allocation_failure_at_create(ldl):
+    """A failing device allocation during ldl_create returns NOMEM and leaves
+    nothing behind; the next create succeeds."""
+    g = planted_partition(n=1000, block=50, seed=9)
+    for k in (1, 5, 40):
+        ldl.load().ldl_debug_fail_alloc_after(k)
+        with pytest.raises(ldl.LdlError) as e:
+            ldl.LDL.from_graph(g)
+        assert e.value.status == ldl.LDL_E_NOMEM
+    ldl.load().ldl_debug_fail_alloc_after(0)
+    o, d = _pair(ldl, g)
+    _assert_same(o, d, "after injected failures")
