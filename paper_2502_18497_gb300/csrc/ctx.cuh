@@ -18,8 +18,8 @@ struct Adj {
 };
 
 struct LevelState {
-  SlackCSR<int32_t> out0, in0;   // level 0
-  SlackCSR<int64_t> out, in;     // levels >= 1
+  SlackCSR<int32_t> out0, in0;   // level 0 (directed: in-rows at rows n..2n-1 of out0)
+  SlackCSR<int64_t> out, in;     // levels >= 1 (same layout)
   SlackCSR<int32_t> children;    // keyed by level r+1 node: its level-r members (r < T)
   DBuf<int32_t> lab, par, cnt;   // P^r, pi_r (NONE = -1), number of level r-1 children
   DBuf<int64_t> kout, kin;       // strengths (kin aliases kout when undirected)
@@ -80,7 +80,7 @@ struct ldl_ctx {
   DBuf<int64_t> rsum, rsum2;
   DBuf<int32_t> ndx, ndx2;
   DBuf<int64_t> ndko, ndki, ndko2, ndki2;
-  DBuf<u64> crk, crv, fk;
+  DBuf<u64> crk, crv, fk, trk, trv;
   DBuf<int64_t> chunk_cnt, chunk_pre;
   DBuf<int64_t> hub_ecnt, hub_epre, pb_hi;
   DBuf<uint64_t> pb_lo;
@@ -110,17 +110,21 @@ inline Adj<int32_t> adj_out0(ldl_ctx& c) {
   auto& g = c.lv[0].out0;
   return Adj<int32_t>{g.off.p, g.len.p, g.col.p, g.w.p};
 }
+// Directed graphs keep the in-rows of a level in the same slack CSR as its
+// out-rows, at rows n..2n-1.
 inline Adj<int32_t> adj_in0(ldl_ctx& c) {
-  auto& g = c.directed ? c.lv[0].in0 : c.lv[0].out0;
-  return Adj<int32_t>{g.off.p, g.len.p, g.col.p, g.w.p};
+  auto& g = c.lv[0].out0;
+  const int64_t o = c.directed ? c.n : 0;
+  return Adj<int32_t>{g.off.p + o, g.len.p + o, g.col.p, g.w.p};
 }
 inline Adj<int64_t> adj_out(ldl_ctx& c, int r) {
   auto& g = c.lv[r].out;
   return Adj<int64_t>{g.off.p, g.len.p, g.col.p, g.w.p};
 }
 inline Adj<int64_t> adj_in(ldl_ctx& c, int r) {
-  auto& g = c.directed ? c.lv[r].in : c.lv[r].out;
-  return Adj<int64_t>{g.off.p, g.len.p, g.col.p, g.w.p};
+  auto& g = c.lv[r].out;
+  const int64_t o = c.directed ? c.n : 0;
+  return Adj<int64_t>{g.off.p + o, g.len.p + o, g.col.p, g.w.p};
 }
 inline int64_t* kin_of(ldl_ctx& c, int r) { return c.directed ? c.lv[r].kin.p : c.lv[r].kout.p; }
 inline int64_t* Kin_of(ldl_ctx& c) { return c.directed ? c.Kin.p : c.Kout.p; }

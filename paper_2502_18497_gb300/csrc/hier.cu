@@ -106,10 +106,12 @@ __global__ void k_emit_arcs(const u64* ukeys, const int64_t* delta, int64_t nu, 
   }
 }
 
-__global__ void k_transpose(const u64* k, const u64* v, int64_t n, int bits, u64* ok, u64* ov) {
+// (row, col) -> (col + row_off, row): the in-direction records of a level
+// whose in-rows live at row_off (directed graphs keep both in one CSR).
+__global__ void k_transpose(const u64* k, const u64* v, int64_t n, int bits, u64* ok, u64* ov, int64_t row_off) {
   const u64 mask = (((u64)1) << bits) - 1;
   GRID_STRIDE(i, n) {
-    ok[i] = ((k[i] & mask) << bits) | (k[i] >> bits);
+    ok[i] = (((k[i] & mask) + (u64)row_off) << bits) | (k[i] >> bits);
     ov[i] = v[i];
   }
 }
@@ -668,24 +670,40 @@ int64_t ingest(ldl_ctx& c, const ldl_update* upd, int64_t count, int on_device, 
   return na;
 }
 
-// apply sorted unique records to a level's out (and transposed in) adjacency
+// Sorted unique out-records of a directed level -> the same records followed
+// by their in-direction copies (rows n..2n-1), still sorted: (rk2, rv2), 2*nr.
+static void combine_in_out(ldl_ctx& c, const u64* keys, const u64* vals, int64_t nr) {
+  c.rk2.reserve(2 * nr + 1, c.s);
+  c.rv2.reserve(2 * nr + 1, c.s);
+  c.trk.reserve(nr + 1, c.s);
+  c.trv.reserve(nr + 1, c.s);
+  k_transpose<<<grid_for(nr, TPB), TPB, 0, c.s>>>(keys, vals, nr, c.bits, c.trk.p, c.trv.p, c.n);
+  CKL("k_transpose");
+  // the out-records are ordered by row, so a stable sort on the new row alone
+  // gives (in-row, col) order
+  sort_pairs(c.trk, c.trv, c.tk, c.tv, nr, 2 * c.bits + 1, c.P, c.s, c.bits);
+  CK(cudaMemcpyAsync(c.rk2.p, keys, sizeof(u64) * (size_t)nr, cudaMemcpyDeviceToDevice, c.s));
+  CK(cudaMemcpyAsync(c.rv2.p, vals, sizeof(u64) * (size_t)nr, cudaMemcpyDeviceToDevice, c.s));
+  CK(cudaMemcpyAsync(c.rk2.p + nr, c.trk.p, sizeof(u64) * (size_t)nr, cudaMemcpyDeviceToDevice, c.s));
+  CK(cudaMemcpyAsync(c.rv2.p + nr, c.trv.p, sizeof(u64) * (size_t)nr, cudaMemcpyDeviceToDevice, c.s));
+}
+
+// apply sorted unique records to a level's adjacency (both directions)
 static void apply_level(ldl_ctx& c, int r, DBuf<u64>& keys, DBuf<u64>& vals, int64_t nr) {
   if (nr <= 0) return;
-  if (r == 0)
-    csr_apply<int32_t>(c.lv[0].out0, keys.p, (const int64_t*)vals.p, nr, c.bits, c.CS, c.P, c.s, c.d_sc);
-  else
-    csr_apply<int64_t>(c.lv[r].out, keys.p, (const int64_t*)vals.p, nr, c.bits, c.CS, c.P, c.s, c.d_sc);
+  const u64* k = keys.p;
+  const u64* v = vals.p;
+  int64_t m = nr;
   if (c.directed) {
-    c.rk2.reserve(nr, c.s);
-    c.rv2.reserve(nr, c.s);
-    k_transpose<<<grid_for(nr, TPB), TPB, 0, c.s>>>(keys.p, vals.p, nr, c.bits, c.rk2.p, c.rv2.p);
-    CKL("k_transpose");
-    sort_pairs(c.rk2, c.rv2, c.tk, c.tv, nr, 2 * c.bits, c.P, c.s);
-    if (r == 0)
-      csr_apply<int32_t>(c.lv[0].in0, c.rk2.p, (const int64_t*)c.rv2.p, nr, c.bits, c.CS, c.P, c.s, c.d_sc);
-    else
-      csr_apply<int64_t>(c.lv[r].in, c.rk2.p, (const int64_t*)c.rv2.p, nr, c.bits, c.CS, c.P, c.s, c.d_sc);
+    combine_in_out(c, keys.p, vals.p, nr);
+    k = c.rk2.p;
+    v = c.rv2.p;
+    m = 2 * nr;
   }
+  if (r == 0)
+    csr_apply<int32_t>(c.lv[0].out0, k, (const int64_t*)v, m, c.bits, c.CS, c.P, c.s, c.d_sc);
+  else
+    csr_apply<int64_t>(c.lv[r].out, k, (const int64_t*)v, m, c.bits, c.CS, c.P, c.s, c.d_sc);
 }
 
 // Map records (keys, vals) of level q to level q+1, reduce, and apply there.
@@ -881,14 +899,11 @@ void aggregate(ldl_ctx& c, int r, int32_t epD, int32_t epC, int32_t epA_next, bo
     if (nr) CK(cudaMemcpyAsync(c.fk.p, c.rk.p, sizeof(u64) * (size_t)nr, cudaMemcpyDeviceToDevice, c.s));
     if (build) {
       // level r+1 starts empty: build its adjacency and the children lists
-      csr_build<int64_t>(N.out, c.n, c.rk.p, c.rsum.p, nr, c.bits, 25, c.CS, c.P, c.s);
       if (c.directed) {
-        c.rk2.reserve(nr + 1, c.s);
-        c.rv2.reserve(nr + 1, c.s);
-        k_transpose<<<grid_for(nr, TPB), TPB, 0, c.s>>>(c.rk.p, c.rv.p, nr, c.bits, c.rk2.p, c.rv2.p);
-        CKL("k_transpose");
-        sort_pairs(c.rk2, c.rv2, c.tk, c.tv, nr, 2 * c.bits, c.P, c.s);
-        csr_build<int64_t>(N.in, c.n, c.rk2.p, (const int64_t*)c.rv2.p, nr, c.bits, 25, c.CS, c.P, c.s);
+        combine_in_out(c, c.rk.p, c.rv.p, nr);
+        csr_build<int64_t>(N.out, 2 * c.n, c.rk2.p, (const int64_t*)c.rv2.p, 2 * nr, c.bits, 25, c.CS, c.P, c.s);
+      } else {
+        csr_build<int64_t>(N.out, c.n, c.rk.p, c.rsum.p, nr, c.bits, 25, c.CS, c.P, c.s);
       }
       csr_build<int32_t>(L.children, c.n, c.crk.p, (const int64_t*)c.crv.p, ncr, c.bits, 25, c.CS, c.P, c.s);
     } else {
@@ -1071,10 +1086,10 @@ void upload_graph(ldl_ctx& c, int64_t nnz, const int64_t* row_ptr, const int32_t
   if (na) {
     c.rk2.reserve(na + 1, c.s);
     c.rv2.reserve(na + 1, c.s);
-    k_transpose<<<grid_for(na, TPB), TPB, 0, c.s>>>(c.rk.p, c.rv.p, na, c.bits, c.rk2.p, c.rv2.p);
-    CKL("k_transpose");
-    sort_pairs(c.rk2, c.rv2, c.tk, c.tv, na, 2 * c.bits, c.P, c.s);
     if (!c.directed) {
+      k_transpose<<<grid_for(na, TPB), TPB, 0, c.s>>>(c.rk.p, c.rv.p, na, c.bits, c.rk2.p, c.rv2.p, 0);
+      CKL("k_transpose");
+      sort_pairs(c.rk2, c.rv2, c.tk, c.tv, na, 2 * c.bits, c.P, c.s, c.bits);  // rows already ordered
       reset_err(c);
       k_compare<<<grid_for(na, TPB), TPB, 0, c.s>>>(c.rk.p, (const int64_t*)c.rv.p, c.rk2.p, c.rv2.p, na,
                                                     err_ptr(c));
@@ -1083,8 +1098,12 @@ void upload_graph(ldl_ctx& c, int64_t nnz, const int64_t* row_ptr, const int32_t
     }
   }
   LevelState& L0 = c.lv[0];
-  csr_build<int32_t>(L0.out0, n, c.rk.p, (const int64_t*)c.rv.p, na, c.bits, 25, c.CS, c.P, c.s);
-  if (c.directed) csr_build<int32_t>(L0.in0, n, c.rk2.p, (const int64_t*)c.rv2.p, na, c.bits, 25, c.CS, c.P, c.s);
+  if (c.directed) {
+    combine_in_out(c, c.rk.p, c.rv.p, na);
+    csr_build<int32_t>(L0.out0, 2 * n, c.rk2.p, (const int64_t*)c.rv2.p, 2 * na, c.bits, 25, c.CS, c.P, c.s);
+  } else {
+    csr_build<int32_t>(L0.out0, n, c.rk.p, (const int64_t*)c.rv.p, na, c.bits, 25, c.CS, c.P, c.s);
+  }
   // strengths, m, labels, community totals
   CK(cudaMemsetAsync(&c.d_sc->dm, 0, sizeof(int64_t), c.s));
   const int gw = grid_for(n * 32, TPB);

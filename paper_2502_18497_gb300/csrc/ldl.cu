@@ -140,7 +140,7 @@ static void free_all(ldl_ctx& c) {
                           &c.cdst, &c.cst, &c.bv, &c.bsrc, &c.bdst, &c.best, &c.role, &c.oldlab, &c.par_old,
                           &c.lab_before, &c.binS, &c.binM, &c.binM2, &c.binL, &c.gkeys, &c.ndx, &c.ndx2};
   for (auto* b : b32) b->release();
-  DBuf<u64>* bu[] = {&c.rk, &c.rv, &c.tk, &c.tv, &c.rk2, &c.rv2, &c.crk, &c.crv, &c.fk};
+  DBuf<u64>* bu[] = {&c.rk, &c.rv, &c.tk, &c.tv, &c.rk2, &c.rv2, &c.crk, &c.crv, &c.fk, &c.trk, &c.trv};
   for (auto* b : bu) b->release();
   c.cglo.release();
   c.pb_lo.release();

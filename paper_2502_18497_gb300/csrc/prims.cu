@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const u64* keys, cons
 }
 
 // Whole sort in one block (n <= RS_TILE): every pass in shared memory.
-__global__ void __launch_bounds__(RS_THREADS) k_rs_small(u64* keys, u64* vals, int n, int bits) {
+__global__ void __launch_bounds__(RS_THREADS) k_rs_small(u64* keys, u64* vals, int n, int lo_bit, int bits) {
   extern __shared__ u64 sm[];
   u64* kb[2] = {sm, sm + RS_TILE};
   u64* vb[2] = {sm + 2 * RS_TILE, sm + 3 * RS_TILE};
@@ -176,7 +176,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_small(u64* keys, u64* vals, i
     vb[0][i] = vals[i];
   }
   int cur = 0;
-  for (int shift = 0; shift < bits; shift += 8) {
+  for (int shift = lo_bit; shift < bits; shift += 8) {
     for (int d = tid; d < 256; d += RS_THREADS) hist[d] = 0;
     __syncthreads();
     for (int i = tid; i < n; i += RS_THREADS) atomicAdd(&hist[(kb[cur][i] >> shift) & 255], 1);
@@ -312,19 +312,20 @@ int64_t scan_exclusive_i32(const int32_t* in, int64_t* out, int64_t n, Prims& P,
   return tot;
 }
 
-void radix_sort_pairs(u64*& keys, u64*& vals, u64*& tk, u64*& tv, int64_t n, int bits, Prims& P, cudaStream_t s) {
-  if (n <= 1 || bits <= 0) return;
+void radix_sort_pairs(u64*& keys, u64*& vals, u64*& tk, u64*& tv, int64_t n, int bits, Prims& P, cudaStream_t s,
+                      int lo_bit) {
+  if (n <= 1 || bits <= lo_bit) return;
   if (n <= RS_TILE) {
     const int smem = 4 * RS_TILE * (int)sizeof(u64);
     CK(cudaFuncSetAttribute(k_rs_small, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    k_rs_small<<<1, RS_THREADS, smem, s>>>(keys, vals, (int)n, bits);
+    k_rs_small<<<1, RS_THREADS, smem, s>>>(keys, vals, (int)n, lo_bit, bits);
     CKL("k_rs_small");
     return;
   }
   const int64_t nb = (n + RS_TILE - 1) / RS_TILE;
   P.hist.reserve(256 * nb + 1, s);
   P.hoff.reserve(256 * nb + 1, s);
-  for (int shift = 0; shift < bits; shift += 8) {
+  for (int shift = lo_bit; shift < bits; shift += 8) {
     k_rs_hist<<<(unsigned)nb, RS_THREADS, 0, s>>>(keys, n, shift, nb, P.hist.p);
     CKL("k_rs_hist");
     scan_exclusive(P.hist.p, P.hoff.p, 256 * nb, P, s, false);

@@ -19,7 +19,9 @@ int64_t scan_exclusive_i32(const int32_t* in, int64_t* out, int64_t n, Prims& P,
 // Stable LSD radix sort of n (key, value) pairs on the low `bits` key bits,
 // 8 bits per pass.  The sorted data ends in (keys, vals); the pointers are
 // swapped with (tk, tv) as the passes ping-pong.
-void radix_sort_pairs(u64*& keys, u64*& vals, u64*& tk, u64*& tv, int64_t n, int bits, Prims& P, cudaStream_t s);
+// Only key bits [lo_bit, bits) are sorted on (the order of keys equal there is kept).
+void radix_sort_pairs(u64*& keys, u64*& vals, u64*& tk, u64*& tv, int64_t n, int bits, Prims& P, cudaStream_t s,
+                      int lo_bit = 0);
 
 // Sorted keys -> unique keys with the int64 sum of their values, zero sums
 // dropped, order kept.  Returns the number of output pairs (synchronises).
@@ -38,11 +40,11 @@ inline void swap_buf(DBuf<T>& a, DBuf<T>& b) {
 
 // Sort the first n pairs of (k, v) in place (by DBuf identity) using (tk, tv).
 inline void sort_pairs(DBuf<u64>& k, DBuf<u64>& v, DBuf<u64>& tk, DBuf<u64>& tv, int64_t n, int bits, Prims& P,
-                       cudaStream_t s) {
+                       cudaStream_t s, int lo_bit = 0) {
   tk.reserve(n, s);
   tv.reserve(n, s);
   u64 *kp = k.p, *vp = v.p, *tkp = tk.p, *tvp = tv.p;
-  radix_sort_pairs(kp, vp, tkp, tvp, n, bits, P, s);
+  radix_sort_pairs(kp, vp, tkp, tvp, n, bits, P, s, lo_bit);
   if (kp != k.p) {
     swap_buf(k, tk);
     swap_buf(v, tv);
