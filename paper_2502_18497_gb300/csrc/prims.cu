@@ -118,14 +118,20 @@ __global__ void k_rs_hist(const u64* keys, int64_t n, int shift, int64_t nb, int
   for (int d = threadIdx.x; d < 256; d += RS_THREADS) ghist[(int64_t)d * nb + blockIdx.x] = h[d];
 }
 
+// goff holds tile-local exclusive prefixes of the digit-major histogram and
+// gbs the scanned tile sums: the global offset of entry i is
+// goff[i] + gbs[i / SC_TILE] (the scan's final add pass is folded in here).
 __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const u64* keys, const u64* vals, u64* okeys,
                                                            u64* ovals, int64_t n, int shift, int64_t nb,
-                                                           const int64_t* goff) {
+                                                           const int64_t* goff, const int64_t* gbs) {
   __shared__ int64_t run[256];
   __shared__ int32_t tot[256];
   __shared__ int32_t wcnt[RS_THREADS / WARP][257];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  for (int d = tid; d < 256; d += RS_THREADS) run[d] = goff[(int64_t)d * nb + blockIdx.x];
+  for (int d = tid; d < 256; d += RS_THREADS) {
+    const int64_t i = (int64_t)d * nb + blockIdx.x;
+    run[d] = goff[i] + gbs[i / SC_TILE];
+  }
   const int64_t base = (int64_t)blockIdx.x * RS_TILE;
   __syncthreads();
   for (int ch = 0; ch < RS_ITEMS; ++ch) {
@@ -328,8 +334,13 @@ void radix_sort_pairs(u64*& keys, u64*& vals, u64*& tk, u64*& tv, int64_t n, int
   for (int shift = lo_bit; shift < bits; shift += 8) {
     k_rs_hist<<<(unsigned)nb, RS_THREADS, 0, s>>>(keys, n, shift, nb, P.hist.p);
     CKL("k_rs_hist");
-    scan_exclusive(P.hist.p, P.hoff.p, 256 * nb, P, s, false);
-    k_rs_scatter<<<(unsigned)nb, RS_THREADS, 0, s>>>(keys, vals, tk, tv, n, shift, nb, P.hoff.p);
+    const int64_t hn = 256 * nb, hb = (hn + SC_TILE - 1) / SC_TILE;
+    P.bsum.reserve(hb + 1, s);
+    k_scan_tile<int64_t><<<(unsigned)hb, SC_THREADS, 0, s>>>(P.hist.p, P.hoff.p, hn, P.bsum.p);
+    CKL("k_scan_tile");
+    k_scan_bsums<<<1, SC_THREADS, 0, s>>>(P.bsum.p, hb, nullptr);
+    CKL("k_scan_bsums");
+    k_rs_scatter<<<(unsigned)nb, RS_THREADS, 0, s>>>(keys, vals, tk, tv, n, shift, nb, P.hoff.p, P.bsum.p);
     CKL("k_rs_scatter");
     u64* t = keys; keys = tk; tk = t;
     t = vals; vals = tv; tv = t;

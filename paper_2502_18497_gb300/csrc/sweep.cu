@@ -496,6 +496,76 @@ __global__ void k_dec_finish(int32_t nc, const int32_t* cst, const int32_t* cv, 
   }
 }
 
+// Whole decoupling filter in one block when the candidates are few: the
+// claim / decide / role phases of every round are separated by block
+// barriers, and the loop ends when no candidate is undecided (at most one
+// round per candidate, since every round decides the earliest undecided
+// one).  *stat receives the number of rounds, or -1 if that bound was hit.
+constexpr int DEC_SMALL = 8192;
+constexpr int DEC_THREADS = 1024;
+
+__global__ void __launch_bounds__(DEC_THREADS) k_dec_block(int32_t nc, int32_t* cst, const int32_t* cv,
+                                                           const int32_t* src, const int32_t* dst,
+                                                           const int64_t* ghi, const uint64_t* glo, int32_t* role,
+                                                           int32_t* best, int32_t* bv, int32_t* bsrc, int32_t* bdst,
+                                                           int32_t* nb, int32_t* stat) {
+  __shared__ int32_t left;
+  const int tid = threadIdx.x;
+  for (int32_t i = tid; i < nc; i += DEC_THREADS) cst[i] = 0;
+  __syncthreads();
+  int32_t rounds = 0;
+  bool ok = true;
+  for (;;) {
+    for (int32_t i = tid; i < nc; i += DEC_THREADS) {
+      if (cst[i] != 0) continue;
+      if (role[src[i]] == 0) claim(best, src[i], i, ghi, glo, cv);
+      if (role[dst[i]] == 0) claim(best, dst[i], i, ghi, glo, cv);
+    }
+    if (tid == 0) left = 0;
+    __syncthreads();
+    int32_t mine = 0;
+    for (int32_t i = tid; i < nc; i += DEC_THREADS) {
+      if (cst[i] != 0) continue;
+      const int32_t ra = role[src[i]], rb = role[dst[i]];
+      const bool da = ra != 0 || best[src[i]] == i;
+      const bool db = rb != 0 || best[dst[i]] == i;
+      if (da && db) cst[i] = (ra != 2 && rb != 1) ? 3 : 2;
+      else ++mine;
+    }
+    if (mine) atomicAdd(&left, mine);
+    __syncthreads();
+    for (int32_t i = tid; i < nc; i += DEC_THREADS) {
+      best[src[i]] = -1;
+      best[dst[i]] = -1;
+      if (cst[i] == 3) {
+        role[src[i]] = 1;
+        role[dst[i]] = 2;
+        cst[i] = 1;
+      }
+    }
+    ++rounds;
+    __syncthreads();
+    const int32_t l = left;
+    __syncthreads();  // every thread has read `left` before it is reset
+    if (l == 0) break;
+    if (rounds > nc + 1) {
+      ok = false;
+      break;
+    }
+  }
+  for (int32_t i = tid; i < nc; i += DEC_THREADS) {
+    role[src[i]] = 0;
+    role[dst[i]] = 0;
+    if (cst[i] == 1) {
+      const int32_t p = atomicAdd(nb, 1);
+      bv[p] = cv[i];
+      bsrc[p] = src[i];
+      bdst[p] = dst[i];
+    }
+  }
+  if (tid == 0) *stat = ok ? rounds : -1;
+}
+
 // ---------------------------------------------------------------- commit (move)
 __global__ void k_commit_mark(int32_t nb, const int32_t* bv, const int32_t* bsrc, const int32_t* bdst,
                               int32_t* lab, int32_t* oldlab, int32_t* stB, int32_t epB, int32_t* stT, int32_t epT,
@@ -841,12 +911,25 @@ int32_t sweep(ldl_ctx& c, int r, int mode, const int32_t* list, int idx_n, int64
 
 int32_t decouple(ldl_ctx& c, int32_t nc) {
   if (nc <= 0) return 0;
+  if (nc <= DEC_SMALL) {
+    zero_cnt(c, K_B);
+    k_dec_block<<<1, DEC_THREADS, 0, c.s>>>(nc, c.cst.p, c.cv.p, c.csrc.p, c.cdst.p, c.cghi.p, c.cglo.p, c.role.p,
+                                            c.best.p, c.bv.p, c.bsrc.p, c.bdst.p, c.dcnt + K_B, c.dcnt + K_UNDEC);
+    CKL("k_dec_block");
+    int32_t out[2];  // K_B, K_UNDEC are adjacent
+    ++c.syncs;
+    CK(cudaMemcpyAsync(out, c.dcnt + K_B, sizeof(out), cudaMemcpyDeviceToHost, c.s));
+    CK(cudaStreamSynchronize(c.s));
+    if (out[1] < 0) ldl_throw(LDL_E_INVALID, "internal: decoupling did not converge");
+    c.res.decouple_rounds += out[1];
+    return out[0];
+  }
   CK(cudaMemsetAsync(c.cst.p, 0, sizeof(int32_t) * (size_t)nc, c.s));
   const int g = grid_for(nc, TPB);
   int rounds = 0;
   while (true) {
     // a few rounds per host check: rounds past completion change nothing
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < 2; ++k) {
       k_dec_claim<<<g, TPB, 0, c.s>>>(nc, c.cst.p, c.csrc.p, c.cdst.p, c.cghi.p, c.cglo.p, c.cv.p, c.role.p,
                                       c.best.p);
       CKL("k_dec_claim");
@@ -857,8 +940,8 @@ int32_t decouple(ldl_ctx& c, int32_t nc) {
       CKL("k_dec_roles");
       ++rounds;
     }
+    c.res.decouple_rounds += 2;
     if (rd_cnt(c, K_UNDEC) == 0) break;
-    c.res.decouple_rounds += 4;
     if (rounds > 4 * (int64_t)nc + 64) ldl_throw(LDL_E_INVALID, "internal: decoupling did not converge");
   }
   zero_cnt(c, K_B);
