@@ -248,12 +248,17 @@ int64_t ldl_launch_count(void);
 /*
  * Per-kernel statistics of the BestMove / BestRef sweep kernels, measured
  * with CUDA events on the context's stream while enabled (enabling resets
- * them).  out[12] = {launches, ms, algorithmic bytes, entries} for the warp
- * bin (one warp per low-degree node), the block bin (one block per mid-degree
- * node) and the hub path (hub rows spread over the GPU), in that order.  Algorithmic bytes
- * count, per adjacency entry, the neighbour id, its weight and its label
- * (refinement: also its parent); per swept node its offsets, lengths, label
- * and strengths; per evaluated (node, target) pair the target's totals.
+ * them).  out[16] = {launches, ms, algorithmic bytes, entries} for, in this
+ * order, k_sweep_warp (one warp per node of <= 96 entries), k_sweep_block with
+ * 128 threads (<= 384 entries), k_sweep_block with 256 threads (<= 2048) and
+ * the hub path (rows spread over the GPU; four kernels per sweep).
+ * Algorithmic bytes count, per adjacency entry, the neighbour id, its weight
+ * and its label (refinement: also its parent); per swept node its offsets,
+ * lengths, label and strengths; per evaluated (node, target) pair the
+ * target's totals.  Collection adds no host synchronisation: events and
+ * device counters are resolved by ldl_get_kernel_stats, which waits for the
+ * context's stream.  Both return LDL_E_INVALID on a null pointer and
+ * LDL_E_CUDA on a CUDA error.
  */
 ldl_status ldl_set_kernel_stats(ldl_ctx* ctx, int32_t on);
 ldl_status ldl_get_kernel_stats(const ldl_ctx* ctx, double* out);

@@ -240,9 +240,9 @@ struct DevScalars {
   int64_t scanned;  // adjacency entries scanned
   int64_t err_key;  // packed (index << 8 | status) of the first failing update
   int64_t pool_top;
-  int64_t sw_entries[3];  // sweep kernels (0: warp bin, 1: block bin, 2: hub path): entries read
-  int64_t sw_pairs[3];    // distinct (node, target) pairs evaluated
-  int64_t sw_nodes[3];    // nodes swept
+  int64_t sw_entries[4];  // sweep kernels (0: warp bin, 1: 128-thread block bin, 2: 256-thread block bin,
+                          // 3: hub path): adjacency entries read since statistics were enabled
+  int64_t sw_bytes[4];    // algorithmic bytes of the same sweeps
   int32_t cnt[16];  // list counters
   int32_t undecided;
   int32_t pad;

@@ -97,8 +97,9 @@ struct ldl_ctx {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr, ev3 = nullptr;
   // per-kernel statistics of the sweep kernels (enabled by ldl_set_kernel_stats)
   int kstats = 0;
-  cudaEvent_t kev[4] = {nullptr, nullptr, nullptr, nullptr};
-  double ks_launch[3] = {0, 0, 0}, ks_ms[3] = {0, 0, 0}, ks_bytes[3] = {0, 0, 0}, ks_entries[3] = {0, 0, 0};
+  std::vector<cudaEvent_t> kev;  // five events per sweep since enabling, bracketing the four groups
+  size_t kev_used = 0;
+  double ks_launch[4] = {0, 0, 0, 0};
   int64_t syncs = 0;  // host synchronisations in the current batch
   std::string err;
 

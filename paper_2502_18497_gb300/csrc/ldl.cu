@@ -157,10 +157,9 @@ static void free_all(ldl_ctx& c) {
   if (c.ev2) cudaEventDestroy(c.ev2);
   if (c.ev3) cudaEventDestroy(c.ev3);
   c.ev0 = c.ev1 = c.ev2 = c.ev3 = nullptr;
-  for (auto& ev : c.kev) {
-    if (ev) cudaEventDestroy(ev);
-    ev = nullptr;
-  }
+  for (auto& ev : c.kev) cudaEventDestroy(ev);
+  c.kev.clear();
+  c.kev_used = 0;
 }
 
 // ---------------------------------------------------------------- move loop
@@ -427,7 +426,6 @@ ldl_status ldl_create(const ldl_params* params, int64_t n, int64_t nnz, const in
     CK(cudaEventCreate(&c->ev1));
     CK(cudaEventCreate(&c->ev2));
     CK(cudaEventCreate(&c->ev3));
-    for (auto& ev : c->kev) CK(cudaEventCreate(&ev));
     c->lv.resize(p.L + 1);
     alloc_globals(*c);
     level_alloc(*c, 0);
@@ -637,18 +635,40 @@ ldl_status ldl_copy_changed(const ldl_ctx* cc, int32_t* ids, int32_t* labels) {
 
 ldl_status ldl_set_kernel_stats(ldl_ctx* c, int32_t on) {
   if (!c) return LDL_E_INVALID;
-  c->kstats = on ? 1 : 0;
-  for (int k = 0; k < 3; ++k) c->ks_launch[k] = c->ks_ms[k] = c->ks_bytes[k] = c->ks_entries[k] = 0;
+  try {
+    c->kstats = on ? 1 : 0;
+    c->kev_used = 0;
+    for (int k = 0; k < 4; ++k) c->ks_launch[k] = 0;
+    CK(cudaMemsetAsync(c->d_sc->sw_entries, 0, sizeof(int64_t) * 8, c->s));
+    CK(cudaStreamSynchronize(c->s));
+  } catch (const LdlError& e) {
+    c->err = e.msg;
+    return e.st;
+  }
   return LDL_OK;
 }
 
 ldl_status ldl_get_kernel_stats(const ldl_ctx* c, double* out) {
   if (!c || !out) return LDL_E_INVALID;
-  for (int k = 0; k < 3; ++k) {
-    out[4 * k + 0] = c->ks_launch[k];
-    out[4 * k + 1] = c->ks_ms[k];
-    out[4 * k + 2] = c->ks_bytes[k];
-    out[4 * k + 3] = c->ks_entries[k];
+  try {
+    double ms[4] = {0, 0, 0, 0};
+    if (c->kev_used) CK(cudaEventSynchronize(c->kev[c->kev_used - 1]));
+    for (size_t i = 0; i + 5 <= c->kev_used; i += 5)
+      for (int k = 0; k < 4; ++k) {
+        float t = 0;
+        CK(cudaEventElapsedTime(&t, c->kev[i + k], c->kev[i + k + 1]));
+        ms[k] += t;
+      }
+    DevScalars h;
+    CK(cudaMemcpy(&h, c->d_sc, sizeof(DevScalars), cudaMemcpyDeviceToHost));
+    for (int k = 0; k < 4; ++k) {
+      out[4 * k + 0] = c->ks_launch[k];
+      out[4 * k + 1] = ms[k];
+      out[4 * k + 2] = (double)h.sw_bytes[k];
+      out[4 * k + 3] = (double)h.sw_entries[k];
+    }
+  } catch (const LdlError& e) {
+    return e.st;
   }
   return LDL_OK;
 }

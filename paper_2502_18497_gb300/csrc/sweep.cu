@@ -136,6 +136,18 @@ __device__ inline i128 gain_of(int32_t key, int64_t acc, int64_t wa, int32_t a, 
   }
 }
 
+// Algorithmic bytes of a sweep (the minimum a sweep must move): per adjacency
+// entry the neighbour id, its weight and its label (refinement: also its
+// parent); per swept node its offsets, lengths, label and strengths; per
+// evaluated (node, target) pair the target's totals.
+template <class WT, int MODE>
+__device__ inline int64_t sweep_bytes(bool directed, int64_t entries, int64_t nodes, int64_t pairs) {
+  const int64_t per_entry = 4 + sizeof(WT) + 4 + (MODE == 1 ? 4 : 0);
+  const int64_t per_node = (8 + 4) * (directed ? 2 : 1) + 4 + 16 + 4;
+  const int64_t per_pair = directed ? 16 : 8;
+  return per_entry * entries + per_node * nodes + per_pair * pairs;
+}
+
 template <class WT>
 __device__ inline void emit_cand(const SweepArgs<WT>& A, int32_t v, int32_t src, const Best& b) {
   const int32_t p = atomicAdd(A.ncand, 1);
@@ -199,8 +211,8 @@ __global__ void __launch_bounds__(TPB) k_sweep_warp(SweepArgs<WT> A, const int32
       atomic_add_i64(A.scanned, scanned);
       atomic_add_i64(&A.stats->sw_entries[0], scanned);
     }
-    if (pairs) atomic_add_i64(&A.stats->sw_pairs[0], pairs);
-    if (nodes) atomic_add_i64(&A.stats->sw_nodes[0], nodes);
+    if (scanned | pairs | nodes)
+      atomic_add_i64(&A.stats->sw_bytes[0], sweep_bytes<WT, MODE>(A.directed, scanned, nodes, pairs));
   }
 }
 
@@ -248,7 +260,7 @@ __global__ void __launch_bounds__(NT) k_sweep_block(SweepArgs<WT> A, const int32
     pairs = warp_sum_i64(pairs);
     if (lane == 0) {
       wb[wid] = b;
-      if (pairs) atomic_add_i64(&A.stats->sw_pairs[1], pairs);
+      if (pairs) atomic_add_i64(&A.stats->sw_bytes[NT == 128 ? 1 : 2], sweep_bytes<WT, MODE>(A.directed, 0, 0, pairs));
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -258,8 +270,8 @@ __global__ void __launch_bounds__(NT) k_sweep_block(SweepArgs<WT> A, const int32
       if (r.have) emit_cand(A, v, MODE == 0 ? a : v, r);
       const int64_t ent = (int64_t)A.out.len[v] + (A.directed ? A.in.len[v] : 0);
       atomic_add_i64(A.scanned, ent);
-      atomic_add_i64(&A.stats->sw_entries[1], ent);
-      atomic_add_i64(&A.stats->sw_nodes[1], 1);
+      atomic_add_i64(&A.stats->sw_entries[NT == 128 ? 1 : 2], ent);
+      atomic_add_i64(&A.stats->sw_bytes[NT == 128 ? 1 : 2], sweep_bytes<WT, MODE>(A.directed, ent, 1, 0));
     }
     __syncthreads();
   }
@@ -336,7 +348,8 @@ __global__ void k_hub_acc(SweepArgs<WT> A, ChunkMap m, const int64_t* loff, cons
   }
   if (lane == 0 && scanned) {
     atomic_add_i64(A.scanned, scanned);
-    atomic_add_i64(&A.stats->sw_entries[2], scanned);
+    atomic_add_i64(&A.stats->sw_entries[3], scanned);
+    atomic_add_i64(&A.stats->sw_bytes[3], sweep_bytes<WT, MODE>(A.directed, scanned, 0, 0));
   }
 }
 
@@ -382,7 +395,7 @@ __global__ void __launch_bounds__(TPB) k_hub_eval(SweepArgs<WT> A, const int32_t
     pairs = warp_sum_i64(pairs);
     if (lane == 0) {
       wb[wid] = b;
-      if (pairs) atomic_add_i64(&A.stats->sw_pairs[2], pairs);
+      if (pairs) atomic_add_i64(&A.stats->sw_bytes[3], sweep_bytes<WT, MODE>(A.directed, 0, 0, pairs));
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -413,7 +426,7 @@ __global__ void k_hub_final(SweepArgs<WT> A, const int32_t* hubs, int32_t nh, co
     b = warp_best(b);
     if (lane == 0) {
       const int32_t v = hubs[i];
-      atomic_add_i64(&A.stats->sw_nodes[2], 1);
+      atomic_add_i64(&A.stats->sw_bytes[3], sweep_bytes<WT, MODE>(A.directed, 0, 1, 0));
       if (b.have) emit_cand(A, v, MODE == 0 ? A.lab[v] : v, b);
     }
   }
@@ -777,6 +790,18 @@ void union_into(ldl_ctx& c, const int32_t* list, int idx_n, int32_t* stamp, int3
   CKL("k_union");
 }
 
+// the next five statistics events of the context, created on first use
+static cudaEvent_t* kstats_events(ldl_ctx& c) {
+  while (c.kev.size() < c.kev_used + 5) {
+    cudaEvent_t e;
+    CK(cudaEventCreate(&e));
+    c.kev.push_back(e);
+  }
+  cudaEvent_t* e = c.kev.data() + c.kev_used;
+  c.kev_used += 5;
+  return e;
+}
+
 template <class WT, int MODE>
 static int32_t sweep_t(ldl_ctx& c, int r, Adj<WT> out, Adj<WT> in, const int32_t* list, int idx_n, int64_t n_hint) {
   LevelState& L = c.lv[r];
@@ -806,9 +831,6 @@ static int32_t sweep_t(ldl_ctx& c, int r, Adj<WT> out, Adj<WT> in, const int32_t
   A.ncand = c.dcnt + K_CAND;
   A.scanned = &c.d_sc->scanned;
   A.stats = c.d_sc;
-  if (c.kstats) {
-    CK(cudaMemsetAsync(c.d_sc->sw_entries, 0, sizeof(int64_t) * 9, c.s));
-  }
   zero_cnt(c, K_CAND);
   zero_cnt(c, K_SMALL);
   zero_cnt(c, K_MID);
@@ -826,25 +848,27 @@ static int32_t sweep_t(ldl_ctx& c, int r, Adj<WT> out, Adj<WT> in, const int32_t
   CK(cudaMemcpyAsync(&cm2, c.dcnt + K_MID2, sizeof(int32_t), cudaMemcpyDeviceToHost, c.s));
   CK(cudaMemcpyAsync(&tab, &c.d_sc->need, sizeof(int64_t), cudaMemcpyDeviceToHost, c.s));
   CK(cudaStreamSynchronize(c.s));
-  if (c.kstats) CK(cudaEventRecord(c.kev[0], c.s));
+  cudaEvent_t* kev = c.kstats ? kstats_events(c) : nullptr;
+  if (kev) CK(cudaEventRecord(kev[0], c.s));
   if (counts[0] > 0) {
     k_sweep_warp<WT, MODE><<<grid_for((int64_t)counts[0] * 32, TPB), TPB, 0, c.s>>>(A, c.binS.p, c.dcnt + K_SMALL);
     CKL("k_sweep_warp");
   }
-  if (c.kstats) CK(cudaEventRecord(c.kev[1], c.s));
+  if (kev) CK(cudaEventRecord(kev[1], c.s));
   if (counts[1] > 0) {
     const size_t sm = (sizeof(int64_t) + sizeof(int32_t)) * 1024;
     k_sweep_block<WT, MODE, 128, 1024><<<grid_for(counts[1], 1, 152 * 16), 128, sm, c.s>>>(A, c.binM.p,
                                                                                          c.dcnt + K_MID);
     CKL("k_sweep_block(mid1)");
   }
+  if (kev) CK(cudaEventRecord(kev[2], c.s));
   if (cm2 > 0) {
     const size_t sm = (sizeof(int64_t) + sizeof(int32_t)) * HB;
     CK(cudaFuncSetAttribute(k_sweep_block<WT, MODE, 256, HB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     k_sweep_block<WT, MODE, 256, HB><<<grid_for(cm2, 1, 152 * 4), 256, sm, c.s>>>(A, c.binM2.p, c.dcnt + K_MID2);
     CKL("k_sweep_block(mid2)");
   }
-  if (c.kstats) CK(cudaEventRecord(c.kev[2], c.s));
+  if (kev) CK(cudaEventRecord(kev[3], c.s));
   if (counts[2] > 0) {
     const int32_t nh = counts[2];
     c.gkeys.reserve(tab, c.s);
@@ -875,28 +899,14 @@ static int32_t sweep_t(ldl_ctx& c, int r, Adj<WT> out, Adj<WT> in, const int32_t
                                                                            c.pb_lo.p, c.pb_c.p);
     CKL("k_hub_final");
   }
-  if (c.kstats) {
-    CK(cudaEventRecord(c.kev[3], c.s));
-    CK(cudaEventSynchronize(c.kev[3]));
-    float ms[3] = {0, 0, 0};
-    for (int k = 0; k < 3; ++k) CK(cudaEventElapsedTime(&ms[k], c.kev[k], c.kev[k + 1]));
-    DevScalars h;
-    CK(cudaMemcpy(&h, c.d_sc, sizeof(DevScalars), cudaMemcpyDeviceToHost));
-    // algorithmic bytes: per entry the neighbour id, its weight and its
-    // label (refine: also its parent); per node offsets, lengths, label and
-    // strengths; per evaluated pair the target's two totals
-    const double per_entry = 4.0 + sizeof(WT) + 4.0 + (MODE == 1 ? 4.0 : 0.0);
-    const double per_node = (8.0 + 4.0) * (c.directed ? 2 : 1) + 4.0 + 16.0 + 4.0;
-    const double per_pair = c.directed ? 16.0 : 8.0;
-    const int launches[3] = {counts[0] > 0, (counts[1] > 0) + (cm2 > 0), counts[2] > 0 ? 4 : 0};
-    for (int k = 0; k < 3; ++k) {
-      if (!launches[k]) continue;
-      c.ks_launch[k] += launches[k];
-      c.ks_ms[k] += ms[k];
-      c.ks_entries[k] += (double)h.sw_entries[k];
-      c.ks_bytes[k] += per_entry * (double)h.sw_entries[k] + per_node * (double)h.sw_nodes[k] +
-                       per_pair * (double)h.sw_pairs[k];
-    }
+  if (kev) {
+    // times and bytes are resolved when the statistics are read, so that
+    // collecting them adds no host synchronisation to the sweep
+    CK(cudaEventRecord(kev[4], c.s));
+    c.ks_launch[0] += counts[0] > 0;
+    c.ks_launch[1] += counts[1] > 0;
+    c.ks_launch[2] += cm2 > 0;
+    c.ks_launch[3] += counts[2] > 0 ? 4 : 0;
   }
   return rd_cnt(c, K_CAND);
 }

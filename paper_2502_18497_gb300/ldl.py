@@ -276,10 +276,10 @@ class LDL:
         self._check(load().ldl_set_kernel_stats(self._h, int(on)))
 
     def kernel_stats(self) -> dict:
-        t = np.zeros(12, np.float64)
+        t = np.zeros(16, np.float64)
         self._check(load().ldl_get_kernel_stats(self._h, _ptr(t)))
         out = {}
-        for k, name in enumerate(("sweep_warp", "sweep_block", "sweep_hub")):
+        for k, name in enumerate(("sweep_warp", "sweep_block128", "sweep_block256", "sweep_hub")):
             out[name] = dict(launches=t[4 * k], ms=t[4 * k + 1], bytes=t[4 * k + 2], entries=t[4 * k + 3])
         return out
 
