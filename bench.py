@@ -466,8 +466,9 @@ def main():
     achieved = k["bytes"] / (k["ms"] / 1e3) / 1e9 if k["ms"] > 0 else 0.0
     sha = hashlib.sha256(open(os.path.join(ROOT, "paper_2502_18497_gb300", "csrc", "sweep.cu"), "rb").read()).hexdigest()
     traffic = NCU_TRAFFIC["bytes_per_launch"] if NCU_TRAFFIC["sha256"] == sha and NCU_TRAFFIC["kernel"] == dom else None
-    names = {"sweep_warp": "k_sweep_warp", "sweep_block128": "k_sweep_block<..., 128, 1024>",
-             "sweep_block256": "k_sweep_block<..., 256, 4096>", "sweep_hub": "hub path (k_hub_acc + k_hub_eval)"}
+    names = {"sweep_group8": "k_sweep_group<..., 8>", "sweep_warp": "k_sweep_group<..., 32>",
+             "sweep_block128": "k_sweep_block<..., 128, 1024>", "sweep_block256": "k_sweep_block<..., 256, 4096>",
+             "sweep_hub": "hub path (k_hub_acc + k_hub_eval + k_hub_final)"}
     roofline = {"bound": "hbm", "kernel": names.get(dom, dom), "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": peak_src, "traffic": traffic,
                 "launches": k["launches"], "ms_total": k["ms"], "algorithmic_bytes_per_launch":

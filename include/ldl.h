@@ -248,10 +248,12 @@ int64_t ldl_launch_count(void);
 /*
  * Per-kernel statistics of the BestMove / BestRef sweep kernels, measured
  * with CUDA events on the context's stream while enabled (enabling resets
- * them).  out[16] = {launches, ms, algorithmic bytes, entries} for, in this
- * order, k_sweep_warp (one warp per node of <= 96 entries), k_sweep_block with
- * 128 threads (<= 384 entries), k_sweep_block with 256 threads (<= 2048) and
- * the hub path (rows spread over the GPU; four kernels per sweep).
+ * them).  out[20] = {launches, ms, algorithmic bytes, entries} for, in this
+ * order, k_sweep_group with 8-lane groups (one group per node of <= 24
+ * entries), k_sweep_group with whole warps (<= 96 entries), k_sweep_block
+ * with 128 threads (<= 384 entries), k_sweep_block with 256 threads
+ * (<= 2048) and the hub path (rows spread over the GPU; four kernels per
+ * sweep).
  * Algorithmic bytes count, per adjacency entry, the neighbour id, its weight
  * and its label (refinement: also its parent); per swept node its offsets,
  * lengths, label and strengths; per evaluated (node, target) pair the

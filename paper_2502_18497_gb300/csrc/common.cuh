@@ -106,6 +106,24 @@ __device__ inline i128 shfl_i128(i128 v, int src) {
   return i128_of(hi, lo);
 }
 
+// Width-w variants: lanes are split into segments of w (a power of two);
+// shuffles stay inside a lane's own segment.
+__device__ inline i128 shfl_down_i128_w(i128 v, int d, int w) {
+  uint64_t lo = (uint64_t)v;
+  int64_t hi = (int64_t)(v >> 64);
+  lo = __shfl_down_sync(0xffffffffu, lo, d, w);
+  hi = __shfl_down_sync(0xffffffffu, hi, d, w);
+  return i128_of(hi, lo);
+}
+
+__device__ inline i128 shfl_i128_w(i128 v, int src, int w) {
+  uint64_t lo = (uint64_t)v;
+  int64_t hi = (int64_t)(v >> 64);
+  lo = __shfl_sync(0xffffffffu, lo, src, w);
+  hi = __shfl_sync(0xffffffffu, hi, src, w);
+  return i128_of(hi, lo);
+}
+
 __device__ inline i128 warp_sum_i128(i128 v) {
   for (int d = 16; d > 0; d >>= 1) v += shfl_down_i128(v, d);
   return v;  // valid in lane 0
@@ -147,6 +165,23 @@ __device__ inline Best warp_best(Best x) {
   x.g = shfl_i128(x.g, 0);
   x.c = __shfl_sync(0xffffffffu, x.c, 0);
   x.have = __shfl_sync(0xffffffffu, x.have, 0);
+  return x;
+}
+
+// The same argmax over each segment of G lanes (every lane of the warp takes
+// part; the result lands in every lane of the segment).
+template <int G>
+__device__ inline Best group_best(Best x) {
+  for (int d = G / 2; d > 0; d >>= 1) {
+    Best o;
+    o.g = shfl_down_i128_w(x.g, d, G);
+    o.c = __shfl_down_sync(0xffffffffu, x.c, d, G);
+    o.have = __shfl_down_sync(0xffffffffu, x.have, d, G);
+    if (best_better(o, x)) x = o;
+  }
+  x.g = shfl_i128_w(x.g, 0, G);
+  x.c = __shfl_sync(0xffffffffu, x.c, 0, G);
+  x.have = __shfl_sync(0xffffffffu, x.have, 0, G);
   return x;
 }
 
@@ -230,6 +265,8 @@ struct SlackCSR {
 
 // ---------------------------------------------------------------- scalar block
 // One small device struct read back in a single copy.
+constexpr int KS_GROUPS = 5;  // sweep kernel groups with their own statistics
+
 struct DevScalars {
   I128 dq;          // numerator change of the current mini-batch
   I128 dp;          // change of sum_C K_out K_in
@@ -240,9 +277,10 @@ struct DevScalars {
   int64_t scanned;  // adjacency entries scanned
   int64_t err_key;  // packed (index << 8 | status) of the first failing update
   int64_t pool_top;
-  int64_t sw_entries[4];  // sweep kernels (0: warp bin, 1: 128-thread block bin, 2: 256-thread block bin,
-                          // 3: hub path): adjacency entries read since statistics were enabled
-  int64_t sw_bytes[4];    // algorithmic bytes of the same sweeps
+  int64_t sw_entries[KS_GROUPS];  // sweep kernel groups (0: 8-lane groups, 1: warps, 2: 128-thread blocks,
+                                  // 3: 256-thread blocks, 4: hub path): adjacency entries read since
+                                  // statistics were enabled
+  int64_t sw_bytes[KS_GROUPS];    // algorithmic bytes of the same sweeps
   int32_t cnt[16];  // list counters
   int32_t undecided;
   int32_t pad;

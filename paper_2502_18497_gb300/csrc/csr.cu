@@ -123,16 +123,40 @@ __device__ inline int64_t find_seg(const int64_t* pre, int64_t nseg, int64_t t) 
   return lo;
 }
 
+// last s in [lo, hi] with pre[s] <= t
+__device__ inline int64_t seg_in(const int64_t* pre, int64_t lo, int64_t hi, int64_t t) {
+  while (lo < hi) {
+    const int64_t mid = (lo + hi + 1) >> 1;
+    if (pre[mid] <= t) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Items [0, total) split into segments by the exclusive scan pre.  Each warp
+// takes runs of SEG_RUN consecutive items: two warp-uniform searches bound the
+// run's segments, and each item then searches only that narrow range.
+constexpr int SEG_RUN = 256;
+#define FOR_SEG_ITEMS(t, s, pre, nseg, total)                                                       \
+  const int64_t warp_ = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;                     \
+  const int64_t nwarps_ = ((int64_t)gridDim.x * blockDim.x) >> 5;                                   \
+  for (int64_t c0_ = warp_ * SEG_RUN; c0_ < (total); c0_ += nwarps_ * SEG_RUN) {                   \
+    const int64_t c1_ = min(c0_ + SEG_RUN, (int64_t)(total)) - 1;                                   \
+    const int64_t slo_ = find_seg(pre, nseg, c0_), shi_ = find_seg(pre, nseg, c1_);                 \
+    for (int64_t t = c0_ + (threadIdx.x & 31); t <= c1_; t += 32) {                                 \
+      const int64_t s = seg_in(pre, slo_, shi_, t);
+#define END_SEG_ITEMS \
+  }                   \
+  }
+
 template <class WT>
 __global__ void k_copy_scratch(const int64_t* off, const int64_t* seg_row, int64_t nseg, const int64_t* soff,
                                int64_t total, const int32_t* col, const WT* w, int32_t* scol, WT* sw) {
-  GRID_STRIDE(t, total) {
-    const int64_t s = find_seg(soff, nseg, t);
+  FOR_SEG_ITEMS(t, s, soff, nseg, total)
     const int64_t row = seg_row[s];
     const int64_t k = t - soff[s];
     scol[t] = col[off[row] + k];
     sw[t] = w[off[row] + k];
-  }
+  END_SEG_ITEMS
 }
 
 __global__ void k_relocate(int64_t nseg, const int64_t* seg_row, const int32_t* newcap, int64_t* off, int32_t* cap,
@@ -155,8 +179,7 @@ __global__ void k_scatter_rows(int64_t nseg, int64_t nrec, const int64_t* seg_st
                                const int32_t* fins, const int64_t* pins, const int64_t* pdel, int bshift,
                                const int64_t* off, int32_t* col, WT* w) {
   const u64 cmask = (((u64)1) << bshift) - 1;
-  GRID_STRIDE(t, total) {
-    const int64_t s = find_seg(woff, nseg, t);
+  FOR_SEG_ITEMS(t, s, woff, nseg, total)
     const int64_t a = seg_start[s];
     const int64_t b = s + 1 < nseg ? seg_start[s + 1] : nrec;
     const int64_t row = seg_row[s];
@@ -189,7 +212,7 @@ __global__ void k_scatter_rows(int64_t nseg, int64_t nrec, const int64_t* seg_st
       w[off[row] + dst] = (WT)delta[J];
       (void)fins;
     }
-  }
+  END_SEG_ITEMS
 }
 
 __global__ void k_set_len(int64_t nseg, int64_t nrec, const int64_t* seg_start, const int64_t* seg_row,
@@ -379,7 +402,7 @@ void csr_apply(SlackCSR<WT>& g, const u64* keys, const int64_t* delta, int64_t n
     DBuf<WT>& sw = S.template sw_of<WT>();
     sw.reserve(stotal + 1, s);
     if (stotal > 0) {
-      k_copy_scratch<WT><<<grid_for(stotal, TPB), TPB, 0, s>>>(g.off.p, S.segrow.p, nseg, S.soff.p, stotal, g.col.p,
+      k_copy_scratch<WT><<<grid_for((stotal + 7) / 8, TPB), TPB, 0, s>>>(g.off.p, S.segrow.p, nseg, S.soff.p, stotal, g.col.p,
                                                                g.w.p, S.scol.p, sw.p);
       CKL("k_copy_scratch");
     }
@@ -389,7 +412,7 @@ void csr_apply(SlackCSR<WT>& g, const u64* keys, const int64_t* delta, int64_t n
       CKL("k_relocate");
       g.pool_top += need;
     }
-    k_scatter_rows<WT><<<grid_for(wtotal, TPB), TPB, 0, s>>>(nseg, nrec, S.seg.p, S.segrow.p, S.woff.p, S.soff.p,
+    k_scatter_rows<WT><<<grid_for((wtotal + 7) / 8, TPB), TPB, 0, s>>>(nseg, nrec, S.seg.p, S.segrow.p, S.woff.p, S.soff.p,
                                                              wtotal, S.scol.p, sw.p, keys, delta, S.lb.p, S.fins.p,
                                                              S.pins.p, S.pdel.p, bshift, g.off.p, g.col.p, g.w.p);
     CKL("k_scatter_rows");

@@ -108,7 +108,7 @@ static void alloc_globals(ldl_ctx& c) {
   }
   DBuf<int32_t>* ls[] = {&c.lU, &c.lS, &c.lUstar, &c.lMv, &c.lM0, &c.lD, &c.lC, &c.lR, &c.lR2, &c.lX, &c.lT,
                          &c.lE, &c.lE2, &c.lCh, &c.lChg, &c.lTmp, &c.cv, &c.csrc, &c.cdst, &c.cst, &c.bv,
-                         &c.bsrc, &c.bdst, &c.oldlab, &c.par_old, &c.lab_before, &c.binS, &c.binM, &c.binM2, &c.binL};
+                         &c.bsrc, &c.bdst, &c.oldlab, &c.par_old, &c.lab_before, &c.binT, &c.binS, &c.binM, &c.binM2, &c.binL};
   for (auto* b : ls) b->exact(n);
   c.best.exact(n);
   CK(cudaMemsetAsync(c.best.p, 0xff, sizeof(int32_t) * (size_t)n, c.s));
@@ -138,7 +138,7 @@ static void free_all(ldl_ctx& c) {
                           &c.stE, &c.stCh, &c.lU, &c.lS, &c.lUstar, &c.lMv, &c.lM0, &c.lD, &c.lC, &c.lR,
                           &c.lR2, &c.lX, &c.lT, &c.lE, &c.lE2, &c.lCh, &c.lChg, &c.lTmp, &c.cv, &c.csrc,
                           &c.cdst, &c.cst, &c.bv, &c.bsrc, &c.bdst, &c.best, &c.role, &c.oldlab, &c.par_old,
-                          &c.lab_before, &c.binS, &c.binM, &c.binM2, &c.binL, &c.gkeys, &c.ndx, &c.ndx2};
+                          &c.lab_before, &c.binT, &c.binS, &c.binM, &c.binM2, &c.binL, &c.gkeys, &c.ndx, &c.ndx2};
   for (auto* b : b32) b->release();
   DBuf<u64>* bu[] = {&c.rk, &c.rv, &c.tk, &c.tv, &c.rk2, &c.rv2, &c.crk, &c.crv, &c.fk, &c.trk, &c.trv};
   for (auto* b : bu) b->release();
@@ -638,8 +638,8 @@ ldl_status ldl_set_kernel_stats(ldl_ctx* c, int32_t on) {
   try {
     c->kstats = on ? 1 : 0;
     c->kev_used = 0;
-    for (int k = 0; k < 4; ++k) c->ks_launch[k] = 0;
-    CK(cudaMemsetAsync(c->d_sc->sw_entries, 0, sizeof(int64_t) * 8, c->s));
+    for (int k = 0; k < KS_GROUPS; ++k) c->ks_launch[k] = 0;
+    CK(cudaMemsetAsync(c->d_sc->sw_entries, 0, sizeof(int64_t) * 2 * KS_GROUPS, c->s));
     CK(cudaStreamSynchronize(c->s));
   } catch (const LdlError& e) {
     c->err = e.msg;
@@ -651,17 +651,17 @@ ldl_status ldl_set_kernel_stats(ldl_ctx* c, int32_t on) {
 ldl_status ldl_get_kernel_stats(const ldl_ctx* c, double* out) {
   if (!c || !out) return LDL_E_INVALID;
   try {
-    double ms[4] = {0, 0, 0, 0};
+    double ms[KS_GROUPS] = {0, 0, 0, 0, 0};
     if (c->kev_used) CK(cudaEventSynchronize(c->kev[c->kev_used - 1]));
-    for (size_t i = 0; i + 5 <= c->kev_used; i += 5)
-      for (int k = 0; k < 4; ++k) {
+    for (size_t i = 0; i + KS_GROUPS + 1 <= c->kev_used; i += KS_GROUPS + 1)
+      for (int k = 0; k < KS_GROUPS; ++k) {
         float t = 0;
         CK(cudaEventElapsedTime(&t, c->kev[i + k], c->kev[i + k + 1]));
         ms[k] += t;
       }
     DevScalars h;
     CK(cudaMemcpy(&h, c->d_sc, sizeof(DevScalars), cudaMemcpyDeviceToHost));
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < KS_GROUPS; ++k) {
       out[4 * k + 0] = c->ks_launch[k];
       out[4 * k + 1] = ms[k];
       out[4 * k + 2] = (double)h.sw_bytes[k];

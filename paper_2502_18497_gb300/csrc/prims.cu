@@ -104,66 +104,118 @@ __global__ void k_scan_add(int64_t* out, int64_t n, const int64_t* bsum) {
 constexpr int RS_THREADS = 256;
 constexpr int RS_ITEMS = 8;
 constexpr int RS_TILE = RS_THREADS * RS_ITEMS;
+static_assert(RS_THREADS == 256 && SC_THREADS == 256, "one thread per digit");
 
 __global__ void k_rs_hist(const u64* keys, int64_t n, int shift, int64_t nb, int64_t* ghist) {
   __shared__ uint32_t h[256];
   for (int i = threadIdx.x; i < 256; i += RS_THREADS) h[i] = 0;
-  __syncthreads();
+  const int lane = threadIdx.x & 31;
   const int64_t base = (int64_t)blockIdx.x * RS_TILE;
-  for (int k = 0; k < RS_ITEMS; ++k) {
-    int64_t i = base + (int64_t)k * RS_THREADS + threadIdx.x;
-    if (i < n) atomicAdd(&h[(keys[i] >> shift) & 255], 1u);
+  int d[RS_ITEMS];
+  for (int k = 0; k < RS_ITEMS; ++k) {  // all loads in flight before any shuffle
+    const int64_t i = base + (int64_t)k * RS_THREADS + threadIdx.x;
+    d[k] = i < n ? (int)((keys[i] >> shift) & 255) : 256;
   }
   __syncthreads();
-  for (int d = threadIdx.x; d < 256; d += RS_THREADS) ghist[(int64_t)d * nb + blockIdx.x] = h[d];
+  for (int k = 0; k < RS_ITEMS; ++k) {
+    // one shared atomic per distinct digit of the warp (skewed digits collide)
+    const unsigned peers = __match_any_sync(0xffffffffu, d[k]);
+    if (d[k] < 256 && lane == __ffs(peers) - 1) atomicAdd(&h[d[k]], (uint32_t)__popc(peers));
+  }
+  __syncthreads();
+  for (int x = threadIdx.x; x < 256; x += RS_THREADS) ghist[(int64_t)x * nb + blockIdx.x] = h[x];
 }
 
-// goff holds tile-local exclusive prefixes of the digit-major histogram and
-// gbs the scanned tile sums: the global offset of entry i is
-// goff[i] + gbs[i / SC_TILE] (the scan's final add pass is folded in here).
-__global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const u64* keys, const u64* vals, u64* okeys,
-                                                           u64* ovals, int64_t n, int shift, int64_t nb,
-                                                           const int64_t* goff, const int64_t* gbs) {
-  __shared__ int64_t run[256];
-  __shared__ int32_t tot[256];
-  __shared__ int32_t wcnt[RS_THREADS / WARP][257];
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  for (int d = tid; d < 256; d += RS_THREADS) {
-    const int64_t i = (int64_t)d * nb + blockIdx.x;
-    run[d] = goff[i] + gbs[i / SC_TILE];
+// One block per digit: exclusive scan of the digit's tile counts in place,
+// and the digit's total.
+__global__ void __launch_bounds__(SC_THREADS) k_rs_dscan(int64_t* ghist, int64_t nb, int64_t* dtot) {
+  int64_t* row = ghist + (int64_t)blockIdx.x * nb;
+  int64_t carry = 0;
+  for (int64_t b0 = 0; b0 < nb; b0 += SC_THREADS) {
+    const int64_t b = b0 + threadIdx.x;
+    const int64_t v = b < nb ? row[b] : 0;
+    int64_t total;
+    const int64_t ex = block_excl_scan_i64(v, &total);
+    if (b < nb) row[b] = carry + ex;
+    carry += total;
   }
+  if (threadIdx.x == 0) dtot[blockIdx.x] = carry;
+}
+
+// One tile of RS_TILE pairs per block.  Each warp ranks a contiguous sub-tile
+// of RS_ITEMS * 32 pairs (rounds of 32, stable), the block turns the warp
+// counts into digit-sorted positions inside the tile, the tile is staged in
+// shared memory in digit order, and consecutive threads then write
+// consecutive output slots of each digit.  The global start of (digit d,
+// tile b) is the exclusive prefix of the digit totals dtot at d plus the
+// per-digit scanned tile count goff[d * nb + b].
+__global__ void __launch_bounds__(RS_THREADS, 4) k_rs_scatter(const u64* keys, const u64* vals, u64* okeys,
+                                                              u64* ovals, int64_t n, int shift, int64_t nb,
+                                                              const int64_t* goff, const int64_t* dtot) {
+  constexpr int NW = RS_THREADS / WARP;
+  __shared__ int32_t whist[NW][256];  // per-warp digit counts, then per-warp exclusive bases
+  __shared__ int32_t tstart[256];     // tile-local start of each digit
+  __shared__ int64_t gstart[256];     // global start of each digit for this tile
+  __shared__ u64 sk[RS_TILE];
+  __shared__ u64 sv[RS_TILE];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int64_t base = (int64_t)blockIdx.x * RS_TILE;
-  __syncthreads();
-  for (int ch = 0; ch < RS_ITEMS; ++ch) {
-    const int64_t i = base + (int64_t)ch * RS_THREADS + tid;
-    const bool valid = i < n;
-    const u64 key = valid ? keys[i] : 0;
-    const u64 val = valid ? vals[i] : 0;
-    const int d = valid ? (int)((key >> shift) & 255) : 256;
-    for (int x = lane; x < 257; x += 32) wcnt[wid][x] = 0;
-    __syncwarp();
+  const int tile_n = (int)min((int64_t)RS_TILE, n - base);
+  for (int d = lane; d < 256; d += 32) whist[wid][d] = 0;
+  {
+    int64_t total;
+    const int64_t dbase = block_excl_scan_i64(dtot[tid], &total);  // RS_THREADS == 256 digits
+    gstart[tid] = dbase + goff[(int64_t)tid * nb + blockIdx.x];
+  }
+  u64 key[RS_ITEMS], val[RS_ITEMS];
+  int rk[RS_ITEMS];
+  for (int k = 0; k < RS_ITEMS; ++k) {
+    const int li = wid * (RS_ITEMS * 32) + k * 32 + lane;
+    const bool valid = li < tile_n;
+    key[k] = valid ? keys[base + li] : 0;
+    val[k] = valid ? vals[base + li] : 0;
+  }
+  for (int k = 0; k < RS_ITEMS; ++k) {
+    const int li = wid * (RS_ITEMS * 32) + k * 32 + lane;
+    const int d = li < tile_n ? (int)((key[k] >> shift) & 255) : 256;
     const unsigned peers = __match_any_sync(0xffffffffu, d);
-    const int rank = __popc(peers & ((1u << lane) - 1u));
-    if (rank == 0) wcnt[wid][d] = __popc(peers);
-    __syncthreads();
-    if (tid < 256) {
-      int acc = 0;
-      for (int w = 0; w < RS_THREADS / WARP; ++w) {
-        int c = wcnt[w][tid];
-        wcnt[w][tid] = acc;
-        acc += c;
-      }
-      tot[tid] = acc;
+    const int before = d < 256 ? whist[wid][d] : 0;
+    rk[k] = before + __popc(peers & ((1u << lane) - 1u));
+    __syncwarp();
+    if (d < 256 && lane == __ffs(peers) - 1) whist[wid][d] = before + __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+  // thread d: exclusive scan of digit d over the warps, then over the digits
+  int cnt = 0;
+  {
+    const int d = tid;  // RS_THREADS == 256
+    for (int w = 0; w < NW; ++w) {
+      const int c = whist[w][d];
+      whist[w][d] = cnt;
+      cnt += c;
     }
-    __syncthreads();
-    if (valid) {
-      const int64_t pos = run[d] + wcnt[wid][d] + rank;
-      okeys[pos] = key;
-      ovals[pos] = val;
+  }
+  int64_t total;
+  const int64_t ds = block_excl_scan_i64(cnt, &total);
+  tstart[tid] = (int32_t)ds;
+  __syncthreads();
+  for (int k = 0; k < RS_ITEMS; ++k) {
+    const int li = wid * (RS_ITEMS * 32) + k * 32 + lane;
+    if (li < tile_n) {
+      const int d = (int)((key[k] >> shift) & 255);
+      const int p = tstart[d] + whist[wid][d] + rk[k];
+      sk[p] = key[k];
+      sv[p] = val[k];
     }
-    __syncthreads();
-    if (tid < 256) run[tid] += tot[tid];
-    __syncthreads();
+  }
+  __syncthreads();
+  for (int j = tid; j < tile_n; j += RS_THREADS) {
+    const u64 k = sk[j];
+    const int d = (int)((k >> shift) & 255);
+    const int64_t p = gstart[d] + (j - tstart[d]);
+    okeys[p] = k;
+    ovals[p] = sv[j];
   }
 }
 
@@ -240,18 +292,46 @@ __global__ void k_heads(const u64* keys, int64_t n, int32_t* flag) {
     flag[i] = (i == 0 || keys[i] != keys[i - 1]) ? 1 : 0;
 }
 
-__global__ void k_segsum(const u64* keys, const u64* vals, int64_t n, const int64_t* pos, const int32_t* flag,
-                         u64* ukeys, int64_t* usum) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    int64_t s = pos[i] + flag[i] - 1;  // segment index
-    if (flag[i]) ukeys[s] = keys[i];
-    atomic_add_i64(&usum[s], (int64_t)vals[i]);
+// Segment sums of sorted keys: each thread takes RBK_RUN consecutive pairs.
+// A segment that starts and ends inside the run is stored; a segment that
+// crosses a run boundary is added atomically at its head (usum is zeroed
+// first).  The head of a run's leading partial segment is found by a binary
+// search for the first equal key.
+constexpr int RBK_RUN = 8;
+__global__ void k_segsum(const u64* keys, const u64* vals, int64_t n, int64_t* usum) {
+  const int64_t nt = (n + RBK_RUN - 1) / RBK_RUN;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nt; r += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i0 = r * RBK_RUN, i1 = min(i0 + RBK_RUN, n);
+    int64_t head = i0;
+    if (i0 > 0 && keys[i0 - 1] == keys[i0]) {
+      int64_t lo = 0, hi = i0;
+      const u64 k = keys[i0];
+      while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (keys[mid] < k) lo = mid + 1; else hi = mid;
+      }
+      head = lo;
+    }
+    int64_t acc = 0;
+    for (int64_t i = i0; i < i1; ++i) {
+      if (i > i0 && keys[i] != keys[i - 1]) {
+        if (head < i0) atomic_add_i64(&usum[head], acc);
+        else usum[head] = acc;
+        head = i;
+        acc = 0;
+      }
+      acc += (int64_t)vals[i];
+    }
+    const bool open_end = i1 < n && keys[i1] == keys[i1 - 1];
+    if (head < i0 || open_end) atomic_add_i64(&usum[head], acc);
+    else usum[head] = acc;
   }
 }
 
-__global__ void k_nonzero(const int64_t* usum, int64_t nu, int32_t* flag) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nu; i += (int64_t)gridDim.x * blockDim.x)
-    flag[i] = usum[i] != 0;
+// flag = segment head with a nonzero sum
+__global__ void k_nonzero_heads(const u64* keys, const int64_t* usum, int64_t n, int32_t* flag) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    flag[i] = (i == 0 || keys[i] != keys[i - 1]) && usum[i] != 0;
 }
 
 __global__ void k_compact_pairs(const u64* ukeys, const int64_t* usum, int64_t nu, const int32_t* flag,
@@ -330,17 +410,13 @@ void radix_sort_pairs(u64*& keys, u64*& vals, u64*& tk, u64*& tv, int64_t n, int
   }
   const int64_t nb = (n + RS_TILE - 1) / RS_TILE;
   P.hist.reserve(256 * nb + 1, s);
-  P.hoff.reserve(256 * nb + 1, s);
+  P.bsum.reserve(256, s);
   for (int shift = lo_bit; shift < bits; shift += 8) {
     k_rs_hist<<<(unsigned)nb, RS_THREADS, 0, s>>>(keys, n, shift, nb, P.hist.p);
     CKL("k_rs_hist");
-    const int64_t hn = 256 * nb, hb = (hn + SC_TILE - 1) / SC_TILE;
-    P.bsum.reserve(hb + 1, s);
-    k_scan_tile<int64_t><<<(unsigned)hb, SC_THREADS, 0, s>>>(P.hist.p, P.hoff.p, hn, P.bsum.p);
-    CKL("k_scan_tile");
-    k_scan_bsums<<<1, SC_THREADS, 0, s>>>(P.bsum.p, hb, nullptr);
-    CKL("k_scan_bsums");
-    k_rs_scatter<<<(unsigned)nb, RS_THREADS, 0, s>>>(keys, vals, tk, tv, n, shift, nb, P.hoff.p, P.bsum.p);
+    k_rs_dscan<<<256, SC_THREADS, 0, s>>>(P.hist.p, nb, P.bsum.p);
+    CKL("k_rs_dscan");
+    k_rs_scatter<<<(unsigned)nb, RS_THREADS, 0, s>>>(keys, vals, tk, tv, n, shift, nb, P.hist.p, P.bsum.p);
     CKL("k_rs_scatter");
     u64* t = keys; keys = tk; tk = t;
     t = vals; vals = tv; tv = t;
@@ -358,20 +434,16 @@ int64_t reduce_by_key(const u64* keys, const u64* vals, int64_t n, u64* okeys, i
   if (n <= 0) return 0;
   P.flag.reserve(n + 1, s);
   P.pos.reserve(n + 1, s);
-  P.ukeys.reserve(n + 1, s);
   P.usum.reserve(n + 1, s);
-  const int g = grid_for(n, 256);
-  k_heads<<<g, 256, 0, s>>>(keys, n, P.flag.p);
-  CKL("k_heads");
-  int64_t nu = scan_exclusive_i32(P.flag.p, P.pos.p, n, P, s, true);
-  CK(cudaMemsetAsync(P.usum.p, 0, sizeof(int64_t) * (size_t)nu, s));
-  k_segsum<<<g, 256, 0, s>>>(keys, vals, n, P.pos.p, P.flag.p, P.ukeys.p, P.usum.p);
+  // a segment crossing a run boundary is summed atomically into a zeroed slot
+  CK(cudaMemsetAsync(P.usum.p, 0, sizeof(int64_t) * (size_t)n, s));
+  k_segsum<<<grid_for((n + RBK_RUN - 1) / RBK_RUN, 256), 256, 0, s>>>(keys, vals, n, P.usum.p);
   CKL("k_segsum");
-  const int g2 = grid_for(nu, 256);
-  k_nonzero<<<g2, 256, 0, s>>>(P.usum.p, nu, P.flag.p);
-  CKL("k_nonzero");
-  int64_t nz = scan_exclusive_i32(P.flag.p, P.pos.p, nu, P, s, true);
-  k_compact_pairs<<<g2, 256, 0, s>>>(P.ukeys.p, P.usum.p, nu, P.flag.p, P.pos.p, okeys, ovals);
+  const int g = grid_for(n, 256);
+  k_nonzero_heads<<<g, 256, 0, s>>>(keys, P.usum.p, n, P.flag.p);
+  CKL("k_nonzero_heads");
+  const int64_t nz = scan_exclusive_i32(P.flag.p, P.pos.p, n, P, s, true);
+  k_compact_pairs<<<g, 256, 0, s>>>(keys, P.usum.p, n, P.flag.p, P.pos.p, okeys, ovals);
   CKL("k_compact_pairs");
   return nz;
 }

@@ -3,12 +3,11 @@
 #include "common.cuh"
 
 struct Prims {  // scratch owned by a context
-  DBuf<int64_t> bsum, hist, hoff, pos, usum;
+  DBuf<int64_t> bsum, hist, pos, usum;
   DBuf<int32_t> flag;
-  DBuf<u64> ukeys;
   void release() {
-    bsum.release(); hist.release(); hoff.release(); pos.release(); usum.release();
-    flag.release(); ukeys.release();
+    bsum.release(); hist.release(); pos.release(); usum.release();
+    flag.release();
   }
 };
 

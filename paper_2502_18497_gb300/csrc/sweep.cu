@@ -10,7 +10,8 @@ namespace {
 
 constexpr int TPB = 256;
 constexpr int HW = 256;      // per-warp hash slots (small bin)
-constexpr int SMALL_DEG = 96;
+constexpr int TINY_DEG = 24;   // groups of 8 lanes, 64 slots
+constexpr int SMALL_DEG = 96;  // one warp, 256 slots
 constexpr int HB = 4096;     // per-block hash slots (upper mid bin)
 constexpr int MID1_DEG = 384;  // lower mid bin: 128 threads, 1024 slots
 constexpr int MID_DEG = 2048;
@@ -158,61 +159,73 @@ __device__ inline void emit_cand(const SweepArgs<WT>& A, int32_t v, int32_t src,
   A.cglo[p] = (uint64_t)b.g;
 }
 
-// one warp per node, warp-private shared hash
-template <class WT, int MODE>
-__global__ void __launch_bounds__(TPB) k_sweep_warp(SweepArgs<WT> A, const int32_t* list, const int32_t* nlist) {
-  __shared__ int32_t hk[TPB / 32][HW];
-  __shared__ int64_t hv[TPB / 32][HW];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+// One group of G lanes per node with a group-private shared hash of
+// HW * G / 32 slots (G = 8 for the lowest degrees, G = 32 above).  All groups
+// of a warp advance together, so the warp-wide shuffles of the argmax see
+// every lane; a group without a node in an iteration only takes part in them.
+template <class WT, int MODE, int G>
+__global__ void __launch_bounds__(TPB, 5) k_sweep_group(SweepArgs<WT> A, const int32_t* list, const int32_t* nlist) {
+  constexpr int HG = HW * G / 32;
+  constexpr int GPW = 32 / G;  // groups per warp
+  __shared__ int32_t hk[TPB / G][HG];
+  __shared__ int64_t hv[TPB / G][HG];
+  const int lane = threadIdx.x & 31, gl = threadIdx.x & (G - 1);
+  int32_t* K = hk[threadIdx.x / G];
+  int64_t* V = hv[threadIdx.x / G];
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  int32_t* K = hk[wid];
-  int64_t* V = hv[wid];
+  const int64_t ngroups = ((int64_t)gridDim.x * blockDim.x) / G;
   const int32_t nl = *nlist;
   const int64_t mult = A.directed ? 1 : 2;
   int64_t scanned = 0, pairs = 0, nodes = 0;
-  for (int64_t t = warp; t < nl; t += nw) {
-    const int32_t v = list[t];
-    const int32_t deg = A.out.len[v] + (A.directed ? A.in.len[v] : 0);
-    int H = 32;
-    while (H < 2 * deg && H < HW) H <<= 1;
-    for (int k = lane; k < H; k += 32) {
+  for (int64_t base = warp * GPW; base < nl; base += ngroups) {
+    const int64_t t = base + lane / G;
+    const bool act = t < nl;
+    const int32_t v = act ? list[t] : 0;
+    const int32_t deg = act ? A.out.len[v] + (A.directed ? A.in.len[v] : 0) : 0;
+    int H = G;
+    while (H < 2 * deg && H < HG) H <<= 1;
+    for (int k = gl; k < H; k += G) {
       K[k] = -1;
       V[k] = 0;
     }
     __syncwarp();
-    const int32_t a = A.lab[v];
-    accumulate<WT, MODE>(A, A.out, v, a, K, V, H - 1, lane, 32);
-    if (A.directed) accumulate<WT, MODE>(A, A.in, v, a, K, V, H - 1, lane, 32);
-    if (lane == 0) scanned += deg;
-    __syncwarp();
-    const int64_t wa = MODE == 0 ? hash_get(K, V, H - 1, a) : 0;
-    const int64_t ko = A.kout[v], ki = A.kin[v];
     Best b{0, 0, 0};
-    if (lane == 0) ++nodes;
-    for (int k = lane; k < H; k += 32) {
-      const int32_t key = K[k];
-      if (key < 0) continue;
-      if (MODE == 0 ? key == a : key == v) continue;
-      ++pairs;
-      const i128 g = gain_of<MODE>(key, V[k], wa, a, ko, ki, A.Tout, A.Tin, A.m, A.gn, A.gd, mult);
-      if (g > 0) {
-        Best c{g, key, 1};
-        if (best_better(c, b)) b = c;
+    int32_t a = 0;
+    if (act) {
+      a = A.lab[v];
+      accumulate<WT, MODE>(A, A.out, v, a, K, V, H - 1, gl, G);
+      if (A.directed) accumulate<WT, MODE>(A, A.in, v, a, K, V, H - 1, gl, G);
+      if (gl == 0) {
+        scanned += deg;
+        ++nodes;
       }
     }
-    b = warp_best(b);
-    if (lane == 0 && b.have) emit_cand(A, v, MODE == 0 ? a : v, b);
+    __syncwarp();
+    if (act) {
+      const int64_t wa = MODE == 0 ? hash_get(K, V, H - 1, a) : 0;
+      const int64_t ko = A.kout[v], ki = A.kin[v];
+      for (int k = gl; k < H; k += G) {
+        const int32_t key = K[k];
+        if (key < 0) continue;
+        if (MODE == 0 ? key == a : key == v) continue;
+        ++pairs;
+        const i128 g = gain_of<MODE>(key, V[k], wa, a, ko, ki, A.Tout, A.Tin, A.m, A.gn, A.gd, mult);
+        if (g > 0) {
+          Best c{g, key, 1};
+          if (best_better(c, b)) b = c;
+        }
+      }
+    }
+    b = group_best<G>(b);
+    if (act && gl == 0 && b.have) emit_cand(A, v, MODE == 0 ? a : v, b);
     __syncwarp();
   }
-  pairs = warp_sum_i64(pairs);
-  if (lane == 0) {
-    if (scanned) {
-      atomic_add_i64(A.scanned, scanned);
-      atomic_add_i64(&A.stats->sw_entries[0], scanned);
-    }
-    if (scanned | pairs | nodes)
-      atomic_add_i64(&A.stats->sw_bytes[0], sweep_bytes<WT, MODE>(A.directed, scanned, nodes, pairs));
+  const int64_t bytes = warp_sum_i64(sweep_bytes<WT, MODE>(A.directed, scanned, nodes, pairs));
+  scanned = warp_sum_i64(scanned);
+  if (lane == 0 && (scanned | bytes)) {
+    atomic_add_i64(A.scanned, scanned);
+    atomic_add_i64(&A.stats->sw_entries[G == 32 ? 1 : 0], scanned);
+    atomic_add_i64(&A.stats->sw_bytes[G == 32 ? 1 : 0], bytes);
   }
 }
 
@@ -225,6 +238,7 @@ __global__ void __launch_bounds__(NT) k_sweep_block(SweepArgs<WT> A, const int32
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int32_t nl = *nlist;
   const int64_t mult = A.directed ? 1 : 2;
+  int64_t ent_all = 0, nodes = 0, pairs_all = 0;
   for (int64_t t = blockIdx.x; t < nl; t += gridDim.x) {
     const int32_t v = list[t];
     int64_t* V = (int64_t*)smem;
@@ -257,47 +271,55 @@ __global__ void __launch_bounds__(NT) k_sweep_block(SweepArgs<WT> A, const int32
       }
     }
     b = warp_best(b);
-    pairs = warp_sum_i64(pairs);
-    if (lane == 0) {
-      wb[wid] = b;
-      if (pairs) atomic_add_i64(&A.stats->sw_bytes[NT == 128 ? 1 : 2], sweep_bytes<WT, MODE>(A.directed, 0, 0, pairs));
-    }
+    if (lane == 0) wb[wid] = b;
+    pairs_all += pairs;
     __syncthreads();
     if (threadIdx.x == 0) {
       Best r = wb[0];
       for (int w = 1; w < NT / 32; ++w)
         if (best_better(wb[w], r)) r = wb[w];
       if (r.have) emit_cand(A, v, MODE == 0 ? a : v, r);
-      const int64_t ent = (int64_t)A.out.len[v] + (A.directed ? A.in.len[v] : 0);
-      atomic_add_i64(A.scanned, ent);
-      atomic_add_i64(&A.stats->sw_entries[NT == 128 ? 1 : 2], ent);
-      atomic_add_i64(&A.stats->sw_bytes[NT == 128 ? 1 : 2], sweep_bytes<WT, MODE>(A.directed, ent, 1, 0));
+      ent_all += d;
+      ++nodes;
     }
     __syncthreads();
+  }
+  // statistics once per block
+  const int64_t bytes = warp_sum_i64(sweep_bytes<WT, MODE>(A.directed, ent_all, nodes, pairs_all));
+  if (lane == 0 && bytes) atomic_add_i64(&A.stats->sw_bytes[NT == 128 ? 2 : 3], bytes);
+  if (threadIdx.x == 0 && ent_all) {
+    atomic_add_i64(A.scanned, ent_all);
+    atomic_add_i64(&A.stats->sw_entries[NT == 128 ? 2 : 3], ent_all);
   }
 }
 
 template <class WT>
 __global__ void k_bin(Adj<WT> out, Adj<WT> in, int directed, const int32_t* list, const int32_t* nlist,
-                      int32_t* bs, int32_t* ns, int32_t* bm, int32_t* nm, int32_t* bm2, int32_t* nm2,
-                      int32_t* bl, int32_t* nlarge, int64_t* loff, int64_t* lsz, int64_t* tabtop) {
+                      int32_t* bt, int32_t* nt, int32_t* bs, int32_t* ns, int32_t* bm, int32_t* nm, int32_t* bm2,
+                      int32_t* nm2, int32_t* bl, int32_t* nlarge, int64_t* lsz, int64_t* tabtop) {
   const int32_t nl = *nlist;
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nl; t += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t v = list[t];
-    const int64_t d = (int64_t)out.len[v] + (directed ? in.len[v] : 0);
-    if (d <= SMALL_DEG) {
-      bs[atomicAdd(ns, 1)] = v;
-    } else if (d <= MID1_DEG) {
-      bm[atomicAdd(nm, 1)] = v;
-    } else if (d <= MID_DEG) {
-      bm2[atomicAdd(nm2, 1)] = v;
-    } else {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  // warp-uniform trip count so that the appends can be warp-aggregated
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < nl; base += stride) {
+    const int64_t t = base + (threadIdx.x & 31);
+    int bin = -1;
+    int32_t v = 0;
+    int64_t d = 0;
+    if (t < nl) {
+      v = list[t];
+      d = (int64_t)out.len[v] + (directed ? in.len[v] : 0);
+      bin = d <= TINY_DEG ? 0 : d <= SMALL_DEG ? 1 : d <= MID1_DEG ? 2 : d <= MID_DEG ? 3 : 4;
+    }
+    warp_append(bin == 0, v, bt, nt);
+    warp_append(bin == 1, v, bs, ns);
+    warp_append(bin == 2, v, bm, nm);
+    warp_append(bin == 3, v, bm2, nm2);
+    if (bin == 4) {
       int64_t sz = 1;
       while (sz < 2 * d) sz <<= 1;
       const int32_t p = atomicAdd(nlarge, 1);
       bl[p] = v;
       lsz[p] = sz;
-      (void)loff;
       atomicAdd((unsigned long long*)tabtop, (unsigned long long)sz);
     }
   }
@@ -348,8 +370,8 @@ __global__ void k_hub_acc(SweepArgs<WT> A, ChunkMap m, const int64_t* loff, cons
   }
   if (lane == 0 && scanned) {
     atomic_add_i64(A.scanned, scanned);
-    atomic_add_i64(&A.stats->sw_entries[3], scanned);
-    atomic_add_i64(&A.stats->sw_bytes[3], sweep_bytes<WT, MODE>(A.directed, scanned, 0, 0));
+    atomic_add_i64(&A.stats->sw_entries[4], scanned);
+    atomic_add_i64(&A.stats->sw_bytes[4], sweep_bytes<WT, MODE>(A.directed, scanned, 0, 0));
   }
 }
 
@@ -395,7 +417,7 @@ __global__ void __launch_bounds__(TPB) k_hub_eval(SweepArgs<WT> A, const int32_t
     pairs = warp_sum_i64(pairs);
     if (lane == 0) {
       wb[wid] = b;
-      if (pairs) atomic_add_i64(&A.stats->sw_bytes[3], sweep_bytes<WT, MODE>(A.directed, 0, 0, pairs));
+      if (pairs) atomic_add_i64(&A.stats->sw_bytes[4], sweep_bytes<WT, MODE>(A.directed, 0, 0, pairs));
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -426,7 +448,7 @@ __global__ void k_hub_final(SweepArgs<WT> A, const int32_t* hubs, int32_t nh, co
     b = warp_best(b);
     if (lane == 0) {
       const int32_t v = hubs[i];
-      atomic_add_i64(&A.stats->sw_bytes[3], sweep_bytes<WT, MODE>(A.directed, 0, 1, 0));
+      atomic_add_i64(&A.stats->sw_bytes[4], sweep_bytes<WT, MODE>(A.directed, 0, 1, 0));
       if (b.have) emit_cand(A, v, MODE == 0 ? A.lab[v] : v, b);
     }
   }
@@ -790,15 +812,15 @@ void union_into(ldl_ctx& c, const int32_t* list, int idx_n, int32_t* stamp, int3
   CKL("k_union");
 }
 
-// the next five statistics events of the context, created on first use
+// the next KS_GROUPS + 1 statistics events of the context, created on first use
 static cudaEvent_t* kstats_events(ldl_ctx& c) {
-  while (c.kev.size() < c.kev_used + 5) {
+  while (c.kev.size() < c.kev_used + KS_GROUPS + 1) {
     cudaEvent_t e;
     CK(cudaEventCreate(&e));
     c.kev.push_back(e);
   }
   cudaEvent_t* e = c.kev.data() + c.kev_used;
-  c.kev_used += 5;
+  c.kev_used += KS_GROUPS + 1;
   return e;
 }
 
@@ -832,45 +854,52 @@ static int32_t sweep_t(ldl_ctx& c, int r, Adj<WT> out, Adj<WT> in, const int32_t
   A.scanned = &c.d_sc->scanned;
   A.stats = c.d_sc;
   zero_cnt(c, K_CAND);
+  zero_cnt(c, K_TINY);
   zero_cnt(c, K_SMALL);
   zero_cnt(c, K_MID);
+  zero_cnt(c, K_MID2);
   zero_cnt(c, K_LARGE);
   CK(cudaMemsetAsync(&c.d_sc->need, 0, sizeof(int64_t), c.s));
-  zero_cnt(c, K_MID2);
-  k_bin<WT><<<grid_for(n_hint, TPB), TPB, 0, c.s>>>(out, in, c.directed, list, c.dcnt + idx_n, c.binS.p,
-                                                     c.dcnt + K_SMALL, c.binM.p, c.dcnt + K_MID, c.binM2.p,
-                                                     c.dcnt + K_MID2, c.binL.p, c.dcnt + K_LARGE, c.binLoff.p,
-                                                     c.binLsz.p, &c.d_sc->need);
+  k_bin<WT><<<grid_for(n_hint, TPB), TPB, 0, c.s>>>(out, in, c.directed, list, c.dcnt + idx_n, c.binT.p,
+                                                     c.dcnt + K_TINY, c.binS.p, c.dcnt + K_SMALL, c.binM.p,
+                                                     c.dcnt + K_MID, c.binM2.p, c.dcnt + K_MID2, c.binL.p,
+                                                     c.dcnt + K_LARGE, c.binLsz.p, &c.d_sc->need);
   CKL("k_bin");
-  int32_t counts[3], cm2 = 0;
+  // counters K_SMALL .. K_TINY in one read
+  int32_t cn[K_TINY - K_SMALL + 1];
   int64_t tab = 0;
-  CK(cudaMemcpyAsync(counts, c.dcnt + K_SMALL, sizeof(int32_t) * 3, cudaMemcpyDeviceToHost, c.s));
-  CK(cudaMemcpyAsync(&cm2, c.dcnt + K_MID2, sizeof(int32_t), cudaMemcpyDeviceToHost, c.s));
+  CK(cudaMemcpyAsync(cn, c.dcnt + K_SMALL, sizeof(cn), cudaMemcpyDeviceToHost, c.s));
   CK(cudaMemcpyAsync(&tab, &c.d_sc->need, sizeof(int64_t), cudaMemcpyDeviceToHost, c.s));
   CK(cudaStreamSynchronize(c.s));
+  const int32_t ct = cn[K_TINY - K_SMALL], cs = cn[0], cm = cn[K_MID - K_SMALL], cm2 = cn[K_MID2 - K_SMALL];
+  const int32_t ch = cn[K_LARGE - K_SMALL];
   cudaEvent_t* kev = c.kstats ? kstats_events(c) : nullptr;
   if (kev) CK(cudaEventRecord(kev[0], c.s));
-  if (counts[0] > 0) {
-    k_sweep_warp<WT, MODE><<<grid_for((int64_t)counts[0] * 32, TPB), TPB, 0, c.s>>>(A, c.binS.p, c.dcnt + K_SMALL);
-    CKL("k_sweep_warp");
+  if (ct > 0) {
+    k_sweep_group<WT, MODE, 8><<<grid_for((int64_t)ct * 8, TPB), TPB, 0, c.s>>>(A, c.binT.p, c.dcnt + K_TINY);
+    CKL("k_sweep_group<8>");
   }
   if (kev) CK(cudaEventRecord(kev[1], c.s));
-  if (counts[1] > 0) {
-    const size_t sm = (sizeof(int64_t) + sizeof(int32_t)) * 1024;
-    k_sweep_block<WT, MODE, 128, 1024><<<grid_for(counts[1], 1, 152 * 16), 128, sm, c.s>>>(A, c.binM.p,
-                                                                                         c.dcnt + K_MID);
-    CKL("k_sweep_block(mid1)");
+  if (cs > 0) {
+    k_sweep_group<WT, MODE, 32><<<grid_for((int64_t)cs * 32, TPB), TPB, 0, c.s>>>(A, c.binS.p, c.dcnt + K_SMALL);
+    CKL("k_sweep_group<32>");
   }
   if (kev) CK(cudaEventRecord(kev[2], c.s));
+  if (cm > 0) {
+    const size_t sm = (sizeof(int64_t) + sizeof(int32_t)) * 1024;
+    k_sweep_block<WT, MODE, 128, 1024><<<grid_for(cm, 1, 152 * 16), 128, sm, c.s>>>(A, c.binM.p, c.dcnt + K_MID);
+    CKL("k_sweep_block(mid1)");
+  }
+  if (kev) CK(cudaEventRecord(kev[3], c.s));
   if (cm2 > 0) {
     const size_t sm = (sizeof(int64_t) + sizeof(int32_t)) * HB;
     CK(cudaFuncSetAttribute(k_sweep_block<WT, MODE, 256, HB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     k_sweep_block<WT, MODE, 256, HB><<<grid_for(cm2, 1, 152 * 4), 256, sm, c.s>>>(A, c.binM2.p, c.dcnt + K_MID2);
     CKL("k_sweep_block(mid2)");
   }
-  if (kev) CK(cudaEventRecord(kev[3], c.s));
-  if (counts[2] > 0) {
-    const int32_t nh = counts[2];
+  if (kev) CK(cudaEventRecord(kev[4], c.s));
+  if (ch > 0) {
+    const int32_t nh = ch;
     c.gkeys.reserve(tab, c.s);
     c.gvals.reserve(tab, c.s);
     // table offsets and evaluation chunks per hub, in list order
@@ -902,11 +931,12 @@ static int32_t sweep_t(ldl_ctx& c, int r, Adj<WT> out, Adj<WT> in, const int32_t
   if (kev) {
     // times and bytes are resolved when the statistics are read, so that
     // collecting them adds no host synchronisation to the sweep
-    CK(cudaEventRecord(kev[4], c.s));
-    c.ks_launch[0] += counts[0] > 0;
-    c.ks_launch[1] += counts[1] > 0;
-    c.ks_launch[2] += cm2 > 0;
-    c.ks_launch[3] += counts[2] > 0 ? 4 : 0;
+    CK(cudaEventRecord(kev[5], c.s));
+    c.ks_launch[0] += ct > 0;
+    c.ks_launch[1] += cs > 0;
+    c.ks_launch[2] += cm > 0;
+    c.ks_launch[3] += cm2 > 0;
+    c.ks_launch[4] += ch > 0 ? 4 : 0;
   }
   return rd_cnt(c, K_CAND);
 }

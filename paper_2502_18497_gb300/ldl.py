@@ -141,6 +141,10 @@ def make_params(directed=False, gamma_num=1, gamma_den=1, N=2, L=4, M=5, M_stati
     return p
 
 
+# sweep kernel groups of ldl_get_kernel_stats, in its order
+SWEEP_GROUPS = ("sweep_group8", "sweep_warp", "sweep_block128", "sweep_block256", "sweep_hub")
+
+
 class LDL:
     """One device-resident LD-Leiden instance (ldl_create ... ldl_destroy).
 
@@ -276,10 +280,10 @@ class LDL:
         self._check(load().ldl_set_kernel_stats(self._h, int(on)))
 
     def kernel_stats(self) -> dict:
-        t = np.zeros(16, np.float64)
+        t = np.zeros(4 * len(SWEEP_GROUPS), np.float64)
         self._check(load().ldl_get_kernel_stats(self._h, _ptr(t)))
         out = {}
-        for k, name in enumerate(("sweep_warp", "sweep_block128", "sweep_block256", "sweep_hub")):
+        for k, name in enumerate(SWEEP_GROUPS):
             out[name] = dict(launches=t[4 * k], ms=t[4 * k + 1], bytes=t[4 * k + 2], entries=t[4 * k + 3])
         return out
 
