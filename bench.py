@@ -43,10 +43,22 @@ SCALE, ARCS, WMAX, SEED, BATCH = 20, 1 << 24, 16, 2, 10_000
 WORKLOAD = ("directed R-MAT (0.57,0.19,0.19,0.05), 2^20 vertices, 2^24 arcs, weights 1..16; "
             "batches of 10^4 arc updates (80% insert / 20% delete)")
 
-# DRAM traffic of the dominant sweep kernel from one ncu capture, valid only
-# for the sweep source it was taken with (sha256 of csrc/sweep.cu); bytes per
-# launch at this workload.  None until a capture exists.
-NCU_TRAFFIC = {"sha256": None, "bytes_per_launch": None, "kernel": None}
+# DRAM traffic of the dominant sweep kernel from one ncu capture (dram bytes
+# read + written, summed over its launches in one timed step of the default
+# workload, divided by the launches), valid only for the sweep source it was
+# taken with (sha256 of csrc/sweep.cu).
+NCU_TRAFFIC = {"sha256": "3ff39f400186e2222a190033002ba8a50ac98d2c17197577335ab65de31863ef",
+               "bytes_per_launch": 50898185, "kernel": "sweep_block256"}
+
+
+def _set_rmat_scale(scale: int):
+    """A smaller R-MAT of the same shape (2^scale vertices, 16 arcs per vertex),
+    for profiling captures that must stay small."""
+    global SCALE, ARCS, WORKLOAD
+    if scale == SCALE:
+        return
+    SCALE, ARCS = scale, 1 << (scale + 4)
+    WORKLOAD = WORKLOAD.replace("2^20 vertices, 2^24 arcs", f"2^{scale} vertices, 2^{scale + 4} arcs")
 
 
 def _workload(nbatches: int):
@@ -368,8 +380,11 @@ def main():
     ap.add_argument("--threads", type=int, default=16, help="batched/served: host worker threads")
     ap.add_argument("--tenants", type=int, default=16, help="served form: graphs")
     ap.add_argument("--requests", type=int, default=400, help="served form: requests")
+    ap.add_argument("--rmat-scale", type=int, default=SCALE,
+                    help="R-MAT workload: log2 of the vertex count (default: the full-size stream)")
     ap.add_argument("--load", type=float, default=0.9, help="served form: arrival rate / one-worker capacity")
     args = ap.parse_args()
+    _set_rmat_scale(args.rmat_scale)
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batched":
@@ -461,14 +476,18 @@ def main():
 
     # ---- roofline of the dominant sweep kernel
     peak, peak_src = _peaks()
-    dom = max(ks, key=lambda k: ks[k]["ms"])
+    # the dominant single sweep kernel (the hub path's set-up / evaluation
+    # group is several small kernels and is listed beside it)
+    dom = max((k2 for k2 in ks if k2 != "sweep_hub_rest"), key=lambda k2: ks[k2]["ms"])
     k = ks[dom]
     achieved = k["bytes"] / (k["ms"] / 1e3) / 1e9 if k["ms"] > 0 else 0.0
     sha = hashlib.sha256(open(os.path.join(ROOT, "paper_2502_18497_gb300", "csrc", "sweep.cu"), "rb").read()).hexdigest()
-    traffic = NCU_TRAFFIC["bytes_per_launch"] if NCU_TRAFFIC["sha256"] == sha and NCU_TRAFFIC["kernel"] == dom else None
+    traffic = (NCU_TRAFFIC["bytes_per_launch"] if NCU_TRAFFIC["sha256"] == sha and NCU_TRAFFIC["kernel"] == dom
+               and SCALE == 20 else None)
     names = {"sweep_group8": "k_sweep_group<..., 8>", "sweep_warp": "k_sweep_group<..., 32>",
              "sweep_block128": "k_sweep_block<..., 128, 1024>", "sweep_block256": "k_sweep_block<..., 256, 4096>",
-             "sweep_hub": "hub path (k_hub_acc + k_hub_eval + k_hub_final)"}
+             "sweep_cluster": "k_sweep_cluster (8-block cluster, distributed shared-memory hash)",
+             "sweep_hub_acc": "k_hub_acc", "sweep_hub_rest": "hub path set-up + k_hub_eval + k_hub_final"}
     roofline = {"bound": "hbm", "kernel": names.get(dom, dom), "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": peak_src, "traffic": traffic,
                 "launches": k["launches"], "ms_total": k["ms"], "algorithmic_bytes_per_launch":

@@ -68,6 +68,11 @@ typedef struct {
   int32_t gamma_num, gamma_den;
   int32_t N, L, M, M_static;
   int32_t alpha_inv, beta_inv;
+  /* Sweep scheduling (no effect on results): rows of 2049 .. cluster_max_deg
+   * entries (at most 32768) are swept by one 8-block cluster with a
+   * distributed shared-memory hash instead of the whole-GPU hub path;
+   * 0 (the default) keeps every row above 2048 entries on the hub path. */
+  int32_t cluster_max_deg;
   void* cuda_stream;
 } ldl_params;
 
@@ -248,12 +253,14 @@ int64_t ldl_launch_count(void);
 /*
  * Per-kernel statistics of the BestMove / BestRef sweep kernels, measured
  * with CUDA events on the context's stream while enabled (enabling resets
- * them).  out[20] = {launches, ms, algorithmic bytes, entries} for, in this
+ * them).  out[28] = {launches, ms, algorithmic bytes, entries} for, in this
  * order, k_sweep_group with 8-lane groups (one group per node of <= 24
  * entries), k_sweep_group with whole warps (<= 96 entries), k_sweep_block
  * with 128 threads (<= 384 entries), k_sweep_block with 256 threads
- * (<= 2048) and the hub path (rows spread over the GPU; four kernels per
- * sweep).
+ * (<= 2048), k_sweep_cluster (a cluster of 8 blocks with a distributed
+ * shared-memory hash, <= cluster_max_deg entries), k_hub_acc (the hub rows
+ * spread over the GPU into global hash tables) and the rest of the hub path
+ * (table set-up, evaluation and final reduction kernels).
  * Algorithmic bytes count, per adjacency entry, the neighbour id, its weight
  * and its label (refinement: also its parent); per swept node its offsets,
  * lengths, label and strengths; per evaluated (node, target) pair the

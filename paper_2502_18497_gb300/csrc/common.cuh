@@ -265,7 +265,14 @@ struct SlackCSR {
 
 // ---------------------------------------------------------------- scalar block
 // One small device struct read back in a single copy.
-constexpr int KS_GROUPS = 5;  // sweep kernel groups with their own statistics
+// Sweep kernel groups with their own statistics: 0 8-lane groups, 1 warps,
+// 2 128-thread blocks, 3 256-thread blocks, 4 block clusters, 5 the hub
+// accumulation kernel, 6 the rest of the hub path (table set-up, evaluation,
+// final reduction).  A sweep records KS_EVENTS events; interval j (event j to
+// j + 1) is charged to group ks_interval_group(j).
+constexpr int KS_GROUPS = 7;
+constexpr int KS_EVENTS = 9;
+__host__ __device__ constexpr int ks_interval_group(int j) { return j < 5 ? j : j == 6 ? 5 : 6; }
 
 struct DevScalars {
   I128 dq;          // numerator change of the current mini-batch
@@ -277,9 +284,8 @@ struct DevScalars {
   int64_t scanned;  // adjacency entries scanned
   int64_t err_key;  // packed (index << 8 | status) of the first failing update
   int64_t pool_top;
-  int64_t sw_entries[KS_GROUPS];  // sweep kernel groups (0: 8-lane groups, 1: warps, 2: 128-thread blocks,
-                                  // 3: 256-thread blocks, 4: hub path): adjacency entries read since
-                                  // statistics were enabled
+  int64_t sw_entries[KS_GROUPS];  // per sweep kernel group: adjacency entries read since statistics
+                                  // were enabled
   int64_t sw_bytes[KS_GROUPS];    // algorithmic bytes of the same sweeps
   int32_t cnt[16];  // list counters
   int32_t undecided;

@@ -37,7 +37,7 @@ struct LevelState {
 // Device counters (indices into ldl_ctx::dcnt).
 enum {
   K_U = 0, K_S, K_USTAR, K_MV, K_M0, K_D, K_C, K_R, K_R2, K_X, K_T, K_E, K_E2, K_CH, K_CAND, K_B,
-  K_UNDEC, K_SMALL, K_MID, K_LARGE, K_REC, K_CREC, K_NREC, K_ERR, K_TMP, K_TMP2, K_CHG, K_MID2, K_TINY,
+  K_UNDEC, K_SMALL, K_MID, K_LARGE, K_REC, K_CREC, K_NREC, K_ERR, K_TMP, K_TMP2, K_CHG, K_MID2, K_TINY, K_CLU,
   K_A0 = 32,  // K_A0 + r: |A^r|
   K_COUNT = 48
 };
@@ -71,7 +71,7 @@ struct ldl_ctx {
   DBuf<int32_t> oldlab, par_old, lab_before;
   DBuf<int64_t> snapKo, snapKi, snapE;
   // sweep binning
-  DBuf<int32_t> binT, binS, binM, binM2, binL;
+  DBuf<int32_t> binT, binS, binM, binM2, binC, binL;
   DBuf<int64_t> binLoff, binLsz;
   DBuf<int32_t> gkeys;
   DBuf<int64_t> gvals;
@@ -97,9 +97,9 @@ struct ldl_ctx {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr, ev3 = nullptr;
   // per-kernel statistics of the sweep kernels (enabled by ldl_set_kernel_stats)
   int kstats = 0;
-  std::vector<cudaEvent_t> kev;  // KS_GROUPS + 1 events per sweep since enabling, bracketing the groups
+  std::vector<cudaEvent_t> kev;  // KS_EVENTS events per sweep since enabling
   size_t kev_used = 0;
-  double ks_launch[KS_GROUPS] = {0, 0, 0, 0, 0};
+  double ks_launch[KS_GROUPS] = {0, 0, 0, 0, 0, 0, 0};
   int64_t syncs = 0;  // host synchronisations in the current batch
   std::string err;
 

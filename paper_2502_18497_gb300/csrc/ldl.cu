@@ -108,7 +108,7 @@ static void alloc_globals(ldl_ctx& c) {
   }
   DBuf<int32_t>* ls[] = {&c.lU, &c.lS, &c.lUstar, &c.lMv, &c.lM0, &c.lD, &c.lC, &c.lR, &c.lR2, &c.lX, &c.lT,
                          &c.lE, &c.lE2, &c.lCh, &c.lChg, &c.lTmp, &c.cv, &c.csrc, &c.cdst, &c.cst, &c.bv,
-                         &c.bsrc, &c.bdst, &c.oldlab, &c.par_old, &c.lab_before, &c.binT, &c.binS, &c.binM, &c.binM2, &c.binL};
+                         &c.bsrc, &c.bdst, &c.oldlab, &c.par_old, &c.lab_before, &c.binT, &c.binS, &c.binM, &c.binM2, &c.binC, &c.binL};
   for (auto* b : ls) b->exact(n);
   c.best.exact(n);
   CK(cudaMemsetAsync(c.best.p, 0xff, sizeof(int32_t) * (size_t)n, c.s));
@@ -138,7 +138,7 @@ static void free_all(ldl_ctx& c) {
                           &c.stE, &c.stCh, &c.lU, &c.lS, &c.lUstar, &c.lMv, &c.lM0, &c.lD, &c.lC, &c.lR,
                           &c.lR2, &c.lX, &c.lT, &c.lE, &c.lE2, &c.lCh, &c.lChg, &c.lTmp, &c.cv, &c.csrc,
                           &c.cdst, &c.cst, &c.bv, &c.bsrc, &c.bdst, &c.best, &c.role, &c.oldlab, &c.par_old,
-                          &c.lab_before, &c.binT, &c.binS, &c.binM, &c.binM2, &c.binL, &c.gkeys, &c.ndx, &c.ndx2};
+                          &c.lab_before, &c.binT, &c.binS, &c.binM, &c.binM2, &c.binC, &c.binL, &c.gkeys, &c.ndx, &c.ndx2};
   for (auto* b : b32) b->release();
   DBuf<u64>* bu[] = {&c.rk, &c.rv, &c.tk, &c.tv, &c.rk2, &c.rv2, &c.crk, &c.crv, &c.fk, &c.trk, &c.trv};
   for (auto* b : bu) b->release();
@@ -406,7 +406,7 @@ ldl_status ldl_create(const ldl_params* params, int64_t n, int64_t nnz, const in
   const ldl_params& p = *params;
   if (n <= 0 || n > INT32_MAX - 1 || nnz < 0 || p.L < 0 || p.L > 7 || p.N < 0 || p.M < 0 || p.M_static < 0 ||
       p.alpha_inv <= 0 || p.beta_inv <= 0 || p.gamma_num < 1 || p.gamma_den < 1 || p.gamma_num > 1024 ||
-      p.gamma_den > 1024) {
+      p.gamma_den > 1024 || p.cluster_max_deg < 0) {
     g_create_err = "invalid size or parameter";
     return LDL_E_INVALID;
   }
@@ -651,13 +651,13 @@ ldl_status ldl_set_kernel_stats(ldl_ctx* c, int32_t on) {
 ldl_status ldl_get_kernel_stats(const ldl_ctx* c, double* out) {
   if (!c || !out) return LDL_E_INVALID;
   try {
-    double ms[KS_GROUPS] = {0, 0, 0, 0, 0};
+    double ms[KS_GROUPS] = {0, 0, 0, 0, 0, 0, 0};
     if (c->kev_used) CK(cudaEventSynchronize(c->kev[c->kev_used - 1]));
-    for (size_t i = 0; i + KS_GROUPS + 1 <= c->kev_used; i += KS_GROUPS + 1)
-      for (int k = 0; k < KS_GROUPS; ++k) {
+    for (size_t i = 0; i + KS_EVENTS <= c->kev_used; i += KS_EVENTS)
+      for (int j = 0; j + 1 < KS_EVENTS; ++j) {
         float t = 0;
-        CK(cudaEventElapsedTime(&t, c->kev[i + k], c->kev[i + k + 1]));
-        ms[k] += t;
+        CK(cudaEventElapsedTime(&t, c->kev[i + j], c->kev[i + j + 1]));
+        ms[ks_interval_group(j)] += t;
       }
     DevScalars h;
     CK(cudaMemcpy(&h, c->d_sc, sizeof(DevScalars), cudaMemcpyDeviceToHost));

@@ -3,8 +3,12 @@
 // filter of Sec. III-E as deterministic parallel rounds, and the commit of an
 // accepted mini-batch with the additive repair of the community totals and
 // the exact modularity change dQ(B) (lines 10-11).
+#include <cooperative_groups.h>
+
 #include "chunks.cuh"
 #include "kern.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace {
 
@@ -15,6 +19,9 @@ constexpr int SMALL_DEG = 96;  // one warp, 256 slots
 constexpr int HB = 4096;     // per-block hash slots (upper mid bin)
 constexpr int MID1_DEG = 384;  // lower mid bin: 128 threads, 1024 slots
 constexpr int MID_DEG = 2048;
+constexpr int CL = 8;             // blocks per cluster (hub rows up to CLUSTER_DEG entries)
+constexpr int CL_SLOTS = 8192;    // hash slots per block of a cluster (96 KB of shared memory)
+constexpr int CLUSTER_DEG = CL * CL_SLOTS / 2;  // upper limit of cluster_max_deg
 constexpr int EVAL_CH = 4096;  // hub table slots evaluated per block
 
 // ---------------------------------------------------------------- expand
@@ -296,7 +303,8 @@ __global__ void __launch_bounds__(NT) k_sweep_block(SweepArgs<WT> A, const int32
 template <class WT>
 __global__ void k_bin(Adj<WT> out, Adj<WT> in, int directed, const int32_t* list, const int32_t* nlist,
                       int32_t* bt, int32_t* nt, int32_t* bs, int32_t* ns, int32_t* bm, int32_t* nm, int32_t* bm2,
-                      int32_t* nm2, int32_t* bl, int32_t* nlarge, int64_t* lsz, int64_t* tabtop) {
+                      int32_t* nm2, int32_t* bc, int32_t* nc, int32_t* bl, int32_t* nlarge, int64_t* lsz,
+                      int64_t* tabtop, int32_t cluster_max) {
   const int32_t nl = *nlist;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   // warp-uniform trip count so that the appends can be warp-aggregated
@@ -308,13 +316,14 @@ __global__ void k_bin(Adj<WT> out, Adj<WT> in, int directed, const int32_t* list
     if (t < nl) {
       v = list[t];
       d = (int64_t)out.len[v] + (directed ? in.len[v] : 0);
-      bin = d <= TINY_DEG ? 0 : d <= SMALL_DEG ? 1 : d <= MID1_DEG ? 2 : d <= MID_DEG ? 3 : 4;
+      bin = d <= TINY_DEG ? 0 : d <= SMALL_DEG ? 1 : d <= MID1_DEG ? 2 : d <= MID_DEG ? 3 : d <= cluster_max ? 4 : 5;
     }
     warp_append(bin == 0, v, bt, nt);
     warp_append(bin == 1, v, bs, ns);
     warp_append(bin == 2, v, bm, nm);
     warp_append(bin == 3, v, bm2, nm2);
-    if (bin == 4) {
+    warp_append(bin == 4, v, bc, nc);
+    if (bin == 5) {
       int64_t sz = 1;
       while (sz < 2 * d) sz <<= 1;
       const int32_t p = atomicAdd(nlarge, 1);
@@ -322,6 +331,136 @@ __global__ void k_bin(Adj<WT> out, Adj<WT> in, int directed, const int32_t* list
       lsz[p] = sz;
       atomicAdd((unsigned long long*)tabtop, (unsigned long long)sz);
     }
+  }
+}
+
+// ---------------------------------------------------------------- cluster bin
+// One thread-block cluster of CL blocks per node of MID_DEG < degree <=
+// CLUSTER_DEG.  The node's hash table of H slots (a power of two >= 2 *
+// degree) is spread over the blocks' shared memories: slot h lives in block
+// h / (H / CL) at h % (H / CL), and every thread of the cluster inserts into
+// it with distributed-shared-memory atomics.  Each block then evaluates its
+// own slots, and the blocks' bests meet in block 0.  Every thread of the
+// cluster runs every iteration, so the cluster barriers always complete.
+template <class WT, int MODE>
+__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(TPB)
+    k_sweep_cluster(SweepArgs<WT> A, const int32_t* list, const int32_t* nlist) {
+  extern __shared__ unsigned char smem[];
+  int64_t* V = (int64_t*)smem;
+  int32_t* K = (int32_t*)(smem + sizeof(int64_t) * CL_SLOTS);
+  __shared__ Best wb[TPB / 32];
+  __shared__ Best cbest[CL];
+  __shared__ int64_t s_wa;
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t cid = blockIdx.x / CL, ncl = gridDim.x / CL;
+  const int32_t nl = *nlist;
+  const int64_t mult = A.directed ? 1 : 2;
+  int64_t ent_all = 0, nodes = 0, pairs_all = 0;
+  for (int64_t t = cid; t < nl; t += ncl) {
+    const int32_t v = list[t];
+    const int64_t d = (int64_t)A.out.len[v] + (A.directed ? A.in.len[v] : 0);
+    uint32_t H = CL * 64;
+    while (H < 2 * d && H < (uint32_t)(CL * CL_SLOTS)) H <<= 1;
+    const uint32_t HL = H / CL;
+    for (uint32_t k = threadIdx.x; k < HL; k += TPB) {
+      K[k] = -1;
+      V[k] = 0;
+    }
+    cl.sync();
+    const int32_t a = A.lab[v];
+    for (int side = 0; side < (A.directed ? 2 : 1); ++side) {
+      const Adj<WT>& adj = side ? A.in : A.out;
+      const int64_t o = adj.off[v];
+      const int32_t l = adj.len[v];
+      // warp-uniform trip count: lanes with equal keys find their slot once
+      // (one remote compare-and-swap probe by the lowest such lane), then
+      // every lane adds its weight with a remote reduction
+      for (int32_t base = rank * TPB + wid * 32; base < l; base += CL * TPB) {
+        const int32_t k = base + lane;
+        int32_t key = -1;
+        int64_t w = 0;
+        if (k < l) {
+          const int32_t u = adj.col[o + k];
+          if (u != v && (MODE == 0 || A.lab[u] == a)) {
+            key = MODE == 0 ? A.lab[u] : A.par[u];
+            w = (int64_t)adj.w[o + k];
+          }
+        }
+        const unsigned peers = __match_any_sync(0xffffffffu, key);
+        const int leader = __ffs(peers) - 1;
+        uint32_t h = 0;
+        if (key >= 0 && lane == leader) {
+          h = hash32((uint32_t)key) & (H - 1);
+          while (true) {
+            const int32_t prev = atomicCAS(&cl.map_shared_rank(K, (int)(h / HL))[h % HL], -1, key);
+            if (prev == -1 || prev == key) break;
+            h = (h + 1) & (H - 1);
+          }
+        }
+        h = __shfl_sync(0xffffffffu, h, leader);
+        if (key >= 0)
+          atomicAdd((unsigned long long*)&cl.map_shared_rank(V, (int)(h / HL))[h % HL], (unsigned long long)w);
+      }
+    }
+    cl.sync();
+    if (threadIdx.x == 0) {
+      int64_t wa = 0;
+      if (MODE == 0) {
+        uint32_t h = hash32((uint32_t)a) & (H - 1);
+        while (true) {
+          const int32_t k = cl.map_shared_rank(K, (int)(h / HL))[h % HL];
+          if (k == a) {
+            wa = cl.map_shared_rank(V, (int)(h / HL))[h % HL];
+            break;
+          }
+          if (k == -1) break;
+          h = (h + 1) & (H - 1);
+        }
+      }
+      s_wa = wa;
+    }
+    __syncthreads();
+    const int64_t wa = s_wa;
+    const int64_t ko = A.kout[v], ki = A.kin[v];
+    Best b{0, 0, 0};
+    for (uint32_t k = threadIdx.x; k < HL; k += TPB) {
+      const int32_t key = K[k];
+      if (key < 0) continue;
+      if (MODE == 0 ? key == a : key == v) continue;
+      ++pairs_all;
+      const i128 g = gain_of<MODE>(key, V[k], wa, a, ko, ki, A.Tout, A.Tin, A.m, A.gn, A.gd, mult);
+      if (g > 0) {
+        Best c{g, key, 1};
+        if (best_better(c, b)) b = c;
+      }
+    }
+    b = warp_best(b);
+    if (lane == 0) wb[wid] = b;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      Best r = wb[0];
+      for (int w = 1; w < TPB / 32; ++w)
+        if (best_better(wb[w], r)) r = wb[w];
+      cl.map_shared_rank(cbest, 0)[rank] = r;
+    }
+    cl.sync();
+    if (rank == 0 && threadIdx.x == 0) {
+      Best r = cbest[0];
+      for (int q = 1; q < CL; ++q)
+        if (best_better(cbest[q], r)) r = cbest[q];
+      if (r.have) emit_cand(A, v, MODE == 0 ? a : v, r);
+      ent_all += d;
+      ++nodes;
+    }
+  }
+  cl.sync();  // no block leaves while another may still touch its shared memory
+  const int64_t bytes = warp_sum_i64(sweep_bytes<WT, MODE>(A.directed, ent_all, nodes, pairs_all));
+  if (lane == 0 && bytes) atomic_add_i64(&A.stats->sw_bytes[4], bytes);
+  if (threadIdx.x == 0 && ent_all) {
+    atomic_add_i64(A.scanned, ent_all);
+    atomic_add_i64(&A.stats->sw_entries[4], ent_all);
   }
 }
 
@@ -359,19 +498,38 @@ __global__ void k_hub_acc(SweepArgs<WT> A, ChunkMap m, const int64_t* loff, cons
     const uint32_t mask = (uint32_t)lsz[ch.idx] - 1;
     const Adj<WT>& adj = ch.row ? A.in : A.out;
     const int64_t o = adj.off[v];
-    for (int32_t k = ch.k0 + lane; k < ch.k1; k += 32) {
-      const int32_t u = adj.col[o + k];
-      if (u == v) continue;
-      if (MODE == 1 && A.lab[u] != cv_) continue;
-      const int32_t key = MODE == 0 ? A.lab[u] : A.par[u];
-      hash_add(K, V, mask, key, (int64_t)adj.w[o + k]);
+    for (int32_t base = ch.k0; base < ch.k1; base += 32) {  // warp-uniform
+      const int32_t k = base + lane;
+      int32_t key = -1;
+      int64_t w = 0;
+      if (k < ch.k1) {
+        const int32_t u = adj.col[o + k];
+        if (u != v && (MODE == 0 || A.lab[u] == cv_)) {
+          key = MODE == 0 ? A.lab[u] : A.par[u];
+          w = (int64_t)adj.w[o + k];
+        }
+      }
+      // lanes with equal keys: one probe by the lowest, then one reduction each
+      const unsigned peers = __match_any_sync(0xffffffffu, key);
+      const int leader = __ffs(peers) - 1;
+      uint32_t h = 0;
+      if (key >= 0 && lane == leader) {
+        h = hash32((uint32_t)key) & mask;
+        while (true) {
+          const int32_t prev = atomicCAS(&K[h], -1, key);
+          if (prev == -1 || prev == key) break;
+          h = (h + 1) & mask;
+        }
+      }
+      h = __shfl_sync(0xffffffffu, h, leader);
+      if (key >= 0) atomicAdd((unsigned long long*)&V[h], (unsigned long long)w);
     }
     if (lane == 0) scanned += ch.k1 - ch.k0;
   }
   if (lane == 0 && scanned) {
     atomic_add_i64(A.scanned, scanned);
-    atomic_add_i64(&A.stats->sw_entries[4], scanned);
-    atomic_add_i64(&A.stats->sw_bytes[4], sweep_bytes<WT, MODE>(A.directed, scanned, 0, 0));
+    atomic_add_i64(&A.stats->sw_entries[5], scanned);
+    atomic_add_i64(&A.stats->sw_bytes[5], sweep_bytes<WT, MODE>(A.directed, scanned, 0, 0));
   }
 }
 
@@ -417,7 +575,7 @@ __global__ void __launch_bounds__(TPB) k_hub_eval(SweepArgs<WT> A, const int32_t
     pairs = warp_sum_i64(pairs);
     if (lane == 0) {
       wb[wid] = b;
-      if (pairs) atomic_add_i64(&A.stats->sw_bytes[4], sweep_bytes<WT, MODE>(A.directed, 0, 0, pairs));
+      if (pairs) atomic_add_i64(&A.stats->sw_bytes[6], sweep_bytes<WT, MODE>(A.directed, 0, 0, pairs));
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -448,7 +606,7 @@ __global__ void k_hub_final(SweepArgs<WT> A, const int32_t* hubs, int32_t nh, co
     b = warp_best(b);
     if (lane == 0) {
       const int32_t v = hubs[i];
-      atomic_add_i64(&A.stats->sw_bytes[4], sweep_bytes<WT, MODE>(A.directed, 0, 1, 0));
+      atomic_add_i64(&A.stats->sw_bytes[6], sweep_bytes<WT, MODE>(A.directed, 0, 1, 0));
       if (b.have) emit_cand(A, v, MODE == 0 ? A.lab[v] : v, b);
     }
   }
@@ -812,15 +970,15 @@ void union_into(ldl_ctx& c, const int32_t* list, int idx_n, int32_t* stamp, int3
   CKL("k_union");
 }
 
-// the next KS_GROUPS + 1 statistics events of the context, created on first use
+// the next KS_EVENTS statistics events of the context, created on first use
 static cudaEvent_t* kstats_events(ldl_ctx& c) {
-  while (c.kev.size() < c.kev_used + KS_GROUPS + 1) {
+  while (c.kev.size() < c.kev_used + KS_EVENTS) {
     cudaEvent_t e;
     CK(cudaEventCreate(&e));
     c.kev.push_back(e);
   }
   cudaEvent_t* e = c.kev.data() + c.kev_used;
-  c.kev_used += KS_GROUPS + 1;
+  c.kev_used += KS_EVENTS;
   return e;
 }
 
@@ -858,21 +1016,23 @@ static int32_t sweep_t(ldl_ctx& c, int r, Adj<WT> out, Adj<WT> in, const int32_t
   zero_cnt(c, K_SMALL);
   zero_cnt(c, K_MID);
   zero_cnt(c, K_MID2);
+  zero_cnt(c, K_CLU);
   zero_cnt(c, K_LARGE);
   CK(cudaMemsetAsync(&c.d_sc->need, 0, sizeof(int64_t), c.s));
   k_bin<WT><<<grid_for(n_hint, TPB), TPB, 0, c.s>>>(out, in, c.directed, list, c.dcnt + idx_n, c.binT.p,
                                                      c.dcnt + K_TINY, c.binS.p, c.dcnt + K_SMALL, c.binM.p,
-                                                     c.dcnt + K_MID, c.binM2.p, c.dcnt + K_MID2, c.binL.p,
-                                                     c.dcnt + K_LARGE, c.binLsz.p, &c.d_sc->need);
+                                                     c.dcnt + K_MID, c.binM2.p, c.dcnt + K_MID2, c.binC.p,
+                                                     c.dcnt + K_CLU, c.binL.p, c.dcnt + K_LARGE, c.binLsz.p,
+                                                     &c.d_sc->need, std::min(c.prm.cluster_max_deg, CLUSTER_DEG));
   CKL("k_bin");
-  // counters K_SMALL .. K_TINY in one read
-  int32_t cn[K_TINY - K_SMALL + 1];
+  // counters K_SMALL .. K_CLU in one read
+  int32_t cn[K_CLU - K_SMALL + 1];
   int64_t tab = 0;
   CK(cudaMemcpyAsync(cn, c.dcnt + K_SMALL, sizeof(cn), cudaMemcpyDeviceToHost, c.s));
   CK(cudaMemcpyAsync(&tab, &c.d_sc->need, sizeof(int64_t), cudaMemcpyDeviceToHost, c.s));
   CK(cudaStreamSynchronize(c.s));
   const int32_t ct = cn[K_TINY - K_SMALL], cs = cn[0], cm = cn[K_MID - K_SMALL], cm2 = cn[K_MID2 - K_SMALL];
-  const int32_t ch = cn[K_LARGE - K_SMALL];
+  const int32_t cc = cn[K_CLU - K_SMALL], ch = cn[K_LARGE - K_SMALL];
   cudaEvent_t* kev = c.kstats ? kstats_events(c) : nullptr;
   if (kev) CK(cudaEventRecord(kev[0], c.s));
   if (ct > 0) {
@@ -898,6 +1058,14 @@ static int32_t sweep_t(ldl_ctx& c, int r, Adj<WT> out, Adj<WT> in, const int32_t
     CKL("k_sweep_block(mid2)");
   }
   if (kev) CK(cudaEventRecord(kev[4], c.s));
+  if (cc > 0) {
+    const size_t sm = (sizeof(int64_t) + sizeof(int32_t)) * CL_SLOTS;
+    CK(cudaFuncSetAttribute(k_sweep_cluster<WT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    const int ncl = std::min<int>(cc, 152 * 2 / CL);
+    k_sweep_cluster<WT, MODE><<<ncl * CL, TPB, sm, c.s>>>(A, c.binC.p, c.dcnt + K_CLU);
+    CKL("k_sweep_cluster");
+  }
+  if (kev) CK(cudaEventRecord(kev[5], c.s));
   if (ch > 0) {
     const int32_t nh = ch;
     c.gkeys.reserve(tab, c.s);
@@ -917,9 +1085,11 @@ static int32_t sweep_t(ldl_ctx& c, int r, Adj<WT> out, Adj<WT> in, const int32_t
     k_hub_init<<<grid_for(tab, TPB), TPB, 0, c.s>>>(c.gkeys.p, c.gvals.p, tab);
     CKL("k_hub_init");
     ChunkMap m = chunk_map(c, c.binL.p, c.dcnt + K_LARGE, nh, out.len, c.directed ? in.len : nullptr);
+    if (kev) CK(cudaEventRecord(kev[6], c.s));
     k_hub_acc<WT, MODE><<<grid_for((int64_t)nh * 2048, TPB, 152 * 16), TPB, 0, c.s>>>(A, m, c.binLoff.p, c.binLsz.p,
                                                                                       c.gkeys.p, c.gvals.p);
     CKL("k_hub_acc");
+    if (kev) CK(cudaEventRecord(kev[7], c.s));
     k_hub_eval<WT, MODE><<<grid_for(ech, 1, 152 * 8), TPB, 0, c.s>>>(A, c.binL.p, nh, c.binLoff.p, c.binLsz.p,
                                                                     c.hub_epre.p, c.gkeys.p, c.gvals.p, c.pb_hi.p,
                                                                     c.pb_lo.p, c.pb_c.p);
@@ -927,16 +1097,21 @@ static int32_t sweep_t(ldl_ctx& c, int r, Adj<WT> out, Adj<WT> in, const int32_t
     k_hub_final<WT, MODE><<<grid_for((int64_t)nh * 32, TPB), TPB, 0, c.s>>>(A, c.binL.p, nh, c.hub_epre.p, c.pb_hi.p,
                                                                            c.pb_lo.p, c.pb_c.p);
     CKL("k_hub_final");
+  } else if (kev) {
+    CK(cudaEventRecord(kev[6], c.s));
+    CK(cudaEventRecord(kev[7], c.s));
   }
   if (kev) {
     // times and bytes are resolved when the statistics are read, so that
     // collecting them adds no host synchronisation to the sweep
-    CK(cudaEventRecord(kev[5], c.s));
+    CK(cudaEventRecord(kev[8], c.s));
     c.ks_launch[0] += ct > 0;
     c.ks_launch[1] += cs > 0;
     c.ks_launch[2] += cm > 0;
     c.ks_launch[3] += cm2 > 0;
-    c.ks_launch[4] += ch > 0 ? 4 : 0;
+    c.ks_launch[4] += cc > 0;
+    c.ks_launch[5] += ch > 0;
+    c.ks_launch[6] += ch > 0 ? 3 : 0;
   }
   return rd_cnt(c, K_CAND);
 }

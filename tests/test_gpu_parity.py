@@ -81,16 +81,23 @@ def test_planted_partition_full(ldl):
         assert np.array_equal(o.labels(), np.asarray(d.labels()))
 
 
-def test_rmat_directed_reduced(ldl):
+@pytest.mark.parametrize("cluster_max_deg", [0, 32768])
+def test_rmat_directed_reduced(ldl, cluster_max_deg):
     """Directed R-MAT with the paper-stream skew at 2^14 vertices / 2^18 arcs,
-    20 batches of 1,000 arc updates (80% inserts, 20% deletes)."""
+    20 batches of 1,000 arc updates (80% inserts, 20% deletes); rows above
+    2048 entries swept by the whole-GPU hub path or by block clusters."""
     g = rmat_directed(scale=14, arcs=1 << 18, seed=12)
-    o, d = _pair(ldl, g)
+    o = Oracle(g)
+    d = ldl.LDL.from_graph(g, cluster_max_deg=cluster_max_deg)
     _assert_same(o, d, "create", adjacency=False)
+    d.set_kernel_stats(True)
     for t, b in enumerate(rmat_stream(g, batches=20, size=1000, seed=12)):
         assert o.apply(b) == 0
         d.apply(b)
         _assert_same(o, d, f"batch {t}", adjacency=(t % 5 == 4))
+    ks = d.kernel_stats()
+    assert (ks["sweep_cluster"]["launches"] > 0) == (cluster_max_deg > 0)
+    assert ks["sweep_hub_acc"]["launches"] > 0 or cluster_max_deg > 0
 
 
 def test_rmat_directed_full_size(ldl):
