@@ -133,7 +133,9 @@ ldl_status ldl_create(const ldl_params* params, int64_t n, int64_t nnz, const in
  *   out      optional (may be NULL); filled on LDL_OK.
  * Errors: RANGE, INVALID, NEG_WEIGHT, NO_EDGE, OVERFLOW (the lowest-index
  * failing update decides; single-update checks come before sequence checks),
- * NOMEM, CUDA.  On error the state is unchanged.
+ * NOMEM, CUDA.  On these errors the state is unchanged.  TIMEOUT: a bounded
+ * wait inside a device scan gave up (never expected; the state is then not
+ * to be trusted and the context should be destroyed).
  */
 ldl_status ldl_apply_batch(ldl_ctx* ctx, const ldl_update* updates, int64_t count,
                            int32_t updates_on_device, ldl_result* out);

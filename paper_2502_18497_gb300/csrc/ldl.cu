@@ -247,6 +247,8 @@ static int64_t refine_loop(ldl_ctx& c, int r, int rounds, int32_t epD) {
   return merges;
 }
 
+static void check_scan_wait(ldl_ctx& c);
+
 // ---------------------------------------------------------------- static build
 static void static_build(ldl_ctx& c) {
   const int L = c.prm.L;
@@ -277,7 +279,7 @@ static void static_build(ldl_ctx& c) {
     const int32_t epC = c.next_epoch();
     aggregate(c, r, epD, epC, 0, true);
   }
-  CK(cudaStreamSynchronize(c.s));
+  check_scan_wait(c);
 }
 
 // ---------------------------------------------------------------- batch update
@@ -358,7 +360,20 @@ static void apply_batch(ldl_ctx& c, const ldl_update* upd, int64_t count, int on
   c.res.n_changed = changed_labels(c, epCh);
   c.res.host_syncs = c.syncs;
   CK(cudaMemcpyAsync(&c.res.edges_scanned, &c.d_sc->scanned, sizeof(int64_t), cudaMemcpyDeviceToHost, c.s));
+  check_scan_wait(c);
+}
+
+// Reads the look-back scans' error flag (and synchronises): a bounded wait
+// that gave up leaves results that cannot be trusted.
+static void check_scan_wait(ldl_ctx& c) {
+  int32_t* f = scan_error_flag(c.P);
+  int32_t bad = 0;
+  if (f) CK(cudaMemcpyAsync(&bad, f, sizeof(int32_t), cudaMemcpyDeviceToHost, c.s));
   CK(cudaStreamSynchronize(c.s));
+  if (bad) {
+    CK(cudaMemsetAsync(f, 0, sizeof(int32_t), c.s));
+    ldl_throw(LDL_E_TIMEOUT, "a device scan's bounded wait gave up");
+  }
 }
 
 template <class WT>

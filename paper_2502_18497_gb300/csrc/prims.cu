@@ -33,26 +33,6 @@ __device__ inline int64_t block_excl_scan_i64(int64_t v, int64_t* total) {
   return before + x - v;
 }
 
-template <class T>
-__global__ void k_scan_tile(const T* in, int64_t* out, int64_t n, int64_t* bsum) {
-  const int64_t base = (int64_t)blockIdx.x * SC_TILE + (int64_t)threadIdx.x * SC_ITEMS;
-  int64_t loc[SC_ITEMS];
-  int64_t s = 0;
-  for (int k = 0; k < SC_ITEMS; ++k) {
-    int64_t i = base + k;
-    loc[k] = i < n ? (int64_t)in[i] : 0;
-    s += loc[k];
-  }
-  int64_t tot;
-  int64_t pre = block_excl_scan_i64(s, &tot);
-  for (int k = 0; k < SC_ITEMS; ++k) {
-    int64_t i = base + k;
-    if (i < n) out[i] = pre;
-    pre += loc[k];
-  }
-  if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
-}
-
 // whole input in one tile: scan and total in one launch
 template <class T>
 __global__ void k_scan_one(const T* in, int64_t* out, int64_t n, int64_t* total) {
@@ -74,29 +54,66 @@ __global__ void k_scan_one(const T* in, int64_t* out, int64_t n, int64_t* total)
   if (threadIdx.x == 0 && total) *total = tot;
 }
 
-__global__ void k_scan_bsums(int64_t* bsum, int64_t nb, int64_t* total) {
-  __shared__ int64_t carry;
-  if (threadIdx.x == 0) carry = 0;
-  __syncthreads();
-  for (int64_t base = 0; base < nb; base += SC_THREADS) {
-    int64_t i = base + threadIdx.x;
-    int64_t v = i < nb ? bsum[i] : 0;
-    int64_t tot;
-    int64_t pre = block_excl_scan_i64(v, &tot);
-    if (i < nb) bsum[i] = carry + pre;
-    __syncthreads();
-    if (threadIdx.x == 0) carry += tot;
-    __syncthreads();
-  }
-  if (threadIdx.x == 0 && total) *total = carry;
-}
+// Single-pass scan with decoupled look-back.  Tiles are claimed in order
+// from a counter, so a tile only waits on tiles claimed before it, and every
+// tile publishes its own aggregate before it waits: the waits always end.
+// A tile's state word packs (value << 10 | epoch << 2 | status) with status
+// 1 = tile aggregate, 2 = inclusive prefix; words of another epoch (an
+// earlier scan) read as not ready.  Inputs are non-negative counts below
+// 2^53.  The wait is bounded all the same: past LB_SPINS polls the tile sets
+// *err and carries on (the host turns the flag into LDL_E_TIMEOUT).
+constexpr int LB_ITEMS = 8;
+constexpr int LB_TILE = SC_THREADS * LB_ITEMS;
+constexpr uint32_t LB_SPINS = 1u << 20;
 
-__global__ void k_scan_add(int64_t* out, int64_t n, const int64_t* bsum) {
-  const int64_t base = (int64_t)blockIdx.x * SC_TILE;
-  const int64_t add = bsum[blockIdx.x];
-  for (int k = threadIdx.x; k < SC_TILE; k += SC_THREADS) {
-    int64_t i = base + k;
-    if (i < n) out[i] += add;
+template <class T>
+__global__ void __launch_bounds__(SC_THREADS) k_scan_lb(const T* in, int64_t* out, int64_t n, u64* st, int32_t* ctr,
+                                                        uint32_t ep, int64_t* total, int32_t* err) {
+  __shared__ int64_t s_tile, s_pre;
+  if (threadIdx.x == 0) s_tile = atomicAdd(ctr, 1);
+  __syncthreads();
+  const int64_t tile = s_tile;
+  const int64_t base = tile * LB_TILE + (int64_t)threadIdx.x * LB_ITEMS;
+  int64_t loc[LB_ITEMS];
+  int64_t sum = 0;
+  for (int k = 0; k < LB_ITEMS; ++k) {
+    const int64_t i = base + k;
+    loc[k] = i < n ? (int64_t)in[i] : 0;
+    sum += loc[k];
+  }
+  int64_t agg;
+  const int64_t pre = block_excl_scan_i64(sum, &agg);
+  if (threadIdx.x == 0) {
+    const u64 tag = (u64)(ep & 255u) << 2;
+    int64_t acc = 0;
+    if (tile > 0) {
+      atomicExch((unsigned long long*)&st[tile], ((u64)agg << 10) | tag | 1u);
+      uint32_t spins = 0;
+      for (int64_t j = tile - 1; j >= 0;) {
+        const u64 x = *(volatile const u64*)&st[j];
+        if (((x >> 2) & 255u) != (ep & 255u) || (x & 3u) == 0) {
+          if (++spins > LB_SPINS) {
+            atomicExch(err, 1);
+            break;
+          }
+          __nanosleep(32);
+          continue;
+        }
+        acc += (int64_t)(x >> 10);
+        if ((x & 3u) == 2u) break;
+        --j;
+      }
+    }
+    atomicExch((unsigned long long*)&st[tile], ((u64)(acc + agg) << 10) | tag | 2u);
+    s_pre = acc;
+    if ((tile + 1) * LB_TILE >= n && total) *total = acc + agg;
+  }
+  __syncthreads();
+  int64_t p = s_pre + pre;
+  for (int k = 0; k < LB_ITEMS; ++k) {
+    const int64_t i = base + k;
+    if (i < n) out[i] = p;
+    p += loc[k];
   }
 }
 
@@ -346,57 +363,60 @@ __global__ void k_compact_pairs(const u64* ukeys, const int64_t* usum, int64_t n
 }  // namespace
 
 // ---------------------------------------------------------------- host wrappers
-int64_t scan_exclusive(const int64_t* in, int64_t* out, int64_t n, Prims& P, cudaStream_t s, bool want_total) {
-  if (n <= 0) return 0;
-  int64_t nb = (n + SC_TILE - 1) / SC_TILE;
-  P.bsum.reserve(nb + 1, s);
-  if (nb == 1) {
-    k_scan_one<int64_t><<<1, SC_THREADS, 0, s>>>(in, out, n, P.bsum.p + 1);
-    CKL("k_scan_one");
-    if (!want_total) return -1;
-    int64_t tot = 0;
-    CK(cudaMemcpyAsync(&tot, P.bsum.p + 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    return tot;
+// Look-back state for the next multi-tile scan of n items: the tile words,
+// this scan's epoch (1..255) and its tile counter.  When the epoch wraps, or
+// the state grows, everything is cleared so that no stale word matches.
+static uint32_t lb_begin(Prims& P, int64_t n, cudaStream_t s) {
+  const int64_t tiles = (n + LB_TILE - 1) / LB_TILE;
+  if (P.lb_ctl.cap == 0) {
+    P.lb_ctl.exact(257);  // 256 epoch counters + the error flag
+    CK(cudaMemsetAsync(P.lb_ctl.p, 0, sizeof(int32_t) * 257, s));
+    P.lb_ep = 0;
   }
-  k_scan_tile<int64_t><<<(unsigned)nb, SC_THREADS, 0, s>>>(in, out, n, P.bsum.p);
-  CKL("k_scan_tile");
-  k_scan_bsums<<<1, SC_THREADS, 0, s>>>(P.bsum.p, nb, P.bsum.p + nb);
-  CKL("k_scan_bsums");
-  k_scan_add<<<(unsigned)nb, SC_THREADS, 0, s>>>(out, n, P.bsum.p);
-  CKL("k_scan_add");
+  bool clear = false;
+  if (tiles > P.lb_st.cap) {
+    P.lb_st.reserve(tiles, s);
+    clear = true;
+  }
+  if (++P.lb_ep > 255) clear = true;
+  if (clear) {
+    CK(cudaMemsetAsync(P.lb_st.p, 0, sizeof(u64) * (size_t)P.lb_st.cap, s));
+    CK(cudaMemsetAsync(P.lb_ctl.p, 0, sizeof(int32_t) * 256, s));
+    P.lb_ep = 1;
+  }
+  return P.lb_ep;
+}
+
+template <class T>
+static int64_t scan_t(const T* in, int64_t* out, int64_t n, Prims& P, cudaStream_t s, bool want_total) {
+  if (n <= 0) return 0;
+  P.bsum.reserve(2, s);
+  if (n <= SC_TILE) {
+    k_scan_one<T><<<1, SC_THREADS, 0, s>>>(in, out, n, P.bsum.p + 1);
+    CKL("k_scan_one");
+  } else {
+    const uint32_t ep = lb_begin(P, n, s);
+    const int64_t tiles = (n + LB_TILE - 1) / LB_TILE;
+    k_scan_lb<T><<<(unsigned)tiles, SC_THREADS, 0, s>>>(in, out, n, P.lb_st.p, P.lb_ctl.p + ep, ep, P.bsum.p + 1,
+                                                        P.lb_ctl.p + 256);
+    CKL("k_scan_lb");
+  }
   if (!want_total) return -1;
   int64_t tot = 0;
-  CK(cudaMemcpyAsync(&tot, P.bsum.p + nb, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(&tot, P.bsum.p + 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   return tot;
 }
 
-int64_t scan_exclusive_i32(const int32_t* in, int64_t* out, int64_t n, Prims& P, cudaStream_t s, bool want_total) {
-  if (n <= 0) return 0;
-  int64_t nb = (n + SC_TILE - 1) / SC_TILE;
-  P.bsum.reserve(nb + 1, s);
-  if (nb == 1) {
-    k_scan_one<int32_t><<<1, SC_THREADS, 0, s>>>(in, out, n, P.bsum.p + 1);
-    CKL("k_scan_one");
-    if (!want_total) return -1;
-    int64_t tot = 0;
-    CK(cudaMemcpyAsync(&tot, P.bsum.p + 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    return tot;
-  }
-  k_scan_tile<int32_t><<<(unsigned)nb, SC_THREADS, 0, s>>>(in, out, n, P.bsum.p);
-  CKL("k_scan_tile32");
-  k_scan_bsums<<<1, SC_THREADS, 0, s>>>(P.bsum.p, nb, P.bsum.p + nb);
-  CKL("k_scan_bsums");
-  k_scan_add<<<(unsigned)nb, SC_THREADS, 0, s>>>(out, n, P.bsum.p);
-  CKL("k_scan_add");
-  if (!want_total) return -1;
-  int64_t tot = 0;
-  CK(cudaMemcpyAsync(&tot, P.bsum.p + nb, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
-  return tot;
+int64_t scan_exclusive(const int64_t* in, int64_t* out, int64_t n, Prims& P, cudaStream_t s, bool want_total) {
+  return scan_t<int64_t>(in, out, n, P, s, want_total);
 }
+
+int64_t scan_exclusive_i32(const int32_t* in, int64_t* out, int64_t n, Prims& P, cudaStream_t s, bool want_total) {
+  return scan_t<int32_t>(in, out, n, P, s, want_total);
+}
+
+int32_t* scan_error_flag(Prims& P) { return P.lb_ctl.cap ? P.lb_ctl.p + 256 : nullptr; }
 
 void radix_sort_pairs(u64*& keys, u64*& vals, u64*& tk, u64*& tv, int64_t n, int bits, Prims& P, cudaStream_t s,
                       int lo_bit) {

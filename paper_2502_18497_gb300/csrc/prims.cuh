@@ -5,15 +5,22 @@
 struct Prims {  // scratch owned by a context
   DBuf<int64_t> bsum, hist, pos, usum;
   DBuf<int32_t> flag;
+  DBuf<u64> lb_st;       // look-back scan: per-tile state words
+  DBuf<int32_t> lb_ctl;  // look-back scan: 256 epoch tile counters, then the error flag
+  uint32_t lb_ep = 0;
   void release() {
     bsum.release(); hist.release(); pos.release(); usum.release();
-    flag.release();
+    flag.release(); lb_st.release(); lb_ctl.release();
+    lb_ep = 0;
   }
 };
 
 // out[i] = sum of in[0..i); returns the total when want_total (synchronises).
 int64_t scan_exclusive(const int64_t* in, int64_t* out, int64_t n, Prims& P, cudaStream_t s, bool want_total);
 int64_t scan_exclusive_i32(const int32_t* in, int64_t* out, int64_t n, Prims& P, cudaStream_t s, bool want_total);
+// Device flag set when a scan's bounded look-back wait gave up (nullptr
+// before the first multi-tile scan).
+int32_t* scan_error_flag(Prims& P);
 
 // Stable LSD radix sort of n (key, value) pairs on the low `bits` key bits,
 // 8 bits per pass.  The sorted data ends in (keys, vals); the pointers are
