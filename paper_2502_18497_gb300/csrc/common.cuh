@@ -269,10 +269,11 @@ struct SlackCSR {
 // 2 128-thread blocks, 3 256-thread blocks, 4 block clusters, 5 the hub
 // accumulation kernel, 6 the rest of the hub path (table set-up, evaluation,
 // final reduction).  A sweep records KS_EVENTS events; interval j (event j to
-// j + 1) is charged to group ks_interval_group(j).
+// j + 1) is charged to group ks_interval_group(j), or to none (-1: the host's
+// wait for the bin counts).
 constexpr int KS_GROUPS = 7;
-constexpr int KS_EVENTS = 9;
-__host__ __device__ constexpr int ks_interval_group(int j) { return j < 5 ? j : j == 6 ? 5 : 6; }
+constexpr int KS_EVENTS = 10;
+__host__ __device__ constexpr int ks_interval_group(int j) { return j < 5 ? j : j == 5 ? -1 : j == 7 ? 5 : 6; }
 
 struct DevScalars {
   I128 dq;          // numerator change of the current mini-batch
@@ -284,6 +285,7 @@ struct DevScalars {
   int64_t scanned;  // adjacency entries scanned
   int64_t err_key;  // packed (index << 8 | status) of the first failing update
   int64_t pool_top;
+  int64_t seg_n, seg_stot, seg_wtot;  // CSR update: segments, scratch and rebuild totals
   int64_t sw_entries[KS_GROUPS];  // per sweep kernel group: adjacency entries read since statistics
                                   // were enabled
   int64_t sw_bytes[KS_GROUPS];    // algorithmic bytes of the same sweeps

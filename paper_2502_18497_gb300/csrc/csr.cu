@@ -74,9 +74,10 @@ __global__ void k_seg_info(const u64* keys, int64_t nrec, int bshift, const int3
 }
 
 // Per segment: new length, whether the row is rebuilt, relocation size.
-__global__ void k_plan(int64_t nseg, int64_t nrec, const int64_t* seg_start, const int64_t* seg_row,
+__global__ void k_plan(const int64_t* nsegp, int64_t nrec, const int64_t* seg_start, const int64_t* seg_row,
                        const int64_t* pins, const int64_t* pdel, const int32_t* len, const int32_t* cap,
                        int32_t* newcap, int64_t* scratch_len, int64_t* work_len, int64_t* need) {
+  const int64_t nseg = *nsegp;
   GRID_STRIDE(s, nseg) {
     const int64_t a = seg_start[s];
     const int64_t b = s + 1 < nseg ? seg_start[s + 1] : nrec;
@@ -366,34 +367,38 @@ void csr_apply(SlackCSR<WT>& g, const u64* keys, const int64_t* delta, int64_t n
   k_rec_flags<<<gr, TPB, 0, s>>>(keys, delta, nrec, bshift, S.pos.p, S.oldw.p, S.fins.p, S.fdel.p, S.fhead.p,
                                  &d_sc->cnt[C_Z]);
   CKL("k_rec_flags");
-  scan_exclusive_i32(S.fins.p, S.pins.p, nrec + 1, P, s, false);
-  scan_exclusive_i32(S.fdel.p, S.pdel.p, nrec + 1, P, s, false);
-  const int64_t nseg = scan_exclusive_i32(S.fhead.p, S.segid.p, nrec, P, s, true);
-  S.seg.reserve(nseg + 1, s);
-  S.segrow.reserve(nseg + 1, s);
-  S.newcap.reserve(nseg + 1, s);
-  S.slen.reserve(nseg + 2, s);
-  S.wlen.reserve(nseg + 2, s);
-  S.soff.reserve(nseg + 2, s);
-  S.woff.reserve(nseg + 2, s);
+  scan_exclusive_i32_to(S.fins.p, S.pins.p, nrec + 1, nullptr, nrec + 1, nullptr, P, s);
+  scan_exclusive_i32_to(S.fdel.p, S.pdel.p, nrec + 1, nullptr, nrec + 1, nullptr, P, s);
+  // the segment count stays on the device: segment arrays are sized for one
+  // segment per record, and the plan and its scans read the count there
+  scan_exclusive_i32_to(S.fhead.p, S.segid.p, nrec, nullptr, nrec, &d_sc->seg_n, P, s);
+  S.seg.reserve(nrec + 1, s);
+  S.segrow.reserve(nrec + 1, s);
+  S.newcap.reserve(nrec + 1, s);
+  S.slen.reserve(nrec + 2, s);
+  S.wlen.reserve(nrec + 2, s);
+  S.soff.reserve(nrec + 2, s);
+  S.woff.reserve(nrec + 2, s);
   k_seg_info<<<gr, TPB, 0, s>>>(keys, nrec, bshift, S.fhead.p, S.segid.p, S.seg.p, S.segrow.p);
   CKL("k_seg_info");
   CK(cudaMemsetAsync(&d_sc->need, 0, sizeof(int64_t), s));
-  const int gs = grid_for(nseg, TPB);
-  k_plan<<<gs, TPB, 0, s>>>(nseg, nrec, S.seg.p, S.segrow.p, S.pins.p, S.pdel.p, g.len.p, g.cap.p, S.newcap.p,
-                            S.slen.p, S.wlen.p, &d_sc->need);
+  k_plan<<<gr, TPB, 0, s>>>(&d_sc->seg_n, nrec, S.seg.p, S.segrow.p, S.pins.p, S.pdel.p, g.len.p, g.cap.p,
+                            S.newcap.p, S.slen.p, S.wlen.p, &d_sc->need);
   CKL("k_plan");
-  scan_exclusive(S.slen.p, S.soff.p, nseg + 1, P, s, false);
-  scan_exclusive(S.wlen.p, S.woff.p, nseg + 1, P, s, false);
-  int64_t tot[3] = {0, 0, 0};
+  scan_exclusive_to(S.slen.p, S.soff.p, 1, &d_sc->seg_n, nrec + 1, &d_sc->seg_stot, P, s);
+  scan_exclusive_to(S.wlen.p, S.woff.p, 1, &d_sc->seg_n, nrec + 1, &d_sc->seg_wtot, P, s);
+  static_assert(offsetof(DevScalars, seg_stot) == offsetof(DevScalars, seg_n) + 8 &&
+                    offsetof(DevScalars, seg_wtot) == offsetof(DevScalars, seg_n) + 16,
+                "adjacent totals");
+  int64_t tot[4] = {0, 0, 0, 0};  // need, nseg, scratch total, rebuild total
   int32_t bad = 0;
   CK(cudaMemcpyAsync(&tot[0], &d_sc->need, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-  CK(cudaMemcpyAsync(&tot[1], S.soff.p + nseg, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-  CK(cudaMemcpyAsync(&tot[2], S.woff.p + nseg, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(&tot[1], &d_sc->seg_n, 3 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(&bad, &d_sc->cnt[C_Z], sizeof(int32_t), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   if (bad) ldl_throw(LDL_E_INVALID, "internal: adjacency update would make a weight negative");
-  const int64_t need = tot[0], stotal = tot[1], wtotal = tot[2];
+  const int64_t need = tot[0], nseg = tot[1], stotal = tot[2], wtotal = tot[3];
+  const int gs = grid_for(nseg, TPB);
   if (g.pool_top + need > g.col.cap) compact_pool<WT>(g, need, S, P, s);
   k_update<WT><<<gr, TPB, 0, s>>>(g.off.p, keys, delta, nrec, bshift, S.pos.p, S.oldw.p, g.w.p);
   CKL("k_update");

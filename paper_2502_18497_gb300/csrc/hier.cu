@@ -944,8 +944,8 @@ void aggregate(ldl_ctx& c, int r, int32_t epD, int32_t epC, int32_t epA_next, bo
     int ie = K_E;
     int32_t* le2 = c.lE2.p;
     int ie2 = K_E2;
+    int32_t ne = rd_cnt(c, ie);
     for (int q = r + 1; q <= c.T; ++q) {
-      const int32_t ne = rd_cnt(c, ie);
       if (ne == 0) break;
       const bool has_up = q < c.T;
       const int32_t epE2 = c.next_epoch();
@@ -959,7 +959,12 @@ void aggregate(ldl_ctx& c, int r, int32_t epD, int32_t epC, int32_t epA_next, bo
                                                   c.dcnt + K_CREC, c.stE.p, epE2, le2, c.dcnt + ie2,
                                                   c.dcnt + K_ERR);
       CKL("k_exist");
-      const int64_t nd = rd_cnt(c, K_CREC);
+      // children records of this level and the next level's list, in one read
+      int32_t nd = 0, ne_next = 0;
+      ++c.syncs;
+      CK(cudaMemcpyAsync(&nd, c.dcnt + K_CREC, sizeof(int32_t), cudaMemcpyDeviceToHost, c.s));
+      CK(cudaMemcpyAsync(&ne_next, c.dcnt + ie2, sizeof(int32_t), cudaMemcpyDeviceToHost, c.s));
+      CK(cudaStreamSynchronize(c.s));
       if (nd > 0) {
         sort_pairs(c.crk, c.crv, c.tk, c.tv, nd, 2 * c.bits, c.P, c.s);
         csr_apply<int32_t>(c.lv[q].children, c.crk.p, (const int64_t*)c.crv.p, nd, c.bits, c.CS, c.P, c.s, c.d_sc);
@@ -970,6 +975,7 @@ void aggregate(ldl_ctx& c, int r, int32_t epD, int32_t epC, int32_t epA_next, bo
       int ti = ie;
       ie = ie2;
       ie2 = ti;
+      ne = ne_next;
     }
     if (rd_cnt(c, K_ERR)) ldl_throw(LDL_E_INVALID, "internal: new supernode already has a parent");
   } else {

@@ -15,8 +15,15 @@ void expand_set(ldl_ctx& c, int r, const int32_t* list, int idx_n, int32_t* stam
 void filter_alive(ldl_ctx& c, int r, const int32_t* list, int idx_n, int32_t* olist, int idx_out, int64_t n_hint);
 void union_into(ldl_ctx& c, const int32_t* list, int idx_n, int32_t* stamp, int32_t ep, int32_t* olist, int idx_out,
                 int64_t n_hint);
-int32_t sweep(ldl_ctx& c, int r, int mode, const int32_t* list, int idx_n, int64_t n_hint);
-int32_t decouple(ldl_ctx& c, int32_t nc);
+// BestMove (mode 0) / BestRef (mode 1) over the listed nodes; the candidates
+// and their count (counter K_CAND) stay on the device.
+void sweep(ldl_ctx& c, int r, int mode, const int32_t* list, int idx_n, int64_t n_hint);
+// Decoupling filter over the last sweep's candidates: returns their number
+// and the number accepted (the accepted moves are in bv / bsrc / bdst).
+struct DecoupleOut {
+  int32_t nc, nb;
+};
+DecoupleOut decouple(ldl_ctx& c);
 CommitOut commit_move(ldl_ctx& c, int r, int32_t nb, int32_t epB, int32_t epT, int32_t epCh);
 void rollback_move(ldl_ctx& c, int r, int32_t nb, int32_t ntc);
 void mark_moved(ldl_ctx& c, int r, int32_t nb, int32_t epMv, int32_t epM0);

@@ -180,12 +180,13 @@ static void move_loop(ldl_ctx& c, int r, int rounds, int32_t epU, int32_t epMv, 
     const int32_t nS = rd_cnt(c, K_S);
     stage_end(c, ST_EXPAND);
     stage_begin(c);
-    const int32_t nc = sweep(c, r, 0, c.lS.p, K_S, nS);
+    sweep(c, r, 0, c.lS.p, K_S, nS);
     stage_end(c, ST_BEST);
-    if (nc == 0) break;
     stage_begin(c);
-    const int32_t nb = decouple(c, nc);
+    const DecoupleOut dd = decouple(c);
     stage_end(c, ST_DECOUPLE);
+    const int32_t nc = dd.nc, nb = dd.nb;
+    if (nc == 0) break;
     c.res.rejected += nc - nb;
     if (nb == 0) break;
     stage_begin(c);
@@ -229,9 +230,10 @@ static int64_t refine_loop(ldl_ctx& c, int r, int rounds, int32_t epD) {
     const int32_t nR = rd_cnt(c, iR);
     if (nR == 0) break;
     c.res.rounds++;
-    const int32_t nc = sweep(c, r, 1, R, iR, nR);
+    sweep(c, r, 1, R, iR, nR);
+    const DecoupleOut dd = decouple(c);
+    const int32_t nc = dd.nc, nb = dd.nb;
     if (nc == 0) break;
-    const int32_t nb = decouple(c, nc);
     c.res.rejected += nc - nb;
     if (nb == 0) break;
     commit_ref(c, r, nb);
@@ -671,6 +673,7 @@ ldl_status ldl_get_kernel_stats(const ldl_ctx* c, double* out) {
     for (size_t i = 0; i + KS_EVENTS <= c->kev_used; i += KS_EVENTS)
       for (int j = 0; j + 1 < KS_EVENTS; ++j) {
         float t = 0;
+        if (ks_interval_group(j) < 0) continue;
         CK(cudaEventElapsedTime(&t, c->kev[i + j], c->kev[i + j + 1]));
         ms[ks_interval_group(j)] += t;
       }

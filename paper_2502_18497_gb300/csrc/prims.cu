@@ -35,7 +35,8 @@ __device__ inline int64_t block_excl_scan_i64(int64_t v, int64_t* total) {
 
 // whole input in one tile: scan and total in one launch
 template <class T>
-__global__ void k_scan_one(const T* in, int64_t* out, int64_t n, int64_t* total) {
+__global__ void k_scan_one(const T* in, int64_t* out, int64_t n, const int64_t* n_dev, int64_t* total) {
+  if (n_dev) n += *n_dev;
   const int64_t base = (int64_t)threadIdx.x * SC_ITEMS;
   int64_t loc[SC_ITEMS];
   int64_t s = 0;
@@ -67,12 +68,15 @@ constexpr int LB_TILE = SC_THREADS * LB_ITEMS;
 constexpr uint32_t LB_SPINS = 1u << 20;
 
 template <class T>
-__global__ void __launch_bounds__(SC_THREADS) k_scan_lb(const T* in, int64_t* out, int64_t n, u64* st, int32_t* ctr,
-                                                        uint32_t ep, int64_t* total, int32_t* err) {
+__global__ void __launch_bounds__(SC_THREADS) k_scan_lb(const T* in, int64_t* out, int64_t n, const int64_t* n_dev,
+                                                        u64* st, int32_t* ctr, uint32_t ep, int64_t* total,
+                                                        int32_t* err) {
   __shared__ int64_t s_tile, s_pre;
+  if (n_dev) n += *n_dev;  // launched for an upper bound; tiles past n leave at once
   if (threadIdx.x == 0) s_tile = atomicAdd(ctr, 1);
   __syncthreads();
   const int64_t tile = s_tile;
+  if (tile * LB_TILE >= n && tile > 0) return;
   const int64_t base = tile * LB_TILE + (int64_t)threadIdx.x * LB_ITEMS;
   int64_t loc[LB_ITEMS];
   int64_t sum = 0;
@@ -387,20 +391,28 @@ static uint32_t lb_begin(Prims& P, int64_t n, cudaStream_t s) {
   return P.lb_ep;
 }
 
+// n items, or (n_dev != nullptr) *n_dev + n items with n_max an upper bound;
+// the total goes to total_dev (device) when given.
+template <class T>
+static void scan_launch(const T* in, int64_t* out, int64_t n, const int64_t* n_dev, int64_t n_max, int64_t* total_dev,
+                        Prims& P, cudaStream_t s) {
+  if (n_max <= SC_TILE) {
+    k_scan_one<T><<<1, SC_THREADS, 0, s>>>(in, out, n, n_dev, total_dev);
+    CKL("k_scan_one");
+  } else {
+    const uint32_t ep = lb_begin(P, n_max, s);
+    const int64_t tiles = (n_max + LB_TILE - 1) / LB_TILE;
+    k_scan_lb<T><<<(unsigned)tiles, SC_THREADS, 0, s>>>(in, out, n, n_dev, P.lb_st.p, P.lb_ctl.p + ep, ep, total_dev,
+                                                        P.lb_ctl.p + 256);
+    CKL("k_scan_lb");
+  }
+}
+
 template <class T>
 static int64_t scan_t(const T* in, int64_t* out, int64_t n, Prims& P, cudaStream_t s, bool want_total) {
   if (n <= 0) return 0;
   P.bsum.reserve(2, s);
-  if (n <= SC_TILE) {
-    k_scan_one<T><<<1, SC_THREADS, 0, s>>>(in, out, n, P.bsum.p + 1);
-    CKL("k_scan_one");
-  } else {
-    const uint32_t ep = lb_begin(P, n, s);
-    const int64_t tiles = (n + LB_TILE - 1) / LB_TILE;
-    k_scan_lb<T><<<(unsigned)tiles, SC_THREADS, 0, s>>>(in, out, n, P.lb_st.p, P.lb_ctl.p + ep, ep, P.bsum.p + 1,
-                                                        P.lb_ctl.p + 256);
-    CKL("k_scan_lb");
-  }
+  scan_launch<T>(in, out, n, nullptr, n, P.bsum.p + 1, P, s);
   if (!want_total) return -1;
   int64_t tot = 0;
   CK(cudaMemcpyAsync(&tot, P.bsum.p + 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
@@ -414,6 +426,18 @@ int64_t scan_exclusive(const int64_t* in, int64_t* out, int64_t n, Prims& P, cud
 
 int64_t scan_exclusive_i32(const int32_t* in, int64_t* out, int64_t n, Prims& P, cudaStream_t s, bool want_total) {
   return scan_t<int32_t>(in, out, n, P, s, want_total);
+}
+
+void scan_exclusive_to(const int64_t* in, int64_t* out, int64_t n, const int64_t* n_dev, int64_t n_max,
+                       int64_t* total_dev, Prims& P, cudaStream_t s) {
+  if (n_max <= 0) return;
+  scan_launch<int64_t>(in, out, n, n_dev, n_max, total_dev, P, s);
+}
+
+void scan_exclusive_i32_to(const int32_t* in, int64_t* out, int64_t n, const int64_t* n_dev, int64_t n_max,
+                           int64_t* total_dev, Prims& P, cudaStream_t s) {
+  if (n_max <= 0) return;
+  scan_launch<int32_t>(in, out, n, n_dev, n_max, total_dev, P, s);
 }
 
 int32_t* scan_error_flag(Prims& P) { return P.lb_ctl.cap ? P.lb_ctl.p + 256 : nullptr; }

@@ -18,6 +18,13 @@ struct Prims {  // scratch owned by a context
 // out[i] = sum of in[0..i); returns the total when want_total (synchronises).
 int64_t scan_exclusive(const int64_t* in, int64_t* out, int64_t n, Prims& P, cudaStream_t s, bool want_total);
 int64_t scan_exclusive_i32(const int32_t* in, int64_t* out, int64_t n, Prims& P, cudaStream_t s, bool want_total);
+// The same without a host read: the length is n, or *n_dev + n when n_dev is
+// given (then n_max bounds it and sizes the launch); the total is written to
+// total_dev (device) when that is not null.
+void scan_exclusive_to(const int64_t* in, int64_t* out, int64_t n, const int64_t* n_dev, int64_t n_max,
+                       int64_t* total_dev, Prims& P, cudaStream_t s);
+void scan_exclusive_i32_to(const int32_t* in, int64_t* out, int64_t n, const int64_t* n_dev, int64_t n_max,
+                           int64_t* total_dev, Prims& P, cudaStream_t s);
 // Device flag set when a scan's bounded look-back wait gave up (nullptr
 // before the first multi-tile scan).
 int32_t* scan_error_flag(Prims& P);

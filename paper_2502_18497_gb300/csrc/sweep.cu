@@ -697,13 +697,18 @@ __global__ void k_dec_finish(int32_t nc, const int32_t* cst, const int32_t* cv, 
 constexpr int DEC_SMALL = 8192;
 constexpr int DEC_THREADS = 1024;
 
-__global__ void __launch_bounds__(DEC_THREADS) k_dec_block(int32_t nc, int32_t* cst, const int32_t* cv,
+__global__ void __launch_bounds__(DEC_THREADS) k_dec_block(const int32_t* ncp, int32_t* cst, const int32_t* cv,
                                                            const int32_t* src, const int32_t* dst,
                                                            const int64_t* ghi, const uint64_t* glo, int32_t* role,
                                                            int32_t* best, int32_t* bv, int32_t* bsrc, int32_t* bdst,
                                                            int32_t* nb, int32_t* stat) {
   __shared__ int32_t left;
   const int tid = threadIdx.x;
+  const int32_t nc = *ncp;
+  if (nc > DEC_SMALL) {  // left to the multi-block rounds
+    if (tid == 0) *stat = -2;
+    return;
+  }
   for (int32_t i = tid; i < nc; i += DEC_THREADS) cst[i] = 0;
   __syncthreads();
   int32_t rounds = 0;
@@ -983,7 +988,7 @@ static cudaEvent_t* kstats_events(ldl_ctx& c) {
 }
 
 template <class WT, int MODE>
-static int32_t sweep_t(ldl_ctx& c, int r, Adj<WT> out, Adj<WT> in, const int32_t* list, int idx_n, int64_t n_hint) {
+static void sweep_t(ldl_ctx& c, int r, Adj<WT> out, Adj<WT> in, const int32_t* list, int idx_n, int64_t n_hint) {
   LevelState& L = c.lv[r];
   SweepArgs<WT> A;
   A.out = out;
@@ -1025,6 +1030,41 @@ static int32_t sweep_t(ldl_ctx& c, int r, Adj<WT> out, Adj<WT> in, const int32_t
                                                      c.dcnt + K_CLU, c.binL.p, c.dcnt + K_LARGE, c.binLsz.p,
                                                      &c.d_sc->need, std::min(c.prm.cluster_max_deg, CLUSTER_DEG));
   CKL("k_bin");
+  // Every bin but the hubs is swept by a grid-stride kernel that reads its
+  // bin's count on the device, so these launch before the counts come back
+  // and the host's wait below overlaps them.  n_hint bounds every bin.
+  cudaEvent_t* kev = c.kstats ? kstats_events(c) : nullptr;
+  if (kev) CK(cudaEventRecord(kev[0], c.s));
+  k_sweep_group<WT, MODE, 8><<<grid_for(n_hint * 8, TPB, 152 * 5), TPB, 0, c.s>>>(A, c.binT.p, c.dcnt + K_TINY);
+  CKL("k_sweep_group<8>");
+  if (kev) CK(cudaEventRecord(kev[1], c.s));
+  k_sweep_group<WT, MODE, 32><<<grid_for(n_hint * 32, TPB, 152 * 5), TPB, 0, c.s>>>(A, c.binS.p,
+                                                                                    c.dcnt + K_SMALL);
+  CKL("k_sweep_group<32>");
+  if (kev) CK(cudaEventRecord(kev[2], c.s));
+  {
+    const size_t sm = (sizeof(int64_t) + sizeof(int32_t)) * 1024;
+    k_sweep_block<WT, MODE, 128, 1024><<<grid_for(n_hint, 1, 152 * 16), 128, sm, c.s>>>(A, c.binM.p,
+                                                                                     c.dcnt + K_MID);
+    CKL("k_sweep_block(mid1)");
+  }
+  if (kev) CK(cudaEventRecord(kev[3], c.s));
+  {
+    const size_t sm = (sizeof(int64_t) + sizeof(int32_t)) * HB;
+    CK(cudaFuncSetAttribute(k_sweep_block<WT, MODE, 256, HB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_sweep_block<WT, MODE, 256, HB><<<grid_for(n_hint, 1, 152 * 4), 256, sm, c.s>>>(A, c.binM2.p,
+                                                                                   c.dcnt + K_MID2);
+    CKL("k_sweep_block(mid2)");
+  }
+  if (kev) CK(cudaEventRecord(kev[4], c.s));
+  if (c.prm.cluster_max_deg > MID_DEG) {
+    const size_t sm = (sizeof(int64_t) + sizeof(int32_t)) * CL_SLOTS;
+    CK(cudaFuncSetAttribute(k_sweep_cluster<WT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    const int ncl = (int)std::min<int64_t>(n_hint, 152 * 2 / CL);
+    k_sweep_cluster<WT, MODE><<<ncl * CL, TPB, sm, c.s>>>(A, c.binC.p, c.dcnt + K_CLU);
+    CKL("k_sweep_cluster");
+  }
+  if (kev) CK(cudaEventRecord(kev[5], c.s));
   // counters K_SMALL .. K_CLU in one read
   int32_t cn[K_CLU - K_SMALL + 1];
   int64_t tab = 0;
@@ -1033,39 +1073,7 @@ static int32_t sweep_t(ldl_ctx& c, int r, Adj<WT> out, Adj<WT> in, const int32_t
   CK(cudaStreamSynchronize(c.s));
   const int32_t ct = cn[K_TINY - K_SMALL], cs = cn[0], cm = cn[K_MID - K_SMALL], cm2 = cn[K_MID2 - K_SMALL];
   const int32_t cc = cn[K_CLU - K_SMALL], ch = cn[K_LARGE - K_SMALL];
-  cudaEvent_t* kev = c.kstats ? kstats_events(c) : nullptr;
-  if (kev) CK(cudaEventRecord(kev[0], c.s));
-  if (ct > 0) {
-    k_sweep_group<WT, MODE, 8><<<grid_for((int64_t)ct * 8, TPB), TPB, 0, c.s>>>(A, c.binT.p, c.dcnt + K_TINY);
-    CKL("k_sweep_group<8>");
-  }
-  if (kev) CK(cudaEventRecord(kev[1], c.s));
-  if (cs > 0) {
-    k_sweep_group<WT, MODE, 32><<<grid_for((int64_t)cs * 32, TPB), TPB, 0, c.s>>>(A, c.binS.p, c.dcnt + K_SMALL);
-    CKL("k_sweep_group<32>");
-  }
-  if (kev) CK(cudaEventRecord(kev[2], c.s));
-  if (cm > 0) {
-    const size_t sm = (sizeof(int64_t) + sizeof(int32_t)) * 1024;
-    k_sweep_block<WT, MODE, 128, 1024><<<grid_for(cm, 1, 152 * 16), 128, sm, c.s>>>(A, c.binM.p, c.dcnt + K_MID);
-    CKL("k_sweep_block(mid1)");
-  }
-  if (kev) CK(cudaEventRecord(kev[3], c.s));
-  if (cm2 > 0) {
-    const size_t sm = (sizeof(int64_t) + sizeof(int32_t)) * HB;
-    CK(cudaFuncSetAttribute(k_sweep_block<WT, MODE, 256, HB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    k_sweep_block<WT, MODE, 256, HB><<<grid_for(cm2, 1, 152 * 4), 256, sm, c.s>>>(A, c.binM2.p, c.dcnt + K_MID2);
-    CKL("k_sweep_block(mid2)");
-  }
-  if (kev) CK(cudaEventRecord(kev[4], c.s));
-  if (cc > 0) {
-    const size_t sm = (sizeof(int64_t) + sizeof(int32_t)) * CL_SLOTS;
-    CK(cudaFuncSetAttribute(k_sweep_cluster<WT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    const int ncl = std::min<int>(cc, 152 * 2 / CL);
-    k_sweep_cluster<WT, MODE><<<ncl * CL, TPB, sm, c.s>>>(A, c.binC.p, c.dcnt + K_CLU);
-    CKL("k_sweep_cluster");
-  }
-  if (kev) CK(cudaEventRecord(kev[5], c.s));
+  if (kev) CK(cudaEventRecord(kev[6], c.s));  // the wait above is charged to no kernel
   if (ch > 0) {
     const int32_t nh = ch;
     c.gkeys.reserve(tab, c.s);
@@ -1085,11 +1093,11 @@ static int32_t sweep_t(ldl_ctx& c, int r, Adj<WT> out, Adj<WT> in, const int32_t
     k_hub_init<<<grid_for(tab, TPB), TPB, 0, c.s>>>(c.gkeys.p, c.gvals.p, tab);
     CKL("k_hub_init");
     ChunkMap m = chunk_map(c, c.binL.p, c.dcnt + K_LARGE, nh, out.len, c.directed ? in.len : nullptr);
-    if (kev) CK(cudaEventRecord(kev[6], c.s));
+    if (kev) CK(cudaEventRecord(kev[7], c.s));
     k_hub_acc<WT, MODE><<<grid_for((int64_t)nh * 2048, TPB, 152 * 16), TPB, 0, c.s>>>(A, m, c.binLoff.p, c.binLsz.p,
                                                                                       c.gkeys.p, c.gvals.p);
     CKL("k_hub_acc");
-    if (kev) CK(cudaEventRecord(kev[7], c.s));
+    if (kev) CK(cudaEventRecord(kev[8], c.s));
     k_hub_eval<WT, MODE><<<grid_for(ech, 1, 152 * 8), TPB, 0, c.s>>>(A, c.binL.p, nh, c.binLoff.p, c.binLsz.p,
                                                                     c.hub_epre.p, c.gkeys.p, c.gvals.p, c.pb_hi.p,
                                                                     c.pb_lo.p, c.pb_c.p);
@@ -1098,13 +1106,13 @@ static int32_t sweep_t(ldl_ctx& c, int r, Adj<WT> out, Adj<WT> in, const int32_t
                                                                            c.pb_lo.p, c.pb_c.p);
     CKL("k_hub_final");
   } else if (kev) {
-    CK(cudaEventRecord(kev[6], c.s));
     CK(cudaEventRecord(kev[7], c.s));
+    CK(cudaEventRecord(kev[8], c.s));
   }
   if (kev) {
     // times and bytes are resolved when the statistics are read, so that
     // collecting them adds no host synchronisation to the sweep
-    CK(cudaEventRecord(kev[8], c.s));
+    CK(cudaEventRecord(kev[9], c.s));
     c.ks_launch[0] += ct > 0;
     c.ks_launch[1] += cs > 0;
     c.ks_launch[2] += cm > 0;
@@ -1113,31 +1121,38 @@ static int32_t sweep_t(ldl_ctx& c, int r, Adj<WT> out, Adj<WT> in, const int32_t
     c.ks_launch[5] += ch > 0;
     c.ks_launch[6] += ch > 0 ? 3 : 0;
   }
-  return rd_cnt(c, K_CAND);
 }
 
-int32_t sweep(ldl_ctx& c, int r, int mode, const int32_t* list, int idx_n, int64_t n_hint) {
-  if (r == 0)
-    return mode == 0 ? sweep_t<int32_t, 0>(c, r, adj_out0(c), adj_in0(c), list, idx_n, n_hint)
-                     : sweep_t<int32_t, 1>(c, r, adj_out0(c), adj_in0(c), list, idx_n, n_hint);
-  return mode == 0 ? sweep_t<int64_t, 0>(c, r, adj_out(c, r), adj_in(c, r), list, idx_n, n_hint)
-                   : sweep_t<int64_t, 1>(c, r, adj_out(c, r), adj_in(c, r), list, idx_n, n_hint);
+void sweep(ldl_ctx& c, int r, int mode, const int32_t* list, int idx_n, int64_t n_hint) {
+  if (r == 0) {
+    if (mode == 0) sweep_t<int32_t, 0>(c, r, adj_out0(c), adj_in0(c), list, idx_n, n_hint);
+    else sweep_t<int32_t, 1>(c, r, adj_out0(c), adj_in0(c), list, idx_n, n_hint);
+  } else {
+    if (mode == 0) sweep_t<int64_t, 0>(c, r, adj_out(c, r), adj_in(c, r), list, idx_n, n_hint);
+    else sweep_t<int64_t, 1>(c, r, adj_out(c, r), adj_in(c, r), list, idx_n, n_hint);
+  }
 }
 
-int32_t decouple(ldl_ctx& c, int32_t nc) {
-  if (nc <= 0) return 0;
-  if (nc <= DEC_SMALL) {
-    zero_cnt(c, K_B);
-    k_dec_block<<<1, DEC_THREADS, 0, c.s>>>(nc, c.cst.p, c.cv.p, c.csrc.p, c.cdst.p, c.cghi.p, c.cglo.p, c.role.p,
-                                            c.best.p, c.bv.p, c.bsrc.p, c.bdst.p, c.dcnt + K_B, c.dcnt + K_UNDEC);
-    CKL("k_dec_block");
-    int32_t out[2];  // K_B, K_UNDEC are adjacent
-    ++c.syncs;
-    CK(cudaMemcpyAsync(out, c.dcnt + K_B, sizeof(out), cudaMemcpyDeviceToHost, c.s));
-    CK(cudaStreamSynchronize(c.s));
-    if (out[1] < 0) ldl_throw(LDL_E_INVALID, "internal: decoupling did not converge");
-    c.res.decouple_rounds += out[1];
-    return out[0];
+DecoupleOut decouple(ldl_ctx& c) {
+  // The single-block filter runs first and reads the candidate count on the
+  // device; one read then returns the count, the accepted number and the
+  // filter's status (-2: too many candidates for one block).
+  static_assert(K_B == K_CAND + 1 && K_UNDEC == K_CAND + 2, "adjacent counters");
+  zero_cnt(c, K_B);
+  k_dec_block<<<1, DEC_THREADS, 0, c.s>>>(c.dcnt + K_CAND, c.cst.p, c.cv.p, c.csrc.p, c.cdst.p, c.cghi.p, c.cglo.p,
+                                          c.role.p, c.best.p, c.bv.p, c.bsrc.p, c.bdst.p, c.dcnt + K_B,
+                                          c.dcnt + K_UNDEC);
+  CKL("k_dec_block");
+  int32_t out[3];
+  ++c.syncs;
+  CK(cudaMemcpyAsync(out, c.dcnt + K_CAND, sizeof(out), cudaMemcpyDeviceToHost, c.s));
+  CK(cudaStreamSynchronize(c.s));
+  const int32_t nc = out[0];
+  if (nc <= 0) return {0, 0};
+  if (out[2] != -2) {
+    if (out[2] < 0) ldl_throw(LDL_E_INVALID, "internal: decoupling did not converge");
+    c.res.decouple_rounds += out[2];
+    return {nc, out[1]};
   }
   CK(cudaMemsetAsync(c.cst.p, 0, sizeof(int32_t) * (size_t)nc, c.s));
   const int g = grid_for(nc, TPB);
@@ -1163,7 +1178,7 @@ int32_t decouple(ldl_ctx& c, int32_t nc) {
   k_dec_finish<<<g, TPB, 0, c.s>>>(nc, c.cst.p, c.cv.p, c.csrc.p, c.cdst.p, c.role.p, c.bv.p, c.bsrc.p, c.bdst.p,
                                    c.dcnt + K_B);
   CKL("k_dec_finish");
-  return rd_cnt(c, K_B);
+  return {nc, rd_cnt(c, K_B)};
 }
 
 CommitOut commit_move(ldl_ctx& c, int r, int32_t nb, int32_t epB, int32_t epT, int32_t epCh) {
@@ -1199,13 +1214,14 @@ CommitOut commit_move(ldl_ctx& c, int r, int32_t nb, int32_t epB, int32_t epT, i
                                                                c.prm.gamma_num, c.prm.gamma_den, c.d_sc);
   CKL("k_commit_dq");
   DevScalars h;
-  CK(cudaMemcpyAsync(&h, c.d_sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, c.s));
-  CK(cudaStreamSynchronize(c.s));
   CommitOut o;
+  ++c.syncs;
+  CK(cudaMemcpyAsync(&h, c.d_sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, c.s));
+  CK(cudaMemcpyAsync(&o.ntc, c.dcnt + K_T, sizeof(int32_t), cudaMemcpyDeviceToHost, c.s));
+  CK(cudaStreamSynchronize(c.s));
   o.dq = i128_of(h.dq.hi, h.dq.lo);
   o.dp = i128_of(h.dp.hi, h.dp.lo);
   o.de = h.de;
-  o.ntc = rd_cnt(c, K_T);
   return o;
 }
 
