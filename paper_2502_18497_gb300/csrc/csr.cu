@@ -226,21 +226,16 @@ __global__ void k_set_len(int64_t nseg, int64_t nrec, const int64_t* seg_start, 
   }
 }
 
-// compaction: rows copied contiguously into a fresh pool (offsets = scan of caps)
+// compaction: every live entry is one item (rows located through the scan of
+// the row lengths), copied to its row's new offset (the scan of the caps)
 template <class WT>
-__global__ void k_compact_rows(int64_t n, const int64_t* off, const int32_t* len, const int64_t* noff,
-                               const int32_t* col, const WT* w, int32_t* ncol, WT* nw) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwp = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t v = warp; v < n; v += nwp) {
-    const int64_t o = off[v], d = noff[v];
-    const int32_t l = len[v];
-    for (int32_t k = lane; k < l; k += 32) {
-      ncol[d + k] = col[o + k];
-      nw[d + k] = w[o + k];
-    }
-  }
+__global__ void k_compact_rows(int64_t n, const int64_t* off, const int64_t* lpre, int64_t total,
+                               const int64_t* noff, const int32_t* col, const WT* w, int32_t* ncol, WT* nw) {
+  FOR_SEG_ITEMS(t, v, lpre, n, total)
+    const int64_t k = t - lpre[v];
+    ncol[noff[v] + k] = col[off[v] + k];
+    nw[noff[v] + k] = w[off[v] + k];
+  END_SEG_ITEMS
 }
 
 // ---------------------------------------------------------------- build
@@ -331,11 +326,17 @@ static void compact_pool(SlackCSR<WT>& g, int64_t extra, CsrScratch& S, Prims& P
   k_i32_to_i64<<<grid_for(n, TPB), TPB, 0, s>>>(g.cap.p, S.tmp64.p, n);
   CKL("k_i32_to_i64");
   const int64_t total = scan_exclusive(S.tmp64.p, S.rs.p, n, P, s, true);  // new offsets
-  const int64_t pool = total + extra + (total + extra) / 4 + 4096;
+  // the same headroom again: rows that outgrow their slack move to the pool's
+  // end, so a level whose rows churn refills it quickly
+  const int64_t pool = 2 * (total + extra) + 4096;
   int32_t* c2 = (int32_t*)dalloc(sizeof(int32_t) * (size_t)pool);
   WT* w2 = (WT*)dalloc(sizeof(WT) * (size_t)pool);
-  k_compact_rows<WT><<<grid_for(n * 32, TPB), TPB, 0, s>>>(n, g.off.p, g.len.p, S.rs.p, g.col.p, g.w.p, c2, w2);
-  CKL("k_compact_rows");
+  const int64_t live = scan_exclusive_i32(g.len.p, S.tmp64.p, n, P, s, true);
+  if (live > 0) {
+    k_compact_rows<WT><<<grid_for((live + 7) / 8, TPB), TPB, 0, s>>>(n, g.off.p, S.tmp64.p, live, S.rs.p, g.col.p,
+                                                                     g.w.p, c2, w2);
+    CKL("k_compact_rows");
+  }
   CK(cudaMemcpyAsync(g.off.p, S.rs.p, sizeof(int64_t) * (size_t)n, cudaMemcpyDeviceToDevice, s));
   CK(cudaStreamSynchronize(s));
   dfree(g.col.p);

@@ -63,9 +63,9 @@ extern "C" ldl_status ldl_estimate_bytes(const ldl_params* p, int64_t n, int64_t
   const int64_t per_node_global = 64 * 4 + 10 * 8;                 // stamps, lists, candidates, scratch
   const int64_t per_node_level = 3 * 4 + 2 * 8 + 1 + 2 * 4 + 3 * 8; // lab/par/cnt, k, alive, frontier, CSRs
   const int64_t dir = p->directed ? 2 : 1;
-  const int64_t adj0 = dir * nnz * 8 * 5 / 4;                       // level 0 with 25% slack
-  const int64_t upper = dir * nnz * 12;                              // aggregate levels (bounded by level 0)
-  const int64_t records = nnz * 16 * 4;                              // sort / reduce buffers
+  const int64_t adj0 = dir * nnz * 8 * 5 / 2;  // level 0: 25% slack, doubled by a pool compaction
+  const int64_t upper = dir * nnz * 12 * 2;     // aggregate levels (bounded by level 0), same headroom
+  const int64_t records = dir * nnz * 16 * 6;   // sort ping-pong, reduce and CSR update scratch
   *bytes = n * (per_node_global + levels * per_node_level) + adj0 + upper + records + (64 << 20);
   return LDL_OK;
 }

@@ -330,35 +330,55 @@ __global__ void k_emit(Adj<WT> out, Adj<WT> in, ChunkMap m, const int32_t* par, 
     const int32_t po = par_old[u], pn = par[u];
     const Adj<WT>& A = ch.row ? in : out;
     const int64_t o = A.off[u];
-    for (int32_t base = ch.k0; base < ch.k1; base += 32) {
-      const int32_t k = base + lane;
-      bool w1 = false, w2 = false;
-      u64 k1 = 0, v1 = 0, k2 = 0, v2 = 0;
-      if (k < ch.k1) {
+    // 64 entries per step, up to four records per lane, one counter atomic
+    // per warp and step
+    for (int32_t base = ch.k0; base < ch.k1; base += 64) {
+      u64 rkey[4] = {0, 0, 0, 0}, rval[4] = {0, 0, 0, 0};
+      bool ok[4] = {false, false, false, false};  // fixed slots: (first entry -, +), (second entry -, +)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int32_t k = base + h * 32 + lane;
+        if (k >= ch.k1) continue;
         const int32_t v = A.col[o + k];
         const int64_t w = (int64_t)A.w[o + k];
         const bool vc = stC[v] == epC;
         if (ch.row == 0) {  // arc (u, v) from u's out-row
           const int32_t pvo = vc ? par_old[v] : par[v];
           const int32_t pvn = par[v];
-          w1 = po >= 0 && pvo >= 0;
-          k1 = ((u64)po << bits) | (u64)pvo;
-          v1 = (u64)(-w);
-          w2 = true;
-          k2 = ((u64)pn << bits) | (u64)pvn;
-          v2 = (u64)w;
+          ok[2 * h] = po >= 0 && pvo >= 0;
+          rkey[2 * h] = ((u64)po << bits) | (u64)pvo;
+          rval[2 * h] = (u64)(-w);
+          ok[2 * h + 1] = true;
+          rkey[2 * h + 1] = ((u64)pn << bits) | (u64)pvn;
+          rval[2 * h + 1] = (u64)w;
         } else if (!vc) {  // arc (v, u) from u's in-row, v unchanged
           const int32_t pv = par[v];
-          w1 = po >= 0;
-          k1 = ((u64)pv << bits) | (u64)po;
-          v1 = (u64)(-w);
-          w2 = true;
-          k2 = ((u64)pv << bits) | (u64)pn;
-          v2 = (u64)w;
+          ok[2 * h] = po >= 0;
+          rkey[2 * h] = ((u64)pv << bits) | (u64)po;
+          rval[2 * h] = (u64)(-w);
+          ok[2 * h + 1] = true;
+          rkey[2 * h + 1] = ((u64)pv << bits) | (u64)pn;
+          rval[2 * h + 1] = (u64)w;
         }
       }
-      warp_append_rec(w1, k1, v1, rk, rv, cnt);
-      warp_append_rec(w2, k2, v2, rk, rv, cnt);
+      const int nrec = (int)ok[0] + (int)ok[1] + (int)ok[2] + (int)ok[3];
+      int incl = nrec;  // warp inclusive scan of the per-lane counts
+      for (int d = 1; d < 32; d <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += y;
+      }
+      const int wtot = __shfl_sync(0xffffffffu, incl, 31);
+      int32_t wbase = 0;
+      if (lane == 31 && wtot) wbase = atomicAdd(cnt, wtot);
+      wbase = __shfl_sync(0xffffffffu, wbase, 31);
+      int32_t p = wbase + incl - nrec;
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (ok[j]) {
+          rk[p] = rkey[j];
+          rv[p] = rval[j];
+          ++p;
+        }
     }
   }
 }

@@ -147,17 +147,26 @@ __global__ void k_rs_hist(const u64* keys, int64_t n, int shift, int64_t nb, int
   for (int x = threadIdx.x; x < 256; x += RS_THREADS) ghist[(int64_t)x * nb + blockIdx.x] = h[x];
 }
 
-// One block per digit: exclusive scan of the digit's tile counts in place,
-// and the digit's total.
+// One block per digit: exclusive scan of the digit's tile counts in place
+// (8 consecutive counts per thread per step), and the digit's total.
 __global__ void __launch_bounds__(SC_THREADS) k_rs_dscan(int64_t* ghist, int64_t nb, int64_t* dtot) {
+  constexpr int IT = 8;
   int64_t* row = ghist + (int64_t)blockIdx.x * nb;
   int64_t carry = 0;
-  for (int64_t b0 = 0; b0 < nb; b0 += SC_THREADS) {
-    const int64_t b = b0 + threadIdx.x;
-    const int64_t v = b < nb ? row[b] : 0;
+  for (int64_t b0 = 0; b0 < nb; b0 += SC_THREADS * IT) {
+    const int64_t base = b0 + (int64_t)threadIdx.x * IT;
+    int64_t v[IT];
+    int64_t sum = 0;
+    for (int k = 0; k < IT; ++k) {
+      v[k] = base + k < nb ? row[base + k] : 0;
+      sum += v[k];
+    }
     int64_t total;
-    const int64_t ex = block_excl_scan_i64(v, &total);
-    if (b < nb) row[b] = carry + ex;
+    int64_t ex = carry + block_excl_scan_i64(sum, &total);
+    for (int k = 0; k < IT; ++k) {
+      if (base + k < nb) row[base + k] = ex;
+      ex += v[k];
+    }
     carry += total;
   }
   if (threadIdx.x == 0) dtot[blockIdx.x] = carry;
