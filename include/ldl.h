@@ -278,6 +278,13 @@ ldl_status ldl_get_kernel_stats(const ldl_ctx* ctx, double* out);
  * k = 0 disables.  Lets a test check that NOMEM leaves the state intact. */
 void ldl_debug_fail_alloc_after(int64_t k);
 
+/* Test hook for the bounded waits: runs a two-tile device scan in which the
+ * first tile never publishes its sum, so the second tile's look-back wait
+ * runs out (after about 2^20 polls).  Returns LDL_E_TIMEOUT when the wait gave
+ * up and reported it (the expected outcome), LDL_OK if it did not, or
+ * LDL_E_NOMEM / LDL_E_CUDA.  Touches no context. */
+ldl_status ldl_debug_scan_wait_timeout(void);
+
 #ifdef __cplusplus
 }
 #endif

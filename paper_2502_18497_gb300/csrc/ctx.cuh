@@ -73,8 +73,11 @@ struct ldl_ctx {
   // sweep binning
   DBuf<int32_t> binT, binS, binM, binM2, binC, binL;
   DBuf<int64_t> binLoff, binLsz;
-  DBuf<int32_t> gkeys;
+  DBuf<int32_t> gkeys;   // hub hash tables (kept clean: all -1 / 0 between sweeps)
   DBuf<int64_t> gvals;
+  int64_t gtab_clean = 0;  // capacity of gkeys / gvals known to be clean
+  DBuf<int32_t> glist;   // per hub: the table slots its sweep occupied
+  DBuf<int32_t> hcnt;    // per hub: number of occupied slots
   // records
   DBuf<u64> rk, rv, tk, tv, rk2, rv2;
   DBuf<int64_t> rsum, rsum2;

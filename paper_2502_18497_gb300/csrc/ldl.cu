@@ -138,13 +138,15 @@ static void free_all(ldl_ctx& c) {
                           &c.stE, &c.stCh, &c.lU, &c.lS, &c.lUstar, &c.lMv, &c.lM0, &c.lD, &c.lC, &c.lR,
                           &c.lR2, &c.lX, &c.lT, &c.lE, &c.lE2, &c.lCh, &c.lChg, &c.lTmp, &c.cv, &c.csrc,
                           &c.cdst, &c.cst, &c.bv, &c.bsrc, &c.bdst, &c.best, &c.role, &c.oldlab, &c.par_old,
-                          &c.lab_before, &c.binT, &c.binS, &c.binM, &c.binM2, &c.binC, &c.binL, &c.gkeys, &c.ndx, &c.ndx2};
+                          &c.lab_before, &c.binT, &c.binS, &c.binM, &c.binM2, &c.binC, &c.binL, &c.gkeys, &c.ndx, &c.ndx2,
+                          &c.glist, &c.hcnt};
   for (auto* b : b32) b->release();
   DBuf<u64>* bu[] = {&c.rk, &c.rv, &c.tk, &c.tv, &c.rk2, &c.rv2, &c.crk, &c.crv, &c.fk, &c.trk, &c.trv};
   for (auto* b : bu) b->release();
   c.cglo.release();
   c.pb_lo.release();
   c.pb_c.release();
+  c.gtab_clean = 0;
   c.upd.release();
   c.P.release();
   c.CS.release();
@@ -626,6 +628,14 @@ ldl_status ldl_set_timing(ldl_ctx* c, int32_t on) {
 }
 
 void ldl_debug_fail_alloc_after(int64_t k) { g_fail_after.store(k > 0 ? k : 0); }
+
+ldl_status ldl_debug_scan_wait_timeout(void) {
+  try {
+    return scan_wait_gives_up(nullptr) ? LDL_E_TIMEOUT : LDL_OK;
+  } catch (const LdlError& e) {
+    return e.st;
+  }
+}
 
 int64_t ldl_launch_count(void) { return g_launches.load(); }
 

@@ -451,6 +451,37 @@ void scan_exclusive_i32_to(const int32_t* in, int64_t* out, int64_t n, const int
 
 int32_t* scan_error_flag(Prims& P) { return P.lb_ctl.cap ? P.lb_ctl.p + 256 : nullptr; }
 
+bool scan_wait_gives_up(cudaStream_t s) {
+  // Two tiles; the tile counter starts at 1 and one block runs, so tile 1
+  // waits on tile 0, which nothing publishes: the bounded wait must give up.
+  Prims P;
+  const int64_t n = 2 * LB_TILE;
+  int32_t bad = 0;
+  int64_t *in = nullptr, *out = nullptr;
+  try {
+    in = (int64_t*)dalloc(sizeof(int64_t) * (size_t)n);
+    out = (int64_t*)dalloc(sizeof(int64_t) * (size_t)(n + 1));
+    CK(cudaMemsetAsync(in, 0, sizeof(int64_t) * (size_t)n, s));
+    const uint32_t ep = lb_begin(P, n, s);
+    const int32_t one = 1;
+    CK(cudaMemcpyAsync(P.lb_ctl.p + ep, &one, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    k_scan_lb<int64_t><<<1, SC_THREADS, 0, s>>>(in, out, n, nullptr, P.lb_st.p, P.lb_ctl.p + ep, ep, out + n,
+                                                P.lb_ctl.p + 256);
+    CKL("k_scan_lb");
+    CK(cudaMemcpyAsync(&bad, P.lb_ctl.p + 256, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+  } catch (...) {
+    if (in) dfree(in);
+    if (out) dfree(out);
+    P.release();
+    throw;
+  }
+  dfree(in);
+  dfree(out);
+  P.release();
+  return bad != 0;
+}
+
 void radix_sort_pairs(u64*& keys, u64*& vals, u64*& tk, u64*& tv, int64_t n, int bits, Prims& P, cudaStream_t s,
                       int lo_bit) {
   if (n <= 1 || bits <= lo_bit) return;

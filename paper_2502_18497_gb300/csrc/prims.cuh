@@ -28,6 +28,9 @@ void scan_exclusive_i32_to(const int32_t* in, int64_t* out, int64_t n, const int
 // Device flag set when a scan's bounded look-back wait gave up (nullptr
 // before the first multi-tile scan).
 int32_t* scan_error_flag(Prims& P);
+// Runs a scan whose first tile is never published; true when the waiting tile
+// gave up and raised the error flag (a check of the bounded wait).
+bool scan_wait_gives_up(cudaStream_t s);
 
 // Stable LSD radix sort of n (key, value) pairs on the low `bits` key bits,
 // 8 bits per pass.  The sorted data ends in (keys, vals); the pointers are

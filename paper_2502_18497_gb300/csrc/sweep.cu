@@ -17,7 +17,7 @@ constexpr int HW = 256;      // per-warp hash slots (small bin)
 constexpr int TINY_DEG = 24;   // groups of 8 lanes, 64 slots
 constexpr int SMALL_DEG = 96;  // one warp, 256 slots
 constexpr int HB = 4096;     // per-block hash slots (upper mid bin)
-constexpr int MID1_DEG = 384;  // lower mid bin: 128 threads, 1024 slots
+constexpr int MID1_DEG = 1024;  // lower mid bin: 128 threads, 2048 slots
 constexpr int MID_DEG = 2048;
 constexpr int CL = 8;             // blocks per cluster (hub rows up to CLUSTER_DEG entries)
 constexpr int CL_SLOTS = 8192;    // hash slots per block of a cluster (96 KB of shared memory)
@@ -117,14 +117,29 @@ __device__ inline int64_t hash_get(const int32_t* K, const int64_t* V, uint32_t 
 template <class WT, int MODE>
 __device__ inline void accumulate(const SweepArgs<WT>& A, const Adj<WT>& adj, int32_t v, int32_t cv_, int32_t* K,
                                   int64_t* V, uint32_t mask, int tid, int nthreads) {
+  // ACC entries per thread per step: their loads and label gathers are all in
+  // flight before the first insert
+  constexpr int ACC = 4;
   const int64_t o = adj.off[v];
   const int32_t l = adj.len[v];
-  for (int32_t k = tid; k < l; k += nthreads) {
-    const int32_t u = adj.col[o + k];
-    if (u == v) continue;
-    if (MODE == 1 && A.lab[u] != cv_) continue;
-    const int32_t key = MODE == 0 ? A.lab[u] : A.par[u];
-    hash_add(K, V, mask, key, (int64_t)adj.w[o + k]);
+  for (int32_t k0 = tid; k0 < l; k0 += ACC * nthreads) {
+    int32_t u[ACC];
+    int64_t w[ACC];
+#pragma unroll
+    for (int j = 0; j < ACC; ++j) {
+      const int32_t k = k0 + j * nthreads;
+      u[j] = k < l ? adj.col[o + k] : -1;
+      w[j] = k < l ? (int64_t)adj.w[o + k] : 0;
+    }
+    int32_t key[ACC];
+#pragma unroll
+    for (int j = 0; j < ACC; ++j) {
+      key[j] = -1;
+      if (u[j] >= 0 && u[j] != v && (MODE == 0 || A.lab[u[j]] == cv_)) key[j] = MODE == 0 ? A.lab[u[j]] : A.par[u[j]];
+    }
+#pragma unroll
+    for (int j = 0; j < ACC; ++j)
+      if (key[j] >= 0) hash_add(K, V, mask, key[j], w[j]);
   }
 }
 
@@ -154,6 +169,53 @@ __device__ inline int64_t sweep_bytes(bool directed, int64_t entries, int64_t no
   const int64_t per_node = (8 + 4) * (directed ? 2 : 1) + 4 + 16 + 4;
   const int64_t per_pair = directed ? 16 : 8;
   return per_entry * entries + per_node * nodes + per_pair * pairs;
+}
+
+// Evaluates the slots start, start + step, ... < H of a node's table: the
+// exact gain (as gain_of) into every target but `self`, the best kept in b.
+// EV slots per step have their totals gathered before any gain is computed.
+template <int MODE>
+__device__ inline void eval_slots(const int32_t* K, const int64_t* V, uint32_t H, uint32_t start, uint32_t step,
+                                  int32_t self, int32_t a, int64_t wa, int64_t ko, int64_t ki, const int64_t* Tout,
+                                  const int64_t* Tin, int64_t m, int64_t gn, int64_t gd, int64_t mult, Best& b,
+                                  int64_t& pairs) {
+  constexpr int EV = 1;
+  const int64_t tia = MODE == 0 ? Tin[a] : 0, toa = MODE == 0 ? Tout[a] : 0;
+  for (uint32_t k0 = start; k0 < H; k0 += EV * step) {
+    int32_t key[EV];
+    int64_t acc[EV], ti[EV], to[EV];
+#pragma unroll
+    for (int j = 0; j < EV; ++j) {
+      const uint32_t k = k0 + j * step;
+      key[j] = k < H ? K[k] : -1;
+      if (key[j] == self) key[j] = -1;
+      acc[j] = key[j] >= 0 ? V[k] : 0;
+    }
+#pragma unroll
+    for (int j = 0; j < EV; ++j) {
+      ti[j] = key[j] >= 0 ? Tin[key[j]] : 0;
+      to[j] = key[j] >= 0 ? Tout[key[j]] : 0;
+    }
+#pragma unroll
+    for (int j = 0; j < EV; ++j) {
+      if (key[j] < 0) continue;
+      ++pairs;
+      i128 g;
+      if (MODE == 0) {
+        const i128 dw = (i128)mult * (acc[j] - wa);
+        const i128 dd = (i128)ko * (ti[j] - tia + ki) + (i128)ki * (to[j] - toa + ko);
+        g = (i128)gd * m * dw - (i128)gn * dd;
+      } else {
+        const i128 dw = (i128)mult * acc[j];
+        const i128 dd = (i128)ko * ti[j] + (i128)ki * to[j];
+        g = (i128)gd * m * dw - (i128)gn * dd;
+      }
+      if (g > 0) {
+        Best c{g, key[j], 1};
+        if (best_better(c, b)) b = c;
+      }
+    }
+  }
 }
 
 template <class WT>
@@ -211,17 +273,8 @@ __global__ void __launch_bounds__(TPB, 5) k_sweep_group(SweepArgs<WT> A, const i
     if (act) {
       const int64_t wa = MODE == 0 ? hash_get(K, V, H - 1, a) : 0;
       const int64_t ko = A.kout[v], ki = A.kin[v];
-      for (int k = gl; k < H; k += G) {
-        const int32_t key = K[k];
-        if (key < 0) continue;
-        if (MODE == 0 ? key == a : key == v) continue;
-        ++pairs;
-        const i128 g = gain_of<MODE>(key, V[k], wa, a, ko, ki, A.Tout, A.Tin, A.m, A.gn, A.gd, mult);
-        if (g > 0) {
-          Best c{g, key, 1};
-          if (best_better(c, b)) b = c;
-        }
-      }
+      eval_slots<MODE>(K, V, (uint32_t)H, (uint32_t)gl, (uint32_t)G, MODE == 0 ? a : v, a, wa, ko, ki, A.Tout, A.Tin,
+                       A.m, A.gn, A.gd, mult, b, pairs);
     }
     b = group_best<G>(b);
     if (act && gl == 0 && b.have) emit_cand(A, v, MODE == 0 ? a : v, b);
@@ -266,17 +319,8 @@ __global__ void __launch_bounds__(NT) k_sweep_block(SweepArgs<WT> A, const int32
     const int64_t ko = A.kout[v], ki = A.kin[v];
     Best b{0, 0, 0};
     int64_t pairs = 0;
-    for (uint32_t k = threadIdx.x; k < H; k += NT) {
-      const int32_t key = K[k];
-      if (key < 0) continue;
-      if (MODE == 0 ? key == a : key == v) continue;
-      ++pairs;
-      const i128 g = gain_of<MODE>(key, V[k], wa, a, ko, ki, A.Tout, A.Tin, A.m, A.gn, A.gd, mult);
-      if (g > 0) {
-        Best c{g, key, 1};
-        if (best_better(c, b)) b = c;
-      }
-    }
+    eval_slots<MODE>(K, V, H, threadIdx.x, NT, MODE == 0 ? a : v, a, wa, ko, ki, A.Tout, A.Tin, A.m, A.gn, A.gd,
+                     mult, b, pairs);
     b = warp_best(b);
     if (lane == 0) wb[wid] = b;
     pairs_all += pairs;
@@ -465,9 +509,12 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(TPB)
 }
 
 // ---------------------------------------------------------------- hubs
-// Hub rows are spread over the whole GPU: one global hash table per hub,
-// filled by chunks of its rows, then evaluated in slot chunks whose partial
-// bests are reduced per hub.
+// Hub rows are spread over the whole GPU: one global hash table per hub
+// (a power of two >= 2 * degree), filled by chunks of its rows.  A probe that
+// claims an empty slot appends it to the hub's slot list (at most degree
+// entries, so hub i's list fits at loff[i] / 2), and only the listed slots are
+// evaluated, in chunks whose partial bests are reduced per hub, and then
+// cleared, so the tables stay clean between sweeps without a full re-fill.
 __global__ void k_hub_init(int32_t* K, int64_t* V, int64_t total) {
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
     K[t] = -1;
@@ -475,14 +522,34 @@ __global__ void k_hub_init(int32_t* K, int64_t* V, int64_t total) {
   }
 }
 
-__global__ void k_eval_counts(const int64_t* lsz, int32_t nh, int64_t* ecnt) {
+__global__ void k_eval_counts(const int32_t* hcnt, int32_t nh, int64_t* ecnt) {
   for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i <= nh; i += gridDim.x * blockDim.x)
-    ecnt[i] = i < nh ? (lsz[i] + EVAL_CH - 1) / EVAL_CH : 0;
+    ecnt[i] = i < nh ? (hcnt[i] + EVAL_CH - 1) / EVAL_CH : 0;
+}
+
+// listed slots back to empty (after the evaluation)
+__global__ void k_hub_clear(int32_t nh, const int64_t* loff, const int64_t* epre, const int32_t* hcnt,
+                            const int32_t* glist, int32_t* gK, int64_t* gV) {
+  const int64_t total = epre[nh];
+  for (int64_t e = blockIdx.x; e < total; e += gridDim.x) {
+    int64_t lo = 0, hi = nh;
+    while (hi - lo > 1) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (epre[mid] <= e) lo = mid; else hi = mid;
+    }
+    const int64_t s0 = (e - epre[lo]) * EVAL_CH, s1 = min((int64_t)hcnt[lo], s0 + EVAL_CH);
+    const int32_t* L = glist + loff[lo] / 2;
+    for (int64_t j = s0 + threadIdx.x; j < s1; j += blockDim.x) {
+      const int64_t slot = loff[lo] + L[j];
+      gK[slot] = -1;
+      gV[slot] = 0;
+    }
+  }
 }
 
 template <class WT, int MODE>
 __global__ void k_hub_acc(SweepArgs<WT> A, ChunkMap m, const int64_t* loff, const int64_t* lsz, int32_t* gK,
-                          int64_t* gV) {
+                          int64_t* gV, int32_t* glist, int32_t* hcnt) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -517,7 +584,11 @@ __global__ void k_hub_acc(SweepArgs<WT> A, ChunkMap m, const int64_t* loff, cons
         h = hash32((uint32_t)key) & mask;
         while (true) {
           const int32_t prev = atomicCAS(&K[h], -1, key);
-          if (prev == -1 || prev == key) break;
+          if (prev == -1) {  // a new key: list its slot
+            glist[loff[ch.idx] / 2 + atomicAdd(&hcnt[ch.idx], 1)] = (int32_t)h;
+            break;
+          }
+          if (prev == key) break;
           h = (h + 1) & mask;
         }
       }
@@ -536,8 +607,9 @@ __global__ void k_hub_acc(SweepArgs<WT> A, ChunkMap m, const int64_t* loff, cons
 template <class WT, int MODE>
 __global__ void __launch_bounds__(TPB) k_hub_eval(SweepArgs<WT> A, const int32_t* hubs, int32_t nh,
                                                   const int64_t* loff, const int64_t* lsz, const int64_t* epre,
-                                                  const int32_t* gK, const int64_t* gV, int64_t* pb_hi,
-                                                  uint64_t* pb_lo, int32_t* pb_c) {
+                                                  const int32_t* gK, const int64_t* gV, const int32_t* glist,
+                                                  const int32_t* hcnt, int64_t* pb_hi, uint64_t* pb_lo,
+                                                  int32_t* pb_c) {
   __shared__ Best wb[TPB / 32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int64_t mult = A.directed ? 1 : 2;
@@ -554,18 +626,19 @@ __global__ void __launch_bounds__(TPB) k_hub_eval(SweepArgs<WT> A, const int32_t
     const int64_t* V = gV + loff[i];
     const uint32_t H = (uint32_t)lsz[i];
     const int64_t s0 = (e - epre[i]) * EVAL_CH;
-    const int64_t s1 = min((int64_t)H, s0 + EVAL_CH);
+    const int64_t s1 = min((int64_t)hcnt[i], s0 + EVAL_CH);
+    const int32_t* Lst = glist + loff[i] / 2;
     const int32_t a = A.lab[v];
     const int64_t wa = MODE == 0 ? hash_get(K, V, H - 1, a) : 0;
     const int64_t ko = A.kout[v], ki = A.kin[v];
     Best b{0, 0, 0};
     int64_t pairs = 0;
-    for (int64_t k = s0 + threadIdx.x; k < s1; k += TPB) {
-      const int32_t key = K[k];
-      if (key < 0) continue;
+    for (int64_t j = s0 + threadIdx.x; j < s1; j += TPB) {
+      const int32_t slot = Lst[j];
+      const int32_t key = K[slot];
       if (MODE == 0 ? key == a : key == v) continue;
       ++pairs;
-      const i128 g = gain_of<MODE>(key, V[k], wa, a, ko, ki, A.Tout, A.Tin, A.m, A.gn, A.gd, mult);
+      const i128 g = gain_of<MODE>(key, V[slot], wa, a, ko, ki, A.Tout, A.Tin, A.m, A.gn, A.gd, mult);
       if (g > 0) {
         Best c{g, key, 1};
         if (best_better(c, b)) b = c;
@@ -1043,8 +1116,8 @@ static void sweep_t(ldl_ctx& c, int r, Adj<WT> out, Adj<WT> in, const int32_t* l
   CKL("k_sweep_group<32>");
   if (kev) CK(cudaEventRecord(kev[2], c.s));
   {
-    const size_t sm = (sizeof(int64_t) + sizeof(int32_t)) * 1024;
-    k_sweep_block<WT, MODE, 128, 1024><<<grid_for(n_hint, 1, 152 * 16), 128, sm, c.s>>>(A, c.binM.p,
+    const size_t sm = (sizeof(int64_t) + sizeof(int32_t)) * 2048;
+    k_sweep_block<WT, MODE, 128, 2048><<<grid_for(n_hint, 1, 152 * 16), 128, sm, c.s>>>(A, c.binM.p,
                                                                                      c.dcnt + K_MID);
     CKL("k_sweep_block(mid1)");
   }
@@ -1078,33 +1151,42 @@ static void sweep_t(ldl_ctx& c, int r, Adj<WT> out, Adj<WT> in, const int32_t* l
     const int32_t nh = ch;
     c.gkeys.reserve(tab, c.s);
     c.gvals.reserve(tab, c.s);
-    // table offsets and evaluation chunks per hub, in list order
+    if (c.gtab_clean != c.gkeys.cap || c.gvals.cap != c.gkeys.cap) {  // fresh tables: fill once
+      k_hub_init<<<grid_for(c.gkeys.cap, TPB), TPB, 0, c.s>>>(c.gkeys.p, c.gvals.p, c.gkeys.cap);
+      CKL("k_hub_init");
+      c.gtab_clean = c.gkeys.cap;
+    }
+    c.glist.reserve(tab / 2 + 1, c.s);
+    c.hcnt.reserve(nh + 1, c.s);
+    CK(cudaMemsetAsync(c.hcnt.p, 0, sizeof(int32_t) * (size_t)(nh + 1), c.s));
+    // table offsets per hub, in list order
     CK(cudaMemsetAsync(c.binLsz.p + nh, 0, sizeof(int64_t), c.s));
     scan_exclusive(c.binLsz.p, c.binLoff.p, nh + 1, c.P, c.s, false);
     c.hub_ecnt.reserve(nh + 2, c.s);
     c.hub_epre.reserve(nh + 2, c.s);
-    k_eval_counts<<<grid_for(nh + 1, TPB), TPB, 0, c.s>>>(c.binLsz.p, nh, c.hub_ecnt.p);
-    CKL("k_eval_counts");
-    scan_exclusive(c.hub_ecnt.p, c.hub_epre.p, nh + 1, c.P, c.s, false);
-    const int64_t ech = tab / EVAL_CH + nh + 1;
+    const int64_t ech = tab / 2 / EVAL_CH + nh + 1;  // bounds the evaluation chunks
     c.pb_hi.reserve(ech, c.s);
     c.pb_lo.reserve(ech, c.s);
     c.pb_c.reserve(ech, c.s);
-    k_hub_init<<<grid_for(tab, TPB), TPB, 0, c.s>>>(c.gkeys.p, c.gvals.p, tab);
-    CKL("k_hub_init");
     ChunkMap m = chunk_map(c, c.binL.p, c.dcnt + K_LARGE, nh, out.len, c.directed ? in.len : nullptr);
     if (kev) CK(cudaEventRecord(kev[7], c.s));
-    k_hub_acc<WT, MODE><<<grid_for((int64_t)nh * 2048, TPB, 152 * 16), TPB, 0, c.s>>>(A, m, c.binLoff.p, c.binLsz.p,
-                                                                                      c.gkeys.p, c.gvals.p);
+    k_hub_acc<WT, MODE><<<grid_for((int64_t)nh * 2048, TPB, 152 * 16), TPB, 0, c.s>>>(
+        A, m, c.binLoff.p, c.binLsz.p, c.gkeys.p, c.gvals.p, c.glist.p, c.hcnt.p);
     CKL("k_hub_acc");
     if (kev) CK(cudaEventRecord(kev[8], c.s));
-    k_hub_eval<WT, MODE><<<grid_for(ech, 1, 152 * 8), TPB, 0, c.s>>>(A, c.binL.p, nh, c.binLoff.p, c.binLsz.p,
-                                                                    c.hub_epre.p, c.gkeys.p, c.gvals.p, c.pb_hi.p,
-                                                                    c.pb_lo.p, c.pb_c.p);
+    // evaluation chunks per hub from its occupied-slot count (device only)
+    k_eval_counts<<<grid_for(nh + 1, TPB), TPB, 0, c.s>>>(c.hcnt.p, nh, c.hub_ecnt.p);
+    CKL("k_eval_counts");
+    scan_exclusive(c.hub_ecnt.p, c.hub_epre.p, nh + 1, c.P, c.s, false);
+    const int ge = grid_for(ech, 1, 152 * 8);
+    k_hub_eval<WT, MODE><<<ge, TPB, 0, c.s>>>(A, c.binL.p, nh, c.binLoff.p, c.binLsz.p, c.hub_epre.p, c.gkeys.p,
+                                              c.gvals.p, c.glist.p, c.hcnt.p, c.pb_hi.p, c.pb_lo.p, c.pb_c.p);
     CKL("k_hub_eval");
     k_hub_final<WT, MODE><<<grid_for((int64_t)nh * 32, TPB), TPB, 0, c.s>>>(A, c.binL.p, nh, c.hub_epre.p, c.pb_hi.p,
                                                                            c.pb_lo.p, c.pb_c.p);
     CKL("k_hub_final");
+    k_hub_clear<<<ge, TPB, 0, c.s>>>(nh, c.binLoff.p, c.hub_epre.p, c.hcnt.p, c.glist.p, c.gkeys.p, c.gvals.p);
+    CKL("k_hub_clear");
   } else if (kev) {
     CK(cudaEventRecord(kev[7], c.s));
     CK(cudaEventRecord(kev[8], c.s));
@@ -1119,7 +1201,7 @@ static void sweep_t(ldl_ctx& c, int r, Adj<WT> out, Adj<WT> in, const int32_t* l
     c.ks_launch[3] += cm2 > 0;
     c.ks_launch[4] += cc > 0;
     c.ks_launch[5] += ch > 0;
-    c.ks_launch[6] += ch > 0 ? 3 : 0;
+    c.ks_launch[6] += ch > 0 ? 3 : 0;  // evaluation, final reduction, clearing
   }
 }
 

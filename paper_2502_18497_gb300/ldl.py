@@ -77,6 +77,7 @@ def load(path: Optional[str] = None):
         "ldl_stage_times": (I32, [P, P]),
         "ldl_set_timing": (I32, [P, I32]),
         "ldl_debug_fail_alloc_after": (None, [I64]),
+        "ldl_debug_scan_wait_timeout": (I32, []),
         "ldl_copy_changed": (I32, [P, P, P]),
         "ldl_copy_changed_noalloc": (I32, [P, P, P]),
         "ldl_launch_count": (I64, []),
@@ -103,7 +104,7 @@ def exported_symbols():
     return ["ldl_default_params", "ldl_create", "ldl_apply_batch", "ldl_modularity",
             "ldl_modularity_num", "ldl_destroy", "ldl_last_error", "ldl_levels", "ldl_get_level",
             "ldl_level_nnz", "ldl_get_adjacency", "ldl_get_communities", "ldl_stage_times",
-            "ldl_set_timing", "ldl_debug_fail_alloc_after", "ldl_copy_changed", "ldl_copy_changed_noalloc", "ldl_launch_count",
+            "ldl_set_timing", "ldl_debug_fail_alloc_after", "ldl_debug_scan_wait_timeout", "ldl_copy_changed", "ldl_copy_changed_noalloc", "ldl_launch_count",
             "ldl_set_kernel_stats", "ldl_get_kernel_stats", "ldl_apply_batches", "ldl_estimate_bytes",
             "ldl_server_create", "ldl_server_admit", "ldl_server_submit", "ldl_server_wait",
             "ldl_server_destroy"]

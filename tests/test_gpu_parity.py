@@ -163,3 +163,13 @@ def test_injected_allocation_failure_at_create(ldl):
     ldl.load().ldl_debug_fail_alloc_after(0)
     o, d = _pair(ldl, g)
     _assert_same(o, d, "after injected failures")
+
+
+def test_bounded_scan_wait_reports_timeout(ldl):
+    """A device scan whose first tile never publishes: the waiting tile gives
+    up after its bounded number of polls and the library reports TIMEOUT
+    (no hang, and the context-free check leaves the device usable)."""
+    assert ldl.load().ldl_debug_scan_wait_timeout() == ldl.LDL_E_TIMEOUT
+    g = planted_partition(n=1000, block=50, seed=8)
+    o, d = _pair(ldl, g)
+    _assert_same(o, d, "create after the timeout check")
