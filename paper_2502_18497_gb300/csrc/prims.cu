@@ -87,30 +87,45 @@ __global__ void __launch_bounds__(SC_THREADS) k_scan_lb(const T* in, int64_t* ou
   }
   int64_t agg;
   const int64_t pre = block_excl_scan_i64(sum, &agg);
-  if (threadIdx.x == 0) {
+  if (threadIdx.x < 32) {
+    // warp 0 looks back over 32 predecessors at a time: it sums aggregates
+    // until the nearest inclusive prefix, waiting only for tiles before it
+    const int lane = threadIdx.x;
     const u64 tag = (u64)(ep & 255u) << 2;
     int64_t acc = 0;
     if (tile > 0) {
-      atomicExch((unsigned long long*)&st[tile], ((u64)agg << 10) | tag | 1u);
+      if (lane == 0) atomicExch((unsigned long long*)&st[tile], ((u64)agg << 10) | tag | 1u);
       uint32_t spins = 0;
-      for (int64_t j = tile - 1; j >= 0;) {
-        const u64 x = *(volatile const u64*)&st[j];
-        if (((x >> 2) & 255u) != (ep & 255u) || (x & 3u) == 0) {
-          if (++spins > LB_SPINS) {
-            atomicExch(err, 1);
-            break;
-          }
-          __nanosleep(32);
+      for (int64_t j0 = tile - 1;;) {
+        const int64_t j = j0 - lane;
+        u64 x = 0;
+        if (j >= 0) x = *(volatile const u64*)&st[j];
+        const bool ready = j < 0 || (((x >> 2) & 255u) == (ep & 255u) && (x & 3u) != 0);
+        const unsigned rmask = __ballot_sync(0xffffffffu, ready);
+        const unsigned pmask = __ballot_sync(0xffffffffu, j >= 0 && ready && (x & 3u) == 2u);
+        const int nr = rmask == 0xffffffffu ? 32 : __ffs(~rmask) - 1;  // nearest tile not ready
+        const int fp = pmask ? __ffs(pmask) - 1 : 32;                  // nearest inclusive prefix
+        if (fp < nr || nr == 32) {
+          const int upto = fp < 32 ? fp : 31;
+          const int64_t v = (j >= 0 && lane <= upto) ? (int64_t)(x >> 10) : 0;
+          acc += warp_sum_i64(v);
+          acc = __shfl_sync(0xffffffffu, acc, 0);
+          if (fp < 32) break;
+          j0 -= 32;
           continue;
         }
-        acc += (int64_t)(x >> 10);
-        if ((x & 3u) == 2u) break;
-        --j;
+        if (++spins > LB_SPINS) {
+          if (lane == 0) atomicExch(err, 1);
+          break;
+        }
+        __nanosleep(32);
       }
     }
-    atomicExch((unsigned long long*)&st[tile], ((u64)(acc + agg) << 10) | tag | 2u);
-    s_pre = acc;
-    if ((tile + 1) * LB_TILE >= n && total) *total = acc + agg;
+    if (lane == 0) {
+      atomicExch((unsigned long long*)&st[tile], ((u64)(acc + agg) << 10) | tag | 2u);
+      s_pre = acc;
+      if ((tile + 1) * LB_TILE >= n && total) *total = acc + agg;
+    }
   }
   __syncthreads();
   int64_t p = s_pre + pre;
