@@ -385,7 +385,7 @@ struct Orc {
   }
 
   // ---------------------------------------------------------------- Move loop
-  // Algorithm 1 lines 6-15.  Returns the union of the frontiers U (U*) and
+  // The local-move loop of Algorithm 1.  Returns the union of the frontiers U (U*) and
   // appends the moved nodes to `moved`.
   std::vector<int32_t> move_loop(int r, std::vector<int32_t> U, int rounds,
                                  std::vector<int32_t>& moved) {
@@ -519,7 +519,7 @@ struct Orc {
     return lv[r].par[v] == v && lv[r + 1].cnt[v] == 1;
   }
 
-  // Refinement rounds (Algorithm 1 lines 16-22).  Returns the number of
+  // Refinement rounds (the refinement loop of Algorithm 1).  Returns the number of
   // merges committed.
   i64 refine_loop(int r, const std::vector<int32_t>& D, int rounds) {
     Level& Lr = lv[r];
@@ -819,7 +819,7 @@ struct Orc {
     i64 mnew = m;
     for (auto& d : deltas) mnew += (directed || d.first.first == d.first.second) ? d.second : 2 * d.second;
     if (mnew >= ((i64)1 << 50)) return ST_OVERFLOW;
-    // Algorithm 1 line 1: apply the batch to level 0, S_t = changed endpoints
+    // Algorithm 1: apply the batch to level 0, S_t = changed endpoints
     std::vector<ERec> arcs;
     for (auto& d : deltas) {
       arcs.push_back(d);
@@ -834,7 +834,7 @@ struct Orc {
       St.push_back(a.first.second);
     }
     uniq(St);
-    // line 2: repair m, degrees, community totals and the aggregate chain
+    // repair m, degrees, community totals and the aggregate chain
     std::vector<ERec> chain(arcs);
     for (auto& a : arcs) {
       const int32_t i = a.first.first, j = a.first.second;
@@ -863,14 +863,14 @@ struct Orc {
     }
     Q = q_from_stats();
     Qrep = Q;
-    // line 3: InitFrontier
+    // InitFrontier
     std::vector<std::vector<int32_t>> A(T + 1);
     A[0] = St;
     for (int r = 1; r <= T; ++r) {
       for (int32_t v : A[r - 1]) A[r].push_back(lv[r - 1].par[v]);
       uniq(A[r]);
     }
-    // lines 4-27
+    // the passes: per level move, push-down, refine, aggregate
     for (int pass = 0; pass < N; ++pass) {
       ctr.passes++;
       const i128 Qpass = Q;

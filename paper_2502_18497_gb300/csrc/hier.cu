@@ -1,7 +1,7 @@
-// Hierarchy maintenance of Algorithm 1: batch ingest and validation (line 1),
-// statistic repair along the parent chain (line 2, InitFrontier line 3),
-// label push-down after supernode moves, TouchedRefined / dissolve (line 16),
-// and the Eq. 3 subtract-add aggregate repair with NextFrontier (lines 23-24).
+// Hierarchy maintenance of Algorithm 1: batch ingest and validation (the
+// batch's application to level 0), statistic repair along the parent chain
+// and InitFrontier, label push-down after supernode moves, TouchedRefined /
+// dissolve, and the Eq. 3 subtract-add aggregate repair with NextFrontier.
 #include "chunks.cuh"
 #include "kern.cuh"
 
@@ -749,9 +749,9 @@ static int64_t propagate_once(ldl_ctx& c, int q, DBuf<u64>& keys, DBuf<u64>& val
 
 void repair_batch(ldl_ctx& c, int64_t na, const int32_t* epA, int32_t epT, int64_t dm) {
   if (na <= 0) return;
-  // Algorithm 1 line 1: the batch changes level 0
+  // Algorithm 1, applying the batch: it changes level 0
   apply_level(c, 0, c.rk, c.rv, na);
-  // line 2: m, degrees, community totals (exactly, with sum_C K_out K_in)
+  // statistic repair: m, degrees, community totals (exactly, with sum_C K_out K_in)
   LevelState& L0 = c.lv[0];
   zero_cnt(c, K_T);
   k_dirty<<<grid_for(na, TPB), TPB, 0, c.s>>>(c.rk.p, na, c.bits, L0.lab.p, c.stT.p, epT, c.lT.p, c.dcnt + K_T);

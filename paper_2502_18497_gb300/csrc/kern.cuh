@@ -19,11 +19,12 @@ void union_into(ldl_ctx& c, const int32_t* list, int idx_n, int32_t* stamp, int3
 // and their count (counter K_CAND) stay on the device.
 void sweep(ldl_ctx& c, int r, int mode, const int32_t* list, int idx_n, int64_t n_hint);
 // Decoupling filter over the last sweep's candidates: returns their number
-// and the number accepted (the accepted moves are in bv / bsrc / bdst).
+// and the number accepted (the accepted moves are in bv / bsrc / bdst), and
+// counter `extra` (when >= 0) read in the same host wait.
 struct DecoupleOut {
-  int32_t nc, nb;
+  int32_t nc, nb, extra;
 };
-DecoupleOut decouple(ldl_ctx& c);
+DecoupleOut decouple(ldl_ctx& c, int extra = -1);
 CommitOut commit_move(ldl_ctx& c, int r, int32_t nb, int32_t epB, int32_t epT, int32_t epCh);
 void rollback_move(ldl_ctx& c, int r, int32_t nb, int32_t ntc);
 void mark_moved(ldl_ctx& c, int r, int32_t nb, int32_t epMv, int32_t epM0);

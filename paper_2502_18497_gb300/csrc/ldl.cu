@@ -165,14 +165,15 @@ static void free_all(ldl_ctx& c) {
 }
 
 // ---------------------------------------------------------------- move loop
-// Algorithm 1 lines 6-15 at level r.  Precondition: lU holds U = A^r, and
+// The local-move loop of Algorithm 1 at level r.  Precondition: lU holds U = A^r, and
 // lUstar / stU (epoch epU) hold U*.  Moved nodes go to lMv (epMv) and, at
 // level 0, to lM0 (epM0).
-static void move_loop(ldl_ctx& c, int r, int rounds, int32_t epU, int32_t epMv, int32_t epM0, int32_t epCh) {
+static void move_loop(ldl_ctx& c, int r, int rounds, int32_t epU, int32_t epMv, int32_t epM0, int32_t epCh,
+                      int32_t nU) {
+  // nU = |U| on entry; later rounds take it from the end of the previous one
   const i128 Q0 = qnum(c);
   const int64_t ainv = c.prm.alpha_inv, binv = c.prm.beta_inv;
   for (int j = 0; j < rounds; ++j) {
-    const int32_t nU = rd_cnt(c, K_U);
     if (nU == 0) break;
     c.res.rounds++;
     stage_begin(c);
@@ -212,12 +213,13 @@ static void move_loop(ldl_ctx& c, int r, int rounds, int32_t epU, int32_t epMv, 
     const int32_t nU2 = rd_cnt(c, K_U);
     union_into(c, c.lU.p, K_U, c.stU.p, epU, c.lUstar.p, K_USTAR, nU2);
     stage_end(c, ST_EXPAND);
+    nU = nU2;
     if (co.dq * (i128)ainv < Q0) break;
     if ((int64_t)nb * binv < (int64_t)nS) break;
   }
 }
 
-// Algorithm 1 lines 16-22 at level r over the dissolved set lD (epoch epD).
+// The refinement loop of Algorithm 1 at level r over the dissolved set lD (epoch epD).
 static int64_t refine_loop(ldl_ctx& c, int r, int rounds, int32_t epD) {
   const int32_t nD = rd_cnt(c, K_D);
   if (nD == 0) return 0;
@@ -229,12 +231,16 @@ static int64_t refine_loop(ldl_ctx& c, int r, int rounds, int32_t epD) {
   int64_t merges = 0;
   const int64_t binv = c.prm.beta_inv;
   for (int j = 0; j < rounds; ++j) {
-    const int32_t nR = rd_cnt(c, iR);
-    if (nR == 0) break;
+    // R is a subset of D, so nD bounds the sweep's launch; |R| comes back with
+    // the decoupling result (an empty R gives no candidates and ends the loop)
     c.res.rounds++;
-    sweep(c, r, 1, R, iR, nR);
-    const DecoupleOut dd = decouple(c);
-    const int32_t nc = dd.nc, nb = dd.nb;
+    sweep(c, r, 1, R, iR, nD);
+    const DecoupleOut dd = decouple(c, iR);
+    const int32_t nc = dd.nc, nb = dd.nb, nR = dd.extra;
+    if (nR == 0) {
+      c.res.rounds--;
+      break;
+    }
     if (nc == 0) break;
     c.res.rejected += nc - nb;
     if (nb == 0) break;
@@ -266,7 +272,7 @@ static void static_build(ldl_ctx& c) {
     zero_cnt(c, K_MV);
     zero_cnt(c, K_M0);
     zero_cnt(c, K_CH);
-    move_loop(c, r, c.prm.M_static, epU, epMv, epM0, epCh);
+    move_loop(c, r, c.prm.M_static, epU, epMv, epM0, epCh, nU);
     if (r > 0) pushdown(c, r, epCh);
     if (r == L) break;
     level_alloc(c, r + 1);
@@ -329,7 +335,7 @@ static void apply_batch(ldl_ctx& c, const ldl_update* upd, int64_t count, int on
       union_into(c, c.lU.p, K_U, c.stU.p, epU, c.lUstar.p, K_USTAR, nU);
       const int32_t epMv = c.next_epoch();
       zero_cnt(c, K_MV);
-      move_loop(c, r, c.prm.M, epU, epMv, epM0, epCh);
+      move_loop(c, r, c.prm.M, epU, epMv, epM0, epCh, nU);
       if (r > 0) {
         stage_begin(c);
         pushdown(c, r, epCh);

@@ -1,8 +1,8 @@
-// Frontier sweeps of Algorithm 1: candidate-set expansion (lines 8, 12, 21),
-// BestMove / BestRef with the exact Eq. 2 gain (lines 9, 18), the decoupling
+// Frontier sweeps of Algorithm 1: candidate-set expansion (Expand, SPExpand),
+// BestMove / BestRef with the exact Eq. 2 gain, the decoupling
 // filter of Sec. III-E as deterministic parallel rounds, and the commit of an
 // accepted mini-batch with the additive repair of the community totals and
-// the exact modularity change dQ(B) (lines 10-11).
+// the exact modularity change dQ(B) with its rollback test.
 #include <cooperative_groups.h>
 
 #include "chunks.cuh"
@@ -1215,7 +1215,7 @@ void sweep(ldl_ctx& c, int r, int mode, const int32_t* list, int idx_n, int64_t 
   }
 }
 
-DecoupleOut decouple(ldl_ctx& c) {
+DecoupleOut decouple(ldl_ctx& c, int extra) {
   // The single-block filter runs first and reads the candidate count on the
   // device; one read then returns the count, the accepted number and the
   // filter's status (-2: too many candidates for one block).
@@ -1225,16 +1225,17 @@ DecoupleOut decouple(ldl_ctx& c) {
                                           c.role.p, c.best.p, c.bv.p, c.bsrc.p, c.bdst.p, c.dcnt + K_B,
                                           c.dcnt + K_UNDEC);
   CKL("k_dec_block");
-  int32_t out[3];
+  int32_t out[3], ex = 0;
   ++c.syncs;
   CK(cudaMemcpyAsync(out, c.dcnt + K_CAND, sizeof(out), cudaMemcpyDeviceToHost, c.s));
+  if (extra >= 0) CK(cudaMemcpyAsync(&ex, c.dcnt + extra, sizeof(int32_t), cudaMemcpyDeviceToHost, c.s));
   CK(cudaStreamSynchronize(c.s));
   const int32_t nc = out[0];
-  if (nc <= 0) return {0, 0};
+  if (nc <= 0) return {0, 0, ex};
   if (out[2] != -2) {
     if (out[2] < 0) ldl_throw(LDL_E_INVALID, "internal: decoupling did not converge");
     c.res.decouple_rounds += out[2];
-    return {nc, out[1]};
+    return {nc, out[1], ex};
   }
   CK(cudaMemsetAsync(c.cst.p, 0, sizeof(int32_t) * (size_t)nc, c.s));
   const int g = grid_for(nc, TPB);
@@ -1260,7 +1261,8 @@ DecoupleOut decouple(ldl_ctx& c) {
   k_dec_finish<<<g, TPB, 0, c.s>>>(nc, c.cst.p, c.cv.p, c.csrc.p, c.cdst.p, c.role.p, c.bv.p, c.bsrc.p, c.bdst.p,
                                    c.dcnt + K_B);
   CKL("k_dec_finish");
-  return {nc, rd_cnt(c, K_B)};
+  const int32_t nb = rd_cnt(c, K_B);
+  return {nc, nb, ex};
 }
 
 CommitOut commit_move(ldl_ctx& c, int r, int32_t nb, int32_t epB, int32_t epT, int32_t epCh) {

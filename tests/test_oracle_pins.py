@@ -129,7 +129,7 @@ def test_decouple_is_the_greedy_filter():
 
 # --------------------------------------------------------------------- repair
 def test_level0_matches_generator_edge_set():
-    """Batch application (Algorithm 1 line 1) reproduces the generator's own
+    """Batch application (the first step of Algorithm 1) reproduces the generator's own
     record of the evolving edge set, including reweights and deletes."""
     for seed, g in _graphs(12):
         for o, st in _stream_states(g, seed, batches=6):
