@@ -73,6 +73,10 @@ typedef struct {
    * distributed shared-memory hash instead of the whole-GPU hub path;
    * 0 (the default) keeps every row above 2048 entries on the hub path. */
   int32_t cluster_max_deg;
+  /* 1: collect the sweep kernel statistics (ldl_get_kernel_stats) from the
+   * start, so that they cover the static build inside ldl_create; 0 (the
+   * default): off until ldl_set_kernel_stats. */
+  int32_t kernel_stats;
   void* cuda_stream;
 } ldl_params;
 

@@ -452,6 +452,7 @@ ldl_status ldl_create(const ldl_params* params, int64_t n, int64_t nnz, const in
     CK(cudaEventCreate(&c->ev2));
     CK(cudaEventCreate(&c->ev3));
     c->lv.resize(p.L + 1);
+    c->kstats = p.kernel_stats ? 1 : 0;
     alloc_globals(*c);
     level_alloc(*c, 0);
     upload_graph(*c, nnz, row_ptr, col, w);
