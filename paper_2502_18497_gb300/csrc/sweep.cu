@@ -580,17 +580,25 @@ __global__ void k_hub_acc(SweepArgs<WT> A, ChunkMap m, const int64_t* loff, cons
       const unsigned peers = __match_any_sync(0xffffffffu, key);
       const int leader = __ffs(peers) - 1;
       uint32_t h = 0;
+      bool fresh = false;
       if (key >= 0 && lane == leader) {
         h = hash32((uint32_t)key) & mask;
         while (true) {
           const int32_t prev = atomicCAS(&K[h], -1, key);
-          if (prev == -1) {  // a new key: list its slot
-            glist[loff[ch.idx] / 2 + atomicAdd(&hcnt[ch.idx], 1)] = (int32_t)h;
+          if (prev == -1 || prev == key) {
+            fresh = prev == -1;
             break;
           }
-          if (prev == key) break;
           h = (h + 1) & mask;
         }
+      }
+      // new keys of the warp (all of one hub) are listed with one counter atomic
+      const unsigned fm = __ballot_sync(0xffffffffu, fresh);
+      if (fm) {
+        int32_t base = 0;
+        if (lane == __ffs(fm) - 1) base = atomicAdd(&hcnt[ch.idx], __popc(fm));
+        base = __shfl_sync(0xffffffffu, base, __ffs(fm) - 1);
+        if (fresh) glist[loff[ch.idx] / 2 + base + __popc(fm & ((1u << lane) - 1u))] = (int32_t)h;
       }
       h = __shfl_sync(0xffffffffu, h, leader);
       if (key >= 0) atomicAdd((unsigned long long*)&V[h], (unsigned long long)w);
