@@ -66,6 +66,14 @@ struct DBuf {
 };
 
 // ---------------------------------------------------------------- int128 helpers
+// One device value to copy to the host (see host_read).
+struct HostRead {
+  const void* src;  // device
+  void* dst;        // host
+  int32_t bytes;
+};
+using HostReadFn = void (*)(void* owner, const HostRead* r, int n);
+
 struct I128 {  // two's complement halves; host and device
   int64_t hi;
   uint64_t lo;

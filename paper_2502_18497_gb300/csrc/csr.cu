@@ -393,10 +393,9 @@ void csr_apply(SlackCSR<WT>& g, const u64* keys, const int64_t* delta, int64_t n
                 "adjacent totals");
   int64_t tot[4] = {0, 0, 0, 0};  // need, nseg, scratch total, rebuild total
   int32_t bad = 0;
-  CK(cudaMemcpyAsync(&tot[0], &d_sc->need, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-  CK(cudaMemcpyAsync(&tot[1], &d_sc->seg_n, 3 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-  CK(cudaMemcpyAsync(&bad, &d_sc->cnt[C_Z], sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
+  const HostRead rr[3] = {{&d_sc->need, &tot[0], sizeof(int64_t)}, {&d_sc->seg_n, &tot[1], 3 * sizeof(int64_t)},
+                          {&d_sc->cnt[C_Z], &bad, sizeof(int32_t)}};
+  P.read(rr, 3, s);
   if (bad) ldl_throw(LDL_E_INVALID, "internal: adjacency update would make a weight negative");
   const int64_t need = tot[0], nseg = tot[1], stotal = tot[2], wtotal = tot[3];
   const int gs = grid_for(nseg, TPB);

@@ -104,6 +104,11 @@ struct ldl_ctx {
   size_t kev_used = 0;
   double ks_launch[KS_GROUPS] = {0, 0, 0, 0, 0, 0, 0};
   int64_t syncs = 0;  // host synchronisations in the current batch
+  // host reads of device values: a pinned, device-mapped page (word 0 is the
+  // sequence number of the last read, the payload follows)
+  volatile int64_t* h_pub = nullptr;
+  int64_t* d_pub = nullptr;
+  int64_t pub_seq = 0;
   std::string err;
 
   int32_t next_epoch() { return ++epoch; }
@@ -134,6 +139,10 @@ inline int64_t* kin_of(ldl_ctx& c, int r) { return c.directed ? c.lv[r].kin.p : 
 inline int64_t* Kin_of(ldl_ctx& c) { return c.directed ? c.Kin.p : c.Kout.p; }
 
 // host reads of device counters (synchronise)
+// Copies device values to the host once the context's stream has reached
+// this point: a one-block kernel writes them into the pinned page and then the
+// sequence number, which the host polls (a stream error ends the wait).
+void host_read(ldl_ctx& c, const HostRead* r, int n);
 int32_t rd_cnt(ldl_ctx& c, int idx);
 void zero_cnt(ldl_ctx& c, int idx);
 void set_cnt(ldl_ctx& c, int idx, int32_t v);

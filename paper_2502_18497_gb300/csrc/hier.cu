@@ -623,8 +623,8 @@ void gather_labels(ldl_ctx& c, const int32_t* ids, int32_t k, int32_t* out) {
 }
 static void throw_err(ldl_ctx& c, unsigned long long* d_err, const char* what) {
   unsigned long long e = 0;
-  CK(cudaMemcpyAsync(&e, d_err, sizeof(e), cudaMemcpyDeviceToHost, c.s));
-  CK(cudaStreamSynchronize(c.s));
+  const HostRead r{d_err, &e, sizeof(e)};
+  host_read(c, &r, 1);
   if (e != ~0ull) {
     const int code = (int)(e & 255);
     const long long idx = (long long)(e >> 8);
@@ -678,8 +678,10 @@ int64_t ingest(ldl_ctx& c, const ldl_update* upd, int64_t count, int on_device, 
                                             c.directed, c.rsum2.p, err_ptr(c), &c.d_sc->dm);
   CKL("k_seq");
   throw_err(c, err_ptr(c), "invalid update sequence");
-  CK(cudaMemcpyAsync(dm, &c.d_sc->dm, sizeof(int64_t), cudaMemcpyDeviceToHost, c.s));
-  CK(cudaStreamSynchronize(c.s));
+  {
+    const HostRead r{&c.d_sc->dm, dm, sizeof(int64_t)};
+    host_read(c, &r, 1);
+  }
   if (c.m + *dm >= ((int64_t)1 << 50) || c.m + *dm < 0) ldl_throw(LDL_E_OVERFLOW, "total weight m would reach 2^50");
   zero_cnt(c, K_REC);
   k_emit_arcs<<<grid_for(nu, TPB), TPB, 0, c.s>>>(c.rk2.p, c.rsum2.p, nu, c.bits, c.directed, c.rk.p, c.rv.p,
@@ -766,12 +768,14 @@ void repair_batch(ldl_ctx& c, int64_t na, const int32_t* epA, int32_t epT, int64
   CKL("k_stat_arcs");
   k_psum<<<grid_for(2 * na, TPB), TPB, 0, c.s>>>(c.lT.p, c.dcnt + K_T, c.Kout.p, Kin_of(c), &c.d_sc->p_new);
   CKL("k_psum");
-  DevScalars h;
-  CK(cudaMemcpyAsync(&h, c.d_sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, c.s));
-  CK(cudaStreamSynchronize(c.s));
+  I128 p_old, p_new;
+  int64_t de = 0;
+  const HostRead rr[3] = {{&c.d_sc->p_old, &p_old, sizeof(I128)}, {&c.d_sc->p_new, &p_new, sizeof(I128)},
+                          {&c.d_sc->de, &de, sizeof(int64_t)}};
+  host_read(c, rr, 3);
   c.m += dm;
-  c.E += h.de;
-  c.Psum += i128_of(h.p_new.hi, h.p_new.lo) - i128_of(h.p_old.hi, h.p_old.lo);
+  c.E += de;
+  c.Psum += i128_of(p_new.hi, p_new.lo) - i128_of(p_old.hi, p_old.lo);
   // the aggregate chain: W_r(anc(i), anc(j)) += delta, strengths, A^r
   int64_t cur = na;
   for (int q = 0; q < c.T; ++q) {
@@ -859,8 +863,10 @@ static void emit_records(ldl_ctx& c, int r, Adj<WT> out, Adj<WT> in, int32_t nC,
   k_deg_sum<WT><<<grid_for(nC, TPB), TPB, 0, c.s>>>(out, in, c.lC.p, c.dcnt + K_C, &c.d_sc->need);
   CKL("k_deg_sum");
   int64_t deg = 0;
-  CK(cudaMemcpyAsync(&deg, &c.d_sc->need, sizeof(int64_t), cudaMemcpyDeviceToHost, c.s));
-  CK(cudaStreamSynchronize(c.s));
+  {
+    const HostRead r{&c.d_sc->need, &deg, sizeof(int64_t)};
+    host_read(c, &r, 1);
+  }
   const int64_t cap = 2 * deg + 16;
   c.rk2.reserve(cap, c.s);
   c.rv2.reserve(cap, c.s);
@@ -981,10 +987,8 @@ void aggregate(ldl_ctx& c, int r, int32_t epD, int32_t epC, int32_t epA_next, bo
       CKL("k_exist");
       // children records of this level and the next level's list, in one read
       int32_t nd = 0, ne_next = 0;
-      ++c.syncs;
-      CK(cudaMemcpyAsync(&nd, c.dcnt + K_CREC, sizeof(int32_t), cudaMemcpyDeviceToHost, c.s));
-      CK(cudaMemcpyAsync(&ne_next, c.dcnt + ie2, sizeof(int32_t), cudaMemcpyDeviceToHost, c.s));
-      CK(cudaStreamSynchronize(c.s));
+      const HostRead rr[2] = {{c.dcnt + K_CREC, &nd, sizeof(int32_t)}, {c.dcnt + ie2, &ne_next, sizeof(int32_t)}};
+      host_read(c, rr, 2);
       if (nd > 0) {
         sort_pairs(c.crk, c.crv, c.tk, c.tv, nd, 2 * c.bits, c.P, c.s);
         csr_apply<int32_t>(c.lv[q].children, c.crk.p, (const int64_t*)c.crv.p, nd, c.bits, c.CS, c.P, c.s, c.d_sc);

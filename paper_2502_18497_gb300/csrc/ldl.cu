@@ -46,19 +46,73 @@ void dfree(void* p) {
   if (p) cudaFree(p);
 }
 
-int32_t rd_cnt(ldl_ctx& c, int idx) {
+namespace {
+constexpr int PUB_MAX = 8;        // values per read
+constexpr int PUB_BYTES = 4000;   // payload bytes per read
+struct PubReq {
+  const unsigned char* src[PUB_MAX];
+  int32_t off[PUB_MAX], bytes[PUB_MAX];
+  int32_t n;
+};
+
+__global__ void k_publish(PubReq q, unsigned char* payload, int64_t* seq_word, int64_t seq) {
+  for (int i = 0; i < q.n; ++i)
+    for (int b = threadIdx.x; b < q.bytes[i]; b += blockDim.x) payload[q.off[i] + b] = q.src[i][b];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence_system();  // the payload is visible to the host before the sequence number
+    *(volatile int64_t*)seq_word = seq;
+  }
+}
+
+__global__ void k_set_i32(int32_t* p, int32_t v) { *p = v; }
+}  // namespace
+
+void host_read(ldl_ctx& c, const HostRead* r, int n) {
   ++c.syncs;
+  PubReq q{};
+  int32_t off = 0;
+  if (n > PUB_MAX) ldl_throw(LDL_E_INVALID, "internal: host read of too many values");
+  for (int i = 0; i < n; ++i) {
+    q.src[i] = (const unsigned char*)r[i].src;
+    q.off[i] = off;
+    q.bytes[i] = r[i].bytes;
+    off += (r[i].bytes + 7) & ~7;
+  }
+  if (off > PUB_BYTES) ldl_throw(LDL_E_INVALID, "internal: host read too large");
+  q.n = n;
+  const int64_t seq = ++c.pub_seq;
+  k_publish<<<1, 64, 0, c.s>>>(q, (unsigned char*)(c.d_pub + 1), c.d_pub, seq);
+  CKL("k_publish");
+  // Poll the mapped sequence word.  Every so often ask the stream: an error
+  // ends the wait with that error; an idle stream whose write is still not
+  // seen falls back to a full synchronisation before failing.
+  for (uint64_t spins = 1; c.h_pub[0] != seq; ++spins) {
+    if ((spins & 4095) == 0) {
+      const cudaError_t e = cudaStreamQuery(c.s);
+      if (e == cudaErrorNotReady) continue;
+      CK(e);
+      CK(cudaStreamSynchronize(c.s));
+      if (c.h_pub[0] != seq) ldl_throw(LDL_E_CUDA, "internal: a published value never reached the host");
+    }
+  }
+  std::atomic_thread_fence(std::memory_order_acquire);
+  const unsigned char* pay = (const unsigned char*)(c.h_pub + 1);
+  for (int i = 0; i < n; ++i) memcpy(r[i].dst, pay + q.off[i], (size_t)r[i].bytes);
+}
+
+int32_t rd_cnt(ldl_ctx& c, int idx) {
   int32_t v = 0;
-  CK(cudaMemcpyAsync(&v, c.dcnt + idx, sizeof(int32_t), cudaMemcpyDeviceToHost, c.s));
-  CK(cudaStreamSynchronize(c.s));
+  const HostRead r{c.dcnt + idx, &v, sizeof(int32_t)};
+  host_read(c, &r, 1);
   return v;
 }
 
 void zero_cnt(ldl_ctx& c, int idx) { CK(cudaMemsetAsync(c.dcnt + idx, 0, sizeof(int32_t), c.s)); }
 
 void set_cnt(ldl_ctx& c, int idx, int32_t v) {
-  CK(cudaMemcpyAsync(c.dcnt + idx, &v, sizeof(int32_t), cudaMemcpyHostToDevice, c.s));
-  CK(cudaStreamSynchronize(c.s));
+  k_set_i32<<<1, 1, 0, c.s>>>(c.dcnt + idx, v);
+  CKL("k_set_i32");
 }
 
 void stage_begin(ldl_ctx& c) {
@@ -125,6 +179,8 @@ static void alloc_globals(ldl_ctx& c) {
   CK(cudaMemsetAsync(c.d_sc, 0, sizeof(DevScalars), c.s));
   c.dcnt = (int32_t*)dalloc(sizeof(int32_t) * K_COUNT);
   CK(cudaMemsetAsync(c.dcnt, 0, sizeof(int32_t) * K_COUNT, c.s));
+  c.P.rd = [](void* owner, const HostRead* r, int n) { host_read(*(ldl_ctx*)owner, r, n); };
+  c.P.rd_owner = &c;
 }
 
 static void free_all(ldl_ctx& c) {
@@ -154,6 +210,9 @@ static void free_all(ldl_ctx& c) {
   if (c.dcnt) dfree(c.dcnt);
   c.d_sc = nullptr;
   c.dcnt = nullptr;
+  if (c.h_pub) cudaFreeHost((void*)c.h_pub);
+  c.h_pub = nullptr;
+  c.d_pub = nullptr;
   if (c.ev0) cudaEventDestroy(c.ev0);
   if (c.ev1) cudaEventDestroy(c.ev1);
   if (c.ev2) cudaEventDestroy(c.ev2);
@@ -447,6 +506,15 @@ ldl_status ldl_create(const ldl_params* params, int64_t n, int64_t nnz, const in
     c->directed = p.directed ? 1 : 0;
     c->bits = std::max(1, bits_for(n));
     c->s = (cudaStream_t)p.cuda_stream;
+    {
+      void* hp = nullptr;
+      CK(cudaHostAlloc(&hp, 4096, cudaHostAllocMapped));
+      c->h_pub = (volatile int64_t*)hp;
+      c->h_pub[0] = 0;
+      void* dp = nullptr;
+      CK(cudaHostGetDevicePointer(&dp, hp, 0));
+      c->d_pub = (int64_t*)dp;
+    }
     CK(cudaEventCreate(&c->ev0));
     CK(cudaEventCreate(&c->ev1));
     CK(cudaEventCreate(&c->ev2));

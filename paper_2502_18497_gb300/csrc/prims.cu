@@ -439,8 +439,8 @@ static int64_t scan_t(const T* in, int64_t* out, int64_t n, Prims& P, cudaStream
   scan_launch<T>(in, out, n, nullptr, n, P.bsum.p + 1, P, s);
   if (!want_total) return -1;
   int64_t tot = 0;
-  CK(cudaMemcpyAsync(&tot, P.bsum.p + 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
+  const HostRead r{P.bsum.p + 1, &tot, sizeof(int64_t)};
+  P.read(&r, 1, s);
   return tot;
 }
 

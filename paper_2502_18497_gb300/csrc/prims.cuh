@@ -8,6 +8,17 @@ struct Prims {  // scratch owned by a context
   DBuf<u64> lb_st;       // look-back scan: per-tile state words
   DBuf<int32_t> lb_ctl;  // look-back scan: 256 epoch tile counters, then the error flag
   uint32_t lb_ep = 0;
+  // how totals reach the host (nullptr: a copy and a stream synchronisation)
+  HostReadFn rd = nullptr;
+  void* rd_owner = nullptr;
+  void read(const HostRead* r, int n, cudaStream_t s) {
+    if (rd) {
+      rd(rd_owner, r, n);
+      return;
+    }
+    for (int i = 0; i < n; ++i) CK(cudaMemcpyAsync(r[i].dst, r[i].src, (size_t)r[i].bytes, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+  }
   void release() {
     bsum.release(); hist.release(); pos.release(); usum.release();
     flag.release(); lb_st.release(); lb_ctl.release();

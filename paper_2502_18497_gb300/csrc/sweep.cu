@@ -1149,9 +1149,10 @@ static void sweep_t(ldl_ctx& c, int r, Adj<WT> out, Adj<WT> in, const int32_t* l
   // counters K_SMALL .. K_CLU in one read
   int32_t cn[K_CLU - K_SMALL + 1];
   int64_t tab = 0;
-  CK(cudaMemcpyAsync(cn, c.dcnt + K_SMALL, sizeof(cn), cudaMemcpyDeviceToHost, c.s));
-  CK(cudaMemcpyAsync(&tab, &c.d_sc->need, sizeof(int64_t), cudaMemcpyDeviceToHost, c.s));
-  CK(cudaStreamSynchronize(c.s));
+  {
+    const HostRead rr[2] = {{c.dcnt + K_SMALL, cn, (int32_t)sizeof(cn)}, {&c.d_sc->need, &tab, sizeof(int64_t)}};
+    host_read(c, rr, 2);
+  }
   const int32_t ct = cn[K_TINY - K_SMALL], cs = cn[0], cm = cn[K_MID - K_SMALL], cm2 = cn[K_MID2 - K_SMALL];
   const int32_t cc = cn[K_CLU - K_SMALL], ch = cn[K_LARGE - K_SMALL];
   if (kev) CK(cudaEventRecord(kev[6], c.s));  // the wait above is charged to no kernel
@@ -1234,10 +1235,11 @@ DecoupleOut decouple(ldl_ctx& c, int extra) {
                                           c.dcnt + K_UNDEC);
   CKL("k_dec_block");
   int32_t out[3], ex = 0;
-  ++c.syncs;
-  CK(cudaMemcpyAsync(out, c.dcnt + K_CAND, sizeof(out), cudaMemcpyDeviceToHost, c.s));
-  if (extra >= 0) CK(cudaMemcpyAsync(&ex, c.dcnt + extra, sizeof(int32_t), cudaMemcpyDeviceToHost, c.s));
-  CK(cudaStreamSynchronize(c.s));
+  {
+    const HostRead rr[2] = {{c.dcnt + K_CAND, out, (int32_t)sizeof(out)},
+                            {c.dcnt + (extra >= 0 ? extra : K_CAND), &ex, sizeof(int32_t)}};
+    host_read(c, rr, extra >= 0 ? 2 : 1);
+  }
   const int32_t nc = out[0];
   if (nc <= 0) return {0, 0, ex};
   if (out[2] != -2) {
@@ -1305,15 +1307,13 @@ CommitOut commit_move(ldl_ctx& c, int r, int32_t nb, int32_t epB, int32_t epT, i
                                                                c.snapKo.p, c.snapKi.p, c.snapE.p, c.m,
                                                                c.prm.gamma_num, c.prm.gamma_den, c.d_sc);
   CKL("k_commit_dq");
-  DevScalars h;
   CommitOut o;
-  ++c.syncs;
-  CK(cudaMemcpyAsync(&h, c.d_sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, c.s));
-  CK(cudaMemcpyAsync(&o.ntc, c.dcnt + K_T, sizeof(int32_t), cudaMemcpyDeviceToHost, c.s));
-  CK(cudaStreamSynchronize(c.s));
-  o.dq = i128_of(h.dq.hi, h.dq.lo);
-  o.dp = i128_of(h.dp.hi, h.dp.lo);
-  o.de = h.de;
+  I128 dq, dp;
+  const HostRead rr[4] = {{&c.d_sc->dq, &dq, sizeof(I128)}, {&c.d_sc->dp, &dp, sizeof(I128)},
+                          {&c.d_sc->de, &o.de, sizeof(int64_t)}, {c.dcnt + K_T, &o.ntc, sizeof(int32_t)}};
+  host_read(c, rr, 4);
+  o.dq = i128_of(dq.hi, dq.lo);
+  o.dp = i128_of(dp.hi, dp.lo);
   return o;
 }
 
