@@ -711,54 +711,71 @@ __device__ inline void claim(int32_t* best, int32_t c, int32_t i, const int64_t*
   }
 }
 
-__global__ void k_dec_claim(int32_t nc, const int32_t* cst, const int32_t* src, const int32_t* dst,
-                            const int64_t* ghi, const uint64_t* glo, const int32_t* cv, const int32_t* role,
-                            int32_t* best) {
-  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) {
-    if (cst[i] != 0) continue;
-    if (role[src[i]] == 0) claim(best, src[i], i, ghi, glo, cv);
-    if (role[dst[i]] == 0) claim(best, dst[i], i, ghi, glo, cv);
-  }
-}
-
 // A candidate is decided once every earlier candidate touching its source and
 // its target is decided: either the community already has a role (set by its
 // first accepted candidate, which precedes every undecided one) or this
-// candidate is the earliest undecided one touching it.
-__global__ void k_dec_decide(int32_t nc, int32_t* cst, const int32_t* src, const int32_t* dst, const int32_t* role,
-                             const int32_t* best, int32_t* undecided) {
-  int32_t left = 0;
-  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) {
-    if (cst[i] != 0) continue;
-    const int32_t ra = role[src[i]], rb = role[dst[i]];
-    const bool da = ra != 0 || best[src[i]] == i;
-    const bool db = rb != 0 || best[dst[i]] == i;
-    if (da && db) {
-      cst[i] = (ra != 2 && rb != 1) ? 3 : 2;  // 3: accepted, roles pending
-    } else {
-      ++left;
+// candidate is the earliest undecided one touching it.  A round: every
+// undecided candidate claims its still role-free communities (CAS keeping the
+// earliest), then the decidable ones are decided, then accepted candidates
+// give their communities roles (emitter / acceptor) and the claims are reset.
+
+// Whole decoupling filter in one cooperative launch when the candidates are
+// many: the three phases of a round, one grid barrier after each, and the
+// round counters alternate between two slots (the
+// next round's slot is cleared while the current one is still being read).
+// Every block reads the same count after the barrier, so all leave together;
+// at most nc + 1 rounds (each decides the earliest undecided candidate).
+__global__ void __launch_bounds__(TPB) k_dec_grid(int32_t nc, int32_t* cst, const int32_t* cv, const int32_t* src,
+                                                  const int32_t* dst, const int64_t* ghi, const uint64_t* glo,
+                                                  int32_t* role, int32_t* best, int32_t* bv, int32_t* bsrc,
+                                                  int32_t* bdst, int32_t* nb, int32_t* undecided, int32_t* stat) {
+  cg::grid_group grid = cg::this_grid();
+  const int32_t tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+  for (int32_t i = tid; i < nc; i += nth) cst[i] = 0;
+  if (tid == 0) undecided[0] = undecided[1] = 0;
+  grid.sync();
+  int32_t rounds = 0;
+  bool ok = true;
+  for (;;) {
+    const int par = rounds & 1;
+    for (int32_t i = tid; i < nc; i += nth) {
+      if (cst[i] != 0) continue;
+      if (role[src[i]] == 0) claim(best, src[i], i, ghi, glo, cv);
+      if (role[dst[i]] == 0) claim(best, dst[i], i, ghi, glo, cv);
+    }
+    grid.sync();
+    int32_t left = 0;
+    for (int32_t i = tid; i < nc; i += nth) {
+      if (cst[i] != 0) continue;
+      const int32_t ra = role[src[i]], rb = role[dst[i]];
+      const bool da = ra != 0 || best[src[i]] == i;
+      const bool db = rb != 0 || best[dst[i]] == i;
+      if (da && db) cst[i] = (ra != 2 && rb != 1) ? 3 : 2;
+      else ++left;
+    }
+    left = warp_sum_i32(left);
+    if ((threadIdx.x & 31) == 0 && left) atomicAdd(&undecided[par], left);
+    grid.sync();
+    for (int32_t i = tid; i < nc; i += nth) {
+      best[src[i]] = -1;
+      best[dst[i]] = -1;
+      if (cst[i] == 3) {
+        role[src[i]] = 1;
+        role[dst[i]] = 2;
+        cst[i] = 1;
+      }
+    }
+    if (tid == 0) undecided[par ^ 1] = 0;
+    grid.sync();
+    const int32_t l = *(volatile int32_t*)&undecided[par];
+    ++rounds;
+    if (l == 0) break;
+    if (rounds > nc + 1) {
+      ok = false;
+      break;
     }
   }
-  if (left) atomicAdd(undecided, left);
-}
-
-__global__ void k_dec_roles(int32_t nc, int32_t* cst, const int32_t* src, const int32_t* dst, int32_t* role,
-                            int32_t* best) {
-  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) {
-    best[src[i]] = -1;
-    best[dst[i]] = -1;
-    if (cst[i] == 3) {
-      role[src[i]] = 1;  // emitter
-      role[dst[i]] = 2;  // acceptor
-      cst[i] = 1;
-    }
-  }
-}
-
-__global__ void k_dec_finish(int32_t nc, const int32_t* cst, const int32_t* cv, const int32_t* src,
-                             const int32_t* dst, int32_t* role, int32_t* bv, int32_t* bsrc, int32_t* bdst,
-                             int32_t* nb) {
-  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) {
+  for (int32_t i = tid; i < nc; i += nth) {
     role[src[i]] = 0;
     role[dst[i]] = 0;
     if (cst[i] == 1) {
@@ -768,6 +785,7 @@ __global__ void k_dec_finish(int32_t nc, const int32_t* cst, const int32_t* cv, 
       bdst[p] = dst[i];
     }
   }
+  if (tid == 0) *stat = ok ? rounds : -1;
 }
 
 // Whole decoupling filter in one block when the candidates are few: the
@@ -1247,33 +1265,34 @@ DecoupleOut decouple(ldl_ctx& c, int extra) {
     c.res.decouple_rounds += out[2];
     return {nc, out[1], ex};
   }
-  CK(cudaMemsetAsync(c.cst.p, 0, sizeof(int32_t) * (size_t)nc, c.s));
-  const int g = grid_for(nc, TPB);
-  int rounds = 0;
-  while (true) {
-    // a few rounds per host check: rounds past completion change nothing
-    for (int k = 0; k < 2; ++k) {
-      k_dec_claim<<<g, TPB, 0, c.s>>>(nc, c.cst.p, c.csrc.p, c.cdst.p, c.cghi.p, c.cglo.p, c.cv.p, c.role.p,
-                                      c.best.p);
-      CKL("k_dec_claim");
-      zero_cnt(c, K_UNDEC);
-      k_dec_decide<<<g, TPB, 0, c.s>>>(nc, c.cst.p, c.csrc.p, c.cdst.p, c.role.p, c.best.p, c.dcnt + K_UNDEC);
-      CKL("k_dec_decide");
-      k_dec_roles<<<g, TPB, 0, c.s>>>(nc, c.cst.p, c.csrc.p, c.cdst.p, c.role.p, c.best.p);
-      CKL("k_dec_roles");
-      ++rounds;
-    }
-    c.res.decouple_rounds += 2;
-    if (rd_cnt(c, K_UNDEC) == 0) break;
-    if (rounds > 4 * (int64_t)nc + 64) ldl_throw(LDL_E_INVALID, "internal: decoupling did not converge");
-  }
+  // many candidates: one cooperative launch of co-resident blocks runs all rounds
+  int dev = 0, sms = 0, per_sm = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dec_grid, TPB, 0));
+  const int g = std::max(1, std::min(grid_for(nc, TPB), sms * per_sm));
   zero_cnt(c, K_B);
-  k_dec_finish<<<g, TPB, 0, c.s>>>(nc, c.cst.p, c.cv.p, c.csrc.p, c.cdst.p, c.role.p, c.bv.p, c.bsrc.p, c.bdst.p,
-                                   c.dcnt + K_B);
-  CKL("k_dec_finish");
-  const int32_t nb = rd_cnt(c, K_B);
-  return {nc, nb, ex};
+  static_assert(K_TMP2 == K_TMP + 1, "adjacent counters");
+  int32_t ncv = nc;
+  int32_t* cst = c.cst.p;
+  const int32_t *cvp = c.cv.p, *srcp = c.csrc.p, *dstp = c.cdst.p;
+  const int64_t* ghi = c.cghi.p;
+  const uint64_t* glo = c.cglo.p;
+  int32_t *role = c.role.p, *best = c.best.p, *bv = c.bv.p, *bsrc = c.bsrc.p, *bdst = c.bdst.p;
+  int32_t* nbp = c.dcnt + K_B;
+  int32_t* undec = c.dcnt + K_TMP;  // K_TMP, K_TMP2: the two round counters
+  int32_t* stat = c.dcnt + K_UNDEC;
+  void* args[] = {&ncv, &cst, &cvp, &srcp, &dstp, &ghi, &glo, &role, &best, &bv, &bsrc, &bdst, &nbp, &undec, &stat};
+  CK(cudaLaunchCooperativeKernel((const void*)k_dec_grid, dim3(g), dim3(TPB), args, 0, c.s));
+  CKL("k_dec_grid");
+  int32_t fin[2];  // K_B, K_UNDEC
+  const HostRead rr{c.dcnt + K_B, fin, sizeof(fin)};
+  host_read(c, &rr, 1);
+  if (fin[1] < 0) ldl_throw(LDL_E_INVALID, "internal: decoupling did not converge");
+  c.res.decouple_rounds += fin[1];
+  return {nc, fin[0], ex};
 }
+
 
 CommitOut commit_move(ldl_ctx& c, int r, int32_t nb, int32_t epB, int32_t epT, int32_t epCh) {
   LevelState& L = c.lv[r];
