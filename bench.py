@@ -48,8 +48,8 @@ WORKLOAD = ("directed R-MAT (0.57,0.19,0.19,0.05), 2^20 vertices, 2^24 arcs, wei
 # workload, divided by the launches that had nodes to sweep: the bins are
 # launched unconditionally and an empty launch moves ~23 KB), valid only for
 # the sweep source it was taken with (sha256 of csrc/sweep.cu).
-NCU_TRAFFIC = {"sha256": "c7da0c04650a95e6e4c90a0d79408f3ef7480177226e23d2be92fd4fbb63f05b",
-               "bytes_per_launch": 56717792, "kernel": "sweep_block128"}
+NCU_TRAFFIC = {"sha256": "00db9d8b467953a69ab87626d5cbed559a4c6fb964ea7b3ff8f99189326148d6",
+               "bytes_per_launch": 56707328, "kernel": "sweep_block128"}
 
 
 def _set_rmat_scale(scale: int):
