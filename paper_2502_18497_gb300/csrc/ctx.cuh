@@ -84,7 +84,7 @@ struct ldl_ctx {
   DBuf<int32_t> ndx, ndx2;
   DBuf<int64_t> ndko, ndki, ndko2, ndki2;
   DBuf<u64> crk, crv, fk, trk, trv;
-  DBuf<int64_t> chunk_cnt, chunk_pre;
+  DBuf<int64_t> chunk_pre;
   DBuf<int64_t> hub_ecnt, hub_epre, pb_hi;
   DBuf<uint64_t> pb_lo;
   DBuf<int32_t> pb_c;

@@ -188,7 +188,7 @@ static void free_all(ldl_ctx& c) {
   for (auto& L : c.lv) L.release();
   DBuf<int64_t>* b64[] = {&c.Kout, &c.Kin, &c.e, &c.cghi, &c.snapKo, &c.snapKi, &c.snapE, &c.binLoff, &c.binLsz,
                           &c.gvals, &c.rsum, &c.rsum2, &c.ndko, &c.ndki, &c.ndko2, &c.ndki2,
-                          &c.chunk_cnt, &c.chunk_pre, &c.hub_ecnt, &c.hub_epre, &c.pb_hi};
+                          &c.chunk_pre, &c.hub_ecnt, &c.hub_epre, &c.pb_hi};
   for (auto* b : b64) b->release();
   DBuf<int32_t>* b32[] = {&c.stS, &c.stU, &c.stMv, &c.stB, &c.stM0, &c.stD, &c.stC, &c.stR, &c.stX, &c.stT,
                           &c.stE, &c.stCh, &c.lU, &c.lS, &c.lUstar, &c.lMv, &c.lM0, &c.lD, &c.lC, &c.lR,

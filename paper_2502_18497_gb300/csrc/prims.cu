@@ -33,16 +33,40 @@ __device__ inline int64_t block_excl_scan_i64(int64_t v, int64_t* total) {
   return before + x - v;
 }
 
-// whole input in one tile: scan and total in one launch
+// Scan inputs: an array, or the chunk count of each node of a list
+// (chunks.cuh: ceil(len / chunk) per row, at least 1 per listed node, 0 past
+// the list's device-side count).
 template <class T>
-__global__ void k_scan_one(const T* in, int64_t* out, int64_t n, const int64_t* n_dev, int64_t* total) {
+struct ArrayIn {
+  const T* p;
+  __device__ int64_t operator()(int64_t i) const { return (int64_t)p[i]; }
+};
+
+struct ChunkCountIn {
+  const int32_t* list;
+  const int32_t* nlist;
+  int64_t n_hint;
+  const int32_t* la;
+  const int32_t* lb;
+  int32_t chunk;
+  __device__ int64_t operator()(int64_t i) const {
+    if (i >= n_hint || i >= *nlist) return 0;
+    const int32_t v = list[i];
+    const int64_t c = (la[v] + chunk - 1) / chunk + (lb ? (lb[v] + chunk - 1) / chunk : 0);
+    return c > 0 ? c : 1;
+  }
+};
+
+// whole input in one tile: scan and total in one launch
+template <class In>
+__global__ void k_scan_one(In in, int64_t* out, int64_t n, const int64_t* n_dev, int64_t* total) {
   if (n_dev) n += *n_dev;
   const int64_t base = (int64_t)threadIdx.x * SC_ITEMS;
   int64_t loc[SC_ITEMS];
   int64_t s = 0;
   for (int k = 0; k < SC_ITEMS; ++k) {
     int64_t i = base + k;
-    loc[k] = i < n ? (int64_t)in[i] : 0;
+    loc[k] = i < n ? in(i) : 0;
     s += loc[k];
   }
   int64_t tot;
@@ -67,8 +91,8 @@ constexpr int LB_ITEMS = 8;
 constexpr int LB_TILE = SC_THREADS * LB_ITEMS;
 constexpr uint32_t LB_SPINS = 1u << 20;
 
-template <class T>
-__global__ void __launch_bounds__(SC_THREADS) k_scan_lb(const T* in, int64_t* out, int64_t n, const int64_t* n_dev,
+template <class In>
+__global__ void __launch_bounds__(SC_THREADS) k_scan_lb(In in, int64_t* out, int64_t n, const int64_t* n_dev,
                                                         u64* st, int32_t* ctr, uint32_t ep, int64_t* total,
                                                         int32_t* err) {
   __shared__ int64_t s_tile, s_pre;
@@ -82,7 +106,7 @@ __global__ void __launch_bounds__(SC_THREADS) k_scan_lb(const T* in, int64_t* ou
   int64_t sum = 0;
   for (int k = 0; k < LB_ITEMS; ++k) {
     const int64_t i = base + k;
-    loc[k] = i < n ? (int64_t)in[i] : 0;
+    loc[k] = i < n ? in(i) : 0;
     sum += loc[k];
   }
   int64_t agg;
@@ -417,17 +441,17 @@ static uint32_t lb_begin(Prims& P, int64_t n, cudaStream_t s) {
 
 // n items, or (n_dev != nullptr) *n_dev + n items with n_max an upper bound;
 // the total goes to total_dev (device) when given.
-template <class T>
-static void scan_launch(const T* in, int64_t* out, int64_t n, const int64_t* n_dev, int64_t n_max, int64_t* total_dev,
+template <class In>
+static void scan_launch(In in, int64_t* out, int64_t n, const int64_t* n_dev, int64_t n_max, int64_t* total_dev,
                         Prims& P, cudaStream_t s) {
   if (n_max <= SC_TILE) {
-    k_scan_one<T><<<1, SC_THREADS, 0, s>>>(in, out, n, n_dev, total_dev);
+    k_scan_one<In><<<1, SC_THREADS, 0, s>>>(in, out, n, n_dev, total_dev);
     CKL("k_scan_one");
   } else {
     const uint32_t ep = lb_begin(P, n_max, s);
     const int64_t tiles = (n_max + LB_TILE - 1) / LB_TILE;
-    k_scan_lb<T><<<(unsigned)tiles, SC_THREADS, 0, s>>>(in, out, n, n_dev, P.lb_st.p, P.lb_ctl.p + ep, ep, total_dev,
-                                                        P.lb_ctl.p + 256);
+    k_scan_lb<In><<<(unsigned)tiles, SC_THREADS, 0, s>>>(in, out, n, n_dev, P.lb_st.p, P.lb_ctl.p + ep, ep,
+                                                         total_dev, P.lb_ctl.p + 256);
     CKL("k_scan_lb");
   }
 }
@@ -436,7 +460,7 @@ template <class T>
 static int64_t scan_t(const T* in, int64_t* out, int64_t n, Prims& P, cudaStream_t s, bool want_total) {
   if (n <= 0) return 0;
   P.bsum.reserve(2, s);
-  scan_launch<T>(in, out, n, nullptr, n, P.bsum.p + 1, P, s);
+  scan_launch(ArrayIn<T>{in}, out, n, nullptr, n, P.bsum.p + 1, P, s);
   if (!want_total) return -1;
   int64_t tot = 0;
   const HostRead r{P.bsum.p + 1, &tot, sizeof(int64_t)};
@@ -455,13 +479,18 @@ int64_t scan_exclusive_i32(const int32_t* in, int64_t* out, int64_t n, Prims& P,
 void scan_exclusive_to(const int64_t* in, int64_t* out, int64_t n, const int64_t* n_dev, int64_t n_max,
                        int64_t* total_dev, Prims& P, cudaStream_t s) {
   if (n_max <= 0) return;
-  scan_launch<int64_t>(in, out, n, n_dev, n_max, total_dev, P, s);
+  scan_launch(ArrayIn<int64_t>{in}, out, n, n_dev, n_max, total_dev, P, s);
 }
 
 void scan_exclusive_i32_to(const int32_t* in, int64_t* out, int64_t n, const int64_t* n_dev, int64_t n_max,
                            int64_t* total_dev, Prims& P, cudaStream_t s) {
   if (n_max <= 0) return;
-  scan_launch<int32_t>(in, out, n, n_dev, n_max, total_dev, P, s);
+  scan_launch(ArrayIn<int32_t>{in}, out, n, n_dev, n_max, total_dev, P, s);
+}
+
+void scan_chunk_counts(const int32_t* list, const int32_t* nlist, int64_t n_hint, const int32_t* la,
+                       const int32_t* lb, int32_t chunk, int64_t* out, Prims& P, cudaStream_t s) {
+  scan_launch(ChunkCountIn{list, nlist, n_hint, la, lb, chunk}, out, n_hint + 1, nullptr, n_hint + 1, nullptr, P, s);
 }
 
 int32_t* scan_error_flag(Prims& P) { return P.lb_ctl.cap ? P.lb_ctl.p + 256 : nullptr; }
@@ -480,7 +509,7 @@ bool scan_wait_gives_up(cudaStream_t s) {
     const uint32_t ep = lb_begin(P, n, s);
     const int32_t one = 1;
     CK(cudaMemcpyAsync(P.lb_ctl.p + ep, &one, sizeof(int32_t), cudaMemcpyHostToDevice, s));
-    k_scan_lb<int64_t><<<1, SC_THREADS, 0, s>>>(in, out, n, nullptr, P.lb_st.p, P.lb_ctl.p + ep, ep, out + n,
+    k_scan_lb<ArrayIn<int64_t>><<<1, SC_THREADS, 0, s>>>(ArrayIn<int64_t>{in}, out, n, nullptr, P.lb_st.p, P.lb_ctl.p + ep, ep, out + n,
                                                 P.lb_ctl.p + 256);
     CKL("k_scan_lb");
     CK(cudaMemcpyAsync(&bad, P.lb_ctl.p + 256, sizeof(int32_t), cudaMemcpyDeviceToHost, s));

@@ -36,6 +36,11 @@ void scan_exclusive_to(const int64_t* in, int64_t* out, int64_t n, const int64_t
                        int64_t* total_dev, Prims& P, cudaStream_t s);
 void scan_exclusive_i32_to(const int32_t* in, int64_t* out, int64_t n, const int64_t* n_dev, int64_t n_max,
                            int64_t* total_dev, Prims& P, cudaStream_t s);
+// Exclusive scan (n_hint + 1 entries) of the chunk counts of the listed nodes:
+// entry i < *nlist is ceil(la[v] / chunk) + ceil(lb[v] / chunk) for v =
+// list[i] (at least 1), later entries 0.  No host read.
+void scan_chunk_counts(const int32_t* list, const int32_t* nlist, int64_t n_hint, const int32_t* la,
+                       const int32_t* lb, int32_t chunk, int64_t* out, Prims& P, cudaStream_t s);
 // Device flag set when a scan's bounded look-back wait gave up (nullptr
 // before the first multi-tile scan).
 int32_t* scan_error_flag(Prims& P);
