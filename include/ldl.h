@@ -19,9 +19,12 @@
  *   - Undirected graphs are symmetric weight matrices: an edge {i, j} is the
  *     two arcs (i, j) and (j, i); a self-loop is one arc.  m = sum_ij w_ij.
  *   - Level-0 weights are int32 >= 1; aggregate weights and all totals int64.
- *   - Every entry point returns an ldl_status; LDL_OK is 0.  On any error the
- *     state is left exactly as it was before the call (a batch is atomic) and
- *     ldl_last_error() describes the failure.
+ *   - Every entry point returns an ldl_status; LDL_OK is 0, and
+ *     ldl_last_error() describes a failure.  A batch rejected by validation
+ *     (RANGE, INVALID, NEG_WEIGHT, NO_EDGE, OVERFLOW) leaves the state exactly
+ *     as it was before the call; NOMEM, CUDA or TIMEOUT in the middle of a
+ *     batch may leave it partly updated, and the context should then be
+ *     destroyed.
  *   - Pointers marked "host" are read or written with ordinary host access;
  *     "device" pointers are GPU global memory of the context's device.
  *   - The context owns all device state.  Pointers it returns stay valid until

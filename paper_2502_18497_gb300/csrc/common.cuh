@@ -224,22 +224,6 @@ __device__ inline void warp_append(bool want, int32_t x, int32_t* list, int32_t*
   if (want) list[base + __popc(m & ((1u << lane) - 1u))] = x;
 }
 
-// Same for (key, value) records.
-__device__ inline void warp_append_rec(bool want, uint64_t k, uint64_t v, uint64_t* rk, uint64_t* rv, int32_t* count) {
-  const unsigned m = __ballot_sync(0xffffffffu, want);
-  if (!m) return;
-  const int lane = threadIdx.x & 31;
-  const int leader = __ffs(m) - 1;
-  int32_t base = 0;
-  if (lane == leader) base = atomicAdd(count, __popc(m));
-  base = __shfl_sync(0xffffffffu, base, leader);
-  if (want) {
-    const int32_t p = base + __popc(m & ((1u << lane) - 1u));
-    rk[p] = k;
-    rv[p] = v;
-  }
-}
-
 // Claims x for the set with epoch ep (true only for the first claimer).
 __device__ inline bool stamp_claim(int32_t* stamp, int32_t ep, int32_t x) {
   if (stamp[x] == ep) return false;

@@ -581,9 +581,6 @@ __global__ void k_alive_list(const uint8_t* alive, int64_t n, int32_t* l, int32_
   }
 }
 
-__global__ void k_all_alive(const int32_t* cnt, int64_t n, uint8_t* alive) {
-  GRID_STRIDE(i, n) alive[i] = cnt[i] > 0 ? 1 : 0;
-}
 
 __global__ void k_esum(const int64_t* e, const int64_t* Kout, const int64_t* Kin, int64_t n, int64_t* E, I128* P) {
   int64_t se = 0;
