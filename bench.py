@@ -48,8 +48,8 @@ WORKLOAD = ("directed R-MAT (0.57,0.19,0.19,0.05), 2^20 vertices, 2^24 arcs, wei
 # workload, divided by the launches that had nodes to sweep: the bins are
 # launched unconditionally and an empty launch moves ~23 KB), valid only for
 # the sweep source it was taken with (sha256 of csrc/sweep.cu).
-NCU_TRAFFIC = {"sha256": "00db9d8b467953a69ab87626d5cbed559a4c6fb964ea7b3ff8f99189326148d6",
-               "bytes_per_launch": 56707328, "kernel": "sweep_block128"}
+NCU_TRAFFIC = {"sha256": "2f7b304250d5ee67e235df5506332dcec7b8be9280adb15f01daba8fca323b4d",
+               "bytes_per_launch": 56684176, "kernel": "sweep_block128"}
 
 
 def _set_rmat_scale(scale: int):
@@ -396,6 +396,24 @@ def run_powerlaw(args):
     print(json.dumps(line), flush=True)
 
 
+def run_autotune(args):
+    """Coordinate-descent tuning of the sweep scheduling knobs on the R-MAT
+    stream (each candidate re-checked to give the same partition); prints the
+    best knobs and every candidate's time per batch."""
+    import torch
+    from paper_2502_18497_gb300.autotune import tune
+    g, batches = _workload(args.steps)
+    torch.cuda.synchronize()
+    res = tune(g, batches, cache=args.autotune_cache, key=f"rmat{SCALE}_b{BATCH}")
+    line = {"metric": "updates/s", "value": BATCH / (res["ms_per_batch"] / 1e3), "unit": "updates/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": 0, "ms_per_step": res["ms_per_batch"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic", "form": "autotune",
+            "config": {"workload": WORKLOAD}, "best": {"bin_deg": res["bin_deg"],
+                                                       "cluster_max_deg": res["cluster_max_deg"]},
+            "default_ms_per_batch": res["default_ms_per_batch"], "candidates": res["candidates"]}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -406,7 +424,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--ref-budget", type=float, default=120.0, help="seconds of oracle batches (reference arm)")
     ap.add_argument("--stage-times", action="store_true", help="per-stage device times (adds syncs)")
-    ap.add_argument("--workload", default="rmat", choices=["rmat", "batched", "served", "powerlaw"])
+    ap.add_argument("--workload", default="rmat", choices=["rmat", "batched", "served", "powerlaw", "autotune"])
+    ap.add_argument("--autotune-cache", default=None, help="autotune: JSON file the result is merged into")
     ap.add_argument("--scale", type=int, default=24, help="powerlaw: log2 of the vertex count")
     ap.add_argument("--graphs", type=int, default=512, help="batched form: number of graphs")
     ap.add_argument("--threads", type=int, default=16, help="batched/served: host worker threads")
@@ -425,6 +444,8 @@ def main():
         return run_served(args)
     if args.workload == "powerlaw":
         return run_powerlaw(args)
+    if args.workload == "autotune":
+        return run_autotune(args)
 
     import torch
     ws, rank, local = _dist()

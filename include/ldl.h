@@ -80,6 +80,14 @@ typedef struct {
    * start, so that they cover the static build inside ldl_create; 0 (the
    * default): off until ldl_set_kernel_stats. */
   int32_t kernel_stats;
+  /* Degree bins of the sweeps (no effect on results): a node with d
+   * adjacency entries (out + in) goes to 8-lane groups if d <= bin_deg[0],
+   * one warp if d <= bin_deg[1], a 128-thread block if d <= bin_deg[2], a
+   * 256-thread block if d <= bin_deg[3], else to the cluster / hub paths.
+   * 0 keeps an entry's default (24, 96, 1024, 2048); the bounds must not
+   * decrease and must not exceed (32, 128, 1024, 2048), the largest degrees
+   * whose hash tables stay at most half full (LDL_E_INVALID otherwise). */
+  int32_t bin_deg[4];
   void* cuda_stream;
 } ldl_params;
 

@@ -1,0 +1,91 @@
+"""Autotuner for the sweep scheduling knobs: the degree-bin bounds
+(``bin_deg``) and the rows given to thread-block clusters
+(``cluster_max_deg``).
+
+No knob changes a result, so every candidate must reproduce the first
+candidate's labels bit for bit (checked; a mismatch raises).  A candidate
+builds its own context from the same snapshot, applies the same batches from
+device memory and is timed with CUDA events.  The search is a coordinate
+descent from the library's defaults: each knob in turn takes the value of its
+list that is fastest with the others held at the best so far.  With
+``cache`` the result is merged into a JSON file under ``key``.
+"""
+import json
+import os
+
+import numpy as np
+
+DEFAULT_BINS = (24, 96, 1024, 2048)
+# values tried per knob (each bin bound within the library's limits 32, 128,
+# 1024, 2048 and not below the bound before it)
+SEARCH = {
+    "bin0": (16, 24, 32),
+    "bin1": (64, 96, 128),
+    "bin2": (256, 384, 1024),
+    "bin3": (1024, 2048),
+    "cluster_max_deg": (0, 8192),
+}
+
+
+def _valid(bins):
+    return all(bins[i] <= bins[i + 1] for i in range(3))
+
+
+def tune(g, batches, cache=None, key=None, search=None):
+    import torch
+    from .ldl import LDL
+
+    search = search or SEARCH
+    dev = [torch.from_numpy(np.ascontiguousarray(b)).cuda() for b in batches]
+    seen = {}
+    ref = [None]
+
+    def run(bins, cl):
+        k = (tuple(bins), cl)
+        if k in seen:
+            return seen[k]
+        d = LDL.from_graph(g, bin_deg=bins, cluster_max_deg=cl)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for b in dev:
+            d.apply(b, on_device=True)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / max(len(dev), 1)
+        labels = np.asarray(d.labels()).copy()
+        d.close()
+        if ref[0] is None:
+            ref[0] = labels
+        elif not np.array_equal(ref[0], labels):
+            raise RuntimeError(f"scheduling knobs {k} changed the partition")
+        seen[k] = ms
+        return ms
+
+    best_bins, best_cl = list(DEFAULT_BINS), 0
+    best_ms = run(best_bins, best_cl)
+    for name, values in search.items():
+        for val in values:
+            bins, cl = list(best_bins), best_cl
+            if name == "cluster_max_deg":
+                cl = val
+            else:
+                bins[int(name[3:])] = val
+            if not _valid(bins):
+                continue
+            ms = run(bins, cl)
+            if ms < best_ms:
+                best_bins, best_cl, best_ms = bins, cl, ms
+    out = {"bin_deg": best_bins, "cluster_max_deg": best_cl, "ms_per_batch": best_ms,
+           "default_ms_per_batch": seen[(DEFAULT_BINS, 0)],
+           "candidates": [{"bin_deg": list(k[0]), "cluster_max_deg": k[1], "ms_per_batch": v}
+                          for k, v in seen.items()]}
+    if cache:
+        data = {}
+        if os.path.exists(cache):
+            with open(cache) as f:
+                data = json.load(f)
+        data[key or "default"] = out
+        with open(cache, "w") as f:
+            json.dump(data, f, indent=1)
+    return out

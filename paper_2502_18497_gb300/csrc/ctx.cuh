@@ -46,6 +46,7 @@ struct ldl_ctx {
   ldl_params prm{};
   int64_t n = 0;
   int directed = 0;
+  int32_t bin_deg[4] = {0, 0, 0, 0};  // resolved sweep degree bins
   int bits = 1;          // bits to hold a node id
   int T = 0;             // top level
   cudaStream_t s = 0;

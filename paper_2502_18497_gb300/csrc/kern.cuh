@@ -9,6 +9,13 @@ struct CommitOut {
   int32_t ntc; // touched communities
 };
 
+// Degree bins of the sweeps: a node with d adjacency entries goes to the
+// first bin whose bound is >= d (8-lane groups, warps, 128-thread blocks,
+// 256-thread blocks; beyond: clusters / hub path).  Default bounds, and the
+// largest bound each bin's hash table allows while staying at most half full.
+constexpr int32_t BIN_DEFAULT[4] = {24, 96, 1024, 2048};
+constexpr int32_t BIN_MAX[4] = {32, 128, 1024, 2048};
+
 // ---- sweep.cu
 void expand_set(ldl_ctx& c, int r, const int32_t* list, int idx_n, int32_t* stamp, int32_t ep, int32_t* olist,
                 int idx_out, int64_t n_hint);

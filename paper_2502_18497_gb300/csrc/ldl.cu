@@ -494,6 +494,14 @@ ldl_status ldl_create(const ldl_params* params, int64_t n, int64_t nnz, const in
     g_create_err = "invalid size or parameter";
     return LDL_E_INVALID;
   }
+  int32_t bins[4];
+  for (int i = 0; i < 4; ++i) {
+    bins[i] = p.bin_deg[i] ? p.bin_deg[i] : BIN_DEFAULT[i];
+    if (bins[i] < 0 || bins[i] > BIN_MAX[i] || (i > 0 && bins[i] < bins[i - 1])) {
+      g_create_err = "invalid sweep degree bins";
+      return LDL_E_INVALID;
+    }
+  }
   if (row_ptr[0] != 0 || row_ptr[n] != nnz) {
     g_create_err = "row_ptr must start at 0 and end at nnz";
     return LDL_E_INVALID;
@@ -521,6 +529,7 @@ ldl_status ldl_create(const ldl_params* params, int64_t n, int64_t nnz, const in
     CK(cudaEventCreate(&c->ev3));
     c->lv.resize(p.L + 1);
     c->kstats = p.kernel_stats ? 1 : 0;
+    for (int i = 0; i < 4; ++i) c->bin_deg[i] = bins[i];
     alloc_globals(*c);
     level_alloc(*c, 0);
     upload_graph(*c, nnz, row_ptr, col, w);

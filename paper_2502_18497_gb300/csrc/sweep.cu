@@ -14,14 +14,15 @@ namespace {
 
 constexpr int TPB = 256;
 constexpr int HW = 256;      // per-warp hash slots (small bin)
-constexpr int TINY_DEG = 24;   // groups of 8 lanes, 64 slots
-constexpr int SMALL_DEG = 96;  // one warp, 256 slots
 constexpr int HB = 4096;     // per-block hash slots (upper mid bin)
-constexpr int MID1_DEG = 1024;  // lower mid bin: 128 threads, 2048 slots
-constexpr int MID_DEG = 2048;
+constexpr int MID_DEG = 2048;   // rows above it: clusters (optional) or the hub path
 constexpr int CL = 8;             // blocks per cluster (hub rows up to CLUSTER_DEG entries)
 constexpr int CL_SLOTS = 8192;    // hash slots per block of a cluster (96 KB of shared memory)
 constexpr int CLUSTER_DEG = CL * CL_SLOTS / 2;  // upper limit of cluster_max_deg
+// the bin bounds a context may use keep every table at most half full
+static_assert(BIN_MAX[0] == HW * 8 / 32 / 2 && BIN_MAX[1] == HW / 2 && BIN_MAX[2] == 2048 / 2 &&
+                  BIN_MAX[3] == HB / 2 && BIN_MAX[3] == MID_DEG,
+              "bin bounds and table sizes");
 constexpr int EVAL_CH = 4096;  // hub table slots evaluated per block
 
 // ---------------------------------------------------------------- expand
@@ -348,7 +349,8 @@ template <class WT>
 __global__ void k_bin(Adj<WT> out, Adj<WT> in, int directed, const int32_t* list, const int32_t* nlist,
                       int32_t* bt, int32_t* nt, int32_t* bs, int32_t* ns, int32_t* bm, int32_t* nm, int32_t* bm2,
                       int32_t* nm2, int32_t* bc, int32_t* nc, int32_t* bl, int32_t* nlarge, int64_t* lsz,
-                      int64_t* tabtop, int32_t cluster_max) {
+                      int64_t* tabtop, int32_t t0, int32_t t1, int32_t t2, int32_t t3,
+                      int32_t cluster_max) {
   const int32_t nl = *nlist;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   // warp-uniform trip count so that the appends can be warp-aggregated
@@ -360,7 +362,7 @@ __global__ void k_bin(Adj<WT> out, Adj<WT> in, int directed, const int32_t* list
     if (t < nl) {
       v = list[t];
       d = (int64_t)out.len[v] + (directed ? in.len[v] : 0);
-      bin = d <= TINY_DEG ? 0 : d <= SMALL_DEG ? 1 : d <= MID1_DEG ? 2 : d <= MID_DEG ? 3 : d <= cluster_max ? 4 : 5;
+      bin = d <= t0 ? 0 : d <= t1 ? 1 : d <= t2 ? 2 : d <= t3 ? 3 : d <= cluster_max ? 4 : 5;
     }
     warp_append(bin == 0, v, bt, nt);
     warp_append(bin == 1, v, bs, ns);
@@ -1127,7 +1129,8 @@ static void sweep_t(ldl_ctx& c, int r, Adj<WT> out, Adj<WT> in, const int32_t* l
                                                      c.dcnt + K_TINY, c.binS.p, c.dcnt + K_SMALL, c.binM.p,
                                                      c.dcnt + K_MID, c.binM2.p, c.dcnt + K_MID2, c.binC.p,
                                                      c.dcnt + K_CLU, c.binL.p, c.dcnt + K_LARGE, c.binLsz.p,
-                                                     &c.d_sc->need, std::min(c.prm.cluster_max_deg, CLUSTER_DEG));
+                                                     &c.d_sc->need, c.bin_deg[0], c.bin_deg[1], c.bin_deg[2],
+                                                     c.bin_deg[3], std::min(c.prm.cluster_max_deg, CLUSTER_DEG));
   CKL("k_bin");
   // Every bin but the hubs is swept by a grid-stride kernel that reads its
   // bin's count on the device, so these launch before the counts come back
@@ -1156,7 +1159,7 @@ static void sweep_t(ldl_ctx& c, int r, Adj<WT> out, Adj<WT> in, const int32_t* l
     CKL("k_sweep_block(mid2)");
   }
   if (kev) CK(cudaEventRecord(kev[4], c.s));
-  if (c.prm.cluster_max_deg > MID_DEG) {
+  if (c.prm.cluster_max_deg > c.bin_deg[3]) {
     const size_t sm = (sizeof(int64_t) + sizeof(int32_t)) * CL_SLOTS;
     CK(cudaFuncSetAttribute(k_sweep_cluster<WT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     const int ncl = (int)std::min<int64_t>(n_hint, 152 * 2 / CL);

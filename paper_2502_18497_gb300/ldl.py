@@ -29,7 +29,7 @@ class ldl_params(C.Structure):
     _fields_ = [("directed", C.c_int32), ("gamma_num", C.c_int32), ("gamma_den", C.c_int32),
                 ("N", C.c_int32), ("L", C.c_int32), ("M", C.c_int32), ("M_static", C.c_int32),
                 ("alpha_inv", C.c_int32), ("beta_inv", C.c_int32), ("cluster_max_deg", C.c_int32),
-                ("kernel_stats", C.c_int32), ("cuda_stream", C.c_void_p)]
+                ("kernel_stats", C.c_int32), ("bin_deg", C.c_int32 * 4), ("cuda_stream", C.c_void_p)]
 
 
 class ldl_result(C.Structure):
@@ -133,7 +133,7 @@ class Level:
 
 
 def make_params(directed=False, gamma_num=1, gamma_den=1, N=2, L=4, M=5, M_static=20, alpha_inv=1000,
-                beta_inv=100, stream=None, cluster_max_deg=0, kernel_stats=0) -> ldl_params:
+                beta_inv=100, stream=None, cluster_max_deg=0, kernel_stats=0, bin_deg=None) -> ldl_params:
     p = ldl_params()
     load().ldl_default_params(C.byref(p))
     p.directed, p.gamma_num, p.gamma_den = int(directed), gamma_num, gamma_den
@@ -141,6 +141,9 @@ def make_params(directed=False, gamma_num=1, gamma_den=1, N=2, L=4, M=5, M_stati
     p.alpha_inv, p.beta_inv = alpha_inv, beta_inv
     p.cluster_max_deg = cluster_max_deg
     p.kernel_stats = kernel_stats
+    if bin_deg is not None:
+        for i, t in enumerate(bin_deg):
+            p.bin_deg[i] = int(t)
     p.cuda_stream = stream
     return p
 
@@ -158,10 +161,10 @@ class LDL:
 
     def __init__(self, n, row_ptr, col, w, directed=False, gamma_num=1, gamma_den=1, N=2, L=4, M=5,
                  M_static=20, alpha_inv=1000, beta_inv=100, stream=None, server=None, cluster_max_deg=0,
-                 kernel_stats=0):
+                 kernel_stats=0, bin_deg=None):
         lib = load()
         p = make_params(directed, gamma_num, gamma_den, N, L, M, M_static, alpha_inv, beta_inv, stream,
-                        cluster_max_deg, kernel_stats)
+                        cluster_max_deg, kernel_stats, bin_deg)
         self.n = int(n)
         self.directed = bool(directed)
         rp = np.ascontiguousarray(row_ptr, dtype=np.int64)

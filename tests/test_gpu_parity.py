@@ -81,14 +81,15 @@ def test_planted_partition_full(ldl):
         assert np.array_equal(o.labels(), np.asarray(d.labels()))
 
 
-@pytest.mark.parametrize("cluster_max_deg", [0, 32768])
-def test_rmat_directed_reduced(ldl, cluster_max_deg):
+@pytest.mark.parametrize("cluster_max_deg,bin_deg", [(0, None), (32768, None), (0, (16, 64, 256, 1024))])
+def test_rmat_directed_reduced(ldl, cluster_max_deg, bin_deg):
     """Directed R-MAT with the paper-stream skew at 2^14 vertices / 2^18 arcs,
     20 batches of 1,000 arc updates (80% inserts, 20% deletes); rows above
-    2048 entries swept by the whole-GPU hub path or by block clusters."""
+    2048 entries swept by the whole-GPU hub path or by block clusters, and
+    non-default degree bins (scheduling only: the result must not change)."""
     g = rmat_directed(scale=14, arcs=1 << 18, seed=12)
     o = Oracle(g)
-    d = ldl.LDL.from_graph(g, cluster_max_deg=cluster_max_deg)
+    d = ldl.LDL.from_graph(g, cluster_max_deg=cluster_max_deg, bin_deg=bin_deg)
     _assert_same(o, d, "create", adjacency=False)
     d.set_kernel_stats(True)
     for t, b in enumerate(rmat_stream(g, batches=20, size=1000, seed=12)):
