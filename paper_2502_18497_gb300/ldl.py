@@ -14,7 +14,7 @@ from typing import Optional
 
 import numpy as np
 
-from .build import LIB, build
+from .build import build
 
 LDL_OK, LDL_E_INVALID, LDL_E_RANGE, LDL_E_NO_EDGE, LDL_E_NEG_WEIGHT, LDL_E_NOMEM, LDL_E_CUDA, \
     LDL_E_TIMEOUT, LDL_E_OVERFLOW = range(9)

@@ -8,7 +8,6 @@ form) or submitted interleaved from several producer threads (served form).
 import ctypes
 import threading
 
-import numpy as np
 import pytest
 
 from oracle import Oracle
