@@ -31,19 +31,43 @@ def _valid(bins):
     return all(bins[i] <= bins[i + 1] for i in range(3))
 
 
+def coordinate_descent(run, search=None, defaults=DEFAULT_BINS):
+    """Pure search: run(bins, cluster_max_deg) -> ms (cached per setting).
+    Returns (best_bins, best_cluster_max_deg, best_ms, {setting: ms})."""
+    search = search or SEARCH
+    seen = {}
+
+    def once(bins, cl):
+        k = (tuple(bins), cl)
+        if k not in seen:
+            seen[k] = run(list(bins), cl)
+        return seen[k]
+
+    best_bins, best_cl = list(defaults), 0
+    best_ms = once(best_bins, best_cl)
+    for name, values in search.items():
+        for val in values:
+            bins, cl = list(best_bins), best_cl
+            if name == "cluster_max_deg":
+                cl = val
+            else:
+                bins[int(name[3:])] = val
+            if not _valid(bins):
+                continue
+            ms = once(bins, cl)
+            if ms < best_ms:
+                best_bins, best_cl, best_ms = bins, cl, ms
+    return best_bins, best_cl, best_ms, seen
+
+
 def tune(g, batches, cache=None, key=None, search=None):
     import torch
     from .ldl import LDL
 
-    search = search or SEARCH
     dev = [torch.from_numpy(np.ascontiguousarray(b)).cuda() for b in batches]
-    seen = {}
     ref = [None]
 
     def run(bins, cl):
-        k = (tuple(bins), cl)
-        if k in seen:
-            return seen[k]
         d = LDL.from_graph(g, bin_deg=bins, cluster_max_deg=cl)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -58,24 +82,10 @@ def tune(g, batches, cache=None, key=None, search=None):
         if ref[0] is None:
             ref[0] = labels
         elif not np.array_equal(ref[0], labels):
-            raise RuntimeError(f"scheduling knobs {k} changed the partition")
-        seen[k] = ms
+            raise RuntimeError(f"scheduling knobs {bins}, {cl} changed the partition")
         return ms
 
-    best_bins, best_cl = list(DEFAULT_BINS), 0
-    best_ms = run(best_bins, best_cl)
-    for name, values in search.items():
-        for val in values:
-            bins, cl = list(best_bins), best_cl
-            if name == "cluster_max_deg":
-                cl = val
-            else:
-                bins[int(name[3:])] = val
-            if not _valid(bins):
-                continue
-            ms = run(bins, cl)
-            if ms < best_ms:
-                best_bins, best_cl, best_ms = bins, cl, ms
+    best_bins, best_cl, best_ms, seen = coordinate_descent(run, search)
     out = {"bin_deg": best_bins, "cluster_max_deg": best_cl, "ms_per_batch": best_ms,
            "default_ms_per_batch": seen[(DEFAULT_BINS, 0)],
            "candidates": [{"bin_deg": list(k[0]), "cluster_max_deg": k[1], "ms_per_batch": v}
