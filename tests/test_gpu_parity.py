@@ -174,3 +174,19 @@ def test_bounded_scan_wait_reports_timeout(ldl):
     g = planted_partition(n=1000, block=50, seed=8)
     o, d = _pair(ldl, g)
     _assert_same(o, d, "create after the timeout check")
+
+
+def test_hand_derived_fixtures(ldl):
+    """The CUDA path on the hand-derived fixtures of tests/golden/: partition
+    and exact Eq. 1 numerator after creation and after each batch."""
+    from tests.golden_io import blocks_of, cases, load, q_matches
+    for name in cases():
+        g, batches, expect = load(name)
+        d = ldl.LDL.from_graph(g)
+        for t in range(len(expect)):
+            if t:
+                d.apply(batches[t - 1])
+            blocks, q = expect[t]
+            assert blocks_of(d.labels()) == blocks, name
+            m, qnum = d.numerator()
+            assert q_matches(m, qnum, q), (name, t, m, qnum, q)
