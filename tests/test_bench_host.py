@@ -30,3 +30,24 @@ def test_roofline_of_idle_kernels_is_zero():
 def test_traffic_guard_names_a_known_group():
     t = bench.NCU_TRAFFIC
     assert t["kernel"] in bench.SWEEP_KERNELS and t["bytes_per_launch"] > 0 and len(t["sha256"]) == 64
+
+
+def test_reference_arm_prints_its_contract_line():
+    """`bench.py --impl reference` (the oracle on the host) on a tiny stream:
+    one JSON line with the reference arm's keys."""
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--rmat-scale", "12",
+                          "--steps", "2", "--warmup", "0", "--ref-budget", "5"],
+                         capture_output=True, text=True, timeout=600, cwd=root)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == "updates/s" and d["value"] > 0
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert d["higher_is_better"] is True and d["vs_baseline"] is None
