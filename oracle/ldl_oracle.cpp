@@ -52,6 +52,10 @@
 //
 // Pins (tests/test_oracle_*.py): Eq. 1 against an O(n^2) brute-force double
 // sum; the gain against brute-force recomputed modularity for every (v, b);
+// the target and gain that best_move and best_ref choose (the functions the
+// loops call, run on one node) against an exhaustive argmax of brute-force
+// numerator changes over the admissible targets (positive gains only,
+// adjacent targets only, lowest id on ties; gamma 1 and 3/2);
 // the decoupling filter against its defining greedy property; the repaired
 // hierarchy against a from-scratch Eq. 3 rebuild after every batch; delete
 // then re-insert restoring every statistic; undirected == symmetric directed;
@@ -1084,6 +1088,62 @@ void orc_gain(void* h, int32_t r, int32_t v, int32_t b, int64_t* g_hi, uint64_t*
            (i128)o->gn * ((i128)ko * (o->Kin[b] - o->Kin[a] + ki) + (i128)ki * (o->Kout[b] - o->Kout[a] + ko));
   *g_hi = (int64_t)(g >> 64);
   *g_lo = (uint64_t)g;
+}
+
+// BestMove of the single node v at level r, computed by the same best_move
+// the move loop calls (the search counters are left as they were).  Returns 1
+// with the chosen target community and its exact gain, or 0 when v has no
+// adjacent community with a positive gain (or is not alive).
+int32_t orc_best_move(void* h, int32_t r, int32_t v, int32_t* target, int64_t* g_hi, uint64_t* g_lo) {
+  Orc* o = (Orc*)h;
+  if (r < 0 || r > o->T || v < 0 || v >= o->n) return -1;
+  const Counters keep = o->ctr;
+  std::vector<Cand> c = o->best_move(r, std::vector<int32_t>{v});
+  o->ctr = keep;
+  if (c.empty()) return 0;
+  *target = c[0].dst;
+  *g_hi = (int64_t)(c[0].g >> 64);
+  *g_lo = (uint64_t)c[0].g;
+  return 1;
+}
+
+// BestRef of the single node v at level r < T (v must be a singleton refined
+// community), by the same best_ref the refinement loop calls.  Returns 1 with
+// the target refined community and its exact gain, 0 when there is none, -1
+// on bad arguments.
+int32_t orc_best_ref(void* h, int32_t r, int32_t v, int32_t* target, int64_t* g_hi, uint64_t* g_lo) {
+  Orc* o = (Orc*)h;
+  if (r < 0 || r >= o->T || v < 0 || v >= o->n || !o->singleton(r, v)) return -1;
+  const Counters keep = o->ctr;
+  std::vector<Cand> c = o->best_ref(r, std::vector<int32_t>{v});
+  o->ctr = keep;
+  if (c.empty()) return 0;
+  *target = c[0].dst;
+  *g_hi = (int64_t)(c[0].g >> 64);
+  *g_lo = (uint64_t)c[0].g;
+  return 1;
+}
+
+// Test set-up: replaces the partition of a one-level state (T == 0) by lab
+// (ids in [0, n)) and recomputes the community totals, internal weights and
+// the Eq. 1 numerator from level 0.  Returns 0, or 1 when T > 0 or a label
+// is out of range (nothing changed).
+int32_t orc_set_partition(void* h, const int32_t* lab) {
+  Orc* o = (Orc*)h;
+  if (o->T != 0) return 1;
+  for (int64_t v = 0; v < o->n; ++v)
+    if (lab[v] < 0 || lab[v] >= o->n) return 1;
+  Level& L0 = o->lv[0];
+  for (int64_t v = 0; v < o->n; ++v) L0.lab[v] = lab[v];
+  for (int64_t c = 0; c < o->n; ++c) { o->Kout[c] = 0; o->Kin[c] = 0; o->e[c] = 0; }
+  for (int64_t v = 0; v < o->n; ++v)
+    for (auto& p : L0.out[v]) {
+      o->Kout[L0.lab[v]] += p.second;
+      o->Kin[L0.lab[p.first]] += p.second;
+      if (L0.lab[v] == L0.lab[p.first]) o->e[L0.lab[v]] += p.second;
+    }
+  o->Q = o->q_from_stats();
+  return 0;
 }
 
 // Decoupling filter on an explicit candidate list; accepted[k] = 1 or 0.

@@ -61,6 +61,12 @@ def _load():
         lib.orc_check.argtypes = [P]
         lib.orc_gain.argtypes = [P, C.c_int32, C.c_int32, C.c_int32, P, P]
         lib.orc_decouple.argtypes = [C.c_int64, P, P, P, P, P, C.c_int64, P]
+        lib.orc_best_move.restype = C.c_int32
+        lib.orc_best_move.argtypes = [P, C.c_int32, C.c_int32, P, P, P]
+        lib.orc_best_ref.restype = C.c_int32
+        lib.orc_best_ref.argtypes = [P, C.c_int32, C.c_int32, P, P, P]
+        lib.orc_set_partition.restype = C.c_int32
+        lib.orc_set_partition.argtypes = [P, P]
         _lib = lib
     return _lib
 
@@ -176,6 +182,32 @@ class Oracle:
 
     def labels(self) -> np.ndarray:
         return self.level(0).lab
+
+    def _best(self, fn, r: int, v: int):
+        t = np.zeros(1, np.int32)
+        hi = np.zeros(1, np.int64)
+        lo = np.zeros(1, np.uint64)
+        have = int(fn(self._h, r, v, _ptr(t), _ptr(hi), _ptr(lo)))
+        if have < 0:
+            raise ValueError(f"bad arguments r={r} v={v}")
+        return (int(t[0]), (int(hi[0]) << 64) + int(lo[0])) if have else None
+
+    def best_move(self, r: int, v: int):
+        """(target, gain) the move loop's BestMove picks for node v at level r,
+        or None when v has no adjacent community with a positive gain."""
+        return self._best(_load().orc_best_move, r, v)
+
+    def best_ref(self, r: int, v: int):
+        """(target, gain) the refinement loop's BestRef picks for the singleton
+        node v at level r < top, or None."""
+        return self._best(_load().orc_best_ref, r, v)
+
+    def set_partition(self, lab) -> None:
+        """Test set-up of a one-level state: replace the level-0 partition and
+        recompute the community statistics from it."""
+        a = np.ascontiguousarray(lab, dtype=np.int32)
+        if int(_load().orc_set_partition(self._h, _ptr(a))) != 0:
+            raise ValueError("set_partition needs a one-level state and labels in [0, n)")
 
 
 def decouple(v, src, dst, gains, id_space: Optional[int] = None) -> np.ndarray:
