@@ -29,6 +29,9 @@
  *     "device" pointers are GPU global memory of the context's device.
  *   - The context owns all device state.  Pointers it returns stay valid until
  *     the next ldl_apply_batch() or ldl_destroy() on that context.
+ *   - A context lives on the device that was current at ldl_create(); every
+ *     entry point makes that device current for its duration and restores the
+ *     caller's current device before it returns.
  *   - A context is not thread safe; distinct contexts are independent.
  */
 #ifndef LDL_H
@@ -106,10 +109,18 @@ typedef struct {
 } ldl_update;
 
 /*
- * Result of the last batch.  labels is the level-0 partition P_t (device,
- * int32[n], owned by the context).  changed lists the vertices whose label
- * differs from before the batch (device, int32[n_changed]).  levels is the
- * hierarchy height T+1.  The counters describe the work done.
+ * Result of the last batch: the pair (H_t, P_t) that Algorithm 1 returns.
+ * labels is the level-0 partition P_t (device, int32[n], owned by the
+ * context).  changed lists the vertices whose label differs from before the
+ * batch (device, int32[n_changed]).  levels is the hierarchy height T+1, and
+ * the hierarchy H_t itself is given per level r < levels as host arrays of
+ * device pointers (all owned by the context): parent[r] is pi_r (int32[n]; -1
+ * for nodes absent at level r and at the top level), comm[r] is the level-r
+ * community labels P^r (int32[n]), refined[r] is the refined community of
+ * every level-r node (int32[n]; refined communities are named by their
+ * level-(r+1) node, so refined[r] and parent[r] are the same array), and
+ * alive[r] marks the nodes that exist at level r (uint8[n]).  Node ids are in
+ * [0, n) at every level.  The counters describe the work done.
  */
 typedef struct {
   const int32_t* labels;
@@ -117,6 +128,10 @@ typedef struct {
   const int32_t* changed;
   int64_t n_changed;
   int32_t levels;
+  const int32_t* const* parent;
+  const int32_t* const* comm;
+  const int32_t* const* refined;
+  const uint8_t* const* alive;
   int64_t frontier_nodes[8]; /* |A^r| summed over passes, per level */
   int64_t edges_scanned;     /* adjacency entries read by BestMove / BestRef */
   int64_t moves, refine_moves, rejected, rollbacks, rounds, agg_records;
@@ -271,10 +286,10 @@ int64_t ldl_launch_count(void);
  * Per-kernel statistics of the BestMove / BestRef sweep kernels, measured
  * with CUDA events on the context's stream while enabled (enabling resets
  * them).  out[28] = {launches, ms, algorithmic bytes, entries} for, in this
- * order, k_sweep_group with 8-lane groups (one group per node of <= 24
- * entries), k_sweep_group with whole warps (<= 96 entries), k_sweep_block
- * with 128 threads (<= 384 entries), k_sweep_block with 256 threads
- * (<= 2048), k_sweep_cluster (a cluster of 8 blocks with a distributed
+ * order, k_sweep_group with 8-lane groups (one group per node of at most
+ * bin_deg[0] entries), k_sweep_group with whole warps (<= bin_deg[1]),
+ * k_sweep_block with 128 threads (<= bin_deg[2]), k_sweep_block with 256
+ * threads (<= bin_deg[3]), k_sweep_cluster (a cluster of 8 blocks with a distributed
  * shared-memory hash, <= cluster_max_deg entries), k_hub_acc (the hub rows
  * spread over the GPU into global hash tables) and the rest of the hub path
  * (table set-up, evaluation and final reduction kernels).
@@ -292,6 +307,20 @@ ldl_status ldl_get_kernel_stats(const ldl_ctx* ctx, double* out);
 /* Test hook: make the k-th device allocation from now on fail (k >= 1);
  * k = 0 disables.  Lets a test check that NOMEM leaves the state intact. */
 void ldl_debug_fail_alloc_after(int64_t k);
+
+/*
+ * Test hook for the decoupling filter of Sec. III-E: runs the library's
+ * device filter (the one-block rounds for up to 8192 candidates, the
+ * cooperative multi-block rounds above) on `count` explicit candidates
+ * (host arrays): node v[k] moving from community src[k] to dst[k] with the
+ * exact gain (g_hi[k], g_lo[k]) (two's-complement halves of an int128).
+ * accepted[k] receives 1 for an accepted candidate, 0 otherwise.  Ids lie in
+ * [0, n) of the context, nodes are distinct, src != dst and count <= n
+ * (LDL_E_INVALID otherwise).  Uses the context's scratch buffers only: its
+ * graph, hierarchy and result are unchanged.
+ */
+ldl_status ldl_debug_decouple(ldl_ctx* ctx, int64_t count, const int32_t* v, const int32_t* src, const int32_t* dst,
+                              const int64_t* g_hi, const uint64_t* g_lo, uint8_t* accepted);
 
 /* Test hook for the bounded waits: runs a two-tile device scan in which the
  * first tile never publishes its sum, so the second tile's look-back wait

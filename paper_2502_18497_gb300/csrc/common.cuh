@@ -231,12 +231,25 @@ __device__ inline bool stamp_claim(int32_t* stamp, int32_t ep, int32_t x) {
 }
 
 inline int div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
-inline int grid_for(int64_t n, int block, int cap = 152 * 32) {
+// Streaming multiprocessors of the current device (queried once per device).
+int device_sms();
+// Blocks for n items of `block` per block, at most per_sm blocks per SM of
+// the current device (grid-stride kernels cover the rest).
+inline int grid_for(int64_t n, int block, int per_sm = 32) {
   int64_t g = (n + block - 1) / block;
+  const int64_t cap = (int64_t)per_sm * device_sms();
   if (g < 1) g = 1;
   if (g > cap) g = cap;
   return (int)g;
 }
+
+// Makes the context's device current for the duration of an entry point and
+// restores the caller's device afterwards.
+struct DeviceScope {
+  int prev = -1, dev = -1;
+  explicit DeviceScope(int d);
+  ~DeviceScope();
+};
 
 // ---------------------------------------------------------------- slack CSR
 // Rows in [0, n): row v occupies pool[off[v], off[v]+len[v]) with capacity

@@ -44,6 +44,7 @@ enum {
 
 struct ldl_ctx {
   ldl_params prm{};
+  int dev = 0;           // the CUDA device the context lives on
   int64_t n = 0;
   int directed = 0;
   int32_t bin_deg[4] = {0, 0, 0, 0};  // resolved sweep degree bins
@@ -95,6 +96,10 @@ struct ldl_ctx {
 
   // counters of the last batch
   ldl_result res{};
+  // per-level device pointers handed out in ldl_result (host arrays)
+  const int32_t* out_par[8] = {nullptr};
+  const int32_t* out_lab[8] = {nullptr};
+  const uint8_t* out_alive[8] = {nullptr};
   int64_t frontier[8] = {0};
   int timing = 0;
   double stage_ms[16] = {0};

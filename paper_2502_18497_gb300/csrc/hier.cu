@@ -801,7 +801,7 @@ void pushdown(ldl_ctx& c, int r, int32_t epCh) {
     int32_t* dst = q > 0 ? bufs[flip] : nullptr;
     zero_cnt(c, idxs[flip]);
     ChunkMap m = chunk_map(c, src, c.dcnt + idx, n, L.children.len.p, nullptr);
-    k_push<<<grid_for((int64_t)n * 64, TPB, 152 * 16), TPB, 0, c.s>>>(
+    k_push<<<grid_for((int64_t)n * 64, TPB, 16), TPB, 0, c.s>>>(
         m, c.lv[q + 1].lab.p, ch, L.lab.p, dst, c.dcnt + idxs[flip], q == 0 ? c.stCh.p : nullptr, epCh, c.lCh.p,
         c.dcnt + K_CH, c.lab_before.p);
     CKL("k_push");
@@ -833,7 +833,7 @@ int32_t dissolve(ldl_ctx& c, int r, int32_t epD, int32_t epX, bool all_nodes) {
     if (nx > 0) {
       Adj<int32_t> ch{L.children.off.p, L.children.len.p, L.children.col.p, L.children.w.p};
       ChunkMap m = chunk_map(c, c.lX.p, c.dcnt + K_X, nx, L.children.len.p, nullptr);
-      k_collect<<<grid_for((int64_t)nx * 64, TPB, 152 * 16), TPB, 0, c.s>>>(ch, m, c.stD.p, epD, c.lD.p,
+      k_collect<<<grid_for((int64_t)nx * 64, TPB, 16), TPB, 0, c.s>>>(ch, m, c.stD.p, epD, c.lD.p,
                                                                            c.dcnt + K_D);
       CKL("k_collect");
     }
@@ -869,7 +869,7 @@ static void emit_records(ldl_ctx& c, int r, Adj<WT> out, Adj<WT> in, int32_t nC,
   c.rv2.reserve(cap, c.s);
   zero_cnt(c, K_REC);
   ChunkMap m = chunk_map(c, c.lC.p, c.dcnt + K_C, nC, out.len, in.len);
-  k_emit<WT><<<grid_for((int64_t)nC * 64, TPB, 152 * 16), TPB, 0, c.s>>>(out, in, m, c.lv[r].par.p, c.par_old.p,
+  k_emit<WT><<<grid_for((int64_t)nC * 64, TPB, 16), TPB, 0, c.s>>>(out, in, m, c.lv[r].par.p, c.par_old.p,
                                                                           c.stC.p, epC, c.bits, c.rk2.p, c.rv2.p,
                                                                           c.dcnt + K_REC);
   CKL("k_emit");

@@ -47,6 +47,32 @@ void dfree(void* p) {
 }
 
 namespace {
+constexpr int kMaxDev = 64;
+std::atomic<int> g_sms[kMaxDev];  // 0: not queried yet
+}  // namespace
+
+int device_sms() {
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDev) ldl_throw(LDL_E_CUDA, "device ordinal out of range");
+  int v = g_sms[dev].load(std::memory_order_relaxed);
+  if (v > 0) return v;
+  CK(cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev));
+  if (v <= 0) ldl_throw(LDL_E_CUDA, "device reports no multiprocessors");
+  g_sms[dev].store(v, std::memory_order_relaxed);
+  return v;
+}
+
+DeviceScope::DeviceScope(int d) : dev(d) {
+  CK(cudaGetDevice(&prev));
+  if (prev != dev) CK(cudaSetDevice(dev));
+}
+
+DeviceScope::~DeviceScope() {
+  if (prev >= 0 && prev != dev) cudaSetDevice(prev);
+}
+
+namespace {
 constexpr int PUB_MAX = 8;        // values per read
 constexpr int PUB_BYTES = 4000;   // payload bytes per read
 struct PubReq {
@@ -509,6 +535,7 @@ ldl_status ldl_create(const ldl_params* params, int64_t n, int64_t nnz, const in
   ldl_ctx* c = new (std::nothrow) ldl_ctx();
   if (!c) return LDL_E_NOMEM;
   try {
+    CK(cudaGetDevice(&c->dev));
     c->prm = p;
     c->n = n;
     c->directed = p.directed ? 1 : 0;
@@ -553,6 +580,7 @@ ldl_status ldl_apply_batch(ldl_ctx* c, const ldl_update* updates, int64_t count,
     return LDL_E_INVALID;
   }
   try {
+    DeviceScope ds(c->dev);
     apply_batch(*c, updates, count, on_device);
     CK(cudaStreamSynchronize(c->s));
   } catch (const LdlError& e) {
@@ -566,6 +594,16 @@ ldl_status ldl_apply_batch(ldl_ctx* c, const ldl_update* updates, int64_t count,
     out->n = c->n;
     out->changed = c->lChg.p;
     out->levels = c->T + 1;
+    for (int r = 0; r < 8; ++r) {
+      const bool has = r <= c->T;
+      c->out_par[r] = has ? c->lv[r].par.p : nullptr;
+      c->out_lab[r] = has ? c->lv[r].lab.p : nullptr;
+      c->out_alive[r] = has ? c->lv[r].alive.p : nullptr;
+    }
+    out->parent = c->out_par;
+    out->comm = c->out_lab;
+    out->refined = c->out_par;
+    out->alive = c->out_alive;
   }
   return LDL_OK;
 }
@@ -593,6 +631,7 @@ ldl_status ldl_modularity_num(const ldl_ctx* c, int64_t* q_hi, uint64_t* q_lo, i
 void ldl_destroy(ldl_ctx* c) {
   if (!c) return;
   try {
+    DeviceScope ds(c->dev);
     free_all(*c);
   } catch (...) {
   }
@@ -608,6 +647,7 @@ ldl_status ldl_get_level(const ldl_ctx* cc, int32_t r, int32_t* lab, int32_t* pa
   if (!cc || r < 0 || r > cc->T) return LDL_E_INVALID;
   ldl_ctx& c = const_cast<ldl_ctx&>(*cc);
   try {
+    DeviceScope ds(c.dev);
     const LevelState& L = c.lv[r];
     const size_t n = (size_t)c.n;
     if (lab) CK(cudaMemcpyAsync(lab, L.lab.p, 4 * n, cudaMemcpyDeviceToHost, c.s));
@@ -630,6 +670,7 @@ ldl_status ldl_level_nnz(const ldl_ctx* cc, int32_t r, int64_t* nnz) {
   if (!cc || !nnz || r < 0 || r > cc->T) return LDL_E_INVALID;
   ldl_ctx& c = const_cast<ldl_ctx&>(*cc);
   try {
+    DeviceScope ds(c.dev);
     std::vector<int32_t> len((size_t)c.n);
     const DBuf<int32_t>& lp = r == 0 ? c.lv[0].out0.len : c.lv[r].out.len;
     CK(cudaMemcpyAsync(len.data(), lp.p, 4 * (size_t)c.n, cudaMemcpyDeviceToHost, c.s));
@@ -648,6 +689,7 @@ ldl_status ldl_get_adjacency(const ldl_ctx* cc, int32_t r, int64_t* row_ptr, int
   if (!cc || !row_ptr || r < 0 || r > cc->T) return LDL_E_INVALID;
   ldl_ctx& c = const_cast<ldl_ctx&>(*cc);
   try {
+    DeviceScope ds(c.dev);
     std::vector<int64_t> off;
     std::vector<int32_t> len, cl;
     std::vector<std::pair<int32_t, int64_t>> row;
@@ -686,6 +728,7 @@ ldl_status ldl_get_communities(const ldl_ctx* cc, int64_t* kout, int64_t* kin, i
   if (!cc) return LDL_E_INVALID;
   ldl_ctx& c = const_cast<ldl_ctx&>(*cc);
   try {
+    DeviceScope ds(c.dev);
     const size_t n = (size_t)c.n;
     if (kout) CK(cudaMemcpyAsync(kout, c.Kout.p, 8 * n, cudaMemcpyDeviceToHost, c.s));
     if (kin) CK(cudaMemcpyAsync(kin, Kin_of(c), 8 * n, cudaMemcpyDeviceToHost, c.s));
@@ -723,6 +766,50 @@ ldl_status ldl_debug_scan_wait_timeout(void) {
 
 int64_t ldl_launch_count(void) { return g_launches.load(); }
 
+ldl_status ldl_debug_decouple(ldl_ctx* c, int64_t count, const int32_t* v, const int32_t* src, const int32_t* dst,
+                              const int64_t* g_hi, const uint64_t* g_lo, uint8_t* accepted) {
+  if (!c || count < 0 || count > c->n || (count > 0 && (!v || !src || !dst || !g_hi || !g_lo || !accepted)))
+    return LDL_E_INVALID;
+  std::vector<uint8_t> seen((size_t)c->n, 0);
+  for (int64_t k = 0; k < count; ++k) {
+    if (v[k] < 0 || v[k] >= c->n || src[k] < 0 || src[k] >= c->n || dst[k] < 0 || dst[k] >= c->n ||
+        src[k] == dst[k] || seen[(size_t)v[k]]) {
+      c->err = "ldl_debug_decouple: ids must lie in [0, n), nodes must be distinct and src != dst";
+      return LDL_E_INVALID;
+    }
+    seen[(size_t)v[k]] = 1;
+  }
+  try {
+    DeviceScope ds(c->dev);
+    ldl_ctx& x = *c;
+    const size_t k = (size_t)count;
+    if (k) {
+      CK(cudaMemcpyAsync(x.cv.p, v, 4 * k, cudaMemcpyHostToDevice, x.s));
+      CK(cudaMemcpyAsync(x.csrc.p, src, 4 * k, cudaMemcpyHostToDevice, x.s));
+      CK(cudaMemcpyAsync(x.cdst.p, dst, 4 * k, cudaMemcpyHostToDevice, x.s));
+      CK(cudaMemcpyAsync(x.cghi.p, g_hi, 8 * k, cudaMemcpyHostToDevice, x.s));
+      CK(cudaMemcpyAsync(x.cglo.p, g_lo, 8 * k, cudaMemcpyHostToDevice, x.s));
+    }
+    set_cnt(x, K_CAND, (int32_t)count);
+    const ldl_result keep = x.res;
+    const int64_t keep_syncs = x.syncs;
+    const DecoupleOut d = decouple(x);
+    x.res = keep;
+    x.syncs = keep_syncs;
+    std::vector<int32_t> bv((size_t)std::max(d.nb, 1));
+    if (d.nb > 0) CK(cudaMemcpyAsync(bv.data(), x.bv.p, 4 * (size_t)d.nb, cudaMemcpyDeviceToHost, x.s));
+    CK(cudaStreamSynchronize(x.s));
+    std::vector<uint8_t> acc((size_t)x.n, 0);
+    for (int32_t i = 0; i < d.nb; ++i) acc[(size_t)bv[(size_t)i]] = 1;
+    for (int64_t i = 0; i < count; ++i) accepted[i] = acc[(size_t)v[i]];
+  } catch (const LdlError& e) {
+    c->err = e.msg;
+    cudaGetLastError();
+    return e.st;
+  }
+  return LDL_OK;
+}
+
 ldl_status ldl_copy_changed(const ldl_ctx* cc, int32_t* ids, int32_t* labels) {
   if (!cc) return LDL_E_INVALID;
   ldl_ctx& c = const_cast<ldl_ctx&>(*cc);
@@ -730,6 +817,7 @@ ldl_status ldl_copy_changed(const ldl_ctx* cc, int32_t* ids, int32_t* labels) {
   if (k == 0) return LDL_OK;
   if (!ids) return LDL_E_INVALID;
   try {
+    DeviceScope ds(c.dev);
     CK(cudaMemcpyAsync(ids, c.lChg.p, sizeof(int32_t) * (size_t)k, cudaMemcpyDeviceToHost, c.s));
     CK(cudaStreamSynchronize(c.s));
     if (labels) {
@@ -747,6 +835,7 @@ ldl_status ldl_copy_changed(const ldl_ctx* cc, int32_t* ids, int32_t* labels) {
 ldl_status ldl_set_kernel_stats(ldl_ctx* c, int32_t on) {
   if (!c) return LDL_E_INVALID;
   try {
+    DeviceScope ds(c->dev);
     c->kstats = on ? 1 : 0;
     c->kev_used = 0;
     for (int k = 0; k < KS_GROUPS; ++k) c->ks_launch[k] = 0;
@@ -762,6 +851,7 @@ ldl_status ldl_set_kernel_stats(ldl_ctx* c, int32_t on) {
 ldl_status ldl_get_kernel_stats(const ldl_ctx* c, double* out) {
   if (!c || !out) return LDL_E_INVALID;
   try {
+    DeviceScope ds(c->dev);
     double ms[KS_GROUPS] = {0, 0, 0, 0, 0, 0, 0};
     if (c->kev_used) CK(cudaEventSynchronize(c->kev[c->kev_used - 1]));
     for (size_t i = 0; i + KS_EVENTS <= c->kev_used; i += KS_EVENTS)

@@ -7,6 +7,9 @@
 // them the same result as ldl_copy_changed while touching no allocator: the
 // labels of the changed vertices are gathered into a fixed static device
 // array and copied to the caller's host arrays from there.
+#include <algorithm>
+#include <mutex>
+
 #include "kern.cuh"
 
 // Largest number of changed vertices one call can return.
@@ -22,7 +25,11 @@ static __device__ __align__(256) int32_t g_noalloc_labels[LDL_NOALLOC_MAX_CHANGE
 namespace {
 
 constexpr int kMaxDevices = 64;
+// Device address of the array on each device, resolved once per device (the
+// host-side symbol is only a stand-in and must never reach a kernel).
+std::once_flag g_once[kMaxDevices];
 int32_t* g_ptr[kMaxDevices] = {nullptr};
+cudaError_t g_ptr_err[kMaxDevices] = {cudaSuccess};
 
 __global__ void k_gather_noalloc(const int32_t* ids, int32_t k, const int32_t* lab, int32_t* out) {
   for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < k; i += gridDim.x * blockDim.x) out[i] = lab[ids[i]];
@@ -44,31 +51,43 @@ extern "C" ldl_status ldl_copy_changed_noalloc(const ldl_ctx* cc, int32_t* ids, 
             std::to_string(LDL_NOALLOC_MAX_CHANGED) + "; use ldl_copy_changed";
     return LDL_E_INVALID;
   }
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
-    c.err = std::string("ldl_copy_changed_noalloc: no usable current device: ") + cudaGetErrorString(e);
+  const int dev = c.dev;
+  if (dev < 0 || dev >= kMaxDevices) {
+    c.err = "ldl_copy_changed_noalloc: device ordinal out of range";
     return LDL_E_CUDA;
   }
-  // first call on this device: resolve the device address of the array (the
-  // host-side symbol is only a stand-in and must not reach a kernel)
-  if (!g_ptr[dev]) {
+  // the context's device is current for the whole call (and the caller's
+  // device is restored on return), so the address looked up below and the
+  // kernel's launch both belong to the device that holds the context
+  int prev = -1;
+  cudaError_t e = cudaGetDevice(&prev);
+  if (e == cudaSuccess && prev != dev) e = cudaSetDevice(dev);
+  if (e != cudaSuccess) {
+    c.err = std::string("ldl_copy_changed_noalloc: cannot make the context's device current: ") +
+            cudaGetErrorString(e);
+    return LDL_E_CUDA;
+  }
+  std::call_once(g_once[dev], [dev] {
     void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_labels);
-    if (e != cudaSuccess || !p) {
-      c.err = std::string("ldl_copy_changed_noalloc: cudaGetSymbolAddress failed: ") + cudaGetErrorString(e);
-      return LDL_E_CUDA;
-    }
-    g_ptr[dev] = (int32_t*)p;
+    g_ptr_err[dev] = cudaGetSymbolAddress(&p, g_noalloc_labels);
+    if (g_ptr_err[dev] == cudaSuccess && !p) g_ptr_err[dev] = cudaErrorInvalidSymbol;
+    if (g_ptr_err[dev] == cudaSuccess) g_ptr[dev] = (int32_t*)p;
+  });
+  if (g_ptr_err[dev] != cudaSuccess) {
+    c.err = std::string("ldl_copy_changed_noalloc: cudaGetSymbolAddress failed: ") + cudaGetErrorString(g_ptr_err[dev]);
+    if (prev >= 0 && prev != dev) cudaSetDevice(prev);
+    return LDL_E_CUDA;
   }
   int32_t* scratch = g_ptr[dev];
   const int32_t kk = (int32_t)k;
-  k_gather_noalloc<<<grid_for(kk, 256), 256, 0, c.s>>>(c.lChg.p, kk, c.lv[0].lab.p, scratch);
+  const int grid = (int)std::min<int64_t>(((int64_t)kk + 255) / 256, 4096);
+  k_gather_noalloc<<<grid, 256, 0, c.s>>>(c.lChg.p, kk, c.lv[0].lab.p, scratch);
   g_launches.fetch_add(1, std::memory_order_relaxed);
   e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaMemcpyAsync(ids, c.lChg.p, sizeof(int32_t) * (size_t)kk, cudaMemcpyDeviceToHost, c.s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(labels, scratch, sizeof(int32_t) * (size_t)kk, cudaMemcpyDeviceToHost, c.s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c.s);
+  if (prev >= 0 && prev != dev) cudaSetDevice(prev);
   if (e != cudaSuccess) {
     c.err = std::string("ldl_copy_changed_noalloc: ") + cudaGetErrorString(e);
     return LDL_E_CUDA;

@@ -1046,7 +1046,7 @@ __global__ void k_spexpand(Adj<WT> out, Adj<WT> in, ChunkMap m, const int32_t* l
 }  // namespace
 
 // ================================================================== host side
-static int chunk_grid(int64_t n_hint) { return grid_for(n_hint * 64, TPB, 152 * 16); }
+static int chunk_grid(int64_t n_hint) { return grid_for(n_hint * 64, TPB, 16); }
 
 void expand_set(ldl_ctx& c, int r, const int32_t* list, int idx_n, int32_t* stamp, int32_t ep, int32_t* olist,
                 int idx_out, int64_t n_hint) {
@@ -1137,16 +1137,16 @@ static void sweep_t(ldl_ctx& c, int r, Adj<WT> out, Adj<WT> in, const int32_t* l
   // and the host's wait below overlaps them.  n_hint bounds every bin.
   cudaEvent_t* kev = c.kstats ? kstats_events(c) : nullptr;
   if (kev) CK(cudaEventRecord(kev[0], c.s));
-  k_sweep_group<WT, MODE, 8><<<grid_for(n_hint * 8, TPB, 152 * 5), TPB, 0, c.s>>>(A, c.binT.p, c.dcnt + K_TINY);
+  k_sweep_group<WT, MODE, 8><<<grid_for(n_hint * 8, TPB, 5), TPB, 0, c.s>>>(A, c.binT.p, c.dcnt + K_TINY);
   CKL("k_sweep_group<8>");
   if (kev) CK(cudaEventRecord(kev[1], c.s));
-  k_sweep_group<WT, MODE, 32><<<grid_for(n_hint * 32, TPB, 152 * 5), TPB, 0, c.s>>>(A, c.binS.p,
+  k_sweep_group<WT, MODE, 32><<<grid_for(n_hint * 32, TPB, 5), TPB, 0, c.s>>>(A, c.binS.p,
                                                                                     c.dcnt + K_SMALL);
   CKL("k_sweep_group<32>");
   if (kev) CK(cudaEventRecord(kev[2], c.s));
   {
     const size_t sm = (sizeof(int64_t) + sizeof(int32_t)) * 2048;
-    k_sweep_block<WT, MODE, 128, 2048><<<grid_for(n_hint, 1, 152 * 16), 128, sm, c.s>>>(A, c.binM.p,
+    k_sweep_block<WT, MODE, 128, 2048><<<grid_for(n_hint, 1, 16), 128, sm, c.s>>>(A, c.binM.p,
                                                                                      c.dcnt + K_MID);
     CKL("k_sweep_block(mid1)");
   }
@@ -1154,7 +1154,7 @@ static void sweep_t(ldl_ctx& c, int r, Adj<WT> out, Adj<WT> in, const int32_t* l
   {
     const size_t sm = (sizeof(int64_t) + sizeof(int32_t)) * HB;
     CK(cudaFuncSetAttribute(k_sweep_block<WT, MODE, 256, HB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    k_sweep_block<WT, MODE, 256, HB><<<grid_for(n_hint, 1, 152 * 4), 256, sm, c.s>>>(A, c.binM2.p,
+    k_sweep_block<WT, MODE, 256, HB><<<grid_for(n_hint, 1, 4), 256, sm, c.s>>>(A, c.binM2.p,
                                                                                    c.dcnt + K_MID2);
     CKL("k_sweep_block(mid2)");
   }
@@ -1162,7 +1162,7 @@ static void sweep_t(ldl_ctx& c, int r, Adj<WT> out, Adj<WT> in, const int32_t* l
   if (c.prm.cluster_max_deg > c.bin_deg[3]) {
     const size_t sm = (sizeof(int64_t) + sizeof(int32_t)) * CL_SLOTS;
     CK(cudaFuncSetAttribute(k_sweep_cluster<WT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    const int ncl = (int)std::min<int64_t>(n_hint, 152 * 2 / CL);
+    const int ncl = (int)std::min<int64_t>(n_hint, std::max(1, device_sms() * 2 / CL));
     k_sweep_cluster<WT, MODE><<<ncl * CL, TPB, sm, c.s>>>(A, c.binC.p, c.dcnt + K_CLU);
     CKL("k_sweep_cluster");
   }
@@ -1200,7 +1200,7 @@ static void sweep_t(ldl_ctx& c, int r, Adj<WT> out, Adj<WT> in, const int32_t* l
     c.pb_c.reserve(ech, c.s);
     ChunkMap m = chunk_map(c, c.binL.p, c.dcnt + K_LARGE, nh, out.len, c.directed ? in.len : nullptr);
     if (kev) CK(cudaEventRecord(kev[7], c.s));
-    k_hub_acc<WT, MODE><<<grid_for((int64_t)nh * 2048, TPB, 152 * 16), TPB, 0, c.s>>>(
+    k_hub_acc<WT, MODE><<<grid_for((int64_t)nh * 2048, TPB, 16), TPB, 0, c.s>>>(
         A, m, c.binLoff.p, c.binLsz.p, c.gkeys.p, c.gvals.p, c.glist.p, c.hcnt.p);
     CKL("k_hub_acc");
     if (kev) CK(cudaEventRecord(kev[8], c.s));
@@ -1208,7 +1208,7 @@ static void sweep_t(ldl_ctx& c, int r, Adj<WT> out, Adj<WT> in, const int32_t* l
     k_eval_counts<<<grid_for(nh + 1, TPB), TPB, 0, c.s>>>(c.hcnt.p, nh, c.hub_ecnt.p);
     CKL("k_eval_counts");
     scan_exclusive(c.hub_ecnt.p, c.hub_epre.p, nh + 1, c.P, c.s, false);
-    const int ge = grid_for(ech, 1, 152 * 8);
+    const int ge = grid_for(ech, 1, 8);
     k_hub_eval<WT, MODE><<<ge, TPB, 0, c.s>>>(A, c.binL.p, nh, c.binLoff.p, c.binLsz.p, c.hub_epre.p, c.gkeys.p,
                                               c.gvals.p, c.glist.p, c.hcnt.p, c.pb_hi.p, c.pb_lo.p, c.pb_c.p);
     CKL("k_hub_eval");
@@ -1269,9 +1269,8 @@ DecoupleOut decouple(ldl_ctx& c, int extra) {
     return {nc, out[1], ex};
   }
   // many candidates: one cooperative launch of co-resident blocks runs all rounds
-  int dev = 0, sms = 0, per_sm = 0;
-  CK(cudaGetDevice(&dev));
-  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  int per_sm = 0;
+  const int sms = device_sms();
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dec_grid, TPB, 0));
   const int g = std::max(1, std::min(grid_for(nc, TPB), sms * per_sm));
   zero_cnt(c, K_B);

@@ -35,6 +35,8 @@ class ldl_params(C.Structure):
 class ldl_result(C.Structure):
     _fields_ = [("labels", C.c_void_p), ("n", C.c_int64), ("changed", C.c_void_p),
                 ("n_changed", C.c_int64), ("levels", C.c_int32),
+                ("parent", C.c_void_p), ("comm", C.c_void_p), ("refined", C.c_void_p),
+                ("alive", C.c_void_p),
                 ("frontier_nodes", C.c_int64 * 8), ("edges_scanned", C.c_int64),
                 ("moves", C.c_int64), ("refine_moves", C.c_int64), ("rejected", C.c_int64),
                 ("rollbacks", C.c_int64), ("rounds", C.c_int64), ("agg_records", C.c_int64),
@@ -90,6 +92,7 @@ def load(path: Optional[str] = None):
         "ldl_server_submit": (I32, [P, P, P, I64, P]),
         "ldl_server_wait": (I32, [P, I64, I32, P, P, P, P]),
         "ldl_server_destroy": (None, [P]),
+        "ldl_debug_decouple": (I32, [P, I64, P, P, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -107,7 +110,7 @@ def exported_symbols():
             "ldl_set_timing", "ldl_debug_fail_alloc_after", "ldl_debug_scan_wait_timeout", "ldl_copy_changed", "ldl_copy_changed_noalloc", "ldl_launch_count",
             "ldl_set_kernel_stats", "ldl_get_kernel_stats", "ldl_apply_batches", "ldl_estimate_bytes",
             "ldl_server_create", "ldl_server_admit", "ldl_server_submit", "ldl_server_wait",
-            "ldl_server_destroy"]
+            "ldl_server_destroy", "ldl_debug_decouple"]
 
 
 def launch_count() -> int:
@@ -285,6 +288,43 @@ class LDL:
         lab = np.zeros(k, np.int32)
         self._check(load().ldl_copy_changed_noalloc(self._h, _ptr(ids), _ptr(lab)))
         return ids, lab
+
+    def debug_decouple(self, v, src, dst, gains) -> np.ndarray:
+        """Runs the device decoupling filter on explicit candidates (gains are
+        Python ints up to 127 bits); returns the 0/1 accepted mask."""
+        v = np.ascontiguousarray(v, dtype=np.int32)
+        src = np.ascontiguousarray(src, dtype=np.int32)
+        dst = np.ascontiguousarray(dst, dtype=np.int32)
+        g = [int(x) for x in gains]
+        hi = np.array([x >> 64 for x in g], dtype=np.int64)
+        lo = np.array([x & ((1 << 64) - 1) for x in g], dtype=np.uint64)
+        out = np.zeros(len(v), np.uint8)
+        self._check(load().ldl_debug_decouple(self._h, len(v), _ptr(v), _ptr(src), _ptr(dst), _ptr(hi), _ptr(lo),
+                                              _ptr(out)))
+        return out
+
+    def hierarchy(self):
+        """Per level r of the last result: (parent, comm, refined, alive) copied
+        from the device pointers that ldl_apply_batch returned."""
+        import torch
+
+        r = self.last
+        n = self.n
+        out = []
+
+        class _Dev:
+            def __init__(self, ptr, typestr):
+                self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr, "data": (ptr, False),
+                                                 "version": 2}
+
+        def rd(arr, k, typestr):
+            ptr = C.cast(arr, C.POINTER(C.c_void_p))[k]
+            return torch.as_tensor(_Dev(ptr, typestr), device="cuda").cpu().numpy().copy()
+
+        for k in range(r.levels):
+            out.append(dict(parent=rd(r.parent, k, "<i4"), comm=rd(r.comm, k, "<i4"),
+                            refined=rd(r.refined, k, "<i4"), alive=rd(r.alive, k, "|u1")))
+        return out
 
     def set_kernel_stats(self, on: bool = True):
         self._check(load().ldl_set_kernel_stats(self._h, int(on)))
