@@ -34,10 +34,15 @@
 //   - Expand(V) = V plus its graph neighbours; touched communities and parents
 //     are recorded (they drive refinement and NextFrontier) but do not enrol
 //     their members.
-//   - Refinement dissolves every refined community that holds a node of the
-//     level's move frontiers (all U's, including A^r) into singletons; only
-//     still-singleton dissolved nodes move, into refined communities adjacent
-//     to them inside their own community, by the same gain with a = {v}.
+//   - Refinement of a batch update (TouchedRefined) is local: a node whose
+//     label no longer equals its refined community's label (it moved, or took
+//     its members' new label) leaves it as a singleton; the refined
+//     communities that lost a node or hold an endpoint of a deleted arc are
+//     split into their connected components (the seed's component keeps the
+//     id, others are named by their lowest member); only singletons of the
+//     reset or renamed nodes move, into refined communities adjacent to them
+//     inside their own community, by the same gain with a = {v}.  The static
+//     build refines from singletons.
 //   - Rollback iff dQ(B) < 0; stop the move loop iff dQ(B)*alpha_inv < Q0num
 //     or |V|*beta_inv < |S|; refine stops iff |V|*beta_inv < |R|; either loop
 //     stops when B is empty.
@@ -99,19 +104,6 @@ i64 row_get(const Row& r, int32_t c) {
   return (it != r.end() && it->first == c) ? it->second : 0;
 }
 
-void row_add(Row& r, int32_t c, i64 d) {
-  if (d == 0) return;
-  auto it = std::lower_bound(r.begin(), r.end(), std::make_pair(c, (i64)INT64_MIN));
-  if (it != r.end() && it->first == c) {
-    it->second += d;
-    if (it->second < 0) die("negative weight");
-    if (it->second == 0) r.erase(it);
-  } else {
-    if (d < 0) die("negative weight on insert");
-    r.insert(it, std::make_pair(c, d));
-  }
-}
-
 struct Level {
   std::vector<Row> out, in;          // in: used only for directed graphs
   std::vector<i64> kout, kin;        // node strengths at this level
@@ -119,6 +111,7 @@ struct Level {
   std::vector<int32_t> par;          // pi_r: parent (level r+1 node), NONE if none
   std::vector<int32_t> cnt;          // number of level r-1 children (level 0: 1)
   std::vector<uint8_t> alive;
+  std::vector<int32_t> brk;          // endpoints of arcs deleted since this level was last refined
 };
 
 struct Cand {
@@ -165,11 +158,6 @@ struct Orc {
     L0.alive.assign(n, 0);
   }
 
-  void add_arc(int r, int32_t x, int32_t y, i64 d) {
-    row_add(lv[r].out[x], y, d);
-    if (directed) row_add(lv[r].in[y], x, d);
-  }
-
   // Eq. 1 numerator from the community statistics.
   i128 q_from_stats() const {
     i128 q = 0;
@@ -214,8 +202,9 @@ struct Orc {
 
   // Adds grouped records (sorted by (row, col), nonzero) to the rows: each
   // touched row is merged with its records in one pass; entries that reach
-  // zero disappear.
-  static void merge_rows_with(std::vector<Row>& rows, const std::vector<ERec>& recs) {
+  // zero disappear (their endpoints are appended to `gone` when given).
+  static void merge_rows_with(std::vector<Row>& rows, const std::vector<ERec>& recs,
+                              std::vector<int32_t>* gone = nullptr) {
     Row merged;
     for (size_t i = 0; i < recs.size();) {
       const int32_t x = recs[i].first.first;
@@ -235,6 +224,7 @@ struct Orc {
           const i64 v = row[a].second + recs[b].second;
           if (v < 0) die("negative weight");
           if (v != 0) merged.push_back(std::make_pair(row[a].first, v));
+          else if (gone) { gone->push_back(x); gone->push_back(row[a].first); }
           ++a;
           ++b;
         }
@@ -244,9 +234,11 @@ struct Orc {
     }
   }
 
-  // Applies grouped arc records to level r (out-rows, and in-rows when directed).
+  // Applies grouped arc records to level r (out-rows, and in-rows when
+  // directed); the endpoints of arcs that disappear are recorded for the
+  // level's next refinement.
   void apply_arcs(int r, const std::vector<ERec>& recs) {
-    merge_rows_with(lv[r].out, recs);
+    merge_rows_with(lv[r].out, recs, &lv[r].brk);
     if (directed) {
       std::vector<ERec> t;
       t.reserve(recs.size());
@@ -437,10 +429,11 @@ struct Orc {
   }
 
   // ---------------------------------------------------------------- Refine
-  // TouchedRefined + dissolve: every alive level-r node whose refined
-  // community holds a node of Ustar (plus parentless new nodes) becomes a
-  // singleton refined community named by its own id.  Level r+1 strengths
-  // and child counts follow live.  Returns D; par_old receives old parents.
+  // Static build: every alive level-r node whose refined community holds a
+  // node of Ustar (plus parentless new nodes) becomes a singleton refined
+  // community named by its own id (with Ustar = all nodes, refinement starts
+  // from singletons).  Level r+1 strengths and child counts follow live.
+  // Returns D; par_old receives old parents.
   std::vector<int32_t> dissolve(int r, const std::vector<int32_t>& Ustar,
                                 std::vector<int32_t>& par_old) {
     Level& Lr = lv[r];
@@ -475,6 +468,92 @@ struct Orc {
       Ln.kin[u] += Lr.kin[u];
       Ln.cnt[u] += 1;
     }
+    return D;
+  }
+
+  // TouchedRefined of a batch update at level r (Sec. III-C: refinement
+  // revisits only the communities touched by accepted moves).  A refined
+  // community lies inside one community, so a level-r node whose label no
+  // longer equals its refined community's label (it moved at level r, or its
+  // label was taken from its members' moves at level r-1) leaves it and
+  // becomes a singleton named by its own id, as does a parentless new node;
+  // such nodes all lie in Ustar.  Every refined community that lost a node,
+  // or holds an endpoint of a level-r arc deleted since the level was last
+  // refined, is re-checked for connectivity over the arcs among its remaining
+  // members (a refined community stays connected): the component holding the
+  // community's seed node keeps the community's id, any other component is
+  // renamed after its lowest member (an id no refined community uses).
+  // Untouched refined communities keep their ids and members.  Level r+1
+  // strengths and child counts follow.  Returns D, every node whose refined
+  // community was reset or renamed; par_old receives their old parents.
+  std::vector<int32_t> split(int r, const std::vector<int32_t>& Ustar, std::vector<int32_t>& par_old) {
+    Level& Lr = lv[r];
+    Level& Ln = lv[r + 1];
+    std::vector<uint8_t> inD(n, 0), mv(n, 0), chk(n, 0);
+    std::vector<int32_t> D, CK, leave;
+    auto reparent = [&](int32_t u, int32_t p) {
+      const int32_t po = Lr.par[u];
+      if (!inD[u]) { inD[u] = 1; par_old[u] = po; D.push_back(u); }
+      if (po != NONE) { Ln.kout[po] -= Lr.kout[u]; Ln.kin[po] -= Lr.kin[u]; Ln.cnt[po] -= 1; }
+      Lr.par[u] = p;
+      Ln.kout[p] += Lr.kout[u]; Ln.kin[p] += Lr.kin[u]; Ln.cnt[p] += 1;
+    };
+    auto check_later = [&](int32_t X) {
+      if (X != NONE && !chk[X]) { chk[X] = 1; CK.push_back(X); }
+    };
+    for (int32_t u : Ustar) {
+      if (!Lr.alive[u]) continue;
+      const int32_t X = Lr.par[u];
+      if (X == NONE || Ln.lab[X] != Lr.lab[u]) { mv[u] = 1; leave.push_back(u); check_later(X); }
+    }
+    for (int32_t z : Lr.brk)
+      if (Lr.alive[z]) check_later(Lr.par[z]);
+    for (int32_t u : leave) reparent(u, u);
+    for (i64 u = 0; u < n; ++u)
+      if (Lr.alive[u] && (Lr.par[u] == NONE || Ln.lab[Lr.par[u]] != Lr.lab[u]) && !mv[u])
+        die("node outside the frontier left its refined community's community");
+    // remaining members of the re-checked communities, in ascending id order
+    std::sort(CK.begin(), CK.end());
+    std::vector<std::vector<int32_t>> mem(CK.size());
+    std::vector<int32_t> slot(n, -1);
+    for (size_t k = 0; k < CK.size(); ++k) slot[CK[k]] = (int32_t)k;
+    for (i64 u = 0; u < n; ++u)
+      if (Lr.alive[u] && !mv[u] && Lr.par[u] != NONE && slot[Lr.par[u]] >= 0) mem[slot[Lr.par[u]]].push_back((int32_t)u);
+    std::vector<uint8_t> seen(n, 0);
+    std::vector<int32_t> comp, stack;
+    for (size_t k = 0; k < CK.size(); ++k) {
+      const int32_t X = CK[k];
+      const bool seed_stays = Lr.alive[X] && !mv[X] && Lr.par[X] == X;
+      for (int32_t s0 : mem[k]) {
+        if (seen[s0]) continue;
+        // one component by depth-first search over arcs among remaining members
+        comp.assign(1, s0);
+        stack.assign(1, s0);
+        seen[s0] = 1;
+        bool has_seed = false;
+        while (!stack.empty()) {
+          const int32_t u = stack.back();
+          stack.pop_back();
+          if (u == X) has_seed = true;
+          auto visit = [&](const Row& row) {
+            for (auto& p : row) {
+              const int32_t y = p.first;
+              if (!seen[y] && !mv[y] && Lr.par[y] == X && Lr.alive[y]) {
+                seen[y] = 1;
+                comp.push_back(y);
+                stack.push_back(y);
+              }
+            }
+          };
+          visit(Lr.out[u]);
+          if (directed) visit(Lr.in[u]);
+        }
+        if (seed_stays && has_seed) continue;
+        const int32_t name = *std::min_element(comp.begin(), comp.end());
+        for (int32_t u : comp) reparent(u, name);
+      }
+    }
+    Lr.brk.clear();
     return D;
   }
 
@@ -670,10 +749,9 @@ struct Orc {
 
   // ---------------------------------------------------------------- levels
   // Refine and aggregate level r (r < T); returns NextFrontier for r+1.
-  std::vector<int32_t> refine_aggregate(int r, const std::vector<int32_t>& Ustar, int rounds,
-                                        i64* merges_out) {
+  std::vector<int32_t> refine_aggregate(int r, const std::vector<int32_t>& Ustar, int rounds, i64* merges_out) {
     std::vector<int32_t> par_old(n, NONE);
-    std::vector<int32_t> D = dissolve(r, Ustar, par_old);
+    std::vector<int32_t> D = split(r, Ustar, par_old);
     i64 merges = refine_loop(r, D, rounds);
     if (merges_out) *merges_out = merges;
     std::vector<int32_t> rel(Ustar);
@@ -772,6 +850,7 @@ struct Orc {
       }
       aggregate(r, D, par_old, D);
     }
+    for (auto& Lq : lv) Lq.brk.clear();
     return ST_OK;
   }
 
@@ -824,6 +903,7 @@ struct Orc {
     for (auto& d : deltas) mnew += (directed || d.first.first == d.first.second) ? d.second : 2 * d.second;
     if (mnew >= ((i64)1 << 50)) return ST_OVERFLOW;
     // Algorithm 1: apply the batch to level 0, S_t = changed endpoints
+    for (auto& Lq : lv) Lq.brk.clear();
     std::vector<ERec> arcs;
     for (auto& d : deltas) {
       arcs.push_back(d);

@@ -63,6 +63,18 @@ __global__ void k_rec_flags(const u64* keys, const int64_t* delta, int64_t nrec,
   }
 }
 
+// endpoints of the entries a record removes (rows below t.rows)
+__global__ void k_track_del(const u64* keys, const int32_t* fdel, int64_t nrec, int bshift, DelTrack t) {
+  const u64 cmask = (((u64)1) << bshift) - 1;
+  GRID_STRIDE(i, nrec) {
+    if (!fdel[i]) continue;
+    const int64_t row = (int64_t)(keys[i] >> bshift);
+    if (row >= t.rows) continue;
+    stamp_add(t.stamp, t.ep, (int32_t)row, t.list, t.cnt);
+    stamp_add(t.stamp, t.ep, (int32_t)(keys[i] & cmask), t.list, t.cnt);
+  }
+}
+
 __global__ void k_seg_info(const u64* keys, int64_t nrec, int bshift, const int32_t* fhead, const int64_t* segid,
                            int64_t* seg_start, int64_t* seg_row) {
   GRID_STRIDE(i, nrec) {
@@ -350,7 +362,7 @@ static void compact_pool(SlackCSR<WT>& g, int64_t extra, CsrScratch& S, Prims& P
 
 template <class WT>
 void csr_apply(SlackCSR<WT>& g, const u64* keys, const int64_t* delta, int64_t nrec, int bshift, CsrScratch& S,
-               Prims& P, cudaStream_t s, DevScalars* d_sc) {
+               Prims& P, cudaStream_t s, DevScalars* d_sc, const DelTrack* trk) {
   if (nrec <= 0) return;
   S.pos.reserve(nrec + 1, s);
   S.lb.reserve(nrec + 1, s);
@@ -368,6 +380,10 @@ void csr_apply(SlackCSR<WT>& g, const u64* keys, const int64_t* delta, int64_t n
   k_rec_flags<<<gr, TPB, 0, s>>>(keys, delta, nrec, bshift, S.pos.p, S.oldw.p, S.fins.p, S.fdel.p, S.fhead.p,
                                  &d_sc->cnt[C_Z]);
   CKL("k_rec_flags");
+  if (trk) {
+    k_track_del<<<gr, TPB, 0, s>>>(keys, S.fdel.p, nrec, bshift, *trk);
+    CKL("k_track_del");
+  }
   scan_exclusive_i32_to(S.fins.p, S.pins.p, nrec + 1, nullptr, nrec + 1, nullptr, P, s);
   scan_exclusive_i32_to(S.fdel.p, S.pdel.p, nrec + 1, nullptr, nrec + 1, nullptr, P, s);
   // the segment count stays on the device: segment arrays are sized for one
@@ -435,6 +451,6 @@ template void csr_lookup<int32_t>(const SlackCSR<int32_t>&, const u64*, int64_t,
 template void csr_lookup<int64_t>(const SlackCSR<int64_t>&, const u64*, int64_t, int, int32_t*, int64_t*,
                                   CsrScratch&, Prims&, cudaStream_t, int32_t*);
 template void csr_apply<int32_t>(SlackCSR<int32_t>&, const u64*, const int64_t*, int64_t, int, CsrScratch&, Prims&,
-                                 cudaStream_t, DevScalars*);
+                                 cudaStream_t, DevScalars*, const DelTrack*);
 template void csr_apply<int64_t>(SlackCSR<int64_t>&, const u64*, const int64_t*, int64_t, int, CsrScratch&, Prims&,
-                                 cudaStream_t, DevScalars*);
+                                 cudaStream_t, DevScalars*, const DelTrack*);

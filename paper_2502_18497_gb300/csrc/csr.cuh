@@ -34,8 +34,20 @@ template <class WT>
 void csr_lookup(const SlackCSR<WT>& g, const u64* keys, int64_t nrec, int bshift, int32_t* pos, int64_t* oldw,
                 CsrScratch& S, Prims& P, cudaStream_t s, int32_t* d_nseg);
 
+// Where csr_apply records the endpoints (row and column) of the entries it
+// removes, for records whose row is below `rows`: a dedup stamp with its
+// epoch, a list and its device counter.
+struct DelTrack {
+  int32_t* stamp;
+  int32_t ep;
+  int32_t* list;
+  int32_t* cnt;
+  int64_t rows;
+};
+
 // Add delta to each record's entry: absent entries are inserted, entries that
-// reach zero are removed.  Synchronises once (pool growth decision).
+// reach zero are removed (their endpoints go to *trk when given).
+// Synchronises once (pool growth decision).
 template <class WT>
 void csr_apply(SlackCSR<WT>& g, const u64* keys, const int64_t* delta, int64_t nrec, int bshift, CsrScratch& S,
-               Prims& P, cudaStream_t s, DevScalars* d_sc);
+               Prims& P, cudaStream_t s, DevScalars* d_sc, const DelTrack* trk = nullptr);

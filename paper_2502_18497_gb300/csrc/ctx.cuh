@@ -25,11 +25,13 @@ struct LevelState {
   DBuf<int64_t> kout, kin;       // strengths (kin aliases kout when undirected)
   DBuf<uint8_t> alive;
   DBuf<int32_t> stA, lA;         // frontier A^r (dedup stamp + list)
+  DBuf<int32_t> stK, lK;         // endpoints of arcs deleted since the level was last refined
+  int32_t brk_ep = 0;            // epoch of stK
   bool allocated = false;
   void release() {
     out0.release(); in0.release(); out.release(); in.release(); children.release();
     lab.release(); par.release(); cnt.release(); kout.release(); kin.release(); alive.release();
-    stA.release(); lA.release();
+    stA.release(); lA.release(); stK.release(); lK.release();
     allocated = false;
   }
 };
@@ -38,8 +40,10 @@ struct LevelState {
 enum {
   K_U = 0, K_S, K_USTAR, K_MV, K_M0, K_D, K_C, K_R, K_R2, K_X, K_T, K_E, K_E2, K_CH, K_CAND, K_B,
   K_UNDEC, K_SMALL, K_MID, K_LARGE, K_REC, K_CREC, K_NREC, K_ERR, K_TMP, K_TMP2, K_CHG, K_MID2, K_TINY, K_CLU,
-  K_A0 = 32,  // K_A0 + r: |A^r|
-  K_COUNT = 48
+  K_G, K_CCF,
+  K_A0 = 32,   // K_A0 + r: |A^r|
+  K_BRK0 = 48, // K_BRK0 + r: endpoints of deleted level-r arcs
+  K_COUNT = 56
 };
 
 struct ldl_ctx {
@@ -63,8 +67,9 @@ struct ldl_ctx {
   int32_t epoch = 0;
 
   // dedup stamps (one int32 per node id) and lists
-  DBuf<int32_t> stS, stU, stMv, stB, stM0, stD, stC, stR, stX, stT, stE, stCh;
-  DBuf<int32_t> lU, lS, lUstar, lMv, lM0, lD, lC, lR, lR2, lX, lT, lE, lE2, lCh, lChg, lTmp;
+  DBuf<int32_t> stS, stU, stMv, stB, stM0, stD, stC, stR, stX, stT, stE, stCh, stL;
+  DBuf<int32_t> lU, lS, lUstar, lMv, lM0, lD, lC, lR, lR2, lX, lT, lE, lE2, lCh, lChg, lTmp, lG;
+  DBuf<int32_t> comp;  // connected-component labels of the refinement's re-check
   // candidates and accepted moves
   DBuf<int32_t> cv, csrc, cdst, cst, bv, bsrc, bdst, best, role;
   DBuf<int64_t> cghi;

@@ -1,7 +1,8 @@
 // Hierarchy maintenance of Algorithm 1: batch ingest and validation (the
 // batch's application to level 0), statistic repair along the parent chain
-// and InitFrontier, label push-down after supernode moves, TouchedRefined /
-// dissolve, and the Eq. 3 subtract-add aggregate repair with NextFrontier.
+// and InitFrontier, label push-down after supernode moves, the refined-community
+// split of TouchedRefined, and the Eq. 3 subtract-add aggregate repair with
+// NextFrontier.
 #include "chunks.cuh"
 #include "kern.cuh"
 
@@ -224,39 +225,6 @@ __global__ void k_push(ChunkMap m, const int32_t* lab_up, Adj<int32_t> ch_adj, i
 }
 
 // ---------------------------------------------------------------- dissolve
-__global__ void k_touched(const int32_t* lU, const int32_t* nU, const int32_t* par, int32_t* stD, int32_t epD,
-                          int32_t* lD, int32_t* nD, int32_t* stX, int32_t epX, int32_t* lX, int32_t* nX) {
-  const int32_t n = *nU;
-  for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-    const int32_t u = lU[k];
-    const int32_t p = par[u];
-    if (p < 0) stamp_add(stD, epD, u, lD, nD);
-    else stamp_add(stX, epX, p, lX, nX);
-  }
-}
-
-__global__ void k_collect(Adj<int32_t> ch_adj, ChunkMap m, int32_t* stD, int32_t epD, int32_t* lD, int32_t* nD) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  const int64_t total = m.pre[m.n_hint];
-  for (int64_t c = warp; c < total; c += nw) {
-    const Chunk ch = chunk_of(m, c);
-    if (ch.row < 0) continue;
-    const int64_t o = ch_adj.off[ch.v];
-    for (int32_t base = ch.k0; base < ch.k1; base += 32) {
-      const int32_t k = base + lane;
-      bool want = false;
-      int32_t u = 0;
-      if (k < ch.k1) {
-        u = ch_adj.col[o + k];
-        want = stamp_claim(stD, epD, u);
-      }
-      warp_append(want, u, lD, nD);
-    }
-  }
-}
-
 __global__ void k_stamp_list(const int32_t* l, const int32_t* n, int32_t* st, int32_t ep) {
   const int32_t m = *n;
   for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x) st[l[k]] = ep;
@@ -290,6 +258,172 @@ __global__ void k_reset_par(const int32_t* lD, int32_t nD, int32_t* par, int64_t
     kout1[u] = 0;
     if (directed) kin1[u] = 0;
     cnt1[u] = 0;
+  }
+}
+
+// ---------------------------------------------------------------- split
+// TouchedRefined of a batch update (see split()).  The refined communities
+// holding an endpoint of a deleted level-r arc are re-checked (before any
+// node leaves, so with their current parents).
+__global__ void k_brk_check(const int32_t* lK, const int32_t* nK, const uint8_t* alive, const int32_t* par,
+                            int32_t* stX, int32_t epX, int32_t* lX, int32_t* nX) {
+  const int32_t n = *nK;
+  for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const int32_t z = lK[k];
+    if (alive[z] && par[z] >= 0) stamp_add(stX, epX, par[z], lX, nX);
+  }
+}
+
+// A node of U* whose label differs from its refined community's label (or
+// that has no refined community) leaves it as a singleton named by its own
+// id; its old refined community is re-checked.
+__global__ void k_leave(const int32_t* lU, const int32_t* nU, const uint8_t* alive, const int32_t* lab,
+                        const int32_t* labN, int32_t* par, int32_t* par_old, const int64_t* kout, const int64_t* kin,
+                        int64_t* kout1, int64_t* kin1, int32_t* cnt1, int directed, int32_t* stL, int32_t epL,
+                        int32_t* stD, int32_t epD, int32_t* lD, int32_t* nD, int32_t* stX, int32_t epX, int32_t* lX,
+                        int32_t* nX) {
+  const int32_t n = *nU;
+  for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const int32_t u = lU[k];
+    if (!alive[u]) continue;
+    const int32_t X = par[u];
+    if (X >= 0 && labN[X] == lab[u]) continue;
+    stL[u] = epL;
+    par_old[u] = X;
+    if (X >= 0) {
+      stamp_add(stX, epX, X, lX, nX);
+      atomic_add_i64(&kout1[X], -kout[u]);
+      if (directed) atomic_add_i64(&kin1[X], -kin[u]);
+      atomicAdd(&cnt1[X], -1);
+    }
+    par[u] = u;
+    atomic_add_i64(&kout1[u], kout[u]);
+    if (directed) atomic_add_i64(&kin1[u], kin[u]);
+    atomicAdd(&cnt1[u], 1);
+    stamp_add(stD, epD, u, lD, nD);
+  }
+}
+
+// Remaining members of the re-checked refined communities (their children
+// that did not leave); each starts as its own component.
+__global__ void k_members(Adj<int32_t> ch_adj, ChunkMap m, const int32_t* stL, int32_t epL, int32_t* comp,
+                          int32_t* lG, int32_t* nG) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t total = m.pre[m.n_hint];
+  for (int64_t c = warp; c < total; c += nw) {
+    const Chunk ch = chunk_of(m, c);
+    if (ch.row < 0) continue;
+    const int64_t o = ch_adj.off[ch.v];
+    for (int32_t base = ch.k0; base < ch.k1; base += 32) {
+      const int32_t k = base + lane;
+      bool want = false;
+      int32_t u = 0;
+      if (k < ch.k1) {
+        u = ch_adj.col[o + k];
+        want = stL[u] != epL;
+        if (want) comp[u] = u;
+      }
+      warp_append(want, u, lG, nG);
+    }
+  }
+}
+
+// One hooking step of the connected components over the arcs between two
+// remaining members of the same refined community: the root label of the
+// larger side is lowered to the smaller label.  Labels only decrease and stay
+// member ids of the component, so the iteration ends with every component
+// labelled by its lowest member.
+template <class WT>
+__global__ void k_cc_hook(Adj<WT> out, Adj<WT> in, ChunkMap m, const int32_t* par, const int32_t* stL, int32_t epL,
+                          int32_t* comp, int32_t* changed) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t total = m.pre[m.n_hint];
+  bool any = false;
+  for (int64_t c = warp; c < total; c += nw) {
+    const Chunk ch = chunk_of(m, c);
+    if (ch.row < 0) continue;
+    const int32_t u = ch.v;
+    const int32_t X = par[u];
+    const Adj<WT>& A = ch.row ? in : out;
+    const int64_t o = A.off[u];
+    for (int32_t k = ch.k0 + lane; k < ch.k1; k += 32) {
+      const int32_t y = A.col[o + k];
+      if (y == u || par[y] != X || stL[y] == epL) continue;
+      const int32_t a = comp[u], b = comp[y];
+      if (a == b) continue;
+      const int32_t hi = a > b ? a : b, lo = a > b ? b : a;
+      if (atomicMin(&comp[hi], lo) > lo) any = true;
+    }
+  }
+  if (__any_sync(0xffffffffu, any) && lane == 0) atomicExch(changed, 1);
+}
+
+// Pointer jumping: every member's label follows its label's label (a bounded
+// number of steps per launch; the host repeats hooking and jumping until
+// nothing changes).
+__global__ void k_cc_jump(const int32_t* lG, const int32_t* nG, int32_t* comp, int32_t* changed) {
+  const int32_t n = *nG;
+  bool any = false;
+  for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const int32_t u = lG[k];
+    int32_t a = comp[u];
+    for (int step = 0; step < 64; ++step) {
+      const int32_t b = comp[a];
+      if (b == a) break;
+      a = b;
+    }
+    if (a != comp[u]) {
+      comp[u] = a;
+      any = true;
+    }
+  }
+  if (any) atomicExch(changed, 1);
+}
+
+// A component keeps its refined community's id when it holds the community's
+// seed node (the node with that id, still a member); any other component is
+// renamed after its lowest member.
+__global__ void k_rename(const int32_t* lG, const int32_t* nG, const int32_t* comp, const uint8_t* alive,
+                         const int32_t* stL, int32_t epL, int32_t* par, int32_t* par_old, const int64_t* kout,
+                         const int64_t* kin, int64_t* kout1, int64_t* kin1, int32_t* cnt1, int directed,
+                         int32_t* stD, int32_t epD, int32_t* lD, int32_t* nD) {
+  const int32_t n = *nG;
+  for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const int32_t u = lG[k];
+    const int32_t X = par[u];
+    const int32_t root = comp[u];
+    const bool keep = alive[X] && stL[X] != epL && par[X] == X && comp[X] == root;
+    if (keep) continue;
+    par_old[u] = X;
+    par[u] = root;
+    atomic_add_i64(&kout1[X], -kout[u]);
+    if (directed) atomic_add_i64(&kin1[X], -kin[u]);
+    atomicAdd(&cnt1[X], -1);
+    atomic_add_i64(&kout1[root], kout[u]);
+    if (directed) atomic_add_i64(&kin1[root], kin[u]);
+    atomicAdd(&cnt1[root], 1);
+    stamp_add(stD, epD, u, lD, nD);
+  }
+}
+
+// the listed nodes that are singleton refined communities
+__global__ void k_singletons(const int32_t* l, const int32_t* n, const int32_t* par, const int32_t* cnt1, int32_t* out,
+                             int32_t* nout) {
+  const int32_t m = *n;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < m; base += stride) {
+    const int64_t k = base + (threadIdx.x & 31);
+    int32_t u = 0;
+    bool want = false;
+    if (k < m) {
+      u = l[k];
+      want = par[u] == u && cnt1[u] == 1;
+    }
+    warp_append(want, u, out, nout);
   }
 }
 
@@ -707,9 +841,13 @@ static void combine_in_out(ldl_ctx& c, const u64* keys, const u64* vals, int64_t
   CK(cudaMemcpyAsync(c.rv2.p + nr, c.trv.p, sizeof(u64) * (size_t)nr, cudaMemcpyDeviceToDevice, c.s));
 }
 
-// apply sorted unique records to a level's adjacency (both directions)
+// apply sorted unique records to a level's adjacency (both directions); the
+// endpoints of arcs that disappear are recorded for the level's next
+// refinement
 static void apply_level(ldl_ctx& c, int r, DBuf<u64>& keys, DBuf<u64>& vals, int64_t nr) {
   if (nr <= 0) return;
+  LevelState& Lr = c.lv[r];
+  const DelTrack trk{Lr.stK.p, Lr.brk_ep, Lr.lK.p, c.dcnt + K_BRK0 + r, c.n};
   const u64* k = keys.p;
   const u64* v = vals.p;
   int64_t m = nr;
@@ -720,9 +858,9 @@ static void apply_level(ldl_ctx& c, int r, DBuf<u64>& keys, DBuf<u64>& vals, int
     m = 2 * nr;
   }
   if (r == 0)
-    csr_apply<int32_t>(c.lv[0].out0, k, (const int64_t*)v, m, c.bits, c.CS, c.P, c.s, c.d_sc);
+    csr_apply<int32_t>(c.lv[0].out0, k, (const int64_t*)v, m, c.bits, c.CS, c.P, c.s, c.d_sc, &trk);
   else
-    csr_apply<int64_t>(c.lv[r].out, k, (const int64_t*)v, m, c.bits, c.CS, c.P, c.s, c.d_sc);
+    csr_apply<int64_t>(c.lv[r].out, k, (const int64_t*)v, m, c.bits, c.CS, c.P, c.s, c.d_sc, &trk);
 }
 
 // Map records (keys, vals) of level q to level q+1, reduce, and apply there.
@@ -814,30 +952,16 @@ void pushdown(ldl_ctx& c, int r, int32_t epCh) {
   }
 }
 
-int32_t dissolve(ldl_ctx& c, int r, int32_t epD, int32_t epX, bool all_nodes) {
+// Static build: every alive level-r node becomes a singleton refined
+// community (refinement starts from singletons).  Returns |D| (list lD).
+int32_t dissolve_all(ldl_ctx& c, int r, int32_t epD) {
   LevelState& L = c.lv[r];
   LevelState& N = c.lv[r + 1];
   zero_cnt(c, K_D);
-  if (all_nodes) {
-    k_alive_list<<<grid_for(c.n, TPB), TPB, 0, c.s>>>(r ? L.alive.p : nullptr, c.n, c.lD.p, c.dcnt + K_D);
-    CKL("k_alive_list");
-    k_stamp_list<<<grid_for(c.n, TPB), TPB, 0, c.s>>>(c.lD.p, c.dcnt + K_D, c.stD.p, epD);
-    CKL("k_stamp_list");
-  } else {
-    const int32_t nu = rd_cnt(c, K_USTAR);
-    zero_cnt(c, K_X);
-    k_touched<<<grid_for(nu, TPB), TPB, 0, c.s>>>(c.lUstar.p, c.dcnt + K_USTAR, L.par.p, c.stD.p, epD, c.lD.p,
-                                                  c.dcnt + K_D, c.stX.p, epX, c.lX.p, c.dcnt + K_X);
-    CKL("k_touched");
-    const int32_t nx = rd_cnt(c, K_X);
-    if (nx > 0) {
-      Adj<int32_t> ch{L.children.off.p, L.children.len.p, L.children.col.p, L.children.w.p};
-      ChunkMap m = chunk_map(c, c.lX.p, c.dcnt + K_X, nx, L.children.len.p, nullptr);
-      k_collect<<<grid_for((int64_t)nx * 64, TPB, 16), TPB, 0, c.s>>>(ch, m, c.stD.p, epD, c.lD.p,
-                                                                           c.dcnt + K_D);
-      CKL("k_collect");
-    }
-  }
+  k_alive_list<<<grid_for(c.n, TPB), TPB, 0, c.s>>>(r ? L.alive.p : nullptr, c.n, c.lD.p, c.dcnt + K_D);
+  CKL("k_alive_list");
+  k_stamp_list<<<grid_for(c.n, TPB), TPB, 0, c.s>>>(c.lD.p, c.dcnt + K_D, c.stD.p, epD);
+  CKL("k_stamp_list");
   const int32_t nd = rd_cnt(c, K_D);
   if (nd > 0) {
     k_dissolve<<<grid_for(nd, TPB), TPB, 0, c.s>>>(c.lD.p, c.dcnt + K_D, L.par.p, c.par_old.p, L.kout.p,
@@ -847,11 +971,95 @@ int32_t dissolve(ldl_ctx& c, int r, int32_t epD, int32_t epX, bool all_nodes) {
   return nd;
 }
 
+int32_t singletons_of(ldl_ctx& c, int r, const int32_t* list, int idx_n, int64_t n_hint, int32_t* out, int idx_out) {
+  zero_cnt(c, idx_out);
+  if (n_hint > 0) {
+    k_singletons<<<grid_for(n_hint, TPB), TPB, 0, c.s>>>(list, c.dcnt + idx_n, c.lv[r].par.p, c.lv[r + 1].cnt.p, out,
+                                                         c.dcnt + idx_out);
+    CKL("k_singletons");
+  }
+  return rd_cnt(c, idx_out);
+}
+
 void reset_par(ldl_ctx& c, int r, int32_t nD) {
   if (nD <= 0) return;
   k_reset_par<<<grid_for(nD, TPB), TPB, 0, c.s>>>(c.lD.p, nD, c.lv[r].par.p, c.lv[r + 1].kout.p,
                                                   kin_of(c, r + 1), c.lv[r + 1].cnt.p, c.directed);
   CKL("k_reset_par");
+}
+
+template <class WT>
+static void cc_hook(ldl_ctx& c, int r, Adj<WT> out, Adj<WT> in, int32_t nG, int32_t epL) {
+  ChunkMap m = chunk_map(c, c.lG.p, c.dcnt + K_G, nG, out.len, c.directed ? in.len : nullptr);
+  k_cc_hook<WT><<<grid_for((int64_t)nG * 64, TPB, 16), TPB, 0, c.s>>>(out, in, m, c.lv[r].par.p, c.stL.p, epL,
+                                                                      c.comp.p, c.dcnt + K_CCF);
+  CKL("k_cc_hook");
+}
+
+// TouchedRefined of a batch update at level r < T (Sec. III-C: refinement
+// revisits the communities touched by accepted moves).  A refined community
+// lies inside one community, so every node of U* whose label differs from its
+// refined community's label (moved at level r, or relabelled from its members'
+// moves at level r-1), and every parentless new node, leaves it as a
+// singleton named by its own id.  The refined communities that lost a node or
+// hold an endpoint of a level-r arc deleted since the level was last refined
+// are re-checked for connectivity over the arcs among their remaining members
+// (connected components by hooking and pointer jumping): the component with
+// the community's seed node keeps the id, any other is renamed after its
+// lowest member.  Returns |D|, the nodes whose refined community changed
+// (list lD, stamp epD, old parents in par_old); the level's deletion list is
+// consumed.
+int32_t split(ldl_ctx& c, int r, int32_t epD, int32_t epX) {
+  LevelState& L = c.lv[r];
+  LevelState& N = c.lv[r + 1];
+  zero_cnt(c, K_D);
+  zero_cnt(c, K_X);
+  const int32_t nK = rd_cnt(c, K_BRK0 + r);
+  if (nK > 0) {
+    k_brk_check<<<grid_for(nK, TPB), TPB, 0, c.s>>>(L.lK.p, c.dcnt + K_BRK0 + r, L.alive.p, L.par.p, c.stX.p, epX,
+                                                    c.lX.p, c.dcnt + K_X);
+    CKL("k_brk_check");
+  }
+  const int32_t epL = c.next_epoch();
+  const int32_t nu = rd_cnt(c, K_USTAR);
+  if (nu > 0) {
+    k_leave<<<grid_for(nu, TPB), TPB, 0, c.s>>>(c.lUstar.p, c.dcnt + K_USTAR, L.alive.p, L.lab.p, N.lab.p, L.par.p,
+                                                c.par_old.p, L.kout.p, kin_of(c, r), N.kout.p, kin_of(c, r + 1),
+                                                N.cnt.p, c.directed, c.stL.p, epL, c.stD.p, epD, c.lD.p,
+                                                c.dcnt + K_D, c.stX.p, epX, c.lX.p, c.dcnt + K_X);
+    CKL("k_leave");
+  }
+  const int32_t nx = rd_cnt(c, K_X);
+  if (nx > 0) {
+    zero_cnt(c, K_G);
+    Adj<int32_t> ch{L.children.off.p, L.children.len.p, L.children.col.p, L.children.w.p};
+    ChunkMap m = chunk_map(c, c.lX.p, c.dcnt + K_X, nx, L.children.len.p, nullptr);
+    k_members<<<grid_for((int64_t)nx * 64, TPB, 16), TPB, 0, c.s>>>(ch, m, c.stL.p, epL, c.comp.p, c.lG.p,
+                                                                   c.dcnt + K_G);
+    CKL("k_members");
+    const int32_t nG = rd_cnt(c, K_G);
+    if (nG > 0) {
+      // hook and jump until a round changes nothing (labels only decrease, so
+      // this ends; a bound guards against an internal error)
+      for (int it = 0;; ++it) {
+        if (it > 100000) ldl_throw(LDL_E_INVALID, "internal: connected components did not converge");
+        zero_cnt(c, K_CCF);
+        if (r == 0) cc_hook<int32_t>(c, r, adj_out0(c), adj_in0(c), nG, epL);
+        else cc_hook<int64_t>(c, r, adj_out(c, r), adj_in(c, r), nG, epL);
+        k_cc_jump<<<grid_for(nG, TPB), TPB, 0, c.s>>>(c.lG.p, c.dcnt + K_G, c.comp.p, c.dcnt + K_CCF);
+        CKL("k_cc_jump");
+        if (rd_cnt(c, K_CCF) == 0) break;
+      }
+      k_rename<<<grid_for(nG, TPB), TPB, 0, c.s>>>(c.lG.p, c.dcnt + K_G, c.comp.p, L.alive.p, c.stL.p, epL, L.par.p,
+                                                   c.par_old.p, L.kout.p, kin_of(c, r), N.kout.p, kin_of(c, r + 1),
+                                                   N.cnt.p, c.directed, c.stD.p, epD, c.lD.p, c.dcnt + K_D);
+      CKL("k_rename");
+    }
+  }
+  // the deletions of this level are consumed
+  L.brk_ep = c.next_epoch();
+  zero_cnt(c, K_BRK0 + r);
+  return rd_cnt(c, K_D);
 }
 
 template <class WT>
@@ -1046,6 +1254,9 @@ void level_alloc(ldl_ctx& c, int r) {
   L.alive.exact(n);
   L.stA.exact(n);
   L.lA.exact(n);
+  L.stK.exact(n);
+  L.lK.exact(n);
+  CK(cudaMemsetAsync(L.stK.p, 0, sizeof(int32_t) * (size_t)n, c.s));
   CK(cudaMemsetAsync(L.lab.p, 0, sizeof(int32_t) * (size_t)n, c.s));
   CK(cudaMemsetAsync(L.par.p, 0xff, sizeof(int32_t) * (size_t)n, c.s));
   CK(cudaMemsetAsync(L.cnt.p, 0, sizeof(int32_t) * (size_t)n, c.s));

@@ -46,7 +46,10 @@ int64_t ingest(ldl_ctx& c, const ldl_update* upd, int64_t count, int on_device, 
 // the parent chain; marks InitFrontier in the A lists (epA per level).
 void repair_batch(ldl_ctx& c, int64_t na, const int32_t* epA, int32_t epT, int64_t dm);
 void pushdown(ldl_ctx& c, int r, int32_t epCh);
-int32_t dissolve(ldl_ctx& c, int r, int32_t epD, int32_t epX, bool all_nodes);
+int32_t dissolve_all(ldl_ctx& c, int r, int32_t epD);
+int32_t split(ldl_ctx& c, int r, int32_t epD, int32_t epX);
+// the listed level-r nodes that are singleton refined communities -> out
+int32_t singletons_of(ldl_ctx& c, int r, const int32_t* list, int idx_n, int64_t n_hint, int32_t* out, int idx_out);
 void aggregate(ldl_ctx& c, int r, int32_t epD, int32_t epC, int32_t epA_next, bool build);
 // static set-up of level 0 from a host CSR
 void upload_graph(ldl_ctx& c, int64_t nnz, const int64_t* row_ptr, const int32_t* col, const int32_t* w);

@@ -181,13 +181,13 @@ static void alloc_globals(ldl_ctx& c) {
   if (c.directed) c.Kin.exact(n);
   c.e.exact(n);
   DBuf<int32_t>* st[] = {&c.stS, &c.stU, &c.stMv, &c.stB, &c.stM0, &c.stD, &c.stC, &c.stR, &c.stX, &c.stT, &c.stE,
-                         &c.stCh};
+                         &c.stCh, &c.stL};
   for (auto* b : st) {
     b->exact(n);
     CK(cudaMemsetAsync(b->p, 0, sizeof(int32_t) * (size_t)n, c.s));
   }
   DBuf<int32_t>* ls[] = {&c.lU, &c.lS, &c.lUstar, &c.lMv, &c.lM0, &c.lD, &c.lC, &c.lR, &c.lR2, &c.lX, &c.lT,
-                         &c.lE, &c.lE2, &c.lCh, &c.lChg, &c.lTmp, &c.cv, &c.csrc, &c.cdst, &c.cst, &c.bv,
+                         &c.lE, &c.lE2, &c.lCh, &c.lChg, &c.lTmp, &c.lG, &c.comp, &c.cv, &c.csrc, &c.cdst, &c.cst, &c.bv,
                          &c.bsrc, &c.bdst, &c.oldlab, &c.par_old, &c.lab_before, &c.binT, &c.binS, &c.binM, &c.binM2, &c.binC, &c.binL};
   for (auto* b : ls) b->exact(n);
   c.best.exact(n);
@@ -217,7 +217,7 @@ static void free_all(ldl_ctx& c) {
                           &c.chunk_pre, &c.hub_ecnt, &c.hub_epre, &c.pb_hi};
   for (auto* b : b64) b->release();
   DBuf<int32_t>* b32[] = {&c.stS, &c.stU, &c.stMv, &c.stB, &c.stM0, &c.stD, &c.stC, &c.stR, &c.stX, &c.stT,
-                          &c.stE, &c.stCh, &c.lU, &c.lS, &c.lUstar, &c.lMv, &c.lM0, &c.lD, &c.lC, &c.lR,
+                          &c.stE, &c.stCh, &c.stL, &c.lG, &c.comp, &c.lU, &c.lS, &c.lUstar, &c.lMv, &c.lM0, &c.lD, &c.lC, &c.lR,
                           &c.lR2, &c.lX, &c.lT, &c.lE, &c.lE2, &c.lCh, &c.lChg, &c.lTmp, &c.cv, &c.csrc,
                           &c.cdst, &c.cst, &c.bv, &c.bsrc, &c.bdst, &c.best, &c.role, &c.oldlab, &c.par_old,
                           &c.lab_before, &c.binT, &c.binS, &c.binM, &c.binM2, &c.binC, &c.binL, &c.gkeys, &c.ndx, &c.ndx2,
@@ -308,8 +308,8 @@ static void move_loop(ldl_ctx& c, int r, int rounds, int32_t epU, int32_t epMv, 
 static int64_t refine_loop(ldl_ctx& c, int r, int rounds, int32_t epD) {
   const int32_t nD = rd_cnt(c, K_D);
   if (nD == 0) return 0;
-  CK(cudaMemcpyAsync(c.lR.p, c.lD.p, sizeof(int32_t) * (size_t)nD, cudaMemcpyDeviceToDevice, c.s));
-  set_cnt(c, K_R, nD);
+  // R starts as the singleton refined communities of D
+  singletons_of(c, r, c.lD.p, K_D, nD, c.lR.p, K_R);
   int32_t* R = c.lR.p;
   int32_t* R2 = c.lR2.p;
   int iR = K_R, iR2 = K_R2;
@@ -363,7 +363,7 @@ static void static_build(ldl_ctx& c) {
     level_alloc(c, r + 1);
     c.T = r + 1;
     const int32_t epD = c.next_epoch();
-    const int32_t nD = dissolve(c, r, epD, 0, true);
+    const int32_t nD = dissolve_all(c, r, epD);
     const int64_t merges = refine_loop(c, r, c.prm.M_static, epD);
     if (merges == 0) {
       reset_par(c, r, nD);
@@ -397,6 +397,8 @@ static void apply_batch(ldl_ctx& c, const ldl_update* upd, int64_t count, int on
   for (int r = 0; r <= T; ++r) {
     epA[r] = c.next_epoch();
     zero_cnt(c, K_A0 + r);
+    c.lv[r].brk_ep = c.next_epoch();
+    zero_cnt(c, K_BRK0 + r);
   }
   stage_begin(c);
   const int32_t epT = c.next_epoch();
@@ -430,7 +432,7 @@ static void apply_batch(ldl_ctx& c, const ldl_update* upd, int64_t count, int on
         stage_begin(c);
         const int32_t epD = c.next_epoch(), epX = c.next_epoch();
         sub_begin(c);
-        dissolve(c, r, epD, epX, false);
+        split(c, r, epD, epX);
         sub_end(c, SU_REF_DISSOLVE);
         sub_begin(c);
         refine_loop(c, r, c.prm.M, epD);
