@@ -20,11 +20,13 @@
  *     two arcs (i, j) and (j, i); a self-loop is one arc.  m = sum_ij w_ij.
  *   - Level-0 weights are int32 >= 1; aggregate weights and all totals int64.
  *   - Every entry point returns an ldl_status; LDL_OK is 0, and
- *     ldl_last_error() describes a failure.  A batch rejected by validation
- *     (RANGE, INVALID, NEG_WEIGHT, NO_EDGE, OVERFLOW) leaves the state exactly
- *     as it was before the call; NOMEM, CUDA or TIMEOUT in the middle of a
- *     batch may leave it partly updated, and the context should then be
- *     destroyed.
+ *     ldl_last_error() describes a failure.  A batch is atomic: a batch
+ *     rejected by validation (RANGE, INVALID, NEG_WEIGHT, NO_EDGE, OVERFLOW)
+ *     changes nothing, and an error in the middle of a batch (NOMEM, TIMEOUT,
+ *     an internal INVALID) is rolled back, leaving the state exactly as it
+ *     was before the call (see ldl_params.no_rollback).  A CUDA error that
+ *     leaves the device context broken can prevent the rollback; the context
+ *     then reports LDL_E_CUDA on every later call and must be destroyed.
  *   - Pointers marked "host" are read or written with ordinary host access;
  *     "device" pointers are GPU global memory of the context's device.
  *   - The context owns all device state.  Pointers it returns stay valid until
@@ -91,6 +93,16 @@ typedef struct {
    * decrease and must not exceed (32, 128, 1024, 2048), the largest degrees
    * whose hash tables stay at most half full (LDL_E_INVALID otherwise). */
   int32_t bin_deg[4];
+  /* 0 (the default): every ldl_apply_batch is atomic.  Before the batch
+   * changes anything the library copies the per-level node arrays and the
+   * community totals (about 21 bytes per node and level, 29 when directed,
+   * into a buffer kept by the context), and every adjacency update of the
+   * batch logs the old row tables, row contents and weights it overwrites,
+   * so that an error in the middle of the batch (NOMEM, TIMEOUT, an internal
+   * error) restores the state exactly as it was.  1: no copy and no log
+   * (saves that memory and time; an error in the middle of a batch then
+   * leaves the context unusable). */
+  int32_t no_rollback;
   void* cuda_stream;
 } ldl_params;
 
@@ -161,11 +173,11 @@ ldl_status ldl_create(const ldl_params* params, int64_t n, int64_t nnz, const in
  *   updates  host array (updates_on_device = 0) or device array (= 1) of
  *            ldl_update; read only, may be freed after the call.
  *   out      optional (may be NULL); filled on LDL_OK.
- * Errors: RANGE, INVALID, NEG_WEIGHT, NO_EDGE, OVERFLOW (the lowest-index
- * failing update decides; single-update checks come before sequence checks),
- * NOMEM, CUDA.  On these errors the state is unchanged.  TIMEOUT: a bounded
- * wait inside a device scan gave up (never expected; the state is then not
- * to be trusted and the context should be destroyed).
+ * Errors: RANGE, INVALID, NEG_WEIGHT, NO_EDGE, OVERFLOW (validation: the
+ * lowest-index failing update decides; single-update checks come before
+ * sequence checks), NOMEM, TIMEOUT (a bounded wait inside a device scan gave
+ * up), CUDA.  On every error the state is as it was before the call (unless
+ * no_rollback is set, or the CUDA context itself broke).
  */
 ldl_status ldl_apply_batch(ldl_ctx* ctx, const ldl_update* updates, int64_t count,
                            int32_t updates_on_device, ldl_result* out);
@@ -202,17 +214,35 @@ ldl_status ldl_apply_batches(ldl_ctx* const* ctxs, const ldl_update* const* upda
 /* Estimated device bytes of a context with n vertices and nnz stored entries. */
 ldl_status ldl_estimate_bytes(const ldl_params* params, int64_t n, int64_t nnz, int64_t* bytes);
 
+/* Estimated new device bytes one batch of `count` updates may allocate on ctx:
+ * the rollback snapshot (first batch), record buffers beyond their current
+ * capacity, and pool compactions of levels whose slack headroom is short.  A
+ * planning figure for admission, not a bound: a batch that runs out of memory
+ * anyway is rolled back (LDL_E_NOMEM, state unchanged). */
+ldl_status ldl_batch_estimate_bytes(const ldl_ctx* ctx, int64_t count, int64_t* bytes);
+
 /*
  * Served form: a request server with `workers` host threads.  Requests
  * (batches) on one context run in submission order; requests on different
  * contexts overlap on the device (give each context its own stream).
- * ldl_server_admit creates a context only when the device's free memory
- * covers its estimated footprint (LDL_E_NOMEM otherwise, nothing allocated).
- * ldl_server_submit copies the host updates and returns a ticket;
- * ldl_server_wait blocks until the ticket's batch is done (timeout_ms < 0:
- * no limit; LDL_E_TIMEOUT when it runs out) and reports its status, result,
- * time queued and time in service (microseconds).  A ticket can be waited
- * once.  ldl_server_destroy runs the queue dry and joins the workers.
+ * ldl_server_admit creates a context only when the device's free memory,
+ * less what running requests have reserved, covers its estimated footprint
+ * (LDL_E_NOMEM otherwise, nothing allocated); admissions are serialised.
+ * ldl_server_submit copies the host updates and returns a ticket.  Each
+ * request is admitted to the device by memory too: a worker starts the oldest
+ * request whose context is idle and whose estimated growth
+ * (ldl_batch_estimate_bytes) fits the free memory less the reservations of
+ * running requests; a request that does not fit waits (deferred, keeping its
+ * context's order) until a running request finishes, and one that runs out of
+ * memory while others run is rolled back and queued again.  ldl_server_wait
+ * blocks until the ticket's batch is done (timeout_ms < 0: no limit;
+ * LDL_E_TIMEOUT when it runs out) and reports its status, result, time queued
+ * (submission to first start) and time in service (microseconds).  The
+ * result's counters belong to that batch; its device pointers (labels,
+ * changed, the hierarchy) point at the context's live state, which later
+ * requests on the same context may already have changed by the time the wait
+ * returns.  A ticket can be waited once.  ldl_server_destroy runs the queue
+ * dry and joins the workers.
  */
 typedef struct ldl_server ldl_server;
 ldl_status ldl_server_create(int32_t workers, ldl_server** out);
@@ -223,6 +253,14 @@ ldl_status ldl_server_submit(ldl_server* server, ldl_ctx* ctx, const ldl_update*
 ldl_status ldl_server_wait(ldl_server* server, int64_t ticket, int32_t timeout_ms, ldl_status* status,
                            ldl_result* result, double* queue_us, double* service_us);
 void ldl_server_destroy(ldl_server* server);
+
+/* Requests deferred for memory at least once, and requests rolled back and
+ * queued again after running out of memory, since the server started. */
+ldl_status ldl_server_stats(ldl_server* server, int64_t* deferred, int64_t* retried);
+
+/* Test hook: admission decisions use `bytes` as the device's free memory
+ * (-1: ask the device again). */
+ldl_status ldl_server_debug_free_bytes(ldl_server* server, int64_t bytes);
 
 /* ----------------------------------------------------------------------------
  * Introspection (copies device state to host; for tests and tooling).
@@ -307,6 +345,11 @@ ldl_status ldl_get_kernel_stats(const ldl_ctx* ctx, double* out);
 /* Test hook: make the k-th device allocation from now on fail (k >= 1);
  * k = 0 disables.  Lets a test check that NOMEM leaves the state intact. */
 void ldl_debug_fail_alloc_after(int64_t k);
+
+/* Test hook: device allocations attempted by this library so far, in total
+ * and while a batch was in the middle of changing a context's state (after
+ * its snapshot); either pointer may be NULL. */
+void ldl_debug_alloc_counts(int64_t* all, int64_t* in_batch);
 
 /*
  * Test hook for the decoupling filter of Sec. III-E: runs the library's

@@ -6,6 +6,8 @@
 
 #include <atomic>
 #include <string>
+#include <utility>
+#include <vector>
 
 #include "../../include/ldl.h"
 
@@ -262,8 +264,40 @@ struct SlackCSR {
   DBuf<int32_t> col;
   DBuf<WT> w;
   int64_t pool_top = 0;  // host mirror of the first free pool slot
+  // Undo log of a batch that may be rolled back (csr_txn_*).  While logging,
+  // every update records, before it changes anything, the old offset, length
+  // and capacity of each row it touches, the old contents of the rows it
+  // rewrites and the old weights it overwrites; a compaction first saves the
+  // whole offset table, and the pool in use when the batch began is kept
+  // until the batch commits.  A rollback replays the events in reverse.
+  struct Event {
+    bool offsets;          // a saved offset table (before a compaction) or a row chunk
+    int64_t r0, nr;        // row entries
+    int64_t w0, nw;        // weight entries
+    int64_t o0;            // saved offsets
+    int32_t* col;          // the pool the update wrote into
+  };
+  bool logging = false;
+  int32_t* col0 = nullptr;  // the pool at the start of the batch
+  WT* w0 = nullptr;
+  int64_t cap0 = 0, top0 = 0;
+  std::vector<std::pair<int32_t*, WT*>> retired;
+  std::vector<Event> events;
+  int64_t rtop = 0, wtop = 0, ctop = 0, otop = 0;
+  DBuf<int64_t> lrow, loff, lsrc, lpos, lofs;
+  DBuf<int32_t> llen, lcap, lcol;
+  DBuf<WT> lw, lold;
   void release() {
     off.release(); len.release(); cap.release(); col.release(); w.release();
+    for (auto& x : retired) {
+      if (x.first != col.p) dfree(x.first);
+      if (x.second != w.p) dfree(x.second);
+    }
+    retired.clear();
+    lrow.release(); loff.release(); lsrc.release(); lpos.release(); lofs.release();
+    llen.release(); lcap.release(); lcol.release(); lw.release(); lold.release();
+    events.clear();
+    logging = false;
     pool_top = 0;
   }
 };

@@ -126,6 +126,69 @@ __global__ void k_update(const int64_t* off, const u64* keys, const int64_t* del
   }
 }
 
+// ---- undo log (batches that may be rolled back)
+// Row entries: row, old offset, length and capacity, and where its old
+// contents went in the content log (-1: not rewritten by this update).
+__global__ void k_log_rows(int64_t nseg, const int64_t* seg_row, const int64_t* off, const int32_t* len,
+                           const int32_t* cap, const int64_t* slen, const int64_t* soff, int64_t c0, int64_t* lrow,
+                           int64_t* loff, int32_t* llen, int32_t* lcap, int64_t* lsrc) {
+  GRID_STRIDE(s, nseg) {
+    const int64_t row = seg_row[s];
+    lrow[s] = row;
+    loff[s] = off[row];
+    llen[s] = len[row];
+    lcap[s] = cap[row];
+    lsrc[s] = slen[s] > 0 ? c0 + soff[s] : -1;
+  }
+}
+
+// Weight entries: pool position of each record's entry (-1: absent) and
+// the weight it holds before the update.
+template <class WT>
+__global__ void k_log_weights(const u64* keys, int64_t nrec, int bshift, const int64_t* off, const int32_t* pos,
+                              const int64_t* oldw, int64_t* lpos, WT* lold) {
+  GRID_STRIDE(i, nrec) {
+    lpos[i] = pos[i] >= 0 ? off[(int64_t)(keys[i] >> bshift)] + pos[i] : -1;
+    lold[i] = (WT)oldw[i];
+  }
+}
+
+// Rollback of one row chunk: offsets, lengths and capacities come back; a
+// rewritten row's old contents go back where they were when they lie in the
+// batch's first pool below its first free slot (anything else was written
+// into space that held no data of the state being restored).
+template <class WT>
+__global__ void k_undo_rows(int64_t nr, const int64_t* lrow, const int64_t* loff, const int32_t* llen,
+                            const int32_t* lcap, const int64_t* lsrc, const int32_t* lcol, const WT* lw,
+                            int64_t* off, int32_t* len, int32_t* cap, int32_t* col, WT* w, int restore_content,
+                            int64_t top0) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = warp; i < nr; i += nw) {
+    const int64_t row = lrow[i], o = loff[i], src = lsrc[i];
+    const int32_t l = llen[i];
+    if (lane == 0) {
+      off[row] = o;
+      len[row] = l;
+      cap[row] = lcap[i];
+    }
+    if (restore_content && src >= 0 && o + l <= top0)
+      for (int32_t k = lane; k < l; k += 32) {
+        col[o + k] = lcol[src + k];
+        w[o + k] = lw[src + k];
+      }
+  }
+}
+
+template <class WT>
+__global__ void k_undo_weights(int64_t nw, const int64_t* lpos, const WT* lold, WT* w, int64_t top0) {
+  GRID_STRIDE(i, nw) {
+    const int64_t p = lpos[i];
+    if (p >= 0 && p < top0) w[p] = lold[i];
+  }
+}
+
 __device__ inline int64_t find_seg(const int64_t* pre, int64_t nseg, int64_t t) {
   // last s with pre[s] <= t (pre is an exclusive scan, pre[0] = 0)
   int64_t lo = 0, hi = nseg;
@@ -349,10 +412,20 @@ static void compact_pool(SlackCSR<WT>& g, int64_t extra, CsrScratch& S, Prims& P
                                                                      g.w.p, c2, w2);
     CKL("k_compact_rows");
   }
+  if (g.logging) {  // the offset table as it was, for a rollback
+    g.lofs.reserve(g.otop + n, s, true);
+    CK(cudaMemcpyAsync(g.lofs.p + g.otop, g.off.p, sizeof(int64_t) * (size_t)n, cudaMemcpyDeviceToDevice, s));
+    g.events.push_back({true, 0, 0, 0, 0, g.otop, g.col.p});
+    g.otop += n;
+  }
   CK(cudaMemcpyAsync(g.off.p, S.rs.p, sizeof(int64_t) * (size_t)n, cudaMemcpyDeviceToDevice, s));
   CK(cudaStreamSynchronize(s));
-  dfree(g.col.p);
-  dfree(g.w.p);
+  if (g.logging) {
+    g.retired.emplace_back(g.col.p, g.w.p);  // freed when the batch commits
+  } else {
+    dfree(g.col.p);
+    dfree(g.w.p);
+  }
   g.col.p = c2;
   g.col.cap = pool;
   g.w.p = w2;
@@ -416,16 +489,47 @@ void csr_apply(SlackCSR<WT>& g, const u64* keys, const int64_t* delta, int64_t n
   const int64_t need = tot[0], nseg = tot[1], stotal = tot[2], wtotal = tot[3];
   const int gs = grid_for(nseg, TPB);
   if (g.pool_top + need > g.col.cap) compact_pool<WT>(g, need, S, P, s);
+  DBuf<WT>& sw = S.template sw_of<WT>();
+  if (g.logging) {
+    // everything a rollback needs, reserved and written before any change
+    g.lrow.reserve(g.rtop + nseg + 1, s, true);
+    g.loff.reserve(g.rtop + nseg + 1, s, true);
+    g.lsrc.reserve(g.rtop + nseg + 1, s, true);
+    g.llen.reserve(g.rtop + nseg + 1, s, true);
+    g.lcap.reserve(g.rtop + nseg + 1, s, true);
+    g.lpos.reserve(g.wtop + nrec + 1, s, true);
+    g.lold.reserve(g.wtop + nrec + 1, s, true);
+    g.lcol.reserve(g.ctop + stotal + 1, s, true);
+    g.lw.reserve(g.ctop + stotal + 1, s, true);
+    S.scol.reserve(stotal + 1, s);
+    sw.reserve(stotal + 1, s);
+    if (nseg > 0) {
+      k_log_rows<<<gs, TPB, 0, s>>>(nseg, S.segrow.p, g.off.p, g.len.p, g.cap.p, S.slen.p, S.soff.p, g.ctop,
+                                    g.lrow.p + g.rtop, g.loff.p + g.rtop, g.llen.p + g.rtop, g.lcap.p + g.rtop,
+                                    g.lsrc.p + g.rtop);
+      CKL("k_log_rows");
+    }
+    k_log_weights<WT><<<gr, TPB, 0, s>>>(keys, nrec, bshift, g.off.p, S.pos.p, S.oldw.p, g.lpos.p + g.wtop,
+                                         g.lold.p + g.wtop);
+    CKL("k_log_weights");
+    g.events.push_back({false, g.rtop, nseg, g.wtop, nrec, 0, g.col.p});
+    g.rtop += nseg;
+    g.wtop += nrec;
+  }
   k_update<WT><<<gr, TPB, 0, s>>>(g.off.p, keys, delta, nrec, bshift, S.pos.p, S.oldw.p, g.w.p);
   CKL("k_update");
   if (wtotal > 0) {
     S.scol.reserve(stotal + 1, s);
-    DBuf<WT>& sw = S.template sw_of<WT>();
     sw.reserve(stotal + 1, s);
     if (stotal > 0) {
       k_copy_scratch<WT><<<grid_for((stotal + 7) / 8, TPB), TPB, 0, s>>>(g.off.p, S.segrow.p, nseg, S.soff.p, stotal, g.col.p,
                                                                g.w.p, S.scol.p, sw.p);
       CKL("k_copy_scratch");
+      if (g.logging) {  // rows as they are before the rewrite (weights already updated)
+        CK(cudaMemcpyAsync(g.lcol.p + g.ctop, S.scol.p, sizeof(int32_t) * (size_t)stotal, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(g.lw.p + g.ctop, sw.p, sizeof(WT) * (size_t)stotal, cudaMemcpyDeviceToDevice, s));
+        g.ctop += stotal;
+      }
     }
     if (need > 0) {
       CK(cudaMemcpyAsync(&d_sc->pool_top, &g.pool_top, sizeof(int64_t), cudaMemcpyHostToDevice, s));
@@ -441,6 +545,83 @@ void csr_apply(SlackCSR<WT>& g, const u64* keys, const int64_t* delta, int64_t n
     CKL("k_set_len");
   }
 }
+
+template <class WT>
+void csr_txn_begin(SlackCSR<WT>& g) {
+  g.logging = true;
+  g.col0 = g.col.p;
+  g.w0 = g.w.p;
+  g.cap0 = g.col.cap;
+  g.top0 = g.pool_top;
+  g.retired.clear();
+  g.events.clear();
+  g.rtop = g.wtop = g.ctop = g.otop = 0;
+}
+
+template <class WT>
+void csr_txn_commit(SlackCSR<WT>& g, cudaStream_t s) {
+  if (!g.retired.empty()) {
+    CK(cudaStreamSynchronize(s));
+    for (auto& x : g.retired) {
+      dfree(x.first);
+      dfree(x.second);
+    }
+  }
+  g.retired.clear();
+  g.events.clear();
+  g.logging = false;
+}
+
+template <class WT>
+cudaError_t csr_txn_rollback(SlackCSR<WT>& g, cudaStream_t s) {
+  cudaError_t e = cudaSuccess;
+  // undo in reverse order; contents go back only into the batch's first pool
+  for (size_t k = g.events.size(); k-- > 0 && e == cudaSuccess;) {
+    const auto& ev = g.events[k];
+    if (ev.offsets) {
+      e = cudaMemcpyAsync(g.off.p, g.lofs.p + ev.o0, sizeof(int64_t) * (size_t)g.n, cudaMemcpyDeviceToDevice, s);
+      continue;
+    }
+    const int restore = ev.col == g.col0 ? 1 : 0;
+    if (ev.nr > 0) {
+      const int grid = (int)std::min<int64_t>((ev.nr + 7) / 8, 4096);
+      k_undo_rows<WT><<<grid, TPB, 0, s>>>(ev.nr, g.lrow.p + ev.r0, g.loff.p + ev.r0, g.llen.p + ev.r0,
+                                           g.lcap.p + ev.r0, g.lsrc.p + ev.r0, g.lcol.p, g.lw.p, g.off.p, g.len.p,
+                                           g.cap.p, g.col0, g.w0, restore, g.top0);
+      g_launches.fetch_add(1, std::memory_order_relaxed);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && restore && ev.nw > 0) {
+      const int grid = (int)std::min<int64_t>((ev.nw + TPB - 1) / TPB, 4096);
+      k_undo_weights<WT><<<grid, TPB, 0, s>>>(ev.nw, g.lpos.p + ev.w0, g.lold.p + ev.w0, g.w0, g.top0);
+      g_launches.fetch_add(1, std::memory_order_relaxed);
+      e = cudaGetLastError();
+    }
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  // back to the first pool; pools made during the batch go
+  auto drop = [&](int32_t* cp, WT* wp) {
+    if (cp != g.col0) dfree(cp);
+    if (wp != g.w0) dfree(wp);
+  };
+  drop(g.col.p, g.w.p);
+  for (auto& x : g.retired) drop(x.first, x.second);
+  g.retired.clear();
+  g.col.p = g.col0;
+  g.w.p = g.w0;
+  g.col.cap = g.w.cap = g.cap0;
+  g.pool_top = g.top0;
+  g.events.clear();
+  g.logging = false;
+  return e;
+}
+
+template void csr_txn_begin<int32_t>(SlackCSR<int32_t>&);
+template void csr_txn_begin<int64_t>(SlackCSR<int64_t>&);
+template void csr_txn_commit<int32_t>(SlackCSR<int32_t>&, cudaStream_t);
+template void csr_txn_commit<int64_t>(SlackCSR<int64_t>&, cudaStream_t);
+template cudaError_t csr_txn_rollback<int32_t>(SlackCSR<int32_t>&, cudaStream_t);
+template cudaError_t csr_txn_rollback<int64_t>(SlackCSR<int64_t>&, cudaStream_t);
 
 template void csr_build<int32_t>(SlackCSR<int32_t>&, int64_t, const u64*, const int64_t*, int64_t, int, int,
                                  CsrScratch&, Prims&, cudaStream_t);

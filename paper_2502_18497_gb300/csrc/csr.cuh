@@ -45,6 +45,16 @@ struct DelTrack {
   int64_t rows;
 };
 
+// Batch transactions on a CSR (see SlackCSR's undo log): begin logging,
+// commit (free pools replaced during the batch), or roll back to the state
+// at begin.  Rollback only copies (no allocation) and synchronises s.
+template <class WT>
+void csr_txn_begin(SlackCSR<WT>& g);
+template <class WT>
+void csr_txn_commit(SlackCSR<WT>& g, cudaStream_t s);
+template <class WT>
+cudaError_t csr_txn_rollback(SlackCSR<WT>& g, cudaStream_t s);
+
 // Add delta to each record's entry: absent entries are inserted, entries that
 // reach zero are removed (their endpoints go to *trk when given).
 // Synchronises once (pool growth decision).

@@ -121,6 +121,19 @@ struct ldl_ctx {
   int64_t* d_pub = nullptr;
   int64_t pub_seq = 0;
   std::string err;
+  bool broken = false;  // a failed rollback left the state unknown
+
+  // batch transaction (atomic batches): the snapshot of the node arrays and
+  // community totals, and the host scalars (each CSR keeps its undo log)
+  struct SnapSeg {
+    void* p;
+    size_t bytes, off;
+  };
+  DBuf<unsigned char> snap;
+  std::vector<SnapSeg> snap_segs;
+  int64_t snap_m = 0, snap_E = 0;
+  i128 snap_P = 0;
+  bool in_txn = false;
 
   int32_t next_epoch() { return ++epoch; }
 };

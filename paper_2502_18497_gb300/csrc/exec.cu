@@ -6,7 +6,8 @@
 // keeps its own order.  Served form: a request server with a worker pool;
 // requests on one context run in submission order, requests on different
 // contexts overlap on the device; new contexts are admitted only when the
-// device's free memory covers their estimated footprint.
+// device's free memory covers their estimated footprint, and each batch only
+// when the free memory covers its estimated growth (otherwise it waits).
 //
 // Neither form changes the arithmetic: every context's result is the one
 // it would reach alone.
@@ -79,6 +80,9 @@ struct Job {
   int64_t ticket;
   ldl_ctx* ctx;
   std::vector<ldl_update> upd;
+  int64_t need = 0;  // estimated new device bytes of this batch
+  bool counted_deferral = false;
+  int64_t wait_done = 0;  // after a rollback: run again once this many requests completed
   Clock::time_point submit, start, end;
   ldl_status status = LDL_OK;
   ldl_result res{};
@@ -87,8 +91,17 @@ struct Job {
 
 }  // namespace
 
+// Requests wait in one queue.  A worker takes the oldest request whose
+// context is idle and whose estimated memory need fits the device's free
+// memory minus what running requests have reserved; a request that does not
+// fit is deferred (it keeps its place, and later requests of its context wait
+// behind it) until a running request finishes.  Batches are atomic, so a
+// request that still runs out of memory while others run is rolled back and
+// queued again at the front instead of failing; with nothing else running it
+// fails with LDL_E_NOMEM.
 struct ldl_server {
   std::mutex mu;
+  std::mutex admit_mu;  // serialises admission checks with the creation they guard
   std::condition_variable cv_work, cv_done;
   std::deque<Job*> pending;
   std::map<int64_t, Job*> jobs;
@@ -97,31 +110,83 @@ struct ldl_server {
   int64_t next_ticket = 0;
   bool stop = false;
   double margin = 1.10;
+  int64_t free_override = -1;  // test hook: the device's free bytes (-1: ask CUDA)
+  int64_t reserved = 0;        // bytes reserved by running requests
+  int running = 0;
+  int64_t deferred = 0, retried = 0, completed = 0;
+
+  int64_t free_bytes() {
+    if (free_override >= 0) return free_override;
+    size_t f = 0, t = 0;
+    if (cudaMemGetInfo(&f, &t) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    return (int64_t)f;
+  }
+
+  // the oldest runnable request (context idle, memory available), or null;
+  // caller holds mu
+  Job* take() {
+    std::set<ldl_ctx*> blocked;  // contexts with an earlier deferred request
+    int64_t avail = -1;
+    for (auto it = pending.begin(); it != pending.end(); ++it) {
+      Job* j = *it;
+      if (busy.count(j->ctx) || blocked.count(j->ctx)) continue;
+      if (completed < j->wait_done && running > 0) {
+        blocked.insert(j->ctx);
+        continue;
+      }
+      if (running > 0) {
+        if (avail < 0) avail = free_bytes() - reserved;
+        if ((double)j->need * margin > (double)avail) {
+          if (!j->counted_deferral) {
+            j->counted_deferral = true;
+            ++deferred;
+          }
+          blocked.insert(j->ctx);
+          continue;
+        }
+      }
+      pending.erase(it);
+      return j;
+    }
+    return nullptr;
+  }
 
   void run() {
     std::unique_lock<std::mutex> lk(mu);
     for (;;) {
-      Job* job = nullptr;
-      for (auto it = pending.begin(); it != pending.end(); ++it)
-        if (!busy.count((*it)->ctx)) {
-          job = *it;
-          pending.erase(it);
-          break;
-        }
+      Job* job = take();
       if (!job) {
-        if (stop && pending.empty()) return;
+        if (stop && pending.empty() && running == 0) return;
         cv_work.wait(lk);
         continue;
       }
       busy.insert(job->ctx);
+      reserved += job->need;
+      ++running;
+      const bool others = running > 1;
       lk.unlock();
-      job->start = Clock::now();
-      job->status = ldl_apply_batch(job->ctx, job->upd.data(), (int64_t)job->upd.size(), 0, &job->res);
-      job->end = Clock::now();
+      if (job->start == Clock::time_point()) job->start = Clock::now();
+      const ldl_status st = ldl_apply_batch(job->ctx, job->upd.data(), (int64_t)job->upd.size(), 0, &job->res);
+      const Clock::time_point end = Clock::now();
       lk.lock();
       busy.erase(job->ctx);
-      job->done = true;
-      cv_done.notify_all();
+      reserved -= job->need;
+      --running;
+      if (st == LDL_E_NOMEM && (others || running > 0) && !stop) {
+        // rolled back: try again once memory held by other requests is free
+        ++retried;
+        job->wait_done = completed + 1;
+        pending.push_front(job);
+      } else {
+        job->status = st;
+        job->end = end;
+        job->done = true;
+        ++completed;
+        cv_done.notify_all();
+      }
       cv_work.notify_all();
     }
   }
@@ -143,12 +208,15 @@ ldl_status ldl_server_admit(ldl_server* s, const ldl_params* params, int64_t n, 
   int64_t need = 0;
   ldl_status st = ldl_estimate_bytes(params, n, nnz, &need);
   if (st != LDL_OK) return st;
-  size_t free_b = 0, total_b = 0;
-  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
-    cudaGetLastError();
-    return LDL_E_CUDA;
+  // one admission at a time: the free memory seen here is what the creation
+  // below gets (running requests' reservations are subtracted)
+  std::lock_guard<std::mutex> ak(s->admit_mu);
+  int64_t avail = 0;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    avail = s->free_bytes() - s->reserved;
   }
-  if ((double)free_b < (double)need * s->margin) return LDL_E_NOMEM;
+  if ((double)avail < (double)need * s->margin) return LDL_E_NOMEM;
   return ldl_create(params, n, nnz, row_ptr, col, w, out);
 }
 
@@ -157,6 +225,7 @@ ldl_status ldl_server_submit(ldl_server* s, ldl_ctx* ctx, const ldl_update* upda
   Job* j = new Job();
   j->ctx = ctx;
   j->upd.assign(updates, updates + count);
+  if (ldl_batch_estimate_bytes(ctx, count, &j->need) != LDL_OK) j->need = 0;
   j->submit = Clock::now();
   {
     std::lock_guard<std::mutex> lk(s->mu);
@@ -191,6 +260,22 @@ ldl_status ldl_server_wait(ldl_server* s, int64_t ticket, int32_t timeout_ms, ld
   if (service_us) *service_us = std::chrono::duration<double, std::micro>(j->end - j->start).count();
   s->jobs.erase(it);
   delete j;
+  return LDL_OK;
+}
+
+ldl_status ldl_server_stats(ldl_server* s, int64_t* deferred, int64_t* retried) {
+  if (!s) return LDL_E_INVALID;
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (deferred) *deferred = s->deferred;
+  if (retried) *retried = s->retried;
+  return LDL_OK;
+}
+
+ldl_status ldl_server_debug_free_bytes(ldl_server* s, int64_t bytes) {
+  if (!s) return LDL_E_INVALID;
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->free_override = bytes < 0 ? -1 : bytes;
+  s->cv_work.notify_all();
   return LDL_OK;
 }
 

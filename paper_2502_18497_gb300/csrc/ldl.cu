@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "kern.cuh"
@@ -25,8 +26,12 @@ void ldl_cuda_check(cudaError_t e, const char* what, const char* file, int line)
 
 static std::atomic<int64_t> g_fail_after{0};
 std::atomic<int64_t> g_launches{0};
+static std::atomic<int64_t> g_allocs{0}, g_txn_allocs{0};
+static thread_local bool t_in_txn = false;  // this thread is inside a batch transaction
 
 void* dalloc(size_t bytes) {
+  g_allocs.fetch_add(1, std::memory_order_relaxed);
+  if (t_in_txn) g_txn_allocs.fetch_add(1, std::memory_order_relaxed);
   int64_t k = g_fail_after.load();
   if (k > 0) {
     if (g_fail_after.fetch_sub(1) == 1) ldl_throw(LDL_E_NOMEM, "injected allocation failure");
@@ -230,6 +235,7 @@ static void free_all(ldl_ctx& c) {
   c.pb_c.release();
   c.gtab_clean = 0;
   c.upd.release();
+  c.snap.release();
   c.P.release();
   c.CS.release();
   if (c.d_sc) dfree(c.d_sc);
@@ -377,6 +383,85 @@ static void static_build(ldl_ctx& c) {
   check_scan_wait(c);
 }
 
+// ---------------------------------------------------------------- transactions
+// Every CSR of the hierarchy (adjacency of each level, children lists of each
+// level below the top), visited in a fixed order.
+template <class F>
+static void for_each_csr(ldl_ctx& c, F&& f) {
+  f(c.lv[0].out0);
+  for (int r = 1; r <= c.T; ++r) f(c.lv[r].out);
+  for (int r = 0; r < c.T; ++r) f(c.lv[r].children);
+}
+
+// Start of an atomic batch, after validation and before the first change:
+// the node arrays of every level and the community totals are copied into a
+// buffer the context keeps (the only allocation here), and every CSR starts
+// its undo log.
+static void txn_begin(ldl_ctx& c) {
+  const size_t n = (size_t)c.n;
+  c.snap_segs.clear();
+  size_t tot = 0;
+  auto add = [&](void* p, size_t bytes) {
+    if (!p || !bytes) return;
+    c.snap_segs.push_back({p, bytes, tot});
+    tot += (bytes + 255) & ~(size_t)255;
+  };
+  for (int r = 0; r <= c.T; ++r) {
+    LevelState& L = c.lv[r];
+    add(L.lab.p, 4 * n);
+    add(L.par.p, 4 * n);
+    add(L.cnt.p, 4 * n);
+    add(L.kout.p, 8 * n);
+    if (c.directed) add(L.kin.p, 8 * n);
+    add(L.alive.p, n);
+  }
+  add(c.Kout.p, 8 * n);
+  if (c.directed) add(c.Kin.p, 8 * n);
+  add(c.e.p, 8 * n);
+  c.snap.reserve((int64_t)tot, c.s);
+  for (auto& sg : c.snap_segs)
+    CK(cudaMemcpyAsync(c.snap.p + sg.off, sg.p, sg.bytes, cudaMemcpyDeviceToDevice, c.s));
+  for_each_csr(c, [&](auto& g) { csr_txn_begin(g); });
+  c.snap_m = c.m;
+  c.snap_E = c.E;
+  c.snap_P = c.Psum;
+  c.in_txn = true;
+  t_in_txn = true;
+}
+
+// The batch succeeded: pools replaced by compaction during it are freed.
+static void txn_commit(ldl_ctx& c) {
+  if (!c.in_txn) return;
+  t_in_txn = false;
+  for_each_csr(c, [&](auto& g) { csr_txn_commit(g, c.s); });
+  c.in_txn = false;
+}
+
+// The batch failed after it began changing the state: put everything back
+// (copies and frees only, no allocation).
+static void txn_rollback(ldl_ctx& c) {
+  if (!c.in_txn) return;
+  c.in_txn = false;
+  t_in_txn = false;
+  cudaGetLastError();
+  cudaError_t e = cudaStreamSynchronize(c.s);
+  for (auto& sg : c.snap_segs)
+    if (e == cudaSuccess) e = cudaMemcpyAsync(sg.p, c.snap.p + sg.off, sg.bytes, cudaMemcpyDeviceToDevice, c.s);
+  for_each_csr(c, [&](auto& g) {
+    const cudaError_t e2 = csr_txn_rollback(g, c.s);
+    if (e == cudaSuccess) e = e2;
+  });
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c.s);
+  c.m = c.snap_m;
+  c.E = c.snap_E;
+  c.Psum = c.snap_P;
+  c.gtab_clean = 0;  // hub hash tables may hold a half-finished sweep
+  if (e != cudaSuccess) {
+    c.broken = true;
+    ldl_throw(LDL_E_CUDA, std::string("rollback after a failed batch: ") + cudaGetErrorString(e));
+  }
+}
+
 // ---------------------------------------------------------------- batch update
 static void apply_batch(ldl_ctx& c, const ldl_update* upd, int64_t count, int on_device) {
   memset(&c.res, 0, sizeof(c.res));
@@ -393,6 +478,7 @@ static void apply_batch(ldl_ctx& c, const ldl_update* upd, int64_t count, int on
     c.res.n_changed = 0;
     return;
   }
+  if (!c.prm.no_rollback) txn_begin(c);
   std::vector<int32_t> epA(T + 2, 0);
   for (int r = 0; r <= T; ++r) {
     epA[r] = c.next_epoch();
@@ -581,14 +667,26 @@ ldl_status ldl_apply_batch(ldl_ctx* c, const ldl_update* updates, int64_t count,
     c->err = "bad batch arguments";
     return LDL_E_INVALID;
   }
+  if (c->broken) {
+    c->err = "the context's state was lost by an earlier failed rollback; destroy it";
+    return LDL_E_CUDA;
+  }
   try {
     DeviceScope ds(c->dev);
-    apply_batch(*c, updates, count, on_device);
-    CK(cudaStreamSynchronize(c->s));
+    try {
+      apply_batch(*c, updates, count, on_device);
+      CK(cudaStreamSynchronize(c->s));
+      txn_commit(*c);
+    } catch (const LdlError& e) {
+      c->err = e.msg;
+      txn_rollback(*c);
+      cudaGetLastError();
+      return e.st;
+    }
   } catch (const LdlError& e) {
-    c->err = e.msg;
+    c->err += std::string("; ") + e.msg;
     cudaGetLastError();
-    return e.st;
+    return LDL_E_CUDA;
   }
   if (out) {
     *out = c->res;
@@ -607,6 +705,31 @@ ldl_status ldl_apply_batch(ldl_ctx* c, const ldl_update* updates, int64_t count,
     out->refined = c->out_par;
     out->alive = c->out_alive;
   }
+  return LDL_OK;
+}
+
+ldl_status ldl_batch_estimate_bytes(const ldl_ctx* c, int64_t count, int64_t* bytes) {
+  if (!c || !bytes || count < 0) return LDL_E_INVALID;
+  const int64_t n = c->n, levels = c->T + 1;
+  int64_t b = 0;
+  if (!c->prm.no_rollback) {  // the snapshot buffer, allocated by the first atomic batch
+    const int64_t want = levels * n * (c->directed ? 29 : 21) + n * (c->directed ? 24 : 16);
+    if (c->snap.cap < want) b += want;
+  }
+  // records of the repair and of the aggregate levels: a budget of 8 per
+  // update and level beyond the record buffers' current capacity, each kept
+  // in about four 16-byte buffers (keys, values, sort scratch)
+  const int64_t rec = 16 * count * levels;
+  b += std::max<int64_t>(0, rec - c->rk.cap) * 16 * 4;
+  // a pool whose headroom is short may be compacted into one twice its live
+  // capacity, kept beside the old one until the batch commits
+  auto pool = [&](const auto& g, int64_t wbytes) {
+    const int64_t head = g.col.cap - g.pool_top;
+    if (head < g.pool_top / 4 + 4 * count) b += 2 * (g.pool_top + 4 * count) * (4 + wbytes);
+  };
+  pool(c->lv[0].out0, 4);
+  for (int r = 1; r <= c->T; ++r) pool(c->lv[r].out, 8);
+  *bytes = b;
   return LDL_OK;
 }
 
@@ -757,6 +880,11 @@ ldl_status ldl_set_timing(ldl_ctx* c, int32_t on) {
 }
 
 void ldl_debug_fail_alloc_after(int64_t k) { g_fail_after.store(k > 0 ? k : 0); }
+
+void ldl_debug_alloc_counts(int64_t* all, int64_t* in_batch) {
+  if (all) *all = g_allocs.load();
+  if (in_batch) *in_batch = g_txn_allocs.load();
+}
 
 ldl_status ldl_debug_scan_wait_timeout(void) {
   try {

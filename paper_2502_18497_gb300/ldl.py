@@ -29,7 +29,8 @@ class ldl_params(C.Structure):
     _fields_ = [("directed", C.c_int32), ("gamma_num", C.c_int32), ("gamma_den", C.c_int32),
                 ("N", C.c_int32), ("L", C.c_int32), ("M", C.c_int32), ("M_static", C.c_int32),
                 ("alpha_inv", C.c_int32), ("beta_inv", C.c_int32), ("cluster_max_deg", C.c_int32),
-                ("kernel_stats", C.c_int32), ("bin_deg", C.c_int32 * 4), ("cuda_stream", C.c_void_p)]
+                ("kernel_stats", C.c_int32), ("bin_deg", C.c_int32 * 4), ("no_rollback", C.c_int32),
+                ("cuda_stream", C.c_void_p)]
 
 
 class ldl_result(C.Structure):
@@ -93,6 +94,10 @@ def load(path: Optional[str] = None):
         "ldl_server_wait": (I32, [P, I64, I32, P, P, P, P]),
         "ldl_server_destroy": (None, [P]),
         "ldl_debug_decouple": (I32, [P, I64, P, P, P, P, P, P]),
+        "ldl_debug_alloc_counts": (None, [P, P]),
+        "ldl_batch_estimate_bytes": (I32, [P, I64, P]),
+        "ldl_server_stats": (I32, [P, P, P]),
+        "ldl_server_debug_free_bytes": (I32, [P, I64]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -110,11 +115,20 @@ def exported_symbols():
             "ldl_set_timing", "ldl_debug_fail_alloc_after", "ldl_debug_scan_wait_timeout", "ldl_copy_changed", "ldl_copy_changed_noalloc", "ldl_launch_count",
             "ldl_set_kernel_stats", "ldl_get_kernel_stats", "ldl_apply_batches", "ldl_estimate_bytes",
             "ldl_server_create", "ldl_server_admit", "ldl_server_submit", "ldl_server_wait",
-            "ldl_server_destroy", "ldl_debug_decouple"]
+            "ldl_server_destroy", "ldl_debug_decouple", "ldl_debug_alloc_counts", "ldl_batch_estimate_bytes",
+            "ldl_server_stats", "ldl_server_debug_free_bytes"]
 
 
 def launch_count() -> int:
     return int(load().ldl_launch_count())
+
+
+def alloc_counts():
+    """(all, in_batch): device allocations attempted by the library, and those
+    made while a batch was changing a context's state."""
+    a, b = C.c_int64(), C.c_int64()
+    load().ldl_debug_alloc_counts(C.byref(a), C.byref(b))
+    return int(a.value), int(b.value)
 
 
 def _ptr(a):
@@ -136,7 +150,8 @@ class Level:
 
 
 def make_params(directed=False, gamma_num=1, gamma_den=1, N=2, L=4, M=5, M_static=20, alpha_inv=1000,
-                beta_inv=100, stream=None, cluster_max_deg=0, kernel_stats=0, bin_deg=None) -> ldl_params:
+                beta_inv=100, stream=None, cluster_max_deg=0, kernel_stats=0, bin_deg=None,
+                no_rollback=0) -> ldl_params:
     p = ldl_params()
     load().ldl_default_params(C.byref(p))
     p.directed, p.gamma_num, p.gamma_den = int(directed), gamma_num, gamma_den
@@ -144,6 +159,7 @@ def make_params(directed=False, gamma_num=1, gamma_den=1, N=2, L=4, M=5, M_stati
     p.alpha_inv, p.beta_inv = alpha_inv, beta_inv
     p.cluster_max_deg = cluster_max_deg
     p.kernel_stats = kernel_stats
+    p.no_rollback = int(no_rollback)
     if bin_deg is not None:
         for i, t in enumerate(bin_deg):
             p.bin_deg[i] = int(t)
@@ -164,10 +180,10 @@ class LDL:
 
     def __init__(self, n, row_ptr, col, w, directed=False, gamma_num=1, gamma_den=1, N=2, L=4, M=5,
                  M_static=20, alpha_inv=1000, beta_inv=100, stream=None, server=None, cluster_max_deg=0,
-                 kernel_stats=0, bin_deg=None):
+                 kernel_stats=0, bin_deg=None, no_rollback=0):
         lib = load()
         p = make_params(directed, gamma_num, gamma_den, N, L, M, M_static, alpha_inv, beta_inv, stream,
-                        cluster_max_deg, kernel_stats, bin_deg)
+                        cluster_max_deg, kernel_stats, bin_deg, no_rollback)
         self.n = int(n)
         self.directed = bool(directed)
         rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
@@ -393,6 +409,20 @@ class Server:
         if rc != LDL_OK:
             raise LdlError(rc, "wait")
         return int(st.value), res, q.value, sv.value
+
+    def stats(self):
+        """(deferred, retried): requests deferred for memory, and requests
+        rolled back after running out of memory and queued again."""
+        a, b = C.c_int64(), C.c_int64()
+        st = load().ldl_server_stats(self._h, C.byref(a), C.byref(b))
+        if st != LDL_OK:
+            raise LdlError(st, "stats")
+        return int(a.value), int(b.value)
+
+    def debug_free_bytes(self, nbytes: int):
+        """Test hook: admission treats `nbytes` as the device's free memory
+        (-1: ask the device)."""
+        load().ldl_server_debug_free_bytes(self._h, int(nbytes))
 
     def close(self):
         if getattr(self, "_h", None):

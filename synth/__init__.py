@@ -5,6 +5,6 @@ It holds none of the community-detection arithmetic.
 """
 from .streams import (  # noqa: F401
     Graph, csr_from_arcs, unit_f64, splitmix64, uniform_u64, planted_partition, rmat_directed,
-    random_small_graph, EdgeStream, planted_stream, rmat_stream, random_batch,
+    random_small_graph, EdgeStream, planted_stream, rewire_stream, rmat_stream, random_batch,
     powerlaw_planted, powerlaw_stream, config_graph, cached, rmat_workload, multi_graph_workload, sized_stream, INSERT, DELETE, REWEIGHT,
 )

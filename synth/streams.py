@@ -430,6 +430,31 @@ def planted_stream(g: Graph, batches: int = 10, size: int = 100, seed: int = 1,
     return [st.make_batch(n_ins, n_del, n_rew, sampler, wmax) for _ in range(batches)]
 
 
+def rewire_stream(g: Graph, batches: int = 10, size: int = 500, seed: int = 1, block: int = 100,
+                  intra_frac: float = 5.0 / 6.0, wmax: int = 1):
+    """Edge rewiring of a planted-partition graph (the dynamic SBM-style
+    sequences of the paper's synthetic study): every batch deletes size/2
+    existing edges and inserts size/2 new ones drawn by the planted model
+    (intra_frac of them inside a block), so the average degree stays put."""
+    st = EdgeStream.from_graph(g, seed * 1000 + 17)
+    n = g.n
+    nb = n // block
+
+    def sampler(base, cnt):
+        idx = np.arange(base, base + cnt, dtype=np.int64)
+        v = uniform_u64(seed, 56, idx, n)
+        intra = unit_f64(seed, 57, idx) < intra_frac
+        r = uniform_u64(seed, 58, idx, block - 1)
+        r = r + (r >= v % block)
+        same = (v // block) * block + r
+        ob = uniform_u64(seed, 59, idx, nb - 1)
+        ob = ob + (ob >= v // block)
+        other = ob * block + uniform_u64(seed, 60, idx, block)
+        return v, np.where(intra, same, other)
+    half = size // 2
+    return [st.make_batch(half, size - half, 0, sampler, wmax) for _ in range(batches)]
+
+
 def rmat_stream(g: Graph, batches: int = 100, size: int = 10000, seed: int = 2,
                 probs=(0.57, 0.19, 0.19, 0.05), wmax: int = 16, ins_frac: float = 0.8):
     """Batches for the directed R-MAT graph: ins_frac inserts of new arcs drawn

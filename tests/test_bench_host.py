@@ -41,7 +41,7 @@ def test_reference_arm_prints_its_contract_line():
     import sys
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--rmat-scale", "12",
-                          "--steps", "2", "--warmup", "0", "--ref-budget", "5"],
+                          "--steps", "2", "--warmup", "1", "--cpu-budget", "5"],
                          capture_output=True, text=True, timeout=600, cwd=root)
     assert out.returncode == 0, out.stderr[-2000:]
     lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
@@ -51,3 +51,4 @@ def test_reference_arm_prints_its_contract_line():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert d["higher_is_better"] is True and d["vs_baseline"] is None
+    assert d["warmup"] == 1 and "batches 1..2" in d["cpu_baseline"]["sample"]

@@ -53,6 +53,30 @@ def test_batched_form_matches_each_graph_alone(torch_mod):
         assert not msgs, "\n".join(msgs[:6])
 
 
+def test_batched_form_full_size(torch_mod):
+    """The batched-form workload at its benchmark size: 512 independent graphs
+    (vertex counts log-uniform 10^3..10^5, even graphs directed R-MAT, odd
+    graphs undirected planted partitions, ~115M stored entries), two steps of
+    0.1%-of-edges batches applied to all graphs at once from 16 host threads,
+    every graph then compared with its own oracle run (partition, hierarchy
+    arrays, community totals and the exact numerator)."""
+    from paper_2502_18497_gb300 import LDL, apply_batches
+    from synth import multi_graph_workload
+    work = multi_graph_workload(512, steps=2)
+    streams = [torch_mod.cuda.Stream() for _ in range(16)]
+    gpus = [LDL.from_graph(g, stream=streams[k % 16].cuda_stream) for k, (g, _) in enumerate(work)]
+    for step in range(2):
+        apply_batches(gpus, [bs[step] for _, bs in work], threads=16)
+    torch_mod.cuda.synchronize()
+    for k, ((g, bs), d) in enumerate(zip(work, gpus)):
+        o = Oracle(g)
+        for b in bs:
+            assert o.apply(b) == 0
+        msgs = compare_states(o, d, f"graph {k}", adjacency=(k % 32 == 0))
+        assert not msgs, "\n".join(msgs[:6])
+        d.close()
+
+
 def test_served_form_alone_equals_mix(torch_mod):
     from paper_2502_18497_gb300 import Server
     work = _graphs(4)
@@ -78,6 +102,36 @@ def test_served_form_alone_equals_mix(torch_mod):
         for t in tickets[k]:
             st, res, queue_us, service_us = srv.wait(t)
             assert st == 0 and service_us > 0 and queue_us >= 0
+    for k, ((g, bs), d) in enumerate(zip(work, gpus)):
+        o = Oracle(g)
+        for b in bs:
+            assert o.apply(b) == 0
+        msgs = compare_states(o, d, f"tenant {k}")
+        assert not msgs, "\n".join(msgs[:6])
+    srv.close()
+
+
+def test_served_form_defers_batches_under_a_memory_cap(torch_mod):
+    """Per-batch admission by free memory: with the server told the device
+    has almost no free memory, requests that would overlap running ones are
+    deferred until those finish (each runs alone when nothing else runs), the
+    work still completes, and every tenant's state equals its oracle run."""
+    from paper_2502_18497_gb300 import Server
+    work = _graphs(4)
+    srv = Server(workers=4)
+    streams = [torch_mod.cuda.Stream() for _ in work]
+    gpus = [srv.admit(g, stream=s.cuda_stream) for (g, _), s in zip(work, streams)]
+    srv.debug_free_bytes(1)  # nothing fits beside a running request
+    tickets = []
+    for step in range(3):
+        for k in range(len(work)):
+            tickets.append(srv.submit(gpus[k], work[k][1][step]))
+    for t in tickets:
+        st, res, queue_us, service_us = srv.wait(t)
+        assert st == 0 and service_us > 0
+    deferred, retried = srv.stats()
+    assert deferred > 0
+    srv.debug_free_bytes(-1)
     for k, ((g, bs), d) in enumerate(zip(work, gpus)):
         o = Oracle(g)
         for b in bs:

@@ -103,16 +103,17 @@ def test_rmat_directed_reduced(ldl, cluster_max_deg, bin_deg):
 
 def test_rmat_directed_full_size(ldl):
     """The benchmark workload at full size (directed R-MAT, 2^20 vertices,
-    2^24 arcs): the static build and the first two batches of 10^4 updates,
-    compared bit for bit including every level's adjacency."""
+    2^24 arcs): the static build and the first 12 batches of 10^4 updates,
+    compared bit for bit after every batch (every level's adjacency after
+    the first two, the last and every fourth)."""
     from synth import rmat_workload
-    g, bs = rmat_workload(2)
+    g, bs = rmat_workload(12)
     o, d = _pair(ldl, g)
     _assert_same(o, d, "create")
     for t, b in enumerate(bs):
         assert o.apply(b) == 0
         d.apply(b)
-        _assert_same(o, d, f"batch {t}")
+        _assert_same(o, d, f"batch {t}", adjacency=(t < 2 or t % 4 == 3 or t == len(bs) - 1))
 
 
 @pytest.mark.parametrize("bad,status", [
@@ -164,6 +165,40 @@ def test_injected_allocation_failure_at_create(ldl):
     ldl.load().ldl_debug_fail_alloc_after(0)
     o, d = _pair(ldl, g)
     _assert_same(o, d, "after injected failures")
+
+
+@pytest.mark.parametrize("directed", [False, True])
+def test_injected_allocation_failures_during_a_batch_roll_back(ldl, directed):
+    """A device allocation that fails in the middle of ldl_apply_batch (after
+    the batch began changing the state) returns NOMEM and leaves the whole
+    state bit-identical to the oracle's state before the batch; the same batch
+    then applies and matches the oracle after it.  Failures are injected at
+    the 1st, 2nd, ... allocation of successive attempts until one succeeds."""
+    if directed:
+        g = rmat_directed(scale=11, arcs=1 << 14, seed=33)
+        batches = rmat_stream(g, batches=4, size=3000, seed=33)
+    else:
+        g = planted_partition(n=2000, block=50, seed=31)
+        batches = planted_stream(g, batches=4, size=600, seed=31, block=50)
+    o, d = _pair(ldl, g)
+    mid_batch = 0
+    for t, b in enumerate(batches):
+        for k in range(1, 400):
+            _, before = ldl.alloc_counts()
+            ldl.load().ldl_debug_fail_alloc_after(k)
+            st = d.try_apply(b)
+            ldl.load().ldl_debug_fail_alloc_after(0)
+            if st == 0:
+                break
+            assert st == ldl.LDL_E_NOMEM, st
+            _, after = ldl.alloc_counts()
+            mid_batch += after > before
+            _assert_same(o, d, f"batch {t} after a failure at allocation {k}")
+        else:
+            raise AssertionError("the batch never succeeded")
+        assert o.apply(b) == 0
+        _assert_same(o, d, f"batch {t} applied")
+    assert mid_batch > 0
 
 
 def test_bounded_scan_wait_reports_timeout(ldl):
