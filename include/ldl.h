@@ -263,11 +263,45 @@ ldl_status ldl_server_stats(ldl_server* server, int64_t* deferred, int64_t* retr
 ldl_status ldl_server_debug_free_bytes(ldl_server* server, int64_t bytes);
 
 /* ----------------------------------------------------------------------------
+ * Checkpoint / resume and vertex-set growth.  The hierarchy H_t is the state
+ * a batch update resumes from (Sec. III-A); the vertex set V_t may change
+ * between batches (Sec. II).
+ * -------------------------------------------------------------------------- */
+
+/* Writes the context's whole state (parameters, every level's graph, parent
+ * map, labels, strengths and node existence, the community totals and the
+ * exact modularity numerator) to a file.  LDL_E_INVALID if the file cannot
+ * be written; the context is unchanged. */
+ldl_status ldl_save(const ldl_ctx* ctx, const char* path);
+
+/* Creates a context from a file written by ldl_save, on the current device,
+ * without rerunning the static build: it continues exactly where the saved
+ * context stood.  params may be NULL; otherwise only its cuda_stream,
+ * kernel_stats, cluster_max_deg, bin_deg and no_rollback are taken (the
+ * method's parameters N, L, M, alpha, beta, gamma are those saved).
+ * LDL_E_INVALID for a missing, truncated or inconsistent file (the reason is
+ * in ldl_last_error(NULL)); NOMEM, CUDA. */
+ldl_status ldl_load(const char* path, const ldl_params* params, ldl_ctx** out);
+
+/* Grows the vertex set to n_new >= n: the new vertices n .. n_new-1 are
+ * isolated, each its own community and, at every level, its own node whose
+ * parent is the node of the same id one level up (so later batches may
+ * connect them like any vertex).  The modularity is unchanged.  The context
+ * keeps its handle; device pointers it returned before are invalid after
+ * the call.  On an error the context is unchanged (INVALID for n_new < n or
+ * above 2^31-2, NOMEM, CUDA). */
+ldl_status ldl_grow(ldl_ctx* ctx, int64_t n_new);
+
+/* ----------------------------------------------------------------------------
  * Introspection (copies device state to host; for tests and tooling).
  * -------------------------------------------------------------------------- */
 
 /* Hierarchy height T+1. */
 int32_t ldl_levels(const ldl_ctx* ctx);
+
+/* Vertex count n, and 1 for a directed graph (0 undirected); 0 for NULL. */
+int64_t ldl_num_vertices(const ldl_ctx* ctx);
+int32_t ldl_is_directed(const ldl_ctx* ctx);
 
 /*
  * Per-node arrays of level r (0 <= r <= T), each of length n (host, caller

@@ -1226,6 +1226,42 @@ int32_t orc_set_partition(void* h, const int32_t* lab) {
   return 0;
 }
 
+// Growth of the vertex set (Sec. II: V_t may change between batches): the
+// vertices n .. n_new-1 are added isolated, each its own community and, at
+// every level, its own node whose parent is the node of the same id one level
+// up.  Returns 0, or 1 when n_new < n.
+int32_t orc_grow(void* h, int64_t n_new) {
+  Orc* o = (Orc*)h;
+  if (n_new < o->n || n_new > INT32_MAX) return 1;
+  const int64_t n = o->n;
+  for (int r = 0; r <= o->T; ++r) {
+    Level& L = o->lv[r];
+    L.out.resize(n_new);
+    if (o->directed) L.in.resize(n_new);
+    L.kout.resize(n_new, 0);
+    L.kin.resize(n_new, 0);
+    L.lab.resize(n_new);
+    L.par.resize(n_new);
+    L.cnt.resize(n_new, 1);
+    L.alive.resize(n_new, 1);
+    for (int64_t v = n; v < n_new; ++v) {
+      L.lab[v] = (int32_t)v;
+      L.par[v] = r < o->T ? (int32_t)v : NONE;
+    }
+  }
+  o->Kout.resize(n_new, 0);
+  o->Kin.resize(n_new, 0);
+  o->e.resize(n_new, 0);
+  o->acc.resize(n_new, 0);
+  o->acc_has.resize(n_new, 0);
+  o->flag.resize(n_new, 0);
+  o->flag2.resize(n_new, 0);
+  o->oldlab.resize(n_new, 0);
+  o->role.resize(n_new, 0);
+  o->n = n_new;
+  return 0;
+}
+
 // Decoupling filter on an explicit candidate list; accepted[k] = 1 or 0.
 void orc_decouple(int64_t count, const int32_t* v, const int32_t* src, const int32_t* dst,
                   const int64_t* g_hi, const uint64_t* g_lo, int64_t id_space, uint8_t* accepted) {

@@ -67,6 +67,8 @@ def _load():
         lib.orc_best_ref.argtypes = [P, C.c_int32, C.c_int32, P, P, P]
         lib.orc_set_partition.restype = C.c_int32
         lib.orc_set_partition.argtypes = [P, P]
+        lib.orc_grow.restype = C.c_int32
+        lib.orc_grow.argtypes = [P, C.c_int64]
         _lib = lib
     return _lib
 
@@ -201,6 +203,13 @@ class Oracle:
         """(target, gain) the refinement loop's BestRef picks for the singleton
         node v at level r < top, or None."""
         return self._best(_load().orc_best_ref, r, v)
+
+    def grow(self, n_new: int) -> None:
+        """Adds isolated vertices up to n_new (the vertex set may change
+        between batches)."""
+        if int(_load().orc_grow(self._h, int(n_new))) != 0:
+            raise ValueError("grow needs n_new >= n")
+        self.n = int(n_new)
 
     def set_partition(self, lab) -> None:
         """Test set-up of a one-level state: replace the level-0 partition and

@@ -40,7 +40,7 @@ struct LevelState {
 enum {
   K_U = 0, K_S, K_USTAR, K_MV, K_M0, K_D, K_C, K_R, K_R2, K_X, K_T, K_E, K_E2, K_CH, K_CAND, K_B,
   K_UNDEC, K_SMALL, K_MID, K_LARGE, K_REC, K_CREC, K_NREC, K_ERR, K_TMP, K_TMP2, K_CHG, K_MID2, K_TINY, K_CLU,
-  K_G, K_CCF,
+  K_G,
   K_A0 = 32,   // K_A0 + r: |A^r|
   K_BRK0 = 48, // K_BRK0 + r: endpoints of deleted level-r arcs
   K_COUNT = 56
@@ -70,6 +70,8 @@ struct ldl_ctx {
   DBuf<int32_t> stS, stU, stMv, stB, stM0, stD, stC, stR, stX, stT, stE, stCh, stL;
   DBuf<int32_t> lU, lS, lUstar, lMv, lM0, lD, lC, lR, lR2, lX, lT, lE, lE2, lCh, lChg, lTmp, lG;
   DBuf<int32_t> comp;  // connected-component labels of the refinement's re-check
+  DBuf<int32_t> nbr;   // per leaving node: its neighbours in its old refined community
+  DBuf<int32_t> ckf;   // per refined community: stamp when its connectivity must be computed
   // candidates and accepted moves
   DBuf<int32_t> cv, csrc, cdst, cst, bv, bsrc, bdst, best, role;
   DBuf<int64_t> cghi;

@@ -266,11 +266,14 @@ __global__ void k_reset_par(const int32_t* lD, int32_t nD, int32_t* par, int64_t
 // holding an endpoint of a deleted level-r arc are re-checked (before any
 // node leaves, so with their current parents).
 __global__ void k_brk_check(const int32_t* lK, const int32_t* nK, const uint8_t* alive, const int32_t* par,
-                            int32_t* stX, int32_t epX, int32_t* lX, int32_t* nX) {
+                            int32_t* stX, int32_t epX, int32_t* lX, int32_t* nX, int32_t* ckf, int32_t epF) {
   const int32_t n = *nK;
   for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
     const int32_t z = lK[k];
-    if (alive[z] && par[z] >= 0) stamp_add(stX, epX, par[z], lX, nX);
+    if (alive[z] && par[z] >= 0) {
+      stamp_add(stX, epX, par[z], lX, nX);
+      ckf[par[z]] = epF;  // an arc inside it may be gone: its components are computed
+    }
   }
 }
 
@@ -281,7 +284,7 @@ __global__ void k_leave(const int32_t* lU, const int32_t* nU, const uint8_t* ali
                         const int32_t* labN, int32_t* par, int32_t* par_old, const int64_t* kout, const int64_t* kin,
                         int64_t* kout1, int64_t* kin1, int32_t* cnt1, int directed, int32_t* stL, int32_t epL,
                         int32_t* stD, int32_t epD, int32_t* lD, int32_t* nD, int32_t* stX, int32_t epX, int32_t* lX,
-                        int32_t* nX) {
+                        int32_t* nX, int32_t* nbr) {
   const int32_t n = *nU;
   for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
     const int32_t u = lU[k];
@@ -290,6 +293,7 @@ __global__ void k_leave(const int32_t* lU, const int32_t* nU, const uint8_t* ali
     if (X >= 0 && labN[X] == lab[u]) continue;
     stL[u] = epL;
     par_old[u] = X;
+    nbr[u] = 0;
     if (X >= 0) {
       stamp_add(stX, epX, X, lX, nX);
       atomic_add_i64(&kout1[X], -kout[u]);
@@ -304,10 +308,15 @@ __global__ void k_leave(const int32_t* lU, const int32_t* nU, const uint8_t* ali
   }
 }
 
-// Remaining members of the re-checked refined communities (their children
-// that did not leave); each starts as its own component.
-__global__ void k_members(Adj<int32_t> ch_adj, ChunkMap m, const int32_t* stL, int32_t epL, int32_t* comp,
-                          int32_t* lG, int32_t* nG) {
+// A refined community that lost nodes stays connected when every node that
+// left had at most one neighbour in it and no arc inside it was deleted
+// (removing leaves keeps a connected graph connected).  Counts each leaving
+// node's neighbours in its old refined community (an arc seen from both
+// rows of a directed pair counts twice: the test only errs towards a check)
+// and flags the community for a connectivity check at the second one.
+template <class WT>
+__global__ void k_leave_degree(Adj<WT> out, Adj<WT> in, ChunkMap m, const int32_t* par, const int32_t* par_old,
+                               const int32_t* stL, int32_t epL, int32_t* nbr, int32_t* ckf, int32_t epF) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -315,7 +324,35 @@ __global__ void k_members(Adj<int32_t> ch_adj, ChunkMap m, const int32_t* stL, i
   for (int64_t c = warp; c < total; c += nw) {
     const Chunk ch = chunk_of(m, c);
     if (ch.row < 0) continue;
-    const int64_t o = ch_adj.off[ch.v];
+    const int32_t v = ch.v;
+    const int32_t X = par_old[v];
+    if (X < 0 || stL[v] != epL) continue;
+    const Adj<WT>& A = ch.row ? in : out;
+    const int64_t o = A.off[v];
+    for (int32_t k = ch.k0 + lane; k < ch.k1; k += 32) {
+      const int32_t y = A.col[o + k];
+      if (y == v) continue;
+      const bool inX = stL[y] == epL ? par_old[y] == X : par[y] == X;
+      if (inX && atomicAdd(&nbr[v], 1) == 1) ckf[X] = epF;
+    }
+  }
+}
+
+// Remaining members of the re-checked refined communities whose connectivity
+// is in doubt (flagged, or their seed node left); each starts as its own
+// component.
+__global__ void k_members(Adj<int32_t> ch_adj, ChunkMap m, const int32_t* stL, int32_t epL, const int32_t* ckf,
+                          int32_t epF, int32_t* comp, int32_t* lG, int32_t* nG) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t total = m.pre[m.n_hint];
+  for (int64_t c = warp; c < total; c += nw) {
+    const Chunk ch = chunk_of(m, c);
+    if (ch.row < 0) continue;
+    const int32_t X = ch.v;
+    if (ckf[X] != epF && stL[X] != epL) continue;
+    const int64_t o = ch_adj.off[X];
     for (int32_t base = ch.k0; base < ch.k1; base += 32) {
       const int32_t k = base + lane;
       bool want = false;
@@ -330,19 +367,35 @@ __global__ void k_members(Adj<int32_t> ch_adj, ChunkMap m, const int32_t* stL, i
   }
 }
 
-// One hooking step of the connected components over the arcs between two
-// remaining members of the same refined community: the root label of the
-// larger side is lowered to the smaller label.  Labels only decrease and stay
-// member ids of the component, so the iteration ends with every component
-// labelled by its lowest member.
+// Root of x's tree.  Parent links only point to smaller ids of the same
+// component and a root never becomes a root again, so reads that lag behind
+// other threads still lead to a node of x's component; they bypass L1 so that
+// a thread sees links other SMs made.  With `halve`, x's link is shortened to
+// its grandparent on the way (only a non-root's link is ever written, and
+// compare-and-swap hooks only roots, so the two never collide).
+__device__ inline int32_t uf_find(int32_t* comp, int32_t x, bool halve) {
+  int32_t p = __ldcg(&comp[x]);
+  while (p != x) {
+    const int32_t q = __ldcg(&comp[p]);
+    if (halve && q != p) comp[x] = q;
+    x = p;
+    p = q;
+  }
+  return x;
+}
+
+// Connected components of the collected members over the arcs between two
+// remaining members of the same refined community, in one pass: a lock-free
+// union-find that always hooks the larger root under the smaller one (a
+// compare-and-swap that fails because another thread hooked first is
+// retried), so every component ends rooted at its lowest member.
 template <class WT>
-__global__ void k_cc_hook(Adj<WT> out, Adj<WT> in, ChunkMap m, const int32_t* par, const int32_t* stL, int32_t epL,
-                          int32_t* comp, int32_t* changed) {
+__global__ void k_uf(Adj<WT> out, Adj<WT> in, ChunkMap m, const int32_t* par, const int32_t* stL, int32_t epL,
+                     int32_t* comp) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int64_t total = m.pre[m.n_hint];
-  bool any = false;
   for (int64_t c = warp; c < total; c += nw) {
     const Chunk ch = chunk_of(m, c);
     if (ch.row < 0) continue;
@@ -352,36 +405,29 @@ __global__ void k_cc_hook(Adj<WT> out, Adj<WT> in, ChunkMap m, const int32_t* pa
     const int64_t o = A.off[u];
     for (int32_t k = ch.k0 + lane; k < ch.k1; k += 32) {
       const int32_t y = A.col[o + k];
-      if (y == u || par[y] != X || stL[y] == epL) continue;
-      const int32_t a = comp[u], b = comp[y];
-      if (a == b) continue;
-      const int32_t hi = a > b ? a : b, lo = a > b ? b : a;
-      if (atomicMin(&comp[hi], lo) > lo) any = true;
+      if (y <= u || par[y] != X || stL[y] == epL) continue;  // each pair once, from its lower end
+      for (;;) {
+        const int32_t a = uf_find(comp, u, true), b = uf_find(comp, y, true);
+        if (a == b) break;
+        const int32_t hi = a > b ? a : b, lo = a > b ? b : a;
+        if (atomicCAS(&comp[hi], hi, lo) == hi) break;
+      }
     }
   }
-  if (__any_sync(0xffffffffu, any) && lane == 0) atomicExch(changed, 1);
 }
 
-// Pointer jumping: every member's label follows its label's label (a bounded
-// number of steps per launch; the host repeats hooking and jumping until
-// nothing changes).
-__global__ void k_cc_jump(const int32_t* lG, const int32_t* nG, int32_t* comp, int32_t* changed) {
+// Every member's label becomes its component's root (its lowest member).
+// The find here writes nothing but the member's own label: a shortening
+// write could otherwise replace another member's final root by an ancestor
+// read before that root was written.  Every own write is a node of the same
+// component (the root, or before it an ancestor), so other threads' finds
+// still end at the root.
+__global__ void k_uf_final(const int32_t* lG, const int32_t* nG, int32_t* comp) {
   const int32_t n = *nG;
-  bool any = false;
   for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
     const int32_t u = lG[k];
-    int32_t a = comp[u];
-    for (int step = 0; step < 64; ++step) {
-      const int32_t b = comp[a];
-      if (b == a) break;
-      a = b;
-    }
-    if (a != comp[u]) {
-      comp[u] = a;
-      any = true;
-    }
+    comp[u] = uf_find(comp, u, false);
   }
-  if (any) atomicExch(changed, 1);
 }
 
 // A component keeps its refined community's id when it holds the community's
@@ -989,11 +1035,18 @@ void reset_par(ldl_ctx& c, int r, int32_t nD) {
 }
 
 template <class WT>
-static void cc_hook(ldl_ctx& c, int r, Adj<WT> out, Adj<WT> in, int32_t nG, int32_t epL) {
+static void leave_degree(ldl_ctx& c, int r, Adj<WT> out, Adj<WT> in, int32_t nD, int32_t epL, int32_t epF) {
+  ChunkMap m = chunk_map(c, c.lD.p, c.dcnt + K_D, nD, out.len, c.directed ? in.len : nullptr);
+  k_leave_degree<WT><<<grid_for((int64_t)nD * 64, TPB, 16), TPB, 0, c.s>>>(out, in, m, c.lv[r].par.p, c.par_old.p,
+                                                                           c.stL.p, epL, c.nbr.p, c.ckf.p, epF);
+  CKL("k_leave_degree");
+}
+
+template <class WT>
+static void union_find(ldl_ctx& c, int r, Adj<WT> out, Adj<WT> in, int32_t nG, int32_t epL) {
   ChunkMap m = chunk_map(c, c.lG.p, c.dcnt + K_G, nG, out.len, c.directed ? in.len : nullptr);
-  k_cc_hook<WT><<<grid_for((int64_t)nG * 64, TPB, 16), TPB, 0, c.s>>>(out, in, m, c.lv[r].par.p, c.stL.p, epL,
-                                                                      c.comp.p, c.dcnt + K_CCF);
-  CKL("k_cc_hook");
+  k_uf<WT><<<grid_for((int64_t)nG * 64, TPB, 16), TPB, 0, c.s>>>(out, in, m, c.lv[r].par.p, c.stL.p, epL, c.comp.p);
+  CKL("k_uf");
 }
 
 // TouchedRefined of a batch update at level r < T (Sec. III-C: refinement
@@ -1014,10 +1067,11 @@ int32_t split(ldl_ctx& c, int r, int32_t epD, int32_t epX) {
   LevelState& N = c.lv[r + 1];
   zero_cnt(c, K_D);
   zero_cnt(c, K_X);
+  const int32_t epF = c.next_epoch();  // communities whose connectivity is in doubt
   const int32_t nK = rd_cnt(c, K_BRK0 + r);
   if (nK > 0) {
     k_brk_check<<<grid_for(nK, TPB), TPB, 0, c.s>>>(L.lK.p, c.dcnt + K_BRK0 + r, L.alive.p, L.par.p, c.stX.p, epX,
-                                                    c.lX.p, c.dcnt + K_X);
+                                                    c.lX.p, c.dcnt + K_X, c.ckf.p, epF);
     CKL("k_brk_check");
   }
   const int32_t epL = c.next_epoch();
@@ -1026,30 +1080,32 @@ int32_t split(ldl_ctx& c, int r, int32_t epD, int32_t epX) {
     k_leave<<<grid_for(nu, TPB), TPB, 0, c.s>>>(c.lUstar.p, c.dcnt + K_USTAR, L.alive.p, L.lab.p, N.lab.p, L.par.p,
                                                 c.par_old.p, L.kout.p, kin_of(c, r), N.kout.p, kin_of(c, r + 1),
                                                 N.cnt.p, c.directed, c.stL.p, epL, c.stD.p, epD, c.lD.p,
-                                                c.dcnt + K_D, c.stX.p, epX, c.lX.p, c.dcnt + K_X);
+                                                c.dcnt + K_D, c.stX.p, epX, c.lX.p, c.dcnt + K_X, c.nbr.p);
     CKL("k_leave");
   }
-  const int32_t nx = rd_cnt(c, K_X);
+  int32_t cnt2[2] = {0, 0};  // K_D, then K_X (adjacent counters)
+  {
+    const HostRead rr[2] = {{c.dcnt + K_D, &cnt2[0], sizeof(int32_t)}, {c.dcnt + K_X, &cnt2[1], sizeof(int32_t)}};
+    host_read(c, rr, 2);
+  }
+  const int32_t nleft = cnt2[0], nx = cnt2[1];
   if (nx > 0) {
+    if (nleft > 0) {
+      if (r == 0) leave_degree<int32_t>(c, r, adj_out0(c), adj_in0(c), nleft, epL, epF);
+      else leave_degree<int64_t>(c, r, adj_out(c, r), adj_in(c, r), nleft, epL, epF);
+    }
     zero_cnt(c, K_G);
     Adj<int32_t> ch{L.children.off.p, L.children.len.p, L.children.col.p, L.children.w.p};
     ChunkMap m = chunk_map(c, c.lX.p, c.dcnt + K_X, nx, L.children.len.p, nullptr);
-    k_members<<<grid_for((int64_t)nx * 64, TPB, 16), TPB, 0, c.s>>>(ch, m, c.stL.p, epL, c.comp.p, c.lG.p,
-                                                                   c.dcnt + K_G);
+    k_members<<<grid_for((int64_t)nx * 64, TPB, 16), TPB, 0, c.s>>>(ch, m, c.stL.p, epL, c.ckf.p, epF, c.comp.p,
+                                                                   c.lG.p, c.dcnt + K_G);
     CKL("k_members");
     const int32_t nG = rd_cnt(c, K_G);
     if (nG > 0) {
-      // hook and jump until a round changes nothing (labels only decrease, so
-      // this ends; a bound guards against an internal error)
-      for (int it = 0;; ++it) {
-        if (it > 100000) ldl_throw(LDL_E_INVALID, "internal: connected components did not converge");
-        zero_cnt(c, K_CCF);
-        if (r == 0) cc_hook<int32_t>(c, r, adj_out0(c), adj_in0(c), nG, epL);
-        else cc_hook<int64_t>(c, r, adj_out(c, r), adj_in(c, r), nG, epL);
-        k_cc_jump<<<grid_for(nG, TPB), TPB, 0, c.s>>>(c.lG.p, c.dcnt + K_G, c.comp.p, c.dcnt + K_CCF);
-        CKL("k_cc_jump");
-        if (rd_cnt(c, K_CCF) == 0) break;
-      }
+      if (r == 0) union_find<int32_t>(c, r, adj_out0(c), adj_in0(c), nG, epL);
+      else union_find<int64_t>(c, r, adj_out(c, r), adj_in(c, r), nG, epL);
+      k_uf_final<<<grid_for(nG, TPB), TPB, 0, c.s>>>(c.lG.p, c.dcnt + K_G, c.comp.p);
+      CKL("k_uf_final");
       k_rename<<<grid_for(nG, TPB), TPB, 0, c.s>>>(c.lG.p, c.dcnt + K_G, c.comp.p, L.alive.p, c.stL.p, epL, L.par.p,
                                                    c.par_old.p, L.kout.p, kin_of(c, r), N.kout.p, kin_of(c, r + 1),
                                                    N.cnt.p, c.directed, c.stD.p, epD, c.lD.p, c.dcnt + K_D);

@@ -51,6 +51,11 @@ int32_t split(ldl_ctx& c, int r, int32_t epD, int32_t epX);
 // the listed level-r nodes that are singleton refined communities -> out
 int32_t singletons_of(ldl_ctx& c, int r, const int32_t* list, int idx_n, int64_t n_hint, int32_t* out, int idx_out);
 void aggregate(ldl_ctx& c, int r, int32_t epD, int32_t epC, int32_t epA_next, bool build);
+// context set-up and tear-down (ldl.cu)
+void alloc_globals(ldl_ctx& c);
+void free_all(ldl_ctx& c);
+ldl_status ctx_new(const ldl_params& p, int64_t n, ldl_ctx** out);
+void set_create_error(const std::string& msg);
 // static set-up of level 0 from a host CSR
 void upload_graph(ldl_ctx& c, int64_t nnz, const int64_t* row_ptr, const int32_t* col, const int32_t* w);
 void level_alloc(ldl_ctx& c, int r);

@@ -180,19 +180,19 @@ static i128 qnum(const ldl_ctx& c) {
 }
 
 // ---------------------------------------------------------------- allocation
-static void alloc_globals(ldl_ctx& c) {
+void alloc_globals(ldl_ctx& c) {
   const int64_t n = c.n;
   c.Kout.exact(n);
   if (c.directed) c.Kin.exact(n);
   c.e.exact(n);
   DBuf<int32_t>* st[] = {&c.stS, &c.stU, &c.stMv, &c.stB, &c.stM0, &c.stD, &c.stC, &c.stR, &c.stX, &c.stT, &c.stE,
-                         &c.stCh, &c.stL};
+                         &c.stCh, &c.stL, &c.ckf};
   for (auto* b : st) {
     b->exact(n);
     CK(cudaMemsetAsync(b->p, 0, sizeof(int32_t) * (size_t)n, c.s));
   }
   DBuf<int32_t>* ls[] = {&c.lU, &c.lS, &c.lUstar, &c.lMv, &c.lM0, &c.lD, &c.lC, &c.lR, &c.lR2, &c.lX, &c.lT,
-                         &c.lE, &c.lE2, &c.lCh, &c.lChg, &c.lTmp, &c.lG, &c.comp, &c.cv, &c.csrc, &c.cdst, &c.cst, &c.bv,
+                         &c.lE, &c.lE2, &c.lCh, &c.lChg, &c.lTmp, &c.lG, &c.comp, &c.nbr, &c.cv, &c.csrc, &c.cdst, &c.cst, &c.bv,
                          &c.bsrc, &c.bdst, &c.oldlab, &c.par_old, &c.lab_before, &c.binT, &c.binS, &c.binM, &c.binM2, &c.binC, &c.binL};
   for (auto* b : ls) b->exact(n);
   c.best.exact(n);
@@ -214,7 +214,7 @@ static void alloc_globals(ldl_ctx& c) {
   c.P.rd_owner = &c;
 }
 
-static void free_all(ldl_ctx& c) {
+void free_all(ldl_ctx& c) {
   if (c.s) cudaStreamSynchronize(c.s);
   for (auto& L : c.lv) L.release();
   DBuf<int64_t>* b64[] = {&c.Kout, &c.Kin, &c.e, &c.cghi, &c.snapKo, &c.snapKi, &c.snapE, &c.binLoff, &c.binLsz,
@@ -222,7 +222,7 @@ static void free_all(ldl_ctx& c) {
                           &c.chunk_pre, &c.hub_ecnt, &c.hub_epre, &c.pb_hi};
   for (auto* b : b64) b->release();
   DBuf<int32_t>* b32[] = {&c.stS, &c.stU, &c.stMv, &c.stB, &c.stM0, &c.stD, &c.stC, &c.stR, &c.stX, &c.stT,
-                          &c.stE, &c.stCh, &c.stL, &c.lG, &c.comp, &c.lU, &c.lS, &c.lUstar, &c.lMv, &c.lM0, &c.lD, &c.lC, &c.lR,
+                          &c.stE, &c.stCh, &c.stL, &c.lG, &c.comp, &c.nbr, &c.ckf, &c.lU, &c.lS, &c.lUstar, &c.lMv, &c.lM0, &c.lD, &c.lC, &c.lR,
                           &c.lR2, &c.lX, &c.lT, &c.lE, &c.lE2, &c.lCh, &c.lChg, &c.lTmp, &c.cv, &c.csrc,
                           &c.cdst, &c.cst, &c.bv, &c.bsrc, &c.bdst, &c.best, &c.role, &c.oldlab, &c.par_old,
                           &c.lab_before, &c.binT, &c.binS, &c.binM, &c.binM2, &c.binC, &c.binL, &c.gkeys, &c.ndx, &c.ndx2,
@@ -576,33 +576,11 @@ static void copy_adj(ldl_ctx& c, const SlackCSR<WT>& g, std::vector<int64_t>& of
   CK(cudaStreamSynchronize(c.s));
 }
 
-// ================================================================== C ABI
-extern "C" {
-
-void ldl_default_params(ldl_params* p) {
-  if (!p) return;
-  memset(p, 0, sizeof(*p));
-  p->directed = 0;
-  p->gamma_num = 1;
-  p->gamma_den = 1;
-  p->N = 2;
-  p->L = 4;
-  p->M = 5;
-  p->M_static = 20;
-  p->alpha_inv = 1000;
-  p->beta_inv = 100;
-  p->cuda_stream = nullptr;
-}
-
-ldl_status ldl_create(const ldl_params* params, int64_t n, int64_t nnz, const int64_t* row_ptr,
-                      const int32_t* col, const int32_t* w, ldl_ctx** out) {
-  if (!out || !params || !row_ptr || (nnz > 0 && (!col || !w))) {
-    g_create_err = "null argument";
-    return LDL_E_INVALID;
-  }
-  *out = nullptr;
-  const ldl_params& p = *params;
-  if (n <= 0 || n > INT32_MAX - 1 || nnz < 0 || p.L < 0 || p.L > 7 || p.N < 0 || p.M < 0 || p.M_static < 0 ||
+// A context with its parameters checked, its pinned read-back page, events
+// and global arrays allocated, and no levels yet (the caller builds or loads
+// them).  On failure nothing is left behind and g_create_err says why.
+ldl_status ctx_new(const ldl_params& p, int64_t n, ldl_ctx** out) {
+  if (n <= 0 || n > INT32_MAX - 1 || p.L < 0 || p.L > 7 || p.N < 0 || p.M < 0 || p.M_static < 0 ||
       p.alpha_inv <= 0 || p.beta_inv <= 0 || p.gamma_num < 1 || p.gamma_den < 1 || p.gamma_num > 1024 ||
       p.gamma_den > 1024 || p.cluster_max_deg < 0) {
     g_create_err = "invalid size or parameter";
@@ -615,10 +593,6 @@ ldl_status ldl_create(const ldl_params* params, int64_t n, int64_t nnz, const in
       g_create_err = "invalid sweep degree bins";
       return LDL_E_INVALID;
     }
-  }
-  if (row_ptr[0] != 0 || row_ptr[n] != nnz) {
-    g_create_err = "row_ptr must start at 0 and end at nnz";
-    return LDL_E_INVALID;
   }
   ldl_ctx* c = new (std::nothrow) ldl_ctx();
   if (!c) return LDL_E_NOMEM;
@@ -646,6 +620,52 @@ ldl_status ldl_create(const ldl_params* params, int64_t n, int64_t nnz, const in
     c->kstats = p.kernel_stats ? 1 : 0;
     for (int i = 0; i < 4; ++i) c->bin_deg[i] = bins[i];
     alloc_globals(*c);
+  } catch (const LdlError& e) {
+    g_create_err = e.msg;
+    free_all(*c);
+    delete c;
+    cudaGetLastError();
+    return e.st;
+  }
+  *out = c;
+  return LDL_OK;
+}
+
+void set_create_error(const std::string& msg) { g_create_err = msg; }
+
+// ================================================================== C ABI
+extern "C" {
+
+void ldl_default_params(ldl_params* p) {
+  if (!p) return;
+  memset(p, 0, sizeof(*p));
+  p->directed = 0;
+  p->gamma_num = 1;
+  p->gamma_den = 1;
+  p->N = 2;
+  p->L = 4;
+  p->M = 5;
+  p->M_static = 20;
+  p->alpha_inv = 1000;
+  p->beta_inv = 100;
+  p->cuda_stream = nullptr;
+}
+
+ldl_status ldl_create(const ldl_params* params, int64_t n, int64_t nnz, const int64_t* row_ptr,
+                      const int32_t* col, const int32_t* w, ldl_ctx** out) {
+  if (!out || !params || !row_ptr || (nnz > 0 && (!col || !w))) {
+    g_create_err = "null argument";
+    return LDL_E_INVALID;
+  }
+  *out = nullptr;
+  if (nnz < 0 || n <= 0 || n > INT32_MAX - 1 || row_ptr[0] != 0 || row_ptr[n] != nnz) {
+    g_create_err = "row_ptr must start at 0 and end at nnz (n in [1, 2^31-2], nnz >= 0)";
+    return LDL_E_INVALID;
+  }
+  ldl_ctx* c = nullptr;
+  const ldl_status st = ctx_new(*params, n, &c);
+  if (st != LDL_OK) return st;
+  try {
     level_alloc(*c, 0);
     upload_graph(*c, nnz, row_ptr, col, w);
     static_build(*c);
@@ -766,6 +786,10 @@ void ldl_destroy(ldl_ctx* c) {
 const char* ldl_last_error(const ldl_ctx* c) { return c ? c->err.c_str() : g_create_err.c_str(); }
 
 int32_t ldl_levels(const ldl_ctx* c) { return c ? c->T + 1 : 0; }
+
+int64_t ldl_num_vertices(const ldl_ctx* c) { return c ? c->n : 0; }
+
+int32_t ldl_is_directed(const ldl_ctx* c) { return c ? c->directed : 0; }
 
 ldl_status ldl_get_level(const ldl_ctx* cc, int32_t r, int32_t* lab, int32_t* par, int64_t* kout, int64_t* kin,
                          int32_t* cnt, uint8_t* alive) {

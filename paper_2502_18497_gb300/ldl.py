@@ -98,6 +98,11 @@ def load(path: Optional[str] = None):
         "ldl_batch_estimate_bytes": (I32, [P, I64, P]),
         "ldl_server_stats": (I32, [P, P, P]),
         "ldl_server_debug_free_bytes": (I32, [P, I64]),
+        "ldl_save": (I32, [P, C.c_char_p]),
+        "ldl_load": (I32, [C.c_char_p, P, P]),
+        "ldl_grow": (I32, [P, I64]),
+        "ldl_num_vertices": (I64, [P]),
+        "ldl_is_directed": (I32, [P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -116,7 +121,8 @@ def exported_symbols():
             "ldl_set_kernel_stats", "ldl_get_kernel_stats", "ldl_apply_batches", "ldl_estimate_bytes",
             "ldl_server_create", "ldl_server_admit", "ldl_server_submit", "ldl_server_wait",
             "ldl_server_destroy", "ldl_debug_decouple", "ldl_debug_alloc_counts", "ldl_batch_estimate_bytes",
-            "ldl_server_stats", "ldl_server_debug_free_bytes"]
+            "ldl_server_stats", "ldl_server_debug_free_bytes", "ldl_save", "ldl_load", "ldl_grow",
+            "ldl_num_vertices", "ldl_is_directed"]
 
 
 def launch_count() -> int:
@@ -203,6 +209,32 @@ class LDL:
     @classmethod
     def from_graph(cls, g, **kw):
         return cls(g.n, g.row_ptr, g.col, g.w, directed=g.directed, **kw)
+
+    @classmethod
+    def load(cls, path: str, stream=None, **kw):
+        """A context resumed from a file written by save() (ldl_load); n and
+        the direction come from the file."""
+        lib = load()
+        obj = cls.__new__(cls)
+        p = make_params(stream=stream, **kw)
+        h = C.c_void_p()
+        st = lib.ldl_load(os.fsencode(path), C.byref(p), C.byref(h))
+        if st != LDL_OK:
+            raise LdlError(st, lib.ldl_last_error(None).decode())
+        obj._h = h
+        obj.last = ldl_result()
+        obj.n = int(lib.ldl_num_vertices(h))
+        obj.directed = bool(lib.ldl_is_directed(h))
+        return obj
+
+    def save(self, path: str):
+        """Writes the whole state to a file (ldl_save)."""
+        self._check(load().ldl_save(self._h, os.fsencode(path)))
+
+    def grow(self, n_new: int):
+        """Appends isolated vertices up to n_new (ldl_grow)."""
+        self._check(load().ldl_grow(self._h, int(n_new)))
+        self.n = int(n_new)
 
     def close(self):
         if getattr(self, "_h", None):

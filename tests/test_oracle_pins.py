@@ -364,3 +364,33 @@ def test_planted_partition_is_recovered():
     q_planted = (e / m - (ko / m) ** 2).sum()
     assert W_q >= 0.99 * q_planted  # a heuristic: close to, not always above
     assert brute.ari(o.labels(), lab) > 0.95
+
+
+# --------------------------------------------------------------------- growth
+@pytest.mark.parametrize("directed", [False, True])
+def test_growth_keeps_every_invariant(directed):
+    """Vertex-set growth (Sec. II): new isolated vertices leave the Eq. 1
+    numerator unchanged, every invariant of the hierarchy (Eq. 3 rebuild,
+    strengths, label and seed invariants, community totals) holds, and later
+    batches that connect the new vertices keep it so; the numerator still
+    equals the brute-force Eq. 1 sum on the grown graph."""
+    for seed in range(6):
+        g = random_small_graph(10 + seed, 0.3, directed, wmax=3, seed=600 + seed)
+        if not g.nnz:
+            continue
+        o = Oracle(g, L=2, M_static=3)
+        st = EdgeStream.from_graph(g, seed)
+        b = random_batch(st, 3, 1, 1, 3, seed)
+        assert o.apply(b) == 0
+        m0, q0 = o.scalars()
+        o.grow(g.n + 5)
+        assert o.check() == ""
+        assert o.scalars() == (m0, q0)
+        assert (o.labels()[g.n:] == np.arange(g.n, g.n + 5)).all()
+        st2 = EdgeStream(g.n + 5, st.directed, st.keys // st.n * (g.n + 5) + st.keys % st.n, st.wts, seed)
+        for t in range(4):
+            b = random_batch(st2, 4, 1, 1, 3, seed * 11 + t)
+            assert o.apply(b) == 0
+            assert o.check() == ""
+            W = brute.dense(_graph_of_stream(st2))
+            assert o.scalars()[1] == brute.q_numerator(W, o.labels().tolist())
