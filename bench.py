@@ -499,11 +499,11 @@ def run_autotune(args):
     best knobs and every candidate's time per batch."""
     import torch
     from paper_2502_18497_gb300.autotune import tune
-    g, batches = _workload(args.steps)
+    g, batches = _workload(args.steps + 1)
     torch.cuda.synchronize()
     res = tune(g, batches, cache=args.autotune_cache, key=f"rmat{SCALE}_b{BATCH}")
     line = {"metric": "updates/s", "value": BATCH / (res["ms_per_batch"] / 1e3), "unit": "updates/s", "n_gpus": 1,
-            "steps": args.steps, "warmup": 0, "ms_per_step": res["ms_per_batch"], "higher_is_better": True,
+            "steps": args.steps, "warmup": 1, "ms_per_step": res["ms_per_batch"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic", "form": "autotune",
             "config": {"workload": WORKLOAD}, "best": {"bin_deg": res["bin_deg"],
                                                        "cluster_max_deg": res["cluster_max_deg"]},

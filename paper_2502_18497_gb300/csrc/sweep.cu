@@ -13,14 +13,15 @@ namespace cg = cooperative_groups;
 namespace {
 
 constexpr int TPB = 256;
-constexpr int HW = 256;      // per-warp hash slots (small bin)
+constexpr int HG8 = 64;      // hash slots per 8-lane group (lowest bin)
+constexpr int HG32 = 256;    // hash slots per warp (second bin)
 constexpr int HB = 4096;     // per-block hash slots (upper mid bin)
 constexpr int MID_DEG = 2048;   // rows above it: clusters (optional) or the hub path
 constexpr int CL = 8;             // blocks per cluster (hub rows up to CLUSTER_DEG entries)
 constexpr int CL_SLOTS = 8192;    // hash slots per block of a cluster (96 KB of shared memory)
 constexpr int CLUSTER_DEG = CL * CL_SLOTS / 2;  // upper limit of cluster_max_deg
 // the bin bounds a context may use keep every table at most half full
-static_assert(BIN_MAX[0] == HW * 8 / 32 / 2 && BIN_MAX[1] == HW / 2 && BIN_MAX[2] == 2048 / 2 &&
+static_assert(BIN_MAX[0] == HG8 / 2 && BIN_MAX[1] == HG32 / 2 && BIN_MAX[2] == 2048 / 2 &&
                   BIN_MAX[3] == HB / 2 && BIN_MAX[3] == MID_DEG,
               "bin bounds and table sizes");
 constexpr int EVAL_CH = 4096;  // hub table slots evaluated per block
@@ -172,13 +173,54 @@ __device__ inline int64_t sweep_bytes(bool directed, int64_t entries, int64_t no
   return per_entry * entries + per_node * nodes + per_pair * pairs;
 }
 
+// The argmax (gain desc, target asc) in the gain's integer type GT: int64 when
+// the host has checked that no gain or intermediate product of this sweep can
+// reach 2^62 (sweep_gain_fits_i64), else int128.  Both give the same exact
+// gains, so the choice never changes a result.
+template <class GT>
+struct BestG {
+  GT g;
+  int32_t c;
+  int32_t have;
+};
+
+template <class GT>
+__device__ inline bool better(const BestG<GT>& a, const BestG<GT>& b) {
+  if (!a.have) return false;
+  if (!b.have) return true;
+  if (a.g != b.g) return a.g > b.g;
+  return a.c < b.c;
+}
+
+__device__ inline int64_t shfl_down_g(int64_t v, int d, int w) { return __shfl_down_sync(0xffffffffu, v, d, w); }
+__device__ inline i128 shfl_down_g(i128 v, int d, int w) { return shfl_down_i128_w(v, d, w); }
+__device__ inline int64_t shfl_g(int64_t v, int src, int w) { return __shfl_sync(0xffffffffu, v, src, w); }
+__device__ inline i128 shfl_g(i128 v, int src, int w) { return shfl_i128_w(v, src, w); }
+
+// Argmax over each segment of G lanes (every lane takes part; the result
+// lands in every lane of the segment).  G = 32: the whole warp.
+template <class GT, int G>
+__device__ inline BestG<GT> seg_best(BestG<GT> x) {
+  for (int d = G / 2; d > 0; d >>= 1) {
+    BestG<GT> o;
+    o.g = shfl_down_g(x.g, d, G);
+    o.c = __shfl_down_sync(0xffffffffu, x.c, d, G);
+    o.have = __shfl_down_sync(0xffffffffu, x.have, d, G);
+    if (better(o, x)) x = o;
+  }
+  x.g = shfl_g(x.g, 0, G);
+  x.c = __shfl_sync(0xffffffffu, x.c, 0, G);
+  x.have = __shfl_sync(0xffffffffu, x.have, 0, G);
+  return x;
+}
+
 // Evaluates the slots start, start + step, ... < H of a node's table: the
 // exact gain (as gain_of) into every target but `self`, the best kept in b.
 // EV slots per step have their totals gathered before any gain is computed.
-template <int MODE>
+template <int MODE, class GT>
 __device__ inline void eval_slots(const int32_t* K, const int64_t* V, uint32_t H, uint32_t start, uint32_t step,
                                   int32_t self, int32_t a, int64_t wa, int64_t ko, int64_t ki, const int64_t* Tout,
-                                  const int64_t* Tin, int64_t m, int64_t gn, int64_t gd, int64_t mult, Best& b,
+                                  const int64_t* Tin, int64_t m, int64_t gn, int64_t gd, int64_t mult, BestG<GT>& b,
                                   int64_t& pairs) {
   constexpr int EV = 1;
   const int64_t tia = MODE == 0 ? Tin[a] : 0, toa = MODE == 0 ? Tout[a] : 0;
@@ -201,19 +243,19 @@ __device__ inline void eval_slots(const int32_t* K, const int64_t* V, uint32_t H
     for (int j = 0; j < EV; ++j) {
       if (key[j] < 0) continue;
       ++pairs;
-      i128 g;
+      GT g;
       if (MODE == 0) {
-        const i128 dw = (i128)mult * (acc[j] - wa);
-        const i128 dd = (i128)ko * (ti[j] - tia + ki) + (i128)ki * (to[j] - toa + ko);
-        g = (i128)gd * m * dw - (i128)gn * dd;
+        const GT dw = (GT)mult * (GT)(acc[j] - wa);
+        const GT dd = (GT)ko * (GT)(ti[j] - tia + ki) + (GT)ki * (GT)(to[j] - toa + ko);
+        g = (GT)gd * (GT)m * dw - (GT)gn * dd;
       } else {
-        const i128 dw = (i128)mult * acc[j];
-        const i128 dd = (i128)ko * ti[j] + (i128)ki * to[j];
-        g = (i128)gd * m * dw - (i128)gn * dd;
+        const GT dw = (GT)mult * (GT)acc[j];
+        const GT dd = (GT)ko * (GT)ti[j] + (GT)ki * (GT)to[j];
+        g = (GT)gd * (GT)m * dw - (GT)gn * dd;
       }
       if (g > 0) {
-        Best c{g, key[j], 1};
-        if (best_better(c, b)) b = c;
+        BestG<GT> c{g, key[j], 1};
+        if (better(c, b)) b = c;
       }
     }
   }
@@ -229,13 +271,24 @@ __device__ inline void emit_cand(const SweepArgs<WT>& A, int32_t v, int32_t src,
   A.cglo[p] = (uint64_t)b.g;
 }
 
+template <class WT, class GT>
+__device__ inline void emit_cand(const SweepArgs<WT>& A, int32_t v, int32_t src, const BestG<GT>& b) {
+  const int32_t p = atomicAdd(A.ncand, 1);
+  A.cv[p] = v;
+  A.csrc[p] = src;
+  A.cdst[p] = b.c;
+  A.cghi[p] = (int64_t)((i128)b.g >> 64);
+  A.cglo[p] = (uint64_t)b.g;
+}
+
 // One group of G lanes per node with a group-private shared hash of
-// HW * G / 32 slots (G = 8 for the lowest degrees, G = 32 above).  All groups
+// HG8 slots (G = 8, the lowest degrees) or HG32 slots (G = 32, a warp per
+// node).  All groups
 // of a warp advance together, so the warp-wide shuffles of the argmax see
 // every lane; a group without a node in an iteration only takes part in them.
-template <class WT, int MODE, int G>
+template <class WT, int MODE, int G, class GT>
 __global__ void __launch_bounds__(TPB, 5) k_sweep_group(SweepArgs<WT> A, const int32_t* list, const int32_t* nlist) {
-  constexpr int HG = HW * G / 32;
+  constexpr int HG = G == 8 ? HG8 : HG32;
   constexpr int GPW = 32 / G;  // groups per warp
   __shared__ int32_t hk[TPB / G][HG];
   __shared__ int64_t hv[TPB / G][HG];
@@ -259,7 +312,7 @@ __global__ void __launch_bounds__(TPB, 5) k_sweep_group(SweepArgs<WT> A, const i
       V[k] = 0;
     }
     __syncwarp();
-    Best b{0, 0, 0};
+    BestG<GT> b{0, 0, 0};
     int32_t a = 0;
     if (act) {
       a = A.lab[v];
@@ -274,10 +327,10 @@ __global__ void __launch_bounds__(TPB, 5) k_sweep_group(SweepArgs<WT> A, const i
     if (act) {
       const int64_t wa = MODE == 0 ? hash_get(K, V, H - 1, a) : 0;
       const int64_t ko = A.kout[v], ki = A.kin[v];
-      eval_slots<MODE>(K, V, (uint32_t)H, (uint32_t)gl, (uint32_t)G, MODE == 0 ? a : v, a, wa, ko, ki, A.Tout, A.Tin,
-                       A.m, A.gn, A.gd, mult, b, pairs);
+      eval_slots<MODE, GT>(K, V, (uint32_t)H, (uint32_t)gl, (uint32_t)G, MODE == 0 ? a : v, a, wa, ko, ki, A.Tout,
+                           A.Tin, A.m, A.gn, A.gd, mult, b, pairs);
     }
-    b = group_best<G>(b);
+    b = seg_best<GT, G>(b);
     if (act && gl == 0 && b.have) emit_cand(A, v, MODE == 0 ? a : v, b);
     __syncwarp();
   }
@@ -292,10 +345,10 @@ __global__ void __launch_bounds__(TPB, 5) k_sweep_group(SweepArgs<WT> A, const i
 
 // one block per node; the hash lives in dynamic shared memory (mid degrees)
 // or in a global-memory slice (hubs, table != nullptr)
-template <class WT, int MODE, int NT, int HMAX>
+template <class WT, int MODE, int NT, int HMAX, class GT>
 __global__ void __launch_bounds__(NT) k_sweep_block(SweepArgs<WT> A, const int32_t* list, const int32_t* nlist) {
   extern __shared__ unsigned char smem[];
-  __shared__ Best wb[NT / 32];
+  __shared__ BestG<GT> wb[NT / 32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int32_t nl = *nlist;
   const int64_t mult = A.directed ? 1 : 2;
@@ -318,18 +371,18 @@ __global__ void __launch_bounds__(NT) k_sweep_block(SweepArgs<WT> A, const int32
     __syncthreads();
     const int64_t wa = MODE == 0 ? hash_get(K, V, H - 1, a) : 0;
     const int64_t ko = A.kout[v], ki = A.kin[v];
-    Best b{0, 0, 0};
+    BestG<GT> b{0, 0, 0};
     int64_t pairs = 0;
-    eval_slots<MODE>(K, V, H, threadIdx.x, NT, MODE == 0 ? a : v, a, wa, ko, ki, A.Tout, A.Tin, A.m, A.gn, A.gd,
-                     mult, b, pairs);
-    b = warp_best(b);
+    eval_slots<MODE, GT>(K, V, H, threadIdx.x, NT, MODE == 0 ? a : v, a, wa, ko, ki, A.Tout, A.Tin, A.m, A.gn, A.gd,
+                         mult, b, pairs);
+    b = seg_best<GT, 32>(b);
     if (lane == 0) wb[wid] = b;
     pairs_all += pairs;
     __syncthreads();
     if (threadIdx.x == 0) {
-      Best r = wb[0];
+      BestG<GT> r = wb[0];
       for (int w = 1; w < NT / 32; ++w)
-        if (best_better(wb[w], r)) r = wb[w];
+        if (better(wb[w], r)) r = wb[w];
       if (r.have) emit_cand(A, v, MODE == 0 ? a : v, r);
       ent_all += d;
       ++nodes;
@@ -1077,6 +1130,39 @@ void union_into(ldl_ctx& c, const int32_t* list, int idx_n, int32_t* stamp, int3
 }
 
 // the next KS_EVENTS statistics events of the context, created on first use
+// No exact gain of a sweep, nor any intermediate product of it, reaches 2^62
+// when (2 gamma_den + 4 gamma_num) m^2 < 2^62: |w(v,.)| <= m, strengths and
+// totals are at most m, so gd*m*|dw| <= 2 gd m^2 and gn*|dd| <= 4 gn m^2.
+static bool sweep_gain_fits_i64(const ldl_ctx& c) {
+  const i128 m = (i128)c.m;
+  const i128 bound = (i128)(2 * (int64_t)c.prm.gamma_den + 4 * (int64_t)c.prm.gamma_num) * m * m;
+  return bound < ((i128)1 << 62);
+}
+
+// The bins of nodes with at most 2048 entries, in the gain type GT.
+template <class WT, int MODE, class GT>
+static void sweep_bins(ldl_ctx& c, const SweepArgs<WT>& A, int64_t n_hint, cudaEvent_t* kev) {
+  k_sweep_group<WT, MODE, 8, GT><<<grid_for(n_hint * 8, TPB, 5), TPB, 0, c.s>>>(A, c.binT.p, c.dcnt + K_TINY);
+  CKL("k_sweep_group<8>");
+  if (kev) CK(cudaEventRecord(kev[1], c.s));
+  k_sweep_group<WT, MODE, 32, GT><<<grid_for(n_hint * 32, TPB, 5), TPB, 0, c.s>>>(A, c.binS.p, c.dcnt + K_SMALL);
+  CKL("k_sweep_group<32>");
+  if (kev) CK(cudaEventRecord(kev[2], c.s));
+  {
+    const size_t sm = (sizeof(int64_t) + sizeof(int32_t)) * 2048;
+    k_sweep_block<WT, MODE, 128, 2048, GT><<<grid_for(n_hint, 1, 16), 128, sm, c.s>>>(A, c.binM.p, c.dcnt + K_MID);
+    CKL("k_sweep_block(mid1)");
+  }
+  if (kev) CK(cudaEventRecord(kev[3], c.s));
+  {
+    const size_t sm = (sizeof(int64_t) + sizeof(int32_t)) * HB;
+    CK(cudaFuncSetAttribute(k_sweep_block<WT, MODE, 256, HB, GT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)sm));
+    k_sweep_block<WT, MODE, 256, HB, GT><<<grid_for(n_hint, 1, 4), 256, sm, c.s>>>(A, c.binM2.p, c.dcnt + K_MID2);
+    CKL("k_sweep_block(mid2)");
+  }
+}
+
 static cudaEvent_t* kstats_events(ldl_ctx& c) {
   while (c.kev.size() < c.kev_used + KS_EVENTS) {
     cudaEvent_t e;
@@ -1137,27 +1223,8 @@ static void sweep_t(ldl_ctx& c, int r, Adj<WT> out, Adj<WT> in, const int32_t* l
   // and the host's wait below overlaps them.  n_hint bounds every bin.
   cudaEvent_t* kev = c.kstats ? kstats_events(c) : nullptr;
   if (kev) CK(cudaEventRecord(kev[0], c.s));
-  k_sweep_group<WT, MODE, 8><<<grid_for(n_hint * 8, TPB, 5), TPB, 0, c.s>>>(A, c.binT.p, c.dcnt + K_TINY);
-  CKL("k_sweep_group<8>");
-  if (kev) CK(cudaEventRecord(kev[1], c.s));
-  k_sweep_group<WT, MODE, 32><<<grid_for(n_hint * 32, TPB, 5), TPB, 0, c.s>>>(A, c.binS.p,
-                                                                                    c.dcnt + K_SMALL);
-  CKL("k_sweep_group<32>");
-  if (kev) CK(cudaEventRecord(kev[2], c.s));
-  {
-    const size_t sm = (sizeof(int64_t) + sizeof(int32_t)) * 2048;
-    k_sweep_block<WT, MODE, 128, 2048><<<grid_for(n_hint, 1, 16), 128, sm, c.s>>>(A, c.binM.p,
-                                                                                     c.dcnt + K_MID);
-    CKL("k_sweep_block(mid1)");
-  }
-  if (kev) CK(cudaEventRecord(kev[3], c.s));
-  {
-    const size_t sm = (sizeof(int64_t) + sizeof(int32_t)) * HB;
-    CK(cudaFuncSetAttribute(k_sweep_block<WT, MODE, 256, HB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    k_sweep_block<WT, MODE, 256, HB><<<grid_for(n_hint, 1, 4), 256, sm, c.s>>>(A, c.binM2.p,
-                                                                                   c.dcnt + K_MID2);
-    CKL("k_sweep_block(mid2)");
-  }
+  if (sweep_gain_fits_i64(c)) sweep_bins<WT, MODE, int64_t>(c, A, n_hint, kev);
+  else sweep_bins<WT, MODE, i128>(c, A, n_hint, kev);
   if (kev) CK(cudaEventRecord(kev[4], c.s));
   if (c.prm.cluster_max_deg > c.bin_deg[3]) {
     const size_t sm = (sizeof(int64_t) + sizeof(int32_t)) * CL_SLOTS;

@@ -553,10 +553,14 @@ def powerlaw_planted(n: int = 1 << 24, mean_deg: float = 32.0, deg_exp: float = 
 
 
 def powerlaw_stream(g: Graph, size: int, batches: int, seed: int = 3, ins_frac: float = 0.8,
-                    region_factor: int = 4):
+                    region_factor: int = 4, sizes=None):
     """Batches whose endpoints lie in a seed region: a BFS ball around a seeded
-    random vertex grown to at least region_factor*size vertices."""
+    random vertex grown to at least region_factor*size vertices.  With
+    `sizes`, one consistent stream of batches of those sizes instead (the
+    region grown for the largest)."""
     n = g.n
+    if sizes is not None:
+        size = int(max(sizes))
     start = int(uniform_u64(seed, 101, np.array([size]), n)[0])
     want = max(2, region_factor * size)
     seen = np.zeros(n, dtype=bool)
@@ -575,16 +579,15 @@ def powerlaw_stream(g: Graph, size: int, batches: int, seed: int = 3, ins_frac: 
         front = nb
     region = np.concatenate(region)
     st = EdgeStream.from_graph(g, seed * 1000 + 11 + size)
-    n_ins = int(round(size * ins_frac))
-    n_del = size - n_ins
 
     def sampler(base, cnt):
         idx = np.arange(base, base + cnt, dtype=np.int64)
         return (region[uniform_u64(seed, 102, idx, len(region))],
                 region[uniform_u64(seed, 103, idx, len(region))])
     out = []
-    for _ in range(batches):
-        out.append(_region_batch(st, n_ins, n_del, sampler, region, seed))
+    for sz in (sizes if sizes is not None else [size] * batches):
+        n_ins = int(round(sz * ins_frac))
+        out.append(_region_batch(st, n_ins, int(sz) - n_ins, sampler, region, seed))
     return out
 
 

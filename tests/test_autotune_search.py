@@ -10,11 +10,11 @@ def test_descends_to_the_cheapest_reachable_setting():
     def cost(bins, cl):
         calls.append((tuple(bins), cl))
         assert all(bins[i] <= bins[i + 1] for i in range(3))
-        # separable: cheapest at bins (32, 64, 384, 1024) and cluster 0
-        return abs(bins[0] - 32) + abs(bins[1] - 64) + abs(bins[2] - 384) + abs(bins[3] - 1024) + cl / 1000
+        # separable: cheapest at bins (32, 96, 384, 1024) and cluster 0
+        return abs(bins[0] - 32) + abs(bins[1] - 96) + abs(bins[2] - 384) + abs(bins[3] - 1024) + cl / 1000
 
     best_bins, best_cl, best_ms, seen = coordinate_descent(cost)
-    assert best_bins == [32, 64, 384, 1024] and best_cl == 0 and best_ms == 0
+    assert best_bins == [32, 96, 384, 1024] and best_cl == 0 and best_ms == 0
     assert calls[0] == (tuple(DEFAULT_BINS), 0)
     assert len(calls) == len(set(calls)) == len(seen)
     assert len(calls) <= 1 + sum(len(v) for v in SEARCH.values())

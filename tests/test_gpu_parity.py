@@ -7,6 +7,8 @@ totals, m and the Eq. 1 numerator) after creation and after every batch.
 Integer state must match exactly; the reported modularity within 1e-12
 relative.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -225,3 +227,24 @@ def test_hand_derived_fixtures(ldl):
             assert blocks_of(d.labels()) == blocks, name
             m, qnum = d.numerator()
             assert q_matches(m, qnum, q), (name, t, m, qnum, q)
+
+
+@pytest.mark.slow
+@pytest.mark.skipif(os.environ.get("LDL_FULL_PARITY") != "1",
+                    reason="full-size power-law parity takes tens of minutes (generator and oracle); "
+                           "set LDL_FULL_PARITY=1")
+def test_powerlaw_planted_full_size(ldl):
+    """The power-law planted partition at its benchmark size (2^24 vertices,
+    ~242M edges): the static build, then one region-localised stream of
+    batches of 10^2, 10^2, 10^3, 10^3, 10^4 and 10^4 updates, compared bit for
+    bit after every batch (every level's adjacency after the last)."""
+    from synth import powerlaw_planted, powerlaw_stream
+    g = powerlaw_planted(n=1 << 24, seed=3)
+    sizes = [100, 100, 1000, 1000, 10000, 10000]
+    bs = powerlaw_stream(g, size=max(sizes), batches=len(sizes), seed=3, sizes=sizes)
+    o, d = _pair(ldl, g)
+    _assert_same(o, d, "create", adjacency=False)
+    for t, b in enumerate(bs):
+        assert o.apply(b) == 0
+        d.apply(b)
+        _assert_same(o, d, f"batch {t} ({len(b)} updates)", adjacency=(t == len(bs) - 1))

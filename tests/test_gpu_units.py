@@ -131,3 +131,28 @@ def test_planted_stream_rational_gamma(ldl, directed):
         d.apply(b)
         msgs = compare_states(o, d, f"batch {t}")
         assert not msgs, "\n".join(msgs[:8])
+
+
+@pytest.mark.parametrize("directed", [False, True])
+def test_random_streams_with_huge_weights(ldl, directed):
+    """Weights up to 2^30 make m^2 far larger than 2^62, so the sweeps take
+    their int128 gain path (small totals take the int64 one): the whole state
+    still equals the oracle's after creation and every batch."""
+    for seed in range(4):
+        g = random_small_graph(30 + 7 * seed, 0.2, directed, wmax=1 << 30, seed=700 + seed)
+        if not g.nnz:
+            continue
+        params = dict(L=2 + seed % 3, M_static=5, M=3, N=2)
+        o = Oracle(g, **params)
+        d = ldl.LDL.from_graph(g, **params)
+        assert 6 * d.numerator()[0] ** 2 >= 1 << 62
+        msgs = compare_states(o, d, f"seed {seed} create")
+        assert not msgs, "\n".join(msgs[:8])
+        st = EdgeStream.from_graph(g, seed)
+        for t in range(6):
+            m = len(st.keys)
+            b = random_batch(st, 5, min(3, m), min(2, max(0, m - 3)), 1 << 30, seed * 31 + t)
+            assert o.apply(b) == 0
+            d.apply(b)
+            msgs = compare_states(o, d, f"seed {seed} batch {t}")
+            assert not msgs, "\n".join(msgs[:8])
