@@ -1139,14 +1139,13 @@ static void emit_records(ldl_ctx& c, int r, Adj<WT> out, Adj<WT> in, int32_t nC,
   CKL("k_emit");
 }
 
-void aggregate(ldl_ctx& c, int r, int32_t epD, int32_t epC, int32_t epA_next, bool build) {
+void aggregate(ldl_ctx& c, int r, int32_t epD, int32_t epC, int32_t epA_next, bool build, int32_t nD) {
   (void)epD;
   LevelState& L = c.lv[r];
   LevelState& N = c.lv[r + 1];
   // changed nodes
   sub_begin(c);
   zero_cnt(c, K_C);
-  const int32_t nD = rd_cnt(c, K_D);
   k_changed<<<grid_for(nD, TPB), TPB, 0, c.s>>>(c.lD.p, c.dcnt + K_D, L.par.p, c.par_old.p, c.stC.p, epC, c.lC.p,
                                                 c.dcnt + K_C);
   CKL("k_changed");
@@ -1262,7 +1261,7 @@ void aggregate(ldl_ctx& c, int r, int32_t epD, int32_t epC, int32_t epA_next, bo
       ie2 = ti;
       ne = ne_next;
     }
-    if (rd_cnt(c, K_ERR)) ldl_throw(LDL_E_INVALID, "internal: new supernode already has a parent");
+    // the error flag K_ERR is read once at the end of the batch (or of the static build)
   } else {
     sub_end(c, SU_AGG_EMIT);
     sub_begin(c);

@@ -50,7 +50,8 @@ int32_t dissolve_all(ldl_ctx& c, int r, int32_t epD);
 int32_t split(ldl_ctx& c, int r, int32_t epD, int32_t epX);
 // the listed level-r nodes that are singleton refined communities -> out
 int32_t singletons_of(ldl_ctx& c, int r, const int32_t* list, int idx_n, int64_t n_hint, int32_t* out, int idx_out);
-void aggregate(ldl_ctx& c, int r, int32_t epD, int32_t epC, int32_t epA_next, bool build);
+// nD = |D| (list lD), the nodes whose refined community changed.
+void aggregate(ldl_ctx& c, int r, int32_t epD, int32_t epC, int32_t epA_next, bool build, int32_t nD);
 // context set-up and tear-down (ldl.cu)
 void alloc_globals(ldl_ctx& c);
 void free_all(ldl_ctx& c);

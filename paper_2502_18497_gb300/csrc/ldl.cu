@@ -311,8 +311,7 @@ static void move_loop(ldl_ctx& c, int r, int rounds, int32_t epU, int32_t epMv, 
 }
 
 // The refinement loop of Algorithm 1 at level r over the dissolved set lD (epoch epD).
-static int64_t refine_loop(ldl_ctx& c, int r, int rounds, int32_t epD) {
-  const int32_t nD = rd_cnt(c, K_D);
+static int64_t refine_loop(ldl_ctx& c, int r, int rounds, int32_t epD, int32_t nD) {
   if (nD == 0) return 0;
   // R starts as the singleton refined communities of D
   singletons_of(c, r, c.lD.p, K_D, nD, c.lR.p, K_R);
@@ -354,6 +353,7 @@ static void check_scan_wait(ldl_ctx& c);
 static void static_build(ldl_ctx& c) {
   const int L = c.prm.L;
   c.T = 0;
+  zero_cnt(c, K_ERR);
   for (int r = 0; r <= L; ++r) {
     const int32_t nU = alive_list(c, r, c.lU.p, K_U);
     const int32_t epU = c.next_epoch();
@@ -370,7 +370,7 @@ static void static_build(ldl_ctx& c) {
     c.T = r + 1;
     const int32_t epD = c.next_epoch();
     const int32_t nD = dissolve_all(c, r, epD);
-    const int64_t merges = refine_loop(c, r, c.prm.M_static, epD);
+    const int64_t merges = refine_loop(c, r, c.prm.M_static, epD, nD);
     if (merges == 0) {
       reset_par(c, r, nD);
       level_free(c, r + 1);
@@ -378,8 +378,9 @@ static void static_build(ldl_ctx& c) {
       break;
     }
     const int32_t epC = c.next_epoch();
-    aggregate(c, r, epD, epC, 0, true);
+    aggregate(c, r, epD, epC, 0, true, nD);
   }
+  if (rd_cnt(c, K_ERR)) ldl_throw(LDL_E_INVALID, "internal: new supernode already has a parent");
   check_scan_wait(c);
 }
 
@@ -474,6 +475,7 @@ static void apply_batch(ldl_ctx& c, const ldl_update* upd, int64_t count, int on
   stage_end(c, ST_INGEST);
   const int32_t epCh = c.next_epoch();
   zero_cnt(c, K_CH);
+  zero_cnt(c, K_ERR);
   if (na == 0) {
     c.res.n_changed = 0;
     return;
@@ -518,15 +520,15 @@ static void apply_batch(ldl_ctx& c, const ldl_update* upd, int64_t count, int on
         stage_begin(c);
         const int32_t epD = c.next_epoch(), epX = c.next_epoch();
         sub_begin(c);
-        split(c, r, epD, epX);
+        const int32_t nD = split(c, r, epD, epX);
         sub_end(c, SU_REF_DISSOLVE);
         sub_begin(c);
-        refine_loop(c, r, c.prm.M, epD);
+        refine_loop(c, r, c.prm.M, epD, nD);
         sub_end(c, SU_REF_LOOP);
         stage_end(c, ST_REFINE);
         stage_begin(c);
         const int32_t epC = c.next_epoch();
-        aggregate(c, r, epD, epC, epA[r + 1], false);
+        aggregate(c, r, epD, epC, epA[r + 1], false, nD);
         stage_end(c, ST_AGG);
       }
     }
@@ -541,6 +543,7 @@ static void apply_batch(ldl_ctx& c, const ldl_update* upd, int64_t count, int on
     if ((qnum(c) - Qpass) * (i128)ainv < Qpass) break;
   }
   c.res.n_changed = changed_labels(c, epCh);
+  if (rd_cnt(c, K_ERR)) ldl_throw(LDL_E_INVALID, "internal: new supernode already has a parent");
   c.res.host_syncs = c.syncs;
   CK(cudaMemcpyAsync(&c.res.edges_scanned, &c.d_sc->scanned, sizeof(int64_t), cudaMemcpyDeviceToHost, c.s));
   check_scan_wait(c);

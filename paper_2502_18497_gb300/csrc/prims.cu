@@ -1,6 +1,12 @@
 // Device primitives: exclusive scan, stable LSD radix sort of (key, value)
 // pairs, and reduce-by-key of sorted pairs.  Hand-written; no library sort.
+#include <cooperative_groups.h>
+
+#include <algorithm>
+
 #include "prims.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace {
 
@@ -166,11 +172,13 @@ constexpr int RS_ITEMS = 8;
 constexpr int RS_TILE = RS_THREADS * RS_ITEMS;
 static_assert(RS_THREADS == 256 && SC_THREADS == 256, "one thread per digit");
 
-__global__ void k_rs_hist(const u64* keys, int64_t n, int shift, int64_t nb, int64_t* ghist) {
+// Digit histogram of tile b (RS_TILE keys from b * RS_TILE) into column b
+// of ghist (digit-major: ghist[d * nb + b]).
+__device__ inline void rs_hist_tile(const u64* keys, int64_t n, int shift, int64_t nb, int64_t* ghist, int64_t b) {
   __shared__ uint32_t h[256];
   for (int i = threadIdx.x; i < 256; i += RS_THREADS) h[i] = 0;
   const int lane = threadIdx.x & 31;
-  const int64_t base = (int64_t)blockIdx.x * RS_TILE;
+  const int64_t base = b * RS_TILE;
   int d[RS_ITEMS];
   for (int k = 0; k < RS_ITEMS; ++k) {  // all loads in flight before any shuffle
     const int64_t i = base + (int64_t)k * RS_THREADS + threadIdx.x;
@@ -183,14 +191,19 @@ __global__ void k_rs_hist(const u64* keys, int64_t n, int shift, int64_t nb, int
     if (d[k] < 256 && lane == __ffs(peers) - 1) atomicAdd(&h[d[k]], (uint32_t)__popc(peers));
   }
   __syncthreads();
-  for (int x = threadIdx.x; x < 256; x += RS_THREADS) ghist[(int64_t)x * nb + blockIdx.x] = h[x];
+  for (int x = threadIdx.x; x < 256; x += RS_THREADS) ghist[(int64_t)x * nb + b] = h[x];
+  __syncthreads();  // h is reset by the block's next tile
+}
+
+__global__ void k_rs_hist(const u64* keys, int64_t n, int shift, int64_t nb, int64_t* ghist) {
+  rs_hist_tile(keys, n, shift, nb, ghist, blockIdx.x);
 }
 
 // One block per digit: exclusive scan of the digit's tile counts in place
 // (8 consecutive counts per thread per step), and the digit's total.
-__global__ void __launch_bounds__(SC_THREADS) k_rs_dscan(int64_t* ghist, int64_t nb, int64_t* dtot) {
+__device__ inline void rs_dscan_digit(int64_t* ghist, int64_t nb, int64_t* dtot, int d) {
   constexpr int IT = 8;
-  int64_t* row = ghist + (int64_t)blockIdx.x * nb;
+  int64_t* row = ghist + (int64_t)d * nb;
   int64_t carry = 0;
   for (int64_t b0 = 0; b0 < nb; b0 += SC_THREADS * IT) {
     const int64_t base = b0 + (int64_t)threadIdx.x * IT;
@@ -208,7 +221,11 @@ __global__ void __launch_bounds__(SC_THREADS) k_rs_dscan(int64_t* ghist, int64_t
     }
     carry += total;
   }
-  if (threadIdx.x == 0) dtot[blockIdx.x] = carry;
+  if (threadIdx.x == 0) dtot[d] = carry;
+}
+
+__global__ void __launch_bounds__(SC_THREADS) k_rs_dscan(int64_t* ghist, int64_t nb, int64_t* dtot) {
+  rs_dscan_digit(ghist, nb, dtot, blockIdx.x);
 }
 
 // One tile of RS_TILE pairs per block.  Each warp ranks a contiguous sub-tile
@@ -218,9 +235,8 @@ __global__ void __launch_bounds__(SC_THREADS) k_rs_dscan(int64_t* ghist, int64_t
 // consecutive output slots of each digit.  The global start of (digit d,
 // tile b) is the exclusive prefix of the digit totals dtot at d plus the
 // per-digit scanned tile count goff[d * nb + b].
-__global__ void __launch_bounds__(RS_THREADS, 4) k_rs_scatter(const u64* keys, const u64* vals, u64* okeys,
-                                                              u64* ovals, int64_t n, int shift, int64_t nb,
-                                                              const int64_t* goff, const int64_t* dtot) {
+__device__ inline void rs_scatter_tile(const u64* keys, const u64* vals, u64* okeys, u64* ovals, int64_t n, int shift,
+                                       int64_t nb, const int64_t* goff, const int64_t* dtot, int64_t b) {
   constexpr int NW = RS_THREADS / WARP;
   __shared__ int32_t whist[NW][256];  // per-warp digit counts, then per-warp exclusive bases
   __shared__ int32_t tstart[256];     // tile-local start of each digit
@@ -228,13 +244,13 @@ __global__ void __launch_bounds__(RS_THREADS, 4) k_rs_scatter(const u64* keys, c
   __shared__ u64 sk[RS_TILE];
   __shared__ u64 sv[RS_TILE];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const int64_t base = (int64_t)blockIdx.x * RS_TILE;
+  const int64_t base = b * RS_TILE;
   const int tile_n = (int)min((int64_t)RS_TILE, n - base);
   for (int d = lane; d < 256; d += 32) whist[wid][d] = 0;
   {
     int64_t total;
     const int64_t dbase = block_excl_scan_i64(dtot[tid], &total);  // RS_THREADS == 256 digits
-    gstart[tid] = dbase + goff[(int64_t)tid * nb + blockIdx.x];
+    gstart[tid] = dbase + goff[(int64_t)tid * nb + b];
   }
   u64 key[RS_ITEMS], val[RS_ITEMS];
   int rk[RS_ITEMS];
@@ -285,6 +301,34 @@ __global__ void __launch_bounds__(RS_THREADS, 4) k_rs_scatter(const u64* keys, c
     const int64_t p = gstart[d] + (j - tstart[d]);
     okeys[p] = k;
     ovals[p] = sv[j];
+  }
+  __syncthreads();  // the tile buffers are reused by the caller's next tile
+}
+
+__global__ void __launch_bounds__(RS_THREADS, 4) k_rs_scatter(const u64* keys, const u64* vals, u64* okeys,
+                                                              u64* ovals, int64_t n, int shift, int64_t nb,
+                                                              const int64_t* goff, const int64_t* dtot) {
+  rs_scatter_tile(keys, vals, okeys, ovals, n, shift, nb, goff, dtot, blockIdx.x);
+}
+
+// The whole multi-tile sort in one cooperative launch (all nb tiles'
+// blocks co-resident): per 8-bit pass the tile histograms, the per-digit
+// scans over tiles and the scatter, separated by grid barriers, ping-ponging
+// between (keys, vals) and (tk, tv).  Replaces three launches per pass.
+__global__ void __launch_bounds__(RS_THREADS, 4) k_rs_coop(u64* keys, u64* vals, u64* tk, u64* tv, int64_t n,
+                                                           int lo_bit, int bits, int64_t nb, int64_t* ghist,
+                                                           int64_t* dtot) {
+  cg::grid_group grid = cg::this_grid();
+  u64 *ik = keys, *iv = vals, *ok = tk, *ov = tv;
+  for (int shift = lo_bit; shift < bits; shift += 8) {
+    for (int64_t b = blockIdx.x; b < nb; b += gridDim.x) rs_hist_tile(ik, n, shift, nb, ghist, b);
+    grid.sync();
+    for (int d = blockIdx.x; d < 256; d += gridDim.x) rs_dscan_digit(ghist, nb, dtot, d);
+    grid.sync();
+    for (int64_t b = blockIdx.x; b < nb; b += gridDim.x) rs_scatter_tile(ik, iv, ok, ov, n, shift, nb, ghist, dtot, b);
+    grid.sync();
+    u64* t = ik; ik = ok; ok = t;
+    t = iv; iv = ov; ov = t;
   }
 }
 
@@ -539,6 +583,24 @@ void radix_sort_pairs(u64*& keys, u64*& vals, u64*& tk, u64*& tv, int64_t n, int
   const int64_t nb = (n + RS_TILE - 1) / RS_TILE;
   P.hist.reserve(256 * nb + 1, s);
   P.bsum.reserve(256, s);
+  // up to a few hundred tiles: one cooperative launch for all passes
+  static thread_local int coop_per_sm = -1;
+  if (coop_per_sm < 0) CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&coop_per_sm, k_rs_coop, RS_THREADS, 0));
+  const int64_t coop_max = (int64_t)coop_per_sm * device_sms();
+  if (nb <= coop_max && nb <= 1024) {
+    const int grid = (int)std::max<int64_t>(nb, std::min<int64_t>(256, coop_max));
+    int64_t n_ = n, nb_ = nb;
+    int lo_ = lo_bit, bits_ = bits;
+    int64_t *gh = P.hist.p, *dt = P.bsum.p;
+    void* args[] = {&keys, &vals, &tk, &tv, &n_, &lo_, &bits_, &nb_, &gh, &dt};
+    CK(cudaLaunchCooperativeKernel((const void*)k_rs_coop, dim3(grid), dim3(RS_THREADS), args, 0, s));
+    CKL("k_rs_coop");
+    for (int shift = lo_bit; shift < bits; shift += 8) {  // where the result ended up
+      u64* t = keys; keys = tk; tk = t;
+      t = vals; vals = tv; tv = t;
+    }
+    return;
+  }
   for (int shift = lo_bit; shift < bits; shift += 8) {
     k_rs_hist<<<(unsigned)nb, RS_THREADS, 0, s>>>(keys, n, shift, nb, P.hist.p);
     CKL("k_rs_hist");

@@ -145,6 +145,55 @@ __device__ inline void accumulate(const SweepArgs<WT>& A, const Adj<WT>& adj, in
   }
 }
 
+// accumulate() for a row whose offset and length the caller already holds.
+template <class WT, int MODE>
+__device__ inline void accumulate_row(const SweepArgs<WT>& A, const int32_t* col, const WT* wt, int64_t o, int32_t l,
+                                      int32_t v, int32_t cv_, int32_t* K, int64_t* V, uint32_t mask, int tid,
+                                      int nthreads) {
+  constexpr int ACC = 4;
+  for (int32_t k0 = tid; k0 < l; k0 += ACC * nthreads) {
+    int32_t u[ACC];
+    int64_t w[ACC];
+#pragma unroll
+    for (int j = 0; j < ACC; ++j) {
+      const int32_t k = k0 + j * nthreads;
+      u[j] = k < l ? col[o + k] : -1;
+      w[j] = k < l ? (int64_t)wt[o + k] : 0;
+    }
+    int32_t key[ACC];
+#pragma unroll
+    for (int j = 0; j < ACC; ++j) {
+      key[j] = -1;
+      if (u[j] >= 0 && u[j] != v && (MODE == 0 || A.lab[u[j]] == cv_)) key[j] = MODE == 0 ? A.lab[u[j]] : A.par[u[j]];
+    }
+#pragma unroll
+    for (int j = 0; j < ACC; ++j)
+      if (key[j] >= 0) hash_add(K, V, mask, key[j], w[j]);
+  }
+}
+
+// A node's row offsets and lengths, label and strengths, loaded one node
+// ahead of its sweep so that these dependent loads overlap the previous
+// node's work.
+struct NodeMeta {
+  int32_t v, a, lo, li;
+  int64_t oo, oi, ko, ki;
+};
+
+template <class WT>
+__device__ inline NodeMeta node_meta(const SweepArgs<WT>& A, int32_t v) {
+  NodeMeta m;
+  m.v = v;
+  m.lo = A.out.len[v];
+  m.oo = A.out.off[v];
+  m.li = A.directed ? A.in.len[v] : 0;
+  m.oi = A.directed ? A.in.off[v] : 0;
+  m.a = A.lab[v];
+  m.ko = A.kout[v];
+  m.ki = A.kin[v];
+  return m;
+}
+
 // Exact gain of v into key (see Eq. 2 with a' = a \ {v}).
 template <int MODE>
 __device__ inline i128 gain_of(int32_t key, int64_t acc, int64_t wa, int32_t a, int64_t ko, int64_t ki,
@@ -353,11 +402,15 @@ __global__ void __launch_bounds__(NT) k_sweep_block(SweepArgs<WT> A, const int32
   const int32_t nl = *nlist;
   const int64_t mult = A.directed ? 1 : 2;
   int64_t ent_all = 0, nodes = 0, pairs_all = 0;
+  NodeMeta nxt{};
+  if (blockIdx.x < nl) nxt = node_meta(A, list[blockIdx.x]);
   for (int64_t t = blockIdx.x; t < nl; t += gridDim.x) {
-    const int32_t v = list[t];
+    const NodeMeta cur = nxt;
+    if (t + gridDim.x < nl) nxt = node_meta(A, list[t + gridDim.x]);  // in flight during this node
+    const int32_t v = cur.v;
     int64_t* V = (int64_t*)smem;
     int32_t* K = (int32_t*)(smem + sizeof(int64_t) * HMAX);
-    const int64_t d = (int64_t)A.out.len[v] + (A.directed ? A.in.len[v] : 0);
+    const int64_t d = (int64_t)cur.lo + cur.li;
     uint32_t H = 256;
     while (H < 2 * d && H < HMAX) H <<= 1;
     for (uint32_t k = threadIdx.x; k < H; k += NT) {
@@ -365,12 +418,12 @@ __global__ void __launch_bounds__(NT) k_sweep_block(SweepArgs<WT> A, const int32
       V[k] = 0;
     }
     __syncthreads();
-    const int32_t a = A.lab[v];
-    accumulate<WT, MODE>(A, A.out, v, a, K, V, H - 1, threadIdx.x, NT);
-    if (A.directed) accumulate<WT, MODE>(A, A.in, v, a, K, V, H - 1, threadIdx.x, NT);
+    const int32_t a = cur.a;
+    accumulate_row<WT, MODE>(A, A.out.col, A.out.w, cur.oo, cur.lo, v, a, K, V, H - 1, threadIdx.x, NT);
+    if (A.directed) accumulate_row<WT, MODE>(A, A.in.col, A.in.w, cur.oi, cur.li, v, a, K, V, H - 1, threadIdx.x, NT);
     __syncthreads();
     const int64_t wa = MODE == 0 ? hash_get(K, V, H - 1, a) : 0;
-    const int64_t ko = A.kout[v], ki = A.kin[v];
+    const int64_t ko = cur.ko, ki = cur.ki;
     BestG<GT> b{0, 0, 0};
     int64_t pairs = 0;
     eval_slots<MODE, GT>(K, V, H, threadIdx.x, NT, MODE == 0 ? a : v, a, wa, ko, ki, A.Tout, A.Tin, A.m, A.gn, A.gd,

@@ -156,3 +156,27 @@ def test_random_streams_with_huge_weights(ldl, directed):
             d.apply(b)
             msgs = compare_states(o, d, f"seed {seed} batch {t}")
             assert not msgs, "\n".join(msgs[:8])
+
+
+@pytest.mark.parametrize("directed", [False, True])
+def test_streams_without_rollback_match(ldl, directed):
+    """ldl_params.no_rollback = 1 (no batch snapshot, no undo log) changes no
+    result: the state equals the oracle's after every batch, and the batch
+    estimate of such a context carries no snapshot."""
+    from synth import rmat_directed, rmat_stream
+    if directed:
+        g = rmat_directed(scale=12, arcs=1 << 16, seed=91)
+        bs = rmat_stream(g, batches=5, size=600, seed=91)
+    else:
+        g = planted_partition(n=4000, block=50, seed=91)
+        bs = planted_stream(g, batches=5, size=150, seed=91, block=50)
+    o = Oracle(g)
+    d = ldl.LDL.from_graph(g, no_rollback=1)
+    import ctypes
+    est = ctypes.c_int64()
+    assert ldl.load().ldl_batch_estimate_bytes(d._h, 150, ctypes.byref(est)) == 0 and est.value >= 0
+    for t, b in enumerate(bs):
+        assert o.apply(b) == 0
+        d.apply(b)
+        msgs = compare_states(o, d, f"batch {t}")
+        assert not msgs, "\n".join(msgs[:8])
