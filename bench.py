@@ -48,8 +48,8 @@ WORKLOAD = ("directed R-MAT (0.57,0.19,0.19,0.05), 2^20 vertices, 2^24 arcs, wei
 # workload, divided by the launches that had nodes to sweep: the bins are
 # launched unconditionally and an empty launch moves ~23 KB), valid only for
 # the sweep source it was taken with (sha256 of csrc/sweep.cu).
-NCU_TRAFFIC = {"sha256": "2f7b304250d5ee67e235df5506332dcec7b8be9280adb15f01daba8fca323b4d",
-               "bytes_per_launch": 56684176, "kernel": "sweep_block128"}
+NCU_TRAFFIC = {"sha256": "44c72d96031231d1cd44fb9626a5b9c744343002c49d17ba77891e1eb467f039",
+               "bytes_per_launch": 44905443, "kernel": "sweep_block128"}
 
 
 def _set_rmat_scale(scale: int):
