@@ -399,6 +399,16 @@ void ldl_debug_alloc_counts(int64_t* all, int64_t* in_batch);
 ldl_status ldl_debug_decouple(ldl_ctx* ctx, int64_t count, const int32_t* v, const int32_t* src, const int32_t* dst,
                               const int64_t* g_hi, const uint64_t* g_lo, uint8_t* accepted);
 
+/* Test hook for the device radix sort that orders every record set (batch
+ * updates, aggregate records, pending records, children records) before it
+ * is reduced or applied: sorts `count` (key, value) pairs (host arrays,
+ * replaced by their sorted order) stably by the low `bits` bits of the key
+ * (1 <= bits <= 64; higher key bits must be zero).  The library picks the
+ * one-block, single cooperative launch or multi-launch form by count, as it
+ * does for its own sorts.  Uses the context's scratch buffers and stream
+ * only.  Returns LDL_E_INVALID on bad arguments. */
+ldl_status ldl_debug_sort_pairs(ldl_ctx* ctx, int64_t count, uint64_t* keys, uint64_t* vals, int32_t bits);
+
 /* Test hook for the bounded waits: runs a two-tile device scan in which the
  * first tile never publishes its sum, so the second tile's look-back wait
  * runs out (after about 2^20 polls).  Returns LDL_E_TIMEOUT when the wait gave

@@ -27,11 +27,16 @@ struct LevelState {
   DBuf<int32_t> stA, lA;         // frontier A^r (dedup stamp + list)
   DBuf<int32_t> stK, lK;         // endpoints of arcs deleted since the level was last refined
   int32_t brk_ep = 0;            // epoch of stK
+  // weight records of this level not yet applied to its adjacency (levels >= 1
+  // of a batch update: unsorted, unreduced; count in dcnt[K_PEND0 + r])
+  DBuf<u64> pk, pv;
+  int64_t pend_ub = 0;           // host bound on the pending count
   bool allocated = false;
   void release() {
     out0.release(); in0.release(); out.release(); in.release(); children.release();
     lab.release(); par.release(); cnt.release(); kout.release(); kin.release(); alive.release();
-    stA.release(); lA.release(); stK.release(); lK.release();
+    stA.release(); lA.release(); stK.release(); lK.release(); pk.release(); pv.release();
+    pend_ub = 0;
     allocated = false;
   }
 };
@@ -43,7 +48,8 @@ enum {
   K_G,
   K_A0 = 32,   // K_A0 + r: |A^r|
   K_BRK0 = 48, // K_BRK0 + r: endpoints of deleted level-r arcs
-  K_COUNT = 56
+  K_PEND0 = 56, // K_PEND0 + r: pending weight records of level r
+  K_COUNT = 64
 };
 
 struct ldl_ctx {
@@ -90,8 +96,8 @@ struct ldl_ctx {
   // records
   DBuf<u64> rk, rv, tk, tv, rk2, rv2;
   DBuf<int64_t> rsum, rsum2;
-  DBuf<int32_t> ndx, ndx2;
-  DBuf<int64_t> ndko, ndki, ndko2, ndki2;
+  DBuf<int32_t> ndx;
+  DBuf<int64_t> ndko, ndki;
   DBuf<u64> crk, crv, fk, trk, trv;
   DBuf<int64_t> chunk_pre;
   DBuf<int64_t> hub_ecnt, hub_epre, pb_hi;

@@ -163,32 +163,62 @@ __global__ void k_stat_arcs(const u64* keys, const int64_t* delta, int64_t na, i
   if (sde) atomic_add_i64(de, sde);
 }
 
-// Map level-q records through pi_q to level q+1 (records whose endpoint has
-// no parent are dropped).  Optionally adds strengths and marks A^{q+1}.
-__global__ void k_map_records(const u64* keys, const int64_t* vals, int64_t n, int bits, const int32_t* par,
-                              int64_t* kout, int64_t* kin, int directed, u64* ok, u64* ov, int32_t* cnt) {
+// Per-level pointers for walks up the parent chain (levels 0..7).
+struct Chain {
+  const int32_t* par[8];  // pi_q
+  int64_t* kout[8];
+  int64_t* kin[8];
+  u64* pk[8];             // pending weight records of level q
+  u64* pv[8];
+  int32_t* stA[8];        // frontier A^q: stamp, epoch, list
+  int32_t epA[8];
+  int32_t* lA[8];
+};
+
+// Weight records (keys, vals) of level q0 carried up the hierarchy: with
+// `self` a record joins level q0's pending list; mapped through pi_q0,
+// pi_q0+1, ... it joins the pending list of every level above up to `top`,
+// until an endpoint has no parent (W_{q+1}(pi(i), pi(j)) takes the weight of
+// every level-q arc (i, j)).  With `add_k` the strengths of those levels take
+// the weight as well.  Records are not reduced here: the pending list of a
+// level is sorted, summed and applied when the level is next read.
+__global__ void k_chain_records(const u64* keys, const int64_t* vals, int64_t n, int bits, int q0, int top, int self,
+                                int add_k, int directed, Chain ch, int32_t* pcnt) {
   const u64 mask = (((u64)1) << bits) - 1;
   GRID_STRIDE(t, n) {
-    const int32_t x = par[keys[t] >> bits], y = par[keys[t] & mask];
-    if (x < 0 || y < 0) continue;
+    int32_t x = (int32_t)(keys[t] >> bits), y = (int32_t)(keys[t] & mask);
     const int64_t d = vals[t];
-    if (kout) {
-      atomic_add_i64(&kout[x], d);
-      if (directed) atomic_add_i64(&kin[y], d);
+    if (self) {
+      const int32_t p = atomicAdd(&pcnt[q0], 1);
+      ch.pk[q0][p] = keys[t];
+      ch.pv[q0][p] = (u64)d;
     }
-    const int32_t p = atomicAdd(cnt, 1);
-    ok[p] = ((u64)x << bits) | (u64)y;
-    ov[p] = (u64)d;
+    for (int q = q0; q < top; ++q) {
+      x = ch.par[q][x];
+      y = ch.par[q][y];
+      if (x < 0 || y < 0) break;
+      if (add_k) {
+        atomic_add_i64(&ch.kout[q + 1][x], d);
+        if (directed) atomic_add_i64(&ch.kin[q + 1][y], d);
+      }
+      const int32_t p = atomicAdd(&pcnt[q + 1], 1);
+      ch.pk[q + 1][p] = ((u64)x << bits) | (u64)y;
+      ch.pv[q + 1][p] = (u64)d;
+    }
   }
 }
 
-// InitFrontier above level 0: A^{q+1} = pi_q(A^q).
-__global__ void k_map_list(const int32_t* l, const int32_t* n, const int32_t* par, int32_t* stA, int32_t epA,
-                           int32_t* lA, int32_t* nA) {
-  const int32_t m = *n;
+// InitFrontier above level 0: A^{q+1} = pi_q(A^q) for every q < top, by
+// walking each node of A^0 up its parent chain.  A walk stops at a node that
+// is already marked: the walk that marked it goes on above it.
+__global__ void k_chain_frontier(const int32_t* l0, const int32_t* n0, int top, Chain ch, int32_t* nA) {
+  const int32_t m = *n0;
   for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x) {
-    const int32_t p = par[l[k]];
-    if (p >= 0) stamp_add(stA, epA, p, lA, nA);
+    int32_t x = l0[k];
+    for (int q = 0; q < top; ++q) {
+      x = ch.par[q][x];
+      if (x < 0 || !stamp_add(ch.stA[q + 1], ch.epA[q + 1], x, ch.lA[q + 1], &nA[q + 1])) break;
+    }
   }
 }
 
@@ -594,18 +624,21 @@ __global__ void k_emit_nodes(const int32_t* lC, const int32_t* nC, const int32_t
   }
 }
 
-__global__ void k_map_nodes(const int32_t* ndx, const int64_t* ndko, const int64_t* ndki, int32_t n,
-                            const int32_t* par, int64_t* kout, int64_t* kin, int directed, int32_t* ox,
-                            int64_t* oko, int64_t* oki, int32_t* cnt) {
-  for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-    const int32_t x = par[ndx[k]];
-    if (x < 0) continue;
-    atomic_add_i64(&kout[x], ndko[k]);
-    if (directed) atomic_add_i64(&kin[x], ndki[k]);
-    const int32_t p = atomicAdd(cnt, 1);
-    ox[p] = x;
-    oko[p] = ndko[k];
-    oki[p] = ndki[k];
+// Strength moves (node, out delta, in delta) of level-q0 nodes carried to
+// every ancestor level up to `top` (the strengths of a supernode are the sums
+// of its members').
+__global__ void k_chain_nodes(const int32_t* ndx, const int64_t* ndko, const int64_t* ndki, const int32_t* n,
+                              int q0, int top, int directed, Chain ch) {
+  const int32_t m = *n;
+  for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x) {
+    int32_t x = ndx[k];
+    const int64_t ko = ndko[k], ki = ndki[k];
+    for (int q = q0; q < top; ++q) {
+      x = ch.par[q][x];
+      if (x < 0) break;
+      atomic_add_i64(&ch.kout[q + 1][x], ko);
+      if (directed) atomic_add_i64(&ch.kin[q + 1][x], ki);
+    }
   }
 }
 
@@ -890,15 +923,15 @@ static void combine_in_out(ldl_ctx& c, const u64* keys, const u64* vals, int64_t
 // apply sorted unique records to a level's adjacency (both directions); the
 // endpoints of arcs that disappear are recorded for the level's next
 // refinement
-static void apply_level(ldl_ctx& c, int r, DBuf<u64>& keys, DBuf<u64>& vals, int64_t nr) {
+static void apply_level(ldl_ctx& c, int r, const u64* keys, const int64_t* vals, int64_t nr) {
   if (nr <= 0) return;
   LevelState& Lr = c.lv[r];
   const DelTrack trk{Lr.stK.p, Lr.brk_ep, Lr.lK.p, c.dcnt + K_BRK0 + r, c.n};
-  const u64* k = keys.p;
-  const u64* v = vals.p;
+  const u64* k = keys;
+  const u64* v = (const u64*)vals;
   int64_t m = nr;
   if (c.directed) {
-    combine_in_out(c, keys.p, vals.p, nr);
+    combine_in_out(c, keys, (const u64*)vals, nr);
     k = c.rk2.p;
     v = c.rv2.p;
     m = 2 * nr;
@@ -909,31 +942,65 @@ static void apply_level(ldl_ctx& c, int r, DBuf<u64>& keys, DBuf<u64>& vals, int
     csr_apply<int64_t>(c.lv[r].out, k, (const int64_t*)v, m, c.bits, c.CS, c.P, c.s, c.d_sc, &trk);
 }
 
-// Map records (keys, vals) of level q to level q+1, reduce, and apply there.
-// Result (reduced) ends in (keys, vals); returns the count.
-static int64_t propagate_once(ldl_ctx& c, int q, DBuf<u64>& keys, DBuf<u64>& vals, int64_t n, bool add_k) {
-  if (n <= 0) return 0;
-  LevelState& up = c.lv[q + 1];
-  c.rk2.reserve(n, c.s);
-  c.rv2.reserve(n, c.s);
-  zero_cnt(c, K_REC);
-  k_map_records<<<grid_for(n, TPB), TPB, 0, c.s>>>(keys.p, (const int64_t*)vals.p, n, c.bits, c.lv[q].par.p,
-                                                   add_k ? up.kout.p : nullptr, add_k ? kin_of(c, q + 1) : nullptr,
-                                                   c.directed, c.rk2.p, c.rv2.p, c.dcnt + K_REC);
-  CKL("k_map_records");
-  const int64_t nm = rd_cnt(c, K_REC);
-  sort_pairs(c.rk2, c.rv2, c.tk, c.tv, nm, 2 * c.bits, c.P, c.s);
-  c.rsum.reserve(nm + 1, c.s);
-  const int64_t nr = reduce_by_key(c.rk2.p, c.rv2.p, nm, keys.p, c.rsum.p, c.P, c.s);
-  if (nr) CK(cudaMemcpyAsync(vals.p, c.rsum.p, sizeof(int64_t) * (size_t)nr, cudaMemcpyDeviceToDevice, c.s));
-  apply_level(c, q + 1, keys, vals, nr);
-  return nr;
+static Chain chain_of(ldl_ctx& c, const int32_t* epA) {
+  Chain ch{};
+  for (int q = 0; q <= c.T && q < 8; ++q) {
+    LevelState& L = c.lv[q];
+    ch.par[q] = L.par.p;
+    ch.kout[q] = L.kout.p;
+    ch.kin[q] = kin_of(c, q);
+    ch.pk[q] = L.pk.p;
+    ch.pv[q] = L.pv.p;
+    ch.stA[q] = L.stA.p;
+    ch.lA[q] = L.lA.p;
+    ch.epA[q] = epA ? epA[q] : 0;
+  }
+  return ch;
+}
+
+// Records of level q0 onto the pending lists of level q0 (with `self`) and
+// of every level above: each list is grown (keeping its contents) to hold n
+// more.
+static void chain_records(ldl_ctx& c, const u64* keys, const int64_t* vals, int64_t n, int q0, bool self,
+                          bool add_k) {
+  if (n <= 0 || (!self && q0 >= c.T)) return;
+  for (int q = self ? q0 : q0 + 1; q <= c.T; ++q) {
+    LevelState& L = c.lv[q];
+    L.pk.reserve(L.pend_ub + n + 1, c.s, true);
+    L.pv.reserve(L.pend_ub + n + 1, c.s, true);
+    L.pend_ub += n;
+  }
+  k_chain_records<<<grid_for(n, TPB), TPB, 0, c.s>>>(keys, vals, n, c.bits, q0, c.T, self ? 1 : 0, add_k ? 1 : 0,
+                                                     c.directed, chain_of(c, nullptr), c.dcnt + K_PEND0);
+  CKL("k_chain_records");
+}
+
+void pending_reset(ldl_ctx& c) {
+  for (auto& L : c.lv) L.pend_ub = 0;
+  CK(cudaMemsetAsync(c.dcnt + K_PEND0, 0, sizeof(int32_t) * 8, c.s));
+}
+
+// Level q's pending records, sorted by (row, col) and summed per arc (zero
+// sums dropped), applied to its adjacency: the level's weights become
+// current before anything reads them.
+void flush_level(ldl_ctx& c, int q) {
+  LevelState& L = c.lv[q];
+  if (L.pend_ub == 0) return;
+  const int64_t n = rd_cnt(c, K_PEND0 + q);
+  L.pend_ub = 0;
+  zero_cnt(c, K_PEND0 + q);
+  if (n <= 0) return;
+  sort_pairs(L.pk, L.pv, c.tk, c.tv, n, 2 * c.bits, c.P, c.s);
+  c.rk.reserve(n + 1, c.s);
+  c.rsum.reserve(n + 1, c.s);
+  const int64_t nr = reduce_by_key(L.pk.p, L.pv.p, n, c.rk.p, c.rsum.p, c.P, c.s);
+  apply_level(c, q, c.rk.p, c.rsum.p, nr);
 }
 
 void repair_batch(ldl_ctx& c, int64_t na, const int32_t* epA, int32_t epT, int64_t dm) {
   if (na <= 0) return;
   // Algorithm 1, applying the batch: it changes level 0
-  apply_level(c, 0, c.rk, c.rv, na);
+  apply_level(c, 0, c.rk.p, (const int64_t*)c.rv.p, na);
   // statistic repair: m, degrees, community totals (exactly, with sum_C K_out K_in)
   LevelState& L0 = c.lv[0];
   zero_cnt(c, K_T);
@@ -957,18 +1024,14 @@ void repair_batch(ldl_ctx& c, int64_t na, const int32_t* epA, int32_t epT, int64
   c.m += dm;
   c.E += de;
   c.Psum += i128_of(p_new.hi, p_new.lo) - i128_of(p_old.hi, p_old.lo);
-  // the aggregate chain: W_r(anc(i), anc(j)) += delta, strengths, A^r
-  int64_t cur = na;
-  for (int q = 0; q < c.T; ++q) {
-    const int32_t nq = rd_cnt(c, K_A0 + q);
-    if (nq > 0) {
-      k_map_list<<<grid_for(nq, TPB), TPB, 0, c.s>>>(c.lv[q].lA.p, c.dcnt + K_A0 + q, c.lv[q].par.p,
-                                                     c.lv[q + 1].stA.p, epA[q + 1], c.lv[q + 1].lA.p,
-                                                     c.dcnt + K_A0 + q + 1);
-      CKL("k_map_list");
-    }
-    if (cur > 0) cur = propagate_once(c, q, c.rk, c.rv, cur, true);
-  }
+  if (c.T == 0) return;
+  // InitFrontier: A^{q+1} = pi_q(A^q) along the chain
+  k_chain_frontier<<<grid_for(2 * na, TPB), TPB, 0, c.s>>>(L0.lA.p, c.dcnt + K_A0, c.T, chain_of(c, epA),
+                                                           c.dcnt + K_A0);
+  CKL("k_chain_frontier");
+  // the aggregate chain: W_q(anc(i), anc(j)) += delta and the strengths of
+  // every level above 0; the weights are applied when each level is next read
+  chain_records(c, c.rk.p, (const int64_t*)c.rv.p, na, 0, false, true);
 }
 
 void pushdown(ldl_ctx& c, int r, int32_t epCh) {
@@ -1193,30 +1256,18 @@ void aggregate(ldl_ctx& c, int r, int32_t epD, int32_t epC, int32_t epA_next, bo
       }
       csr_build<int32_t>(L.children, c.n, c.crk.p, (const int64_t*)c.crv.p, ncr, c.bits, 25, c.CS, c.P, c.s);
     } else {
-      apply_level(c, r + 1, c.rk, c.rv, nr);
+      // the level r+1 records join its pending list and, mapped through the
+      // current parents, the lists of the levels above; the strength moves
+      // reach every ancestor level at once
+      chain_records(c, c.rk.p, (const int64_t*)c.rv.p, nr, r + 1, true, false);
       csr_apply<int32_t>(L.children, c.crk.p, (const int64_t*)c.crv.p, ncr, c.bits, c.CS, c.P, c.s, c.d_sc);
     }
     sub_end(c, SU_AGG_APPLY);
     sub_begin(c);
-    // propagate level r+1 changes up the current parent chain
-    int64_t cur = nr;
-    int32_t nnd = rd_cnt(c, K_NREC);
-    for (int q = r + 1; q < c.T; ++q) {
-      if (cur > 0) cur = propagate_once(c, q, c.rk, c.rv, cur, false);
-      if (nnd > 0) {
-        c.ndx2.reserve(nnd + 1, c.s);
-        c.ndko2.reserve(nnd + 1, c.s);
-        c.ndki2.reserve(nnd + 1, c.s);
-        zero_cnt(c, K_TMP);
-        k_map_nodes<<<grid_for(nnd, TPB), TPB, 0, c.s>>>(c.ndx.p, c.ndko.p, c.ndki.p, nnd, c.lv[q].par.p,
-                                                         c.lv[q + 1].kout.p, kin_of(c, q + 1), c.directed,
-                                                         c.ndx2.p, c.ndko2.p, c.ndki2.p, c.dcnt + K_TMP);
-        CKL("k_map_nodes");
-        nnd = rd_cnt(c, K_TMP);
-        swap_buf(c.ndx, c.ndx2);
-        swap_buf(c.ndko, c.ndko2);
-        swap_buf(c.ndki, c.ndki2);
-      }
+    if (!build && r + 1 < c.T) {
+      k_chain_nodes<<<grid_for(2 * (int64_t)nC, TPB), TPB, 0, c.s>>>(c.ndx.p, c.ndko.p, c.ndki.p, c.dcnt + K_NREC,
+                                                                      r + 1, c.T, c.directed, chain_of(c, nullptr));
+      CKL("k_chain_nodes");
     }
     sub_end(c, SU_AGG_UP);
     sub_begin(c);

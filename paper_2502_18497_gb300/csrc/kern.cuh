@@ -45,6 +45,8 @@ int64_t ingest(ldl_ctx& c, const ldl_update* upd, int64_t count, int on_device, 
 // Apply the level-0 arcs to the adjacency and repair every statistic along
 // the parent chain; marks InitFrontier in the A lists (epA per level).
 void repair_batch(ldl_ctx& c, int64_t na, const int32_t* epA, int32_t epT, int64_t dm);
+void pending_reset(ldl_ctx& c);
+void flush_level(ldl_ctx& c, int q);
 void pushdown(ldl_ctx& c, int r, int32_t epCh);
 int32_t dissolve_all(ldl_ctx& c, int r, int32_t epD);
 int32_t split(ldl_ctx& c, int r, int32_t epD, int32_t epX);

@@ -218,14 +218,14 @@ void free_all(ldl_ctx& c) {
   if (c.s) cudaStreamSynchronize(c.s);
   for (auto& L : c.lv) L.release();
   DBuf<int64_t>* b64[] = {&c.Kout, &c.Kin, &c.e, &c.cghi, &c.snapKo, &c.snapKi, &c.snapE, &c.binLoff, &c.binLsz,
-                          &c.gvals, &c.rsum, &c.rsum2, &c.ndko, &c.ndki, &c.ndko2, &c.ndki2,
+                          &c.gvals, &c.rsum, &c.rsum2, &c.ndko, &c.ndki,
                           &c.chunk_pre, &c.hub_ecnt, &c.hub_epre, &c.pb_hi};
   for (auto* b : b64) b->release();
   DBuf<int32_t>* b32[] = {&c.stS, &c.stU, &c.stMv, &c.stB, &c.stM0, &c.stD, &c.stC, &c.stR, &c.stX, &c.stT,
                           &c.stE, &c.stCh, &c.stL, &c.lG, &c.comp, &c.nbr, &c.ckf, &c.lU, &c.lS, &c.lUstar, &c.lMv, &c.lM0, &c.lD, &c.lC, &c.lR,
                           &c.lR2, &c.lX, &c.lT, &c.lE, &c.lE2, &c.lCh, &c.lChg, &c.lTmp, &c.cv, &c.csrc,
                           &c.cdst, &c.cst, &c.bv, &c.bsrc, &c.bdst, &c.best, &c.role, &c.oldlab, &c.par_old,
-                          &c.lab_before, &c.binT, &c.binS, &c.binM, &c.binM2, &c.binC, &c.binL, &c.gkeys, &c.ndx, &c.ndx2,
+                          &c.lab_before, &c.binT, &c.binS, &c.binM, &c.binM2, &c.binC, &c.binL, &c.gkeys, &c.ndx,
                           &c.glist, &c.hcnt};
   for (auto* b : b32) b->release();
   DBuf<u64>* bu[] = {&c.rk, &c.rv, &c.tk, &c.tv, &c.rk2, &c.rv2, &c.crk, &c.crv, &c.fk, &c.trk, &c.trv};
@@ -467,6 +467,7 @@ static void txn_rollback(ldl_ctx& c) {
 static void apply_batch(ldl_ctx& c, const ldl_update* upd, int64_t count, int on_device) {
   memset(&c.res, 0, sizeof(c.res));
   c.syncs = 0;
+  pending_reset(c);
   CK(cudaMemsetAsync(&c.d_sc->scanned, 0, sizeof(int64_t), c.s));
   const int T = c.T;
   int64_t dm = 0;
@@ -510,6 +511,9 @@ static void apply_batch(ldl_ctx& c, const ldl_update* upd, int64_t count, int on
       union_into(c, c.lU.p, K_U, c.stU.p, epU, c.lUstar.p, K_USTAR, nU);
       const int32_t epMv = c.next_epoch();
       zero_cnt(c, K_MV);
+      stage_begin(c);
+      flush_level(c, r);  // the level's weights are read from here on
+      stage_end(c, ST_AGG);
       move_loop(c, r, c.prm.M, epU, epMv, epM0, epCh, nU);
       if (r > 0) {
         stage_begin(c);
@@ -542,6 +546,9 @@ static void apply_batch(ldl_ctx& c, const ldl_update* upd, int64_t count, int on
     if (rd_cnt(c, K_A0) == 0) break;
     if ((qnum(c) - Qpass) * (i128)ainv < Qpass) break;
   }
+  stage_begin(c);
+  for (int r = 1; r <= T; ++r) flush_level(c, r);
+  stage_end(c, ST_AGG);
   c.res.n_changed = changed_labels(c, epCh);
   if (rd_cnt(c, K_ERR)) ldl_throw(LDL_E_INVALID, "internal: new supernode already has a parent");
   c.res.host_syncs = c.syncs;
@@ -744,6 +751,8 @@ ldl_status ldl_batch_estimate_bytes(const ldl_ctx* c, int64_t count, int64_t* by
   // in about four 16-byte buffers (keys, values, sort scratch)
   const int64_t rec = 16 * count * levels;
   b += std::max<int64_t>(0, rec - c->rk.cap) * 16 * 4;
+  // pending records of the levels above 0, applied when a level is next read
+  for (int r = 1; r <= c->T; ++r) b += std::max<int64_t>(0, rec - c->lv[r].pk.cap) * 16;
   // a pool whose headroom is short may be compacted into one twice its live
   // capacity, kept beside the old one until the batch commits
   auto pool = [&](const auto& g, int64_t wbytes) {
@@ -922,6 +931,51 @@ ldl_status ldl_debug_scan_wait_timeout(void) {
 }
 
 int64_t ldl_launch_count(void) { return g_launches.load(); }
+
+ldl_status ldl_debug_sort_pairs(ldl_ctx* c, int64_t count, uint64_t* keys, uint64_t* vals, int32_t bits) {
+  if (!c || count < 0 || bits < 1 || bits > 64 || (count > 0 && (!keys || !vals))) return LDL_E_INVALID;
+  if (bits < 64) {
+    for (int64_t i = 0; i < count; ++i)
+      if (keys[i] >> bits) {
+        c->err = "ldl_debug_sort_pairs: a key has bits above `bits`";
+        return LDL_E_INVALID;
+      }
+  }
+  ldl_ctx& x = *c;
+  DBuf<u64> dk, dv, tk, tv;
+  ldl_status st = LDL_OK;
+  try {
+    DeviceScope ds(c->dev);
+    const size_t k = (size_t)count;
+    dk.reserve(count + 1, x.s);
+    dv.reserve(count + 1, x.s);
+    if (k) {
+      CK(cudaMemcpyAsync(dk.p, keys, 8 * k, cudaMemcpyHostToDevice, x.s));
+      CK(cudaMemcpyAsync(dv.p, vals, 8 * k, cudaMemcpyHostToDevice, x.s));
+    }
+    sort_pairs(dk, dv, tk, tv, count, bits, x.P, x.s);
+    if (k) {
+      CK(cudaMemcpyAsync(keys, dk.p, 8 * k, cudaMemcpyDeviceToHost, x.s));
+      CK(cudaMemcpyAsync(vals, dv.p, 8 * k, cudaMemcpyDeviceToHost, x.s));
+    }
+    CK(cudaStreamSynchronize(x.s));
+  } catch (const LdlError& e) {
+    c->err = e.msg;
+    cudaGetLastError();
+    st = e.st;
+  }
+  try {
+    DeviceScope ds(c->dev);
+    cudaStreamSynchronize(x.s);
+    dk.release();
+    dv.release();
+    tk.release();
+    tv.release();
+  } catch (const LdlError& e) {
+    if (st == LDL_OK) st = e.st;
+  }
+  return st;
+}
 
 ldl_status ldl_debug_decouple(ldl_ctx* c, int64_t count, const int32_t* v, const int32_t* src, const int32_t* dst,
                               const int64_t* g_hi, const uint64_t* g_lo, uint8_t* accepted) {

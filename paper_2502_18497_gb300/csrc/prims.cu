@@ -332,70 +332,192 @@ __global__ void __launch_bounds__(RS_THREADS, 4) k_rs_coop(u64* keys, u64* vals,
   }
 }
 
-// Whole sort in one block (n <= RS_TILE): every pass in shared memory.
+// Whole sort in one block (n <= RS_TILE).  Each thread holds RS_ITEMS pairs
+// in registers across the passes: per 8-bit pass every warp ranks its
+// contiguous sub-tile (rounds of 32, stable), the block turns the per-warp
+// digit counts into positions, the pairs are placed in shared memory in
+// digit order and read back in the same warp-contiguous layout.
 __global__ void __launch_bounds__(RS_THREADS) k_rs_small(u64* keys, u64* vals, int n, int lo_bit, int bits) {
-  extern __shared__ u64 sm[];
-  u64* kb[2] = {sm, sm + RS_TILE};
-  u64* vb[2] = {sm + 2 * RS_TILE, sm + 3 * RS_TILE};
-  __shared__ int32_t hist[256];
-  __shared__ int64_t run[256];
-  __shared__ int32_t tot[256];
-  __shared__ int32_t wcnt[RS_THREADS / WARP][257];
+  constexpr int NW = RS_THREADS / WARP;
+  __shared__ int32_t whist[NW][256];
+  __shared__ int32_t tstart[256];
+  __shared__ u64 sk[RS_TILE];
+  __shared__ u64 sv[RS_TILE];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  for (int i = tid; i < n; i += RS_THREADS) {
-    kb[0][i] = keys[i];
-    vb[0][i] = vals[i];
+  u64 key[RS_ITEMS], val[RS_ITEMS];
+  for (int k = 0; k < RS_ITEMS; ++k) {
+    const int li = wid * (RS_ITEMS * 32) + k * 32 + lane;
+    key[k] = li < n ? keys[li] : 0;
+    val[k] = li < n ? vals[li] : 0;
   }
-  int cur = 0;
   for (int shift = lo_bit; shift < bits; shift += 8) {
-    for (int d = tid; d < 256; d += RS_THREADS) hist[d] = 0;
-    __syncthreads();
-    for (int i = tid; i < n; i += RS_THREADS) atomicAdd(&hist[(kb[cur][i] >> shift) & 255], 1);
-    __syncthreads();
-    if (tid == 0) {
-      int64_t acc = 0;
-      for (int d = 0; d < 256; ++d) {
-        run[d] = acc;
-        acc += hist[d];
-      }
-    }
-    __syncthreads();
-    for (int ch = 0; ch * RS_THREADS < n; ++ch) {
-      const int i = ch * RS_THREADS + tid;
-      const bool valid = i < n;
-      const u64 key = valid ? kb[cur][i] : 0;
-      const u64 val = valid ? vb[cur][i] : 0;
-      const int d = valid ? (int)((key >> shift) & 255) : 256;
-      for (int x = lane; x < 257; x += 32) wcnt[wid][x] = 0;
-      __syncwarp();
+    for (int d = lane; d < 256; d += 32) whist[wid][d] = 0;
+    __syncwarp();
+    int rk[RS_ITEMS];
+    for (int k = 0; k < RS_ITEMS; ++k) {
+      const int li = wid * (RS_ITEMS * 32) + k * 32 + lane;
+      const int d = li < n ? (int)((key[k] >> shift) & 255) : 256;
       const unsigned peers = __match_any_sync(0xffffffffu, d);
-      const int rank = __popc(peers & ((1u << lane) - 1u));
-      if (rank == 0) wcnt[wid][d] = __popc(peers);
-      __syncthreads();
-      if (tid < 256) {
-        int acc = 0;
-        for (int w = 0; w < RS_THREADS / WARP; ++w) {
-          int cc = wcnt[w][tid];
-          wcnt[w][tid] = acc;
-          acc += cc;
-        }
-        tot[tid] = acc;
-      }
-      __syncthreads();
-      if (valid) {
-        const int64_t pos = run[d] + wcnt[wid][d] + rank;
-        kb[cur ^ 1][pos] = key;
-        vb[cur ^ 1][pos] = val;
-      }
-      __syncthreads();
-      if (tid < 256) run[tid] += tot[tid];
-      __syncthreads();
+      const int before = d < 256 ? whist[wid][d] : 0;
+      rk[k] = before + __popc(peers & ((1u << lane) - 1u));
+      __syncwarp();
+      if (d < 256 && lane == __ffs(peers) - 1) whist[wid][d] = before + __popc(peers);
+      __syncwarp();
     }
-    cur ^= 1;
+    __syncthreads();
+    int cnt = 0;
+    for (int w = 0; w < NW; ++w) {  // thread = digit (RS_THREADS == 256)
+      const int c = whist[w][tid];
+      whist[w][tid] = cnt;
+      cnt += c;
+    }
+    int64_t total;
+    tstart[tid] = (int32_t)block_excl_scan_i64(cnt, &total);
+    __syncthreads();
+    for (int k = 0; k < RS_ITEMS; ++k) {
+      const int li = wid * (RS_ITEMS * 32) + k * 32 + lane;
+      if (li < n) {
+        const int d = (int)((key[k] >> shift) & 255);
+        const int p = tstart[d] + whist[wid][d] + rk[k];
+        sk[p] = key[k];
+        sv[p] = val[k];
+      }
+    }
+    __syncthreads();
+    for (int k = 0; k < RS_ITEMS; ++k) {
+      const int li = wid * (RS_ITEMS * 32) + k * 32 + lane;
+      if (li < n) {
+        key[k] = sk[li];
+        val[k] = sv[li];
+      }
+    }
+    __syncthreads();  // whist, tstart and the staging buffers are rewritten next pass
   }
-  for (int i = tid; i < n; i += RS_THREADS) {
-    keys[i] = kb[cur][i];
-    vals[i] = vb[cur][i];
+  for (int k = 0; k < RS_ITEMS; ++k) {
+    const int li = wid * (RS_ITEMS * 32) + k * 32 + lane;
+    if (li < n) {
+      keys[li] = key[k];
+      vals[li] = val[k];
+    }
+  }
+}
+
+// Whole sort in one thread-block cluster of CS_CL blocks (n <= CS_CL *
+// CS_TILE): block c holds the pairs at positions [c * CS_TILE, (c+1) *
+// CS_TILE), CS_ITEMS per thread in registers.  Per 8-bit pass every warp
+// ranks its contiguous sub-tile (stable), each block publishes its digit
+// counts in shared memory, and after a cluster barrier every block reads all
+// blocks' counts (distributed shared memory) to place each of its pairs at
+// its global position: digit start + counts of lower blocks + counts of
+// lower warps + rank.  The pair is stored into the shared memory of the block
+// that owns that position; after a second barrier each block reloads its
+// slice.  The pairs never leave the chip between passes.
+constexpr int CS_THREADS = 512;
+constexpr int CS_ITEMS = 12;
+constexpr int CS_TILE = CS_THREADS * CS_ITEMS;  // 6144 pairs, 96 KB per block
+constexpr int CS_CL = 8;
+constexpr int CS_NW = CS_THREADS / WARP;
+constexpr int CS_MAX = CS_CL * CS_TILE;
+
+__global__ void __cluster_dims__(CS_CL, 1, 1) __launch_bounds__(CS_THREADS, 1)
+    k_rs_cluster(u64* keys, u64* vals, int n, int lo_bit, int bits) {
+  extern __shared__ u64 cs_smem[];
+  u64* sk = cs_smem;
+  u64* sv = cs_smem + CS_TILE;
+  __shared__ int32_t whist[CS_NW][256];
+  __shared__ int32_t hist[256];   // this block's digit counts, read by the whole cluster
+  __shared__ int32_t s_tot[256];  // cluster-wide digit counts
+  __shared__ int32_t tpos[256];   // global start of (digit, this block)
+  cg::cluster_group cl = cg::this_cluster();
+  const int c = (int)cl.block_rank();
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int base = c * CS_TILE;
+  const int tile_n = max(0, min(CS_TILE, n - base));
+  u64 key[CS_ITEMS], val[CS_ITEMS];
+  for (int k = 0; k < CS_ITEMS; ++k) {
+    const int li = wid * (CS_ITEMS * 32) + k * 32 + lane;
+    key[k] = li < tile_n ? keys[base + li] : 0;
+    val[k] = li < tile_n ? vals[base + li] : 0;
+  }
+  for (int shift = lo_bit; shift < bits; shift += 8) {
+    for (int d = lane; d < 256; d += 32) whist[wid][d] = 0;
+    __syncwarp();
+    int rk[CS_ITEMS];
+    for (int k = 0; k < CS_ITEMS; ++k) {
+      const int li = wid * (CS_ITEMS * 32) + k * 32 + lane;
+      const int d = li < tile_n ? (int)((key[k] >> shift) & 255) : 256;
+      const unsigned peers = __match_any_sync(0xffffffffu, d);
+      const int before = d < 256 ? whist[wid][d] : 0;
+      rk[k] = before + __popc(peers & ((1u << lane) - 1u));
+      __syncwarp();
+      if (d < 256 && lane == __ffs(peers) - 1) whist[wid][d] = before + __popc(peers);
+      __syncwarp();
+    }
+    __syncthreads();
+    if (tid < 256) {  // thread = digit: exclusive prefix over the warps
+      int cnt = 0;
+      for (int w = 0; w < CS_NW; ++w) {
+        const int x = whist[w][tid];
+        whist[w][tid] = cnt;
+        cnt += x;
+      }
+      hist[tid] = cnt;
+    }
+    cl.sync();  // every block's counts are published
+    if (tid < 256) {
+      int tot = 0, lower = 0;
+      for (int b = 0; b < CS_CL; ++b) {
+        const int x = cl.map_shared_rank(hist, b)[tid];
+        tot += x;
+        if (b < c) lower += x;
+      }
+      s_tot[tid] = tot;
+      tpos[tid] = lower;
+    }
+    __syncthreads();
+    if (wid == 0) {  // digit starts: exclusive scan of the totals, 8 digits per lane
+      int v[8], sum = 0;
+      for (int j = 0; j < 8; ++j) {
+        v[j] = s_tot[lane * 8 + j];
+        sum += v[j];
+      }
+      int incl = sum;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      int run = incl - sum;
+      for (int j = 0; j < 8; ++j) {
+        tpos[lane * 8 + j] += run;
+        run += v[j];
+      }
+    }
+    __syncthreads();
+    for (int k = 0; k < CS_ITEMS; ++k) {
+      const int li = wid * (CS_ITEMS * 32) + k * 32 + lane;
+      if (li < tile_n) {
+        const int d = (int)((key[k] >> shift) & 255);
+        const int p = tpos[d] + whist[wid][d] + rk[k];
+        const int owner = p / CS_TILE, slot = p - owner * CS_TILE;
+        cl.map_shared_rank(sk, owner)[slot] = key[k];
+        cl.map_shared_rank(sv, owner)[slot] = val[k];
+      }
+    }
+    cl.sync();  // every pair is in place; counts and staging are reused next pass
+    for (int k = 0; k < CS_ITEMS; ++k) {
+      const int li = wid * (CS_ITEMS * 32) + k * 32 + lane;
+      if (li < tile_n) {
+        key[k] = sk[li];
+        val[k] = sv[li];
+      }
+    }
+  }
+  for (int k = 0; k < CS_ITEMS; ++k) {
+    const int li = wid * (CS_ITEMS * 32) + k * 32 + lane;
+    if (li < tile_n) {
+      keys[base + li] = key[k];
+      vals[base + li] = val[k];
+    }
   }
 }
 
@@ -574,10 +696,21 @@ void radix_sort_pairs(u64*& keys, u64*& vals, u64*& tk, u64*& tv, int64_t n, int
                       int lo_bit) {
   if (n <= 1 || bits <= lo_bit) return;
   if (n <= RS_TILE) {
-    const int smem = 4 * RS_TILE * (int)sizeof(u64);
-    CK(cudaFuncSetAttribute(k_rs_small, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    k_rs_small<<<1, RS_THREADS, smem, s>>>(keys, vals, (int)n, lo_bit, bits);
+    k_rs_small<<<1, RS_THREADS, 0, s>>>(keys, vals, (int)n, lo_bit, bits);
     CKL("k_rs_small");
+    return;
+  }
+  if (n <= CS_MAX) {  // one cluster, the pairs kept on chip
+    const int smem = 2 * CS_TILE * (int)sizeof(u64);
+    static thread_local int cs_attr_dev = -1;
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    if (cs_attr_dev != dev) {
+      CK(cudaFuncSetAttribute(k_rs_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+      cs_attr_dev = dev;
+    }
+    k_rs_cluster<<<CS_CL, CS_THREADS, smem, s>>>(keys, vals, (int)n, lo_bit, bits);
+    CKL("k_rs_cluster");
     return;
   }
   const int64_t nb = (n + RS_TILE - 1) / RS_TILE;

@@ -94,6 +94,7 @@ def load(path: Optional[str] = None):
         "ldl_server_wait": (I32, [P, I64, I32, P, P, P, P]),
         "ldl_server_destroy": (None, [P]),
         "ldl_debug_decouple": (I32, [P, I64, P, P, P, P, P, P]),
+        "ldl_debug_sort_pairs": (I32, [P, I64, P, P, I32]),
         "ldl_debug_alloc_counts": (None, [P, P]),
         "ldl_batch_estimate_bytes": (I32, [P, I64, P]),
         "ldl_server_stats": (I32, [P, P, P]),
@@ -122,7 +123,7 @@ def exported_symbols():
             "ldl_server_create", "ldl_server_admit", "ldl_server_submit", "ldl_server_wait",
             "ldl_server_destroy", "ldl_debug_decouple", "ldl_debug_alloc_counts", "ldl_batch_estimate_bytes",
             "ldl_server_stats", "ldl_server_debug_free_bytes", "ldl_save", "ldl_load", "ldl_grow",
-            "ldl_num_vertices", "ldl_is_directed"]
+            "ldl_num_vertices", "ldl_is_directed", "ldl_debug_sort_pairs"]
 
 
 def launch_count() -> int:
@@ -350,6 +351,14 @@ class LDL:
         self._check(load().ldl_debug_decouple(self._h, len(v), _ptr(v), _ptr(src), _ptr(dst), _ptr(hi), _ptr(lo),
                                               _ptr(out)))
         return out
+
+    def debug_sort_pairs(self, keys, vals, bits: int):
+        """Sorts (key, value) pairs on the device, stably by the low `bits`
+        key bits; returns the sorted copies."""
+        k = np.array(keys, dtype=np.uint64, copy=True)
+        v = np.array(vals, dtype=np.uint64, copy=True)
+        self._check(load().ldl_debug_sort_pairs(self._h, len(k), _ptr(k), _ptr(v), bits))
+        return k, v
 
     def hierarchy(self):
         """Per level r of the last result: (parent, comm, refined, alive) copied

@@ -180,3 +180,30 @@ def test_streams_without_rollback_match(ldl, directed):
         d.apply(b)
         msgs = compare_states(o, d, f"batch {t}")
         assert not msgs, "\n".join(msgs[:8])
+
+
+@pytest.mark.parametrize("count,bits,dup", [
+    (0, 40, 1), (1, 40, 1), (2, 8, 1), (300, 16, 7), (2047, 40, 1), (2048, 40, 3), (2049, 40, 1),
+    (5000, 9, 50), (6144, 40, 2), (6145, 40, 1), (40000, 40, 4), (49152, 40, 3), (49153, 33, 1),
+    (300000, 40, 8), (1_300_000, 40, 2), (2_500_000, 44, 16),
+])
+def test_device_sort_is_a_stable_sort(ldl, host_ctx, count, bits, dup):
+    """The device radix sort (one block up to 2048 pairs, one 8-block cluster
+    up to 49152, one cooperative launch up to a few hundred tiles, separate
+    launches per pass above) puts
+    the pairs in the order of a stable sort by the low `bits` key bits:
+    values carry each pair's input position, so equal keys must keep their
+    input order.  Keys repeat (each drawn `dup`-fold on average) and some
+    are skewed to one digit, as aggregate records are."""
+    rng = np.random.default_rng(count * 7 + bits)
+    distinct = max(1, count // dup)
+    pool = rng.integers(0, 1 << bits, size=distinct, dtype=np.uint64) if bits < 64 else \
+        rng.integers(0, 1 << 63, size=distinct, dtype=np.uint64)
+    keys = pool[rng.integers(0, distinct, size=count)] if count else np.zeros(0, np.uint64)
+    if count > 10:
+        keys[: count // 10] &= np.uint64((1 << min(bits, 12)) - 1)  # a crowd in the low digits
+    vals = np.arange(count, dtype=np.uint64)
+    k, v = host_ctx.debug_sort_pairs(keys, vals, bits)
+    order = np.argsort(keys, kind="stable")
+    assert np.array_equal(k, keys[order])
+    assert np.array_equal(v, vals[order])
