@@ -149,6 +149,9 @@ typedef struct {
   int64_t moves, refine_moves, rejected, rollbacks, rounds, agg_records;
   int64_t decouple_rounds;   /* parallel resolution rounds of the decoupling filter */
   int64_t host_syncs;        /* counter reads that waited for the device */
+  int64_t pending_records;   /* weight records queued for levels >= 1 (before summing) */
+  int64_t pending_applied;   /* distinct arcs those records changed when applied */
+  int64_t split_members;     /* members of refined communities re-checked for connectivity */
 } ldl_result;
 
 /*

@@ -501,8 +501,6 @@ void csr_apply(SlackCSR<WT>& g, const u64* keys, const int64_t* delta, int64_t n
     g.lold.reserve(g.wtop + nrec + 1, s, true);
     g.lcol.reserve(g.ctop + stotal + 1, s, true);
     g.lw.reserve(g.ctop + stotal + 1, s, true);
-    S.scol.reserve(stotal + 1, s);
-    sw.reserve(stotal + 1, s);
     if (nseg > 0) {
       k_log_rows<<<gs, TPB, 0, s>>>(nseg, S.segrow.p, g.off.p, g.len.p, g.cap.p, S.slen.p, S.soff.p, g.ctop,
                                     g.lrow.p + g.rtop, g.loff.p + g.rtop, g.llen.p + g.rtop, g.lcap.p + g.rtop,
@@ -519,17 +517,25 @@ void csr_apply(SlackCSR<WT>& g, const u64* keys, const int64_t* delta, int64_t n
   k_update<WT><<<gr, TPB, 0, s>>>(g.off.p, keys, delta, nrec, bshift, S.pos.p, S.oldw.p, g.w.p);
   CKL("k_update");
   if (wtotal > 0) {
-    S.scol.reserve(stotal + 1, s);
-    sw.reserve(stotal + 1, s);
+    // the rows to rebuild, as they are before the rewrite (weights already
+    // updated): while a batch is logged they go straight into the undo log,
+    // which the rebuild then reads
+    int32_t* scol = nullptr;
+    WT* swp = nullptr;
+    if (g.logging) {
+      scol = g.lcol.p + g.ctop;
+      swp = g.lw.p + g.ctop;
+      g.ctop += stotal;
+    } else {
+      S.scol.reserve(stotal + 1, s);
+      sw.reserve(stotal + 1, s);
+      scol = S.scol.p;
+      swp = sw.p;
+    }
     if (stotal > 0) {
-      k_copy_scratch<WT><<<grid_for((stotal + 7) / 8, TPB), TPB, 0, s>>>(g.off.p, S.segrow.p, nseg, S.soff.p, stotal, g.col.p,
-                                                               g.w.p, S.scol.p, sw.p);
+      k_copy_scratch<WT><<<grid_for((stotal + 7) / 8, TPB), TPB, 0, s>>>(g.off.p, S.segrow.p, nseg, S.soff.p, stotal,
+                                                                         g.col.p, g.w.p, scol, swp);
       CKL("k_copy_scratch");
-      if (g.logging) {  // rows as they are before the rewrite (weights already updated)
-        CK(cudaMemcpyAsync(g.lcol.p + g.ctop, S.scol.p, sizeof(int32_t) * (size_t)stotal, cudaMemcpyDeviceToDevice, s));
-        CK(cudaMemcpyAsync(g.lw.p + g.ctop, sw.p, sizeof(WT) * (size_t)stotal, cudaMemcpyDeviceToDevice, s));
-        g.ctop += stotal;
-      }
     }
     if (need > 0) {
       CK(cudaMemcpyAsync(&d_sc->pool_top, &g.pool_top, sizeof(int64_t), cudaMemcpyHostToDevice, s));
@@ -538,7 +544,7 @@ void csr_apply(SlackCSR<WT>& g, const u64* keys, const int64_t* delta, int64_t n
       g.pool_top += need;
     }
     k_scatter_rows<WT><<<grid_for((wtotal + 7) / 8, TPB), TPB, 0, s>>>(nseg, nrec, S.seg.p, S.segrow.p, S.woff.p, S.soff.p,
-                                                             wtotal, S.scol.p, sw.p, keys, delta, S.lb.p, S.fins.p,
+                                                             wtotal, scol, swp, keys, delta, S.lb.p, S.fins.p,
                                                              S.pins.p, S.pdel.p, bshift, g.off.p, g.col.p, g.w.p);
     CKL("k_scatter_rows");
     k_set_len<<<gs, TPB, 0, s>>>(nseg, nrec, S.seg.p, S.segrow.p, S.pins.p, S.pdel.p, g.len.p);

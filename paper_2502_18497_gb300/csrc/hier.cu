@@ -182,28 +182,52 @@ struct Chain {
 // every level-q arc (i, j)).  With `add_k` the strengths of those levels take
 // the weight as well.  Records are not reduced here: the pending list of a
 // level is sorted, summed and applied when the level is next read.
+// Warp-aggregated append of one record per lane that wants one (every lane
+// of the warp calls it together): one atomic per warp.
+__device__ inline void warp_append_rec(bool want, u64 key, int64_t v, u64* pk, u64* pv, int32_t* count) {
+  const unsigned m = __ballot_sync(0xffffffffu, want);
+  if (!m) return;
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(m) - 1;
+  int32_t base = 0;
+  if (lane == leader) base = atomicAdd(count, __popc(m));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  if (want) {
+    const int32_t p = base + __popc(m & ((1u << lane) - 1u));
+    pk[p] = key;
+    pv[p] = (u64)v;
+  }
+}
+
 __global__ void k_chain_records(const u64* keys, const int64_t* vals, int64_t n, int bits, int q0, int top, int self,
                                 int add_k, int directed, Chain ch, int32_t* pcnt) {
   const u64 mask = (((u64)1) << bits) - 1;
-  GRID_STRIDE(t, n) {
-    int32_t x = (int32_t)(keys[t] >> bits), y = (int32_t)(keys[t] & mask);
-    const int64_t d = vals[t];
-    if (self) {
-      const int32_t p = atomicAdd(&pcnt[q0], 1);
-      ch.pk[q0][p] = keys[t];
-      ch.pv[q0][p] = (u64)d;
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  // warp-uniform trip counts, so that appends aggregate over the warp
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x + threadIdx.x - lane; base < n; base += stride) {
+    const int64_t t = base + lane;
+    bool on = t < n;
+    u64 key = 0;
+    int64_t d = 0;
+    if (on) {
+      key = keys[t];
+      d = vals[t];
     }
+    int32_t x = (int32_t)(key >> bits), y = (int32_t)(key & mask);
+    if (self) warp_append_rec(on, key, d, ch.pk[q0], ch.pv[q0], &pcnt[q0]);
     for (int q = q0; q < top; ++q) {
-      x = ch.par[q][x];
-      y = ch.par[q][y];
-      if (x < 0 || y < 0) break;
-      if (add_k) {
+      if (on) {
+        x = ch.par[q][x];
+        y = ch.par[q][y];
+        on = x >= 0 && y >= 0;
+      }
+      if (!__any_sync(0xffffffffu, on)) break;
+      if (on && add_k) {
         atomic_add_i64(&ch.kout[q + 1][x], d);
         if (directed) atomic_add_i64(&ch.kin[q + 1][y], d);
       }
-      const int32_t p = atomicAdd(&pcnt[q + 1], 1);
-      ch.pk[q + 1][p] = ((u64)x << bits) | (u64)y;
-      ch.pv[q + 1][p] = (u64)d;
+      warp_append_rec(on, ((u64)x << bits) | (u64)(uint32_t)y, d, ch.pk[q + 1], ch.pv[q + 1], &pcnt[q + 1]);
     }
   }
 }
@@ -994,6 +1018,8 @@ void flush_level(ldl_ctx& c, int q) {
   c.rk.reserve(n + 1, c.s);
   c.rsum.reserve(n + 1, c.s);
   const int64_t nr = reduce_by_key(L.pk.p, L.pv.p, n, c.rk.p, c.rsum.p, c.P, c.s);
+  c.res.pending_records += n;
+  c.res.pending_applied += nr;
   apply_level(c, q, c.rk.p, c.rsum.p, nr);
 }
 
@@ -1131,14 +1157,17 @@ int32_t split(ldl_ctx& c, int r, int32_t epD, int32_t epX) {
   zero_cnt(c, K_D);
   zero_cnt(c, K_X);
   const int32_t epF = c.next_epoch();  // communities whose connectivity is in doubt
-  const int32_t nK = rd_cnt(c, K_BRK0 + r);
+  int32_t nK = 0, nu = 0;  // deleted-arc endpoints of the level, |U*|: one read
+  {
+    const HostRead rr[2] = {{c.dcnt + K_BRK0 + r, &nK, sizeof(int32_t)}, {c.dcnt + K_USTAR, &nu, sizeof(int32_t)}};
+    host_read(c, rr, 2);
+  }
   if (nK > 0) {
     k_brk_check<<<grid_for(nK, TPB), TPB, 0, c.s>>>(L.lK.p, c.dcnt + K_BRK0 + r, L.alive.p, L.par.p, c.stX.p, epX,
                                                     c.lX.p, c.dcnt + K_X, c.ckf.p, epF);
     CKL("k_brk_check");
   }
   const int32_t epL = c.next_epoch();
-  const int32_t nu = rd_cnt(c, K_USTAR);
   if (nu > 0) {
     k_leave<<<grid_for(nu, TPB), TPB, 0, c.s>>>(c.lUstar.p, c.dcnt + K_USTAR, L.alive.p, L.lab.p, N.lab.p, L.par.p,
                                                 c.par_old.p, L.kout.p, kin_of(c, r), N.kout.p, kin_of(c, r + 1),
@@ -1164,6 +1193,7 @@ int32_t split(ldl_ctx& c, int r, int32_t epD, int32_t epX) {
                                                                    c.lG.p, c.dcnt + K_G);
     CKL("k_members");
     const int32_t nG = rd_cnt(c, K_G);
+    c.res.split_members += nG;
     if (nG > 0) {
       if (r == 0) union_find<int32_t>(c, r, adj_out0(c), adj_in0(c), nG, epL);
       else union_find<int64_t>(c, r, adj_out(c, r), adj_in(c, r), nG, epL);

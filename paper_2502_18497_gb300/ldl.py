@@ -41,7 +41,9 @@ class ldl_result(C.Structure):
                 ("frontier_nodes", C.c_int64 * 8), ("edges_scanned", C.c_int64),
                 ("moves", C.c_int64), ("refine_moves", C.c_int64), ("rejected", C.c_int64),
                 ("rollbacks", C.c_int64), ("rounds", C.c_int64), ("agg_records", C.c_int64),
-                ("decouple_rounds", C.c_int64), ("host_syncs", C.c_int64)]
+                ("decouple_rounds", C.c_int64), ("host_syncs", C.c_int64),
+                ("pending_records", C.c_int64), ("pending_applied", C.c_int64),
+                ("split_members", C.c_int64)]
 
 
 class LdlError(RuntimeError):
@@ -400,7 +402,8 @@ class LDL:
                     edges_scanned=r.edges_scanned, moves=r.moves, refine_moves=r.refine_moves,
                     rejected=r.rejected, rollbacks=r.rollbacks, rounds=r.rounds,
                     agg_records=r.agg_records, decouple_rounds=r.decouple_rounds,
-                    host_syncs=r.host_syncs)
+                    host_syncs=r.host_syncs, pending_records=r.pending_records,
+                    pending_applied=r.pending_applied, split_members=r.split_members)
 
 
 def apply_batches(instances, batches, threads: int = 0):
