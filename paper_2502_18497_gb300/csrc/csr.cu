@@ -70,8 +70,13 @@ __global__ void k_track_del(const u64* keys, const int32_t* fdel, int64_t nrec, 
     if (!fdel[i]) continue;
     const int64_t row = (int64_t)(keys[i] >> bshift);
     if (row >= t.rows) continue;
+    const int32_t col = (int32_t)(keys[i] & cmask);
+    // an arc between two different refined communities cannot disconnect
+    // either; a parentless endpoint may have just left its community (an
+    // emptied node), so such arcs are kept
+    if (t.par && (row == col || (t.par[row] >= 0 && t.par[col] >= 0 && t.par[row] != t.par[col]))) continue;
     stamp_add(t.stamp, t.ep, (int32_t)row, t.list, t.cnt);
-    stamp_add(t.stamp, t.ep, (int32_t)(keys[i] & cmask), t.list, t.cnt);
+    stamp_add(t.stamp, t.ep, col, t.list, t.cnt);
   }
 }
 

@@ -43,6 +43,7 @@ struct DelTrack {
   int32_t* list;
   int32_t* cnt;
   int64_t rows;
+  const int32_t* par;  // with it, arcs between two different parents are not recorded
 };
 
 // Batch transactions on a CSR (see SlackCSR's undo log): begin logging,

@@ -950,7 +950,10 @@ static void combine_in_out(ldl_ctx& c, const u64* keys, const u64* vals, int64_t
 static void apply_level(ldl_ctx& c, int r, const u64* keys, const int64_t* vals, int64_t nr) {
   if (nr <= 0) return;
   LevelState& Lr = c.lv[r];
-  const DelTrack trk{Lr.stK.p, Lr.brk_ep, Lr.lK.p, c.dcnt + K_BRK0 + r, c.n};
+  // a deleted arc can only disconnect the refined community holding both of
+  // its endpoints (refined communities are connected); until the level's next
+  // split its parents change only where a node empties and leaves its parent
+  const DelTrack trk{Lr.stK.p, Lr.brk_ep, Lr.lK.p, c.dcnt + K_BRK0 + r, c.n, r < c.T ? Lr.par.p : nullptr};
   const u64* k = keys;
   const u64* v = (const u64*)vals;
   int64_t m = nr;
