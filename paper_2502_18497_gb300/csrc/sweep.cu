@@ -394,19 +394,70 @@ __global__ void __launch_bounds__(TPB, 5) k_sweep_group(SweepArgs<WT> A, const i
 
 // one block per node; the hash lives in dynamic shared memory (mid degrees)
 // or in a global-memory slice (hubs, table != nullptr)
+// Entries of a node's rows staged in registers: entry k of the node is its
+// out-row entry k (k < lo) or its in-row entry k - lo; thread tid holds the
+// entries tid + j * NT.  First the neighbour ids and weights ...
+template <class WT, int NT, int ACC>
+__device__ inline void stage_rows(const SweepArgs<WT>& A, const NodeMeta& m, int32_t (&u)[ACC], int64_t (&w)[ACC]) {
+#pragma unroll
+  for (int j = 0; j < ACC; ++j) {
+    const int32_t k = (int32_t)threadIdx.x + j * NT;
+    u[j] = -1;
+    w[j] = 0;
+    if (k < m.lo) {
+      u[j] = A.out.col[m.oo + k];
+      w[j] = (int64_t)A.out.w[m.oo + k];
+    } else if (k < m.lo + m.li) {
+      u[j] = A.in.col[m.oi + (k - m.lo)];
+      w[j] = (int64_t)A.in.w[m.oi + (k - m.lo)];
+    }
+  }
+}
+
+// ... then each id becomes its hash key (neighbour label, or for BestRef the
+// neighbour's refined community when it shares v's label; -1: skipped).
+template <class WT, int MODE, int ACC>
+__device__ inline void stage_keys(const SweepArgs<WT>& A, int32_t v, int32_t a, int32_t (&u)[ACC]) {
+#pragma unroll
+  for (int j = 0; j < ACC; ++j) {
+    const int32_t x = u[j];
+    int32_t key = -1;
+    if (x >= 0 && x != v) {
+      const int32_t lx = A.lab[x];
+      if (MODE == 0) key = lx;
+      else if (lx == a) key = A.par[x];
+    }
+    u[j] = key;
+  }
+}
+
+// One block of NT threads per node (a row of up to HMAX/2 entries, hash table
+// of up to HMAX slots in shared memory).  Software-pipelined over the block's
+// nodes: the row entries and labels of the next node are loaded into
+// registers while the current node's table is evaluated, and the node after
+// that has its offsets, lengths and strengths loaded one node further ahead,
+// so a node's fill only inserts into shared memory.  Entries beyond the
+// staged HMAX/2 (not produced by the default bins) are inserted directly.
 template <class WT, int MODE, int NT, int HMAX, class GT>
-__global__ void __launch_bounds__(NT) k_sweep_block(SweepArgs<WT> A, const int32_t* list, const int32_t* nlist) {
+__global__ void __launch_bounds__(NT, 1024 / NT) k_sweep_block(SweepArgs<WT> A, const int32_t* list,
+                                                               const int32_t* nlist) {
   extern __shared__ unsigned char smem[];
   __shared__ BestG<GT> wb[NT / 32];
+  constexpr int ACC = HMAX / (2 * NT);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int32_t nl = *nlist;
   const int64_t mult = A.directed ? 1 : 2;
   int64_t ent_all = 0, nodes = 0, pairs_all = 0;
-  NodeMeta nxt{};
-  if (blockIdx.x < nl) nxt = node_meta(A, list[blockIdx.x]);
+  NodeMeta cur{}, nxt{};
+  int32_t ek[ACC];
+  int64_t ew[ACC];
+  if (blockIdx.x < nl) {
+    cur = node_meta(A, list[blockIdx.x]);
+    stage_rows<WT, NT, ACC>(A, cur, ek, ew);
+    stage_keys<WT, MODE, ACC>(A, cur.v, cur.a, ek);
+  }
+  if (blockIdx.x + gridDim.x < nl) nxt = node_meta(A, list[blockIdx.x + gridDim.x]);
   for (int64_t t = blockIdx.x; t < nl; t += gridDim.x) {
-    const NodeMeta cur = nxt;
-    if (t + gridDim.x < nl) nxt = node_meta(A, list[t + gridDim.x]);  // in flight during this node
     const int32_t v = cur.v;
     int64_t* V = (int64_t*)smem;
     int32_t* K = (int32_t*)(smem + sizeof(int64_t) * HMAX);
@@ -419,15 +470,35 @@ __global__ void __launch_bounds__(NT) k_sweep_block(SweepArgs<WT> A, const int32
     }
     __syncthreads();
     const int32_t a = cur.a;
-    accumulate_row<WT, MODE>(A, A.out.col, A.out.w, cur.oo, cur.lo, v, a, K, V, H - 1, threadIdx.x, NT);
-    if (A.directed) accumulate_row<WT, MODE>(A, A.in.col, A.in.w, cur.oi, cur.li, v, a, K, V, H - 1, threadIdx.x, NT);
+#pragma unroll
+    for (int j = 0; j < ACC; ++j)
+      if (ek[j] >= 0) hash_add(K, V, H - 1, ek[j], ew[j]);
+    if (d > ACC * NT) {  // entries beyond the staged ones
+      for (int64_t k = ACC * NT + threadIdx.x; k < d; k += NT) {
+        int32_t x;
+        int64_t wx;
+        if (k < cur.lo) {
+          x = A.out.col[cur.oo + k];
+          wx = (int64_t)A.out.w[cur.oo + k];
+        } else {
+          x = A.in.col[cur.oi + (k - cur.lo)];
+          wx = (int64_t)A.in.w[cur.oi + (k - cur.lo)];
+        }
+        int32_t kx[1] = {x};
+        stage_keys<WT, MODE, 1>(A, v, a, kx);
+        if (kx[0] >= 0) hash_add(K, V, H - 1, kx[0], wx);
+      }
+    }
     __syncthreads();
+    const bool has_next = t + gridDim.x < nl;
+    if (has_next) stage_rows<WT, NT, ACC>(A, nxt, ek, ew);  // in flight during the evaluation
     const int64_t wa = MODE == 0 ? hash_get(K, V, H - 1, a) : 0;
     const int64_t ko = cur.ko, ki = cur.ki;
     BestG<GT> b{0, 0, 0};
     int64_t pairs = 0;
     eval_slots<MODE, GT>(K, V, H, threadIdx.x, NT, MODE == 0 ? a : v, a, wa, ko, ki, A.Tout, A.Tin, A.m, A.gn, A.gd,
                          mult, b, pairs);
+    if (has_next) stage_keys<WT, MODE, ACC>(A, nxt.v, nxt.a, ek);  // label gathers overlap the argmax
     b = seg_best<GT, 32>(b);
     if (lane == 0) wb[wid] = b;
     pairs_all += pairs;
@@ -441,6 +512,8 @@ __global__ void __launch_bounds__(NT) k_sweep_block(SweepArgs<WT> A, const int32
       ++nodes;
     }
     __syncthreads();
+    cur = nxt;
+    if (t + 2 * (int64_t)gridDim.x < nl) nxt = node_meta(A, list[t + 2 * (int64_t)gridDim.x]);
   }
   // statistics once per block
   const int64_t bytes = warp_sum_i64(sweep_bytes<WT, MODE>(A.directed, ent_all, nodes, pairs_all));
