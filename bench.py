@@ -48,8 +48,8 @@ WORKLOAD = ("directed R-MAT (0.57,0.19,0.19,0.05), 2^20 vertices, 2^24 arcs, wei
 # workload, divided by the launches that had nodes to sweep: the bins are
 # launched unconditionally and an empty launch moves ~23 KB), valid only for
 # the sweep source it was taken with (sha256 of csrc/sweep.cu).
-NCU_TRAFFIC = {"sha256": "44c72d96031231d1cd44fb9626a5b9c744343002c49d17ba77891e1eb467f039",
-               "bytes_per_launch": 44905443, "kernel": "sweep_block128"}
+NCU_TRAFFIC = {"sha256": "9600c9ca881567e8f69fbc5efd0df9c1bb7f2ad94804894baa0dd3339f9da866",
+               "bytes_per_launch": 45196117, "kernel": "sweep_block128"}
 
 
 def _set_rmat_scale(scale: int):
@@ -342,6 +342,91 @@ def run_served(args):
     print(json.dumps(line), flush=True)
 
 
+def run_c5(args):
+    """The largest stream's recipe (undirected R-MAT (0.57,0.19,0.19,0.05) at
+    scale 28 with ids below 214,000,000, 3.30e9 distinct edges, unit weights;
+    batches of log-uniform 10..10^6 updates, 70/20/10 inserts / deletes /
+    reweights) scaled down by 2^c5_div so that the hierarchy fits one GPU.
+    The graph is drawn on the GPU (bit-identical to the host generator).
+    Reports the static build's sweep roofline (frontier = every vertex), the
+    plain form (batches back to back from device memory: updates/s, p50/p99
+    batch latency) and the served form on the same graph (one worker, batches
+    arriving as a Poisson stream at 0.5x and 0.9x the plain capacity: p50/p99
+    latency including the wait in the queue)."""
+    import torch
+    from paper_2502_18497_gb300 import LDL, Server
+    from synth import c5_size, c5_stream, unit_f64
+    from synth.streams import rmat_undirected_c5_t
+    k = args.c5_div
+    n, edges, scale = c5_size(k)
+    K, W = args.steps, args.warmup
+    t0 = time.perf_counter()
+    g = rmat_undirected_c5_t(k, device="cuda")
+    torch.cuda.empty_cache()
+    gen_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    bs = c5_stream(g, W + 3 * K, seed=5)
+    stream_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    d = LDL.from_graph(g, kernel_stats=1, no_rollback=int(args.no_rollback))
+    torch.cuda.synchronize()
+    create_s = time.perf_counter() - t0
+    static = _roofline(d.kernel_stats())
+    d.set_kernel_stats(False)
+    del g
+    dev = [torch.from_numpy(np.ascontiguousarray(b)).cuda() for b in bs]
+    for b in dev[:W]:
+        d.apply(b, on_device=True)
+    torch.cuda.synchronize()
+    # plain form: back to back
+    lat, upd = [], 0
+    t0 = time.perf_counter()
+    for b in dev[W:W + K]:
+        t = time.perf_counter()
+        d.apply(b, on_device=True)
+        lat.append(1e3 * (time.perf_counter() - t))
+        upd += int(b.shape[0])
+    torch.cuda.synchronize()
+    plain_s = time.perf_counter() - t0
+    cap = upd / plain_s
+    mean_batch = float(np.mean([len(b) for b in bs[W:]]))
+    served = {}
+    srv = Server(workers=1)
+    for j, load in enumerate((0.5, 0.9)):
+        part = bs[W + (j + 1) * K:W + (j + 2) * K]
+        rate = load * cap / mean_batch
+        gaps = -np.log(1.0 - unit_f64(13, j, np.arange(len(part)))) / rate
+        tickets, u = [], 0
+        t0 = time.perf_counter()
+        due = t0
+        for i, b in enumerate(part):
+            due += gaps[i]
+            while time.perf_counter() < due:
+                pass
+            tickets.append(srv.submit(d, b))
+            u += len(b)
+        sl = []
+        for tk in tickets:
+            st, _, q, sv = srv.wait(tk)
+            assert st == 0, st
+            sl.append((q + sv) / 1e3)
+        el = time.perf_counter() - t0
+        served[str(load)] = {"updates_per_s": u / el, "latency_ms": {"p50": float(np.percentile(sl, 50)),
+                                                                      "p99": float(np.percentile(sl, 99))}}
+    srv.close()
+    line = {"metric": "updates/s", "value": cap, "unit": "updates/s", "n_gpus": 1, "steps": K, "warmup": W,
+            "ms_per_step": 1e3 * plain_s / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "int64", "data": "synthetic", "form": "plain + served (one graph)",
+            "config": {"workload": f"undirected R-MAT (0.57,0.19,0.19,0.05) scale {scale}, {n} vertices, {edges} "
+                                   f"distinct edges, unit weights (the 214M-vertex / 3.30B-edge recipe / 2^{k}); "
+                                   f"batches log-uniform 10..10^6 updates, 70/20/10 insert/delete/reweight",
+                       "create_s": round(create_s, 2), "generate_s": round(gen_s, 2), "stream_s": round(stream_s, 2),
+                       "atomic_batches": not args.no_rollback, "mean_batch": mean_batch},
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+            "served": served, "static_build_roofline": static}
+    print(json.dumps(line), flush=True)
+
+
 def run_powerlaw(args):
     """Batch-size sweep on the LFR-like power-law planted partition
     (2^scale vertices, mean degree 32, exponent 2.5, community sizes 50..50,000,
@@ -524,7 +609,7 @@ def main():
     ap.add_argument("--no-rollback", action="store_true",
                     help="contexts without the per-batch rollback snapshot and undo log (ldl_params.no_rollback)")
     ap.add_argument("--workload", default="rmat",
-                    choices=["rmat", "batched", "served", "powerlaw", "autotune", "quality", "degree"])
+                    choices=["rmat", "batched", "served", "powerlaw", "autotune", "quality", "degree", "c5"])
     ap.add_argument("--autotune-cache", default=None, help="autotune: JSON file the result is merged into")
     ap.add_argument("--scale", type=int, default=24, help="powerlaw: log2 of the vertex count")
     ap.add_argument("--graphs", type=int, default=512, help="batched form: number of graphs")
@@ -534,6 +619,8 @@ def main():
     ap.add_argument("--rmat-scale", type=int, default=SCALE,
                     help="R-MAT workload: log2 of the vertex count (default: the full-size stream)")
     ap.add_argument("--load", type=float, default=0.9, help="served form: arrival rate / one-worker capacity")
+    ap.add_argument("--c5-div", type=int, default=3,
+                    help="c5: log2 of the factor the 214M-vertex / 3.30B-edge recipe is scaled down by")
     args = ap.parse_args()
     _set_rmat_scale(args.rmat_scale)
     if args.impl == "reference":
@@ -550,6 +637,8 @@ def main():
         return run_quality(args)
     if args.workload == "degree":
         return run_degree(args)
+    if args.workload == "c5":
+        return run_c5(args)
 
     import torch
     ws, rank, local = _dist()

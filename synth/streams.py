@@ -627,3 +627,244 @@ def _region_batch(st: EdgeStream, n_ins, n_del, sampler, region, seed):
     st.keys, st.wts = allk[order], allw[order]
     st.batches_made += 1
     return b
+
+
+# ---------------------------------------------------------------- the largest stream
+C5_N = 214_000_000
+C5_EDGES = 3_300_000_000
+C5_SCALE = 28
+_C5_PERM_A = 2_654_435_761  # prime; coprime to 214e6 >> k (= 2^(7-k) * 5^6 * 107)
+
+
+def c5_size(div_log2: int = 0):
+    """(n, distinct undirected edges, R-MAT scale) of the largest stream's
+    recipe scaled down by 2^div_log2."""
+    return C5_N >> div_log2, C5_EDGES >> div_log2, C5_SCALE - div_log2
+
+
+def _c5_perm(x: np.ndarray, n: int) -> np.ndarray:
+    """Affine id permutation x -> (A x + B) mod n (A coprime to n)."""
+    b = int(splitmix64(5, 59, [0])[0]) % n
+    return (x % n * (_C5_PERM_A % n) % n + b) % n  # products stay below 2^62 for n < 2^31
+
+
+def rmat_undirected_c5(div_log2: int = 0, seed: int = 5, chunk: int = 1 << 25,
+                       probs=(0.57, 0.19, 0.19, 0.05)) -> Graph:
+    """Stand-in for the paper's largest streams (214M vertices, 3.30B edges):
+    undirected R-MAT with skew (0.57, 0.19, 0.19, 0.05) at scale 28, draws
+    with an id >= 214,000,000 or a loop rejected, distinct edges kept in order
+    of first draw until 3.30e9 are reached, an affine id permutation applied,
+    unit weights.  div_log2 > 0 scales the recipe down by 2^div_log2 (scale,
+    vertex count and edge count alike)."""
+    n, target, scale = c5_size(div_log2)
+    keys, first = [], []
+    base = 0
+    have = 0
+    while True:
+        cnt = min(chunk, int((target - have) * 1.5) + 4096)
+        s, d = _rmat_draw(seed, 51, base, cnt, scale, probs)
+        ok = (s < n) & (d < n) & (s != d)
+        lo, hi = np.minimum(s, d)[ok], np.maximum(s, d)[ok]
+        keys.append(lo * n + hi)
+        first.append(np.arange(base, base + cnt, dtype=np.int64)[ok])
+        base += cnt
+        have += int(ok.sum())
+        if have < target:
+            continue
+        allk = np.concatenate(keys)
+        allf = np.concatenate(first)
+        order = np.argsort(allk, kind="stable")
+        allk, allf = allk[order], allf[order]
+        u, at = np.unique(allk, return_index=True)
+        if len(u) >= target:
+            sel = np.argsort(allf[at], kind="stable")[:target]
+            key = u[sel]
+            break
+        keys, first = [u], [allf[at]]
+        have = len(u)
+    del keys, first
+    a = _c5_perm(key // n, n)
+    b = _c5_perm(key % n, n)
+    del key
+    # distinct undirected edges: both arcs of each, sorted by (row, col)
+    arc = np.concatenate([a * n + b, b * n + a])
+    del a, b
+    arc.sort()
+    src = arc // n
+    row_ptr = np.zeros(n + 1, dtype=np.int64)
+    row_ptr[1:] = np.cumsum(np.bincount(src, minlength=n))
+    col = (arc % n).astype(np.int32)
+    del arc, src
+    g = Graph(n, False, row_ptr, col, np.ones(len(col), dtype=np.int32))
+    g.name = f"rmat undirected c5 n={n} edges={target}"
+    return g
+
+
+def c5_stream(g: Graph, batches: int, seed: int = 5, max_size: int = 1_000_000, wmax: int = 4,
+              probs=(0.57, 0.19, 0.19, 0.05)):
+    """Batches of the largest stream: sizes log-uniform in [10, max_size], each
+    70% inserts (R-MAT draws with the graph's skew, ids permuted as the
+    graph's; an insert of an edge that exists adds its weight), 20% deletes
+    and 10% reweights (to 1..wmax) of distinct edges of the initial graph (no
+    edge is deleted twice or reweighted after its delete), in a seeded
+    shuffled order.  Vectorised: nothing is copied per batch."""
+    n = g.n
+    scale = max(1, int(n - 1).bit_length())
+    u = unit_f64(seed, 81, np.arange(batches))
+    sizes = np.floor(10.0 ** (1.0 + u * (np.log10(max_size) - 1.0))).astype(np.int64)
+    n_del = np.round(sizes * 0.2).astype(np.int64)
+    n_rew = np.round(sizes * 0.1).astype(np.int64)
+    n_ins = sizes - n_del - n_rew
+    # initial undirected edges (u < v) by index
+    src = np.repeat(np.arange(n, dtype=np.int64), np.diff(g.row_ptr))
+    up = src < g.col
+    eu, ev = src[up], g.col[up].astype(np.int64)
+    del src, up
+    m = len(eu)
+    need = int(n_del.sum() + n_rew.sum())
+    if need > m:
+        raise ValueError("stream deletes and reweights more edges than the graph has")
+    pick = np.zeros(0, dtype=np.int64)
+    want = need + 64
+    while len(pick) < need:
+        want = 2 * want
+        draw = uniform_u64(seed, 82, np.arange(want), m)
+        _, at = np.unique(draw, return_index=True)
+        pick = draw[np.sort(at)]
+    pick = pick[:need]
+    out = []
+    pos = 0
+    ins_base = 0
+    for t in range(batches):
+        nd, nr, ni = int(n_del[t]), int(n_rew[t]), int(n_ins[t])
+        dsel = pick[pos:pos + nd]
+        rsel = pick[pos + nd:pos + nd + nr]
+        pos += nd + nr
+        got_s, got_d = [], []
+        have = 0
+        while have < ni:
+            cnt = 2 * (ni - have) + 64
+            s, d = _rmat_draw(seed, 83, ins_base, cnt, scale, probs)
+            ins_base += cnt
+            ok = (s < n) & (d < n) & (s != d)
+            s, d = _c5_perm(s[ok], n), _c5_perm(d[ok], n)
+            got_s.append(s[:ni - have])
+            got_d.append(d[:ni - have])
+            have += len(got_s[-1])
+        isrc, idst = np.concatenate(got_s), np.concatenate(got_d)
+        iw = uniform_u64(seed, 84, np.arange(ni) + t * 1_000_003, wmax) + 1
+        rw = uniform_u64(seed, 85, np.arange(nr) + t * 1_000_003, wmax) + 1
+        flip = uniform_u64(seed, 86, np.arange(nd + nr) + t * 1_000_003, 2) == 1
+        ds = np.where(flip[:nd], ev[dsel], eu[dsel])
+        dd = np.where(flip[:nd], eu[dsel], ev[dsel])
+        rs = np.where(flip[nd:], ev[rsel], eu[rsel])
+        rd = np.where(flip[nd:], eu[rsel], ev[rsel])
+        bsrc = np.concatenate([isrc, ds, rs])
+        bdst = np.concatenate([idst, dd, rd])
+        op = np.concatenate([np.full(ni, INSERT), np.full(nd, DELETE), np.full(nr, REWEIGHT)])
+        w = np.concatenate([iw, np.zeros(nd, dtype=np.int64), rw])
+        order = np.argsort(splitmix64(seed, 87 + t * 7, np.arange(len(bsrc))), kind="stable")
+        out.append(np.stack([bsrc[order], bdst[order], op[order], w[order]], axis=1).astype(np.int32))
+    return out
+
+
+# ---- the same draws with torch tensors (a GPU builds the largest graphs in
+# seconds); bit-identical to the numpy versions above.
+def _i64(x: int) -> int:
+    """A uint64 constant as the int64 with the same bits."""
+    x &= (1 << 64) - 1
+    return x - (1 << 64) if x >= 1 << 63 else x
+
+
+def _lsr_t(z, k: int):
+    return (z >> k) & ((1 << (64 - k)) - 1)
+
+
+def _mix64_t(z):
+    z = (z ^ _lsr_t(z, 30)) * _i64(0xBF58476D1CE4E5B9)
+    z = (z ^ _lsr_t(z, 27)) * _i64(0x94D049BB133111EB)
+    return z ^ _lsr_t(z, 31)
+
+
+def splitmix64_t(seed: int, purpose: int, idx):
+    """splitmix64 on an int64 torch tensor of indices (values as int64 bits)."""
+    key = _i64(int(_mix64(np.array([seed], dtype=np.uint64) * _GOLDEN + np.uint64(purpose))[0]))
+    return _mix64_t(key + (idx + 1) * _i64(0x9E3779B97F4A7C15))
+
+
+def _rmat_draw_t(seed: int, purpose: int, base: int, count: int, scale: int, probs, device):
+    import torch
+    a, b, c, _ = probs
+    ta, tb, tc = (int(round(x * 65536)) for x in (a, a + b, a + b + c))
+    per = (scale + 3) // 4
+    idx0 = torch.arange(base, base + count, dtype=torch.int64, device=device)
+    src = torch.zeros(count, dtype=torch.int64, device=device)
+    dst = torch.zeros(count, dtype=torch.int64, device=device)
+    for k in range(per):
+        x = splitmix64_t(seed, purpose, idx0 * per + k)
+        for j in range(4):
+            if 4 * k + j >= scale:
+                break
+            u = _lsr_t(x, 16 * j) & 0xFFFF if j else x & 0xFFFF
+            sb = (u >= tb).to(torch.int64)
+            db = (((u >= ta) & (u < tb)) | (u >= tc)).to(torch.int64)
+            src = (src << 1) | sb
+            dst = (dst << 1) | db
+    return src, dst
+
+
+def rmat_undirected_c5_t(div_log2: int = 0, seed: int = 5, device="cuda", chunk: int = 1 << 27,
+                         probs=(0.57, 0.19, 0.19, 0.05)) -> Graph:
+    """rmat_undirected_c5 built with torch on `device` (same graph, bit for
+    bit); the CSR comes back in host memory."""
+    import torch
+    n, target, scale = c5_size(div_log2)
+    keys, first = [], []
+    base = 0
+    have = 0
+    while True:
+        cnt = min(chunk, int((target - have) * 1.5) + 4096)
+        s, d = _rmat_draw_t(seed, 51, base, cnt, scale, probs, device)
+        ok = (s < n) & (d < n) & (s != d)
+        lo, hi = torch.minimum(s, d)[ok], torch.maximum(s, d)[ok]
+        keys.append(lo * n + hi)
+        first.append(torch.arange(base, base + cnt, dtype=torch.int64, device=device)[ok])
+        del s, d, ok, lo, hi
+        base += cnt
+        have += int(keys[-1].numel())
+        if have < target:
+            continue
+        allk = torch.cat(keys)
+        allf = torch.cat(first)
+        keys, first = [], []
+        allk, order = torch.sort(allk, stable=True)
+        allf = allf[order]
+        del order
+        u, cts = torch.unique_consecutive(allk, return_counts=True)
+        starts = torch.cumsum(cts, 0) - cts
+        f = allf[starts]
+        del allk, allf, cts, starts
+        if u.numel() >= target:
+            sel = torch.sort(f, stable=True).indices[:target]
+            key = u[sel]
+            del u, f, sel
+            break
+        keys, first = [u], [f]
+        have = int(u.numel())
+    b0 = int(splitmix64(5, 59, [0])[0]) % n
+    pa = _C5_PERM_A % n
+    a_ = ((key // n) % n * pa % n + b0) % n
+    b_ = ((key % n) % n * pa % n + b0) % n
+    del key
+    arc = torch.cat([a_ * n + b_, b_ * n + a_])
+    del a_, b_
+    arc = torch.sort(arc).values
+    src = arc // n
+    row_ptr = torch.zeros(n + 1, dtype=torch.int64, device=device)
+    row_ptr[1:] = torch.cumsum(torch.bincount(src, minlength=n), 0)
+    col = (arc % n).to(torch.int32)
+    del arc, src
+    g = Graph(n, False, row_ptr.cpu().numpy(), col.cpu().numpy(), np.ones(int(col.numel()), dtype=np.int32))
+    del row_ptr, col
+    g.name = f"rmat undirected c5 n={n} edges={target}"
+    return g
