@@ -373,10 +373,16 @@ def run_c5(args):
     create_s = time.perf_counter() - t0
     static = _roofline(d.kernel_stats())
     d.set_kernel_stats(False)
+    free_b, total_b = torch.cuda.mem_get_info()
+    print(f"c5: n={n} edges={edges} generate {gen_s:.1f} s, stream {stream_s:.1f} s, create {create_s:.1f} s, "
+          f"device memory in use {(total_b - free_b) / 1e9:.1f} of {total_b / 1e9:.1f} GB", file=sys.stderr, flush=True)
     del g
     dev = [torch.from_numpy(np.ascontiguousarray(b)).cuda() for b in bs]
     for b in dev[:W]:
         d.apply(b, on_device=True)
+        f2, _ = torch.cuda.mem_get_info()
+        print(f"c5: warm-up batch of {int(b.shape[0])}: device memory in use {(total_b - f2) / 1e9:.1f} GB",
+              file=sys.stderr, flush=True)
     torch.cuda.synchronize()
     # plain form: back to back
     lat, upd = [], 0
@@ -421,7 +427,8 @@ def run_c5(args):
                                    f"distinct edges, unit weights (the 214M-vertex / 3.30B-edge recipe / 2^{k}); "
                                    f"batches log-uniform 10..10^6 updates, 70/20/10 insert/delete/reweight",
                        "create_s": round(create_s, 2), "generate_s": round(gen_s, 2), "stream_s": round(stream_s, 2),
-                       "atomic_batches": not args.no_rollback, "mean_batch": mean_batch},
+                       "atomic_batches": not args.no_rollback, "mean_batch": mean_batch,
+                       "device_gb_in_use_after_create": round((total_b - free_b) / 1e9, 1)},
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
             "served": served, "static_build_roofline": static}
     print(json.dumps(line), flush=True)
@@ -619,7 +626,7 @@ def main():
     ap.add_argument("--rmat-scale", type=int, default=SCALE,
                     help="R-MAT workload: log2 of the vertex count (default: the full-size stream)")
     ap.add_argument("--load", type=float, default=0.9, help="served form: arrival rate / one-worker capacity")
-    ap.add_argument("--c5-div", type=int, default=3,
+    ap.add_argument("--c5-div", type=int, default=4,
                     help="c5: log2 of the factor the 214M-vertex / 3.30B-edge recipe is scaled down by")
     args = ap.parse_args()
     _set_rmat_scale(args.rmat_scale)

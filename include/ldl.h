@@ -412,6 +412,12 @@ ldl_status ldl_debug_decouple(ldl_ctx* ctx, int64_t count, const int32_t* v, con
  * only.  Returns LDL_E_INVALID on bad arguments. */
 ldl_status ldl_debug_sort_pairs(ldl_ctx* ctx, int64_t count, uint64_t* keys, uint64_t* vals, int32_t bits);
 
+/* Test hook: the number of hub hash-table slots a sweep holds at once
+ * (default 2^28, 3 GB; slots <= 0 restores it).  Hubs whose tables exceed it
+ * together are swept in consecutive groups; a small value makes ordinary
+ * graphs take that path.  Process-wide. */
+void ldl_debug_hub_table_slots(int64_t slots);
+
 /* Test hook for the bounded waits: runs a two-tile device scan in which the
  * first tile never publishes its sum, so the second tile's look-back wait
  * runs out (after about 2^20 polls).  Returns LDL_E_TIMEOUT when the wait gave

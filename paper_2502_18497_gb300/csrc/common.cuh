@@ -321,6 +321,7 @@ struct DevScalars {
   int64_t de;       // change of sum_C e_C
   int64_t dm;       // change of m (batch)
   int64_t need;     // pool slots needed by relocation
+  int64_t need2;    // second accumulator (record counts)
   int64_t scanned;  // adjacency entries scanned
   int64_t err_key;  // packed (index << 8 | status) of the first failing update
   int64_t pool_top;

@@ -46,6 +46,7 @@ enum {
   K_U = 0, K_S, K_USTAR, K_MV, K_M0, K_D, K_C, K_R, K_R2, K_X, K_T, K_E, K_E2, K_CH, K_CAND, K_B,
   K_UNDEC, K_SMALL, K_MID, K_LARGE, K_REC, K_CREC, K_NREC, K_ERR, K_TMP, K_TMP2, K_CHG, K_MID2, K_TINY, K_CLU,
   K_G,
+  K_HUBG,      // hubs of the current hub group
   K_A0 = 32,   // K_A0 + r: |A^r|
   K_BRK0 = 48, // K_BRK0 + r: endpoints of deleted level-r arcs
   K_PEND0 = 56, // K_PEND0 + r: pending weight records of level r

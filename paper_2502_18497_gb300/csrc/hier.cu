@@ -538,13 +538,18 @@ __global__ void k_changed(const int32_t* lD, const int32_t* nD, const int32_t* p
 }
 
 template <class WT>
-__global__ void k_deg_sum(Adj<WT> out, Adj<WT> in, const int32_t* l, const int32_t* n, int64_t* acc) {
+__global__ void k_deg_sum(Adj<WT> out, Adj<WT> in, const int32_t* l, const int32_t* n, int64_t* acc_out,
+                          int64_t* acc_in) {
   const int32_t m = *n;
-  int64_t s = 0;
-  for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x)
-    s += (int64_t)out.len[l[k]] + in.len[l[k]];
-  s = warp_sum_i64(s);
-  if ((threadIdx.x & 31) == 0 && s) atomic_add_i64(acc, s);
+  int64_t so = 0, si = 0;
+  for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x) {
+    so += (int64_t)out.len[l[k]];
+    si += (int64_t)in.len[l[k]];
+  }
+  so = warp_sum_i64(so);
+  si = warp_sum_i64(si);
+  if ((threadIdx.x & 31) == 0 && so) atomic_add_i64(acc_out, so);
+  if ((threadIdx.x & 31) == 0 && si) atomic_add_i64(acc_in, si);
 }
 
 // Subtract-add records of Eq. 3 for every arc incident to a changed node,
@@ -552,7 +557,8 @@ __global__ void k_deg_sum(Adj<WT> out, Adj<WT> in, const int32_t* l, const int32
 // head's in-row when the tail is unchanged).
 template <class WT>
 __global__ void k_emit(Adj<WT> out, Adj<WT> in, ChunkMap m, const int32_t* par, const int32_t* par_old,
-                       const int32_t* stC, int32_t epC, int bits, u64* rk, u64* rv, int32_t* cnt) {
+                       const int32_t* stC, int32_t epC, int bits, u64* rk, u64* rv, int32_t* cnt, int64_t cap,
+                       int32_t* err) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -605,12 +611,16 @@ __global__ void k_emit(Adj<WT> out, Adj<WT> in, ChunkMap m, const int32_t* par, 
       int32_t wbase = 0;
       if (lane == 31 && wtot) wbase = atomicAdd(cnt, wtot);
       wbase = __shfl_sync(0xffffffffu, wbase, 31);
-      int32_t p = wbase + incl - nrec;
+      int64_t p = (int64_t)wbase + incl - nrec;
 #pragma unroll
       for (int j = 0; j < 4; ++j)
         if (ok[j]) {
-          rk[p] = rkey[j];
-          rv[p] = rval[j];
+          if (p < cap) {
+            rk[p] = rkey[j];
+            rv[p] = rval[j];
+          } else {
+            atomicExch(err, 3);  // the record bound was wrong: reported, nothing written past it
+          }
           ++p;
         }
     }
@@ -918,6 +928,11 @@ int64_t ingest(ldl_ctx& c, const ldl_update* upd, int64_t count, int on_device, 
   }
   if (c.m + *dm >= ((int64_t)1 << 50) || c.m + *dm < 0) ldl_throw(LDL_E_OVERFLOW, "total weight m would reach 2^50");
   zero_cnt(c, K_REC);
+  // up to two arcs per distinct key (an undirected edge and its mirror); the
+  // sort above may have swapped rk / rv with its scratch, so their capacity
+  // is only known to cover `count`
+  c.rk.reserve(2 * nu + 2, c.s);
+  c.rv.reserve(2 * nu + 2, c.s);
   k_emit_arcs<<<grid_for(nu, TPB), TPB, 0, c.s>>>(c.rk2.p, c.rsum2.p, nu, c.bits, c.directed, c.rk.p, c.rv.p,
                                                   c.dcnt + K_REC);
   CKL("k_emit_arcs");
@@ -1215,23 +1230,27 @@ int32_t split(ldl_ctx& c, int r, int32_t epD, int32_t epX) {
 }
 
 template <class WT>
-static void emit_records(ldl_ctx& c, int r, Adj<WT> out, Adj<WT> in, int32_t nC, int32_t epC) {
-  CK(cudaMemsetAsync(&c.d_sc->need, 0, sizeof(int64_t), c.s));
-  k_deg_sum<WT><<<grid_for(nC, TPB), TPB, 0, c.s>>>(out, in, c.lC.p, c.dcnt + K_C, &c.d_sc->need);
+static void emit_records(ldl_ctx& c, int r, Adj<WT> out, Adj<WT> in, int32_t nC, int32_t epC, bool build) {
+  static_assert(offsetof(DevScalars, need2) == offsetof(DevScalars, need) + 8, "adjacent accumulators");
+  CK(cudaMemsetAsync(&c.d_sc->need, 0, 2 * sizeof(int64_t), c.s));
+  k_deg_sum<WT><<<grid_for(nC, TPB), TPB, 0, c.s>>>(out, in, c.lC.p, c.dcnt + K_C, &c.d_sc->need, &c.d_sc->need2);
   CKL("k_deg_sum");
-  int64_t deg = 0;
+  int64_t deg[2] = {0, 0};  // out-row and in-row entries of the changed nodes
   {
-    const HostRead r{&c.d_sc->need, &deg, sizeof(int64_t)};
+    const HostRead r{&c.d_sc->need, deg, 2 * sizeof(int64_t)};
     host_read(c, &r, 1);
   }
-  const int64_t cap = 2 * deg + 16;
+  // at most a subtract and an add record per visited entry; in the static
+  // build no node had a parent (no subtract records) and every node is
+  // changed (no in-row records), so one record per out-row entry
+  const int64_t cap = (build ? deg[0] : 2 * (deg[0] + deg[1])) + 16;
   c.rk2.reserve(cap, c.s);
   c.rv2.reserve(cap, c.s);
   zero_cnt(c, K_REC);
   ChunkMap m = chunk_map(c, c.lC.p, c.dcnt + K_C, nC, out.len, in.len);
   k_emit<WT><<<grid_for((int64_t)nC * 64, TPB, 16), TPB, 0, c.s>>>(out, in, m, c.lv[r].par.p, c.par_old.p,
                                                                           c.stC.p, epC, c.bits, c.rk2.p, c.rv2.p,
-                                                                          c.dcnt + K_REC);
+                                                                          c.dcnt + K_REC, cap, c.dcnt + K_ERR);
   CKL("k_emit");
 }
 
@@ -1248,9 +1267,10 @@ void aggregate(ldl_ctx& c, int r, int32_t epD, int32_t epC, int32_t epA_next, bo
   const int32_t nC = rd_cnt(c, K_C);
   int64_t nr = 0;
   if (nC > 0) {
-    if (r == 0) emit_records<int32_t>(c, r, adj_out0(c), adj_in0(c), nC, epC);
-    else emit_records<int64_t>(c, r, adj_out(c, r), adj_in(c, r), nC, epC);
+    if (r == 0) emit_records<int32_t>(c, r, adj_out0(c), adj_in0(c), nC, epC, build);
+    else emit_records<int64_t>(c, r, adj_out(c, r), adj_in(c, r), nC, epC, build);
     const int64_t nrec = rd_cnt(c, K_REC);
+    if (nrec > c.rk2.cap) ldl_throw(LDL_E_INVALID, "internal: aggregate records exceed their bound");
     sub_end(c, SU_AGG_EMIT);
     sub_begin(c);
     sort_pairs(c.rk2, c.rv2, c.tk, c.tv, nrec, 2 * c.bits, c.P, c.s);

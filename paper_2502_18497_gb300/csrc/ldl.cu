@@ -380,8 +380,31 @@ static void static_build(ldl_ctx& c) {
     const int32_t epC = c.next_epoch();
     aggregate(c, r, epD, epC, 0, true, nD);
   }
-  if (rd_cnt(c, K_ERR)) ldl_throw(LDL_E_INVALID, "internal: new supernode already has a parent");
+  if (rd_cnt(c, K_ERR)) ldl_throw(LDL_E_INVALID, "internal: a new supernode already had a parent, or records exceeded their bound");
   check_scan_wait(c);
+}
+
+// The static build's record and table buffers are sized by the whole graph
+// (every node is in the first frontier); batches need a small fraction, so
+// they are freed here and grow again to what batches use.
+static void release_build_scratch(ldl_ctx& c) {
+  CK(cudaStreamSynchronize(c.s));
+  DBuf<u64>* bu[] = {&c.rk, &c.rv, &c.tk, &c.tv, &c.rk2, &c.rv2, &c.crk, &c.crv, &c.fk, &c.trk, &c.trv};
+  for (auto* b : bu) b->release();
+  c.rsum.release();
+  c.rsum2.release();
+  c.gkeys.release();
+  c.gvals.release();
+  c.glist.release();
+  c.gtab_clean = 0;
+  c.pb_hi.release();
+  c.pb_lo.release();
+  c.pb_c.release();
+  c.CS.release();
+  c.P.hist.release();
+  c.P.pos.release();
+  c.P.usum.release();
+  c.P.flag.release();
 }
 
 // ---------------------------------------------------------------- transactions
@@ -550,7 +573,7 @@ static void apply_batch(ldl_ctx& c, const ldl_update* upd, int64_t count, int on
   for (int r = 1; r <= T; ++r) flush_level(c, r);
   stage_end(c, ST_AGG);
   c.res.n_changed = changed_labels(c, epCh);
-  if (rd_cnt(c, K_ERR)) ldl_throw(LDL_E_INVALID, "internal: new supernode already has a parent");
+  if (rd_cnt(c, K_ERR)) ldl_throw(LDL_E_INVALID, "internal: a new supernode already had a parent, or records exceeded their bound");
   c.res.host_syncs = c.syncs;
   CK(cudaMemcpyAsync(&c.res.edges_scanned, &c.d_sc->scanned, sizeof(int64_t), cudaMemcpyDeviceToHost, c.s));
   check_scan_wait(c);
@@ -679,6 +702,7 @@ ldl_status ldl_create(const ldl_params* params, int64_t n, int64_t nnz, const in
     level_alloc(*c, 0);
     upload_graph(*c, nnz, row_ptr, col, w);
     static_build(*c);
+    release_build_scratch(*c);
   } catch (const LdlError& e) {
     g_create_err = e.msg;
     free_all(*c);

@@ -3,6 +3,7 @@
 // filter of Sec. III-E as deterministic parallel rounds, and the commit of an
 // accepted mini-batch with the additive repair of the community totals and
 // the exact modularity change dQ(B) with its rollback test.
+#include <atomic>
 #include <cooperative_groups.h>
 
 #include "chunks.cuh"
@@ -20,6 +21,9 @@ constexpr int MID_DEG = 2048;   // rows above it: clusters (optional) or the hub
 constexpr int CL = 8;             // blocks per cluster (hub rows up to CLUSTER_DEG entries)
 constexpr int CL_SLOTS = 8192;    // hash slots per block of a cluster (96 KB of shared memory)
 constexpr int CLUSTER_DEG = CL * CL_SLOTS / 2;  // upper limit of cluster_max_deg
+constexpr int64_t HUB_TABLE_SLOTS = (int64_t)1 << 28;  // hub hash slots held at once (3 GB)
+// the bound in force (a test hook lowers it)
+std::atomic<int64_t> g_hub_table_slots{HUB_TABLE_SLOTS};
 // the bin bounds a context may use keep every table at most half full
 static_assert(BIN_MAX[0] == HG8 / 2 && BIN_MAX[1] == HG32 / 2 && BIN_MAX[2] == 2048 / 2 &&
                   BIN_MAX[3] == HB / 2 && BIN_MAX[3] == MID_DEG,
@@ -1371,45 +1375,81 @@ static void sweep_t(ldl_ctx& c, int r, Adj<WT> out, Adj<WT> in, const int32_t* l
   const int32_t cc = cn[K_CLU - K_SMALL], ch = cn[K_LARGE - K_SMALL];
   if (kev) CK(cudaEventRecord(kev[6], c.s));  // the wait above is charged to no kernel
   if (ch > 0) {
-    const int32_t nh = ch;
-    c.gkeys.reserve(tab, c.s);
-    c.gvals.reserve(tab, c.s);
+    // Hub tables hold 2..4 slots per entry.  When all hubs' tables together
+    // exceed the slot budget (static builds of the largest graphs), the hubs
+    // are swept in consecutive groups whose tables fit, reusing the space.
+    std::vector<int32_t> gb{0, ch};
+    int64_t tab_use = tab;
+    const int64_t budget = g_hub_table_slots.load();
+    if (tab > budget) {
+      std::vector<int64_t> sz((size_t)ch);
+      CK(cudaMemcpyAsync(sz.data(), c.binLsz.p, sizeof(int64_t) * (size_t)ch, cudaMemcpyDeviceToHost, c.s));
+      CK(cudaStreamSynchronize(c.s));
+      ++c.syncs;
+      gb.assign(1, 0);
+      int64_t acc = 0;
+      tab_use = 0;
+      for (int32_t h = 0; h < ch; ++h) {
+        if (acc + sz[(size_t)h] > budget && h > gb.back()) {
+          gb.push_back(h);
+          tab_use = std::max(tab_use, acc);
+          acc = 0;
+        }
+        acc += sz[(size_t)h];
+      }
+      gb.push_back(ch);
+      tab_use = std::max(tab_use, acc);
+    }
+    c.gkeys.reserve(tab_use, c.s);
+    c.gvals.reserve(tab_use, c.s);
     if (c.gtab_clean != c.gkeys.cap || c.gvals.cap != c.gkeys.cap) {  // fresh tables: fill once
       k_hub_init<<<grid_for(c.gkeys.cap, TPB), TPB, 0, c.s>>>(c.gkeys.p, c.gvals.p, c.gkeys.cap);
       CKL("k_hub_init");
       c.gtab_clean = c.gkeys.cap;
     }
-    c.glist.reserve(tab / 2 + 1, c.s);
-    c.hcnt.reserve(nh + 1, c.s);
-    CK(cudaMemsetAsync(c.hcnt.p, 0, sizeof(int32_t) * (size_t)(nh + 1), c.s));
-    // table offsets per hub, in list order
-    CK(cudaMemsetAsync(c.binLsz.p + nh, 0, sizeof(int64_t), c.s));
-    scan_exclusive(c.binLsz.p, c.binLoff.p, nh + 1, c.P, c.s, false);
-    c.hub_ecnt.reserve(nh + 2, c.s);
-    c.hub_epre.reserve(nh + 2, c.s);
-    const int64_t ech = tab / 2 / EVAL_CH + nh + 1;  // bounds the evaluation chunks
+    c.glist.reserve(tab_use / 2 + 1, c.s);
+    c.hcnt.reserve(ch + 1, c.s);
+    // table sizes end with a zero so that each group's offset scan has a total
+    CK(cudaMemsetAsync(c.binLsz.p + ch, 0, sizeof(int64_t), c.s));
+    c.hub_ecnt.reserve(ch + 2, c.s);
+    c.hub_epre.reserve(ch + 2, c.s);
+    const int64_t ech = tab_use / 2 / EVAL_CH + ch + 1;  // bounds the evaluation chunks of any group
     c.pb_hi.reserve(ech, c.s);
     c.pb_lo.reserve(ech, c.s);
     c.pb_c.reserve(ech, c.s);
-    ChunkMap m = chunk_map(c, c.binL.p, c.dcnt + K_LARGE, nh, out.len, c.directed ? in.len : nullptr);
     if (kev) CK(cudaEventRecord(kev[7], c.s));
-    k_hub_acc<WT, MODE><<<grid_for((int64_t)nh * 2048, TPB, 16), TPB, 0, c.s>>>(
-        A, m, c.binLoff.p, c.binLsz.p, c.gkeys.p, c.gvals.p, c.glist.p, c.hcnt.p);
-    CKL("k_hub_acc");
-    if (kev) CK(cudaEventRecord(kev[8], c.s));
-    // evaluation chunks per hub from its occupied-slot count (device only)
-    k_eval_counts<<<grid_for(nh + 1, TPB), TPB, 0, c.s>>>(c.hcnt.p, nh, c.hub_ecnt.p);
-    CKL("k_eval_counts");
-    scan_exclusive(c.hub_ecnt.p, c.hub_epre.p, nh + 1, c.P, c.s, false);
-    const int ge = grid_for(ech, 1, 8);
-    k_hub_eval<WT, MODE><<<ge, TPB, 0, c.s>>>(A, c.binL.p, nh, c.binLoff.p, c.binLsz.p, c.hub_epre.p, c.gkeys.p,
-                                              c.gvals.p, c.glist.p, c.hcnt.p, c.pb_hi.p, c.pb_lo.p, c.pb_c.p);
-    CKL("k_hub_eval");
-    k_hub_final<WT, MODE><<<grid_for((int64_t)nh * 32, TPB), TPB, 0, c.s>>>(A, c.binL.p, nh, c.hub_epre.p, c.pb_hi.p,
-                                                                           c.pb_lo.p, c.pb_c.p);
-    CKL("k_hub_final");
-    k_hub_clear<<<ge, TPB, 0, c.s>>>(nh, c.binLoff.p, c.hub_epre.p, c.hcnt.p, c.glist.p, c.gkeys.p, c.gvals.p);
-    CKL("k_hub_clear");
+    for (size_t gi = 0; gi + 1 < gb.size(); ++gi) {
+      const int32_t g0 = gb[gi], nh = gb[gi + 1] - g0;
+      const int32_t* L = c.binL.p + g0;
+      int64_t* Lsz = c.binLsz.p + g0;
+      int64_t* Loff = c.binLoff.p + g0;
+      const int32_t* cntp = c.dcnt + K_LARGE;
+      if (gb.size() > 2) {
+        set_cnt(c, K_HUBG, nh);
+        cntp = c.dcnt + K_HUBG;
+      }
+      CK(cudaMemsetAsync(c.hcnt.p, 0, sizeof(int32_t) * (size_t)(nh + 1), c.s));
+      // table offsets per hub of the group, in list order
+      scan_exclusive(Lsz, Loff, nh + 1, c.P, c.s, false);
+      ChunkMap m = chunk_map(c, L, cntp, nh, out.len, c.directed ? in.len : nullptr);
+      k_hub_acc<WT, MODE><<<grid_for((int64_t)nh * 2048, TPB, 16), TPB, 0, c.s>>>(
+          A, m, Loff, Lsz, c.gkeys.p, c.gvals.p, c.glist.p, c.hcnt.p);
+      CKL("k_hub_acc");
+      if (kev && gi + 2 == gb.size()) CK(cudaEventRecord(kev[8], c.s));
+      // evaluation chunks per hub from its occupied-slot count (device only)
+      k_eval_counts<<<grid_for(nh + 1, TPB), TPB, 0, c.s>>>(c.hcnt.p, nh, c.hub_ecnt.p);
+      CKL("k_eval_counts");
+      scan_exclusive(c.hub_ecnt.p, c.hub_epre.p, nh + 1, c.P, c.s, false);
+      const int ge = grid_for(ech, 1, 8);
+      k_hub_eval<WT, MODE><<<ge, TPB, 0, c.s>>>(A, L, nh, Loff, Lsz, c.hub_epre.p, c.gkeys.p, c.gvals.p, c.glist.p,
+                                                c.hcnt.p, c.pb_hi.p, c.pb_lo.p, c.pb_c.p);
+      CKL("k_hub_eval");
+      k_hub_final<WT, MODE><<<grid_for((int64_t)nh * 32, TPB), TPB, 0, c.s>>>(A, L, nh, c.hub_epre.p, c.pb_hi.p,
+                                                                             c.pb_lo.p, c.pb_c.p);
+      CKL("k_hub_final");
+      k_hub_clear<<<ge, TPB, 0, c.s>>>(nh, Loff, c.hub_epre.p, c.hcnt.p, c.glist.p, c.gkeys.p, c.gvals.p);
+      CKL("k_hub_clear");
+    }
   } else if (kev) {
     CK(cudaEventRecord(kev[7], c.s));
     CK(cudaEventRecord(kev[8], c.s));
@@ -1426,6 +1466,10 @@ static void sweep_t(ldl_ctx& c, int r, Adj<WT> out, Adj<WT> in, const int32_t* l
     c.ks_launch[5] += ch > 0;
     c.ks_launch[6] += ch > 0 ? 3 : 0;  // evaluation, final reduction, clearing
   }
+}
+
+extern "C" void ldl_debug_hub_table_slots(int64_t slots) {
+  g_hub_table_slots.store(slots > 0 ? slots : HUB_TABLE_SLOTS);
 }
 
 void sweep(ldl_ctx& c, int r, int mode, const int32_t* list, int idx_n, int64_t n_hint) {

@@ -97,6 +97,7 @@ def load(path: Optional[str] = None):
         "ldl_server_destroy": (None, [P]),
         "ldl_debug_decouple": (I32, [P, I64, P, P, P, P, P, P]),
         "ldl_debug_sort_pairs": (I32, [P, I64, P, P, I32]),
+        "ldl_debug_hub_table_slots": (None, [I64]),
         "ldl_debug_alloc_counts": (None, [P, P]),
         "ldl_batch_estimate_bytes": (I32, [P, I64, P]),
         "ldl_server_stats": (I32, [P, P, P]),
@@ -125,7 +126,7 @@ def exported_symbols():
             "ldl_server_create", "ldl_server_admit", "ldl_server_submit", "ldl_server_wait",
             "ldl_server_destroy", "ldl_debug_decouple", "ldl_debug_alloc_counts", "ldl_batch_estimate_bytes",
             "ldl_server_stats", "ldl_server_debug_free_bytes", "ldl_save", "ldl_load", "ldl_grow",
-            "ldl_num_vertices", "ldl_is_directed", "ldl_debug_sort_pairs"]
+            "ldl_num_vertices", "ldl_is_directed", "ldl_debug_sort_pairs", "ldl_debug_hub_table_slots"]
 
 
 def launch_count() -> int:

@@ -207,3 +207,36 @@ def test_device_sort_is_a_stable_sort(ldl, host_ctx, count, bits, dup):
     order = np.argsort(keys, kind="stable")
     assert np.array_equal(k, keys[order])
     assert np.array_equal(v, vals[order])
+
+
+@pytest.mark.parametrize("directed", [True, False])
+def test_hub_groups_match_oracle(ldl, directed):
+    """A hub-table budget below any hub's table makes every hub sweep run
+    one hub per group (static build and batches): the whole state still
+    equals the oracle's."""
+    from synth import EdgeStream, csr_from_arcs, rmat_directed, rmat_stream
+    g = rmat_directed(scale=14, arcs=1 << (18 if directed else 19), seed=61)
+    s, d, w = g.arcs()
+    if directed:
+        bs = rmat_stream(g, batches=4, size=2000, seed=61)
+        deg = np.bincount(s, minlength=g.n) + np.bincount(d, minlength=g.n)
+    else:
+        g = csr_from_arcs(g.n, s, d, w, directed=False)
+        st = EdgeStream.from_graph(g, 61)
+        bs = [random_batch(st, 1200, 500, 300, 8, 61 + t) for t in range(4)]
+        deg = np.diff(g.row_ptr)
+    assert (deg > 2048).sum() >= 8  # hubs above the last bin
+    lib = ldl.load()
+    lib.ldl_debug_hub_table_slots(1 << 12)
+    try:
+        o = Oracle(g)
+        d = ldl.LDL.from_graph(g)
+        msgs = compare_states(o, d, "create")
+        assert not msgs, "\n".join(msgs[:8])
+        for t, b in enumerate(bs):
+            assert o.apply(b) == 0
+            d.apply(b)
+            msgs = compare_states(o, d, f"batch {t}")
+            assert not msgs, "\n".join(msgs[:8])
+    finally:
+        lib.ldl_debug_hub_table_slots(0)
