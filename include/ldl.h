@@ -219,9 +219,12 @@ ldl_status ldl_estimate_bytes(const ldl_params* params, int64_t n, int64_t nnz, 
 
 /* Estimated new device bytes one batch of `count` updates may allocate on ctx:
  * the rollback snapshot (first batch), record buffers beyond their current
- * capacity, and pool compactions of levels whose slack headroom is short.  A
- * planning figure for admission, not a bound: a batch that runs out of memory
- * anyway is rolled back (LDL_E_NOMEM, state unchanged). */
+ * capacity, and pool compactions of levels whose slack headroom is short, and
+ * at least `count` times the most device memory per update that any earlier
+ * batch of this context asked for (a batch whose frontier reaches hubs can
+ * touch most of the graph).  A planning figure for admission, not a bound: a
+ * batch that runs out of memory anyway is rolled back (LDL_E_NOMEM, state
+ * unchanged). */
 ldl_status ldl_batch_estimate_bytes(const ldl_ctx* ctx, int64_t count, int64_t* bytes);
 
 /*

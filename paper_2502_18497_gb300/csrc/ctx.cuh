@@ -124,6 +124,7 @@ struct ldl_ctx {
   size_t kev_used = 0;
   double ks_launch[KS_GROUPS] = {0, 0, 0, 0, 0, 0, 0};
   int64_t syncs = 0;  // host synchronisations in the current batch
+  int64_t grow_per_update = 0;  // most device bytes a batch of this context allocated per update
   // host reads of device values: a pinned, device-mapped page (word 0 is the
   // sequence number of the last read, the payload follows)
   volatile int64_t* h_pub = nullptr;

@@ -28,10 +28,13 @@ static std::atomic<int64_t> g_fail_after{0};
 std::atomic<int64_t> g_launches{0};
 static std::atomic<int64_t> g_allocs{0}, g_txn_allocs{0};
 static thread_local bool t_in_txn = false;  // this thread is inside a batch transaction
+static thread_local bool t_count_batch = false;  // this thread is applying a batch
+static thread_local int64_t t_batch_bytes = 0;   // device bytes it asked for meanwhile
 
 void* dalloc(size_t bytes) {
   g_allocs.fetch_add(1, std::memory_order_relaxed);
   if (t_in_txn) g_txn_allocs.fetch_add(1, std::memory_order_relaxed);
+  if (t_count_batch) t_batch_bytes += ((int64_t)bytes + (2 << 20) - 1) & ~(int64_t)((2 << 20) - 1);  // device pages
   int64_t k = g_fail_after.load();
   if (k > 0) {
     if (g_fail_after.fetch_sub(1) == 1) ldl_throw(LDL_E_NOMEM, "injected allocation failure");
@@ -725,19 +728,30 @@ ldl_status ldl_apply_batch(ldl_ctx* c, const ldl_update* updates, int64_t count,
     c->err = "the context's state was lost by an earlier failed rollback; destroy it";
     return LDL_E_CUDA;
   }
+  // the device bytes a batch asks for (including a request that fails) per
+  // update, kept as the context's worst case for ldl_batch_estimate_bytes
+  auto learn = [&]() {
+    t_count_batch = false;
+    if (count > 0) c->grow_per_update = std::max(c->grow_per_update, (t_batch_bytes + count - 1) / count);
+  };
   try {
     DeviceScope ds(c->dev);
+    t_batch_bytes = 0;
+    t_count_batch = true;
     try {
       apply_batch(*c, updates, count, on_device);
       CK(cudaStreamSynchronize(c->s));
       txn_commit(*c);
+      learn();
     } catch (const LdlError& e) {
+      learn();
       c->err = e.msg;
       txn_rollback(*c);
       cudaGetLastError();
       return e.st;
     }
   } catch (const LdlError& e) {
+    t_count_batch = false;
     c->err += std::string("; ") + e.msg;
     cudaGetLastError();
     return LDL_E_CUDA;
@@ -785,6 +799,9 @@ ldl_status ldl_batch_estimate_bytes(const ldl_ctx* c, int64_t count, int64_t* by
   };
   pool(c->lv[0].out0, 4);
   for (int r = 1; r <= c->T; ++r) pool(c->lv[r].out, 8);
+  // a batch whose frontier spreads over hubs can need far more: the most any
+  // earlier batch of this context asked for per update bounds it from below
+  b = std::max(b, c->grow_per_update * count);
   *bytes = b;
   return LDL_OK;
 }

@@ -240,3 +240,24 @@ def test_hub_groups_match_oracle(ldl, directed):
             assert not msgs, "\n".join(msgs[:8])
     finally:
         lib.ldl_debug_hub_table_slots(0)
+
+
+def test_batch_estimate_covers_observed_growth(ldl):
+    """ldl_batch_estimate_bytes learns from the batches it has seen: after a
+    batch, the estimate for a batch of the same size covers the device memory
+    that batch added."""
+    import ctypes
+
+    import torch
+    from synth import rmat_directed, rmat_stream
+    g = rmat_directed(scale=14, arcs=1 << 18, seed=62)
+    bs = rmat_stream(g, batches=2, size=20000, seed=62)
+    d = ldl.LDL.from_graph(g)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    d.apply(bs[0])
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    est = ctypes.c_int64()
+    assert ldl.load().ldl_batch_estimate_bytes(d._h, len(bs[1]), ctypes.byref(est)) == 0
+    assert est.value >= free0 - free1 > 0
