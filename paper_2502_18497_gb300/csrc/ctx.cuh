@@ -100,6 +100,8 @@ struct ldl_ctx {
   DBuf<int32_t> ndx;
   DBuf<int64_t> ndko, ndki;
   DBuf<u64> crk, crv, fk, trk, trv;
+  DBuf<u64> flk;      // a pending list's summed records (keys) ...
+  DBuf<int64_t> flv;  // ... and their weight changes
   DBuf<int64_t> chunk_pre;
   DBuf<int64_t> hub_ecnt, hub_epre, pb_hi;
   DBuf<uint64_t> pb_lo;

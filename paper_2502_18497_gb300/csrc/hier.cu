@@ -1006,8 +1006,11 @@ static Chain chain_of(ldl_ctx& c, const int32_t* epA) {
 static void chain_records(ldl_ctx& c, const u64* keys, const int64_t* vals, int64_t n, int q0, bool self,
                           bool add_k) {
   if (n <= 0 || (!self && q0 >= c.T)) return;
+  if (n > INT32_MAX / 2) ldl_throw(LDL_E_OVERFLOW, "too many weight records in one step for the 32-bit counters");
   for (int q = self ? q0 : q0 + 1; q <= c.T; ++q) {
     LevelState& L = c.lv[q];
+    // the device counters are 32-bit: a list that would pass them is applied first
+    if (L.pend_ub + n > INT32_MAX - 1) flush_level(c, q);
     L.pk.reserve(L.pend_ub + n + 1, c.s, true);
     L.pv.reserve(L.pend_ub + n + 1, c.s, true);
     L.pend_ub += n;
@@ -1033,12 +1036,13 @@ void flush_level(ldl_ctx& c, int q) {
   zero_cnt(c, K_PEND0 + q);
   if (n <= 0) return;
   sort_pairs(L.pk, L.pv, c.tk, c.tv, n, 2 * c.bits, c.P, c.s);
-  c.rk.reserve(n + 1, c.s);
-  c.rsum.reserve(n + 1, c.s);
-  const int64_t nr = reduce_by_key(L.pk.p, L.pv.p, n, c.rk.p, c.rsum.p, c.P, c.s);
+  // own output buffers: a flush may run while the caller's records sit in rk / rv
+  c.flk.reserve(n + 1, c.s);
+  c.flv.reserve(n + 1, c.s);
+  const int64_t nr = reduce_by_key(L.pk.p, L.pv.p, n, c.flk.p, c.flv.p, c.P, c.s);
   c.res.pending_records += n;
   c.res.pending_applied += nr;
-  apply_level(c, q, c.rk.p, c.rsum.p, nr);
+  apply_level(c, q, c.flk.p, c.flv.p, nr);
 }
 
 void repair_batch(ldl_ctx& c, int64_t na, const int32_t* epA, int32_t epT, int64_t dm) {
@@ -1244,6 +1248,7 @@ static void emit_records(ldl_ctx& c, int r, Adj<WT> out, Adj<WT> in, int32_t nC,
   // build no node had a parent (no subtract records) and every node is
   // changed (no in-row records), so one record per out-row entry
   const int64_t cap = (build ? deg[0] : 2 * (deg[0] + deg[1])) + 16;
+  if (cap > INT32_MAX) ldl_throw(LDL_E_OVERFLOW, "aggregate records beyond the 32-bit record counter");
   c.rk2.reserve(cap, c.s);
   c.rv2.reserve(cap, c.s);
   zero_cnt(c, K_REC);

@@ -231,8 +231,9 @@ void free_all(ldl_ctx& c) {
                           &c.lab_before, &c.binT, &c.binS, &c.binM, &c.binM2, &c.binC, &c.binL, &c.gkeys, &c.ndx,
                           &c.glist, &c.hcnt};
   for (auto* b : b32) b->release();
-  DBuf<u64>* bu[] = {&c.rk, &c.rv, &c.tk, &c.tv, &c.rk2, &c.rv2, &c.crk, &c.crv, &c.fk, &c.trk, &c.trv};
+  DBuf<u64>* bu[] = {&c.rk, &c.rv, &c.tk, &c.tv, &c.rk2, &c.rv2, &c.crk, &c.crv, &c.fk, &c.trk, &c.trv, &c.flk};
   for (auto* b : bu) b->release();
+  c.flv.release();
   c.cglo.release();
   c.pb_lo.release();
   c.pb_c.release();
