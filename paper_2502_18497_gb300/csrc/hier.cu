@@ -248,8 +248,9 @@ __global__ void k_chain_frontier(const int32_t* l0, const int32_t* n0, int top, 
 
 // ---------------------------------------------------------------- push-down
 // Children of each listed level-(q+1) node take its label at level q.
-__global__ void k_push(ChunkMap m, const int32_t* lab_up, Adj<int32_t> ch_adj, int32_t* lab, int32_t* olist,
-                       int32_t* nout, int32_t* stCh, int32_t epCh, int32_t* lCh, int32_t* nCh, int32_t* lab_before) {
+__global__ void k_push(ChunkMap m, const int32_t* lab_up, Adj<int32_t> ch_adj, const int32_t* par, int32_t* lab,
+                       int32_t* olist, int32_t* nout, int32_t* stCh, int32_t epCh, int32_t* lCh, int32_t* nCh,
+                       int32_t* lab_before) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -261,11 +262,10 @@ __global__ void k_push(ChunkMap m, const int32_t* lab_up, Adj<int32_t> ch_adj, i
     const int64_t o = ch_adj.off[ch.v];
     for (int32_t base = ch.k0; base < ch.k1; base += 32) {
       const int32_t k = base + lane;
-      const bool valid = k < ch.k1;
-      int32_t u = 0;
+      int32_t u = k < ch.k1 ? ch_adj.col[o + k] : 0;
+      const bool valid = k < ch.k1 && par[u] == ch.v;  // a listed node that left (emptied) is skipped
       bool first = false;
       if (valid) {
-        u = ch_adj.col[o + k];
         if (stCh) {
           first = stamp_claim(stCh, epCh, u);
           if (first) lab_before[u] = lab[u];
@@ -395,8 +395,8 @@ __global__ void k_leave_degree(Adj<WT> out, Adj<WT> in, ChunkMap m, const int32_
 // Remaining members of the re-checked refined communities whose connectivity
 // is in doubt (flagged, or their seed node left); each starts as its own
 // component.
-__global__ void k_members(Adj<int32_t> ch_adj, ChunkMap m, const int32_t* stL, int32_t epL, const int32_t* ckf,
-                          int32_t epF, int32_t* comp, int32_t* lG, int32_t* nG) {
+__global__ void k_members(Adj<int32_t> ch_adj, ChunkMap m, const int32_t* par, const int32_t* stL, int32_t epL,
+                          const int32_t* ckf, int32_t epF, int32_t* comp, int32_t* lG, int32_t* nG) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -413,7 +413,7 @@ __global__ void k_members(Adj<int32_t> ch_adj, ChunkMap m, const int32_t* stL, i
       int32_t u = 0;
       if (k < ch.k1) {
         u = ch_adj.col[o + k];
-        want = stL[u] != epL;
+        want = stL[u] != epL && par[u] == X;  // listed nodes that emptied or left are skipped
         if (want) comp[u] = u;
       }
       warp_append(want, u, lG, nG);
@@ -689,8 +689,7 @@ __global__ void k_exist_cands(const int32_t* lC, const int32_t* nC, const int32_
 // Existence at level q: a node with members appears; an emptied node leaves
 // its parent (its weights are already zero), which may empty the parent.
 __global__ void k_exist(const int32_t* lE, const int32_t* nE, const int32_t* cnt, uint8_t* alive, int32_t* par,
-                        int32_t* cnt_up, int bits, u64* ck, u64* cv, int32_t* ncr, int32_t* stE, int32_t epE2,
-                        int32_t* lE2, int32_t* nE2, int32_t* err) {
+                        int32_t* cnt_up, int32_t* stE, int32_t epE2, int32_t* lE2, int32_t* nE2, int32_t* err) {
   const int32_t n = *nE;
   for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
     const int32_t x = lE[k];
@@ -703,10 +702,9 @@ __global__ void k_exist(const int32_t* lE, const int32_t* nE, const int32_t* cnt
       if (par) {
         const int32_t p = par[x];
         if (p >= 0) {
+          // x stays listed among p's children: readers of the children lists
+          // skip every entry whose node no longer has that parent
           atomicAdd(&cnt_up[p], -1);
-          const int32_t q = atomicAdd(ncr, 1);
-          ck[q] = ((u64)p << bits) | (u64)x;
-          cv[q] = (u64)(int64_t)-1;
           par[x] = -1;
           stamp_add(stE, epE2, p, lE2, nE2);
         }
@@ -1097,8 +1095,8 @@ void pushdown(ldl_ctx& c, int r, int32_t epCh) {
     zero_cnt(c, idxs[flip]);
     ChunkMap m = chunk_map(c, src, c.dcnt + idx, n, L.children.len.p, nullptr);
     k_push<<<grid_for((int64_t)n * 64, TPB, 16), TPB, 0, c.s>>>(
-        m, c.lv[q + 1].lab.p, ch, L.lab.p, dst, c.dcnt + idxs[flip], q == 0 ? c.stCh.p : nullptr, epCh, c.lCh.p,
-        c.dcnt + K_CH, c.lab_before.p);
+        m, c.lv[q + 1].lab.p, ch, L.par.p, L.lab.p, dst, c.dcnt + idxs[flip], q == 0 ? c.stCh.p : nullptr, epCh,
+        c.lCh.p, c.dcnt + K_CH, c.lab_before.p);
     CKL("k_push");
     if (q > 0) {
       src = bufs[flip];
@@ -1211,8 +1209,8 @@ int32_t split(ldl_ctx& c, int r, int32_t epD, int32_t epX) {
     zero_cnt(c, K_G);
     Adj<int32_t> ch{L.children.off.p, L.children.len.p, L.children.col.p, L.children.w.p};
     ChunkMap m = chunk_map(c, c.lX.p, c.dcnt + K_X, nx, L.children.len.p, nullptr);
-    k_members<<<grid_for((int64_t)nx * 64, TPB, 16), TPB, 0, c.s>>>(ch, m, c.stL.p, epL, c.ckf.p, epF, c.comp.p,
-                                                                   c.lG.p, c.dcnt + K_G);
+    k_members<<<grid_for((int64_t)nx * 64, TPB, 16), TPB, 0, c.s>>>(ch, m, L.par.p, c.stL.p, epL, c.ckf.p, epF,
+                                                                   c.comp.p, c.lG.p, c.dcnt + K_G);
     CKL("k_members");
     const int32_t nG = rd_cnt(c, K_G);
     c.res.split_members += nG;
@@ -1345,23 +1343,12 @@ void aggregate(ldl_ctx& c, int r, int32_t epD, int32_t epC, int32_t epA_next, bo
       const bool has_up = q < c.T;
       const int32_t epE2 = c.next_epoch();
       zero_cnt(c, ie2);
-      zero_cnt(c, K_CREC);
-      c.crk.reserve(ne + 1, c.s);
-      c.crv.reserve(ne + 1, c.s);
       k_exist<<<grid_for(ne, TPB), TPB, 0, c.s>>>(le, c.dcnt + ie, c.lv[q].cnt.p, c.lv[q].alive.p,
                                                   has_up ? c.lv[q].par.p : nullptr,
-                                                  has_up ? c.lv[q + 1].cnt.p : nullptr, c.bits, c.crk.p, c.crv.p,
-                                                  c.dcnt + K_CREC, c.stE.p, epE2, le2, c.dcnt + ie2,
-                                                  c.dcnt + K_ERR);
+                                                  has_up ? c.lv[q + 1].cnt.p : nullptr, c.stE.p, epE2, le2,
+                                                  c.dcnt + ie2, c.dcnt + K_ERR);
       CKL("k_exist");
-      // children records of this level and the next level's list, in one read
-      int32_t nd = 0, ne_next = 0;
-      const HostRead rr[2] = {{c.dcnt + K_CREC, &nd, sizeof(int32_t)}, {c.dcnt + ie2, &ne_next, sizeof(int32_t)}};
-      host_read(c, rr, 2);
-      if (nd > 0) {
-        sort_pairs(c.crk, c.crv, c.tk, c.tv, nd, 2 * c.bits, c.P, c.s);
-        csr_apply<int32_t>(c.lv[q].children, c.crk.p, (const int64_t*)c.crv.p, nd, c.bits, c.CS, c.P, c.s, c.d_sc);
-      }
+      const int32_t ne_next = rd_cnt(c, ie2);
       int32_t* t = le;
       le = le2;
       le2 = t;
