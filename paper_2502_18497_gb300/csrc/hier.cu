@@ -686,29 +686,43 @@ __global__ void k_exist_cands(const int32_t* lC, const int32_t* nC, const int32_
   }
 }
 
-// Existence at level q: a node with members appears; an emptied node leaves
-// its parent (its weights are already zero), which may empty the parent.
-__global__ void k_exist(const int32_t* lE, const int32_t* nE, const int32_t* cnt, uint8_t* alive, int32_t* par,
-                        int32_t* cnt_up, int32_t* stE, int32_t epE2, int32_t* lE2, int32_t* nE2, int32_t* err) {
+// Existence after a level-q0 aggregate step, for the candidate level-q0 nodes
+// (old and new parents of the changed nodes): a node with members appears
+// (it has no parent yet); a node left without members dies and leaves its
+// parent, and a parent that thereby loses its last member dies in turn, up
+// the chain to level top.  The walk that takes a parent's member count to
+// zero carries on with that parent, so each death is handled once, and the
+// counts above q0 only fall meanwhile.  (An emptied node stays listed among
+// its parent's children; readers of the lists check the parent.)
+struct ExistChain {
+  int32_t* cnt[8];
+  uint8_t* alive[8];
+  int32_t* par[8];
+};
+
+__global__ void k_exist_chain(const int32_t* lE, const int32_t* nE, int q0, int top, ExistChain ch, int32_t* err) {
   const int32_t n = *nE;
   for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-    const int32_t x = lE[k];
-    const int32_t c = cnt[x];
-    if (!alive[x] && c > 0) {
-      alive[x] = 1;
-      if (par && par[x] >= 0) atomicExch(err, 2);
-    } else if (alive[x] && c == 0) {
-      alive[x] = 0;
-      if (par) {
-        const int32_t p = par[x];
-        if (p >= 0) {
-          // x stays listed among p's children: readers of the children lists
-          // skip every entry whose node no longer has that parent
-          atomicAdd(&cnt_up[p], -1);
-          par[x] = -1;
-          stamp_add(stE, epE2, p, lE2, nE2);
-        }
+    int32_t x = lE[k];
+    int q = q0;
+    const int32_t c = ch.cnt[q][x];
+    if (!ch.alive[q][x]) {
+      if (c > 0) {
+        ch.alive[q][x] = 1;
+        if (q < top && ch.par[q][x] >= 0) atomicExch(err, 2);
       }
+      continue;
+    }
+    if (c != 0) continue;
+    for (;;) {  // x at level q has no members left
+      ch.alive[q][x] = 0;
+      if (q >= top) break;
+      const int32_t p = ch.par[q][x];
+      if (p < 0) break;
+      ch.par[q][x] = -1;
+      if (atomicAdd(&ch.cnt[q + 1][p], -1) != 1) break;
+      x = p;
+      ++q;
     }
   }
 }
@@ -1333,30 +1347,15 @@ void aggregate(ldl_ctx& c, int r, int32_t epD, int32_t epC, int32_t epA_next, bo
     k_exist_cands<<<grid_for(nC, TPB), TPB, 0, c.s>>>(c.lC.p, c.dcnt + K_C, L.par.p, c.par_old.p, c.stE.p, epE,
                                                       c.lE.p, c.dcnt + K_E);
     CKL("k_exist_cands");
-    int32_t* le = c.lE.p;
-    int ie = K_E;
-    int32_t* le2 = c.lE2.p;
-    int ie2 = K_E2;
-    int32_t ne = rd_cnt(c, ie);
-    for (int q = r + 1; q <= c.T; ++q) {
-      if (ne == 0) break;
-      const bool has_up = q < c.T;
-      const int32_t epE2 = c.next_epoch();
-      zero_cnt(c, ie2);
-      k_exist<<<grid_for(ne, TPB), TPB, 0, c.s>>>(le, c.dcnt + ie, c.lv[q].cnt.p, c.lv[q].alive.p,
-                                                  has_up ? c.lv[q].par.p : nullptr,
-                                                  has_up ? c.lv[q + 1].cnt.p : nullptr, c.stE.p, epE2, le2,
-                                                  c.dcnt + ie2, c.dcnt + K_ERR);
-      CKL("k_exist");
-      const int32_t ne_next = rd_cnt(c, ie2);
-      int32_t* t = le;
-      le = le2;
-      le2 = t;
-      int ti = ie;
-      ie = ie2;
-      ie2 = ti;
-      ne = ne_next;
+    ExistChain ech{};
+    for (int q = 0; q <= c.T && q < 8; ++q) {
+      ech.cnt[q] = c.lv[q].cnt.p;
+      ech.alive[q] = c.lv[q].alive.p;
+      ech.par[q] = c.lv[q].par.p;
     }
+    k_exist_chain<<<grid_for(2 * (int64_t)nC, TPB), TPB, 0, c.s>>>(c.lE.p, c.dcnt + K_E, r + 1, c.T, ech,
+                                                                    c.dcnt + K_ERR);
+    CKL("k_exist_chain");
     // the error flag K_ERR is read once at the end of the batch (or of the static build)
   } else {
     sub_end(c, SU_AGG_EMIT);
