@@ -32,7 +32,10 @@ struct DecoupleOut {
   int32_t nc, nb, extra;
 };
 DecoupleOut decouple(ldl_ctx& c, int extra = -1);
-CommitOut commit_move(ldl_ctx& c, int r, int32_t nb, int32_t epB, int32_t epT, int32_t epCh);
+// Launches the commit of a mini-batch; commit_read then reads its outcome
+// (with the counter dcnt[extra_idx] in the same read when extra is given).
+void commit_move(ldl_ctx& c, int r, int32_t nb, int32_t epB, int32_t epT, int32_t epCh);
+CommitOut commit_read(ldl_ctx& c, int extra_idx, int32_t* extra);
 void rollback_move(ldl_ctx& c, int r, int32_t nb, int32_t ntc);
 void mark_moved(ldl_ctx& c, int r, int32_t nb, int32_t epMv, int32_t epM0);
 void commit_ref(ldl_ctx& c, int r, int32_t nb);

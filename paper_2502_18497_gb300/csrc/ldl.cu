@@ -289,7 +289,15 @@ static void move_loop(ldl_ctx& c, int r, int rounds, int32_t epU, int32_t epMv, 
     if (nb == 0) break;
     stage_begin(c);
     const int32_t epB = c.next_epoch(), epT = c.next_epoch();
-    CommitOut co = commit_move(c, r, nb, epB, epT, epCh);
+    commit_move(c, r, nb, epB, epT, epCh);
+    // the next frontier U = V ∪ N(V) is expanded before the commit's outcome
+    // comes back (it only marks neighbours), so one read returns both; a
+    // rolled-back mini-batch ends the loop and its expansion is dropped
+    const int32_t epS2 = c.next_epoch();
+    zero_cnt(c, K_U);
+    expand_set(c, r, c.bv.p, K_B, c.stS.p, epS2, c.lU.p, K_U, nb);
+    int32_t nU2 = 0;
+    const CommitOut co = commit_read(c, K_U, &nU2);
     if (co.dq < 0) {
       rollback_move(c, r, nb, co.ntc);
       c.res.rollbacks++;
@@ -302,10 +310,6 @@ static void move_loop(ldl_ctx& c, int r, int rounds, int32_t epU, int32_t epMv, 
     mark_moved(c, r, nb, epMv, epM0);
     stage_end(c, ST_COMMIT);
     stage_begin(c);
-    const int32_t epS2 = c.next_epoch();
-    zero_cnt(c, K_U);
-    expand_set(c, r, c.bv.p, K_B, c.stS.p, epS2, c.lU.p, K_U, nb);
-    const int32_t nU2 = rd_cnt(c, K_U);
     union_into(c, c.lU.p, K_U, c.stU.p, epU, c.lUstar.p, K_USTAR, nU2);
     stage_end(c, ST_EXPAND);
     nU = nU2;

@@ -1533,7 +1533,7 @@ DecoupleOut decouple(ldl_ctx& c, int extra) {
 }
 
 
-CommitOut commit_move(ldl_ctx& c, int r, int32_t nb, int32_t epB, int32_t epT, int32_t epCh) {
+void commit_move(ldl_ctx& c, int r, int32_t nb, int32_t epB, int32_t epT, int32_t epCh) {
   LevelState& L = c.lv[r];
   const int g = grid_for(nb, TPB);
   zero_cnt(c, K_T);
@@ -1565,11 +1565,15 @@ CommitOut commit_move(ldl_ctx& c, int r, int32_t nb, int32_t epB, int32_t epT, i
                                                                c.snapKo.p, c.snapKi.p, c.snapE.p, c.m,
                                                                c.prm.gamma_num, c.prm.gamma_den, c.d_sc);
   CKL("k_commit_dq");
+}
+
+CommitOut commit_read(ldl_ctx& c, int extra_idx, int32_t* extra) {
   CommitOut o;
   I128 dq, dp;
-  const HostRead rr[4] = {{&c.d_sc->dq, &dq, sizeof(I128)}, {&c.d_sc->dp, &dp, sizeof(I128)},
-                          {&c.d_sc->de, &o.de, sizeof(int64_t)}, {c.dcnt + K_T, &o.ntc, sizeof(int32_t)}};
-  host_read(c, rr, 4);
+  const HostRead rr[5] = {{&c.d_sc->dq, &dq, sizeof(I128)}, {&c.d_sc->dp, &dp, sizeof(I128)},
+                          {&c.d_sc->de, &o.de, sizeof(int64_t)}, {c.dcnt + K_T, &o.ntc, sizeof(int32_t)},
+                          {c.dcnt + (extra ? extra_idx : K_T), extra, sizeof(int32_t)}};
+  host_read(c, rr, extra ? 5 : 4);
   o.dq = i128_of(dq.hi, dq.lo);
   o.dp = i128_of(dp.hi, dp.lo);
   return o;
