@@ -1281,7 +1281,11 @@ void aggregate(ldl_ctx& c, int r, int32_t epD, int32_t epC, int32_t epA_next, bo
   k_changed<<<grid_for(nD, TPB), TPB, 0, c.s>>>(c.lD.p, c.dcnt + K_D, L.par.p, c.par_old.p, c.stC.p, epC, c.lC.p,
                                                 c.dcnt + K_C);
   CKL("k_changed");
-  const int32_t nC = rd_cnt(c, K_C);
+  int32_t nC = 0, nUs = 0;  // changed nodes, and |U*| for the relabelling below: one read
+  {
+    const HostRead rr[2] = {{c.dcnt + K_C, &nC, sizeof(int32_t)}, {c.dcnt + K_USTAR, &nUs, sizeof(int32_t)}};
+    host_read(c, rr, 2);
+  }
   int64_t nr = 0;
   if (nC > 0) {
     if (r == 0) emit_records<int32_t>(c, r, adj_out0(c), adj_in0(c), nC, epC, build);
@@ -1362,7 +1366,6 @@ void aggregate(ldl_ctx& c, int r, int32_t epD, int32_t epC, int32_t epA_next, bo
     sub_begin(c);
   }
   // relabel the level-(r+1) images of frontier and dissolved nodes
-  const int32_t nUs = rd_cnt(c, K_USTAR);
   if (nUs > 0) {
     k_relabel<<<grid_for(nUs, TPB), TPB, 0, c.s>>>(c.lUstar.p, c.dcnt + K_USTAR, L.par.p, L.lab.p, N.lab.p);
     CKL("k_relabel");

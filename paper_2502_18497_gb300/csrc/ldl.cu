@@ -530,10 +530,10 @@ static void apply_batch(ldl_ctx& c, const ldl_update* upd, int64_t count, int on
     const int32_t epM0 = c.next_epoch();
     zero_cnt(c, K_M0);
     for (int r = 0; r <= T; ++r) {
-      const int32_t nA = rd_cnt(c, K_A0 + r);
-      if (nA == 0) continue;
+      // |A^r| stays on the device: the filter strides over it with a grid of
+      // two blocks per SM, and one read returns |U|
       zero_cnt(c, K_U);
-      filter_alive(c, r, c.lv[r].lA.p, K_A0 + r, c.lU.p, K_U, nA);
+      filter_alive(c, r, c.lv[r].lA.p, K_A0 + r, c.lU.p, K_U, std::min<int64_t>(c.n, (int64_t)device_sms() * 512));
       const int32_t nU = rd_cnt(c, K_U);
       if (nU == 0) continue;
       if (r < 8) c.res.frontier_nodes[r] += nU;
