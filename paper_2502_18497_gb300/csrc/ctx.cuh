@@ -181,6 +181,16 @@ inline int64_t* Kin_of(ldl_ctx& c) { return c.directed ? c.Kin.p : c.Kout.p; }
 void host_read(ldl_ctx& c, const HostRead* r, int n);
 int32_t rd_cnt(ldl_ctx& c, int idx);
 void zero_cnt(ldl_ctx& c, int idx);
+// One launch that clears several counters (bit i of mask: dcnt[i]) and up to
+// ZERO_SPANS spans of 64-bit device words (p[i], nw[i] <= K_COUNT words).
+constexpr int ZERO_SPANS = 3;
+struct ZeroSpans {
+  uint64_t mask = 0;
+  int64_t* p[ZERO_SPANS] = {nullptr, nullptr, nullptr};
+  int32_t nw[ZERO_SPANS] = {0, 0, 0};
+};
+inline uint64_t cnt_bit(int idx) { return 1ull << idx; }
+void zero_many(ldl_ctx& c, const ZeroSpans& z);
 void set_cnt(ldl_ctx& c, int idx, int32_t v);
 
 // stage timing

@@ -1040,10 +1040,10 @@ void pending_reset(ldl_ctx& c) {
 // Level q's pending records, sorted by (row, col) and summed per arc (zero
 // sums dropped), applied to its adjacency: the level's weights become
 // current before anything reads them.
-void flush_level(ldl_ctx& c, int q) {
+void flush_level(ldl_ctx& c, int q, int64_t known) {
   LevelState& L = c.lv[q];
   if (L.pend_ub == 0) return;
-  const int64_t n = rd_cnt(c, K_PEND0 + q);
+  const int64_t n = known >= 0 ? known : rd_cnt(c, K_PEND0 + q);
   L.pend_ub = 0;
   zero_cnt(c, K_PEND0 + q);
   if (n <= 0) return;
@@ -1063,11 +1063,18 @@ void repair_batch(ldl_ctx& c, int64_t na, const int32_t* epA, int32_t epT, int64
   apply_level(c, 0, c.rk.p, (const int64_t*)c.rv.p, na);
   // statistic repair: m, degrees, community totals (exactly, with sum_C K_out K_in)
   LevelState& L0 = c.lv[0];
-  zero_cnt(c, K_T);
+  {
+    static_assert(offsetof(DevScalars, p_new) == offsetof(DevScalars, p_old) + sizeof(I128), "adjacent scalars");
+    ZeroSpans z;
+    z.mask = cnt_bit(K_T);
+    z.p[0] = (int64_t*)&c.d_sc->p_old;
+    z.nw[0] = (int32_t)(2 * sizeof(I128) / sizeof(int64_t));
+    z.p[1] = &c.d_sc->de;
+    z.nw[1] = 1;
+    zero_many(c, z);
+  }
   k_dirty<<<grid_for(na, TPB), TPB, 0, c.s>>>(c.rk.p, na, c.bits, L0.lab.p, c.stT.p, epT, c.lT.p, c.dcnt + K_T);
   CKL("k_dirty");
-  CK(cudaMemsetAsync(&c.d_sc->p_old, 0, sizeof(I128) * 2, c.s));
-  CK(cudaMemsetAsync(&c.d_sc->de, 0, sizeof(int64_t), c.s));
   k_psum<<<grid_for(2 * na, TPB), TPB, 0, c.s>>>(c.lT.p, c.dcnt + K_T, c.Kout.p, Kin_of(c), &c.d_sc->p_old);
   CKL("k_psum");
   k_stat_arcs<<<grid_for(na, TPB), TPB, 0, c.s>>>(c.rk.p, (const int64_t*)c.rv.p, na, c.bits, c.directed, L0.lab.p,
@@ -1094,11 +1101,12 @@ void repair_batch(ldl_ctx& c, int64_t na, const int32_t* epA, int32_t epT, int64
   chain_records(c, c.rk.p, (const int64_t*)c.rv.p, na, 0, false, true);
 }
 
-void pushdown(ldl_ctx& c, int r, int32_t epCh) {
-  // lMv holds the level-r nodes moved in this level's move loop
+void pushdown(ldl_ctx& c, int r, int32_t epCh, int64_t moved_ub) {
+  // lMv holds the level-r nodes moved in this level's move loop; its count
+  // stays on the device and moved_ub bounds it (0 exactly when it is empty)
   int32_t* src = c.lMv.p;
   int idx = K_MV;
-  int32_t n = rd_cnt(c, K_MV);
+  int64_t n = std::min<int64_t>(moved_ub, c.n);
   int32_t* bufs[2] = {c.lTmp.p, c.lE2.p};
   int idxs[2] = {K_TMP, K_TMP2};
   int flip = 0;
@@ -1140,14 +1148,13 @@ int32_t dissolve_all(ldl_ctx& c, int r, int32_t epD) {
   return nd;
 }
 
-int32_t singletons_of(ldl_ctx& c, int r, const int32_t* list, int idx_n, int64_t n_hint, int32_t* out, int idx_out) {
+void singletons_of(ldl_ctx& c, int r, const int32_t* list, int idx_n, int64_t n_hint, int32_t* out, int idx_out) {
   zero_cnt(c, idx_out);
   if (n_hint > 0) {
     k_singletons<<<grid_for(n_hint, TPB), TPB, 0, c.s>>>(list, c.dcnt + idx_n, c.lv[r].par.p, c.lv[r + 1].cnt.p, out,
                                                          c.dcnt + idx_out);
     CKL("k_singletons");
   }
-  return rd_cnt(c, idx_out);
 }
 
 void reset_par(ldl_ctx& c, int r, int32_t nD) {
@@ -1188,33 +1195,30 @@ static void union_find(ldl_ctx& c, int r, Adj<WT> out, Adj<WT> in, int32_t nG, i
 int32_t split(ldl_ctx& c, int r, int32_t epD, int32_t epX) {
   LevelState& L = c.lv[r];
   LevelState& N = c.lv[r + 1];
-  zero_cnt(c, K_D);
-  zero_cnt(c, K_X);
-  const int32_t epF = c.next_epoch();  // communities whose connectivity is in doubt
-  int32_t nK = 0, nu = 0;  // deleted-arc endpoints of the level, |U*|: one read
   {
-    const HostRead rr[2] = {{c.dcnt + K_BRK0 + r, &nK, sizeof(int32_t)}, {c.dcnt + K_USTAR, &nu, sizeof(int32_t)}};
-    host_read(c, rr, 2);
+    ZeroSpans z;
+    z.mask = cnt_bit(K_D) | cnt_bit(K_X);
+    zero_many(c, z);
   }
-  if (nK > 0) {
-    k_brk_check<<<grid_for(nK, TPB), TPB, 0, c.s>>>(L.lK.p, c.dcnt + K_BRK0 + r, L.alive.p, L.par.p, c.stX.p, epX,
-                                                    c.lX.p, c.dcnt + K_X, c.ckf.p, epF);
-    CKL("k_brk_check");
-  }
+  const int32_t epF = c.next_epoch();  // communities whose connectivity is in doubt
+  // The level's deleted-arc endpoints and U* stay on the device: both kernels
+  // stride over their lists' counts with a grid bounded by the node count.
+  const int gs = grid_for(c.n, TPB, 4);
+  k_brk_check<<<gs, TPB, 0, c.s>>>(L.lK.p, c.dcnt + K_BRK0 + r, L.alive.p, L.par.p, c.stX.p, epX, c.lX.p,
+                                   c.dcnt + K_X, c.ckf.p, epF);
+  CKL("k_brk_check");
   const int32_t epL = c.next_epoch();
-  if (nu > 0) {
-    k_leave<<<grid_for(nu, TPB), TPB, 0, c.s>>>(c.lUstar.p, c.dcnt + K_USTAR, L.alive.p, L.lab.p, N.lab.p, L.par.p,
-                                                c.par_old.p, L.kout.p, kin_of(c, r), N.kout.p, kin_of(c, r + 1),
-                                                N.cnt.p, c.directed, c.stL.p, epL, c.stD.p, epD, c.lD.p,
-                                                c.dcnt + K_D, c.stX.p, epX, c.lX.p, c.dcnt + K_X, c.nbr.p);
-    CKL("k_leave");
-  }
+  k_leave<<<gs, TPB, 0, c.s>>>(c.lUstar.p, c.dcnt + K_USTAR, L.alive.p, L.lab.p, N.lab.p, L.par.p, c.par_old.p,
+                               L.kout.p, kin_of(c, r), N.kout.p, kin_of(c, r + 1), N.cnt.p, c.directed, c.stL.p, epL,
+                               c.stD.p, epD, c.lD.p, c.dcnt + K_D, c.stX.p, epX, c.lX.p, c.dcnt + K_X, c.nbr.p);
+  CKL("k_leave");
   int32_t cnt2[2] = {0, 0};  // K_D, then K_X (adjacent counters)
   {
     const HostRead rr[2] = {{c.dcnt + K_D, &cnt2[0], sizeof(int32_t)}, {c.dcnt + K_X, &cnt2[1], sizeof(int32_t)}};
     host_read(c, rr, 2);
   }
   const int32_t nleft = cnt2[0], nx = cnt2[1];
+  bool renamed = false;  // k_rename appends to lD; otherwise |D| = nleft
   if (nx > 0) {
     if (nleft > 0) {
       if (r == 0) leave_degree<int32_t>(c, r, adj_out0(c), adj_in0(c), nleft, epL, epF);
@@ -1228,6 +1232,7 @@ int32_t split(ldl_ctx& c, int r, int32_t epD, int32_t epX) {
     CKL("k_members");
     const int32_t nG = rd_cnt(c, K_G);
     c.res.split_members += nG;
+    renamed = nG > 0;
     if (nG > 0) {
       if (r == 0) union_find<int32_t>(c, r, adj_out0(c), adj_in0(c), nG, epL);
       else union_find<int64_t>(c, r, adj_out(c, r), adj_in(c, r), nG, epL);
@@ -1242,7 +1247,7 @@ int32_t split(ldl_ctx& c, int r, int32_t epD, int32_t epX) {
   // the deletions of this level are consumed
   L.brk_ep = c.next_epoch();
   zero_cnt(c, K_BRK0 + r);
-  return rd_cnt(c, K_D);
+  return renamed ? rd_cnt(c, K_D) : nleft;
 }
 
 template <class WT>
@@ -1290,7 +1295,28 @@ void aggregate(ldl_ctx& c, int r, int32_t epD, int32_t epC, int32_t epA_next, bo
   if (nC > 0) {
     if (r == 0) emit_records<int32_t>(c, r, adj_out0(c), adj_in0(c), nC, epC, build);
     else emit_records<int64_t>(c, r, adj_out(c, r), adj_in(c, r), nC, epC, build);
-    const int64_t nrec = rd_cnt(c, K_REC);
+    // node and children records (they need only the parents), so that one
+    // read returns both record counts
+    c.ndx.reserve(2 * (int64_t)nC + 2, c.s);
+    c.ndko.reserve(2 * (int64_t)nC + 2, c.s);
+    c.ndki.reserve(2 * (int64_t)nC + 2, c.s);
+    c.crk.reserve(2 * (int64_t)nC + 2, c.s);
+    c.crv.reserve(2 * (int64_t)nC + 2, c.s);
+    {
+      ZeroSpans z;
+      z.mask = cnt_bit(K_NREC) | cnt_bit(K_CREC);
+      zero_many(c, z);
+    }
+    k_emit_nodes<<<grid_for(nC, TPB), TPB, 0, c.s>>>(c.lC.p, c.dcnt + K_C, L.par.p, c.par_old.p, L.kout.p,
+                                                     kin_of(c, r), c.bits, c.ndx.p, c.ndko.p, c.ndki.p,
+                                                     c.dcnt + K_NREC, c.crk.p, c.crv.p, c.dcnt + K_CREC);
+    CKL("k_emit_nodes");
+    int32_t nrec32 = 0, ncr32 = 0;
+    {
+      const HostRead rr[2] = {{c.dcnt + K_REC, &nrec32, sizeof(int32_t)}, {c.dcnt + K_CREC, &ncr32, sizeof(int32_t)}};
+      host_read(c, rr, 2);
+    }
+    const int64_t nrec = nrec32, ncr = ncr32;
     if (nrec > c.rk2.cap) ldl_throw(LDL_E_INVALID, "internal: aggregate records exceed their bound");
     sub_end(c, SU_AGG_EMIT);
     sub_begin(c);
@@ -1303,19 +1329,6 @@ void aggregate(ldl_ctx& c, int r, int32_t epD, int32_t epC, int32_t epA_next, bo
     c.res.agg_records += nr;
     sub_end(c, SU_AGG_SORT);
     sub_begin(c);
-    // node and children records
-    c.ndx.reserve(2 * (int64_t)nC + 2, c.s);
-    c.ndko.reserve(2 * (int64_t)nC + 2, c.s);
-    c.ndki.reserve(2 * (int64_t)nC + 2, c.s);
-    c.crk.reserve(2 * (int64_t)nC + 2, c.s);
-    c.crv.reserve(2 * (int64_t)nC + 2, c.s);
-    zero_cnt(c, K_NREC);
-    zero_cnt(c, K_CREC);
-    k_emit_nodes<<<grid_for(nC, TPB), TPB, 0, c.s>>>(c.lC.p, c.dcnt + K_C, L.par.p, c.par_old.p, L.kout.p,
-                                                     kin_of(c, r), c.bits, c.ndx.p, c.ndko.p, c.ndki.p,
-                                                     c.dcnt + K_NREC, c.crk.p, c.crv.p, c.dcnt + K_CREC);
-    CKL("k_emit_nodes");
-    const int64_t ncr = rd_cnt(c, K_CREC);
     sort_pairs(c.crk, c.crv, c.tk, c.tv, ncr, 2 * c.bits, c.P, c.s);
     // keep the level r+1 record keys for NextFrontier
     c.fk.reserve(nr + 1, c.s);
@@ -1429,16 +1442,12 @@ int32_t alive_list(ldl_ctx& c, int r, int32_t* list, int idx) {
   return rd_cnt(c, idx);
 }
 
-int32_t changed_labels(ldl_ctx& c, int32_t epCh) {
-  (void)epCh;
-  const int32_t n = rd_cnt(c, K_CH);
+void changed_labels_launch(ldl_ctx& c) {
+  // strides over the candidates' device count with a grid bounded by the node count
   zero_cnt(c, K_CHG);
-  if (n > 0) {
-    k_changed_final<<<grid_for(n, TPB), TPB, 0, c.s>>>(c.lCh.p, c.dcnt + K_CH, c.lv[0].lab.p, c.lab_before.p,
-                                                       c.lChg.p, c.dcnt + K_CHG);
-    CKL("k_changed_final");
-  }
-  return rd_cnt(c, K_CHG);
+  k_changed_final<<<grid_for(c.n, TPB, 4), TPB, 0, c.s>>>(c.lCh.p, c.dcnt + K_CH, c.lv[0].lab.p, c.lab_before.p,
+                                                          c.lChg.p, c.dcnt + K_CHG);
+  CKL("k_changed_final");
 }
 
 void upload_graph(ldl_ctx& c, int64_t nnz, const int64_t* row_ptr, const int32_t* col, const int32_t* w) {

@@ -49,12 +49,15 @@ int64_t ingest(ldl_ctx& c, const ldl_update* upd, int64_t count, int on_device, 
 // the parent chain; marks InitFrontier in the A lists (epA per level).
 void repair_batch(ldl_ctx& c, int64_t na, const int32_t* epA, int32_t epT, int64_t dm);
 void pending_reset(ldl_ctx& c);
-void flush_level(ldl_ctx& c, int q);
-void pushdown(ldl_ctx& c, int r, int32_t epCh);
+// known: the level's pending record count when the caller has read it, else -1
+void flush_level(ldl_ctx& c, int q, int64_t known = -1);
+// moved_ub: an upper bound of the level's moved nodes (0 when none moved)
+void pushdown(ldl_ctx& c, int r, int32_t epCh, int64_t moved_ub);
 int32_t dissolve_all(ldl_ctx& c, int r, int32_t epD);
 int32_t split(ldl_ctx& c, int r, int32_t epD, int32_t epX);
 // the listed level-r nodes that are singleton refined communities -> out
-int32_t singletons_of(ldl_ctx& c, int r, const int32_t* list, int idx_n, int64_t n_hint, int32_t* out, int idx_out);
+// (their count stays on the device, at dcnt[idx_out])
+void singletons_of(ldl_ctx& c, int r, const int32_t* list, int idx_n, int64_t n_hint, int32_t* out, int idx_out);
 // nD = |D| (list lD), the nodes whose refined community changed.
 void aggregate(ldl_ctx& c, int r, int32_t epD, int32_t epC, int32_t epA_next, bool build, int32_t nD);
 // context set-up and tear-down (ldl.cu)
@@ -68,5 +71,7 @@ void level_alloc(ldl_ctx& c, int r);
 void level_free(ldl_ctx& c, int r);
 int32_t alive_list(ldl_ctx& c, int r, int32_t* list, int idx);
 void reset_par(ldl_ctx& c, int r, int32_t nD);
-int32_t changed_labels(ldl_ctx& c, int32_t epCh);
+// the level-0 nodes whose label differs from the batch's start -> lChg
+// (count at dcnt[K_CHG], read by the caller)
+void changed_labels_launch(ldl_ctx& c);
 void gather_labels(ldl_ctx& c, const int32_t* ids, int32_t k, int32_t* out);

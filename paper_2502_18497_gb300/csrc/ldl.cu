@@ -100,6 +100,14 @@ __global__ void k_publish(PubReq q, unsigned char* payload, int64_t* seq_word, i
 }
 
 __global__ void k_set_i32(int32_t* p, int32_t v) { *p = v; }
+
+// clears the counters named by the mask and up to ZERO_SPANS spans of 64-bit words
+__global__ void k_zero(int32_t* dcnt, ZeroSpans z) {
+  const int t = threadIdx.x;
+  if (t < K_COUNT && ((z.mask >> t) & 1ull)) dcnt[t] = 0;
+  for (int i = 0; i < ZERO_SPANS; ++i)
+    if (z.p[i] && t < z.nw[i]) z.p[i][t] = 0;
+}
 }  // namespace
 
 void host_read(ldl_ctx& c, const HostRead* r, int n) {
@@ -143,6 +151,13 @@ int32_t rd_cnt(ldl_ctx& c, int idx) {
 }
 
 void zero_cnt(ldl_ctx& c, int idx) { CK(cudaMemsetAsync(c.dcnt + idx, 0, sizeof(int32_t), c.s)); }
+
+void zero_many(ldl_ctx& c, const ZeroSpans& z) {
+  for (int i = 0; i < ZERO_SPANS; ++i)
+    if (z.nw[i] < 0 || z.nw[i] > K_COUNT) ldl_throw(LDL_E_INVALID, "internal: zero span too long");
+  k_zero<<<1, K_COUNT, 0, c.s>>>(c.dcnt, z);
+  CKL("k_zero");
+}
 
 void set_cnt(ldl_ctx& c, int idx, int32_t v) {
   k_set_i32<<<1, 1, 0, c.s>>>(c.dcnt + idx, v);
@@ -263,9 +278,12 @@ void free_all(ldl_ctx& c) {
 // The local-move loop of Algorithm 1 at level r.  Precondition: lU holds U = A^r, and
 // lUstar / stU (epoch epU) hold U*.  Moved nodes go to lMv (epMv) and, at
 // level 0, to lM0 (epM0).
-static void move_loop(ldl_ctx& c, int r, int rounds, int32_t epU, int32_t epMv, int32_t epM0, int32_t epCh,
-                      int32_t nU) {
-  // nU = |U| on entry; later rounds take it from the end of the previous one
+static int64_t move_loop(ldl_ctx& c, int r, int rounds, int32_t epU, int32_t epMv, int32_t epM0, int32_t epCh,
+                         int32_t nU) {
+  // nU = |U| on entry; later rounds take it from the end of the previous one.
+  // Returns the committed moves, an upper bound of the distinct moved nodes
+  // (lMv), which is empty exactly when it is 0.
+  int64_t committed = 0;
   const i128 Q0 = qnum(c);
   const int64_t ainv = c.prm.alpha_inv, binv = c.prm.beta_inv;
   for (int j = 0; j < rounds; ++j) {
@@ -275,15 +293,16 @@ static void move_loop(ldl_ctx& c, int r, int rounds, int32_t epU, int32_t epMv, 
     const int32_t epS = c.next_epoch();
     zero_cnt(c, K_S);
     expand_set(c, r, c.lU.p, K_U, c.stS.p, epS, c.lS.p, K_S, nU);
-    const int32_t nS = rd_cnt(c, K_S);
     stage_end(c, ST_EXPAND);
+    // |S| stays on the device: the sweep's kernels stride over it (n bounds
+    // their grids) and it comes back with the decoupling result for the β test
     stage_begin(c);
-    sweep(c, r, 0, c.lS.p, K_S, nS);
+    sweep(c, r, 0, c.lS.p, K_S, c.n);
     stage_end(c, ST_BEST);
     stage_begin(c);
-    const DecoupleOut dd = decouple(c);
+    const DecoupleOut dd = decouple(c, K_S);
     stage_end(c, ST_DECOUPLE);
-    const int32_t nc = dd.nc, nb = dd.nb;
+    const int32_t nc = dd.nc, nb = dd.nb, nS = dd.extra;
     if (nc == 0) break;
     c.res.rejected += nc - nb;
     if (nb == 0) break;
@@ -307,6 +326,7 @@ static void move_loop(ldl_ctx& c, int r, int rounds, int32_t epU, int32_t epMv, 
     c.E += co.de;
     c.Psum += co.dp;
     c.res.moves += nb;
+    committed += nb;
     mark_moved(c, r, nb, epMv, epM0);
     stage_end(c, ST_COMMIT);
     stage_begin(c);
@@ -316,6 +336,7 @@ static void move_loop(ldl_ctx& c, int r, int rounds, int32_t epU, int32_t epMv, 
     if (co.dq * (i128)ainv < Q0) break;
     if ((int64_t)nb * binv < (int64_t)nS) break;
   }
+  return committed;
 }
 
 // The refinement loop of Algorithm 1 at level r over the dissolved set lD (epoch epD).
@@ -371,8 +392,8 @@ static void static_build(ldl_ctx& c) {
     zero_cnt(c, K_MV);
     zero_cnt(c, K_M0);
     zero_cnt(c, K_CH);
-    move_loop(c, r, c.prm.M_static, epU, epMv, epM0, epCh, nU);
-    if (r > 0) pushdown(c, r, epCh);
+    const int64_t mv = move_loop(c, r, c.prm.M_static, epU, epMv, epM0, epCh, nU);
+    if (r > 0) pushdown(c, r, epCh, mv);
     if (r == L) break;
     level_alloc(c, r + 1);
     c.T = r + 1;
@@ -529,12 +550,21 @@ static void apply_batch(ldl_ctx& c, const ldl_update* upd, int64_t count, int on
     const i128 Qpass = qnum(c);
     const int32_t epM0 = c.next_epoch();
     zero_cnt(c, K_M0);
+    int32_t nM0 = -1;  // |level-0 moves of the pass|, final once level 0 is done
     for (int r = 0; r <= T; ++r) {
       // |A^r| stays on the device: the filter strides over it with a grid of
-      // two blocks per SM, and one read returns |U|
+      // two blocks per SM, and one read returns |U|, the level's pending
+      // record count for its flush and, from level 1 on, |M0|
       zero_cnt(c, K_U);
       filter_alive(c, r, c.lv[r].lA.p, K_A0 + r, c.lU.p, K_U, std::min<int64_t>(c.n, (int64_t)device_sms() * 512));
-      const int32_t nU = rd_cnt(c, K_U);
+      int32_t nU = 0, nP = 0, m0 = 0;
+      {
+        const HostRead rr[3] = {{c.dcnt + K_U, &nU, sizeof(int32_t)},
+                                {c.dcnt + K_PEND0 + r, &nP, sizeof(int32_t)},
+                                {c.dcnt + K_M0, &m0, sizeof(int32_t)}};
+        host_read(c, rr, r > 0 ? 3 : 2);
+        if (r > 0) nM0 = m0;
+      }
       if (nU == 0) continue;
       if (r < 8) c.res.frontier_nodes[r] += nU;
       const int32_t epU = c.next_epoch();
@@ -543,12 +573,12 @@ static void apply_batch(ldl_ctx& c, const ldl_update* upd, int64_t count, int on
       const int32_t epMv = c.next_epoch();
       zero_cnt(c, K_MV);
       stage_begin(c);
-      flush_level(c, r);  // the level's weights are read from here on
+      flush_level(c, r, nP);  // the level's weights are read from here on
       stage_end(c, ST_AGG);
-      move_loop(c, r, c.prm.M, epU, epMv, epM0, epCh, nU);
+      const int64_t mv = move_loop(c, r, c.prm.M, epU, epMv, epM0, epCh, nU);
       if (r > 0) {
         stage_begin(c);
-        pushdown(c, r, epCh);
+        pushdown(c, r, epCh, mv);
         stage_end(c, ST_PUSH);
       }
       if (r < T) {
@@ -568,23 +598,49 @@ static void apply_batch(ldl_ctx& c, const ldl_update* upd, int64_t count, int on
       }
     }
     // frontiers of the next pass: A^0 = Expand_0(level-0 moves), others empty
-    const int32_t nM0 = rd_cnt(c, K_M0);
+    if (nM0 < 0) nM0 = rd_cnt(c, K_M0);
     for (int r = 0; r <= T; ++r) {
       epA[r] = c.next_epoch();
       zero_cnt(c, K_A0 + r);
     }
-    if (nM0 > 0) expand_set(c, 0, c.lM0.p, K_M0, c.lv[0].stA.p, epA[0], c.lv[0].lA.p, K_A0, nM0);
-    if (rd_cnt(c, K_A0) == 0) break;
+    // the expansion holds the moved nodes themselves, so A^0 is empty
+    // exactly when no level-0 node moved
+    if (nM0 == 0) break;
+    expand_set(c, 0, c.lM0.p, K_M0, c.lv[0].stA.p, epA[0], c.lv[0].lA.p, K_A0, nM0);
     if ((qnum(c) - Qpass) * (i128)ainv < Qpass) break;
   }
   stage_begin(c);
-  for (int r = 1; r <= T; ++r) flush_level(c, r);
+  {
+    // the pending counts of every level above 0 in one read (K_PEND0 + r are
+    // adjacent; a flush changes no other level's list)
+    int32_t np[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    if (T >= 1) {
+      const HostRead rr{c.dcnt + K_PEND0 + 1, np, (int32_t)(sizeof(int32_t) * (size_t)std::min(T, 7))};
+      host_read(c, &rr, 1);
+    }
+    for (int r = 1; r <= T; ++r) flush_level(c, r, np[r - 1]);
+  }
   stage_end(c, ST_AGG);
-  c.res.n_changed = changed_labels(c, epCh);
-  if (rd_cnt(c, K_ERR)) ldl_throw(LDL_E_INVALID, "internal: a new supernode already had a parent, or records exceeded their bound");
+  changed_labels_launch(c);
+  // one read: changed labels, the internal error flag, entries scanned and
+  // the look-back scans' error flag
+  int32_t nchg = 0, err = 0, scan_bad = 0;
+  int32_t* scan_flag = scan_error_flag(c.P);
+  {
+    const HostRead rr[4] = {{c.dcnt + K_CHG, &nchg, sizeof(int32_t)},
+                            {c.dcnt + K_ERR, &err, sizeof(int32_t)},
+                            {&c.d_sc->scanned, &c.res.edges_scanned, sizeof(int64_t)},
+                            {scan_flag, &scan_bad, sizeof(int32_t)}};
+    host_read(c, rr, scan_flag ? 4 : 3);
+  }
+  c.res.n_changed = nchg;
   c.res.host_syncs = c.syncs;
-  CK(cudaMemcpyAsync(&c.res.edges_scanned, &c.d_sc->scanned, sizeof(int64_t), cudaMemcpyDeviceToHost, c.s));
-  check_scan_wait(c);
+  CK(cudaStreamSynchronize(c.s));
+  if (err) ldl_throw(LDL_E_INVALID, "internal: a new supernode already had a parent, or records exceeded their bound");
+  if (scan_bad) {
+    CK(cudaMemsetAsync(scan_flag, 0, sizeof(int32_t), c.s));
+    ldl_throw(LDL_E_TIMEOUT, "a device scan's bounded wait gave up");
+  }
 }
 
 // Reads the look-back scans' error flag (and synchronises): a bounded wait

@@ -1333,14 +1333,14 @@ static void sweep_t(ldl_ctx& c, int r, Adj<WT> out, Adj<WT> in, const int32_t* l
   A.ncand = c.dcnt + K_CAND;
   A.scanned = &c.d_sc->scanned;
   A.stats = c.d_sc;
-  zero_cnt(c, K_CAND);
-  zero_cnt(c, K_TINY);
-  zero_cnt(c, K_SMALL);
-  zero_cnt(c, K_MID);
-  zero_cnt(c, K_MID2);
-  zero_cnt(c, K_CLU);
-  zero_cnt(c, K_LARGE);
-  CK(cudaMemsetAsync(&c.d_sc->need, 0, sizeof(int64_t), c.s));
+  {
+    ZeroSpans z;
+    z.mask = cnt_bit(K_CAND) | cnt_bit(K_TINY) | cnt_bit(K_SMALL) | cnt_bit(K_MID) | cnt_bit(K_MID2) |
+             cnt_bit(K_CLU) | cnt_bit(K_LARGE);
+    z.p[0] = &c.d_sc->need;
+    z.nw[0] = 1;
+    zero_many(c, z);
+  }
   k_bin<WT><<<grid_for(n_hint, TPB), TPB, 0, c.s>>>(out, in, c.directed, list, c.dcnt + idx_n, c.binT.p,
                                                      c.dcnt + K_TINY, c.binS.p, c.dcnt + K_SMALL, c.binM.p,
                                                      c.dcnt + K_MID, c.binM2.p, c.dcnt + K_MID2, c.binC.p,
@@ -1536,7 +1536,17 @@ DecoupleOut decouple(ldl_ctx& c, int extra) {
 void commit_move(ldl_ctx& c, int r, int32_t nb, int32_t epB, int32_t epT, int32_t epCh) {
   LevelState& L = c.lv[r];
   const int g = grid_for(nb, TPB);
-  zero_cnt(c, K_T);
+  {
+    // K_T, and the mini-batch's ΔQ numerator, Δ sum K_out K_in and Δ sum e_C
+    static_assert(offsetof(DevScalars, dp) == offsetof(DevScalars, dq) + sizeof(I128), "adjacent scalars");
+    ZeroSpans z;
+    z.mask = cnt_bit(K_T);
+    z.p[0] = (int64_t*)&c.d_sc->dq;
+    z.nw[0] = (int32_t)(2 * sizeof(I128) / sizeof(int64_t));
+    z.p[1] = &c.d_sc->de;
+    z.nw[1] = 1;
+    zero_many(c, z);
+  }
   k_commit_mark<<<g, TPB, 0, c.s>>>(nb, c.bv.p, c.bsrc.p, c.bdst.p, L.lab.p, c.oldlab.p, c.stB.p, epB, c.stT.p, epT,
                                     c.lT.p, c.dcnt + K_T, c.stCh.p, epCh, c.lCh.p, c.dcnt + K_CH, c.lab_before.p,
                                     r == 0);
@@ -1558,9 +1568,6 @@ void commit_move(ldl_ctx& c, int r, int32_t nb, int32_t epB, int32_t epT, int32_
     k_commit_e<int64_t><<<gw, TPB, 0, c.s>>>(o, i, m, c.bsrc.p, c.bdst.p, L.lab.p, c.oldlab.p, c.stB.p, epB, c.e.p);
   }
   CKL("k_commit_e");
-  CK(cudaMemsetAsync(&c.d_sc->dq, 0, sizeof(I128), c.s));
-  CK(cudaMemsetAsync(&c.d_sc->dp, 0, sizeof(I128), c.s));
-  CK(cudaMemsetAsync(&c.d_sc->de, 0, sizeof(int64_t), c.s));
   k_commit_dq<<<grid_for(2 * (int64_t)nb, TPB), TPB, 0, c.s>>>(c.lT.p, c.dcnt + K_T, c.Kout.p, Kin_of(c), c.e.p,
                                                                c.snapKo.p, c.snapKi.p, c.snapE.p, c.m,
                                                                c.prm.gamma_num, c.prm.gamma_den, c.d_sc);
