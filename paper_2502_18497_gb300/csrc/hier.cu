@@ -1250,17 +1250,21 @@ int32_t split(ldl_ctx& c, int r, int32_t epD, int32_t epX) {
   return renamed ? rd_cnt(c, K_D) : nleft;
 }
 
+// Row entries of the changed nodes (list lC, count on the device, at most
+// n_hint) into need (out-rows) and need2 (in-rows).
 template <class WT>
-static void emit_records(ldl_ctx& c, int r, Adj<WT> out, Adj<WT> in, int32_t nC, int32_t epC, bool build) {
+static void deg_sum(ldl_ctx& c, Adj<WT> out, Adj<WT> in, int64_t n_hint) {
   static_assert(offsetof(DevScalars, need2) == offsetof(DevScalars, need) + 8, "adjacent accumulators");
   CK(cudaMemsetAsync(&c.d_sc->need, 0, 2 * sizeof(int64_t), c.s));
-  k_deg_sum<WT><<<grid_for(nC, TPB), TPB, 0, c.s>>>(out, in, c.lC.p, c.dcnt + K_C, &c.d_sc->need, &c.d_sc->need2);
+  k_deg_sum<WT><<<grid_for(n_hint, TPB), TPB, 0, c.s>>>(out, in, c.lC.p, c.dcnt + K_C, &c.d_sc->need,
+                                                        &c.d_sc->need2);
   CKL("k_deg_sum");
-  int64_t deg[2] = {0, 0};  // out-row and in-row entries of the changed nodes
-  {
-    const HostRead r{&c.d_sc->need, deg, 2 * sizeof(int64_t)};
-    host_read(c, &r, 1);
-  }
+}
+
+// deg: out-row and in-row entries of the changed nodes (deg_sum)
+template <class WT>
+static void emit_records(ldl_ctx& c, int r, Adj<WT> out, Adj<WT> in, int32_t nC, int32_t epC, bool build,
+                         const int64_t (&deg)[2]) {
   // at most a subtract and an add record per visited entry; in the static
   // build no node had a parent (no subtract records) and every node is
   // changed (no in-row records), so one record per out-row entry
@@ -1286,15 +1290,21 @@ void aggregate(ldl_ctx& c, int r, int32_t epD, int32_t epC, int32_t epA_next, bo
   k_changed<<<grid_for(nD, TPB), TPB, 0, c.s>>>(c.lD.p, c.dcnt + K_D, L.par.p, c.par_old.p, c.stC.p, epC, c.lC.p,
                                                 c.dcnt + K_C);
   CKL("k_changed");
-  int32_t nC = 0, nUs = 0;  // changed nodes, and |U*| for the relabelling below: one read
+  // the changed nodes' row entries (lC is a subset of lD, so nD bounds the
+  // launch); one read returns them with |C| and |U*| (for the relabelling)
+  if (r == 0) deg_sum<int32_t>(c, adj_out0(c), adj_in0(c), nD);
+  else deg_sum<int64_t>(c, adj_out(c, r), adj_in(c, r), nD);
+  int32_t nC = 0, nUs = 0;
+  int64_t deg[2] = {0, 0};
   {
-    const HostRead rr[2] = {{c.dcnt + K_C, &nC, sizeof(int32_t)}, {c.dcnt + K_USTAR, &nUs, sizeof(int32_t)}};
-    host_read(c, rr, 2);
+    const HostRead rr[3] = {{c.dcnt + K_C, &nC, sizeof(int32_t)}, {c.dcnt + K_USTAR, &nUs, sizeof(int32_t)},
+                            {&c.d_sc->need, deg, 2 * sizeof(int64_t)}};
+    host_read(c, rr, 3);
   }
   int64_t nr = 0;
   if (nC > 0) {
-    if (r == 0) emit_records<int32_t>(c, r, adj_out0(c), adj_in0(c), nC, epC, build);
-    else emit_records<int64_t>(c, r, adj_out(c, r), adj_in(c, r), nC, epC, build);
+    if (r == 0) emit_records<int32_t>(c, r, adj_out0(c), adj_in0(c), nC, epC, build, deg);
+    else emit_records<int64_t>(c, r, adj_out(c, r), adj_in(c, r), nC, epC, build, deg);
     // node and children records (they need only the parents), so that one
     // read returns both record counts
     c.ndx.reserve(2 * (int64_t)nC + 2, c.s);

@@ -23,8 +23,9 @@ void filter_alive(ldl_ctx& c, int r, const int32_t* list, int idx_n, int32_t* ol
 void union_into(ldl_ctx& c, const int32_t* list, int idx_n, int32_t* stamp, int32_t ep, int32_t* olist, int idx_out,
                 int64_t n_hint);
 // BestMove (mode 0) / BestRef (mode 1) over the listed nodes; the candidates
-// and their count (counter K_CAND) stay on the device.
-void sweep(ldl_ctx& c, int r, int mode, const int32_t* list, int idx_n, int64_t n_hint);
+// and their count (counter K_CAND) stay on the device.  Returns the list's
+// length (dcnt[idx_n]), read with the sweep's bin counts.
+int32_t sweep(ldl_ctx& c, int r, int mode, const int32_t* list, int idx_n, int64_t n_hint);
 // Decoupling filter over the last sweep's candidates: returns their number
 // and the number accepted (the accepted moves are in bv / bsrc / bdst), and
 // counter `extra` (when >= 0) read in the same host wait.

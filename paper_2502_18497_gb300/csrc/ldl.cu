@@ -295,14 +295,14 @@ static int64_t move_loop(ldl_ctx& c, int r, int rounds, int32_t epU, int32_t epM
     expand_set(c, r, c.lU.p, K_U, c.stS.p, epS, c.lS.p, K_S, nU);
     stage_end(c, ST_EXPAND);
     // |S| stays on the device: the sweep's kernels stride over it (n bounds
-    // their grids) and it comes back with the decoupling result for the β test
+    // their grids) and it comes back with the sweep's bin counts (β test)
     stage_begin(c);
-    sweep(c, r, 0, c.lS.p, K_S, c.n);
+    const int32_t nS = sweep(c, r, 0, c.lS.p, K_S, c.n);
     stage_end(c, ST_BEST);
     stage_begin(c);
-    const DecoupleOut dd = decouple(c, K_S);
+    const DecoupleOut dd = decouple(c);
     stage_end(c, ST_DECOUPLE);
-    const int32_t nc = dd.nc, nb = dd.nb, nS = dd.extra;
+    const int32_t nc = dd.nc, nb = dd.nb;
     if (nc == 0) break;
     c.res.rejected += nc - nb;
     if (nb == 0) break;
@@ -351,15 +351,15 @@ static int64_t refine_loop(ldl_ctx& c, int r, int rounds, int32_t epD, int32_t n
   const int64_t binv = c.prm.beta_inv;
   for (int j = 0; j < rounds; ++j) {
     // R is a subset of D, so nD bounds the sweep's launch; |R| comes back with
-    // the decoupling result (an empty R gives no candidates and ends the loop)
+    // the sweep's bin counts (an empty R ends the loop before any filter)
     c.res.rounds++;
-    sweep(c, r, 1, R, iR, nD);
-    const DecoupleOut dd = decouple(c, iR);
-    const int32_t nc = dd.nc, nb = dd.nb, nR = dd.extra;
+    const int32_t nR = sweep(c, r, 1, R, iR, nD);
     if (nR == 0) {
       c.res.rounds--;
       break;
     }
+    const DecoupleOut dd = decouple(c);
+    const int32_t nc = dd.nc, nb = dd.nb;
     if (nc == 0) break;
     c.res.rejected += nc - nb;
     if (nb == 0) break;

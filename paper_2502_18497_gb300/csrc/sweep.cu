@@ -981,11 +981,23 @@ __global__ void __launch_bounds__(TPB) k_dec_grid(int32_t nc, int32_t* cst, cons
 constexpr int DEC_SMALL = 8192;
 constexpr int DEC_THREADS = 1024;
 
-__global__ void __launch_bounds__(DEC_THREADS) k_dec_block(const int32_t* ncp, int32_t* cst, const int32_t* cv,
-                                                           const int32_t* src, const int32_t* dst,
-                                                           const int64_t* ghi, const uint64_t* glo, int32_t* role,
-                                                           int32_t* best, int32_t* bv, int32_t* bsrc, int32_t* bdst,
-                                                           int32_t* nb, int32_t* stat) {
+constexpr int DEC_PER = DEC_SMALL / DEC_THREADS;  // candidates per thread
+static_assert(DEC_PER * DEC_THREADS == DEC_SMALL, "whole candidates per thread");
+// the candidates' gains and nodes, staged in shared memory for the claims
+constexpr size_t DEC_SMEM = (size_t)DEC_SMALL * (sizeof(int64_t) + sizeof(uint64_t) + sizeof(int32_t));
+
+// The same rounds in one block for up to DEC_SMALL candidates: thread tid
+// owns candidates tid + j * DEC_THREADS, whose communities and state stay in
+// registers; the gains and nodes that claims compare sit in shared memory.
+__global__ void __launch_bounds__(DEC_THREADS) k_dec_block(const int32_t* ncp, const int32_t* cv, const int32_t* src,
+                                                           const int32_t* dst, const int64_t* ghi,
+                                                           const uint64_t* glo, int32_t* role, int32_t* best,
+                                                           int32_t* bv, int32_t* bsrc, int32_t* bdst, int32_t* nb,
+                                                           int32_t* stat) {
+  extern __shared__ unsigned char dsm[];
+  int64_t* sghi = (int64_t*)dsm;
+  uint64_t* sglo = (uint64_t*)(dsm + sizeof(int64_t) * DEC_SMALL);
+  int32_t* scv = (int32_t*)(dsm + (sizeof(int64_t) + sizeof(uint64_t)) * DEC_SMALL);
   __shared__ int32_t left;
   const int tid = threadIdx.x;
   const int32_t nc = *ncp;
@@ -993,36 +1005,57 @@ __global__ void __launch_bounds__(DEC_THREADS) k_dec_block(const int32_t* ncp, i
     if (tid == 0) *stat = -2;
     return;
   }
-  for (int32_t i = tid; i < nc; i += DEC_THREADS) cst[i] = 0;
+  // state per owned candidate: 0 undecided, 1 accepted, 2 rejected, 3 accepted
+  // this round (roles pending), 4 no candidate
+  int32_t sa[DEC_PER], sb[DEC_PER], st[DEC_PER];
+#pragma unroll
+  for (int j = 0; j < DEC_PER; ++j) {
+    const int32_t i = tid + j * DEC_THREADS;
+    const bool have = i < nc;
+    st[j] = have ? 0 : 4;
+    sa[j] = have ? src[i] : 0;
+    sb[j] = have ? dst[i] : 0;
+    if (have) {
+      sghi[i] = ghi[i];
+      sglo[i] = glo[i];
+      scv[i] = cv[i];
+    }
+  }
   __syncthreads();
   int32_t rounds = 0;
   bool ok = true;
   for (;;) {
-    for (int32_t i = tid; i < nc; i += DEC_THREADS) {
-      if (cst[i] != 0) continue;
-      if (role[src[i]] == 0) claim(best, src[i], i, ghi, glo, cv);
-      if (role[dst[i]] == 0) claim(best, dst[i], i, ghi, glo, cv);
+#pragma unroll
+    for (int j = 0; j < DEC_PER; ++j) {
+      if (st[j] != 0) continue;
+      const int32_t i = tid + j * DEC_THREADS;
+      if (role[sa[j]] == 0) claim(best, sa[j], i, sghi, sglo, scv);
+      if (role[sb[j]] == 0) claim(best, sb[j], i, sghi, sglo, scv);
     }
     if (tid == 0) left = 0;
     __syncthreads();
     int32_t mine = 0;
-    for (int32_t i = tid; i < nc; i += DEC_THREADS) {
-      if (cst[i] != 0) continue;
-      const int32_t ra = role[src[i]], rb = role[dst[i]];
-      const bool da = ra != 0 || best[src[i]] == i;
-      const bool db = rb != 0 || best[dst[i]] == i;
-      if (da && db) cst[i] = (ra != 2 && rb != 1) ? 3 : 2;
+#pragma unroll
+    for (int j = 0; j < DEC_PER; ++j) {
+      if (st[j] != 0) continue;
+      const int32_t i = tid + j * DEC_THREADS;
+      const int32_t ra = role[sa[j]], rb = role[sb[j]];
+      const bool da = ra != 0 || best[sa[j]] == i;
+      const bool db = rb != 0 || best[sb[j]] == i;
+      if (da && db) st[j] = (ra != 2 && rb != 1) ? 3 : 2;
       else ++mine;
     }
     if (mine) atomicAdd(&left, mine);
     __syncthreads();
-    for (int32_t i = tid; i < nc; i += DEC_THREADS) {
-      best[src[i]] = -1;
-      best[dst[i]] = -1;
-      if (cst[i] == 3) {
-        role[src[i]] = 1;
-        role[dst[i]] = 2;
-        cst[i] = 1;
+#pragma unroll
+    for (int j = 0; j < DEC_PER; ++j) {
+      if (st[j] == 4) continue;
+      best[sa[j]] = -1;
+      best[sb[j]] = -1;
+      if (st[j] == 3) {
+        role[sa[j]] = 1;
+        role[sb[j]] = 2;
+        st[j] = 1;
       }
     }
     ++rounds;
@@ -1035,14 +1068,16 @@ __global__ void __launch_bounds__(DEC_THREADS) k_dec_block(const int32_t* ncp, i
       break;
     }
   }
-  for (int32_t i = tid; i < nc; i += DEC_THREADS) {
-    role[src[i]] = 0;
-    role[dst[i]] = 0;
-    if (cst[i] == 1) {
+#pragma unroll
+  for (int j = 0; j < DEC_PER; ++j) {
+    if (st[j] == 4) continue;
+    role[sa[j]] = 0;
+    role[sb[j]] = 0;
+    if (st[j] == 1) {
       const int32_t p = atomicAdd(nb, 1);
-      bv[p] = cv[i];
-      bsrc[p] = src[i];
-      bdst[p] = dst[i];
+      bv[p] = scv[tid + j * DEC_THREADS];
+      bsrc[p] = sa[j];
+      bdst[p] = sb[j];
     }
   }
   if (tid == 0) *stat = ok ? rounds : -1;
@@ -1305,7 +1340,8 @@ static cudaEvent_t* kstats_events(ldl_ctx& c) {
 }
 
 template <class WT, int MODE>
-static void sweep_t(ldl_ctx& c, int r, Adj<WT> out, Adj<WT> in, const int32_t* list, int idx_n, int64_t n_hint) {
+static int32_t sweep_t(ldl_ctx& c, int r, Adj<WT> out, Adj<WT> in, const int32_t* list, int idx_n,
+                       int64_t n_hint) {
   LevelState& L = c.lv[r];
   SweepArgs<WT> A;
   A.out = out;
@@ -1364,12 +1400,14 @@ static void sweep_t(ldl_ctx& c, int r, Adj<WT> out, Adj<WT> in, const int32_t* l
     CKL("k_sweep_cluster");
   }
   if (kev) CK(cudaEventRecord(kev[5], c.s));
-  // counters K_SMALL .. K_CLU in one read
+  // counters K_SMALL .. K_CLU, the hub tables' size and the list's length in one read
   int32_t cn[K_CLU - K_SMALL + 1];
   int64_t tab = 0;
+  int32_t nlist = 0;
   {
-    const HostRead rr[2] = {{c.dcnt + K_SMALL, cn, (int32_t)sizeof(cn)}, {&c.d_sc->need, &tab, sizeof(int64_t)}};
-    host_read(c, rr, 2);
+    const HostRead rr[3] = {{c.dcnt + K_SMALL, cn, (int32_t)sizeof(cn)}, {&c.d_sc->need, &tab, sizeof(int64_t)},
+                            {c.dcnt + idx_n, &nlist, sizeof(int32_t)}};
+    host_read(c, rr, 3);
   }
   const int32_t ct = cn[K_TINY - K_SMALL], cs = cn[0], cm = cn[K_MID - K_SMALL], cm2 = cn[K_MID2 - K_SMALL];
   const int32_t cc = cn[K_CLU - K_SMALL], ch = cn[K_LARGE - K_SMALL];
@@ -1466,20 +1504,20 @@ static void sweep_t(ldl_ctx& c, int r, Adj<WT> out, Adj<WT> in, const int32_t* l
     c.ks_launch[5] += ch > 0;
     c.ks_launch[6] += ch > 0 ? 3 : 0;  // evaluation, final reduction, clearing
   }
+  return nlist;
 }
 
 extern "C" void ldl_debug_hub_table_slots(int64_t slots) {
   g_hub_table_slots.store(slots > 0 ? slots : HUB_TABLE_SLOTS);
 }
 
-void sweep(ldl_ctx& c, int r, int mode, const int32_t* list, int idx_n, int64_t n_hint) {
+int32_t sweep(ldl_ctx& c, int r, int mode, const int32_t* list, int idx_n, int64_t n_hint) {
   if (r == 0) {
-    if (mode == 0) sweep_t<int32_t, 0>(c, r, adj_out0(c), adj_in0(c), list, idx_n, n_hint);
-    else sweep_t<int32_t, 1>(c, r, adj_out0(c), adj_in0(c), list, idx_n, n_hint);
-  } else {
-    if (mode == 0) sweep_t<int64_t, 0>(c, r, adj_out(c, r), adj_in(c, r), list, idx_n, n_hint);
-    else sweep_t<int64_t, 1>(c, r, adj_out(c, r), adj_in(c, r), list, idx_n, n_hint);
+    if (mode == 0) return sweep_t<int32_t, 0>(c, r, adj_out0(c), adj_in0(c), list, idx_n, n_hint);
+    return sweep_t<int32_t, 1>(c, r, adj_out0(c), adj_in0(c), list, idx_n, n_hint);
   }
+  if (mode == 0) return sweep_t<int64_t, 0>(c, r, adj_out(c, r), adj_in(c, r), list, idx_n, n_hint);
+  return sweep_t<int64_t, 1>(c, r, adj_out(c, r), adj_in(c, r), list, idx_n, n_hint);
 }
 
 DecoupleOut decouple(ldl_ctx& c, int extra) {
@@ -1488,9 +1526,10 @@ DecoupleOut decouple(ldl_ctx& c, int extra) {
   // filter's status (-2: too many candidates for one block).
   static_assert(K_B == K_CAND + 1 && K_UNDEC == K_CAND + 2, "adjacent counters");
   zero_cnt(c, K_B);
-  k_dec_block<<<1, DEC_THREADS, 0, c.s>>>(c.dcnt + K_CAND, c.cst.p, c.cv.p, c.csrc.p, c.cdst.p, c.cghi.p, c.cglo.p,
-                                          c.role.p, c.best.p, c.bv.p, c.bsrc.p, c.bdst.p, c.dcnt + K_B,
-                                          c.dcnt + K_UNDEC);
+  CK(cudaFuncSetAttribute(k_dec_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DEC_SMEM));
+  k_dec_block<<<1, DEC_THREADS, DEC_SMEM, c.s>>>(c.dcnt + K_CAND, c.cv.p, c.csrc.p, c.cdst.p, c.cghi.p, c.cglo.p,
+                                                 c.role.p, c.best.p, c.bv.p, c.bsrc.p, c.bdst.p, c.dcnt + K_B,
+                                                 c.dcnt + K_UNDEC);
   CKL("k_dec_block");
   int32_t out[3], ex = 0;
   {
