@@ -438,14 +438,63 @@ __device__ inline int32_t uf_find(int32_t* comp, int32_t x, bool halve) {
   return x;
 }
 
-// Connected components of the collected members over the arcs between two
-// remaining members of the same refined community, in one pass: a lock-free
-// union-find that always hooks the larger root under the smaller one (a
-// compare-and-swap that fails because another thread hooked first is
+// Joins the trees of u and y: always hooks the larger root under the smaller
+// one (a compare-and-swap that fails because another thread hooked first is
 // retried), so every component ends rooted at its lowest member.
+__device__ inline void uf_union(int32_t* comp, int32_t u, int32_t y) {
+  for (;;) {
+    const int32_t a = uf_find(comp, u, true), b = uf_find(comp, y, true);
+    if (a == b) return;
+    const int32_t hi = a > b ? a : b, lo = a > b ? b : a;
+    if (atomicCAS(&comp[hi], hi, lo) == hi) return;
+  }
+}
+
+// Connected components of the collected members over the arcs between two
+// remaining members of the same refined community, by a lock-free union-find
+// with neighbour sampling (the Afforest scheme of Sutton, Ben-Nun and Barak,
+// IPDPS 2018).  First every member is joined along at most UF_SAMPLE of the
+// qualifying arcs among the first 32 entries of its rows (k_uf_sample); in a
+// community that is still connected this already puts most members into the
+// seed node's tree.  Then k_uf walks all arcs of the members that are not (yet)
+// in their community seed's tree.  The components are exact: every arc with an
+// endpoint outside the seed's tree is joined from that endpoint's side (both
+// rows of a member are walked, so the arc is seen from either end), and an arc
+// whose two endpoints were both in the seed's tree when they were checked
+// joins nothing new, because trees only ever merge.
+constexpr int UF_SAMPLE = 2;
+
 template <class WT>
-__global__ void k_uf(Adj<WT> out, Adj<WT> in, ChunkMap m, const int32_t* par, const int32_t* stL, int32_t epL,
-                     int32_t* comp) {
+__global__ void k_uf_sample(Adj<WT> out, Adj<WT> in, int directed, const int32_t* lG, const int32_t* nG,
+                            const int32_t* par, const int32_t* stL, int32_t epL, int32_t* comp) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int32_t n = *nG;
+  for (int64_t t = warp; t < n; t += nw) {
+    const int32_t u = lG[t];
+    const int32_t X = par[u];
+    int taken = 0;  // warp-uniform
+    for (int side = 0; side < (directed ? 2 : 1) && taken < UF_SAMPLE; ++side) {
+      const Adj<WT>& A = side ? in : out;
+      const int32_t l = A.len[u];
+      bool q = false;
+      int32_t y = 0;
+      if (lane < l) {
+        y = A.col[A.off[u] + lane];
+        q = y != u && par[y] == X && stL[y] != epL;
+      }
+      const unsigned mask = __ballot_sync(0xffffffffu, q);
+      const int before = __popc(mask & ((1u << lane) - 1u));
+      if (q && before < UF_SAMPLE - taken) uf_union(comp, u, y);
+      taken += min(__popc(mask), UF_SAMPLE - taken);
+    }
+  }
+}
+
+template <class WT>
+__global__ void k_uf(Adj<WT> out, Adj<WT> in, ChunkMap m, const int32_t* par, const uint8_t* alive,
+                     const int32_t* stL, int32_t epL, int32_t* comp) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -455,17 +504,16 @@ __global__ void k_uf(Adj<WT> out, Adj<WT> in, ChunkMap m, const int32_t* par, co
     if (ch.row < 0) continue;
     const int32_t u = ch.v;
     const int32_t X = par[u];
+    // the community's seed node X is a member when it is alive, stays and is
+    // its own parent (then the members gathering set its tree)
+    const bool seed = alive[X] && stL[X] != epL && par[X] == X;
+    if (seed && uf_find(comp, u, true) == uf_find(comp, X, true)) continue;
     const Adj<WT>& A = ch.row ? in : out;
     const int64_t o = A.off[u];
     for (int32_t k = ch.k0 + lane; k < ch.k1; k += 32) {
       const int32_t y = A.col[o + k];
-      if (y <= u || par[y] != X || stL[y] == epL) continue;  // each pair once, from its lower end
-      for (;;) {
-        const int32_t a = uf_find(comp, u, true), b = uf_find(comp, y, true);
-        if (a == b) break;
-        const int32_t hi = a > b ? a : b, lo = a > b ? b : a;
-        if (atomicCAS(&comp[hi], hi, lo) == hi) break;
-      }
+      if (y == u || par[y] != X || stL[y] == epL) continue;
+      uf_union(comp, u, y);
     }
   }
 }
@@ -1174,8 +1222,13 @@ static void leave_degree(ldl_ctx& c, int r, Adj<WT> out, Adj<WT> in, int32_t nD,
 
 template <class WT>
 static void union_find(ldl_ctx& c, int r, Adj<WT> out, Adj<WT> in, int32_t nG, int32_t epL) {
+  LevelState& L = c.lv[r];
+  k_uf_sample<WT><<<grid_for((int64_t)nG * 32, TPB, 16), TPB, 0, c.s>>>(out, in, c.directed, c.lG.p, c.dcnt + K_G,
+                                                                       L.par.p, c.stL.p, epL, c.comp.p);
+  CKL("k_uf_sample");
   ChunkMap m = chunk_map(c, c.lG.p, c.dcnt + K_G, nG, out.len, c.directed ? in.len : nullptr);
-  k_uf<WT><<<grid_for((int64_t)nG * 64, TPB, 16), TPB, 0, c.s>>>(out, in, m, c.lv[r].par.p, c.stL.p, epL, c.comp.p);
+  k_uf<WT><<<grid_for((int64_t)nG * 64, TPB, 16), TPB, 0, c.s>>>(out, in, m, L.par.p, L.alive.p, c.stL.p, epL,
+                                                                  c.comp.p);
   CKL("k_uf");
 }
 
