@@ -109,7 +109,7 @@ class ClockSampler:
         self.p = None
         try:
             self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                                       "-i", str(index), "-lms", "200"], stdout=subprocess.PIPE,
+                                       "-i", str(index), "-lms", "50"], stdout=subprocess.PIPE,
                                       stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.p = None
@@ -606,7 +606,8 @@ def run_autotune(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default: 50 for the R-MAT stream and its reference arm, else 20)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -629,6 +630,8 @@ def main():
     ap.add_argument("--c5-div", type=int, default=4,
                     help="c5: log2 of the factor the 214M-vertex / 3.30B-edge recipe is scaled down by")
     args = ap.parse_args()
+    if args.steps is None:
+        args.steps = 50 if args.workload == "rmat" else 20
     _set_rmat_scale(args.rmat_scale)
     if args.impl == "reference":
         return run_reference(args)
